@@ -1,0 +1,179 @@
+/*
+ * fraclap.h -- C ABI of the GB300 library for the dense P1 finite element
+ * matrix of the integral fractional Laplacian (-Δ)^s on a polygon (d = 2) or
+ * interval (d = 1) with zero exterior data, and the dense linear algebra of its
+ * iterative solvers.
+ *
+ * Method: Ainsworth & Glusa, "Towards an efficient finite element method for the
+ * integral fractional Laplacian on polygonal domains" (arXiv:1708.03912).
+ *   - operator, constant C(d,s), bilinear form a(u,v) with the boundary term:
+ *     Section 2;
+ *   - P1 space V_h, degree-of-freedom set I_h, A^s_ij = a(phi_i, phi_j): Section 3;
+ *   - element-pair decomposition (eqs. elementPair, elementPairBoundary),
+ *     singular quadrature of touching pairs, diagonal scaling and conjugate
+ *     gradients: Section 5;
+ *   - quadrature orders: Appendix B (here fixed per class, see fl_options).
+ *
+ * Conventions for every entry point:
+ *   - return value: FL_OK (0) or one of the FL_E* codes below; a message is kept
+ *     per handle and returned by fl_last_error().  No call aborts, throws across
+ *     the ABI or traps on the device.
+ *   - pointers named *_dev are device pointers (cudaMalloc / PyTorch memory on the
+ *     current device); pointers named *_host are host pointers.  The caller owns
+ *     every buffer it passes; the library never frees or keeps them after the call
+ *     returns (work queued on `stream` may still read/write them until the stream
+ *     reaches that point).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All device work is enqueued on it; calls return without synchronising
+ *     unless stated.
+ *   - dense matrices are row-major with leading dimension `lda` (elements,
+ *     lda >= n).  The stiffness matrix is symmetric and stored in full.
+ *   - DOF order: increasing vertex index over the vertices in I_h (fl_dof_vertices).
+ */
+#ifndef FRACLAP_H
+#define FRACLAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FL_OK        0
+#define FL_EINVAL    1  /* bad argument, s outside (0,1), degenerate/inverted or non-conforming mesh */
+#define FL_ENOMEM    2  /* device or host allocation failed */
+#define FL_ECUDA     3  /* a CUDA runtime call or kernel launch failed */
+#define FL_ENOTSPD   4  /* CG breakdown: p^T A p <= 0 */
+#define FL_ENOTCONV  5  /* iteration limit reached before the tolerance */
+#define FL_ETIMEOUT  6  /* a bounded device wait gave up */
+#define FL_ENOTIMPL  7  /* combination of options not implemented */
+
+/* degree-of-freedom rule (Section 3) */
+#define FL_DOF_INTERIOR 0 /* interior vertices for every s (default) */
+#define FL_DOF_PAPER    1 /* all vertices if s < 1/2, interior vertices otherwise */
+
+/* arithmetic of the separated-pair quadrature */
+#define FL_FP64  0 /* every step in float64 */
+#define FL_MIXED 1 /* separated pairs (element/element and element/far facet) evaluated in
+                      float32 and summed in float64; touching pairs, near facets and all
+                      reductions in float64 */
+
+/* storage types for matrices handed to fl_matvec / fl_convert */
+#define FL_F64  0
+#define FL_F32  1
+#define FL_BF16 2
+
+typedef struct fl_options {
+    int k_far;    /* Gauss order per dimension, separated pairs at vertex-graph distance >= 2 (default 4) */
+    int k_near;   /* separated pairs at vertex-graph distance 1 and near boundary facets (default 6) */
+    int k_touch;  /* touching element pairs, remaining regular variables (default 8) */
+    int k_bnd;    /* element/boundary-facet pairs that touch (default 8) */
+    int regional; /* 1: drop the boundary term (regional fractional Laplacian, Section 2) */
+} fl_options;
+
+typedef struct fl_ctx* fl_handle;
+
+/* Fill *opt with the defaults listed above. */
+void fl_default_options(fl_options* opt);
+
+/*
+ * Create a handle for a mesh (Section 3).  dim = 1 or 2; vertices_host is
+ * [n_vertices][dim] float64; cells_host is [n_cells][dim+1] int32 vertex indices.
+ * The arrays are copied.  Cells are re-oriented (counter-clockwise / left-to-right).
+ * Boundary facets are the facets owned by exactly one cell.  The host planner runs
+ * here (classification of element pairs, tables); device tables are uploaded lazily
+ * by the first device call.  opt may be NULL (defaults).
+ * Errors: FL_EINVAL for dim not in {1,2}, indices out of range, degenerate cells,
+ * edges shared by more than two triangles, dof_mode unknown, orders outside [1,32].
+ */
+int fl_create(fl_handle* h, int dim, int64_t n_vertices, const double* vertices_host,
+              int64_t n_cells, const int32_t* cells_host, int dof_mode, const fl_options* opt);
+
+/* Release the handle and every device buffer it owns (synchronises the device). */
+void fl_destroy(fl_handle h);
+
+/* Last error message of the handle ("" if none); valid until the next call on h. */
+const char* fl_last_error(fl_handle h);
+
+/* Number n of degrees of freedom for order s (depends on s only under FL_DOF_PAPER). */
+int fl_num_dofs(fl_handle h, double s, int64_t* n);
+
+/* vertex_of_dof_host[n]: the vertex index of each DOF (increasing). */
+int fl_dof_vertices(fl_handle h, double s, int32_t* vertex_of_dof_host);
+
+/*
+ * Dense stiffness matrix A^s_ij = a(phi_i, phi_j) (Sections 2, 3, 5) into
+ * A_dev[n][lda] (float64, full symmetric storage), by element-pair quadrature:
+ * separated pairs with collapsed Gauss rules, touching pairs with regularised
+ * rules whose radial integral is exact, boundary term over the boundary facets.
+ * precision = FL_FP64 or FL_MIXED.  Deterministic: the same call on the same
+ * device gives bitwise identical results (no floating-point atomics).
+ * The handle owns a scratch workspace sized at the first call for this mesh.
+ * Errors: FL_EINVAL (s not in (0,1), lda < n, NULL A), FL_ENOTIMPL (2D with
+ * FL_DOF_PAPER and s < 1/2 unless regional), FL_ENOMEM, FL_ECUDA.
+ */
+int fl_assemble(fl_handle h, double s, int precision, double* A_dev, int64_t lda, void* stream);
+
+/*
+ * Load vector b = ∫ f phi_i (Section 5, system A u = b) into b_dev[n][ldb]
+ * (column r at b_dev + r, row-major n x nrhs).  f_nodal_dev NULL: f = 1 (nrhs must
+ * be 1); else f_nodal_dev is [n_vertices][nrhs] float64 nodal values and f is their
+ * P1 interpolant, b = M f with the P1 mass matrix.
+ */
+int fl_load_vector(fl_handle h, double s, const double* f_nodal_dev, int nrhs,
+                   double* b_dev, int64_t ldb, void* stream);
+
+/*
+ * Y = A X for a dense n x n matrix stored as dtype (FL_F64 / FL_F32 / FL_BF16) with
+ * leading dimension lda; X_dev, Y_dev are [n][nrhs] float64 row-major with leading
+ * dimensions ldx, ldy (>= nrhs).  Accumulation in float64 (FL_F64) or float32 with
+ * float64 per-row totals (FL_F32, FL_BF16).  Streams A once per call.
+ */
+int fl_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, int nrhs,
+              const double* X_dev, int64_t ldx, double* Y_dev, int64_t ldy, void* stream);
+
+/* A_lo_dev (dtype FL_F32 or FL_BF16, leading dimension ld_lo) = A_dev rounded to nearest. */
+int fl_convert(const double* A_dev, int64_t lda, int64_t n, int dtype, void* A_lo_dev,
+               int64_t ld_lo, void* stream);
+
+typedef struct fl_solve_opts {
+    double tol;        /* stop at ||b - A u||_2 <= tol ||b||_2 (default 1e-8) */
+    int maxit;         /* iteration limit of the outer solver (default 10000) */
+    int inner_dtype;   /* FL_F64: plain Jacobi-PCG on A (Section 5); FL_F32: Jacobi-PCG on a
+                          float32 copy inside float64 iterative refinement */
+    const void* A_lo_dev; /* the float32 copy (required when inner_dtype = FL_F32) */
+    int64_t ld_lo;
+    double inner_tol;  /* relative tolerance of each inner solve (default 1e-4) */
+    int inner_maxit;   /* default 2000 */
+} fl_solve_opts;
+
+typedef struct fl_solve_info {
+    int iterations;        /* total (inner) CG iterations */
+    int outer_iterations;  /* refinement steps (1 for plain CG) */
+    double rel_residual;   /* final ||b - A u|| / ||b|| computed in float64 with A */
+    int status;            /* FL_OK, FL_ENOTCONV or FL_ENOTSPD */
+} fl_solve_info;
+
+void fl_default_solve_opts(fl_solve_opts* o);
+
+/*
+ * Solve A u = b for one right-hand side with diagonally preconditioned conjugate
+ * gradients (Section 5; κ(D^-1 A) = O(n^{2s/d}), so O(n^{s/d}) iterations).
+ * A_dev is the float64 matrix (n x n, lda); b_dev, u_dev are [n] float64 (u is
+ * overwritten; the iteration starts from 0).  With inner_dtype = FL_F32 (or
+ * FL_BF16) the Jacobi-PCG runs on the low-precision copy o->A_lo_dev inside float64
+ * iterative refinement u += d, M d = b - A u, until ||b - A u|| <= tol ||b|| with
+ * the float64 A.  The iteration runs on the device; the host reads the scalars
+ * once per iteration.  h supplies the workspace (grown on demand) and the error
+ * message.  info (host) receives counts and the final residual, computed afresh in
+ * float64.  Synchronises `stream`.  Returns FL_OK, FL_ENOTCONV, FL_ENOTSPD,
+ * FL_EINVAL, FL_ENOMEM or FL_ECUDA.
+ */
+int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const double* b_dev, double* u_dev,
+             const fl_solve_opts* o, fl_solve_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FRACLAP_H */

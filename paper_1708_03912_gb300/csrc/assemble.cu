@@ -1,0 +1,1360 @@
+// Dense stiffness matrix of the integral fractional Laplacian by element-pair
+// quadrature (arXiv:1708.03912, Sections 2, 3, 5; Appendix B for the orders).
+//
+// Pipeline of fl_assemble (all on the caller's stream, fixed summation orders):
+//   prep_points    quadrature offsets x_a - c_K of the far rule per cell
+//   far_tile       separated pairs at vertex-graph distance >= 2: one warp per
+//                  32x32 tile of cells (lane = column cell, loop over row cells),
+//                  off-diagonal 3x3 blocks into lane-private shared memory, then a
+//                  per-tile partial block over the tile's local DOF lists; row/column
+//                  sums of the kernel for the diagonal blocks
+//   near_pairs     separated pairs at distance 1 (order k_near), one thread each
+//   touch_pairs    common-edge / common-vertex pairs, float64, one thread each
+//   bnd_far        element x far boundary facet sums (2D), one warp per 32 cells
+//   element        per cell: diagonal block from the row sums, identical pair,
+//                  boundary term (near/touching facets in float64)
+//   gather_csr     sparse near-field values from the contribution slots
+//   compose        dense A = far partials (fixed order) + near-field values
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "context.h"
+#include "device.h"
+
+namespace fl {
+
+#define FL_CUDA_TRY(h, x)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (x);                                                               \
+        if (e_ != cudaSuccess) return set_err(h, FL_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int set_err(fl_ctx* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+// ------------------------------------------------------------------ tables --
+struct RuleOffsets {
+    int qf, qn, kf, kn, kt, kb;
+    int64_t far_lam, far_w, far_phi;
+    int64_t near_lam, near_w, near_phi;
+    int64_t glf_t, glf_w, gln_t, gln_w;   // Gauss points on facets
+    int64_t t_edge, t_vert, t_1d, t_ident, b_own, b_vert;
+    int n_edge, n_vert, n_1d, n_ident, n_own, n_bvert;
+};
+
+template <typename T, int Q, int NV>
+struct FarRule {
+    T w[Q];          // reference weights
+    T wphi[Q * NV];  // reference weight x shape value
+};
+
+// ------------------------------------------------------------- far field --
+template <typename T>
+struct FarArgs {
+    const double* cen;
+    const T* pts;
+    const double* jac;
+    const char* hasdof;
+    const int* loc;
+    const int* ex_ptr;
+    const int* ex_idx;
+    const int* tiles;
+    const int64_t* toff;
+    const int* L_ptr;
+    const int* inc_ptr;
+    const int* inc_ent;
+    T* P;
+    T* Pd;
+    int64_t nc;
+    T expo;
+};
+
+// offsets x_a - c_K of the far rule in the arithmetic type T
+template <typename T, int D>
+__global__ void prep_points(const double* cvx, const double* cen, const double* lam, int q, int64_t nc, T* pts) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nc) return;
+    const double* v = cvx + k * (D + 1) * D;
+    for (int a = 0; a < q; ++a) {
+        for (int d = 0; d < D; ++d) {
+            double x;
+            if (D == 1) x = v[0] + lam[a] * (v[1] - v[0]);
+            else x = v[d] + lam[2 * a] * (v[2 + d] - v[d]) + lam[2 * a + 1] * (v[4 + d] - v[d]);
+            pts[(k * q + a) * D + d] = (T)(x - cen[k * D + d]);
+        }
+    }
+}
+
+template <int D, typename T, int Q, int PW>
+__global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const FarRule<T, Q, D + 1> R, int maxL) {
+    constexpr int NV = D + 1;
+    constexpr int QW = (Q + 31) / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x;
+    const int tix = blockIdx.x;
+    const int I = A.tiles[2 * tix], J = A.tiles[2 * tix + 1];
+    const int nLI = A.L_ptr[I + 1] - A.L_ptr[I];
+    const int nLJ = A.L_ptr[J + 1] - A.L_ptr[J];
+    const int64_t nc = A.nc;
+    const int64_t K0 = (int64_t)I * 32, Kt0 = (int64_t)J * 32;
+    const int nI = (int)min((int64_t)32, nc - K0);
+
+    double* sCen = reinterpret_cast<double*>(smem_raw);      // 32*D
+    double* sJac = sCen + 32 * D;                             // 32
+    T* sPts = reinterpret_cast<T*>(sJac + 32);                // 32*Q*D
+    T* sD = sPts + 32 * Q * D;                                // 32*Q (diagonal tile)
+    T* priv = sD + 32 * Q;                                    // NV*maxL*32
+    int* sLoc = reinterpret_cast<int*>(priv + NV * maxL * 32);  // 32*NV
+    int* sHas = sLoc + 32 * NV;                               // 32
+
+    for (int i = lane; i < nI * Q * D; i += 32) sPts[i] = A.pts[K0 * Q * D + i];
+    for (int i = lane; i < nI * D; i += 32) sCen[i] = A.cen[K0 * D + i];
+    for (int i = lane; i < nI * NV; i += 32) sLoc[i] = A.loc[K0 * NV + i];
+    if (lane < nI) {
+        sJac[lane] = A.jac[K0 + lane];
+        sHas[lane] = A.hasdof[K0 + lane];
+    }
+    for (int i = lane; i < NV * nLI * 32; i += 32) priv[i] = T(0);
+    for (int i = lane; i < 32 * Q; i += 32) sD[i] = T(0);
+    __syncwarp();
+
+    const int64_t Kt = Kt0 + lane;
+    const bool valid = Kt < nc;
+    T pj[Q][D];
+    double cj[D];
+    T wj = T(0);
+    bool hj = false;
+    int ep = 0, ee = 0;
+    if (valid) {
+#pragma unroll
+        for (int b = 0; b < Q; ++b)
+#pragma unroll
+            for (int d = 0; d < D; ++d) pj[b][d] = A.pts[(Kt * Q + b) * D + d];
+#pragma unroll
+        for (int d = 0; d < D; ++d) cj[d] = A.cen[Kt * D + d];
+        wj = (T)A.jac[Kt];
+        hj = A.hasdof[Kt] != 0;
+        ep = A.ex_ptr[Kt];
+        ee = A.ex_ptr[Kt + 1];
+    } else {
+#pragma unroll
+        for (int b = 0; b < Q; ++b)
+#pragma unroll
+            for (int d = 0; d < D; ++d) pj[b][d] = T(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) cj[d] = 0.0;
+    }
+    T S[Q];
+#pragma unroll
+    for (int b = 0; b < Q; ++b) S[b] = T(0);
+
+    for (int kk = 0; kk < nI; ++kk) {
+        const int64_t K = K0 + kk;
+        bool act = valid && (I != J || kk < lane);
+        if (act) {
+            while (ep < ee && A.ex_idx[ep] < K) ++ep;
+            if (ep < ee && A.ex_idx[ep] == K) act = false;
+        }
+        act = act && (hj || sHas[kk] != 0);
+        const bool any = __any_sync(0xffffffffu, act);
+        T myD[QW];
+#pragma unroll
+        for (int w = 0; w < QW; ++w) myD[w] = T(0);
+        if (any) {
+            T dct[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) dct[d] = (T)(sCen[kk * D + d] - cj[d]);
+            const T wK = (T)sJac[kk];
+            T off[NV][NV];
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+#pragma unroll
+                for (int j = 0; j < NV; ++j) off[i][j] = T(0);
+#pragma unroll 1
+            for (int a = 0; a < Q; ++a) {
+                T xa[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) xa[d] = dct[d] + sPts[(kk * Q + a) * D + d];
+                T t[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) t[v] = T(0);
+                const T wa = R.w[a] * wK;
+#pragma unroll
+                for (int b = 0; b < Q; ++b) {
+                    T r2 = T(0);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        T df = xa[d] - pj[b][d];
+                        r2 = fma(df, df, r2);
+                    }
+                    T kv = kpow<PW>(r2, A.expo);
+                    kv = act ? kv : T(0);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) t[v] = fma(R.wphi[b * NV + v], kv, t[v]);
+                    S[b] = fma(wa, kv, S[b]);
+                }
+                T u = t[0];
+#pragma unroll
+                for (int v = 1; v < NV; ++v) u += t[v];
+                u = warp_sum(u * wj);
+#pragma unroll
+                for (int w = 0; w < QW; ++w)
+                    if (a == w * 32 + lane) myD[w] = u;
+#pragma unroll
+                for (int i = 0; i < NV; ++i)
+#pragma unroll
+                    for (int j = 0; j < NV; ++j) off[i][j] = fma(R.wphi[a * NV + i], t[j], off[i][j]);
+            }
+            if (act) {
+                const T sc = wK * wj;
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                    const int li = sLoc[kk * NV + i];
+                    if (li >= 0) {
+#pragma unroll
+                        for (int j = 0; j < NV; ++j) priv[(j * nLI + li) * 32 + lane] += off[i][j] * sc;
+                    }
+                }
+            }
+        }
+        // row sums of cell K from this tile's columns
+#pragma unroll
+        for (int w = 0; w < QW; ++w) {
+            const int a = w * 32 + lane;
+            if (a < Q) {
+                if (I == J) sD[kk * Q + a] += myD[w];
+                else A.Pd[((int64_t)J * nc + K) * Q + a] = myD[w];
+            }
+        }
+    }
+    __syncwarp();
+    if (valid) {
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            T v = S[b];
+            if (I == J) v += sD[lane * Q + b];
+            A.Pd[((int64_t)I * nc + Kt) * Q + b] = v;
+        }
+    }
+    // partial block over the local DOF lists of blocks I and J
+    T* Pt = A.P + A.toff[tix];
+    const int pJ = A.L_ptr[J];
+    for (int idx = lane; idx < nLI * nLJ; idx += 32) {
+        const int li = idx / nLJ, lj = idx - li * nLJ;
+        T acc = T(0);
+        for (int q = A.inc_ptr[pJ + lj]; q < A.inc_ptr[pJ + lj + 1]; ++q) {
+            const int e = A.inc_ent[q];
+            const int l = e / NV, j = e - l * NV;
+            acc += priv[(j * nLI + li) * 32 + l];
+        }
+        Pt[idx] = acc;
+    }
+}
+
+// ------------------------------------------------------------ near pairs --
+// Separated pairs at vertex-graph distance 1 with the order-k_near rule; one thread
+// per unordered pair.  Writes the off-diagonal block (scaled by -C) into the
+// contribution slots and the per-point row sums of both cells into Dn.
+template <int D, typename T, int PW>
+__global__ void near_pair_kernel(int nnear, const int* np_a, const int* np_b, const double* cvx, const double* cen,
+                                 const double* jac, const double* rule, RuleOffsets ro, T expo, double C,
+                                 double* contrib, int64_t slot0, double* Dn) {
+    constexpr int NV = D + 1;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnear) return;
+    const int q = ro.qn;
+    const double* lam = rule + ro.near_lam;
+    const double* w = rule + ro.near_w;
+    const double* phi = rule + ro.near_phi;
+    const int ka = np_a[p], kb = np_b[p];
+    // offsets of the vertices from the centroids, edge vectors, centroid difference
+    T e0a[D], e1a[D], e2a[D], e0b[D], e1b[D], e2b[D], dc[D];
+    const double* va = cvx + (int64_t)ka * NV * D;
+    const double* vb = cvx + (int64_t)kb * NV * D;
+    for (int d = 0; d < D; ++d) {
+        e0a[d] = (T)(va[d] - cen[(int64_t)ka * D + d]);
+        e0b[d] = (T)(vb[d] - cen[(int64_t)kb * D + d]);
+        e1a[d] = (T)(va[D + d] - va[d]);
+        e1b[d] = (T)(vb[D + d] - vb[d]);
+        e2a[d] = (D == 2) ? (T)(va[2 * D + d] - va[d]) : T(0);
+        e2b[d] = (D == 2) ? (T)(vb[2 * D + d] - vb[d]) : T(0);
+        dc[d] = (T)(cen[(int64_t)ka * D + d] - cen[(int64_t)kb * D + d]);
+    }
+    double S[MAXQ_NEAR];
+    for (int b = 0; b < q; ++b) S[b] = 0.0;
+    double off[NV][NV];
+    for (int i = 0; i < NV; ++i)
+        for (int j = 0; j < NV; ++j) off[i][j] = 0.0;
+    const double ja = jac[ka], jb = jac[kb];
+    double* Da = Dn + ((int64_t)p * 2 + 0) * q;
+    double* Db = Dn + ((int64_t)p * 2 + 1) * q;
+    for (int a = 0; a < q; ++a) {
+        T xa[D];
+        for (int d = 0; d < D; ++d) {
+            xa[d] = dc[d] + e0a[d] + (T)lam[a * D] * e1a[d];
+            if (D == 2) xa[d] += (T)lam[a * D + 1] * e2a[d];
+        }
+        T t[NV];
+        for (int v = 0; v < NV; ++v) t[v] = T(0);
+        const T wa = (T)w[a];
+        for (int b = 0; b < q; ++b) {
+            T r2 = T(0);
+            for (int d = 0; d < D; ++d) {
+                T yb = e0b[d] + (T)lam[b * D] * e1b[d];
+                if (D == 2) yb += (T)lam[b * D + 1] * e2b[d];
+                T df = xa[d] - yb;
+                r2 = fma(df, df, r2);
+            }
+            T kv = kpow<PW>(r2, expo);
+            for (int v = 0; v < NV; ++v) t[v] = fma((T)(w[b] * phi[b * NV + v]), kv, t[v]);
+            S[b] += (double)(wa * kv);
+        }
+        double u = 0.0;
+        for (int v = 0; v < NV; ++v) u += (double)t[v];
+        Da[a] = jb * u;
+        for (int i = 0; i < NV; ++i)
+            for (int j = 0; j < NV; ++j) off[i][j] += w[a] * phi[a * NV + i] * (double)t[j];
+    }
+    for (int b = 0; b < q; ++b) Db[b] = ja * S[b];
+    double* out = contrib + slot0 + (int64_t)p * NV * NV;
+    for (int i = 0; i < NV; ++i)
+        for (int j = 0; j < NV; ++j) out[i * NV + j] = -C * ja * jb * off[i][j];
+}
+
+// ---------------------------------------------------------- touching pairs --
+// Common edge / common vertex pairs (2D) and common vertex pairs (1D), float64.
+// Tables (per s) hold the angular / Duffy points with the exact radial factor
+// already folded into their weights.
+template <int PW>
+__global__ void touch_pair_kernel(int ntp, int dim, const int* tp_type, const int* tp_vert, const int* tp_cell,
+                                  const int64_t* tp_slot, const double* V, const double* jac_orig,
+                                  const double* rule, RuleOffsets ro, double s, double C, double* contrib) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ntp) return;
+    const int type = tp_type[p];
+    const int* tv = tp_vert + 5 * p;
+    double* out = contrib + tp_slot[p];
+    const double jK = jac_orig[tp_cell[2 * p]], jM = jac_orig[tp_cell[2 * p + 1]];
+    if (type == 2) {  // 1D common vertex: [a, v, b], h1 = left, h2 = right
+        const double* tb = rule + ro.t_1d;
+        const double h1 = jK, h2 = jM;
+        const double e = -1.0 - 2.0 * s;
+        double acc[3][3] = {};
+        for (int m = 0; m < ro.n_1d; ++m) {
+            const double eta = tb[2 * m], wt = tb[2 * m + 1];
+            const double d1[3] = {1.0, -1.0 + eta, -eta};
+            const double d2[3] = {eta, 1.0 - eta, -1.0};
+            const double k1 = wt * pow(h1 + h2 * eta, e), k2 = wt * pow(h1 * eta + h2, e);
+            for (int i = 0; i < 3; ++i)
+                for (int j = i; j < 3; ++j) acc[i][j] += k1 * d1[i] * d1[j] + k2 * d2[i] * d2[j];
+        }
+        const double sc = C * h1 * h2 / (3.0 - 2.0 * s);
+        for (int i = 0; i < 3; ++i)
+            for (int j = i; j < 3; ++j) out[i * 3 + j] = out[j * 3 + i] = sc * acc[i][j];
+        return;
+    }
+    const double e2 = -(1.0 + s);
+    if (type == 0) {  // common edge [P,Q], thirds R (K) and Rt (M)
+        const double *P_ = V + 2 * tv[0], *Q_ = V + 2 * tv[1], *R_ = V + 2 * tv[2], *Rt = V + 2 * tv[3];
+        const double a[2] = {Q_[0] - P_[0], Q_[1] - P_[1]};
+        const double b[2] = {R_[0] - Q_[0], R_[1] - Q_[1]};
+        const double c[2] = {-(Rt[0] - Q_[0]), -(Rt[1] - Q_[1])};
+        const double* tb = rule + ro.t_edge;
+        double acc[4][4] = {};
+        for (int m = 0; m < ro.n_edge; ++m) {
+            const double* r = tb + 8 * m;  // dphi[4], w1, w2, w3, weight
+            const double x = a[0] * r[4] + b[0] * r[5] + c[0] * r[6];
+            const double y = a[1] * r[4] + b[1] * r[5] + c[1] * r[6];
+            const double f = r[7] * kpow<PW>(x * x + y * y, e2);
+            for (int i = 0; i < 4; ++i)
+                for (int j = i; j < 4; ++j) acc[i][j] += f * r[i] * r[j];
+        }
+        const double sc = C * jK * jM / ((3.0 - 2.0 * s) * (4.0 - 2.0 * s));
+        for (int i = 0; i < 4; ++i)
+            for (int j = i; j < 4; ++j) out[i * 4 + j] = out[j * 4 + i] = sc * acc[i][j];
+    } else {  // common vertex P: K = (P,Q,R), M = (P,Qt,Rt)
+        const double *P_ = V + 2 * tv[0], *Q_ = V + 2 * tv[1], *R_ = V + 2 * tv[2], *Qt = V + 2 * tv[3], *Rt = V + 2 * tv[4];
+        const double a1[2] = {Q_[0] - P_[0], Q_[1] - P_[1]};
+        const double a2[2] = {R_[0] - Q_[0], R_[1] - Q_[1]};
+        const double a3[2] = {-(Qt[0] - P_[0]), -(Qt[1] - P_[1])};
+        const double a4[2] = {-(Rt[0] - Qt[0]), -(Rt[1] - Qt[1])};
+        const double* tb = rule + ro.t_vert;
+        double acc[5][5] = {};
+        for (int m = 0; m < ro.n_vert; ++m) {
+            const double* r = tb + 10 * m;  // dphi[5], x1, x2, y1, y2, weight
+            const double x = a1[0] * r[5] + a2[0] * r[6] + a3[0] * r[7] + a4[0] * r[8];
+            const double y = a1[1] * r[5] + a2[1] * r[6] + a3[1] * r[7] + a4[1] * r[8];
+            const double f = r[9] * kpow<PW>(x * x + y * y, e2);
+            for (int i = 0; i < 5; ++i)
+                for (int j = i; j < 5; ++j) acc[i][j] += f * r[i] * r[j];
+        }
+        const double sc = C * jK * jM / (4.0 - 2.0 * s);
+        for (int i = 0; i < 5; ++i)
+            for (int j = i; j < 5; ++j) out[i * 5 + j] = out[j * 5 + i] = sc * acc[i][j];
+    }
+}
+
+// ------------------------------------------------------ boundary, far facets --
+// 2D: for each cell (lane) the sums B_a = Σ_e Σ_b w_b n_e·(x_a - y_b) |x_a - y_b|^{-2-2s}
+// over all boundary facets not listed as touching/near for that cell.
+template <typename T, int Q, int PW>
+__global__ void __launch_bounds__(32) bnd_far_kernel(int64_t nc, int64_t nf, const double* cen, const T* pts,
+                                                      const char* hasdof, const int* ef_ptr, const int* ef_fac,
+                                                      const int* F, const double* FN, const double* FLEN,
+                                                      const double* V, const double* rule, RuleOffsets ro, T expo,
+                                                      double* Bf) {
+    const int lane = threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * 32 + lane;
+    const bool valid = k < nc && hasdof[k];
+    if (!__any_sync(0xffffffffu, valid)) return;
+    T xa[Q][2];
+    double c[2] = {0.0, 0.0};
+    int ep = 0, ee = 0;
+    if (valid) {
+        for (int a = 0; a < Q; ++a) {
+            xa[a][0] = pts[(k * Q + a) * 2];
+            xa[a][1] = pts[(k * Q + a) * 2 + 1];
+        }
+        c[0] = cen[2 * k];
+        c[1] = cen[2 * k + 1];
+        ep = ef_ptr[k];
+        ee = ef_ptr[k + 1];
+    } else {
+        for (int a = 0; a < Q; ++a) xa[a][0] = xa[a][1] = T(0);
+    }
+    const int kf = ro.kf;
+    const double* gt = rule + ro.glf_t;
+    const double* gw = rule + ro.glf_w;
+    double B[Q];
+    T Bp[Q];
+    for (int a = 0; a < Q; ++a) B[a] = 0.0, Bp[a] = T(0);
+    int since = 0;
+    for (int64_t f = 0; f < nf; ++f) {
+        bool act = valid;
+        if (act) {
+            while (ep < ee && ef_fac[ep] < f) ++ep;
+            if (ep < ee && ef_fac[ep] == f) act = false;
+        }
+        const double* E0 = V + 2 * F[2 * f];
+        const double* E1 = V + 2 * F[2 * f + 1];
+        const T ex = (T)(E1[0] - E0[0]), ey = (T)(E1[1] - E0[1]);
+        const T nx = (T)FN[2 * f], ny = (T)FN[2 * f + 1];
+        const T dcx = (T)(c[0] - E0[0]), dcy = (T)(c[1] - E0[1]);
+        const T L = (T)FLEN[f];
+        for (int b = 0; b < kf; ++b) {
+            const T tb = (T)gt[b], wb = (T)gw[b] * L;
+            const T yx = tb * ex, yy = tb * ey;
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const T dx = dcx + xa[a][0] - yx, dy = dcy + xa[a][1] - yy;
+                T kv = kpow<PW>(fma(dx, dx, dy * dy), expo);
+                kv = act ? kv : T(0);
+                Bp[a] = fma(wb * (nx * dx + ny * dy), kv, Bp[a]);
+            }
+        }
+        if (++since == 32) {
+            for (int a = 0; a < Q; ++a) B[a] += (double)Bp[a], Bp[a] = T(0);
+            since = 0;
+        }
+    }
+    if (valid)
+        for (int a = 0; a < Q; ++a) Bf[k * Q + a] = B[a] + (double)Bp[a];
+}
+
+// ------------------------------------------------------------- per element --
+struct ElemArgs {
+    int dim;
+    int64_t nc, nblk, nf, nnear;
+    const double* cvx;
+    const double* cen;
+    const double* jac;
+    const char* hasdof;
+    const void* Pd;     // T
+    int pd_is_float;
+    const double* Dn;
+    const int* enp_ptr;
+    const int* enp_ent;
+    const double* Bf;
+    const int* ef_ptr;
+    const int* ef_fac;
+    const int* ef_cls;
+    const int* F;
+    const double* FN;
+    const double* FLEN;
+    const double* V;
+    const int* corner;  // nc*nvpc original vertex ids in internal order
+    const double* rule;
+    RuleOffsets ro;
+    double s, C;
+    int regional;
+    double* contrib;
+    int64_t slot0;
+};
+
+template <int PW>
+__global__ void element_kernel(ElemArgs A) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= A.nc || !A.hasdof[k]) return;
+    const int D = A.dim, NV = D + 1;
+    const RuleOffsets& ro = A.ro;
+    const double* rule = A.rule;
+    const double s = A.s, C = A.C;
+    const double* v = A.cvx + k * NV * D;
+    const double jk = A.jac[k];
+    double blk[3][3] = {};
+    const int qf = ro.qf, qn = ro.qn;
+    // diagonal block from the far row sums (fixed order over blocks)
+    {
+        const double* w = rule + ro.far_w;
+        const double* phi = rule + ro.far_phi;
+        for (int a = 0; a < qf; ++a) {
+            double Dk = 0.0;
+            if (A.pd_is_float) {
+                const float* Pd = (const float*)A.Pd;
+                for (int64_t B = 0; B < A.nblk; ++B) Dk += (double)Pd[(B * A.nc + k) * qf + a];
+            } else {
+                const double* Pd = (const double*)A.Pd;
+                for (int64_t B = 0; B < A.nblk; ++B) Dk += Pd[(B * A.nc + k) * qf + a];
+            }
+            double bf = (D == 2 && !A.regional) ? A.Bf[k * qf + a] : 0.0;
+            const double f = jk * w[a] * (C * Dk + C / (2.0 * s) * bf);
+            for (int i = 0; i < NV; ++i)
+                for (int j = i; j < NV; ++j) blk[i][j] += f * phi[a * NV + i] * phi[a * NV + j];
+        }
+    }
+    // near pairs (both roles) and near boundary facets, order-k_near points
+    {
+        const double* w = rule + ro.near_w;
+        const double* phi = rule + ro.near_phi;
+        const double* lam = rule + ro.near_lam;
+        double Bn[MAXQ_NEAR];
+        for (int a = 0; a < qn; ++a) Bn[a] = 0.0;
+        if (!A.regional) {
+            for (int q = A.ef_ptr[k]; q < A.ef_ptr[k + 1]; ++q) {
+                if (A.ef_cls[q] != 1) continue;
+                const int f = A.ef_fac[q];
+                for (int a = 0; a < qn; ++a) {
+                    double xa[2];
+                    for (int d = 0; d < D; ++d) {
+                        xa[d] = v[d] + lam[a * D] * (v[D + d] - v[d]);
+                        if (D == 2) xa[d] += lam[a * D + 1] * (v[2 * D + d] - v[d]);
+                    }
+                    if (D == 1) {
+                        const double y = A.V[A.F[f]];
+                        const double dx = xa[0] - y;
+                        Bn[a] += A.FN[f] * dx * pow(dx * dx, -(1.0 + 2.0 * s) / 2.0);
+                    } else {
+                        const double* E0 = A.V + 2 * A.F[2 * f];
+                        const double* E1 = A.V + 2 * A.F[2 * f + 1];
+                        const double* gt = rule + ro.gln_t;
+                        const double* gw = rule + ro.gln_w;
+                        double acc = 0.0;
+                        for (int b = 0; b < ro.kn; ++b) {
+                            const double yx = E0[0] + gt[b] * (E1[0] - E0[0]);
+                            const double yy = E0[1] + gt[b] * (E1[1] - E0[1]);
+                            const double dx = xa[0] - yx, dy = xa[1] - yy;
+                            acc += gw[b] * A.FLEN[f] * (A.FN[2 * f] * dx + A.FN[2 * f + 1] * dy) *
+                                   kpow<PW>(dx * dx + dy * dy, -(1.0 + s));
+                        }
+                        Bn[a] += acc;
+                    }
+                }
+            }
+        }
+        for (int a = 0; a < qn; ++a) {
+            double Dk = 0.0;
+            for (int q = A.enp_ptr[k]; q < A.enp_ptr[k + 1]; ++q) {
+                const int e = A.enp_ent[q];
+                Dk += A.Dn[(int64_t)e * qn + a];
+            }
+            const double f = jk * w[a] * (C * Dk + C / (2.0 * s) * Bn[a]);
+            for (int i = 0; i < NV; ++i)
+                for (int j = i; j < NV; ++j) blk[i][j] += f * phi[a * NV + i] * phi[a * NV + j];
+        }
+    }
+    // identical pair
+    if (D == 1) {
+        const double val = C * pow(jk, 1.0 - 2.0 * s) / ((2.0 - 2.0 * s) * (3.0 - 2.0 * s));
+        blk[0][0] += val;
+        blk[0][1] -= val;
+        blk[1][1] += val;
+    } else {
+        const double J00 = v[2] - v[0], J10 = v[3] - v[1], J01 = v[4] - v[0], J11 = v[5] - v[1];
+        const double* tb = rule + ro.t_ident;
+        double acc[3][3] = {};
+        for (int m = 0; m < ro.n_ident; ++m) {
+            const double u0 = tb[3 * m], u1 = tb[3 * m + 1], f0 = tb[3 * m + 2];
+            const double jx = J00 * u0 + J01 * u1, jy = J10 * u0 + J11 * u1;
+            const double f = f0 * kpow<PW>(jx * jx + jy * jy, -(1.0 + s));
+            const double g[3] = {-u0 - u1, u0, u1};
+            for (int i = 0; i < 3; ++i)
+                for (int j = i; j < 3; ++j) acc[i][j] += f * g[i] * g[j];
+        }
+        const double beta = 2.0 / ((2.0 - 2.0 * s) * (3.0 - 2.0 * s) * (4.0 - 2.0 * s));
+        const double sc = 0.5 * C * jk * jk * beta;
+        for (int i = 0; i < 3; ++i)
+            for (int j = i; j < 3; ++j) blk[i][j] += sc * acc[i][j];
+    }
+    // boundary facets: touching ones (and, in 1D, far ones)
+    if (!A.regional) {
+        const int* cv = A.corner + k * NV;
+        if (D == 1) {
+            const double* gt = rule + ro.glf_t;  // unused in 1D
+            (void)gt;
+            int ep = A.ef_ptr[k], ee = A.ef_ptr[k + 1];
+            const double* w = rule + ro.far_w;
+            const double* lam = rule + ro.far_lam;
+            const double* phi = rule + ro.far_phi;
+            for (int64_t f = 0; f < A.nf; ++f) {
+                int cls = 0;
+                while (ep < ee && A.ef_fac[ep] < f) ++ep;
+                if (ep < ee && A.ef_fac[ep] == f) cls = A.ef_cls[ep];
+                if (cls == 1) continue;  // near: done above
+                const int e = A.F[f];
+                if (cls == 2) {
+                    // e is an end of K: exact ∫ phi_i phi_j |x-e|^{-2s}
+                    const int me = (cv[0] == e) ? 0 : 1;
+                    double a_[2], b_[2];
+                    a_[me] = 1.0, a_[1 - me] = 0.0;
+                    b_[me] = -1.0, b_[1 - me] = 1.0;
+                    const double sc = C / (2.0 * s) * pow(jk, 1.0 - 2.0 * s);
+                    for (int i = 0; i < 2; ++i)
+                        for (int j = i; j < 2; ++j) {
+                            double val = (a_[i] * b_[j] + a_[j] * b_[i]) / (2.0 - 2.0 * s) + b_[i] * b_[j] / (3.0 - 2.0 * s);
+                            if (a_[i] * a_[j] != 0.0) val += a_[i] * a_[j] / (1.0 - 2.0 * s);
+                            blk[i][j] += sc * val;
+                        }
+                } else {
+                    const double y = A.V[e];
+                    for (int a = 0; a < qf; ++a) {
+                        const double x = v[0] + lam[a] * (v[1] - v[0]);
+                        const double dx = x - y;
+                        const double g = A.FN[f] * dx * pow(dx * dx, -(1.0 + 2.0 * s) / 2.0);
+                        const double fw = C / (2.0 * s) * jk * w[a] * g;
+                        for (int i = 0; i < 2; ++i)
+                            for (int j = i; j < 2; ++j) blk[i][j] += fw * phi[a * 2 + i] * phi[a * 2 + j];
+                    }
+                }
+            }
+        } else {
+            for (int q = A.ef_ptr[k]; q < A.ef_ptr[k + 1]; ++q) {
+                const int cls = A.ef_cls[q];
+                const int f = A.ef_fac[q];
+                if (cls == 2) {
+                    // facet is an edge of K; only the opposite vertex R can carry a DOF
+                    const int E0 = A.F[2 * f], E1 = A.F[2 * f + 1];
+                    int r = 0;
+                    for (int i = 0; i < 3; ++i)
+                        if (cv[i] != E0 && cv[i] != E1) r = i;
+                    const double* pE0 = A.V + 2 * E0;
+                    const double* pE1 = A.V + 2 * E1;
+                    const double* pR = A.V + 2 * cv[r];
+                    const double nx = A.FN[2 * f], ny = A.FN[2 * f + 1];
+                    const double H = nx * (pR[0] - pE1[0]) + ny * (pR[1] - pE1[1]);
+                    const double ax = pE1[0] - pE0[0], ay = pE1[1] - pE0[1];
+                    const double bx = pR[0] - pE1[0], by = pR[1] - pE1[1];
+                    const double* tb = rule + ro.b_own;
+                    double acc = 0.0;
+                    for (int m = 0; m < ro.n_own; ++m) {
+                        const double o1 = tb[3 * m], o2 = tb[3 * m + 1], wt = tb[3 * m + 2];
+                        const double x = ax * o1 + bx * o2, y = ay * o1 + by * o2;
+                        acc += wt * H * o2 * kpow<PW>(x * x + y * y, -(1.0 + s)) * o2 * o2;
+                    }
+                    blk[r][r] += C / (2.0 * s) * jk * A.FLEN[f] * acc / ((3.0 - 2.0 * s) * (4.0 - 2.0 * s));
+                } else if (cls == 3) {
+                    // facet and K share one vertex P
+                    const int fa = A.F[2 * f], fb = A.F[2 * f + 1];
+                    int ip = -1;
+                    for (int i = 0; i < 3; ++i)
+                        if (cv[i] == fa || cv[i] == fb) ip = i;
+                    const int P = cv[ip], E1 = (P == fa) ? fb : fa;
+                    const int iq = (ip + 1) % 3, ir = (ip + 2) % 3;
+                    const double* pP = A.V + 2 * P;
+                    const double* pQ = A.V + 2 * cv[iq];
+                    const double* pR = A.V + 2 * cv[ir];
+                    const double* pE = A.V + 2 * E1;
+                    const double nx = A.FN[2 * f], ny = A.FN[2 * f + 1];
+                    const double gq[2] = {pQ[0] - pP[0], pQ[1] - pP[1]};
+                    const double gr[2] = {pR[0] - pQ[0], pR[1] - pQ[1]};
+                    const double ge[2] = {pE[0] - pP[0], pE[1] - pP[1]};
+                    const double* tb = rule + ro.b_vert;
+                    // local order (P, Q, R): a = e_P, bh = (e_Q - e_P) x1 + (e_R - e_Q) x2
+                    double m0 = 0.0, m1[3] = {0, 0, 0}, m2[3][3] = {};
+                    for (int m = 0; m < ro.n_bvert; ++m) {
+                        const double x1 = tb[4 * m], x2 = tb[4 * m + 1], t = tb[4 * m + 2], wt = tb[4 * m + 3];
+                        const double xpx = gq[0] * x1 + gr[0] * x2, xpy = gq[1] * x1 + gr[1] * x2;
+                        const double N = xpx * nx + xpy * ny;
+                        const double dx = xpx - t * ge[0], dy = xpy - t * ge[1];
+                        const double g = wt * N * kpow<PW>(dx * dx + dy * dy, -(1.0 + s));
+                        const double bh[3] = {-x1, x1 - x2, x2};
+                        m0 += g;
+                        for (int i = 0; i < 3; ++i) {
+                            m1[i] += g * bh[i];
+                            for (int j = i; j < 3; ++j) m2[i][j] += g * bh[i] * bh[j];
+                        }
+                    }
+                    const double sc = C / (2.0 * s) * jk * A.FLEN[f];
+                    const int idx[3] = {ip, iq, ir};
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = i; j < 3; ++j) {
+                            const double ai = (i == 0) ? 1.0 : 0.0, aj = (j == 0) ? 1.0 : 0.0;
+                            double val = m2[i][j] / (4.0 - 2.0 * s) + (ai * m1[j] + aj * m1[i]) / (3.0 - 2.0 * s);
+                            if (ai * aj != 0.0) val += m0 / (2.0 - 2.0 * s);
+                            int I_ = idx[i], J_ = idx[j];
+                            if (I_ > J_) { int tmp = I_; I_ = J_; J_ = tmp; }
+                            blk[I_][J_] += sc * val;
+                        }
+                }
+            }
+        }
+    }
+    double* out = A.contrib + A.slot0 + k * NV * NV;
+    for (int i = 0; i < NV; ++i)
+        for (int j = i; j < NV; ++j) out[i * NV + j] = out[j * NV + i] = blk[i][j];
+}
+
+// ---------------------------------------------------- gather and compose --
+__global__ void gather_csr_kernel(int64_t nnz, const int* csr_row, const int* csr_col, const int64_t* g_ptr,
+                                  const int64_t* g_slot, const double* contrib, double* val) {
+    const int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (z >= nnz) return;
+    if (csr_col[z] < csr_row[z]) return;  // the upper entry serves both
+    double acc = 0.0;
+    for (int64_t q = g_ptr[z]; q < g_ptr[z + 1]; ++q) acc += contrib[g_slot[q]];
+    val[z] = acc;
+}
+
+template <typename T>
+__global__ void compose_far_kernel(int64_t n, int64_t nblk, const int* occ_ptr, const int* occ_blk,
+                                   const int* occ_loc, const int* L_ptr, const int64_t* toff, const T* P,
+                                   double negC, double* A, int64_t lda) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
+    const int64_t lo = min(i, j), hi = max(i, j);
+    double acc = 0.0;
+    for (int a = occ_ptr[lo]; a < occ_ptr[lo + 1]; ++a) {
+        const int64_t Ba = occ_blk[a];
+        const int la = occ_loc[a];
+        for (int b = occ_ptr[hi]; b < occ_ptr[hi + 1]; ++b) {
+            const int64_t Bb = occ_blk[b];
+            const int lb = occ_loc[b];
+            if (Ba < Bb) {
+                const int64_t t = Ba * nblk - Ba * (Ba - 1) / 2 + (Bb - Ba);
+                acc += (double)P[toff[t] + (int64_t)la * (L_ptr[Bb + 1] - L_ptr[Bb]) + lb];
+            } else if (Ba > Bb) {
+                const int64_t t = Bb * nblk - Bb * (Bb - 1) / 2 + (Ba - Bb);
+                acc += (double)P[toff[t] + (int64_t)lb * (L_ptr[Ba + 1] - L_ptr[Ba]) + la];
+            } else {
+                const int64_t t = Ba * nblk - Ba * (Ba - 1) / 2;
+                const int64_t nL = L_ptr[Ba + 1] - L_ptr[Ba];
+                acc += (double)P[toff[t] + (int64_t)la * nL + lb] + (double)P[toff[t] + (int64_t)lb * nL + la];
+            }
+        }
+    }
+    A[i * lda + j] = negC * acc;
+    }
+}
+
+__global__ void add_csr_kernel(int64_t nnz, const int* csr_row, const int* csr_col, const double* val, double* A,
+                               int64_t lda) {
+    const int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (z >= nnz) return;
+    const int64_t i = csr_row[z], j = csr_col[z];
+    if (j < i) return;
+    const double v = val[z];
+    A[i * lda + j] += v;
+    if (j != i) A[j * lda + i] += v;
+}
+
+// ---------------------------------------------------------------- host side --
+namespace {
+
+template <typename X>
+int upload(fl_ctx* h, X*& dst, const std::vector<X>& src) {
+    dst = nullptr;
+    size_t bytes = std::max<size_t>(1, src.size()) * sizeof(X);
+    cudaError_t e = cudaMalloc((void**)&dst, bytes);
+    if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    h->bufs.push_back({dst, bytes});
+    if (!src.empty()) {
+        e = cudaMemcpy(dst, src.data(), src.size() * sizeof(X), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return set_err(h, FL_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    }
+    return FL_OK;
+}
+
+int alloc(fl_ctx* h, void** dst, size_t bytes) {
+    *dst = nullptr;
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+    h->bufs.push_back({*dst, bytes});
+    return FL_OK;
+}
+
+#define FL_TRY(x)               \
+    do {                        \
+        int r_ = (x);           \
+        if (r_ != FL_OK) return r_; \
+    } while (0)
+
+int qf_of(const fl_ctx* h) { return h->dim == 1 ? h->opt.k_far : h->opt.k_far * h->opt.k_far; }
+int qn_of(const fl_ctx* h) { return h->dim == 1 ? h->opt.k_near : h->opt.k_near * h->opt.k_near; }
+
+int ensure_device(fl_ctx* h, int pi) {
+    DevTables& t = h->dev[pi];
+    if (t.ready) return FL_OK;
+    const Plan& P = h->plan[pi];
+    const int D = P.dim, NV = P.nvpc;
+    const int64_t nc = P.nc;
+    // internal-order geometry
+    std::vector<double> cvx(nc * NV * D), cen(nc * D), jac(nc);
+    std::vector<int> corner(nc * NV);
+    for (int64_t k = 0; k < nc; ++k) {
+        const int K = P.perm[k];
+        for (int a = 0; a < NV; ++a) {
+            const int vtx = P.C[(int64_t)K * NV + a];
+            corner[k * NV + a] = vtx;
+            for (int d = 0; d < D; ++d) cvx[(k * NV + a) * D + d] = P.V[(int64_t)vtx * D + d];
+        }
+        for (int d = 0; d < D; ++d) {
+            double sacc = 0;
+            for (int a = 0; a < NV; ++a) sacc += cvx[(k * NV + a) * D + d];
+            cen[k * D + d] = sacc / NV;
+        }
+        jac[k] = P.jac[K];
+    }
+    std::vector<int> csr_row(P.csr_col.size());
+    for (int64_t i = 0; i < P.n; ++i)
+        for (int z = P.csr_ptr[i]; z < P.csr_ptr[i + 1]; ++z) csr_row[z] = (int)i;
+    FL_TRY(upload(h, t.V, P.V));
+    FL_TRY(upload(h, t.jac_orig, P.jac));
+    FL_TRY(upload(h, t.F, P.F));
+    FL_TRY(upload(h, t.FN, P.FN));
+    FL_TRY(upload(h, t.FLEN, P.FLEN));
+    FL_TRY(upload(h, t.cvx, cvx));
+    FL_TRY(upload(h, t.cen, cen));
+    FL_TRY(upload(h, t.jac, jac));
+    FL_TRY(upload(h, t.hasdof, P.hasdof));
+    FL_TRY(upload(h, t.loc, P.loc));
+    FL_TRY(upload(h, t.cdof, P.cdof));
+    FL_TRY(upload(h, t.L_ptr, P.L_ptr));
+    FL_TRY(upload(h, t.inc_ptr, P.inc_ptr));
+    FL_TRY(upload(h, t.inc_ent, P.inc_ent));
+    FL_TRY(upload(h, t.tiles, P.tiles));
+    FL_TRY(upload(h, t.toff, P.toff));
+    FL_TRY(upload(h, t.occ_ptr, P.occ_ptr));
+    FL_TRY(upload(h, t.occ_blk, P.occ_blk));
+    FL_TRY(upload(h, t.occ_loc, P.occ_loc));
+    FL_TRY(upload(h, t.ex_ptr, P.ex_ptr));
+    FL_TRY(upload(h, t.ex_idx, P.ex_idx));
+    FL_TRY(upload(h, t.np_a, P.np_a));
+    FL_TRY(upload(h, t.np_b, P.np_b));
+    FL_TRY(upload(h, t.enp_ptr, P.enp_ptr));
+    FL_TRY(upload(h, t.enp_ent, P.enp_ent));
+    FL_TRY(upload(h, t.tp_type, P.tp_type));
+    FL_TRY(upload(h, t.tp_vert, P.tp_vert));
+    FL_TRY(upload(h, t.tp_cell, P.tp_cell));
+    FL_TRY(upload(h, t.tp_slot, P.tp_slot));
+    FL_TRY(upload(h, t.ef_ptr, P.ef_ptr));
+    FL_TRY(upload(h, t.ef_fac, P.ef_fac));
+    FL_TRY(upload(h, t.ef_cls, P.ef_cls));
+    FL_TRY(upload(h, t.csr_ptr, P.csr_ptr));
+    FL_TRY(upload(h, t.csr_col, P.csr_col));
+    FL_TRY(upload(h, t.csr_row, csr_row));
+    FL_TRY(upload(h, t.g_ptr, P.g_ptr));
+    FL_TRY(upload(h, t.g_slot, P.g_slot));
+    FL_TRY(upload(h, t.vod, P.vod));
+    FL_TRY(upload(h, t.corig, corner));
+    FL_TRY(upload(h, t.cells, P.C));
+    std::vector<int64_t> v2cp(P.v2c_ptr.begin(), P.v2c_ptr.end());
+    FL_TRY(upload(h, t.v2c_ptr, v2cp));
+    FL_TRY(upload(h, t.v2c, P.v2c));
+    const int qf = qf_of(h), qn = qn_of(h);
+    FL_TRY(alloc(h, &t.P, (size_t)P.toff.back() * sizeof(double)));
+    FL_TRY(alloc(h, &t.Pd, (size_t)P.nblk * nc * qf * sizeof(double)));
+    FL_TRY(alloc(h, &t.pts, (size_t)nc * qf * D * sizeof(double)));
+    FL_TRY(alloc(h, (void**)&t.Dn, (size_t)P.np_a.size() * 2 * qn * sizeof(double)));
+    FL_TRY(alloc(h, (void**)&t.Bf, (size_t)nc * qf * sizeof(double)));
+    FL_TRY(alloc(h, (void**)&t.contrib, (size_t)P.nslots * sizeof(double)));
+    FL_TRY(alloc(h, (void**)&t.csr_val, P.csr_col.size() * sizeof(double)));
+    t.ready = true;
+    return FL_OK;
+}
+
+// per-s rule tables, see RuleOffsets
+void build_rules(const fl_ctx* h, double s, std::vector<double>& buf, RuleOffsets& ro) {
+    const int D = h->dim;
+    const fl_options& o = h->opt;
+    buf.clear();
+    auto put = [&](const std::vector<double>& v) {
+        int64_t off = (int64_t)buf.size();
+        buf.insert(buf.end(), v.begin(), v.end());
+        return off;
+    };
+    Rule rf = make_rule(D, o.k_far), rn = make_rule(D, o.k_near);
+    ro.qf = rf.q;
+    ro.qn = rn.q;
+    ro.kf = o.k_far;
+    ro.kn = o.k_near;
+    ro.kt = o.k_touch;
+    ro.kb = o.k_bnd;
+    ro.far_lam = put(rf.lam);
+    ro.far_w = put(rf.w);
+    ro.far_phi = put(rf.phi);
+    ro.near_lam = put(rn.lam);
+    ro.near_w = put(rn.w);
+    ro.near_phi = put(rn.phi);
+    std::vector<double> t, w;
+    gauss01(o.k_far, t, w);
+    ro.glf_t = put(t);
+    ro.glf_w = put(w);
+    gauss01(o.k_near, t, w);
+    ro.gln_t = put(t);
+    ro.gln_w = put(w);
+    std::vector<double> tt, tw;
+    gauss01(o.k_touch, tt, tw);
+    const int kt = o.k_touch;
+    // common edge: four pieces of the l1 directions of (x1-y1, x2, y2)
+    {
+        std::vector<double> tab;
+        for (int piece = 0; piece < 4; ++piece)
+            for (int i = 0; i < kt; ++i)
+                for (int j = 0; j < kt; ++j) {
+                    const double u = tt[i], vv = tt[j], W = tw[i] * tw[j];
+                    double w2, w3, jacp, lam, sig;
+                    if (piece == 0) { sig = 1; w2 = u / 2; w3 = vv * (1 - w2); jacp = 0.5 * (1 - u / 2); lam = 1 - w2; }
+                    else if (piece == 1) { sig = 1; w2 = (1 + u) / 2; w3 = vv * (1 - w2); jacp = 0.25 * (1 - u); lam = w2; }
+                    else if (piece == 2) { sig = -1; w3 = u / 2; w2 = vv * (1 - w3); jacp = 0.5 * (1 - u / 2); lam = 1 - w3; }
+                    else { sig = -1; w3 = (1 + u) / 2; w2 = vv * (1 - w3); jacp = 0.25 * (1 - u); lam = w3; }
+                    const double w1 = sig * (1 - w2 - w3);
+                    // dphi over local (P, Q, R, Rt): cz*w1 + cx*w2 + cy*w3
+                    tab.push_back(-w1);
+                    tab.push_back(w1 - w2 + w3);
+                    tab.push_back(w2);
+                    tab.push_back(-w3);
+                    tab.push_back(w1);
+                    tab.push_back(w2);
+                    tab.push_back(w3);
+                    tab.push_back(W * jacp * std::pow(lam, 2 * s - 3));
+                }
+        ro.n_edge = 4 * kt * kt;
+        ro.t_edge = put(tab);
+    }
+    // common vertex: two Duffy regions, weight eta2 * w
+    {
+        std::vector<double> tab;
+        for (int reg = 0; reg < 2; ++reg)
+            for (int i = 0; i < kt; ++i)
+                for (int j = 0; j < kt; ++j)
+                    for (int l = 0; l < kt; ++l) {
+                        const double e1 = tt[i], e2 = tt[j], e3 = tt[l], W = tw[i] * tw[j] * tw[l];
+                        double x1, x2, y1, y2;
+                        if (reg == 0) { x1 = 1; x2 = e1; y1 = e2; y2 = e2 * e3; }
+                        else { x1 = e2; x2 = e2 * e3; y1 = 1; y2 = e1; }
+                        // local (P, Q, R, Qt, Rt): c1=(eQ-eP), c2=(eR-eQ), c3=-(eQt-eP), c4=-(eRt-eQt)
+                        tab.push_back(-x1 + y1);
+                        tab.push_back(x1 - x2);
+                        tab.push_back(x2);
+                        tab.push_back(-y1 + y2);
+                        tab.push_back(-y2);
+                        tab.push_back(x1);
+                        tab.push_back(x2);
+                        tab.push_back(y1);
+                        tab.push_back(y2);
+                        tab.push_back(W * e2);
+                    }
+        ro.n_vert = 2 * kt * kt * kt;
+        ro.t_vert = put(tab);
+    }
+    // 1D common vertex
+    {
+        std::vector<double> tab;
+        for (int i = 0; i < kt; ++i) {
+            tab.push_back(tt[i]);
+            tab.push_back(tw[i]);
+        }
+        ro.n_1d = kt;
+        ro.t_1d = put(tab);
+    }
+    // identical pair: three angular pieces of [0, pi), weight x rho^{2-2s}
+    {
+        std::vector<double> tab;
+        const double pi = 3.14159265358979323846;
+        const double lo[3] = {0.0, pi / 2, 3 * pi / 4}, hi[3] = {pi / 2, 3 * pi / 4, pi};
+        for (int piece = 0; piece < 3; ++piece)
+            for (int i = 0; i < kt; ++i) {
+                const double th = lo[piece] + (hi[piece] - lo[piece]) * tt[i];
+                const double wt = (hi[piece] - lo[piece]) * tw[i];
+                const double u0 = std::cos(th), u1 = std::sin(th);
+                const double rho = 2.0 / (std::fabs(u0 + u1) + std::fabs(u0) + std::fabs(u1));
+                tab.push_back(u0);
+                tab.push_back(u1);
+                tab.push_back(wt * std::pow(rho, 2 - 2 * s));
+            }
+        ro.n_ident = 3 * kt;
+        ro.t_ident = put(tab);
+    }
+    std::vector<double> bt, bw;
+    gauss01(o.k_bnd, bt, bw);
+    const int kb = o.k_bnd;
+    // boundary, facet is an edge of K: three pieces, weight x lambda^{2s-3}
+    {
+        std::vector<double> tab;
+        const double lo[3] = {0.0, 0.5, 0.0}, hi[3] = {0.5, 1.0, 1.0};
+        for (int piece = 0; piece < 3; ++piece)
+            for (int i = 0; i < kb; ++i) {
+                const double om = lo[piece] + (hi[piece] - lo[piece]) * bt[i];
+                const double wt = (hi[piece] - lo[piece]) * bw[i];
+                const double sig = (piece == 2) ? -1.0 : 1.0;
+                const double lam = (piece == 0) ? 1 - om : (piece == 1 ? om : 1.0);
+                tab.push_back(sig * (1 - om));
+                tab.push_back(om);
+                tab.push_back(wt * std::pow(lam, 2 * s - 3));
+            }
+        ro.n_own = 3 * kb;
+        ro.b_own = put(tab);
+    }
+    // boundary, facet and K share a vertex: two Duffy regions of K x e
+    {
+        std::vector<double> tab;
+        for (int reg = 0; reg < 2; ++reg)
+            for (int i = 0; i < kb; ++i)
+                for (int j = 0; j < kb; ++j) {
+                    const double u = bt[i], vv = bt[j], W = bw[i] * bw[j];
+                    if (reg == 0) { tab.push_back(1.0); tab.push_back(u); tab.push_back(vv); tab.push_back(W); }
+                    else { tab.push_back(u); tab.push_back(u * vv); tab.push_back(1.0); tab.push_back(W * u); }
+                }
+        ro.n_bvert = 2 * kb * kb;
+        ro.b_vert = put(tab);
+    }
+}
+
+int pw_mode(int dim, double s) {
+    const double e4 = -2.0 * (dim + 2.0 * s);  // 4e
+    const double r = std::round(e4);
+    if (std::fabs(e4 - r) > 1e-12) return 0;
+    const int m = -(int)r;
+    return (m >= 3 && m <= 7) ? m : 0;
+}
+
+template <int D, typename T, int Q, int PW>
+int launch_far_t(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro,
+                 double expo, cudaStream_t st) {
+    constexpr int NV = D + 1;
+    FarRule<T, Q, NV> R;
+    for (int a = 0; a < Q; ++a) {
+        R.w[a] = (T)rb[ro.far_w + a];
+        for (int v = 0; v < NV; ++v) R.wphi[a * NV + v] = (T)(rb[ro.far_w + a] * rb[ro.far_phi + a * NV + v]);
+    }
+    FarArgs<T> A;
+    A.cen = t.cen;
+    A.pts = (const T*)t.pts;
+    A.jac = t.jac;
+    A.hasdof = t.hasdof;
+    A.loc = t.loc;
+    A.ex_ptr = t.ex_ptr;
+    A.ex_idx = t.ex_idx;
+    A.tiles = t.tiles;
+    A.toff = t.toff;
+    A.L_ptr = t.L_ptr;
+    A.inc_ptr = t.inc_ptr;
+    A.inc_ent = t.inc_ent;
+    A.P = (T*)t.P;
+    A.Pd = (T*)t.Pd;
+    A.nc = P.nc;
+    A.expo = (T)expo;
+    const int maxL = std::max(1, P.maxL);
+    size_t smem = 32 * D * sizeof(double) + 32 * sizeof(double) + 32 * Q * D * sizeof(T) + 32 * Q * sizeof(T) +
+                  (size_t)NV * maxL * 32 * sizeof(T) + 32 * NV * sizeof(int) + 32 * sizeof(int);
+    auto kern = far_tile_kernel<D, T, Q, PW>;
+    FL_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t ntiles = (int64_t)P.tiles.size() / 2;
+    kern<<<(unsigned)ntiles, 32, smem, st>>>(A, R, maxL);
+    FL_CUDA_TRY(h, cudaGetLastError());
+    return FL_OK;
+}
+
+template <int D, typename T, int Q>
+int launch_far_q(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro,
+                 double expo, int pw, cudaStream_t st) {
+    // specialised square-root forms only for the default orders (k_far = 4)
+    if constexpr (D == 2 && Q == 16) {
+        switch (pw) {
+            case 5: return launch_far_t<D, T, Q, 5>(h, P, t, rb, ro, expo, st);
+            case 6: return launch_far_t<D, T, Q, 6>(h, P, t, rb, ro, expo, st);
+            case 7: return launch_far_t<D, T, Q, 7>(h, P, t, rb, ro, expo, st);
+            default: break;
+        }
+    } else if constexpr (D == 1 && Q == 4) {
+        switch (pw) {
+            case 3: return launch_far_t<D, T, Q, 3>(h, P, t, rb, ro, expo, st);
+            case 4: return launch_far_t<D, T, Q, 4>(h, P, t, rb, ro, expo, st);
+            case 5: return launch_far_t<D, T, Q, 5>(h, P, t, rb, ro, expo, st);
+            default: break;
+        }
+    }
+    return launch_far_t<D, T, Q, 0>(h, P, t, rb, ro, expo, st);
+}
+
+template <typename T>
+int launch_far(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro,
+               double expo, int pw, cudaStream_t st) {
+    const int k = h->opt.k_far;
+    if (P.dim == 2) {
+        switch (k) {
+            case 3: return launch_far_q<2, T, 9>(h, P, t, rb, ro, expo, pw, st);
+            case 4: return launch_far_q<2, T, 16>(h, P, t, rb, ro, expo, pw, st);
+            case 5: return launch_far_q<2, T, 25>(h, P, t, rb, ro, expo, pw, st);
+            case 6: return launch_far_q<2, T, 36>(h, P, t, rb, ro, expo, pw, st);
+            default: break;
+        }
+    } else {
+        switch (k) {
+            case 2: return launch_far_q<1, T, 2>(h, P, t, rb, ro, expo, pw, st);
+            case 3: return launch_far_q<1, T, 3>(h, P, t, rb, ro, expo, pw, st);
+            case 4: return launch_far_q<1, T, 4>(h, P, t, rb, ro, expo, pw, st);
+            case 5: return launch_far_q<1, T, 5>(h, P, t, rb, ro, expo, pw, st);
+            case 6: return launch_far_q<1, T, 6>(h, P, t, rb, ro, expo, pw, st);
+            case 8: return launch_far_q<1, T, 8>(h, P, t, rb, ro, expo, pw, st);
+            default: break;
+        }
+    }
+    return set_err(h, FL_ENOTIMPL, "k_far not compiled for this dimension (2D: 3-6, 1D: 2-6, 8)");
+}
+
+template <typename T, int Q>
+int launch_bnd_q(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, double expo, int pw, cudaStream_t st) {
+    const unsigned nb = (unsigned)((P.nc + 31) / 32);
+    if (Q == 16 && pw == 6) {
+        bnd_far_kernel<T, Q, 6><<<nb, 32, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, t.ef_fac, t.F,
+                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf);
+    } else if (Q == 16 && pw == 5) {
+        bnd_far_kernel<T, Q, 5><<<nb, 32, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, t.ef_fac, t.F,
+                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf);
+    } else if (Q == 16 && pw == 7) {
+        bnd_far_kernel<T, Q, 7><<<nb, 32, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, t.ef_fac, t.F,
+                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf);
+    } else {
+        bnd_far_kernel<T, Q, 0><<<nb, 32, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, t.ef_fac, t.F,
+                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf);
+    }
+    FL_CUDA_TRY(h, cudaGetLastError());
+    return FL_OK;
+}
+
+template <typename T>
+int launch_bnd(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, double expo, int pw, cudaStream_t st) {
+    switch (h->opt.k_far) {
+        case 3: return launch_bnd_q<T, 9>(h, P, t, ro, expo, pw, st);
+        case 4: return launch_bnd_q<T, 16>(h, P, t, ro, expo, pw, st);
+        case 5: return launch_bnd_q<T, 25>(h, P, t, ro, expo, pw, st);
+        case 6: return launch_bnd_q<T, 36>(h, P, t, ro, expo, pw, st);
+        default: return set_err(h, FL_ENOTIMPL, "k_far not compiled");
+    }
+}
+
+}  // namespace
+
+// C(d,s) = 2^{2s} s Γ(s + d/2) / (π^{d/2} Γ(1 - s)), Section 2.
+static double frac_constant(int d, double s) {
+    const double pi = 3.14159265358979323846;
+    return std::pow(2.0, 2 * s) * s * std::tgamma(s + d / 2.0) / (std::pow(pi, d / 2.0) * std::tgamma(1.0 - s));
+}
+
+int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStream_t st) {
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    if (lda < P.n) return set_err(h, FL_EINVAL, "lda < n");
+    if (!A) return set_err(h, FL_EINVAL, "A is NULL");
+    if (precision != FL_FP64 && precision != FL_MIXED) return set_err(h, FL_EINVAL, "unknown precision");
+    if (P.dim == 2 && P.paper_all && !h->opt.regional)
+        return set_err(h, FL_ENOTIMPL, "2D boundary DOFs (FL_DOF_PAPER with s < 1/2) are not implemented");
+    FL_CUDA_TRY(h, cudaSetDevice(h->device));
+    FL_TRY(ensure_device(h, pi));
+    DevTables& t = h->dev[pi];
+    const int D = P.dim;
+    // per-s rule tables
+    std::vector<double> rb;
+    RuleOffsets ro;
+    build_rules(h, s, rb, ro);
+    if (ro.qn > MAXQ_NEAR) return set_err(h, FL_ENOTIMPL, "k_near too large");
+    if (t.rule_len < rb.size()) {
+        void* p = nullptr;
+        FL_TRY(alloc(h, &p, rb.size() * sizeof(double)));
+        t.rule = (double*)p;
+        t.rule_len = rb.size();
+    }
+    FL_CUDA_TRY(h, cudaMemcpyAsync(t.rule, rb.data(), rb.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    const double C = frac_constant(D, s);
+    const double expo = -(D + 2.0 * s) / 2.0;
+    const int pw = pw_mode(D, s);
+    const bool f32 = precision == FL_MIXED;
+    const int64_t nc = P.nc;
+    const unsigned gb = (unsigned)((nc + 127) / 128);
+    // far rule offsets
+    if (D == 2) {
+        if (f32) prep_points<float, 2><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (float*)t.pts);
+        else prep_points<double, 2><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts);
+    } else {
+        if (f32) prep_points<float, 1><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (float*)t.pts);
+        else prep_points<double, 1><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts);
+    }
+    FL_CUDA_TRY(h, cudaGetLastError());
+    // far field
+    if (f32) FL_TRY(launch_far<float>(h, P, t, rb, ro, expo, pw, st));
+    else FL_TRY(launch_far<double>(h, P, t, rb, ro, expo, pw, st));
+    // near separated pairs
+    const int nnear = (int)P.np_a.size();
+    if (nnear > 0) {
+        const unsigned g = (unsigned)((nnear + 63) / 64);
+#define FL_NEAR(DD, TT, PWV)                                                                                    \
+    near_pair_kernel<DD, TT, PWV><<<g, 64, 0, st>>>(nnear, t.np_a, t.np_b, t.cvx, t.cen, t.jac, t.rule, ro, (TT)expo, \
+                                                    C, t.contrib, P.np_slot0, t.Dn)
+        if (D == 2) {
+            if (f32) { if (pw == 6) FL_NEAR(2, float, 6); else FL_NEAR(2, float, 0); }
+            else { if (pw == 5) FL_NEAR(2, double, 5); else if (pw == 6) FL_NEAR(2, double, 6); else if (pw == 7) FL_NEAR(2, double, 7); else FL_NEAR(2, double, 0); }
+        } else {
+            if (f32) { if (pw == 4) FL_NEAR(1, float, 4); else FL_NEAR(1, float, 0); }
+            else { if (pw == 3) FL_NEAR(1, double, 3); else if (pw == 4) FL_NEAR(1, double, 4); else if (pw == 5) FL_NEAR(1, double, 5); else FL_NEAR(1, double, 0); }
+        }
+#undef FL_NEAR
+        FL_CUDA_TRY(h, cudaGetLastError());
+    }
+    // touching pairs (float64)
+    const int ntp = (int)P.tp_type.size();
+    if (ntp > 0) {
+        const unsigned g = (unsigned)((ntp + 63) / 64);
+#define FL_TOUCH(PWV) \
+    touch_pair_kernel<PWV><<<g, 64, 0, st>>>(ntp, D, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, t.rule, ro, s, C, t.contrib)
+        if (D == 2 && pw == 5) FL_TOUCH(5);
+        else if (D == 2 && pw == 6) FL_TOUCH(6);
+        else if (D == 2 && pw == 7) FL_TOUCH(7);
+        else FL_TOUCH(0);
+#undef FL_TOUCH
+        FL_CUDA_TRY(h, cudaGetLastError());
+    }
+    // boundary term over far facets (2D)
+    if (D == 2 && !h->opt.regional && P.nf > 0) {
+        if (f32) FL_TRY(launch_bnd<float>(h, P, t, ro, expo, pw, st));
+        else FL_TRY(launch_bnd<double>(h, P, t, ro, expo, pw, st));
+    }
+    // per element
+    {
+        ElemArgs E;
+        E.dim = D;
+        E.nc = nc;
+        E.nblk = P.nblk;
+        E.nf = P.nf;
+        E.nnear = nnear;
+        E.cvx = t.cvx;
+        E.cen = t.cen;
+        E.jac = t.jac;
+        E.hasdof = t.hasdof;
+        E.Pd = t.Pd;
+        E.pd_is_float = f32 ? 1 : 0;
+        E.Dn = t.Dn;
+        E.enp_ptr = t.enp_ptr;
+        E.enp_ent = t.enp_ent;
+        E.Bf = t.Bf;
+        E.ef_ptr = t.ef_ptr;
+        E.ef_fac = t.ef_fac;
+        E.ef_cls = t.ef_cls;
+        E.F = t.F;
+        E.FN = t.FN;
+        E.FLEN = t.FLEN;
+        E.V = t.V;
+        E.corner = t.corig;
+        E.rule = t.rule;
+        E.ro = ro;
+        E.s = s;
+        E.C = C;
+        E.regional = h->opt.regional;
+        E.contrib = t.contrib;
+        E.slot0 = P.el_slot0;
+        if (D == 2 && pw == 5) element_kernel<5><<<gb, 128, 0, st>>>(E);
+        else if (D == 2 && pw == 6) element_kernel<6><<<gb, 128, 0, st>>>(E);
+        else if (D == 2 && pw == 7) element_kernel<7><<<gb, 128, 0, st>>>(E);
+        else element_kernel<0><<<gb, 128, 0, st>>>(E);
+        FL_CUDA_TRY(h, cudaGetLastError());
+    }
+    // sparse near-field values, then the dense matrix
+    const int64_t nnz = (int64_t)P.csr_col.size();
+    if (nnz > 0) {
+        gather_csr_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, t.csr_row, t.csr_col, t.g_ptr, t.g_slot,
+                                                                         t.contrib, t.csr_val);
+        FL_CUDA_TRY(h, cudaGetLastError());
+    }
+    {
+        dim3 grid((unsigned)((P.n + 127) / 128), (unsigned)std::min<int64_t>(P.n, 65535));
+        if (f32)
+            compose_far_kernel<float><<<grid, 128, 0, st>>>(P.n, P.nblk, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr, t.toff,
+                                                            (const float*)t.P, -C, A, lda);
+        else
+            compose_far_kernel<double><<<grid, 128, 0, st>>>(P.n, P.nblk, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr, t.toff,
+                                                             (const double*)t.P, -C, A, lda);
+        FL_CUDA_TRY(h, cudaGetLastError());
+    }
+    if (nnz > 0) {
+        add_csr_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, t.csr_row, t.csr_col, t.csr_val, A, lda);
+        FL_CUDA_TRY(h, cudaGetLastError());
+    }
+    return FL_OK;
+}
+
+// ----------------------------------------------------------- load vector --
+// b_i = Σ_{K ∋ i} |K| Σ_b M_ab f_b (P1 mass matrix M_ab = (1 + δ_ab)/((d+1)(d+2))),
+// f = 1 when f is NULL; one thread per DOF, cells of its vertex in a fixed order.
+__global__ void load_vector_kernel(int64_t n, int dim, const int* vod, const int64_t* v2c_ptr, const int* v2c,
+                                   const int* cells, const double* jac_orig, const double* f, int nrhs, int r,
+                                   double* b, int64_t ldb) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int NV = dim + 1;
+    const int vtx = vod[i];
+    const double scale = (dim == 2) ? 0.5 : 1.0;  // |K| = jac/2 (2D), jac (1D)
+    const double den = 1.0 / ((dim + 1.0) * (dim + 2.0));
+    double acc = 0.0;
+    for (int64_t q = v2c_ptr[vtx]; q < v2c_ptr[vtx + 1]; ++q) {
+        const int K = v2c[q];
+        const double vol = scale * jac_orig[K];
+        if (!f) {
+            acc += vol / NV;
+        } else {
+            double sacc = 0.0;
+            for (int a = 0; a < NV; ++a) {
+                const int u = cells[(int64_t)K * NV + a];
+                sacc += ((u == vtx) ? 2.0 : 1.0) * f[(int64_t)u * nrhs + r];
+            }
+            acc += vol * den * sacc;
+        }
+    }
+    b[i * ldb + r] = acc;
+}
+
+int load_vector(fl_ctx* h, double s, const double* f, int nrhs, double* b, int64_t ldb, cudaStream_t st) {
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    if (!b || nrhs < 1 || ldb < nrhs) return set_err(h, FL_EINVAL, "bad b / nrhs / ldb");
+    if (!f && nrhs != 1) return set_err(h, FL_EINVAL, "f = 1 needs nrhs = 1");
+    FL_CUDA_TRY(h, cudaSetDevice(h->device));
+    FL_TRY(ensure_device(h, pi));
+    DevTables& t = h->dev[pi];
+    const unsigned g = (unsigned)((P.n + 127) / 128);
+    for (int r = 0; r < nrhs; ++r) {
+        load_vector_kernel<<<g, 128, 0, st>>>(P.n, P.dim, t.vod, t.v2c_ptr, t.v2c, t.cells, t.jac_orig, f, nrhs, r, b, ldb);
+        FL_CUDA_TRY(h, cudaGetLastError());
+    }
+    return FL_OK;
+}
+
+}  // namespace fl

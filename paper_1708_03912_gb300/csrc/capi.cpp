@@ -1,0 +1,151 @@
+// C ABI entry points that manage handles, DOF sets and dispatch to the device code.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <new>
+#include <string>
+
+#include "context.h"
+
+namespace fl {
+int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStream_t st);
+int load_vector(fl_ctx* h, double s, const double* f, int nrhs, double* b, int64_t ldb, cudaStream_t st);
+
+int plan_for(fl_ctx* h, double s) {
+    if (!(s > 0.0 && s < 1.0)) {
+        set_err(h, FL_EINVAL, "s must lie in (0, 1)");
+        return -1;
+    }
+    const int idx = (h->dof_mode == FL_DOF_PAPER && s < 0.5) ? 1 : 0;
+    if (!h->planned[idx]) {
+        // the mesh part always lives in plan[0]
+        h->plan[idx] = h->plan[0];
+        std::string err;
+        int r = plan_dofs(h->plan[idx], idx, err);
+        if (r != FL_OK) {
+            set_err(h, r, err);
+            return -1;
+        }
+        h->planned[idx] = true;
+    }
+    return idx;
+}
+}  // namespace fl
+
+static thread_local std::string g_create_err;
+
+extern "C" {
+
+void fl_default_options(fl_options* o) {
+    if (!o) return;
+    o->k_far = 4;
+    o->k_near = 6;
+    o->k_touch = 8;
+    o->k_bnd = 8;
+    o->regional = 0;
+}
+
+int fl_create(fl_handle* out, int dim, int64_t n_vertices, const double* vertices_host, int64_t n_cells,
+              const int32_t* cells_host, int dof_mode, const fl_options* opt) {
+    g_create_err.clear();
+    if (!out) {
+        g_create_err = "handle pointer is NULL";
+        return FL_EINVAL;
+    }
+    *out = nullptr;
+    fl_options o;
+    fl_default_options(&o);
+    if (opt) o = *opt;
+    if (dof_mode != FL_DOF_INTERIOR && dof_mode != FL_DOF_PAPER) {
+        g_create_err = "unknown dof_mode";
+        return FL_EINVAL;
+    }
+    if (o.k_far < 1 || o.k_far > 32 || o.k_near < 1 || o.k_near > 32 || o.k_touch < 1 || o.k_touch > 32 ||
+        o.k_bnd < 1 || o.k_bnd > 32) {
+        g_create_err = "quadrature orders must lie in [1, 32]";
+        return FL_EINVAL;
+    }
+    fl_ctx* h = new (std::nothrow) fl_ctx;
+    if (!h) {
+        g_create_err = "out of host memory";
+        return FL_ENOMEM;
+    }
+    h->dim = dim;
+    h->dof_mode = dof_mode;
+    h->opt = o;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        dev = 0;
+        cudaGetLastError();
+    }
+    h->device = dev;
+    std::string err;
+    int r;
+    try {
+        r = fl::plan_mesh(h->plan[0], dim, n_vertices, vertices_host, n_cells, cells_host, err);
+        if (r == FL_OK) {
+            r = fl::plan_dofs(h->plan[0], 0, err);
+            if (r == FL_OK) h->planned[0] = true;
+        }
+    } catch (const std::bad_alloc&) {
+        r = FL_ENOMEM;
+        err = "out of host memory in the planner";
+    }
+    if (r != FL_OK) {
+        g_create_err = err;
+        delete h;
+        return r;
+    }
+    *out = h;
+    return FL_OK;
+}
+
+void fl_destroy(fl_handle h) {
+    if (!h) return;
+    if (!h->bufs.empty() || h->solve_ws) {
+        cudaSetDevice(h->device);
+        cudaDeviceSynchronize();
+        for (auto& b : h->bufs) cudaFree(b.p);
+        if (h->solve_ws) cudaFree(h->solve_ws);
+        if (h->solve_host) cudaFreeHost(h->solve_host);
+    }
+    delete h;
+}
+
+const char* fl_last_error(fl_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+int fl_num_dofs(fl_handle h, double s, int64_t* n) {
+    if (!h || !n) return FL_EINVAL;
+    int pi = fl::plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    *n = h->plan[pi].n;
+    return FL_OK;
+}
+
+int fl_dof_vertices(fl_handle h, double s, int32_t* vod) {
+    if (!h || !vod) return FL_EINVAL;
+    int pi = fl::plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const auto& P = h->plan[pi];
+    for (int64_t i = 0; i < P.n; ++i) vod[i] = P.vod[i];
+    return FL_OK;
+}
+
+int fl_assemble(fl_handle h, double s, int precision, double* A_dev, int64_t lda, void* stream) {
+    if (!h) return FL_EINVAL;
+    h->err.clear();
+    try {
+        return fl::assemble(h, s, precision, A_dev, lda, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        return fl::set_err(h, FL_ENOMEM, "out of host memory");
+    }
+}
+
+int fl_load_vector(fl_handle h, double s, const double* f_nodal_dev, int nrhs, double* b_dev, int64_t ldb,
+                   void* stream) {
+    if (!h) return FL_EINVAL;
+    h->err.clear();
+    return fl::load_vector(h, s, f_nodal_dev, nrhs, b_dev, ldb, (cudaStream_t)stream);
+}
+
+}  // extern "C"

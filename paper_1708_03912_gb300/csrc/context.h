@@ -1,0 +1,83 @@
+// Handle (fl_ctx) layout and device-table bookkeeping.  Internal.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace fl {
+
+// One device allocation owned by a handle.
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// Device copies of one Plan (one DOF set).
+struct DevTables {
+    bool ready = false;
+    // mesh
+    double* V = nullptr;        // nv*dim
+    double* jac_orig = nullptr; // nc (original order)
+    int* F = nullptr;
+    double* FN = nullptr;
+    double* FLEN = nullptr;
+    // internal cells
+    double* cvx = nullptr;  // nc*nvpc*dim
+    double* cen = nullptr;  // nc*dim
+    double* jac = nullptr;  // nc
+    char* hasdof = nullptr;
+    int* loc = nullptr;
+    int* cdof = nullptr;
+    int *L_ptr = nullptr, *inc_ptr = nullptr, *inc_ent = nullptr;
+    int* tiles = nullptr;
+    int64_t* toff = nullptr;
+    int *occ_ptr = nullptr, *occ_blk = nullptr, *occ_loc = nullptr;
+    int *ex_ptr = nullptr, *ex_idx = nullptr;
+    int *np_a = nullptr, *np_b = nullptr, *enp_ptr = nullptr, *enp_ent = nullptr;
+    int *tp_type = nullptr, *tp_vert = nullptr, *tp_cell = nullptr;
+    int64_t* tp_slot = nullptr;
+    int *ef_ptr = nullptr, *ef_fac = nullptr, *ef_cls = nullptr;
+    int *csr_ptr = nullptr, *csr_col = nullptr, *csr_row = nullptr;
+    int64_t *g_ptr = nullptr, *g_slot = nullptr;
+    int64_t *v2c_ptr = nullptr;
+    int* v2c = nullptr;
+    int* vod = nullptr;
+    int* corig = nullptr;   // nc*nvpc vertex ids of the internal-order cells
+    int* cells = nullptr;   // nc*nvpc oriented cells in original order
+    // workspace (sized for float64)
+    void* P = nullptr;      // partial far-field tiles
+    void* Pd = nullptr;     // nblk * nc * Qf partial row sums
+    void* pts = nullptr;    // nc * Qf * dim offsets from centroids
+    double* Dn = nullptr;   // nnear * 2 * Qn
+    double* Bf = nullptr;   // nc * Qf boundary sums (far facets)
+    double* contrib = nullptr;
+    double* csr_val = nullptr;
+    double* rule = nullptr; // per-s rule tables (see assemble.cu)
+    size_t rule_len = 0;
+};
+
+}  // namespace fl
+
+struct fl_ctx {
+    int dim = 0;
+    int dof_mode = FL_DOF_INTERIOR;
+    fl_options opt{};
+    int device = 0;
+    std::string err;
+    fl::Plan plan[2];       // [0]: interior vertices, [1]: all vertices
+    bool planned[2] = {false, false};
+    fl::DevTables dev[2];
+    std::vector<fl::DBuf> bufs;
+    void* solve_ws = nullptr;     // solver workspace (device), grown on demand
+    void* solve_host = nullptr;   // pinned scalars read back by the solver
+    size_t solve_ws_bytes = 0;
+};
+
+namespace fl {
+// returns plan index for order s (building it on demand); -1 on error (h->err set)
+int plan_for(fl_ctx* h, double s);
+int set_err(fl_ctx* h, int code, const std::string& msg);
+}  // namespace fl

@@ -1,0 +1,546 @@
+// Dense linear algebra of the solvers (arXiv:1708.03912, Section 5): the dense
+// matrix-vector product, whose cost is n^2 per product, and diagonally
+// preconditioned conjugate gradients, whose iteration count grows like n^{s/d}.
+// Also the float32 / bfloat16 copies used by the mixed-precision refinement.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "context.h"
+#include "device.h"
+
+namespace fl {
+
+// ------------------------------------------------------------------ GEMV --
+// One warp per row; 16-byte vector loads of A when the row start is aligned.
+template <typename TA>
+struct Vec16;
+template <>
+struct Vec16<double> {
+    static constexpr int N = 2;
+};
+template <>
+struct Vec16<float> {
+    static constexpr int N = 4;
+};
+template <>
+struct Vec16<__nv_bfloat16> {
+    static constexpr int N = 8;
+};
+
+template <typename TA>
+__device__ __forceinline__ void unpack16(const uint4& u, float* out);
+template <>
+__device__ __forceinline__ void unpack16<float>(const uint4& u, float* out) {
+    out[0] = __uint_as_float(u.x);
+    out[1] = __uint_as_float(u.y);
+    out[2] = __uint_as_float(u.z);
+    out[3] = __uint_as_float(u.w);
+}
+template <>
+__device__ __forceinline__ void unpack16<__nv_bfloat16>(const uint4& u, float* out) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        out[2 * i] = __uint_as_float(w[i] << 16);
+        out[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+}
+
+// float64 matrix, float64 vector, float64 accumulation
+__global__ void gemv_f64_kernel(int64_t n, const double* __restrict__ A, int64_t lda, const double* __restrict__ x,
+                                int64_t incx, double* __restrict__ y, int64_t incy, int vec) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (row >= n) return;
+    const double* a = A + row * lda;
+    double acc0 = 0.0, acc1 = 0.0;
+    int64_t j0 = 0;
+    if (vec && incx == 1) {
+        const int64_t nv = (n / 64) * 64;
+        const double2* a2 = reinterpret_cast<const double2*>(a);
+        const double2* x2 = reinterpret_cast<const double2*>(x);
+#pragma unroll 4
+        for (int64_t j = lane; j < nv / 2; j += 32) {
+            const double2 av = __ldcs(a2 + j);
+            const double2 xv = x2[j];
+            acc0 = fma(av.x, xv.x, acc0);
+            acc1 = fma(av.y, xv.y, acc1);
+        }
+        j0 = nv;
+    }
+    for (int64_t j = j0 + lane; j < n; j += 32) acc0 = fma(a[j], x[j * incx], acc0);
+    double t = warp_sum(acc0 + acc1);
+    if (lane == 0) y[row * incy] = t;
+}
+
+// float32 / bfloat16 matrix, float32 vector, float32 lane sums, float64 row total
+template <typename TA>
+__global__ void gemv_lo_kernel(int64_t n, const TA* __restrict__ A, int64_t lda, const float* __restrict__ x,
+                               double* __restrict__ y, int64_t incy, int vec) {
+    constexpr int V = Vec16<TA>::N;
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (row >= n) return;
+    const TA* a = A + row * lda;
+    float acc0 = 0.f, acc1 = 0.f;
+    int64_t j0 = 0;
+    if (vec) {
+        const int64_t nv = (n / (32 * V)) * (32 * V);
+        const uint4* a4 = reinterpret_cast<const uint4*>(a);
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+#pragma unroll 4
+        for (int64_t j = lane; j < nv / V; j += 32) {
+            const uint4 u = __ldcs(a4 + j);
+            float av[V];
+            unpack16<TA>(u, av);
+#pragma unroll
+            for (int q = 0; q < V / 4; ++q) {
+                const float4 xv = x4[j * (V / 4) + q];
+                acc0 = fmaf(av[4 * q + 0], xv.x, acc0);
+                acc1 = fmaf(av[4 * q + 1], xv.y, acc1);
+                acc0 = fmaf(av[4 * q + 2], xv.z, acc0);
+                acc1 = fmaf(av[4 * q + 3], xv.w, acc1);
+            }
+        }
+        j0 = nv;
+    }
+    for (int64_t j = j0 + lane; j < n; j += 32) acc0 = fmaf((float)a[j], x[j], acc0);
+    double t = warp_sum((double)acc0 + (double)acc1);
+    if (lane == 0) y[row * incy] = t;
+}
+
+__global__ void to_f32_kernel(int64_t n, const double* x, int64_t incx, float* y) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i * incx];
+}
+
+template <typename TO>
+__global__ void convert_kernel(int64_t n, const double* A, int64_t lda, TO* B, int64_t ldb) {
+    for (int64_t i = blockIdx.y; i < n; i += gridDim.y)
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+            if constexpr (sizeof(TO) == 4) B[i * ldb + j] = (float)A[i * lda + j];
+            else B[i * ldb + j] = __double2bfloat16(A[i * lda + j]);
+        }
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// y = A x for one right-hand side; xf is a float32 scratch copy of x (n) for low-precision A
+static cudaError_t gemv(int dtype, const void* A, int64_t lda, int64_t n, const double* x, int64_t incx, double* y,
+                        int64_t incy, float* xf, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
+    if (dtype == FL_F64) {
+        const int vec = aligned16(A) && (lda % 2 == 0) && aligned16(x);
+        gemv_f64_kernel<<<blocks, 256, 0, st>>>(n, (const double*)A, lda, x, incx, y, incy, vec);
+    } else {
+        to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, incx, xf);
+        if (dtype == FL_F32) {
+            const int vec = aligned16(A) && (lda % 4 == 0) && aligned16(xf);
+            gemv_lo_kernel<float><<<blocks, 256, 0, st>>>(n, (const float*)A, lda, xf, y, incy, vec);
+        } else {
+            const int vec = aligned16(A) && (lda % 8 == 0) && aligned16(xf);
+            gemv_lo_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(n, (const __nv_bfloat16*)A, lda, xf, y, incy, vec);
+        }
+    }
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------- deterministic dots --
+constexpr int RED_BLOCKS = 240;
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+// partial[b] = Σ a_i b_i over this block's grid-stride share
+__global__ void dot_partial_kernel(int64_t n, const double* a, const double* b, double* partial) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(a[i], b[i], acc);
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void sum_partials_kernel(const double* partial, int nb, double* out) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) *out = t;
+}
+
+// ------------------------------------------------------------- PCG parts --
+struct CgScalars {
+    double rz, rz_new, pq, rr, bb, alpha, beta;
+    int breakdown;
+};
+
+__global__ void diag_inv_kernel(int64_t n, int dtype, const void* A, int64_t lda, double* dinv) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d;
+    if (dtype == FL_F64) d = ((const double*)A)[i * lda + i];
+    else if (dtype == FL_F32) d = (double)((const float*)A)[i * lda + i];
+    else d = (double)__bfloat162float(((const __nv_bfloat16*)A)[i * lda + i]);
+    dinv[i] = 1.0 / d;
+}
+
+// r = b - Ax (or r = b when Ax is NULL); x_out = 0 if requested
+__global__ void residual_kernel(int64_t n, const double* b, const double* Ax, double* r) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) r[i] = Ax ? b[i] - Ax[i] : b[i];
+}
+
+// z = dinv r, p = z, partials of r·z and r·r
+__global__ void cg_start_kernel(int64_t n, const double* r, const double* dinv, double* z, double* p, double* prz,
+                                double* prr) {
+    __shared__ double sh[32];
+    double a = 0.0, c = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double zi = dinv[i] * r[i];
+        z[i] = zi;
+        p[i] = zi;
+        a = fma(r[i], zi, a);
+        c = fma(r[i], r[i], c);
+    }
+    const double ta = block_sum(a, sh);
+    const double tc = block_sum(c, sh);
+    if (threadIdx.x == 0) {
+        prz[blockIdx.x] = ta;
+        prr[blockIdx.x] = tc;
+    }
+}
+
+__global__ void cg_init_scalars_kernel(const double* prz, const double* prr, int nb, CgScalars* s) {
+    __shared__ double sh[32];
+    double a = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a += prz[i];
+        c += prr[i];
+    }
+    const double ta = block_sum(a, sh);
+    const double tc = block_sum(c, sh);
+    if (threadIdx.x == 0) {
+        s->rz = ta;
+        s->rr = tc;
+        s->breakdown = 0;
+    }
+}
+
+__global__ void cg_alpha_kernel(const double* ppq, int nb, CgScalars* s) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) a += ppq[i];
+    const double t = block_sum(a, sh);
+    if (threadIdx.x == 0) {
+        s->pq = t;
+        if (!(t > 0.0)) {
+            s->breakdown = 1;
+            s->alpha = 0.0;
+        } else {
+            s->alpha = s->rz / t;
+        }
+    }
+}
+
+// u += α p, r -= α q, z = dinv r, partials of r·z, r·r
+__global__ void cg_update_kernel(int64_t n, const CgScalars* s, double* u, double* r, double* z, const double* p,
+                                 const double* q, const double* dinv, double* prz, double* prr) {
+    __shared__ double sh[32];
+    const double alpha = s->alpha;
+    double a = 0.0, c = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        u[i] = fma(alpha, p[i], u[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        const double zi = dinv[i] * ri;
+        z[i] = zi;
+        a = fma(ri, zi, a);
+        c = fma(ri, ri, c);
+    }
+    const double ta = block_sum(a, sh);
+    const double tc = block_sum(c, sh);
+    if (threadIdx.x == 0) {
+        prz[blockIdx.x] = ta;
+        prr[blockIdx.x] = tc;
+    }
+}
+
+__global__ void cg_beta_kernel(const double* prz, const double* prr, int nb, CgScalars* s) {
+    __shared__ double sh[32];
+    double a = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a += prz[i];
+        c += prr[i];
+    }
+    const double ta = block_sum(a, sh);
+    const double tc = block_sum(c, sh);
+    if (threadIdx.x == 0) {
+        s->beta = ta / s->rz;
+        s->rz = ta;
+        s->rr = tc;
+    }
+}
+
+__global__ void cg_p_kernel(int64_t n, const CgScalars* s, const double* z, double* p) {
+    const double beta = s->beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void axpy_kernel(int64_t n, double a, const double* x, double* y) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = fma(a, x[i], y[i]);
+}
+
+__global__ void zero_kernel(int64_t n, double* x) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = 0.0;
+}
+
+// ------------------------------------------------------- solver workspace --
+struct SolveWork {
+    double *r, *z, *p, *q, *dinv, *dinv_lo, *d, *t, *prz, *prr, *ppq;
+    float* xf;
+    CgScalars* s;
+    CgScalars* s_host;
+};
+
+static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
+    // one contiguous device block per handle, grown on demand
+    static const int NVEC = 9;
+    const size_t need = (size_t)NVEC * n * sizeof(double) + 3 * RED_BLOCKS * sizeof(double) + n * sizeof(float) + 256 +
+                        sizeof(CgScalars) + 1024;
+    void* base = nullptr;
+    if (h->solve_ws_bytes < need) {
+        if (h->solve_ws) {
+            cudaFree(h->solve_ws);
+            cudaFreeHost(h->solve_host);
+        }
+        h->solve_ws = nullptr;
+        h->solve_host = nullptr;
+        h->solve_ws_bytes = 0;
+        if (cudaMalloc(&h->solve_ws, need) != cudaSuccess) return set_err(h, FL_ENOMEM, "cudaMalloc solver workspace");
+        if (cudaMallocHost(&h->solve_host, sizeof(CgScalars)) != cudaSuccess)
+            return set_err(h, FL_ENOMEM, "cudaMallocHost solver scalars");
+        h->solve_ws_bytes = need;
+    }
+    base = h->solve_ws;
+    char* c = (char*)base;
+    auto take = [&](size_t bytes) {
+        char* p = c;
+        c += (bytes + 255) & ~size_t(255);
+        return (void*)p;
+    };
+    w.r = (double*)take(n * sizeof(double));
+    w.z = (double*)take(n * sizeof(double));
+    w.p = (double*)take(n * sizeof(double));
+    w.q = (double*)take(n * sizeof(double));
+    w.dinv = (double*)take(n * sizeof(double));
+    w.dinv_lo = (double*)take(n * sizeof(double));
+    w.d = (double*)take(n * sizeof(double));
+    w.t = (double*)take(n * sizeof(double));
+    w.prz = (double*)take(RED_BLOCKS * sizeof(double));
+    w.prr = (double*)take(RED_BLOCKS * sizeof(double));
+    w.ppq = (double*)take(RED_BLOCKS * sizeof(double));
+    w.xf = (float*)take(n * sizeof(float));
+    w.s = (CgScalars*)take(sizeof(CgScalars));
+    w.s_host = (CgScalars*)h->solve_host;
+    return FL_OK;
+}
+
+#define FL_CU(h, x)                                                                                        \
+    do {                                                                                                   \
+        cudaError_t e_ = (x);                                                                              \
+        if (e_ != cudaSuccess) return set_err(h, FL_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Jacobi-PCG on y = M x (M of type dtype) for M d = rhs from d = 0, relative tolerance tol
+// (||rhs - M d|| by the recursion).  Returns iterations through *its, status code.
+static int pcg(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int64_t ldm, const double* dinv,
+               const double* rhs, double* d, double tol, int maxit, int* its, double* relres, cudaStream_t st) {
+    const unsigned g = (unsigned)((n + 255) / 256);
+    zero_kernel<<<g, 256, 0, st>>>(n, d);
+    residual_kernel<<<g, 256, 0, st>>>(n, rhs, nullptr, w.r);
+    cg_start_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.r, dinv, w.z, w.p, w.prz, w.prr);
+    cg_init_scalars_kernel<<<1, 256, 0, st>>>(w.prz, w.prr, RED_BLOCKS, w.s);
+    FL_CU(h, cudaGetLastError());
+    FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    FL_CU(h, cudaStreamSynchronize(st));
+    const double rr0 = w.s_host->rr;
+    *its = 0;
+    if (rr0 == 0.0) {
+        *relres = 0.0;
+        return FL_OK;
+    }
+    const double stop = tol * tol * rr0;
+    int it = 0;
+    double rr = rr0;
+    while (it < maxit) {
+        FL_CU(h, gemv(dtype, M, ldm, n, w.p, 1, w.q, 1, w.xf, st));
+        dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.p, w.q, w.ppq);
+        cg_alpha_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, w.s);
+        cg_update_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, d, w.r, w.z, w.p, w.q, dinv, w.prz, w.prr);
+        cg_beta_kernel<<<1, 256, 0, st>>>(w.prz, w.prr, RED_BLOCKS, w.s);
+        cg_p_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, w.z, w.p);
+        FL_CU(h, cudaGetLastError());
+        ++it;
+        FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+        FL_CU(h, cudaStreamSynchronize(st));
+        if (w.s_host->breakdown) {
+            *its = it;
+            *relres = std::sqrt(rr / rr0);
+            return set_err(h, FL_ENOTSPD, "CG breakdown: p^T A p <= 0");
+        }
+        rr = w.s_host->rr;
+        if (rr <= stop) break;
+    }
+    *its = it;
+    *relres = std::sqrt(rr / rr0);
+    return (rr <= stop) ? FL_OK : FL_ENOTCONV;
+}
+
+}  // namespace fl
+
+using namespace fl;
+
+extern "C" {
+
+int fl_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, int nrhs, const double* X_dev, int64_t ldx,
+              double* Y_dev, int64_t ldy, void* stream) {
+    if (!A_dev || !X_dev || !Y_dev || n < 1 || nrhs < 1 || lda < n || ldx < nrhs || ldy < nrhs) return FL_EINVAL;
+    if (dtype != FL_F64 && dtype != FL_F32 && dtype != FL_BF16) return FL_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    float* xf = nullptr;
+    if (dtype != FL_F64) {
+        if (cudaMallocAsync((void**)&xf, n * sizeof(float), st) != cudaSuccess) return FL_ENOMEM;
+    }
+    for (int r = 0; r < nrhs; ++r) {
+        if (gemv(dtype, A_dev, lda, n, X_dev + r, ldx, Y_dev + r, ldy, xf, st) != cudaSuccess) return FL_ECUDA;
+    }
+    if (xf) cudaFreeAsync(xf, st);
+    return cudaGetLastError() == cudaSuccess ? FL_OK : FL_ECUDA;
+}
+
+int fl_convert(const double* A_dev, int64_t lda, int64_t n, int dtype, void* A_lo_dev, int64_t ld_lo, void* stream) {
+    if (!A_dev || !A_lo_dev || n < 1 || lda < n || ld_lo < n) return FL_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)std::min<int64_t>(n, 65535));
+    if (dtype == FL_F32) convert_kernel<float><<<grid, 256, 0, st>>>(n, A_dev, lda, (float*)A_lo_dev, ld_lo);
+    else if (dtype == FL_BF16)
+        convert_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(n, A_dev, lda, (__nv_bfloat16*)A_lo_dev, ld_lo);
+    else return FL_EINVAL;
+    return cudaGetLastError() == cudaSuccess ? FL_OK : FL_ECUDA;
+}
+
+void fl_default_solve_opts(fl_solve_opts* o) {
+    if (!o) return;
+    o->tol = 1e-8;
+    o->maxit = 10000;
+    o->inner_dtype = FL_F64;
+    o->A_lo_dev = nullptr;
+    o->ld_lo = 0;
+    o->inner_tol = 1e-4;
+    o->inner_maxit = 2000;
+}
+
+int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const double* b_dev, double* u_dev,
+             const fl_solve_opts* o_in, fl_solve_info* info, void* stream) {
+    if (!h) return FL_EINVAL;
+    h->err.clear();
+    if (!A_dev || !b_dev || !u_dev || n < 1 || lda < n) return set_err(h, FL_EINVAL, "bad solve arguments");
+    fl_solve_opts o;
+    fl_default_solve_opts(&o);
+    if (o_in) o = *o_in;
+    if (o.inner_dtype != FL_F64 && o.inner_dtype != FL_F32 && o.inner_dtype != FL_BF16)
+        return set_err(h, FL_EINVAL, "inner_dtype");
+    if (o.inner_dtype != FL_F64 && (!o.A_lo_dev || o.ld_lo < n))
+        return set_err(h, FL_EINVAL, "low-precision copy missing");
+    cudaStream_t st = (cudaStream_t)stream;
+    FL_CU(h, cudaSetDevice(h->device));
+    SolveWork w;
+    int r = get_work(h, n, w);
+    if (r != FL_OK) return r;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    diag_inv_kernel<<<g, 256, 0, st>>>(n, FL_F64, A_dev, lda, w.dinv);
+    FL_CU(h, cudaGetLastError());
+    fl_solve_info inf{};
+    int status = FL_OK;
+    if (o.inner_dtype == FL_F64) {
+        int its = 0;
+        double rel = 0;
+        status = pcg(h, w, n, FL_F64, A_dev, lda, w.dinv, b_dev, u_dev, o.tol, o.maxit, &its, &rel, st);
+        inf.iterations = its;
+        inf.outer_iterations = 1;
+    } else {
+        // float64 iterative refinement around a low-precision Jacobi-PCG
+        diag_inv_kernel<<<g, 256, 0, st>>>(n, o.inner_dtype, o.A_lo_dev, o.ld_lo, w.dinv_lo);
+        zero_kernel<<<g, 256, 0, st>>>(n, u_dev);
+        dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, b_dev, b_dev, w.ppq);
+        sum_partials_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, &w.s->bb);
+        FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+        FL_CU(h, cudaStreamSynchronize(st));
+        const double bb = w.s_host->bb;
+        int total = 0, outer = 0;
+        status = FL_ENOTCONV;
+        double* rvec = w.t;  // outer residual (w.r is used by the inner solver)
+        while (outer < o.maxit) {
+            // r = b - A u in float64
+            FL_CU(h, gemv(FL_F64, A_dev, lda, n, u_dev, 1, w.q, 1, w.xf, st));
+            residual_kernel<<<g, 256, 0, st>>>(n, b_dev, w.q, rvec);
+            dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, rvec, rvec, w.ppq);
+            sum_partials_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, &w.s->rr);
+            FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+            FL_CU(h, cudaStreamSynchronize(st));
+            const double rel = (bb > 0) ? std::sqrt(w.s_host->rr / bb) : 0.0;
+            if (rel <= o.tol) {
+                status = FL_OK;
+                break;
+            }
+            int its = 0;
+            double irel = 0;
+            int ir = pcg(h, w, n, o.inner_dtype, o.A_lo_dev, o.ld_lo, w.dinv_lo, rvec, w.d, o.inner_tol,
+                         o.inner_maxit, &its, &irel, st);
+            total += its;
+            if (ir == FL_ENOTSPD || ir == FL_ECUDA) {
+                status = ir;
+                break;
+            }
+            axpy_kernel<<<g, 256, 0, st>>>(n, 1.0, w.d, u_dev);
+            ++outer;
+        }
+        inf.iterations = total;
+        inf.outer_iterations = outer;
+    }
+    // final residual in float64
+    FL_CU(h, gemv(FL_F64, A_dev, lda, n, u_dev, 1, w.q, 1, w.xf, st));
+    residual_kernel<<<g, 256, 0, st>>>(n, b_dev, w.q, w.t);
+    dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.t, w.t, w.ppq);
+    sum_partials_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, &w.s->rr);
+    dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, b_dev, b_dev, w.ppq);
+    sum_partials_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, &w.s->bb);
+    FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    FL_CU(h, cudaStreamSynchronize(st));
+    inf.rel_residual = (w.s_host->bb > 0) ? std::sqrt(w.s_host->rr / w.s_host->bb) : 0.0;
+    inf.status = status;
+    if (info) *info = inf;
+    return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,537 @@
+// Host planner: mesh ingest, boundary facets, degrees of freedom, combinatorial
+// classes of element pairs, quadrature tables and the maps that let every device
+// reduction run in a fixed order.
+//
+// Paper references (arXiv:1708.03912): mesh, facets dP_h and DOF set I_h -- Section 3;
+// element-pair decomposition a^{KxK'} + a^{Kxe} -- Section 5; Gauss-type rules of
+// class-dependent order -- Appendix B (orders fixed per class here).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace fl {
+
+// Gauss-Legendre nodes/weights on [0,1] (ascending nodes): Newton iteration on the
+// three-term recurrence of the Legendre polynomials, in long double.
+void gauss01(int k, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(k, 0.0);
+    w.assign(k, 0.0);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int i = 0; i < k; ++i) {
+        long double z = std::cos(pi * (i + 0.75L) / (k + 0.5L));
+        long double p0 = 1, p1 = z, dp = 1;
+        for (int it = 0; it < 200; ++it) {
+            p0 = 1;
+            p1 = z;
+            for (int j = 2; j <= k; ++j) {
+                long double p2 = ((2 * j - 1) * z * p1 - (j - 1) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = k * (z * p1 - p0) / (z * z - 1);
+            long double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs((double)dz) < 1e-19) break;
+        }
+        p0 = 1;
+        p1 = z;
+        for (int j = 2; j <= k; ++j) {
+            long double p2 = ((2 * j - 1) * z * p1 - (j - 1) * p0) / j;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = k * (z * p1 - p0) / (z * z - 1);
+        // z_i decreases with i; store ascending on [0,1]
+        x[k - 1 - i] = (double)((1 + z) / 2);
+        w[k - 1 - i] = (double)(1 / ((1 - z * z) * dp * dp));
+    }
+}
+
+// 1D: Gauss on [0,1].  2D: collapsed (Duffy) product rule on the reference triangle
+// {l1, l2 >= 0, l1 + l2 <= 1}: l1 = t_a, l2 = t_b (1 - t_a), weight w_a w_b (1 - t_a),
+// points a-major.
+Rule make_rule(int dim, int k) {
+    Rule r;
+    r.k = k;
+    std::vector<double> t, w;
+    gauss01(k, t, w);
+    if (dim == 1) {
+        r.q = k;
+        for (int a = 0; a < k; ++a) {
+            r.lam.push_back(t[a]);
+            r.w.push_back(w[a]);
+            r.phi.push_back(1 - t[a]);
+            r.phi.push_back(t[a]);
+        }
+    } else {
+        r.q = k * k;
+        for (int a = 0; a < k; ++a)
+            for (int b = 0; b < k; ++b) {
+                double l1 = t[a], l2 = t[b] * (1 - t[a]);
+                r.lam.push_back(l1);
+                r.lam.push_back(l2);
+                r.w.push_back(w[a] * w[b] * (1 - t[a]));
+                r.phi.push_back(1 - l1 - l2);
+                r.phi.push_back(l1);
+                r.phi.push_back(l2);
+            }
+    }
+    return r;
+}
+
+static void csr_from_lists(const std::vector<std::vector<int>>& L, std::vector<int>& ptr, std::vector<int>& ent) {
+    ptr.assign(L.size() + 1, 0);
+    for (size_t i = 0; i < L.size(); ++i) ptr[i + 1] = ptr[i] + (int)L[i].size();
+    ent.resize(ptr.back());
+    for (size_t i = 0; i < L.size(); ++i) std::copy(L[i].begin(), L[i].end(), ent.begin() + ptr[i]);
+}
+
+static uint32_t spread16(uint32_t x) {
+    x &= 0xffff;
+    x = (x | (x << 8)) & 0x00ff00ff;
+    x = (x | (x << 4)) & 0x0f0f0f0f;
+    x = (x | (x << 2)) & 0x33333333;
+    x = (x | (x << 1)) & 0x55555555;
+    return x;
+}
+
+int plan_mesh(Plan& P, int dim, int64_t nv, const double* V, int64_t nc, const int32_t* C, std::string& err) {
+    if (dim != 1 && dim != 2) { err = "dim must be 1 or 2"; return FL_EINVAL; }
+    if (nv < dim + 1 || nc < 1 || !V || !C) { err = "empty mesh or NULL arrays"; return FL_EINVAL; }
+    if (nv > (1LL << 30) || nc > (1LL << 29)) { err = "mesh too large"; return FL_EINVAL; }
+    P.dim = dim;
+    P.nvpc = dim + 1;
+    P.nv = nv;
+    P.nc = nc;
+    const int m = P.nvpc;
+    P.V.assign(V, V + nv * dim);
+    P.C.assign(C, C + nc * m);
+    for (int64_t i = 0; i < nc * m; ++i)
+        if (P.C[i] < 0 || P.C[i] >= nv) { err = "cell vertex index out of range"; return FL_EINVAL; }
+    for (int64_t i = 0; i < nv * dim; ++i)
+        if (!std::isfinite(P.V[i])) { err = "non-finite vertex coordinate"; return FL_EINVAL; }
+    double scale = 0;
+    for (double x : P.V) scale = std::max(scale, std::fabs(x));
+    if (scale == 0) scale = 1;
+    P.jac.assign(nc, 0.0);
+    for (int64_t k = 0; k < nc; ++k) {
+        int* c = &P.C[k * m];
+        if (dim == 1) {
+            if (P.V[c[0]] > P.V[c[1]]) std::swap(c[0], c[1]);
+            double h = P.V[c[1]] - P.V[c[0]];
+            if (!(h > 0)) { err = "degenerate interval"; return FL_EINVAL; }
+            P.jac[k] = h;
+        } else {
+            const double *a = &P.V[2 * c[0]], *b = &P.V[2 * c[1]], *d = &P.V[2 * c[2]];
+            double det = (b[0] - a[0]) * (d[1] - a[1]) - (b[1] - a[1]) * (d[0] - a[0]);
+            if (det < 0) { std::swap(c[1], c[2]); det = -det; }
+            if (!(det > 2e-14 * scale * scale)) { err = "degenerate triangle"; return FL_EINVAL; }
+            if (c[0] == c[1] || c[1] == c[2] || c[0] == c[2]) { err = "repeated vertex in a cell"; return FL_EINVAL; }
+            P.jac[k] = det;
+        }
+    }
+    // boundary facets with inward normals
+    P.F.clear();
+    P.FN.clear();
+    P.FLEN.clear();
+    if (dim == 1) {
+        std::vector<int> cnt(nv, 0), owner(nv, -1);
+        for (int64_t k = 0; k < nc; ++k)
+            for (int a = 0; a < 2; ++a) { cnt[P.C[2 * k + a]]++; owner[P.C[2 * k + a]] = (int)k; }
+        for (int64_t v = 0; v < nv; ++v) {
+            if (cnt[v] > 2) { err = "vertex shared by more than two intervals"; return FL_EINVAL; }
+            if (cnt[v] == 1) {
+                P.F.push_back((int)v);
+                P.FN.push_back(P.C[2 * owner[v]] == v ? 1.0 : -1.0);
+                P.FLEN.push_back(1.0);
+            }
+        }
+    } else {
+        std::unordered_map<uint64_t, int> idx;
+        std::vector<int> ek, eo, ecount;
+        std::vector<uint64_t> keys;
+        for (int64_t k = 0; k < nc; ++k) {
+            const int* c = &P.C[3 * k];
+            for (int e = 0; e < 3; ++e) {
+                int p = c[e], q = c[(e + 1) % 3], r = c[(e + 2) % 3];
+                uint64_t key = ((uint64_t)std::min(p, q) << 32) | (uint32_t)std::max(p, q);
+                auto it = idx.find(key);
+                if (it == idx.end()) {
+                    idx.emplace(key, (int)keys.size());
+                    keys.push_back(key);
+                    ek.push_back((int)k);
+                    eo.push_back(r);
+                    ecount.push_back(1);
+                } else {
+                    ecount[it->second]++;
+                }
+            }
+        }
+        std::vector<int> order(keys.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return keys[a] < keys[b]; });
+        for (int e : order) {
+            if (ecount[e] > 2) { err = "edge shared by more than two triangles"; return FL_EINVAL; }
+            if (ecount[e] != 1) continue;
+            int p = (int)(keys[e] >> 32), q = (int)(keys[e] & 0xffffffffu), r = eo[e];
+            double tx = P.V[2 * q] - P.V[2 * p], ty = P.V[2 * q + 1] - P.V[2 * p + 1];
+            double L = std::hypot(tx, ty);
+            double nx = -ty / L, ny = tx / L;
+            if (nx * (P.V[2 * r] - P.V[2 * p]) + ny * (P.V[2 * r + 1] - P.V[2 * p + 1]) < 0) { nx = -nx; ny = -ny; }
+            P.F.push_back(p);
+            P.F.push_back(q);
+            P.FN.push_back(nx);
+            P.FN.push_back(ny);
+            P.FLEN.push_back(L);
+        }
+    }
+    P.nf = (int64_t)P.FLEN.size();
+    P.onb.assign(nv, 0);
+    for (int v : P.F) P.onb[v] = 1;
+    // adjacency
+    std::vector<std::vector<int>> v2c(nv), nb(nv), v2f(nv);
+    for (int64_t k = 0; k < nc; ++k)
+        for (int a = 0; a < m; ++a) {
+            int v = P.C[k * m + a];
+            v2c[v].push_back((int)k);
+            for (int b = 0; b < m; ++b)
+                if (b != a) nb[v].push_back(P.C[k * m + b]);
+        }
+    for (auto& l : nb) {
+        std::sort(l.begin(), l.end());
+        l.erase(std::unique(l.begin(), l.end()), l.end());
+    }
+    for (int64_t f = 0; f < P.nf; ++f)
+        for (int a = 0; a < dim; ++a) v2f[P.F[f * dim + a]].push_back((int)f);
+    csr_from_lists(v2c, P.v2c_ptr, P.v2c);
+    csr_from_lists(nb, P.nbr_ptr, P.nbr);
+    csr_from_lists(v2f, P.v2f_ptr, P.v2f);
+    // spatial (Morton) order of cells
+    std::vector<double> cx(nc), cy(nc, 0.0);
+    double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
+    for (int64_t k = 0; k < nc; ++k) {
+        double sx = 0, sy = 0;
+        for (int a = 0; a < m; ++a) {
+            sx += P.V[dim * P.C[k * m + a]];
+            if (dim == 2) sy += P.V[2 * P.C[k * m + a] + 1];
+        }
+        cx[k] = sx / m;
+        cy[k] = sy / m;
+        lo[0] = std::min(lo[0], cx[k]);
+        hi[0] = std::max(hi[0], cx[k]);
+        lo[1] = std::min(lo[1], cy[k]);
+        hi[1] = std::max(hi[1], cy[k]);
+    }
+    std::vector<uint64_t> key(nc);
+    for (int64_t k = 0; k < nc; ++k) {
+        double fx = (hi[0] > lo[0]) ? (cx[k] - lo[0]) / (hi[0] - lo[0]) : 0.0;
+        double fy = (hi[1] > lo[1]) ? (cy[k] - lo[1]) / (hi[1] - lo[1]) : 0.0;
+        uint32_t ix = (uint32_t)std::min(65535.0, fx * 65535.0), iy = (uint32_t)std::min(65535.0, fy * 65535.0);
+        uint32_t z = (dim == 1) ? (uint32_t)std::min(4294967295.0, fx * 4294967295.0) : (spread16(ix) | (spread16(iy) << 1));
+        key[k] = ((uint64_t)z << 32) | (uint64_t)k;
+    }
+    std::sort(key.begin(), key.end());
+    P.perm.resize(nc);
+    P.iperm.resize(nc);
+    for (int64_t i = 0; i < nc; ++i) {
+        P.perm[i] = (int)(key[i] & 0xffffffffu);
+        P.iperm[P.perm[i]] = (int)i;
+    }
+    return FL_OK;
+}
+
+namespace {
+struct Entry {
+    int j;
+    int64_t slot;
+};
+}  // namespace
+
+int plan_dofs(Plan& P, int paper_all, std::string& err) {
+    const int m = P.nvpc, dim = P.dim;
+    const int64_t nc = P.nc, nv = P.nv;
+    P.paper_all = paper_all;
+    P.vod.clear();
+    P.dov.assign(nv, -1);
+    for (int64_t v = 0; v < nv; ++v)
+        if (paper_all || !P.onb[v]) {
+            P.dov[v] = (int)P.vod.size();
+            P.vod.push_back((int)v);
+        }
+    P.n = (int64_t)P.vod.size();
+    if (P.n == 0) { err = "mesh has no degrees of freedom"; return FL_EINVAL; }
+    // internal arrays
+    P.cdof.assign(nc * m, -1);
+    P.hasdof.assign(nc, 0);
+    for (int64_t k = 0; k < nc; ++k) {
+        int K = P.perm[k];
+        for (int a = 0; a < m; ++a) {
+            int d = P.dov[P.C[(int64_t)K * m + a]];
+            P.cdof[k * m + a] = d;
+            if (d >= 0) P.hasdof[k] = 1;
+        }
+    }
+    // blocks and local DOF lists
+    P.nblk = (nc + TILE - 1) / TILE;
+    P.L_ptr.assign(P.nblk + 1, 0);
+    P.L_dof.clear();
+    P.loc.assign(nc * m, -1);
+    P.maxL = 0;
+    for (int64_t B = 0; B < P.nblk; ++B) {
+        std::vector<int> L;
+        for (int64_t k = B * TILE; k < std::min(nc, (B + 1) * TILE); ++k)
+            for (int a = 0; a < m; ++a)
+                if (P.cdof[k * m + a] >= 0) L.push_back(P.cdof[k * m + a]);
+        std::sort(L.begin(), L.end());
+        L.erase(std::unique(L.begin(), L.end()), L.end());
+        for (int64_t k = B * TILE; k < std::min(nc, (B + 1) * TILE); ++k)
+            for (int a = 0; a < m; ++a) {
+                int d = P.cdof[k * m + a];
+                if (d >= 0) P.loc[k * m + a] = (int)(std::lower_bound(L.begin(), L.end(), d) - L.begin());
+            }
+        P.maxL = std::max(P.maxL, (int)L.size());
+        P.L_dof.insert(P.L_dof.end(), L.begin(), L.end());
+        P.L_ptr[B + 1] = (int)P.L_dof.size();
+    }
+    // incidence: for each block position, (lane*m + slot) entries in lane order
+    {
+        std::vector<std::vector<int>> inc(P.L_dof.size());
+        for (int64_t k = 0; k < nc; ++k) {
+            int64_t B = k / TILE;
+            int lane = (int)(k % TILE);
+            for (int a = 0; a < m; ++a)
+                if (P.loc[k * m + a] >= 0) inc[P.L_ptr[B] + P.loc[k * m + a]].push_back(lane * m + a);
+        }
+        csr_from_lists(inc, P.inc_ptr, P.inc_ent);
+    }
+    // tiles (I <= J) and offsets of their partial blocks
+    P.tiles.clear();
+    P.toff.assign(1, 0);
+    for (int64_t I = 0; I < P.nblk; ++I)
+        for (int64_t J = I; J < P.nblk; ++J) {
+            P.tiles.push_back((int)I);
+            P.tiles.push_back((int)J);
+            int64_t nI = P.L_ptr[I + 1] - P.L_ptr[I], nJ = P.L_ptr[J + 1] - P.L_ptr[J];
+            P.toff.push_back(P.toff.back() + nI * nJ);
+        }
+    // occurrences of each DOF in block lists
+    {
+        std::vector<std::vector<int>> ob(P.n), ol(P.n);
+        for (int64_t B = 0; B < P.nblk; ++B)
+            for (int p = P.L_ptr[B]; p < P.L_ptr[B + 1]; ++p) {
+                ob[P.L_dof[p]].push_back((int)B);
+                ol[P.L_dof[p]].push_back(p - P.L_ptr[B]);
+            }
+        csr_from_lists(ob, P.occ_ptr, P.occ_blk);
+        std::vector<int> tmp;
+        csr_from_lists(ol, tmp, P.occ_loc);
+    }
+    // pair classes
+    std::vector<std::vector<int>> ex(nc), enp(nc);
+    std::vector<std::vector<std::pair<int, int>>> ef(nc);
+    P.np_a.clear();
+    P.np_b.clear();
+    P.tp_type.clear();
+    P.tp_vert.clear();
+    P.tp_cell.clear();
+    std::vector<char> mark0(nv, 0), mark1(nv, 0);
+    std::vector<int> touch, nearc, n1;
+    for (int64_t K = 0; K < nc; ++K) {  // original order
+        const int* c = &P.C[K * m];
+        int k = P.iperm[K];
+        n1.clear();
+        for (int a = 0; a < m; ++a) {
+            mark0[c[a]] = 1;
+            n1.push_back(c[a]);
+            for (int q = P.nbr_ptr[c[a]]; q < P.nbr_ptr[c[a] + 1]; ++q) n1.push_back(P.nbr[q]);
+        }
+        std::sort(n1.begin(), n1.end());
+        n1.erase(std::unique(n1.begin(), n1.end()), n1.end());
+        for (int v : n1) mark1[v] = 1;
+        touch.clear();
+        nearc.clear();
+        for (int v : n1) {
+            for (int q = P.v2c_ptr[v]; q < P.v2c_ptr[v + 1]; ++q) {
+                int M = P.v2c[q];
+                if (M == K) continue;
+                if (mark0[v]) touch.push_back(M);
+                else nearc.push_back(M);
+            }
+        }
+        std::sort(touch.begin(), touch.end());
+        touch.erase(std::unique(touch.begin(), touch.end()), touch.end());
+        std::sort(nearc.begin(), nearc.end());
+        nearc.erase(std::unique(nearc.begin(), nearc.end()), nearc.end());
+        std::vector<int> nearonly;
+        std::set_difference(nearc.begin(), nearc.end(), touch.begin(), touch.end(), std::back_inserter(nearonly));
+        // exclusion list of the far-field kernel (internal indices)
+        auto& E = ex[k];
+        E.push_back(k);
+        for (int M : touch) E.push_back(P.iperm[M]);
+        for (int M : nearonly) E.push_back(P.iperm[M]);
+        std::sort(E.begin(), E.end());
+        // touching pairs, canonical: lower original index plays K
+        for (int M : touch) {
+            if (M < K) continue;
+            int km = P.iperm[M];
+            if (!P.hasdof[k] && !P.hasdof[km]) continue;
+            const int* d = &P.C[(int64_t)M * m];
+            int sv[3], ns = 0;
+            for (int a = 0; a < m; ++a)
+                for (int b = 0; b < m; ++b)
+                    if (c[a] == d[b]) sv[ns++] = c[a];
+            int tv[5] = {-1, -1, -1, -1, -1};
+            int type;
+            if (dim == 1) {
+                // left interval has the shared vertex as its right end
+                int left = (c[1] == sv[0]) ? (int)K : M, right = (left == K) ? M : (int)K;
+                tv[0] = P.C[(int64_t)left * 2];
+                tv[1] = sv[0];
+                tv[2] = P.C[(int64_t)right * 2 + 1];
+                type = 2;
+                P.tp_cell.push_back(left);
+                P.tp_cell.push_back(right);
+            } else if (ns == 2) {
+                type = 0;
+                tv[0] = sv[0];
+                tv[1] = sv[1];
+                for (int a = 0; a < 3; ++a)
+                    if (c[a] != sv[0] && c[a] != sv[1]) tv[2] = c[a];
+                for (int a = 0; a < 3; ++a)
+                    if (d[a] != sv[0] && d[a] != sv[1]) tv[3] = d[a];
+                P.tp_cell.push_back((int)K);
+                P.tp_cell.push_back(M);
+            } else {
+                type = 1;
+                int ia = 0, ib = 0;
+                for (int a = 0; a < 3; ++a) {
+                    if (c[a] == sv[0]) ia = a;
+                    if (d[a] == sv[0]) ib = a;
+                }
+                tv[0] = sv[0];
+                tv[1] = c[(ia + 1) % 3];
+                tv[2] = c[(ia + 2) % 3];
+                tv[3] = d[(ib + 1) % 3];
+                tv[4] = d[(ib + 2) % 3];
+                P.tp_cell.push_back((int)K);
+                P.tp_cell.push_back(M);
+            }
+            P.tp_type.push_back(type);
+            for (int a = 0; a < 5; ++a) P.tp_vert.push_back(tv[a]);
+        }
+        // near separated pairs, unordered by internal index
+        for (int M : nearonly) {
+            int km = P.iperm[M];
+            if (km < k) continue;
+            if (!P.hasdof[k] && !P.hasdof[km]) continue;
+            int p = (int)P.np_a.size();
+            P.np_a.push_back(k);
+            P.np_b.push_back(km);
+            enp[k].push_back(2 * p);
+            enp[km].push_back(2 * p + 1);
+        }
+        // boundary facets handled individually (touching or at distance 1)
+        if (P.hasdof[k]) {
+            for (int v : n1)
+                for (int q = P.v2f_ptr[v]; q < P.v2f_ptr[v + 1]; ++q) {
+                    int f = P.v2f[q];
+                    int sh = 0;
+                    for (int a = 0; a < dim; ++a) sh += mark0[P.F[(int64_t)f * dim + a]];
+                    int cls = (sh == 0) ? 1 : (dim == 1 ? 2 : (sh == 2 ? 2 : 3));
+                    ef[k].push_back({f, cls});
+                }
+            auto& l = ef[k];
+            std::sort(l.begin(), l.end());
+            l.erase(std::unique(l.begin(), l.end()), l.end());
+        }
+        for (int a = 0; a < m; ++a) mark0[c[a]] = 0;
+        for (int v : n1) mark1[v] = 0;
+    }
+    csr_from_lists(ex, P.ex_ptr, P.ex_idx);
+    for (auto& l : enp) std::sort(l.begin(), l.end());
+    csr_from_lists(enp, P.enp_ptr, P.enp_ent);
+    P.ef_ptr.assign(nc + 1, 0);
+    P.ef_fac.clear();
+    P.ef_cls.clear();
+    for (int64_t k = 0; k < nc; ++k) {
+        for (auto& pr : ef[k]) {
+            P.ef_fac.push_back(pr.first);
+            P.ef_cls.push_back(pr.second);
+        }
+        P.ef_ptr[k + 1] = (int)P.ef_fac.size();
+    }
+    // contribution slots and the sparse near-field pattern with its gather lists
+    const int64_t ntp = (int64_t)P.tp_type.size(), nnp = (int64_t)P.np_a.size();
+    P.tp_slot.resize(ntp);
+    int64_t cur = 0;
+    for (int64_t p = 0; p < ntp; ++p) {
+        int nl = (P.tp_type[p] == 0) ? 4 : (P.tp_type[p] == 1 ? 5 : 3);
+        P.tp_slot[p] = cur;
+        cur += nl * nl;
+    }
+    P.np_slot0 = cur;
+    cur += nnp * m * m;
+    P.el_slot0 = cur;
+    cur += nc * m * m;
+    P.nslots = cur;
+    std::vector<std::vector<Entry>> rows(P.n);
+    for (int64_t p = 0; p < ntp; ++p) {
+        int nl = (P.tp_type[p] == 0) ? 4 : (P.tp_type[p] == 1 ? 5 : 3);
+        const int* tv = &P.tp_vert[5 * p];
+        for (int a = 0; a < nl; ++a) {
+            int i = P.dov[tv[a]];
+            if (i < 0) continue;
+            for (int b = 0; b < nl; ++b) {
+                int j = P.dov[tv[b]];
+                if (j >= 0) rows[i].push_back({j, P.tp_slot[p] + a * nl + b});
+            }
+        }
+    }
+    for (int64_t p = 0; p < nnp; ++p) {
+        int ka = P.np_a[p], kb = P.np_b[p];
+        for (int a = 0; a < m; ++a) {
+            int i = P.cdof[(int64_t)ka * m + a];
+            for (int b = 0; b < m; ++b) {
+                int j = P.cdof[(int64_t)kb * m + b];
+                if (i < 0 || j < 0) continue;
+                int64_t s = P.np_slot0 + p * m * m + a * m + b;
+                rows[i].push_back({j, s});
+                rows[j].push_back({i, s});
+            }
+        }
+    }
+    for (int64_t k = 0; k < nc; ++k)
+        for (int a = 0; a < m; ++a) {
+            int i = P.cdof[k * m + a];
+            if (i < 0) continue;
+            for (int b = 0; b < m; ++b) {
+                int j = P.cdof[k * m + b];
+                if (j >= 0) rows[i].push_back({j, P.el_slot0 + k * m * m + a * m + b});
+            }
+        }
+    P.csr_ptr.assign(P.n + 1, 0);
+    P.csr_col.clear();
+    P.g_ptr.clear();
+    P.g_slot.clear();
+    for (int64_t i = 0; i < P.n; ++i) {
+        auto& r = rows[i];
+        std::sort(r.begin(), r.end(), [](const Entry& x, const Entry& y) { return x.j < y.j || (x.j == y.j && x.slot < y.slot); });
+        for (size_t q = 0; q < r.size(); ++q) {
+            if (q == 0 || r[q].j != r[q - 1].j) {
+                P.csr_col.push_back(r[q].j);
+                P.g_ptr.push_back((int64_t)P.g_slot.size());
+            }
+            P.g_slot.push_back(r[q].slot);
+        }
+        P.csr_ptr[i + 1] = (int)P.csr_col.size();
+        std::vector<Entry>().swap(r);
+    }
+    P.g_ptr.push_back((int64_t)P.g_slot.size());
+    return FL_OK;
+}
+
+}  // namespace fl

@@ -1,0 +1,245 @@
+"""Python binding of libfraclap (include/fraclap.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; PyTorch supplies
+device memory and the current stream.  The functions carry the C names
+(fl_create, fl_assemble, ...); `Mesh` is a small convenience wrapper around a
+handle.  There is no CPU path: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfraclap.so")
+
+FL_OK, FL_EINVAL, FL_ENOMEM, FL_ECUDA, FL_ENOTSPD, FL_ENOTCONV, FL_ETIMEOUT, FL_ENOTIMPL = range(8)
+FL_DOF_INTERIOR, FL_DOF_PAPER = 0, 1
+FL_FP64, FL_MIXED = 0, 1
+FL_F64, FL_F32, FL_BF16 = 0, 1, 2
+_CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOTSPD", 5: "FL_ENOTCONV",
+          6: "FL_ETIMEOUT", 7: "FL_ENOTIMPL"}
+
+EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
+           "fl_assemble", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve"]
+
+
+class FlError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class fl_options(ctypes.Structure):
+    _fields_ = [("k_far", ctypes.c_int), ("k_near", ctypes.c_int), ("k_touch", ctypes.c_int),
+                ("k_bnd", ctypes.c_int), ("regional", ctypes.c_int)]
+
+
+class fl_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("inner_dtype", ctypes.c_int),
+                ("A_lo_dev", ctypes.c_void_p), ("ld_lo", ctypes.c_int64), ("inner_tol", ctypes.c_double),
+                ("inner_maxit", ctypes.c_int)]
+
+
+class fl_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libfraclap.so (built in-tree by __graft_entry__.build()); raise if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, dbl, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int
+    L.fl_default_options.argtypes = [ctypes.POINTER(fl_options)]
+    L.fl_default_options.restype = None
+    L.fl_create.argtypes = [ctypes.POINTER(vp), ci, i64, vp, i64, vp, ci, ctypes.POINTER(fl_options)]
+    L.fl_create.restype = ci
+    L.fl_destroy.argtypes = [vp]
+    L.fl_destroy.restype = None
+    L.fl_last_error.argtypes = [vp]
+    L.fl_last_error.restype = ctypes.c_char_p
+    L.fl_num_dofs.argtypes = [vp, dbl, ctypes.POINTER(i64)]
+    L.fl_num_dofs.restype = ci
+    L.fl_dof_vertices.argtypes = [vp, dbl, vp]
+    L.fl_dof_vertices.restype = ci
+    L.fl_assemble.argtypes = [vp, dbl, ci, vp, i64, vp]
+    L.fl_assemble.restype = ci
+    L.fl_load_vector.argtypes = [vp, dbl, vp, ci, vp, i64, vp]
+    L.fl_load_vector.restype = ci
+    L.fl_matvec.argtypes = [ci, vp, i64, i64, ci, vp, i64, vp, i64, vp]
+    L.fl_matvec.restype = ci
+    L.fl_convert.argtypes = [vp, i64, i64, ci, vp, i64, vp]
+    L.fl_convert.restype = ci
+    L.fl_default_solve_opts.argtypes = [ctypes.POINTER(fl_solve_opts)]
+    L.fl_default_solve_opts.restype = None
+    L.fl_solve.argtypes = [vp, i64, vp, i64, vp, vp, ctypes.POINTER(fl_solve_opts), ctypes.POINTER(fl_solve_info), vp]
+    L.fl_solve.restype = ci
+    _ = i32
+    _lib = L
+    return L
+
+
+def _check(code, handle=None):
+    if code != FL_OK:
+        msg = lib().fl_last_error(handle).decode(errors="replace")
+        raise FlError(code, msg)
+
+
+def _stream(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ----------------------------------------------------------- C-named calls --
+def fl_default_options():
+    o = fl_options()
+    lib().fl_default_options(ctypes.byref(o))
+    return o
+
+
+def fl_create(vertices, cells, dof_mode=FL_DOF_INTERIOR, options=None):
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    C = np.ascontiguousarray(cells, dtype=np.int32)
+    h = ctypes.c_void_p()
+    opt = options if options is not None else fl_default_options()
+    r = lib().fl_create(ctypes.byref(h), V.shape[1], V.shape[0], V.ctypes.data, C.shape[0], C.ctypes.data, dof_mode,
+                        ctypes.byref(opt))
+    _check(r, None)
+    return h
+
+
+def fl_destroy(h):
+    lib().fl_destroy(h)
+
+
+def fl_num_dofs(h, s):
+    n = ctypes.c_int64()
+    _check(lib().fl_num_dofs(h, s, ctypes.byref(n)), h)
+    return n.value
+
+
+def fl_dof_vertices(h, s):
+    out = np.empty(fl_num_dofs(h, s), dtype=np.int32)
+    _check(lib().fl_dof_vertices(h, s, out.ctypes.data), h)
+    return out
+
+
+def fl_assemble(h, s, precision, A, stream=None):
+    """A: float64 CUDA tensor [n, lda] (row-major, contiguous rows)."""
+    assert A.dtype.is_floating_point and A.element_size() == 8 and A.is_cuda and A.stride(1) == 1
+    _check(lib().fl_assemble(h, s, precision, _ptr(A), A.stride(0), _stream(stream)), h)
+
+
+def fl_load_vector(h, s, f_nodal, b, stream=None):
+    """b: float64 CUDA tensor [n, nrhs]; f_nodal: None (f = 1) or float64 CUDA [n_vertices, nrhs]."""
+    nrhs = b.shape[1] if b.dim() == 2 else 1
+    ldb = b.stride(0) if b.dim() == 2 else 1
+    fp = _ptr(f_nodal) if f_nodal is not None else None
+    _check(lib().fl_load_vector(h, s, fp, nrhs, _ptr(b), ldb, _stream(stream)), h)
+
+
+def fl_matvec(dtype, A, X, Y, stream=None):
+    n = A.shape[0]
+    nrhs = X.shape[1] if X.dim() == 2 else 1
+    ldx = X.stride(0) if X.dim() == 2 else 1
+    ldy = Y.stride(0) if Y.dim() == 2 else 1
+    _check(lib().fl_matvec(dtype, _ptr(A), A.stride(0), n, nrhs, _ptr(X), ldx, _ptr(Y), ldy, _stream(stream)))
+
+
+def fl_convert(A, dtype, out, stream=None):
+    _check(lib().fl_convert(_ptr(A), A.stride(0), A.shape[0], dtype, _ptr(out), out.stride(0), _stream(stream)))
+
+
+def fl_default_solve_opts():
+    o = fl_solve_opts()
+    lib().fl_default_solve_opts(ctypes.byref(o))
+    return o
+
+
+def fl_solve(h, A, b, u, opts=None, stream=None):
+    """Returns fl_solve_info; raises on FL_EINVAL / FL_ENOMEM / FL_ECUDA, not on FL_ENOTCONV / FL_ENOTSPD."""
+    o = opts if opts is not None else fl_default_solve_opts()
+    info = fl_solve_info()
+    r = lib().fl_solve(h, A.shape[0], _ptr(A), A.stride(0), _ptr(b), _ptr(u), ctypes.byref(o), ctypes.byref(info),
+                       _stream(stream))
+    if r not in (FL_OK, FL_ENOTCONV, FL_ENOTSPD):
+        _check(r, h)
+    return info
+
+
+# ------------------------------------------------------------- convenience --
+class Mesh:
+    """Owns one fl_handle.  Orders and the DOF rule are fixed at creation."""
+
+    def __init__(self, vertices, cells, dof_mode="interior", k_far=4, k_near=6, k_touch=8, k_bnd=8, regional=False):
+        o = fl_default_options()
+        o.k_far, o.k_near, o.k_touch, o.k_bnd, o.regional = k_far, k_near, k_touch, k_bnd, int(regional)
+        self.h = fl_create(vertices, cells, FL_DOF_PAPER if dof_mode == "paper" else FL_DOF_INTERIOR, o)
+        self.dim = 1 if np.asarray(vertices).ndim == 1 else np.asarray(vertices).shape[1]
+
+    def close(self):
+        if self.h:
+            fl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_dofs(self, s):
+        return fl_num_dofs(self.h, s)
+
+    def dof_vertices(self, s):
+        return fl_dof_vertices(self.h, s)
+
+    def assemble(self, s, precision="fp64", out=None, stream=None):
+        import torch
+
+        n = self.num_dofs(s)
+        A = out if out is not None else torch.empty((n, n), dtype=torch.float64, device="cuda")
+        fl_assemble(self.h, s, FL_MIXED if precision == "mixed" else FL_FP64, A, stream)
+        return A
+
+    def load_vector(self, s, f_nodal=None, stream=None):
+        import torch
+
+        n = self.num_dofs(s)
+        nrhs = 1 if f_nodal is None else (f_nodal.shape[1] if f_nodal.dim() == 2 else 1)
+        b = torch.empty((n, nrhs), dtype=torch.float64, device="cuda")
+        f = None if f_nodal is None else f_nodal.reshape(f_nodal.shape[0], nrhs).contiguous()
+        fl_load_vector(self.h, s, f, b, stream)
+        return b[:, 0] if nrhs == 1 else b
+
+    def solve(self, A, b, tol=1e-8, maxit=10000, A_lo=None, inner_tol=1e-4, inner_maxit=2000, stream=None):
+        import torch
+
+        o = fl_default_solve_opts()
+        o.tol, o.maxit = tol, maxit
+        if A_lo is not None:
+            o.inner_dtype = FL_F32 if A_lo.dtype == torch.float32 else FL_BF16
+            o.A_lo_dev = A_lo.data_ptr()
+            o.ld_lo = A_lo.stride(0)
+            o.inner_tol, o.inner_maxit = inner_tol, inner_maxit
+        u = torch.empty_like(b)
+        info = fl_solve(self.h, A, b, u, o, stream)
+        return u, info

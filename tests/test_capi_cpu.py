@@ -1,0 +1,77 @@
+"""CPU-side checks of the C ABI: the library loads, exports every entry point the
+header declares, and its host planner (no GPU involved) agrees with the oracle's
+degree-of-freedom sets and rejects invalid meshes."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import OracleMesh
+from paper_1708_03912_gb300 import fraclap as F
+from paper_1708_03912_gb300 import synth
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "fraclap.h")
+
+
+def _lib_or_skip():
+    if not os.path.exists(F.LIB_PATH):
+        pytest.skip("libfraclap.so not built (run __graft_entry__.build())")
+    return F.lib()
+
+
+def test_header_declarations_are_exported():
+    L = _lib_or_skip()
+    text = open(HEADER).read()
+    declared = set(re.findall(r"\b(fl_[a-z_]+)\s*\(", text))
+    declared = {d for d in declared if not d.endswith("_t")}
+    assert declared, "no declarations parsed"
+    for name in sorted(declared):
+        assert hasattr(L, name), f"{name} declared in fraclap.h but not exported"
+    assert set(F.EXPORTS) <= declared
+
+
+@pytest.mark.parametrize("mesh", ["interval", "disc", "square", "lshape"])
+def test_planner_dofs_match_oracle(mesh):
+    _lib_or_skip()
+    V, T = {"interval": synth.interval(20), "disc": synth.disc(6), "square": synth.square(5, 0.2),
+            "lshape": synth.lshape(0.25, 0)}[mesh]
+    for mode in ("interior", "paper"):
+        h = F.fl_create(V, T, F.FL_DOF_PAPER if mode == "paper" else F.FL_DOF_INTERIOR)
+        om = OracleMesh(V, T)
+        for s in (0.3, 0.7):
+            vod = F.fl_dof_vertices(h, s)
+            ov, _ = om.dofs(s, mode)
+            assert np.array_equal(vod, ov)
+        F.fl_destroy(h)
+
+
+def test_create_rejects_bad_input():
+    _lib_or_skip()
+    V, T = synth.square(2)
+    with pytest.raises(F.FlError) as e:
+        F.fl_create(V, np.array([[0, 1, 99]]))
+    assert e.value.code == F.FL_EINVAL
+    Vd = V.copy()
+    with pytest.raises(F.FlError):
+        F.fl_create(np.zeros((3, 2)), np.array([[0, 1, 2]]))  # degenerate
+    # an edge shared by three triangles
+    V3 = np.array([[0, 0], [1, 0], [0.5, 1], [0.5, -1], [0.5, 2.0]], dtype=float)
+    with pytest.raises(F.FlError):
+        F.fl_create(V3, np.array([[0, 1, 2], [0, 1, 3], [0, 4, 1]]))
+    o = F.fl_default_options()
+    o.k_far = 0
+    with pytest.raises(F.FlError):
+        F.fl_create(Vd, T, F.FL_DOF_INTERIOR, o)
+    h = F.fl_create(V, T)
+    with pytest.raises(F.FlError):
+        F.fl_num_dofs(h, 1.0)
+    F.fl_destroy(h)
+
+
+def test_default_options():
+    _lib_or_skip()
+    o = F.fl_default_options()
+    assert (o.k_far, o.k_near, o.k_touch, o.k_bnd, o.regional) == (4, 6, 8, 8, 0)
+    so = F.fl_default_solve_opts()
+    assert so.tol == 1e-8 and so.inner_dtype == F.FL_F64

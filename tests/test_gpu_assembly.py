@@ -1,0 +1,159 @@
+"""GPU parity: the CUDA assembly through the C ABI against the CPU oracle, element by
+element, on the same seeded meshes.  Tolerances: float64 mode |ΔA_ij| <= 1e-12
+sqrt(A_ii A_jj) (quadrature sums in a different order only); mixed mode (float32
+separated pairs) stated, bounded by 2e-5 of the same scale."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import OracleMesh, QuadOrders, assemble_matrix, load_vector  # noqa: E402
+from paper_1708_03912_gb300 import fraclap as F  # noqa: E402
+from paper_1708_03912_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+TOL64 = 1e-12
+
+
+def scaled(A, E):
+    d = np.sqrt(np.outer(np.diag(E), np.diag(E)))
+    return float(np.max(np.abs(A - E) / d))
+
+
+def gpu_matrix(V, T, s, precision="fp64", **kw):
+    m = F.Mesh(V, T, **kw)
+    A = m.assemble(s, precision)
+    torch.cuda.synchronize()
+    out = A.cpu().numpy()
+    m.close()
+    return out
+
+
+@pytest.mark.parametrize("s", [0.25, 0.5, 0.75, 0.6])
+def test_1d_parity(s):
+    for V, T in (synth.interval(16), synth.interval(128), synth.graded_interval(70, 2.0)):
+        Ao, _ = assemble_matrix(OracleMesh(V, T), s)
+        Ag = gpu_matrix(V, T, s)
+        assert scaled(Ag, Ao) < TOL64
+
+
+@pytest.mark.parametrize("s", [0.25, 0.5, 0.75, 0.6])
+def test_2d_parity_disc(s):
+    V, T = synth.disc(10)  # 629 cells: 20 tiles of 32 and a ragged tail
+    Ao, _ = assemble_matrix(OracleMesh(V, T), s)
+    Ag = gpu_matrix(V, T, s)
+    assert scaled(Ag, Ao) < TOL64
+
+
+def test_2d_parity_lshape_and_square():
+    for (V, T), s in ((synth.lshape(0.25, 0), 0.5), (synth.square(7, 0.25), 0.35)):
+        Ao, _ = assemble_matrix(OracleMesh(V, T), s)
+        Ag = gpu_matrix(V, T, s)
+        assert scaled(Ag, Ao) < TOL64
+
+
+def test_orders_and_regional():
+    V, T = synth.square(5, 0.2)
+    o = QuadOrders(k_far=3, k_near=5, k_touch=6, k_bnd=5)
+    Ao, _ = assemble_matrix(OracleMesh(V, T), 0.4, o)
+    Ag = gpu_matrix(V, T, 0.4, k_far=3, k_near=5, k_touch=6, k_bnd=5)
+    assert scaled(Ag, Ao) < TOL64
+    Ao, _ = assemble_matrix(OracleMesh(V, T), 0.4, dof_mode="paper", regional=True)
+    Ag = gpu_matrix(V, T, 0.4, dof_mode="paper", regional=True)
+    assert scaled(Ag, Ao) < TOL64
+    V1, T1 = synth.interval(40)
+    Ao, _ = assemble_matrix(OracleMesh(V1, T1), 0.3, dof_mode="paper")
+    Ag = gpu_matrix(V1, T1, 0.3, dof_mode="paper")
+    assert scaled(Ag, Ao) < TOL64
+
+
+def test_exact_golden_high_orders():
+    gold = json.load(open(os.path.join(GOLD, "square4_exact.json")))
+    V, T = synth.square(4, 0.2)
+    for s, E in gold["matrices"].items():
+        Ag = gpu_matrix(V, T, float(s), k_far=6, k_near=12, k_touch=20, k_bnd=20)
+        assert scaled(Ag, np.array(E)) < 1e-8
+    gold = json.load(open(os.path.join(GOLD, "interval16_exact.json")))
+    V, T = synth.interval(16)
+    for s, E in gold["matrices"].items():
+        Ag = gpu_matrix(V, T, float(s), k_far=8, k_near=12, k_touch=16, k_bnd=16)
+        assert scaled(Ag, np.array(E)) < 1e-10
+
+
+def test_mixed_precision_error_stated():
+    V, T = synth.disc(10)
+    s = 0.75
+    Ao, _ = assemble_matrix(OracleMesh(V, T), s)
+    Am = gpu_matrix(V, T, s, "mixed")
+    err = scaled(Am, Ao)
+    print(f"mixed-mode scaled error vs float64 oracle: {err:.3e}")
+    assert err < 2e-5
+
+
+def test_deterministic_and_symmetric():
+    V, T = synth.disc(8)
+    m = F.Mesh(V, T)
+    for prec in ("fp64", "mixed"):
+        A1 = m.assemble(0.6, prec).cpu()
+        A2 = m.assemble(0.6, prec).cpu()
+        assert torch.equal(A1, A2)
+        assert torch.equal(A1, A1.T)
+    m.close()
+
+
+def test_edge_cases():
+    # one DOF in 1D, a single interior vertex in 2D, s close to 0 and 1
+    V, T = synth.interval(2)
+    for s in (0.05, 0.95):
+        Ao, _ = assemble_matrix(OracleMesh(V, T), s)
+        assert scaled(gpu_matrix(V, T, s), Ao) < TOL64
+    V = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1]], dtype=float)
+    T = np.array([[0, 1, 2], [0, 2, 3], [0, 3, 4], [0, 4, 1]])
+    for s in (0.05, 0.5, 0.95):
+        Ao, _ = assemble_matrix(OracleMesh(V, T), s)
+        assert scaled(gpu_matrix(V, T, s), Ao) < TOL64
+    # padded leading dimension
+    V, T = synth.disc(4)
+    m = F.Mesh(V, T)
+    n = m.num_dofs(0.5)
+    buf = torch.full((n, n + 7), 7.0, dtype=torch.float64, device="cuda")
+    F.fl_assemble(m.h, 0.5, F.FL_FP64, buf)
+    A = m.assemble(0.5)
+    assert torch.equal(buf[:, :n], A) and torch.all(buf[:, n:] == 7.0)
+    with pytest.raises(F.FlError):
+        F.fl_assemble(m.h, 1.5, F.FL_FP64, A)
+    m.close()
+
+
+def test_load_vector_parity():
+    V, T = synth.disc(6)
+    om = OracleMesh(V, T)
+    m = F.Mesh(V, T)
+    b = m.load_vector(0.5).cpu().numpy()
+    assert np.allclose(b, load_vector(om, 0.5), rtol=1e-14, atol=0)
+    f = synth.gaussian_nodal(om.nv, 3)
+    B = m.load_vector(0.5, torch.tensor(f, device="cuda")).cpu().numpy()
+    assert np.allclose(B, load_vector(om, 0.5, f), rtol=1e-12, atol=1e-15)
+    m.close()
+
+
+def test_full_size_disc_sampled_rows():
+    # the quasi-uniform disc of the benchmark (about 3.9k triangles), 12 seeded rows
+    V, T = synth.disc(25)
+    s = 0.75
+    om = OracleMesh(V, T)
+    m = F.Mesh(V, T)
+    A = m.assemble(s, "fp64").cpu().numpy()
+    Am = m.assemble(s, "mixed").cpu().numpy()
+    m.close()
+    n = A.shape[0]
+    rows = synth.random_rows(n, 12)
+    Ar, _ = assemble_matrix(om, s, rows=rows)
+    d = np.sqrt(np.outer(np.diag(A)[rows], np.diag(A)))
+    assert float(np.max(np.abs(A[rows] - Ar) / d)) < TOL64
+    assert float(np.max(np.abs(Am[rows] - Ar) / d)) < 2e-5
+    assert np.array_equal(A, A.T)

@@ -1,0 +1,90 @@
+"""GPU parity of the dense matvec, conversions and the solvers against plain
+float64 references (the oracle's Cholesky solve and numpy products)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import OracleMesh, assemble_matrix, exact, load_vector, solve  # noqa: E402
+from paper_1708_03912_gb300 import fraclap as F  # noqa: E402
+from paper_1708_03912_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def test_matvec_dtypes():
+    g = torch.Generator(device="cpu").manual_seed(5)
+    for n in (1, 37, 256, 1000, 1031):
+        A = torch.randn(n, n, generator=g, dtype=torch.float64).cuda()
+        X = torch.randn(n, 3, generator=g, dtype=torch.float64).cuda()
+        Y = torch.empty(n, 3, dtype=torch.float64, device="cuda")
+        F.fl_matvec(F.FL_F64, A, X, Y)
+        ref = (A.cpu() @ X.cpu()).numpy()
+        assert np.allclose(Y.cpu().numpy(), ref, rtol=1e-13, atol=1e-12 * np.sqrt(n))
+        for dt, tdt, tol in ((F.FL_F32, torch.float32, 1e-5), (F.FL_BF16, torch.bfloat16, 2e-2)):
+            Al = torch.empty(n, n, dtype=tdt, device="cuda")
+            F.fl_convert(A, dt, Al)
+            # round to nearest: within half a unit in the last place of the target type
+            ulp = 2.0 ** -23 if dt == F.FL_F32 else 2.0 ** -7
+            rel = ((Al.double() - A).abs() / A.abs()).max().item()
+            assert rel <= 0.5 * ulp * (1 + 1e-9)
+            F.fl_matvec(dt, Al, X, Y)
+            ref = (Al.double().cpu() @ X.float().double().cpu()).numpy()
+            assert np.allclose(Y.cpu().numpy(), ref, rtol=tol, atol=tol * np.sqrt(n))
+
+
+def test_pcg_matches_cholesky_1d_closed_form():
+    s = 0.25
+    V, T = synth.interval(128)
+    om = OracleMesh(V, T)
+    m = F.Mesh(V, T)
+    A = m.assemble(s)
+    b = m.load_vector(s)
+    u, info = m.solve(A, b, tol=1e-12)
+    assert info.status == F.FL_OK and info.rel_residual <= 1e-12
+    Ao, vod = assemble_matrix(om, s)
+    uo = solve.cholesky_solve(Ao, load_vector(om, s))
+    ug = u.cpu().numpy()
+    assert np.max(np.abs(ug - uo)) <= 1e-8 * np.max(np.abs(uo))
+    # energy identity against the closed form (Section 7.1)
+    gap = exact.energy_f1(1, s) - float(b.cpu().numpy() @ ug)
+    assert 0 < gap < 0.01
+    m.close()
+
+
+def test_pcg_and_mixed_refinement_2d():
+    s = 0.75
+    V, T = synth.disc(12)
+    om = OracleMesh(V, T)
+    m = F.Mesh(V, T)
+    A = m.assemble(s)
+    b = m.load_vector(s)
+    Ao, _ = assemble_matrix(om, s)
+    uo = solve.cholesky_solve(Ao, load_vector(om, s))
+    u, info = m.solve(A, b, tol=1e-12)
+    assert info.status == F.FL_OK
+    assert np.max(np.abs(u.cpu().numpy() - uo)) <= 1e-8 * np.max(np.abs(uo))
+    A32 = torch.empty_like(A, dtype=torch.float32)
+    F.fl_convert(A, F.FL_F32, A32)
+    u2, info2 = m.solve(A, b, tol=1e-10, A_lo=A32, inner_tol=1e-3)
+    assert info2.status == F.FL_OK and info2.rel_residual <= 1e-10 and info2.outer_iterations >= 2
+    assert np.max(np.abs(u2.cpu().numpy() - uo)) <= 1e-7 * np.max(np.abs(uo))
+    # iteration limit is reported, not raised
+    u3, info3 = m.solve(A, b, tol=1e-14, maxit=3)
+    assert info3.status == F.FL_ENOTCONV
+    m.close()
+
+
+def test_pcg_reports_breakdown_on_indefinite_matrix():
+    # [[1,2],[2,1]] has eigenvalues 3 and -1; from b = e_0 the second step meets p^T A p < 0
+    n = 64
+    A = torch.eye(n, dtype=torch.float64, device="cuda")
+    A[0, 1] = A[1, 0] = 2.0
+    b = torch.zeros(n, dtype=torch.float64, device="cuda")
+    b[0] = 1.0
+    V, T = synth.interval(4)
+    m = F.Mesh(V, T)
+    u = torch.empty_like(b)
+    info = F.fl_solve(m.h, A, b, u)
+    assert info.status == F.FL_ENOTSPD
+    m.close()
