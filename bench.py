@@ -1,0 +1,331 @@
+"""Benchmark of the dense fractional-Laplacian hot path on GB300.
+
+One step = one pass of the hot path on the quasi-uniform unit-disc workload
+(25 rings, 3929 triangles, 1887 interior DOFs, s = 0.75, f = 1):
+  assemble A^s (float32 separated pairs, float64 touching pairs / boundary /
+  reductions) -> float32 copy -> load vector -> float64-refined Jacobi-PCG on the
+  float32 copy to ||b - A u|| <= 1e-8 ||b||.
+value = element pairs per second over the whole step: N_el^2 ordered pairs (K, K')
+of the double sum of Section 5 per step, times steps, divided by the timed device
+time (max over ranks).  Side figures: assembly-only pair rate in both precisions,
+the float64 / float32 dense matvec bandwidth on the assembled matrix, and the time
+to 1e-8 of the refined solve against plain float64 Jacobi-PCG.
+
+--impl reference times the CPU oracle (oracle/) on a bounded sample of the same
+workload (element-pair rows), on this machine's host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "disc-quasi-uniform-25-rings", "domain": "unit disc", "rings": 25, "triangles": 3929,
+            "dofs": 1887, "s": 0.75, "f": "1", "dtype_assembly": "f32 separated pairs + f64 near/boundary",
+            "solve": "f64-refined Jacobi-PCG on f32 copy to 1e-8", "l2": "flushed between timed steps (512 MiB write)"}
+METRIC = "element pairs/s assembled; matvec HBM GB/s; solve time to 1e-8 vs plain FP64"
+UNIT = "element pairs/s"
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+
+        def rd():
+            for line in self.proc.stdout:
+                self.rows.append([x.strip() for x in line.split(",")])
+
+        self.thread = threading.Thread(target=rd, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) > 8:
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(seconds_target=15.0):
+    """Time the CPU oracle on element-pair rows of the same workload.  Returns
+    (ordered element pairs evaluated per second, threads, sample description)."""
+    import numpy as np
+
+    from oracle import OracleMesh, assemble_matrix
+    from paper_1708_03912_gb300 import synth
+
+    V, T = synth.disc(WORKLOAD["rings"])
+    om = OracleMesh(V, T)
+    s = WORKLOAD["s"]
+    n = len(om.dofs(s)[0])
+    rows = synth.random_rows(n, 4)
+    # ordered pairs covered: each active cell against every cell (both orders of each unordered pair)
+    active = set()
+    vod = om.dofs(s)[0]
+    for r in rows:
+        active.update(om.cells_of_vertex[vod[r]])
+    t0 = time.perf_counter()
+    assemble_matrix(om, s, rows=rows)
+    dt = time.perf_counter() - t0
+    pairs = 2 * len(active) * om.nc - len(active) ** 2  # unordered pairs touching the active set, x2 ordered
+    threads = int(os.environ.get("OMP_NUM_THREADS", "1"))
+    return pairs / dt, dt, threads, f"{len(rows)} seeded rows = {len(active)} cells x {om.nc} partner cells"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample()
+    t_all = 0.0
+    for _ in range(args.steps):
+        v, dt, threads, desc = oracle_sample()
+        vals.append(v)
+        t_all += dt
+    value = statistics.mean(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * t_all / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(WORKLOAD),
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": desc + ", numpy float64, host cores of the GPU box"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_1708_03912_gb300 import fraclap as F
+    from paper_1708_03912_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    s = WORKLOAD["s"]
+    V, T = synth.disc(WORKLOAD["rings"])
+    n_el = len(T)
+    m = F.Mesh(V, T)
+    n = m.num_dofs(s)
+    stats = F.fl_get_stats(m.h, s)
+    A = torch.empty((n, n), dtype=torch.float64, device=dev)
+    A32 = torch.empty((n, n), dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        m.assemble(s, "mixed", out=A)
+        F.fl_convert(A, F.FL_F32, A32)
+        b = m.load_vector(s)
+        u, info = m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3)
+        return info
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = F.fl_launch_count()
+    total_ms = 0.0
+    infos = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos.append(step())
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    launches = F.fl_launch_count() - launches0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    t_max = total_ms
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps * n_el * n_el / (t_max / 1000.0)
+
+    # ---- side measurements (untimed for the headline) ----
+    def timed(fn, reps=5, flush_between=True):
+        ts = []
+        for _ in range(reps):
+            if flush_between:
+                flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b_ = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b_.record(stream)
+            b_.synchronize()
+            ts.append(a.elapsed_time(b_))
+        return statistics.median(ts)
+
+    asm_mixed_ms = timed(lambda: m.assemble(s, "mixed", out=A))
+    asm_fp64_ms = timed(lambda: m.assemble(s, "fp64", out=A), reps=3)
+    # dominant kernel: the far-field tile kernel, timed by the library's events on this stream
+    F.fl_set_profiling(m.h, True)
+    far_ms = []
+    stage_tot = {k: 0.0 for k in F.STAGES}
+    for _ in range(5):
+        flush.zero_()
+        m.assemble(s, "mixed", out=A)
+        st = F.fl_stage_ms(m.h)
+        far_ms.append(st["far"])
+        for k in st:
+            stage_tot[k] += st[k] / 5
+    F.fl_set_profiling(m.h, False)
+    far_avg = statistics.mean(far_ms)
+    q = 16  # collapsed rule of order 4
+    evals = stats["n_far_pairs"] * q * q
+    # matvec bandwidth on the assembled matrix (L2-resident at this size: 28 MiB fp64)
+    x = torch.randn(n, 1, dtype=torch.float64, device=dev)
+    y = torch.empty(n, 1, dtype=torch.float64, device=dev)
+    mv64 = timed(lambda: F.fl_matvec(F.FL_F64, A, x, y), reps=20)
+    mv32 = timed(lambda: F.fl_matvec(F.FL_F32, A32, x, y), reps=20)
+    # time to 1e-8: refined float32 solve vs plain float64 Jacobi-PCG on the same matrix
+    m.assemble(s, "fp64", out=A)
+    F.fl_convert(A, F.FL_F32, A32)
+    b = m.load_vector(s)
+    sol_mixed = timed(lambda: m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3), reps=3)
+    sol_fp64 = timed(lambda: m.solve(A, b, tol=1e-8), reps=3)
+    _, inf64 = m.solve(A, b, tol=1e-8)
+    _, infmx = m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3)
+
+    # ---- end to end through the public API with host buffers ----
+    def e2e_step():
+        mm = F.Mesh(V, T)
+        AA = mm.assemble(s, "mixed")
+        AL = torch.empty((n, n), dtype=torch.float32, device=dev)
+        F.fl_convert(AA, F.FL_F32, AL)
+        bb = mm.load_vector(s)
+        uu, _ = mm.solve(AA, bb, tol=1e-8, A_lo=AL, inner_tol=1e-3)
+        host = uu.cpu()
+        st_ = F.fl_get_stats(mm.h, s)
+        mm.close()
+        return host, st_
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        _, st_e = e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = int(st_e["h2d_bytes"] + V.nbytes + T.nbytes)
+    d2h = n * 8
+
+    peaks = load_peaks()
+    sm_clock = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    # far kernel (float32, s = 3/4): one MUFU.LG2 (16 results/clk/SM) and one MUFU.EX2 (32/clk/SM on GB300,
+    # measured) per kernel evaluation -> 1 / (1/16 + 1/32) = 10.67 evaluations/clk/SM
+    evals_per_clk_sm = 1.0 / (1.0 / 16 + 1.0 / 32)
+    peak_evals = 152 * evals_per_clk_sm * (peaks.get("sm_max_mhz", 2070.0) * 1e6)
+    achieved = evals / (far_avg / 1000.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": dict(WORKLOAD, cells=n_el, parallelism=f"replicas x{world}"),
+        "roofline": {"bound": "alu", "kernel": "far_tile_kernel<2,float,16,0>", "achieved": achieved / 1e9,
+                     "peak": peak_evals / 1e9, "unit": "Geval/s", "frac": achieved / peak_evals, "traffic": None,
+                     "note": "kernel evaluations |x-y|^{-2-2s}; peak = 152 SMs x 10.67 evals/clk (MUFU lg2 16/clk + "
+                             "ex2 32/clk per SM) x max SM clock; evals = far pairs x 16 x 16"},
+        "stage_ms": stage_tot,
+        "assembly_pairs_per_s": {"mixed": n_el * n_el / (asm_mixed_ms / 1000), "fp64": n_el * n_el / (asm_fp64_ms / 1000)},
+        "matvec": {"n": n, "f64_gbs": n * n * 8 / (mv64 / 1000) / 1e9, "f32_gbs": n * n * 4 / (mv32 / 1000) / 1e9,
+                   "note": "matrix L2-resident at this size"},
+        "solve_ms_to_1e-8": {"f32_refined": sol_mixed, "plain_f64": sol_fp64, "iters_f64": inf64.iterations,
+                             "iters_refined": infmx.iterations, "outer": infmx.outer_iterations},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": {"value": n_el * n_el / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": "Mesh(host arrays) -> planner -> table upload -> assemble -> solve -> u to host"},
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        v, dt, threads, desc = oracle_sample()
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+    m.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -173,6 +173,45 @@ void fl_default_solve_opts(fl_solve_opts* o);
 int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const double* b_dev, double* u_dev,
              const fl_solve_opts* o, fl_solve_info* info, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Measurement hooks (no counterpart in the paper): plan statistics, per-stage
+ * device times of fl_assemble, and a count of kernel launches.
+ * ------------------------------------------------------------------------ */
+typedef struct fl_stats {
+    int64_t n_cells, n_vertices, n_facets, n_dofs;
+    int64_t n_tiles;            /* 32x32 cell tiles of the far-field kernel (upper triangle) */
+    int64_t n_touch_pairs;      /* common edge / common vertex pairs with a DOF */
+    int64_t n_near_pairs;       /* separated pairs at vertex-graph distance 1 with a DOF */
+    int64_t n_far_pairs;        /* remaining unordered separated pairs with a DOF on either side */
+    int64_t n_cells_with_dof;
+    int64_t nnz_nearfield;      /* nonzeros of the sparse near-field part */
+    int64_t h2d_bytes;          /* bytes of planner tables copied host -> device so far */
+    int64_t workspace_bytes;    /* device bytes owned by the handle */
+} fl_stats;
+
+/* Fill *st for the DOF set of order s (plans it if needed). */
+int fl_get_stats(fl_handle h, double s, fl_stats* st);
+
+/* Stages of fl_assemble timed when profiling is on. */
+#define FL_STAGE_PREP    0
+#define FL_STAGE_FAR     1  /* separated pairs at distance >= 2 (the dominant kernel) */
+#define FL_STAGE_NEAR    2
+#define FL_STAGE_TOUCH   3
+#define FL_STAGE_BND     4  /* element x far boundary facet sums */
+#define FL_STAGE_ELEMENT 5
+#define FL_STAGE_COMPOSE 6  /* sparse gather + dense compose */
+#define FL_NSTAGES       7
+
+/* enable = 1: record a CUDA event pair around every stage of each later fl_assemble
+ * on its stream (events only, no synchronisation). */
+int fl_set_profiling(fl_handle h, int enable);
+
+/* Milliseconds of each stage of the last profiled fl_assemble (waits for its events). */
+int fl_stage_ms(fl_handle h, double* ms_out /* [FL_NSTAGES] */);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t fl_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -784,6 +784,8 @@ int upload(fl_ctx* h, X*& dst, const std::vector<X>& src) {
     cudaError_t e = cudaMalloc((void**)&dst, bytes);
     if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     h->bufs.push_back({dst, bytes});
+    h->ws_bytes += (int64_t)bytes;
+    h->h2d_bytes += (int64_t)(src.size() * sizeof(X));
     if (!src.empty()) {
         e = cudaMemcpy(dst, src.data(), src.size() * sizeof(X), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return set_err(h, FL_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
@@ -796,7 +798,19 @@ int alloc(fl_ctx* h, void** dst, size_t bytes) {
     cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
     if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
     h->bufs.push_back({*dst, bytes});
+    h->ws_bytes += (int64_t)bytes;
     return FL_OK;
+}
+
+// CUDA event pair around stage i when profiling is on
+void stage_mark(fl_ctx* h, cudaStream_t st, int i, int end) {
+    if (!h->profiling) return;
+    if (!h->ev_made) {
+        for (int k = 0; k < 2 * FL_NSTAGES; ++k) cudaEventCreate(&h->ev[k]);
+        h->ev_made = true;
+    }
+    cudaEventRecord(h->ev[2 * i + end], st);
+    h->ev_recorded = true;
 }
 
 #define FL_TRY(x)               \
@@ -1077,7 +1091,7 @@ int launch_far_t(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<doubl
     auto kern = far_tile_kernel<D, T, Q, PW>;
     FL_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t ntiles = (int64_t)P.tiles.size() / 2;
-    kern<<<(unsigned)ntiles, 32, smem, st>>>(A, R, maxL);
+    kern<<<(unsigned)ntiles, 32, smem, st>>>(A, R, maxL); fl::count_launch();
     FL_CUDA_TRY(h, cudaGetLastError());
     return FL_OK;
 }
@@ -1135,16 +1149,16 @@ int launch_bnd_q(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, 
     const unsigned nb = (unsigned)((P.nc + 31) / 32);
     if (Q == 16 && pw == 6) {
         bnd_far_kernel<T, Q, 6><<<nb, 32, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, t.ef_fac, t.F,
-                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf);
+                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf); fl::count_launch();
     } else if (Q == 16 && pw == 5) {
         bnd_far_kernel<T, Q, 5><<<nb, 32, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, t.ef_fac, t.F,
-                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf);
+                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf); fl::count_launch();
     } else if (Q == 16 && pw == 7) {
         bnd_far_kernel<T, Q, 7><<<nb, 32, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, t.ef_fac, t.F,
-                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf);
+                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf); fl::count_launch();
     } else {
         bnd_far_kernel<T, Q, 0><<<nb, 32, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, t.ef_fac, t.F,
-                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf);
+                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf); fl::count_launch();
     }
     FL_CUDA_TRY(h, cudaGetLastError());
     return FL_OK;
@@ -1201,17 +1215,24 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
     const int64_t nc = P.nc;
     const unsigned gb = (unsigned)((nc + 127) / 128);
     // far rule offsets
+    stage_mark(h, st, FL_STAGE_PREP, 0);
     if (D == 2) {
-        if (f32) prep_points<float, 2><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (float*)t.pts);
-        else prep_points<double, 2><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts);
+        if (f32) { prep_points<float, 2><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (float*)t.pts); fl::count_launch(); }
+        else { prep_points<double, 2><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts); fl::count_launch(); }
     } else {
-        if (f32) prep_points<float, 1><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (float*)t.pts);
-        else prep_points<double, 1><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts);
+        if (f32) { prep_points<float, 1><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (float*)t.pts); fl::count_launch(); }
+        else { prep_points<double, 1><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts); fl::count_launch(); }
     }
     FL_CUDA_TRY(h, cudaGetLastError());
+    stage_mark(h, st, FL_STAGE_PREP, 1);
     // far field
-    if (f32) FL_TRY(launch_far<float>(h, P, t, rb, ro, expo, pw, st));
+    stage_mark(h, st, FL_STAGE_FAR, 0);
+    // float32: keep only the one-MUFU forms (t^2, t^3); lg2 + ex2 beats rsqrt + sqrt here
+    const int pw32 = (pw == 4 || pw == 6) ? pw : 0;
+    if (f32) FL_TRY(launch_far<float>(h, P, t, rb, ro, expo, pw32, st));
     else FL_TRY(launch_far<double>(h, P, t, rb, ro, expo, pw, st));
+    stage_mark(h, st, FL_STAGE_FAR, 1);
+    stage_mark(h, st, FL_STAGE_NEAR, 0);
     // near separated pairs
     const int nnear = (int)P.np_a.size();
     if (nnear > 0) {
@@ -1227,9 +1248,12 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
             else { if (pw == 3) FL_NEAR(1, double, 3); else if (pw == 4) FL_NEAR(1, double, 4); else if (pw == 5) FL_NEAR(1, double, 5); else FL_NEAR(1, double, 0); }
         }
 #undef FL_NEAR
+        fl::count_launch();
         FL_CUDA_TRY(h, cudaGetLastError());
     }
+    stage_mark(h, st, FL_STAGE_NEAR, 1);
     // touching pairs (float64)
+    stage_mark(h, st, FL_STAGE_TOUCH, 0);
     const int ntp = (int)P.tp_type.size();
     if (ntp > 0) {
         const unsigned g = (unsigned)((ntp + 63) / 64);
@@ -1240,14 +1264,19 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
         else if (D == 2 && pw == 7) FL_TOUCH(7);
         else FL_TOUCH(0);
 #undef FL_TOUCH
+        fl::count_launch();
         FL_CUDA_TRY(h, cudaGetLastError());
     }
+    stage_mark(h, st, FL_STAGE_TOUCH, 1);
     // boundary term over far facets (2D)
+    stage_mark(h, st, FL_STAGE_BND, 0);
     if (D == 2 && !h->opt.regional && P.nf > 0) {
-        if (f32) FL_TRY(launch_bnd<float>(h, P, t, ro, expo, pw, st));
+        if (f32) FL_TRY(launch_bnd<float>(h, P, t, ro, expo, pw32, st));
         else FL_TRY(launch_bnd<double>(h, P, t, ro, expo, pw, st));
     }
+    stage_mark(h, st, FL_STAGE_BND, 1);
     // per element
+    stage_mark(h, st, FL_STAGE_ELEMENT, 0);
     {
         ElemArgs E;
         E.dim = D;
@@ -1280,17 +1309,19 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
         E.regional = h->opt.regional;
         E.contrib = t.contrib;
         E.slot0 = P.el_slot0;
-        if (D == 2 && pw == 5) element_kernel<5><<<gb, 128, 0, st>>>(E);
-        else if (D == 2 && pw == 6) element_kernel<6><<<gb, 128, 0, st>>>(E);
-        else if (D == 2 && pw == 7) element_kernel<7><<<gb, 128, 0, st>>>(E);
-        else element_kernel<0><<<gb, 128, 0, st>>>(E);
+        if (D == 2 && pw == 5) { element_kernel<5><<<gb, 128, 0, st>>>(E); fl::count_launch(); }
+        else if (D == 2 && pw == 6) { element_kernel<6><<<gb, 128, 0, st>>>(E); fl::count_launch(); }
+        else if (D == 2 && pw == 7) { element_kernel<7><<<gb, 128, 0, st>>>(E); fl::count_launch(); }
+        else { element_kernel<0><<<gb, 128, 0, st>>>(E); fl::count_launch(); }
         FL_CUDA_TRY(h, cudaGetLastError());
     }
+    stage_mark(h, st, FL_STAGE_ELEMENT, 1);
     // sparse near-field values, then the dense matrix
+    stage_mark(h, st, FL_STAGE_COMPOSE, 0);
     const int64_t nnz = (int64_t)P.csr_col.size();
     if (nnz > 0) {
         gather_csr_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, t.csr_row, t.csr_col, t.g_ptr, t.g_slot,
-                                                                         t.contrib, t.csr_val);
+                                                                         t.contrib, t.csr_val); fl::count_launch();
         FL_CUDA_TRY(h, cudaGetLastError());
     }
     {
@@ -1301,12 +1332,14 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
         else
             compose_far_kernel<double><<<grid, 128, 0, st>>>(P.n, P.nblk, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr, t.toff,
                                                              (const double*)t.P, -C, A, lda);
+        fl::count_launch();
         FL_CUDA_TRY(h, cudaGetLastError());
     }
     if (nnz > 0) {
-        add_csr_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, t.csr_row, t.csr_col, t.csr_val, A, lda);
+        add_csr_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, t.csr_row, t.csr_col, t.csr_val, A, lda); fl::count_launch();
         FL_CUDA_TRY(h, cudaGetLastError());
     }
+    stage_mark(h, st, FL_STAGE_COMPOSE, 1);
     return FL_OK;
 }
 
@@ -1351,7 +1384,7 @@ int load_vector(fl_ctx* h, double s, const double* f, int nrhs, double* b, int64
     DevTables& t = h->dev[pi];
     const unsigned g = (unsigned)((P.n + 127) / 128);
     for (int r = 0; r < nrhs; ++r) {
-        load_vector_kernel<<<g, 128, 0, st>>>(P.n, P.dim, t.vod, t.v2c_ptr, t.v2c, t.cells, t.jac_orig, f, nrhs, r, b, ldb);
+        load_vector_kernel<<<g, 128, 0, st>>>(P.n, P.dim, t.vod, t.v2c_ptr, t.v2c, t.cells, t.jac_orig, f, nrhs, r, b, ldb); fl::count_launch();
         FL_CUDA_TRY(h, cudaGetLastError());
     }
     return FL_OK;

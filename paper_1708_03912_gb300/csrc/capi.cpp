@@ -32,7 +32,14 @@ int plan_for(fl_ctx* h, double s) {
 }
 }  // namespace fl
 
+#include <atomic>
+
 static thread_local std::string g_create_err;
+static std::atomic<uint64_t> g_launches{0};
+
+namespace fl {
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+}  // namespace fl
 
 extern "C" {
 
@@ -106,6 +113,8 @@ void fl_destroy(fl_handle h) {
         cudaSetDevice(h->device);
         cudaDeviceSynchronize();
         for (auto& b : h->bufs) cudaFree(b.p);
+        if (h->ev_made)
+            for (int k = 0; k < 2 * FL_NSTAGES; ++k) cudaEventDestroy(h->ev[k]);
         if (h->solve_ws) cudaFree(h->solve_ws);
         if (h->solve_host) cudaFreeHost(h->solve_host);
     }
@@ -147,5 +156,55 @@ int fl_load_vector(fl_handle h, double s, const double* f_nodal_dev, int nrhs, d
     h->err.clear();
     return fl::load_vector(h, s, f_nodal_dev, nrhs, b_dev, ldb, (cudaStream_t)stream);
 }
+
+int fl_get_stats(fl_handle h, double s, fl_stats* st) {
+    if (!h || !st) return FL_EINVAL;
+    int pi = fl::plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const fl::Plan& P = h->plan[pi];
+    fl_stats o{};
+    o.n_cells = P.nc;
+    o.n_vertices = P.nv;
+    o.n_facets = P.nf;
+    o.n_dofs = P.n;
+    o.n_tiles = (int64_t)P.tiles.size() / 2;
+    o.n_touch_pairs = (int64_t)P.tp_type.size();
+    o.n_near_pairs = (int64_t)P.np_a.size();
+    int64_t nd = 0;
+    for (char c : P.hasdof) nd += c ? 1 : 0;
+    o.n_cells_with_dof = nd;
+    const int64_t nodof = P.nc - nd;
+    const int64_t all = P.nc * (P.nc - 1) / 2 - nodof * (nodof - 1) / 2;
+    o.n_far_pairs = all - o.n_touch_pairs - o.n_near_pairs;
+    o.nnz_nearfield = (int64_t)P.csr_col.size();
+    o.h2d_bytes = h->h2d_bytes;
+    o.workspace_bytes = h->ws_bytes + (int64_t)h->solve_ws_bytes;
+    *st = o;
+    return FL_OK;
+}
+
+int fl_set_profiling(fl_handle h, int enable) {
+    if (!h) return FL_EINVAL;
+    h->profiling = enable ? 1 : 0;
+    return FL_OK;
+}
+
+int fl_stage_ms(fl_handle h, double* ms) {
+    if (!h || !ms) return FL_EINVAL;
+    if (!h->ev_recorded) return fl::set_err(h, FL_EINVAL, "no profiled fl_assemble yet");
+    if (cudaEventSynchronize(h->ev[2 * FL_NSTAGES - 1]) != cudaSuccess)
+        return fl::set_err(h, FL_ECUDA, "cudaEventSynchronize");
+    for (int i = 0; i < FL_NSTAGES; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, h->ev[2 * i], h->ev[2 * i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            t = 0.f;
+        }
+        ms[i] = (double)t;
+    }
+    return FL_OK;
+}
+
+uint64_t fl_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"

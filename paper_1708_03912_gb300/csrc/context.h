@@ -71,12 +71,20 @@ struct fl_ctx {
     bool planned[2] = {false, false};
     fl::DevTables dev[2];
     std::vector<fl::DBuf> bufs;
+    int profiling = 0;
+    cudaEvent_t ev[2 * FL_NSTAGES] = {};
+    bool ev_made = false;
+    bool ev_recorded = false;
+    int64_t h2d_bytes = 0;
+    int64_t ws_bytes = 0;
     void* solve_ws = nullptr;     // solver workspace (device), grown on demand
     void* solve_host = nullptr;   // pinned scalars read back by the solver
     size_t solve_ws_bytes = 0;
 };
 
 namespace fl {
+// every kernel launch site bumps this counter (fl_launch_count)
+void count_launch(int n = 1);
 // returns plan index for order s (building it on demand); -1 on error (h->err set)
 int plan_for(fl_ctx* h, double s);
 int set_err(fl_ctx* h, int code, const std::string& msg);

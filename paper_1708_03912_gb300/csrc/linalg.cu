@@ -135,15 +135,15 @@ static cudaError_t gemv(int dtype, const void* A, int64_t lda, int64_t n, const 
     const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
     if (dtype == FL_F64) {
         const int vec = aligned16(A) && (lda % 2 == 0) && aligned16(x);
-        gemv_f64_kernel<<<blocks, 256, 0, st>>>(n, (const double*)A, lda, x, incx, y, incy, vec);
+        gemv_f64_kernel<<<blocks, 256, 0, st>>>(n, (const double*)A, lda, x, incx, y, incy, vec); fl::count_launch();
     } else {
-        to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, incx, xf);
+        to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, incx, xf); fl::count_launch();
         if (dtype == FL_F32) {
             const int vec = aligned16(A) && (lda % 4 == 0) && aligned16(xf);
-            gemv_lo_kernel<float><<<blocks, 256, 0, st>>>(n, (const float*)A, lda, xf, y, incy, vec);
+            gemv_lo_kernel<float><<<blocks, 256, 0, st>>>(n, (const float*)A, lda, xf, y, incy, vec); fl::count_launch();
         } else {
             const int vec = aligned16(A) && (lda % 8 == 0) && aligned16(xf);
-            gemv_lo_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(n, (const __nv_bfloat16*)A, lda, xf, y, incy, vec);
+            gemv_lo_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(n, (const __nv_bfloat16*)A, lda, xf, y, incy, vec); fl::count_launch();
         }
     }
     return cudaGetLastError();
@@ -322,11 +322,14 @@ struct SolveWork {
     CgScalars* s_host;
 };
 
+static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
 static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
-    // one contiguous device block per handle, grown on demand
-    static const int NVEC = 9;
-    const size_t need = (size_t)NVEC * n * sizeof(double) + 3 * RED_BLOCKS * sizeof(double) + n * sizeof(float) + 256 +
-                        sizeof(CgScalars) + 1024;
+    // one contiguous device block per handle, grown on demand; the layout below
+    // (eight float64 vectors, three reduction buffers, one float32 vector, scalars)
+    // is carved with the same 256-byte rounding that sizes it
+    const size_t need = 8 * round256(n * sizeof(double)) + 3 * round256(RED_BLOCKS * sizeof(double)) +
+                        round256(n * sizeof(float)) + round256(sizeof(CgScalars));
     void* base = nullptr;
     if (h->solve_ws_bytes < need) {
         if (h->solve_ws) {
@@ -345,7 +348,7 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
     char* c = (char*)base;
     auto take = [&](size_t bytes) {
         char* p = c;
-        c += (bytes + 255) & ~size_t(255);
+        c += round256(bytes);
         return (void*)p;
     };
     w.r = (double*)take(n * sizeof(double));
@@ -362,6 +365,7 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
     w.xf = (float*)take(n * sizeof(float));
     w.s = (CgScalars*)take(sizeof(CgScalars));
     w.s_host = (CgScalars*)h->solve_host;
+    if ((size_t)(c - (char*)base) > need) return set_err(h, FL_EINVAL, "solver workspace layout exceeds its size");
     return FL_OK;
 }
 
@@ -376,10 +380,10 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
 static int pcg(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int64_t ldm, const double* dinv,
                const double* rhs, double* d, double tol, int maxit, int* its, double* relres, cudaStream_t st) {
     const unsigned g = (unsigned)((n + 255) / 256);
-    zero_kernel<<<g, 256, 0, st>>>(n, d);
-    residual_kernel<<<g, 256, 0, st>>>(n, rhs, nullptr, w.r);
-    cg_start_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.r, dinv, w.z, w.p, w.prz, w.prr);
-    cg_init_scalars_kernel<<<1, 256, 0, st>>>(w.prz, w.prr, RED_BLOCKS, w.s);
+    zero_kernel<<<g, 256, 0, st>>>(n, d); fl::count_launch();
+    residual_kernel<<<g, 256, 0, st>>>(n, rhs, nullptr, w.r); fl::count_launch();
+    cg_start_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.r, dinv, w.z, w.p, w.prz, w.prr); fl::count_launch();
+    cg_init_scalars_kernel<<<1, 256, 0, st>>>(w.prz, w.prr, RED_BLOCKS, w.s); fl::count_launch();
     FL_CU(h, cudaGetLastError());
     FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
     FL_CU(h, cudaStreamSynchronize(st));
@@ -394,11 +398,11 @@ static int pcg(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int
     double rr = rr0;
     while (it < maxit) {
         FL_CU(h, gemv(dtype, M, ldm, n, w.p, 1, w.q, 1, w.xf, st));
-        dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.p, w.q, w.ppq);
-        cg_alpha_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, w.s);
-        cg_update_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, d, w.r, w.z, w.p, w.q, dinv, w.prz, w.prr);
-        cg_beta_kernel<<<1, 256, 0, st>>>(w.prz, w.prr, RED_BLOCKS, w.s);
-        cg_p_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, w.z, w.p);
+        dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.p, w.q, w.ppq); fl::count_launch();
+        cg_alpha_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, w.s); fl::count_launch();
+        cg_update_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, d, w.r, w.z, w.p, w.q, dinv, w.prz, w.prr); fl::count_launch();
+        cg_beta_kernel<<<1, 256, 0, st>>>(w.prz, w.prr, RED_BLOCKS, w.s); fl::count_launch();
+        cg_p_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, w.z, w.p); fl::count_launch();
         FL_CU(h, cudaGetLastError());
         ++it;
         FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
@@ -442,10 +446,13 @@ int fl_convert(const double* A_dev, int64_t lda, int64_t n, int dtype, void* A_l
     if (!A_dev || !A_lo_dev || n < 1 || lda < n || ld_lo < n) return FL_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)std::min<int64_t>(n, 65535));
-    if (dtype == FL_F32) convert_kernel<float><<<grid, 256, 0, st>>>(n, A_dev, lda, (float*)A_lo_dev, ld_lo);
-    else if (dtype == FL_BF16)
+    if (dtype == FL_F32) { convert_kernel<float><<<grid, 256, 0, st>>>(n, A_dev, lda, (float*)A_lo_dev, ld_lo); fl::count_launch(); }
+    else if (dtype == FL_BF16) {
         convert_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(n, A_dev, lda, (__nv_bfloat16*)A_lo_dev, ld_lo);
-    else return FL_EINVAL;
+        fl::count_launch();
+    } else {
+        return FL_EINVAL;
+    }
     return cudaGetLastError() == cudaSuccess ? FL_OK : FL_ECUDA;
 }
 
@@ -478,7 +485,7 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
     int r = get_work(h, n, w);
     if (r != FL_OK) return r;
     const unsigned g = (unsigned)((n + 255) / 256);
-    diag_inv_kernel<<<g, 256, 0, st>>>(n, FL_F64, A_dev, lda, w.dinv);
+    diag_inv_kernel<<<g, 256, 0, st>>>(n, FL_F64, A_dev, lda, w.dinv); fl::count_launch();
     FL_CU(h, cudaGetLastError());
     fl_solve_info inf{};
     int status = FL_OK;
@@ -490,10 +497,10 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
         inf.outer_iterations = 1;
     } else {
         // float64 iterative refinement around a low-precision Jacobi-PCG
-        diag_inv_kernel<<<g, 256, 0, st>>>(n, o.inner_dtype, o.A_lo_dev, o.ld_lo, w.dinv_lo);
-        zero_kernel<<<g, 256, 0, st>>>(n, u_dev);
-        dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, b_dev, b_dev, w.ppq);
-        sum_partials_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, &w.s->bb);
+        diag_inv_kernel<<<g, 256, 0, st>>>(n, o.inner_dtype, o.A_lo_dev, o.ld_lo, w.dinv_lo); fl::count_launch();
+        zero_kernel<<<g, 256, 0, st>>>(n, u_dev); fl::count_launch();
+        dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, b_dev, b_dev, w.ppq); fl::count_launch();
+        sum_partials_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, &w.s->bb); fl::count_launch();
         FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
         FL_CU(h, cudaStreamSynchronize(st));
         const double bb = w.s_host->bb;
@@ -503,9 +510,9 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
         while (outer < o.maxit) {
             // r = b - A u in float64
             FL_CU(h, gemv(FL_F64, A_dev, lda, n, u_dev, 1, w.q, 1, w.xf, st));
-            residual_kernel<<<g, 256, 0, st>>>(n, b_dev, w.q, rvec);
-            dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, rvec, rvec, w.ppq);
-            sum_partials_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, &w.s->rr);
+            residual_kernel<<<g, 256, 0, st>>>(n, b_dev, w.q, rvec); fl::count_launch();
+            dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, rvec, rvec, w.ppq); fl::count_launch();
+            sum_partials_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, &w.s->rr); fl::count_launch();
             FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
             FL_CU(h, cudaStreamSynchronize(st));
             const double rel = (bb > 0) ? std::sqrt(w.s_host->rr / bb) : 0.0;
@@ -522,7 +529,7 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
                 status = ir;
                 break;
             }
-            axpy_kernel<<<g, 256, 0, st>>>(n, 1.0, w.d, u_dev);
+            axpy_kernel<<<g, 256, 0, st>>>(n, 1.0, w.d, u_dev); fl::count_launch();
             ++outer;
         }
         inf.iterations = total;
@@ -530,11 +537,11 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
     }
     // final residual in float64
     FL_CU(h, gemv(FL_F64, A_dev, lda, n, u_dev, 1, w.q, 1, w.xf, st));
-    residual_kernel<<<g, 256, 0, st>>>(n, b_dev, w.q, w.t);
-    dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.t, w.t, w.ppq);
-    sum_partials_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, &w.s->rr);
-    dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, b_dev, b_dev, w.ppq);
-    sum_partials_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, &w.s->bb);
+    residual_kernel<<<g, 256, 0, st>>>(n, b_dev, w.q, w.t); fl::count_launch();
+    dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.t, w.t, w.ppq); fl::count_launch();
+    sum_partials_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, &w.s->rr); fl::count_launch();
+    dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, b_dev, b_dev, w.ppq); fl::count_launch();
+    sum_partials_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, &w.s->bb); fl::count_launch();
     FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
     FL_CU(h, cudaStreamSynchronize(st));
     inf.rel_residual = (w.s_host->bb > 0) ? std::sqrt(w.s_host->rr / w.s_host->bb) : 0.0;

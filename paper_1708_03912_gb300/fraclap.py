@@ -23,7 +23,9 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
           6: "FL_ETIMEOUT", 7: "FL_ENOTIMPL"}
 
 EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
-           "fl_assemble", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve"]
+           "fl_assemble", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
+           "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count"]
+STAGES = ["prep", "far", "near", "touch", "bnd", "element", "compose"]
 
 
 class FlError(RuntimeError):
@@ -41,6 +43,12 @@ class fl_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("inner_dtype", ctypes.c_int),
                 ("A_lo_dev", ctypes.c_void_p), ("ld_lo", ctypes.c_int64), ("inner_tol", ctypes.c_double),
                 ("inner_maxit", ctypes.c_int)]
+
+
+class fl_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "n_cells", "n_vertices", "n_facets", "n_dofs", "n_tiles", "n_touch_pairs", "n_near_pairs", "n_far_pairs",
+        "n_cells_with_dof", "nnz_nearfield", "h2d_bytes", "workspace_bytes")]
 
 
 class fl_solve_info(ctypes.Structure):
@@ -84,6 +92,14 @@ def lib():
     L.fl_default_solve_opts.restype = None
     L.fl_solve.argtypes = [vp, i64, vp, i64, vp, vp, ctypes.POINTER(fl_solve_opts), ctypes.POINTER(fl_solve_info), vp]
     L.fl_solve.restype = ci
+    L.fl_get_stats.argtypes = [vp, dbl, ctypes.POINTER(fl_stats)]
+    L.fl_get_stats.restype = ci
+    L.fl_set_profiling.argtypes = [vp, ci]
+    L.fl_set_profiling.restype = ci
+    L.fl_stage_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.fl_stage_ms.restype = ci
+    L.fl_launch_count.argtypes = []
+    L.fl_launch_count.restype = ctypes.c_uint64
     _ = i32
     _lib = L
     return L
@@ -183,6 +199,26 @@ def fl_solve(h, A, b, u, opts=None, stream=None):
     if r not in (FL_OK, FL_ENOTCONV, FL_ENOTSPD):
         _check(r, h)
     return info
+
+
+def fl_get_stats(h, s):
+    st = fl_stats()
+    _check(lib().fl_get_stats(h, s, ctypes.byref(st)), h)
+    return {k: getattr(st, k) for k, _ in fl_stats._fields_}
+
+
+def fl_set_profiling(h, enable=True):
+    _check(lib().fl_set_profiling(h, int(enable)), h)
+
+
+def fl_stage_ms(h):
+    out = (ctypes.c_double * len(STAGES))()
+    _check(lib().fl_stage_ms(h, out), h)
+    return dict(zip(STAGES, list(out)))
+
+
+def fl_launch_count():
+    return int(lib().fl_launch_count())
 
 
 # ------------------------------------------------------------- convenience --

@@ -88,3 +88,18 @@ def test_pcg_reports_breakdown_on_indefinite_matrix():
     info = F.fl_solve(m.h, A, b, u)
     assert info.status == F.FL_ENOTSPD
     m.close()
+
+
+def test_small_systems_solve():
+    # n = 1 (two intervals) and n = 39 (4-ring disc): workspace layout at tiny sizes
+    for (V, T), s in ((synth.interval(2), 0.3), (synth.disc(4), 0.75)):
+        om = OracleMesh(V, T)
+        m = F.Mesh(V, T)
+        A = m.assemble(s)
+        b = m.load_vector(s)
+        u, info = m.solve(A, b, tol=1e-12)
+        Ao, _ = assemble_matrix(om, s)
+        uo = solve.cholesky_solve(Ao, load_vector(om, s))
+        assert info.status == F.FL_OK
+        assert np.max(np.abs(u.cpu().numpy() - uo)) <= 1e-8 * np.max(np.abs(uo))
+        m.close()
