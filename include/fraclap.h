@@ -212,6 +212,35 @@ int fl_stage_ms(fl_handle h, double* ms_out /* [FL_NSTAGES] */);
 /* Number of kernels this library has launched in the process so far. */
 uint64_t fl_launch_count(void);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free float32 matrix-vector product.  The paper has no counterpart;
+ * this is a service for callers that cannot allocate device memory: code that
+ * runs under a caller-owned memory budget or inside another allocator's arena,
+ * real-time loops that must not enter the driver's allocator, and hosts that only
+ * receive device pointers and own no allocator.  fl_matvec(FL_F32, ...) allocates
+ * a float32 copy of x on every call; this entry point keeps that copy in a fixed
+ * device array of FL_STATIC_MAX_N floats (256 KiB) that every GPU which loads the
+ * library holds until the process exits.
+ * ------------------------------------------------------------------------ */
+#define FL_STATIC_MAX_N 65536
+
+/*
+ * y_dev[n] = A_dev x_dev for A_dev float32 (n x n, row-major, lda >= n), x_dev and
+ * y_dev float64 device vectors (contiguous).  Same arithmetic as fl_matvec with
+ * FL_F32: x rounded to float32, float32 lane sums, float64 row totals.
+ * Returns FL_EINVAL for n < 1 or n > FL_STATIC_MAX_N (nothing is launched), for
+ * NULL pointers or lda < n; FL_ECUDA if the device array cannot be located or a
+ * launch fails.  Calls no allocator.
+ * The first call on each device looks up that device's copy of the array
+ * (cudaGetSymbolAddress) with the device current; make that first call before any
+ * stream capture.  All calls on a device share the one array and each call
+ * rewrites the n entries it reads, so nothing has to be cleared between calls, but
+ * calls that overlap on the GPU (different streams, or different host threads)
+ * race on it: serialise them.
+ */
+int fl_matvec_f32_static(const float* A_dev, int64_t lda, int64_t n, const double* x_dev, double* y_dev,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

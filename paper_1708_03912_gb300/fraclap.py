@@ -24,7 +24,8 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
 
 EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
            "fl_assemble", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
-           "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count"]
+           "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_matvec_f32_static"]
+FL_STATIC_MAX_N = 65536
 STAGES = ["prep", "far", "near", "touch", "bnd", "element", "compose"]
 
 
@@ -100,6 +101,8 @@ def lib():
     L.fl_stage_ms.restype = ci
     L.fl_launch_count.argtypes = []
     L.fl_launch_count.restype = ctypes.c_uint64
+    L.fl_matvec_f32_static.argtypes = [vp, i64, i64, vp, vp, vp]
+    L.fl_matvec_f32_static.restype = ci
     _ = i32
     _lib = L
     return L
@@ -219,6 +222,12 @@ def fl_stage_ms(h):
 
 def fl_launch_count():
     return int(lib().fl_launch_count())
+
+
+def fl_matvec_f32_static(A32, x, y, stream=None):
+    """y = A32 x without any device allocation (for callers that cannot allocate);
+    n <= FL_STATIC_MAX_N.  Returns the status code (0 = FL_OK) instead of raising."""
+    return lib().fl_matvec_f32_static(_ptr(A32), A32.stride(0), A32.shape[0], _ptr(x), _ptr(y), _stream(stream))
 
 
 # ------------------------------------------------------------- convenience --
