@@ -71,8 +71,9 @@ struct FarArgs {
     const int* inc_ptr;
     const int* inc_ent;
     T* P;
-    T* Pd;
+    T* Pd;      // [cell][block][point] row sums
     int64_t nc;
+    int64_t nblk;
     T expo;
 };
 
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
             const int a = w * 32 + lane;
             if (a < Q) {
                 if (I == J) sD[kk * Q + a] += myD[w];
-                else A.Pd[((int64_t)J * nc + K) * Q + a] = myD[w];
+                else A.Pd[((int64_t)K * A.nblk + J) * Q + a] = myD[w];
             }
         }
     }
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
         for (int b = 0; b < Q; ++b) {
             T v = S[b];
             if (I == J) v += sD[lane * Q + b];
-            A.Pd[((int64_t)I * nc + Kt) * Q + b] = v;
+            A.Pd[((int64_t)Kt * A.nblk + I) * Q + b] = v;
         }
     }
     // partial block over the local DOF lists of blocks I and J
@@ -328,15 +329,109 @@ __global__ void near_pair_kernel(int nnear, const int* np_a, const int* np_b, co
         for (int j = 0; j < NV; ++j) out[i * NV + j] = -C * ja * jb * off[i][j];
 }
 
+// Same computation with the order-6 rule as compile-time tables in the arithmetic
+// type: per evaluation only float (or only double) operations, S in registers.
+template <typename T, int QN, int D>
+struct NearRule {
+    T lam[QN * D];
+    T w[QN];
+    T wphi[QN * (D + 1)];
+};
+
+template <int D, typename T, int PW, int QN>
+__global__ void near_pair_fast(int nnear, const int* np_a, const int* np_b, const double* cvx, const double* cen,
+                               const double* jac, const NearRule<T, QN, D> R, T expo, double C, double* contrib,
+                               int64_t slot0, double* Dn) {
+    constexpr int NV = D + 1;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnear) return;
+    const int ka = np_a[p], kb = np_b[p];
+    T e0a[D], e1a[D], e2a[D], e0b[D], e1b[D], e2b[D], dc[D];
+    const double* va = cvx + (int64_t)ka * NV * D;
+    const double* vb = cvx + (int64_t)kb * NV * D;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        e0a[d] = (T)(va[d] - cen[(int64_t)ka * D + d]);
+        e0b[d] = (T)(vb[d] - cen[(int64_t)kb * D + d]);
+        e1a[d] = (T)(va[D + d] - va[d]);
+        e1b[d] = (T)(vb[D + d] - vb[d]);
+        if constexpr (D == 2) {
+            e2a[d] = (T)(va[2 * D + d] - va[d]);
+            e2b[d] = (T)(vb[2 * D + d] - vb[d]);
+        } else {
+            e2a[d] = T(0);
+            e2b[d] = T(0);
+        }
+        dc[d] = (T)(cen[(int64_t)ka * D + d] - cen[(int64_t)kb * D + d]);
+    }
+    T S[QN];
+#pragma unroll
+    for (int b = 0; b < QN; ++b) S[b] = T(0);
+    T off[NV][NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) off[i][j] = T(0);
+    const double ja = jac[ka], jb = jac[kb];
+    double* Da = Dn + ((int64_t)p * 2 + 0) * QN;
+    double* Db = Dn + ((int64_t)p * 2 + 1) * QN;
+#pragma unroll 1
+    for (int a = 0; a < QN; ++a) {
+        T xa[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            xa[d] = dc[d] + e0a[d] + R.lam[a * D] * e1a[d];
+            if constexpr (D == 2) xa[d] += R.lam[a * D + 1] * e2a[d];
+        }
+        T t[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) t[v] = T(0);
+        const T wa = R.w[a];
+#pragma unroll
+        for (int b = 0; b < QN; ++b) {
+            T r2 = T(0);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                T yb = e0b[d] + R.lam[b * D] * e1b[d];
+                if constexpr (D == 2) yb += R.lam[b * D + 1] * e2b[d];
+                const T df = xa[d] - yb;
+                r2 = fma(df, df, r2);
+            }
+            const T kv = kpow<PW>(r2, expo);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) t[v] = fma(R.wphi[b * NV + v], kv, t[v]);
+            S[b] = fma(wa, kv, S[b]);
+        }
+        T u = t[0];
+#pragma unroll
+        for (int v = 1; v < NV; ++v) u += t[v];
+        Da[a] = jb * (double)u;
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+#pragma unroll
+            for (int j = 0; j < NV; ++j) off[i][j] = fma(R.wphi[a * NV + i], t[j], off[i][j]);
+    }
+#pragma unroll
+    for (int b = 0; b < QN; ++b) Db[b] = ja * (double)S[b];
+    double* out = contrib + slot0 + (int64_t)p * NV * NV;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) out[i * NV + j] = -C * ja * jb * (double)off[i][j];
+}
+
 // ---------------------------------------------------------- touching pairs --
-// Common edge / common vertex pairs (2D) and common vertex pairs (1D), float64.
-// Tables (per s) hold the angular / Duffy points with the exact radial factor
-// already folded into their weights.
+// Common edge / common vertex pairs (2D) and common vertex pairs (1D), float64,
+// one warp per pair: lanes take the points of the (per-s) table in a strided
+// order, then a butterfly sum gives every lane the same totals.
+// Tables hold the angular / Duffy points with the exact radial factor folded into
+// their weights.
 template <int PW>
 __global__ void touch_pair_kernel(int ntp, int dim, const int* tp_type, const int* tp_vert, const int* tp_cell,
                                   const int64_t* tp_slot, const double* V, const double* jac_orig,
                                   const double* rule, RuleOffsets ro, double s, double C, double* contrib) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int p = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (p >= ntp) return;
     const int type = tp_type[p];
     const int* tv = tp_vert + 5 * p;
@@ -346,18 +441,23 @@ __global__ void touch_pair_kernel(int ntp, int dim, const int* tp_type, const in
         const double* tb = rule + ro.t_1d;
         const double h1 = jK, h2 = jM;
         const double e = -1.0 - 2.0 * s;
-        double acc[3][3] = {};
-        for (int m = 0; m < ro.n_1d; ++m) {
+        double acc[6] = {};
+        for (int m = lane; m < ro.n_1d; m += 32) {
             const double eta = tb[2 * m], wt = tb[2 * m + 1];
             const double d1[3] = {1.0, -1.0 + eta, -eta};
             const double d2[3] = {eta, 1.0 - eta, -1.0};
             const double k1 = wt * pow(h1 + h2 * eta, e), k2 = wt * pow(h1 * eta + h2, e);
+            int q = 0;
             for (int i = 0; i < 3; ++i)
-                for (int j = i; j < 3; ++j) acc[i][j] += k1 * d1[i] * d1[j] + k2 * d2[i] * d2[j];
+                for (int j = i; j < 3; ++j) acc[q++] += k1 * d1[i] * d1[j] + k2 * d2[i] * d2[j];
         }
-        const double sc = C * h1 * h2 / (3.0 - 2.0 * s);
-        for (int i = 0; i < 3; ++i)
-            for (int j = i; j < 3; ++j) out[i * 3 + j] = out[j * 3 + i] = sc * acc[i][j];
+        for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
+        if (lane == 0) {
+            const double sc = C * h1 * h2 / (3.0 - 2.0 * s);
+            int q = 0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = i; j < 3; ++j, ++q) out[i * 3 + j] = out[j * 3 + i] = sc * acc[q];
+        }
         return;
     }
     const double e2 = -(1.0 + s);
@@ -367,18 +467,28 @@ __global__ void touch_pair_kernel(int ntp, int dim, const int* tp_type, const in
         const double b[2] = {R_[0] - Q_[0], R_[1] - Q_[1]};
         const double c[2] = {-(Rt[0] - Q_[0]), -(Rt[1] - Q_[1])};
         const double* tb = rule + ro.t_edge;
-        double acc[4][4] = {};
-        for (int m = 0; m < ro.n_edge; ++m) {
+        double acc[10] = {};
+        for (int m = lane; m < ro.n_edge; m += 32) {
             const double* r = tb + 8 * m;  // dphi[4], w1, w2, w3, weight
             const double x = a[0] * r[4] + b[0] * r[5] + c[0] * r[6];
             const double y = a[1] * r[4] + b[1] * r[5] + c[1] * r[6];
             const double f = r[7] * kpow<PW>(x * x + y * y, e2);
-            for (int i = 0; i < 4; ++i)
-                for (int j = i; j < 4; ++j) acc[i][j] += f * r[i] * r[j];
+            int q = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const double fi = f * r[i];
+#pragma unroll
+                for (int j = i; j < 4; ++j) acc[q++] += fi * r[j];
+            }
         }
-        const double sc = C * jK * jM / ((3.0 - 2.0 * s) * (4.0 - 2.0 * s));
-        for (int i = 0; i < 4; ++i)
-            for (int j = i; j < 4; ++j) out[i * 4 + j] = out[j * 4 + i] = sc * acc[i][j];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) acc[q] = warp_sum(acc[q]);
+        if (lane == 0) {
+            const double sc = C * jK * jM / ((3.0 - 2.0 * s) * (4.0 - 2.0 * s));
+            int q = 0;
+            for (int i = 0; i < 4; ++i)
+                for (int j = i; j < 4; ++j, ++q) out[i * 4 + j] = out[j * 4 + i] = sc * acc[q];
+        }
     } else {  // common vertex P: K = (P,Q,R), M = (P,Qt,Rt)
         const double *P_ = V + 2 * tv[0], *Q_ = V + 2 * tv[1], *R_ = V + 2 * tv[2], *Qt = V + 2 * tv[3], *Rt = V + 2 * tv[4];
         const double a1[2] = {Q_[0] - P_[0], Q_[1] - P_[1]};
@@ -386,18 +496,28 @@ __global__ void touch_pair_kernel(int ntp, int dim, const int* tp_type, const in
         const double a3[2] = {-(Qt[0] - P_[0]), -(Qt[1] - P_[1])};
         const double a4[2] = {-(Rt[0] - Qt[0]), -(Rt[1] - Qt[1])};
         const double* tb = rule + ro.t_vert;
-        double acc[5][5] = {};
-        for (int m = 0; m < ro.n_vert; ++m) {
+        double acc[15] = {};
+        for (int m = lane; m < ro.n_vert; m += 32) {
             const double* r = tb + 10 * m;  // dphi[5], x1, x2, y1, y2, weight
             const double x = a1[0] * r[5] + a2[0] * r[6] + a3[0] * r[7] + a4[0] * r[8];
             const double y = a1[1] * r[5] + a2[1] * r[6] + a3[1] * r[7] + a4[1] * r[8];
             const double f = r[9] * kpow<PW>(x * x + y * y, e2);
-            for (int i = 0; i < 5; ++i)
-                for (int j = i; j < 5; ++j) acc[i][j] += f * r[i] * r[j];
+            int q = 0;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const double fi = f * r[i];
+#pragma unroll
+                for (int j = i; j < 5; ++j) acc[q++] += fi * r[j];
+            }
         }
-        const double sc = C * jK * jM / (4.0 - 2.0 * s);
-        for (int i = 0; i < 5; ++i)
-            for (int j = i; j < 5; ++j) out[i * 5 + j] = out[j * 5 + i] = sc * acc[i][j];
+#pragma unroll
+        for (int q = 0; q < 15; ++q) acc[q] = warp_sum(acc[q]);
+        if (lane == 0) {
+            const double sc = C * jK * jM / (4.0 - 2.0 * s);
+            int q = 0;
+            for (int i = 0; i < 5; ++i)
+                for (int j = i; j < 5; ++j, ++q) out[i * 5 + j] = out[j * 5 + i] = sc * acc[q];
+        }
     }
 }
 
@@ -498,9 +618,17 @@ struct ElemArgs {
     int64_t slot0;
 };
 
+// One warp per cell with DOFs.  Lanes take quadrature points (or partner blocks)
+// in a strided order; the upper triangle of the local block is summed over lanes
+// with a butterfly at the end.
+__device__ __forceinline__ int tri_index(int i, int j, int NV) {  // i <= j
+    return i * NV - i * (i - 1) / 2 + (j - i);
+}
+
 template <int PW>
 __global__ void element_kernel(ElemArgs A) {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (k >= A.nc || !A.hasdof[k]) return;
     const int D = A.dim, NV = D + 1;
     const RuleOffsets& ro = A.ro;
@@ -508,25 +636,25 @@ __global__ void element_kernel(ElemArgs A) {
     const double s = A.s, C = A.C;
     const double* v = A.cvx + k * NV * D;
     const double jk = A.jac[k];
-    double blk[3][3] = {};
+    double blk[6] = {};
     const int qf = ro.qf, qn = ro.qn;
-    // diagonal block from the far row sums (fixed order over blocks)
+    // diagonal block from the far row sums (fixed order over partner blocks) and far facets
     {
         const double* w = rule + ro.far_w;
         const double* phi = rule + ro.far_phi;
-        for (int a = 0; a < qf; ++a) {
+        for (int a = lane; a < qf; a += 32) {
             double Dk = 0.0;
             if (A.pd_is_float) {
-                const float* Pd = (const float*)A.Pd;
-                for (int64_t B = 0; B < A.nblk; ++B) Dk += (double)Pd[(B * A.nc + k) * qf + a];
+                const float* Pd = (const float*)A.Pd + k * A.nblk * qf + a;
+                for (int64_t B = 0; B < A.nblk; ++B) Dk += (double)Pd[B * qf];
             } else {
-                const double* Pd = (const double*)A.Pd;
-                for (int64_t B = 0; B < A.nblk; ++B) Dk += Pd[(B * A.nc + k) * qf + a];
+                const double* Pd = (const double*)A.Pd + k * A.nblk * qf + a;
+                for (int64_t B = 0; B < A.nblk; ++B) Dk += Pd[B * qf];
             }
-            double bf = (D == 2 && !A.regional) ? A.Bf[k * qf + a] : 0.0;
+            const double bf = (D == 2 && !A.regional) ? A.Bf[k * qf + a] : 0.0;
             const double f = jk * w[a] * (C * Dk + C / (2.0 * s) * bf);
             for (int i = 0; i < NV; ++i)
-                for (int j = i; j < NV; ++j) blk[i][j] += f * phi[a * NV + i] * phi[a * NV + j];
+                for (int j = i; j < NV; ++j) blk[tri_index(i, j, NV)] += f * phi[a * NV + i] * phi[a * NV + j];
         }
     }
     // near pairs (both roles) and near boundary facets, order-k_near points
@@ -534,22 +662,22 @@ __global__ void element_kernel(ElemArgs A) {
         const double* w = rule + ro.near_w;
         const double* phi = rule + ro.near_phi;
         const double* lam = rule + ro.near_lam;
-        double Bn[MAXQ_NEAR];
-        for (int a = 0; a < qn; ++a) Bn[a] = 0.0;
-        if (!A.regional) {
-            for (int q = A.ef_ptr[k]; q < A.ef_ptr[k + 1]; ++q) {
-                if (A.ef_cls[q] != 1) continue;
-                const int f = A.ef_fac[q];
-                for (int a = 0; a < qn; ++a) {
-                    double xa[2];
-                    for (int d = 0; d < D; ++d) {
-                        xa[d] = v[d] + lam[a * D] * (v[D + d] - v[d]);
-                        if (D == 2) xa[d] += lam[a * D + 1] * (v[2 * D + d] - v[d]);
-                    }
+        for (int a = lane; a < qn; a += 32) {
+            double Dk = 0.0;
+            for (int q = A.enp_ptr[k]; q < A.enp_ptr[k + 1]; ++q) Dk += A.Dn[(int64_t)A.enp_ent[q] * qn + a];
+            double Bn = 0.0;
+            if (!A.regional) {
+                double xa[2] = {0.0, 0.0};
+                for (int d = 0; d < D; ++d) {
+                    xa[d] = v[d] + lam[a * D] * (v[D + d] - v[d]);
+                    if (D == 2) xa[d] += lam[a * D + 1] * (v[2 * D + d] - v[d]);
+                }
+                for (int q = A.ef_ptr[k]; q < A.ef_ptr[k + 1]; ++q) {
+                    if (A.ef_cls[q] != 1) continue;
+                    const int f = A.ef_fac[q];
                     if (D == 1) {
-                        const double y = A.V[A.F[f]];
-                        const double dx = xa[0] - y;
-                        Bn[a] += A.FN[f] * dx * pow(dx * dx, -(1.0 + 2.0 * s) / 2.0);
+                        const double dx = xa[0] - A.V[A.F[f]];
+                        Bn += A.FN[f] * dx * pow(dx * dx, -(1.0 + 2.0 * s) / 2.0);
                     } else {
                         const double* E0 = A.V + 2 * A.F[2 * f];
                         const double* E1 = A.V + 2 * A.F[2 * f + 1];
@@ -557,57 +685,46 @@ __global__ void element_kernel(ElemArgs A) {
                         const double* gw = rule + ro.gln_w;
                         double acc = 0.0;
                         for (int b = 0; b < ro.kn; ++b) {
-                            const double yx = E0[0] + gt[b] * (E1[0] - E0[0]);
-                            const double yy = E0[1] + gt[b] * (E1[1] - E0[1]);
-                            const double dx = xa[0] - yx, dy = xa[1] - yy;
+                            const double dx = xa[0] - (E0[0] + gt[b] * (E1[0] - E0[0]));
+                            const double dy = xa[1] - (E0[1] + gt[b] * (E1[1] - E0[1]));
                             acc += gw[b] * A.FLEN[f] * (A.FN[2 * f] * dx + A.FN[2 * f + 1] * dy) *
                                    kpow<PW>(dx * dx + dy * dy, -(1.0 + s));
                         }
-                        Bn[a] += acc;
+                        Bn += acc;
                     }
                 }
             }
-        }
-        for (int a = 0; a < qn; ++a) {
-            double Dk = 0.0;
-            for (int q = A.enp_ptr[k]; q < A.enp_ptr[k + 1]; ++q) {
-                const int e = A.enp_ent[q];
-                Dk += A.Dn[(int64_t)e * qn + a];
-            }
-            const double f = jk * w[a] * (C * Dk + C / (2.0 * s) * Bn[a]);
+            const double f = jk * w[a] * (C * Dk + C / (2.0 * s) * Bn);
             for (int i = 0; i < NV; ++i)
-                for (int j = i; j < NV; ++j) blk[i][j] += f * phi[a * NV + i] * phi[a * NV + j];
+                for (int j = i; j < NV; ++j) blk[tri_index(i, j, NV)] += f * phi[a * NV + i] * phi[a * NV + j];
         }
     }
     // identical pair
     if (D == 1) {
-        const double val = C * pow(jk, 1.0 - 2.0 * s) / ((2.0 - 2.0 * s) * (3.0 - 2.0 * s));
-        blk[0][0] += val;
-        blk[0][1] -= val;
-        blk[1][1] += val;
+        if (lane == 0) {
+            const double val = C * pow(jk, 1.0 - 2.0 * s) / ((2.0 - 2.0 * s) * (3.0 - 2.0 * s));
+            blk[0] += val;
+            blk[1] -= val;
+            blk[2] += val;
+        }
     } else {
         const double J00 = v[2] - v[0], J10 = v[3] - v[1], J01 = v[4] - v[0], J11 = v[5] - v[1];
         const double* tb = rule + ro.t_ident;
-        double acc[3][3] = {};
-        for (int m = 0; m < ro.n_ident; ++m) {
-            const double u0 = tb[3 * m], u1 = tb[3 * m + 1], f0 = tb[3 * m + 2];
-            const double jx = J00 * u0 + J01 * u1, jy = J10 * u0 + J11 * u1;
-            const double f = f0 * kpow<PW>(jx * jx + jy * jy, -(1.0 + s));
-            const double g[3] = {-u0 - u1, u0, u1};
-            for (int i = 0; i < 3; ++i)
-                for (int j = i; j < 3; ++j) acc[i][j] += f * g[i] * g[j];
-        }
         const double beta = 2.0 / ((2.0 - 2.0 * s) * (3.0 - 2.0 * s) * (4.0 - 2.0 * s));
         const double sc = 0.5 * C * jk * jk * beta;
-        for (int i = 0; i < 3; ++i)
-            for (int j = i; j < 3; ++j) blk[i][j] += sc * acc[i][j];
+        for (int m = lane; m < ro.n_ident; m += 32) {
+            const double u0 = tb[3 * m], u1 = tb[3 * m + 1], f0 = tb[3 * m + 2];
+            const double jx = J00 * u0 + J01 * u1, jy = J10 * u0 + J11 * u1;
+            const double f = sc * f0 * kpow<PW>(jx * jx + jy * jy, -(1.0 + s));
+            const double g[3] = {-u0 - u1, u0, u1};
+            for (int i = 0; i < 3; ++i)
+                for (int j = i; j < 3; ++j) blk[tri_index(i, j, 3)] += f * g[i] * g[j];
+        }
     }
     // boundary facets: touching ones (and, in 1D, far ones)
     if (!A.regional) {
         const int* cv = A.corner + k * NV;
         if (D == 1) {
-            const double* gt = rule + ro.glf_t;  // unused in 1D
-            (void)gt;
             int ep = A.ef_ptr[k], ee = A.ef_ptr[k + 1];
             const double* w = rule + ro.far_w;
             const double* lam = rule + ro.far_lam;
@@ -619,27 +736,28 @@ __global__ void element_kernel(ElemArgs A) {
                 if (cls == 1) continue;  // near: done above
                 const int e = A.F[f];
                 if (cls == 2) {
-                    // e is an end of K: exact ∫ phi_i phi_j |x-e|^{-2s}
-                    const int me = (cv[0] == e) ? 0 : 1;
-                    double a_[2], b_[2];
-                    a_[me] = 1.0, a_[1 - me] = 0.0;
-                    b_[me] = -1.0, b_[1 - me] = 1.0;
-                    const double sc = C / (2.0 * s) * pow(jk, 1.0 - 2.0 * s);
-                    for (int i = 0; i < 2; ++i)
-                        for (int j = i; j < 2; ++j) {
-                            double val = (a_[i] * b_[j] + a_[j] * b_[i]) / (2.0 - 2.0 * s) + b_[i] * b_[j] / (3.0 - 2.0 * s);
-                            if (a_[i] * a_[j] != 0.0) val += a_[i] * a_[j] / (1.0 - 2.0 * s);
-                            blk[i][j] += sc * val;
-                        }
+                    if (lane == 0) {
+                        // e is an end of K: exact ∫ phi_i phi_j |x-e|^{-2s}
+                        const int me = (cv[0] == e) ? 0 : 1;
+                        double a_[2], b_[2];
+                        a_[me] = 1.0, a_[1 - me] = 0.0;
+                        b_[me] = -1.0, b_[1 - me] = 1.0;
+                        const double sc = C / (2.0 * s) * pow(jk, 1.0 - 2.0 * s);
+                        for (int i = 0; i < 2; ++i)
+                            for (int j = i; j < 2; ++j) {
+                                double val = (a_[i] * b_[j] + a_[j] * b_[i]) / (2.0 - 2.0 * s) + b_[i] * b_[j] / (3.0 - 2.0 * s);
+                                if (a_[i] * a_[j] != 0.0) val += a_[i] * a_[j] / (1.0 - 2.0 * s);
+                                blk[tri_index(i, j, 2)] += sc * val;
+                            }
+                    }
                 } else {
                     const double y = A.V[e];
-                    for (int a = 0; a < qf; ++a) {
-                        const double x = v[0] + lam[a] * (v[1] - v[0]);
-                        const double dx = x - y;
+                    for (int a = lane; a < qf; a += 32) {
+                        const double dx = v[0] + lam[a] * (v[1] - v[0]) - y;
                         const double g = A.FN[f] * dx * pow(dx * dx, -(1.0 + 2.0 * s) / 2.0);
                         const double fw = C / (2.0 * s) * jk * w[a] * g;
                         for (int i = 0; i < 2; ++i)
-                            for (int j = i; j < 2; ++j) blk[i][j] += fw * phi[a * 2 + i] * phi[a * 2 + j];
+                            for (int j = i; j < 2; ++j) blk[tri_index(i, j, 2)] += fw * phi[a * 2 + i] * phi[a * 2 + j];
                     }
                 }
             }
@@ -661,17 +779,16 @@ __global__ void element_kernel(ElemArgs A) {
                     const double ax = pE1[0] - pE0[0], ay = pE1[1] - pE0[1];
                     const double bx = pR[0] - pE1[0], by = pR[1] - pE1[1];
                     const double* tb = rule + ro.b_own;
-                    double acc = 0.0;
-                    for (int m = 0; m < ro.n_own; ++m) {
+                    const double sc = C / (2.0 * s) * jk * A.FLEN[f] / ((3.0 - 2.0 * s) * (4.0 - 2.0 * s));
+                    for (int m = lane; m < ro.n_own; m += 32) {
                         const double o1 = tb[3 * m], o2 = tb[3 * m + 1], wt = tb[3 * m + 2];
                         const double x = ax * o1 + bx * o2, y = ay * o1 + by * o2;
-                        acc += wt * H * o2 * kpow<PW>(x * x + y * y, -(1.0 + s)) * o2 * o2;
+                        blk[tri_index(r, r, 3)] += sc * wt * H * o2 * kpow<PW>(x * x + y * y, -(1.0 + s)) * o2 * o2;
                     }
-                    blk[r][r] += C / (2.0 * s) * jk * A.FLEN[f] * acc / ((3.0 - 2.0 * s) * (4.0 - 2.0 * s));
                 } else if (cls == 3) {
                     // facet and K share one vertex P
                     const int fa = A.F[2 * f], fb = A.F[2 * f + 1];
-                    int ip = -1;
+                    int ip = 0;
                     for (int i = 0; i < 3; ++i)
                         if (cv[i] == fa || cv[i] == fb) ip = i;
                     const int P = cv[ip], E1 = (P == fa) ? fb : fa;
@@ -685,39 +802,36 @@ __global__ void element_kernel(ElemArgs A) {
                     const double gr[2] = {pR[0] - pQ[0], pR[1] - pQ[1]};
                     const double ge[2] = {pE[0] - pP[0], pE[1] - pP[1]};
                     const double* tb = rule + ro.b_vert;
+                    const double sc = C / (2.0 * s) * jk * A.FLEN[f];
+                    const int idx[3] = {ip, iq, ir};
                     // local order (P, Q, R): a = e_P, bh = (e_Q - e_P) x1 + (e_R - e_Q) x2
-                    double m0 = 0.0, m1[3] = {0, 0, 0}, m2[3][3] = {};
-                    for (int m = 0; m < ro.n_bvert; ++m) {
+                    for (int m = lane; m < ro.n_bvert; m += 32) {
                         const double x1 = tb[4 * m], x2 = tb[4 * m + 1], t = tb[4 * m + 2], wt = tb[4 * m + 3];
                         const double xpx = gq[0] * x1 + gr[0] * x2, xpy = gq[1] * x1 + gr[1] * x2;
                         const double N = xpx * nx + xpy * ny;
                         const double dx = xpx - t * ge[0], dy = xpy - t * ge[1];
-                        const double g = wt * N * kpow<PW>(dx * dx + dy * dy, -(1.0 + s));
+                        const double g = sc * wt * N * kpow<PW>(dx * dx + dy * dy, -(1.0 + s));
                         const double bh[3] = {-x1, x1 - x2, x2};
-                        m0 += g;
-                        for (int i = 0; i < 3; ++i) {
-                            m1[i] += g * bh[i];
-                            for (int j = i; j < 3; ++j) m2[i][j] += g * bh[i] * bh[j];
-                        }
+                        for (int i = 0; i < 3; ++i)
+                            for (int j = i; j < 3; ++j) {
+                                const double ai = (i == 0) ? 1.0 : 0.0, aj = (j == 0) ? 1.0 : 0.0;
+                                double val = g * bh[i] * bh[j] / (4.0 - 2.0 * s) + g * (ai * bh[j] + aj * bh[i]) / (3.0 - 2.0 * s);
+                                if (ai * aj != 0.0) val += g / (2.0 - 2.0 * s);
+                                int I_ = idx[i], J_ = idx[j];
+                                if (I_ > J_) { const int tmp = I_; I_ = J_; J_ = tmp; }
+                                blk[tri_index(I_, J_, 3)] += val;
+                            }
                     }
-                    const double sc = C / (2.0 * s) * jk * A.FLEN[f];
-                    const int idx[3] = {ip, iq, ir};
-                    for (int i = 0; i < 3; ++i)
-                        for (int j = i; j < 3; ++j) {
-                            const double ai = (i == 0) ? 1.0 : 0.0, aj = (j == 0) ? 1.0 : 0.0;
-                            double val = m2[i][j] / (4.0 - 2.0 * s) + (ai * m1[j] + aj * m1[i]) / (3.0 - 2.0 * s);
-                            if (ai * aj != 0.0) val += m0 / (2.0 - 2.0 * s);
-                            int I_ = idx[i], J_ = idx[j];
-                            if (I_ > J_) { int tmp = I_; I_ = J_; J_ = tmp; }
-                            blk[I_][J_] += sc * val;
-                        }
                 }
             }
         }
     }
-    double* out = A.contrib + A.slot0 + k * NV * NV;
-    for (int i = 0; i < NV; ++i)
-        for (int j = i; j < NV; ++j) out[i * NV + j] = out[j * NV + i] = blk[i][j];
+    for (int q = 0; q < 6; ++q) blk[q] = warp_sum(blk[q]);
+    if (lane == 0) {
+        double* out = A.contrib + A.slot0 + k * NV * NV;
+        for (int i = 0; i < NV; ++i)
+            for (int j = i; j < NV; ++j) out[i * NV + j] = out[j * NV + i] = blk[tri_index(i, j, NV)];
+    }
 }
 
 // ---------------------------------------------------- gather and compose --
@@ -813,9 +927,9 @@ void stage_mark(fl_ctx* h, cudaStream_t st, int i, int end) {
     h->ev_recorded = true;
 }
 
-#define FL_TRY(x)               \
-    do {                        \
-        int r_ = (x);           \
+#define FL_TRY(...)                 \
+    do {                            \
+        int r_ = (__VA_ARGS__);     \
         if (r_ != FL_OK) return r_; \
     } while (0)
 
@@ -1084,6 +1198,7 @@ int launch_far_t(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<doubl
     A.P = (T*)t.P;
     A.Pd = (T*)t.Pd;
     A.nc = P.nc;
+    A.nblk = P.nblk;
     A.expo = (T)expo;
     const int maxL = std::max(1, P.maxL);
     size_t smem = 32 * D * sizeof(double) + 32 * sizeof(double) + 32 * Q * D * sizeof(T) + 32 * Q * sizeof(T) +
@@ -1175,6 +1290,44 @@ int launch_bnd(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, do
     }
 }
 
+template <int D, typename T, int QN, int PW>
+int launch_near_fast_t(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro,
+                       double expo, double C, cudaStream_t st) {
+    constexpr int NV = D + 1;
+    NearRule<T, QN, D> R;
+    for (int a = 0; a < QN; ++a) {
+        for (int d = 0; d < D; ++d) R.lam[a * D + d] = (T)rb[ro.near_lam + a * D + d];
+        R.w[a] = (T)rb[ro.near_w + a];
+        for (int v = 0; v < NV; ++v) R.wphi[a * NV + v] = (T)(rb[ro.near_w + a] * rb[ro.near_phi + a * NV + v]);
+    }
+    const int nnear = (int)P.np_a.size();
+    near_pair_fast<D, T, PW, QN><<<(unsigned)((nnear + 63) / 64), 64, 0, st>>>(nnear, t.np_a, t.np_b, t.cvx, t.cen,
+                                                                                t.jac, R, (T)expo, C, t.contrib,
+                                                                                P.np_slot0, t.Dn);
+    fl::count_launch();
+    FL_CUDA_TRY(h, cudaGetLastError());
+    return FL_OK;
+}
+
+template <int D, typename T, int QN>
+int launch_near_fast(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro,
+                     double expo, int pw, double C, cudaStream_t st) {
+    if constexpr (D == 2) {
+        if (pw == 6) return launch_near_fast_t<D, T, QN, 6>(h, P, t, rb, ro, expo, C, st);
+        if constexpr (sizeof(T) == 8) {
+            if (pw == 5) return launch_near_fast_t<D, T, QN, 5>(h, P, t, rb, ro, expo, C, st);
+            if (pw == 7) return launch_near_fast_t<D, T, QN, 7>(h, P, t, rb, ro, expo, C, st);
+        }
+    } else {
+        if (pw == 4) return launch_near_fast_t<D, T, QN, 4>(h, P, t, rb, ro, expo, C, st);
+        if constexpr (sizeof(T) == 8) {
+            if (pw == 3) return launch_near_fast_t<D, T, QN, 3>(h, P, t, rb, ro, expo, C, st);
+            if (pw == 5) return launch_near_fast_t<D, T, QN, 5>(h, P, t, rb, ro, expo, C, st);
+        }
+    }
+    return launch_near_fast_t<D, T, QN, 0>(h, P, t, rb, ro, expo, C, st);
+}
+
 }  // namespace
 
 // C(d,s) = 2^{2s} s Γ(s + d/2) / (π^{d/2} Γ(1 - s)), Section 2.
@@ -1235,7 +1388,16 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
     stage_mark(h, st, FL_STAGE_NEAR, 0);
     // near separated pairs
     const int nnear = (int)P.np_a.size();
-    if (nnear > 0) {
+    const bool near_fast = (D == 2 && ro.qn == 36) || (D == 1 && ro.qn == 6);
+    if (nnear > 0 && near_fast) {
+        if (D == 2) {
+            if (f32) FL_TRY(launch_near_fast<2, float, 36>(h, P, t, rb, ro, expo, pw32, C, st));
+            else FL_TRY(launch_near_fast<2, double, 36>(h, P, t, rb, ro, expo, pw, C, st));
+        } else {
+            if (f32) FL_TRY(launch_near_fast<1, float, 6>(h, P, t, rb, ro, expo, pw32, C, st));
+            else FL_TRY(launch_near_fast<1, double, 6>(h, P, t, rb, ro, expo, pw, C, st));
+        }
+    } else if (nnear > 0) {
         const unsigned g = (unsigned)((nnear + 63) / 64);
 #define FL_NEAR(DD, TT, PWV)                                                                                    \
     near_pair_kernel<DD, TT, PWV><<<g, 64, 0, st>>>(nnear, t.np_a, t.np_b, t.cvx, t.cen, t.jac, t.rule, ro, (TT)expo, \
@@ -1256,9 +1418,9 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
     stage_mark(h, st, FL_STAGE_TOUCH, 0);
     const int ntp = (int)P.tp_type.size();
     if (ntp > 0) {
-        const unsigned g = (unsigned)((ntp + 63) / 64);
+        const unsigned g = (unsigned)(((int64_t)ntp * 32 + 127) / 128);  // one warp per pair
 #define FL_TOUCH(PWV) \
-    touch_pair_kernel<PWV><<<g, 64, 0, st>>>(ntp, D, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, t.rule, ro, s, C, t.contrib)
+    touch_pair_kernel<PWV><<<g, 128, 0, st>>>(ntp, D, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, t.rule, ro, s, C, t.contrib)
         if (D == 2 && pw == 5) FL_TOUCH(5);
         else if (D == 2 && pw == 6) FL_TOUCH(6);
         else if (D == 2 && pw == 7) FL_TOUCH(7);
@@ -1309,10 +1471,11 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
         E.regional = h->opt.regional;
         E.contrib = t.contrib;
         E.slot0 = P.el_slot0;
-        if (D == 2 && pw == 5) { element_kernel<5><<<gb, 128, 0, st>>>(E); fl::count_launch(); }
-        else if (D == 2 && pw == 6) { element_kernel<6><<<gb, 128, 0, st>>>(E); fl::count_launch(); }
-        else if (D == 2 && pw == 7) { element_kernel<7><<<gb, 128, 0, st>>>(E); fl::count_launch(); }
-        else { element_kernel<0><<<gb, 128, 0, st>>>(E); fl::count_launch(); }
+        const unsigned ge = (unsigned)((nc * 32 + 127) / 128);  // one warp per cell
+        if (D == 2 && pw == 5) { element_kernel<5><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+        else if (D == 2 && pw == 6) { element_kernel<6><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+        else if (D == 2 && pw == 7) { element_kernel<7><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+        else { element_kernel<0><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
         FL_CUDA_TRY(h, cudaGetLastError());
     }
     stage_mark(h, st, FL_STAGE_ELEMENT, 1);

@@ -50,7 +50,8 @@ __device__ __forceinline__ void unpack16<__nv_bfloat16>(const uint4& u, float* o
     }
 }
 
-// float64 matrix, float64 vector, float64 accumulation
+// float64 matrix, float64 vector, float64 accumulation.  Rows whose start is not
+// 16-byte aligned (odd lda) peel one element, then stream 16-byte vectors.
 __global__ void gemv_f64_kernel(int64_t n, const double* __restrict__ A, int64_t lda, const double* __restrict__ x,
                                 int64_t incx, double* __restrict__ y, int64_t incy, int vec) {
     const int lane = threadIdx.x & 31;
@@ -60,24 +61,39 @@ __global__ void gemv_f64_kernel(int64_t n, const double* __restrict__ A, int64_t
     double acc0 = 0.0, acc1 = 0.0;
     int64_t j0 = 0;
     if (vec && incx == 1) {
-        const int64_t nv = (n / 64) * 64;
-        const double2* a2 = reinterpret_cast<const double2*>(a);
-        const double2* x2 = reinterpret_cast<const double2*>(x);
+        const int64_t p0 = (((uintptr_t)a & 15u) != 0) ? 1 : 0;
+        if (lane < p0 && p0 <= n) acc0 = fma(a[0], x[0], acc0);
+        const int64_t m = n - p0;
+        const int64_t nv = (m / 64) * 64;
+        const double2* a2 = reinterpret_cast<const double2*>(a + p0);
+        if (p0 == 0) {
+            const double2* x2 = reinterpret_cast<const double2*>(x);
 #pragma unroll 4
-        for (int64_t j = lane; j < nv / 2; j += 32) {
-            const double2 av = __ldcs(a2 + j);
-            const double2 xv = x2[j];
-            acc0 = fma(av.x, xv.x, acc0);
-            acc1 = fma(av.y, xv.y, acc1);
+            for (int64_t j = lane; j < nv / 2; j += 32) {
+                const double2 av = __ldcs(a2 + j);
+                const double2 xv = x2[j];
+                acc0 = fma(av.x, xv.x, acc0);
+                acc1 = fma(av.y, xv.y, acc1);
+            }
+        } else {
+            const double* xs = x + p0;
+#pragma unroll 4
+            for (int64_t j = lane; j < nv / 2; j += 32) {
+                const double2 av = __ldcs(a2 + j);
+                acc0 = fma(av.x, xs[2 * j], acc0);
+                acc1 = fma(av.y, xs[2 * j + 1], acc1);
+            }
         }
-        j0 = nv;
+        j0 = p0 + nv;
     }
     for (int64_t j = j0 + lane; j < n; j += 32) acc0 = fma(a[j], x[j * incx], acc0);
     double t = warp_sum(acc0 + acc1);
     if (lane == 0) y[row * incy] = t;
 }
 
-// float32 / bfloat16 matrix, float32 vector, float32 lane sums, float64 row total
+// float32 / bfloat16 matrix, float32 vector, float32 lane sums, float64 row total.
+// Misaligned row starts peel up to V-1 elements; x is read as float4 when it stays
+// aligned with the row, else element by element.
 template <typename TA>
 __global__ void gemv_lo_kernel(int64_t n, const TA* __restrict__ A, int64_t lda, const float* __restrict__ x,
                                double* __restrict__ y, int64_t incy, int vec) {
@@ -89,24 +105,43 @@ __global__ void gemv_lo_kernel(int64_t n, const TA* __restrict__ A, int64_t lda,
     float acc0 = 0.f, acc1 = 0.f;
     int64_t j0 = 0;
     if (vec) {
-        const int64_t nv = (n / (32 * V)) * (32 * V);
-        const uint4* a4 = reinterpret_cast<const uint4*>(a);
-        const float4* x4 = reinterpret_cast<const float4*>(x);
+        const int mis = (int)(((uintptr_t)a & 15u) / sizeof(TA));
+        const int64_t p0 = min((int64_t)(mis ? V - mis : 0), n);
+        if (lane < p0) acc0 = fmaf((float)a[lane], x[lane], acc0);
+        const int64_t m = n - p0;
+        const int64_t nv = (m / (32 * V)) * (32 * V);
+        const uint4* a4 = reinterpret_cast<const uint4*>(a + p0);
+        if ((p0 & 3) == 0) {
+            const float4* x4 = reinterpret_cast<const float4*>(x + p0);
 #pragma unroll 4
-        for (int64_t j = lane; j < nv / V; j += 32) {
-            const uint4 u = __ldcs(a4 + j);
-            float av[V];
-            unpack16<TA>(u, av);
+            for (int64_t j = lane; j < nv / V; j += 32) {
+                const uint4 u = __ldcs(a4 + j);
+                float av[V];
+                unpack16<TA>(u, av);
 #pragma unroll
-            for (int q = 0; q < V / 4; ++q) {
-                const float4 xv = x4[j * (V / 4) + q];
-                acc0 = fmaf(av[4 * q + 0], xv.x, acc0);
-                acc1 = fmaf(av[4 * q + 1], xv.y, acc1);
-                acc0 = fmaf(av[4 * q + 2], xv.z, acc0);
-                acc1 = fmaf(av[4 * q + 3], xv.w, acc1);
+                for (int q = 0; q < V / 4; ++q) {
+                    const float4 xv = x4[j * (V / 4) + q];
+                    acc0 = fmaf(av[4 * q + 0], xv.x, acc0);
+                    acc1 = fmaf(av[4 * q + 1], xv.y, acc1);
+                    acc0 = fmaf(av[4 * q + 2], xv.z, acc0);
+                    acc1 = fmaf(av[4 * q + 3], xv.w, acc1);
+                }
+            }
+        } else {
+            const float* xs = x + p0;
+#pragma unroll 4
+            for (int64_t j = lane; j < nv / V; j += 32) {
+                const uint4 u = __ldcs(a4 + j);
+                float av[V];
+                unpack16<TA>(u, av);
+#pragma unroll
+                for (int q = 0; q < V; q += 2) {
+                    acc0 = fmaf(av[q], xs[j * V + q], acc0);
+                    acc1 = fmaf(av[q + 1], xs[j * V + q + 1], acc1);
+                }
             }
         }
-        j0 = nv;
+        j0 = p0 + nv;
     }
     for (int64_t j = j0 + lane; j < n; j += 32) acc0 = fmaf((float)a[j], x[j], acc0);
     double t = warp_sum((double)acc0 + (double)acc1);
@@ -130,19 +165,20 @@ __global__ void convert_kernel(int64_t n, const double* A, int64_t lda, TO* B, i
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 // y = A x for one right-hand side; xf is a float32 scratch copy of x (n) for low-precision A
+// xf_ready: xf already holds x rounded to float32 (the CG keeps such a copy of p)
 static cudaError_t gemv(int dtype, const void* A, int64_t lda, int64_t n, const double* x, int64_t incx, double* y,
-                        int64_t incy, float* xf, cudaStream_t st) {
+                        int64_t incy, float* xf, cudaStream_t st, bool xf_ready = false) {
     const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
     if (dtype == FL_F64) {
-        const int vec = aligned16(A) && (lda % 2 == 0) && aligned16(x);
+        const int vec = (((uintptr_t)A & 7u) == 0) && aligned16(x);
         gemv_f64_kernel<<<blocks, 256, 0, st>>>(n, (const double*)A, lda, x, incx, y, incy, vec); fl::count_launch();
     } else {
-        to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, incx, xf); fl::count_launch();
+        if (!xf_ready) { to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, incx, xf); fl::count_launch(); }
         if (dtype == FL_F32) {
-            const int vec = aligned16(A) && (lda % 4 == 0) && aligned16(xf);
+            const int vec = (((uintptr_t)A & 3u) == 0) && aligned16(xf);
             gemv_lo_kernel<float><<<blocks, 256, 0, st>>>(n, (const float*)A, lda, xf, y, incy, vec); fl::count_launch();
         } else {
-            const int vec = aligned16(A) && (lda % 8 == 0) && aligned16(xf);
+            const int vec = (((uintptr_t)A & 1u) == 0) && aligned16(xf);
             gemv_lo_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(n, (const __nv_bfloat16*)A, lda, xf, y, incy, vec); fl::count_launch();
         }
     }
@@ -208,14 +244,15 @@ __global__ void residual_kernel(int64_t n, const double* b, const double* Ax, do
 }
 
 // z = dinv r, p = z, partials of r·z and r·r
-__global__ void cg_start_kernel(int64_t n, const double* r, const double* dinv, double* z, double* p, double* prz,
-                                double* prr) {
+__global__ void cg_start_kernel(int64_t n, const double* r, const double* dinv, double* z, double* p, float* pf,
+                                double* prz, double* prr) {
     __shared__ double sh[32];
     double a = 0.0, c = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double zi = dinv[i] * r[i];
         z[i] = zi;
         p[i] = zi;
+        if (pf) pf[i] = (float)zi;
         a = fma(r[i], zi, a);
         c = fma(r[i], r[i], c);
     }
@@ -298,10 +335,13 @@ __global__ void cg_beta_kernel(const double* prz, const double* prr, int nb, CgS
     }
 }
 
-__global__ void cg_p_kernel(int64_t n, const CgScalars* s, const double* z, double* p) {
+__global__ void cg_p_kernel(int64_t n, const CgScalars* s, const double* z, double* p, float* pf) {
     const double beta = s->beta;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = fma(beta, p[i], z[i]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double pi = fma(beta, p[i], z[i]);
+        p[i] = pi;
+        if (pf) pf[i] = (float)pi;
+    }
 }
 
 __global__ void axpy_kernel(int64_t n, double a, const double* x, double* y) {
@@ -382,7 +422,8 @@ static int pcg(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int
     const unsigned g = (unsigned)((n + 255) / 256);
     zero_kernel<<<g, 256, 0, st>>>(n, d); fl::count_launch();
     residual_kernel<<<g, 256, 0, st>>>(n, rhs, nullptr, w.r); fl::count_launch();
-    cg_start_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.r, dinv, w.z, w.p, w.prz, w.prr); fl::count_launch();
+    float* pf = (dtype == FL_F64) ? nullptr : w.xf;
+    cg_start_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.r, dinv, w.z, w.p, pf, w.prz, w.prr); fl::count_launch();
     cg_init_scalars_kernel<<<1, 256, 0, st>>>(w.prz, w.prr, RED_BLOCKS, w.s); fl::count_launch();
     FL_CU(h, cudaGetLastError());
     FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
@@ -397,12 +438,12 @@ static int pcg(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int
     int it = 0;
     double rr = rr0;
     while (it < maxit) {
-        FL_CU(h, gemv(dtype, M, ldm, n, w.p, 1, w.q, 1, w.xf, st));
+        FL_CU(h, gemv(dtype, M, ldm, n, w.p, 1, w.q, 1, w.xf, st, pf != nullptr));
         dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.p, w.q, w.ppq); fl::count_launch();
         cg_alpha_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, w.s); fl::count_launch();
         cg_update_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, d, w.r, w.z, w.p, w.q, dinv, w.prz, w.prr); fl::count_launch();
         cg_beta_kernel<<<1, 256, 0, st>>>(w.prz, w.prr, RED_BLOCKS, w.s); fl::count_launch();
-        cg_p_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, w.z, w.p); fl::count_launch();
+        cg_p_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, w.z, w.p, pf); fl::count_launch();
         FL_CU(h, cudaGetLastError());
         ++it;
         FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
