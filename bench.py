@@ -233,6 +233,7 @@ def main():
             ts.append(a.elapsed_time(b_))
         return statistics.median(ts)
 
+    peaks = load_peaks()
     asm_mixed_ms = timed(lambda: m.assemble(s, "mixed", out=A))
     asm_fp64_ms = timed(lambda: m.assemble(s, "fp64", out=A), reps=3)
     # dominant kernel: the far-field tile kernel, timed by the library's events on this stream
@@ -250,11 +251,18 @@ def main():
     far_avg = statistics.mean(far_ms)
     q = 16  # collapsed rule of order 4
     evals = stats["n_far_pairs"] * q * q
-    # matvec bandwidth on the assembled matrix (L2-resident at this size: 28 MiB fp64)
-    x = torch.randn(n, 1, dtype=torch.float64, device=dev)
-    y = torch.empty(n, 1, dtype=torch.float64, device=dev)
-    mv64 = timed(lambda: F.fl_matvec(F.FL_F64, A, x, y), reps=20)
-    mv32 = timed(lambda: F.fl_matvec(F.FL_F32, A32, x, y), reps=20)
+    # dense matvec bandwidth on an HBM-resident matrix of the graded-disc size (n = 8195:
+    # 537 MB float64, 269 MB float32, both larger than L2), L2 flushed between products
+    nb = 8195
+    Ab = torch.randn(nb, nb, dtype=torch.float64, device=dev)
+    Ab32 = Ab.float()
+    xb = torch.randn(nb, 1, dtype=torch.float64, device=dev)
+    xb1 = xb[:, 0].contiguous()
+    yb = torch.empty(nb, 1, dtype=torch.float64, device=dev)
+    yb1 = torch.empty(nb, dtype=torch.float64, device=dev)
+    mv64 = timed(lambda: F.fl_matvec(F.FL_F64, Ab, xb, yb), reps=10)
+    mv32 = timed(lambda: F.fl_matvec_f32_static(Ab32, xb1, yb1), reps=10)
+    del Ab, Ab32
     # time to 1e-8: refined float32 solve vs plain float64 Jacobi-PCG on the same matrix
     m.assemble(s, "fp64", out=A)
     F.fl_convert(A, F.FL_F32, A32)
@@ -288,7 +296,6 @@ def main():
     h2d = int(st_e["h2d_bytes"] + V.nbytes + T.nbytes)
     d2h = n * 8
 
-    peaks = load_peaks()
     sm_clock = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     # far kernel (float32, s = 3/4): one MUFU.LG2 (16 results/clk/SM) and one MUFU.EX2 (32/clk/SM on GB300,
     # measured) per kernel evaluation -> 1 / (1/16 + 1/32) = 10.67 evaluations/clk/SM
@@ -306,8 +313,9 @@ def main():
                              "ex2 32/clk per SM) x max SM clock; evals = far pairs x 16 x 16"},
         "stage_ms": stage_tot,
         "assembly_pairs_per_s": {"mixed": n_el * n_el / (asm_mixed_ms / 1000), "fp64": n_el * n_el / (asm_fp64_ms / 1000)},
-        "matvec": {"n": n, "f64_gbs": n * n * 8 / (mv64 / 1000) / 1e9, "f32_gbs": n * n * 4 / (mv32 / 1000) / 1e9,
-                   "note": "matrix L2-resident at this size"},
+        "matvec": {"n": nb, "f64_gbs": nb * nb * 8 / (mv64 / 1000) / 1e9, "f32_gbs": nb * nb * 4 / (mv32 / 1000) / 1e9,
+                   "f64_ms": mv64, "f32_ms": mv32, "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                   "note": "bytes of A per product / device time; L2 flushed; f32 through fl_matvec_f32_static"},
         "solve_ms_to_1e-8": {"f32_refined": sol_mixed, "plain_f64": sol_fp64, "iters_f64": inf64.iterations,
                              "iters_refined": infmx.iterations, "outer": infmx.outer_iterations},
         "gpu_launches": int(launches),

@@ -67,9 +67,11 @@ extern "C" {
 typedef struct fl_options {
     int k_far;    /* Gauss order per dimension, separated pairs at vertex-graph distance >= 2 (default 4) */
     int k_near;   /* separated pairs at vertex-graph distance 1 and near boundary facets (default 6) */
-    int k_touch;  /* touching element pairs, remaining regular variables (default 8) */
+    int k_touch;  /* common-edge pairs (and 1D touching pairs), regular variables (default 8);
+                     identical pairs use 2*k_touch angular points per piece */
     int k_bnd;    /* element/boundary-facet pairs that touch (default 8) */
     int regional; /* 1: drop the boundary term (regional fractional Laplacian, Section 2) */
+    int k_vertex; /* common-vertex pairs, 3D regular variables (default 6) */
 } fl_options;
 
 typedef struct fl_ctx* fl_handle;

@@ -23,11 +23,14 @@ Appendix B; all orders are options, see QuadOrders):
   the order they appear in K's counter-clockwise vertex list, cells rotated to
   start at a shared vertex): relative coordinates in which the whole integrand is
   homogeneous of degree -2s, so the radial integral is done in closed form and
-  only smooth angular variables are left to Gauss-Legendre of order k_touch:
-    identical (2D)   : 1D integral over the direction, three pieces of [0, pi);
+  only smooth angular variables are left to Gauss-Legendre:
+    identical (2D)   : 1D integral over the direction, three pieces of [0, pi),
+                       2 k_touch points per piece (the direction integrand sharpens
+                       on anisotropic cells; this rule costs 6 k_touch evaluations);
     common edge (2D) : 2D integral over the l1-unit directions of
                        (x1-y1, x2, y2), four pieces;
-    common vertex(2D): Duffy map of K×K' into [0,1]^4, two regions, 3D Gauss;
+    common vertex(2D): Duffy map of K×K' into [0,1]^4, two regions, 3D Gauss of
+                       order k_vertex;
     1D               : identical in closed form, common vertex by a Duffy map.
 * boundary term: 1D facets are points, so the inner integral is a point value;
   in 2D the inner edge integral uses Gauss order k_near/k_far for
@@ -58,8 +61,9 @@ def frac_constant(d: int, s: float) -> float:
 class QuadOrders:
     k_far: int = 4
     k_near: int = 6
-    k_touch: int = 8
+    k_touch: int = 8     # common-edge pairs; identical pairs use 2 * k_touch angular points per piece
     k_bnd: int = 8
+    k_vertex: int = 6    # common-vertex pairs
 
 
 # ---------------------------------------------------------------- points ----
@@ -397,7 +401,7 @@ def assemble_matrix(mesh: OracleMesh, s: float, orders: QuadOrders = QuadOrders(
             elif shared[m] == 2:
                 loc, blk = common_edge_2d(mesh, s, C, lo, hi, orders.k_touch)
             else:
-                loc, blk = common_vertex_2d(mesh, s, C, lo, hi, orders.k_touch)
+                loc, blk = common_vertex_2d(mesh, s, C, lo, hi, orders.k_vertex)
             sink.add(loc, loc, blk)
         # separated pairs
         for sel, order in (((shared == 0) & near, orders.k_near), ((shared == 0) & ~near, orders.k_far)):
@@ -410,7 +414,7 @@ def assemble_matrix(mesh: OracleMesh, s: float, orders: QuadOrders = QuadOrders(
                 sink.add_off(mesh.C[k], mesh.C[mm], off)
         # identical pair
         if has_dof[k]:
-            loc, blk = identical_1d(mesh, s, C, k) if d == 1 else identical_2d(mesh, s, C, k, orders.k_touch)
+            loc, blk = identical_1d(mesh, s, C, k) if d == 1 else identical_2d(mesh, s, C, k, 2 * orders.k_touch)
             sink.add(loc, loc, blk)
         if has_dof[k] and not regional:
             # boundary facets

@@ -1076,14 +1076,17 @@ void build_rules(const fl_ctx* h, double s, std::vector<double>& buf, RuleOffset
         ro.n_edge = 4 * kt * kt;
         ro.t_edge = put(tab);
     }
-    // common vertex: two Duffy regions, weight eta2 * w
+    // common vertex: two Duffy regions, weight eta2 * w, order k_vertex
     {
         std::vector<double> tab;
+        std::vector<double> vt, vw;
+        gauss01(o.k_vertex, vt, vw);
+        const int kv = o.k_vertex;
         for (int reg = 0; reg < 2; ++reg)
-            for (int i = 0; i < kt; ++i)
-                for (int j = 0; j < kt; ++j)
-                    for (int l = 0; l < kt; ++l) {
-                        const double e1 = tt[i], e2 = tt[j], e3 = tt[l], W = tw[i] * tw[j] * tw[l];
+            for (int i = 0; i < kv; ++i)
+                for (int j = 0; j < kv; ++j)
+                    for (int l = 0; l < kv; ++l) {
+                        const double e1 = vt[i], e2 = vt[j], e3 = vt[l], W = vw[i] * vw[j] * vw[l];
                         double x1, x2, y1, y2;
                         if (reg == 0) { x1 = 1; x2 = e1; y1 = e2; y2 = e2 * e3; }
                         else { x1 = e2; x2 = e2 * e3; y1 = 1; y2 = e1; }
@@ -1099,7 +1102,7 @@ void build_rules(const fl_ctx* h, double s, std::vector<double>& buf, RuleOffset
                         tab.push_back(y2);
                         tab.push_back(W * e2);
                     }
-        ro.n_vert = 2 * kt * kt * kt;
+        ro.n_vert = 2 * kv * kv * kv;
         ro.t_vert = put(tab);
     }
     // 1D common vertex
@@ -1112,22 +1115,24 @@ void build_rules(const fl_ctx* h, double s, std::vector<double>& buf, RuleOffset
         ro.n_1d = kt;
         ro.t_1d = put(tab);
     }
-    // identical pair: three angular pieces of [0, pi), weight x rho^{2-2s}
+    // identical pair: three angular pieces of [0, pi), 2 k_touch points each, weight x rho^{2-2s}
     {
         std::vector<double> tab;
+        std::vector<double> it, iw;
+        gauss01(2 * kt, it, iw);
         const double pi = 3.14159265358979323846;
         const double lo[3] = {0.0, pi / 2, 3 * pi / 4}, hi[3] = {pi / 2, 3 * pi / 4, pi};
         for (int piece = 0; piece < 3; ++piece)
-            for (int i = 0; i < kt; ++i) {
-                const double th = lo[piece] + (hi[piece] - lo[piece]) * tt[i];
-                const double wt = (hi[piece] - lo[piece]) * tw[i];
+            for (int i = 0; i < 2 * kt; ++i) {
+                const double th = lo[piece] + (hi[piece] - lo[piece]) * it[i];
+                const double wt = (hi[piece] - lo[piece]) * iw[i];
                 const double u0 = std::cos(th), u1 = std::sin(th);
                 const double rho = 2.0 / (std::fabs(u0 + u1) + std::fabs(u0) + std::fabs(u1));
                 tab.push_back(u0);
                 tab.push_back(u1);
                 tab.push_back(wt * std::pow(rho, 2 - 2 * s));
             }
-        ro.n_ident = 3 * kt;
+        ro.n_ident = 3 * 2 * kt;
         ro.t_ident = put(tab);
     }
     std::vector<double> bt, bw;

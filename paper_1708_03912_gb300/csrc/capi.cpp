@@ -50,6 +50,7 @@ void fl_default_options(fl_options* o) {
     o->k_touch = 8;
     o->k_bnd = 8;
     o->regional = 0;
+    o->k_vertex = 6;
 }
 
 int fl_create(fl_handle* out, int dim, int64_t n_vertices, const double* vertices_host, int64_t n_cells,
@@ -68,7 +69,7 @@ int fl_create(fl_handle* out, int dim, int64_t n_vertices, const double* vertice
         return FL_EINVAL;
     }
     if (o.k_far < 1 || o.k_far > 32 || o.k_near < 1 || o.k_near > 32 || o.k_touch < 1 || o.k_touch > 32 ||
-        o.k_bnd < 1 || o.k_bnd > 32) {
+        o.k_bnd < 1 || o.k_bnd > 32 || o.k_vertex < 1 || o.k_vertex > 32) {
         g_create_err = "quadrature orders must lie in [1, 32]";
         return FL_EINVAL;
     }
@@ -118,6 +119,8 @@ void fl_destroy(fl_handle h) {
         if (h->solve_ws) cudaFree(h->solve_ws);
         if (h->solve_host) cudaFreeHost(h->solve_host);
     }
+    for (auto& g : h->cg_graphs) cudaGraphExecDestroy(g.exec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
 

@@ -9,6 +9,26 @@
 
 namespace fl {
 
+// Identity of a captured batch of CG iterations (pointers and sizes baked into the graph).
+struct CgGraphKey {
+    int64_t n;
+    int dtype;
+    const void* M;
+    int64_t ldm;
+    const double* dinv;
+    double* d;
+    double* r;
+    float* pf;
+    bool operator==(const CgGraphKey& o) const {
+        return n == o.n && dtype == o.dtype && M == o.M && ldm == o.ldm && dinv == o.dinv && d == o.d && r == o.r &&
+               pf == o.pf;
+    }
+};
+struct CgGraph {
+    CgGraphKey key;
+    cudaGraphExec_t exec;
+};
+
 // One device allocation owned by a handle.
 struct DBuf {
     void* p = nullptr;
@@ -77,6 +97,8 @@ struct fl_ctx {
     bool ev_recorded = false;
     int64_t h2d_bytes = 0;
     int64_t ws_bytes = 0;
+    std::vector<fl::CgGraph> cg_graphs;   // captured CG batches, keyed by their pointers
+    cudaStream_t cap_stream = nullptr;    // stream used only for graph capture
     void* solve_ws = nullptr;     // solver workspace (device), grown on demand
     void* solve_host = nullptr;   // pinned scalars read back by the solver
     size_t solve_ws_bytes = 0;

@@ -223,8 +223,11 @@ __global__ void sum_partials_kernel(const double* partial, int nb, double* out) 
 
 // ------------------------------------------------------------- PCG parts --
 struct CgScalars {
-    double rz, rz_new, pq, rr, bb, alpha, beta;
+    double rz, rz_new, pq, rr, bb, alpha, beta, stop;
     int breakdown;
+    int done;   // set once converged, broken down or out of iterations; later steps are no-ops
+    int it;     // iterations performed
+    int maxit;
 };
 
 __global__ void diag_inv_kernel(int64_t n, int dtype, const void* A, int64_t lda, double* dinv) {
@@ -264,7 +267,8 @@ __global__ void cg_start_kernel(int64_t n, const double* r, const double* dinv, 
     }
 }
 
-__global__ void cg_init_scalars_kernel(const double* prz, const double* prr, int nb, CgScalars* s) {
+__global__ void cg_init_scalars_kernel(const double* prz, const double* prr, int nb, CgScalars* s, double tol,
+                                       int maxit) {
     __shared__ double sh[32];
     double a = 0.0, c = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
@@ -276,7 +280,11 @@ __global__ void cg_init_scalars_kernel(const double* prz, const double* prr, int
     if (threadIdx.x == 0) {
         s->rz = ta;
         s->rr = tc;
+        s->stop = tol * tol * tc;
         s->breakdown = 0;
+        s->it = 0;
+        s->maxit = maxit;
+        s->done = (tc == 0.0 || maxit <= 0) ? 1 : 0;
     }
 }
 
@@ -287,8 +295,11 @@ __global__ void cg_alpha_kernel(const double* ppq, int nb, CgScalars* s) {
     const double t = block_sum(a, sh);
     if (threadIdx.x == 0) {
         s->pq = t;
-        if (!(t > 0.0)) {
+        if (s->done) {
+            s->alpha = 0.0;
+        } else if (!(t > 0.0)) {
             s->breakdown = 1;
+            s->done = 1;
             s->alpha = 0.0;
         } else {
             s->alpha = s->rz / t;
@@ -329,9 +340,15 @@ __global__ void cg_beta_kernel(const double* prz, const double* prr, int nb, CgS
     const double ta = block_sum(a, sh);
     const double tc = block_sum(c, sh);
     if (threadIdx.x == 0) {
-        s->beta = ta / s->rz;
-        s->rz = ta;
-        s->rr = tc;
+        if (s->done) {
+            s->beta = 0.0;
+        } else {
+            s->beta = ta / s->rz;
+            s->rz = ta;
+            s->rr = tc;
+            s->it += 1;
+            if (tc <= s->stop || s->it >= s->maxit) s->done = 1;
+        }
     }
 }
 
@@ -372,6 +389,8 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
                         round256(n * sizeof(float)) + round256(sizeof(CgScalars));
     void* base = nullptr;
     if (h->solve_ws_bytes < need) {
+        for (auto& g : h->cg_graphs) cudaGraphExecDestroy(g.exec);
+        h->cg_graphs.clear();
         if (h->solve_ws) {
             cudaFree(h->solve_ws);
             cudaFreeHost(h->solve_host);
@@ -416,7 +435,47 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
     } while (0)
 
 // Jacobi-PCG on y = M x (M of type dtype) for M d = rhs from d = 0, relative tolerance tol
-// (||rhs - M d|| by the recursion).  Returns iterations through *its, status code.
+// (||rhs - M d|| by the recursion).  The iterations run in batches of CG_BATCH captured in a
+// CUDA graph (cached per handle); the scalars are read back once per batch, and steps after
+// convergence, breakdown or the iteration limit are no-ops on the device.
+constexpr int CG_BATCH = 8;
+
+static void enqueue_cg_iteration(SolveWork& w, int64_t n, int dtype, const void* M, int64_t ldm, const double* dinv,
+                                 double* d, float* pf, cudaStream_t st) {
+    gemv(dtype, M, ldm, n, w.p, 1, w.q, 1, w.xf, st, pf != nullptr);
+    dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.p, w.q, w.ppq);
+    cg_alpha_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, w.s);
+    cg_update_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, d, w.r, w.z, w.p, w.q, dinv, w.prz, w.prr);
+    cg_beta_kernel<<<1, 256, 0, st>>>(w.prz, w.prr, RED_BLOCKS, w.s);
+    cg_p_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, w.z, w.p, pf);
+}
+
+static int cg_graph(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int64_t ldm, const double* dinv,
+                    double* d, float* pf, cudaGraphExec_t* exec) {
+    CgGraphKey key{n, dtype, M, ldm, dinv, d, w.r, pf};
+    for (auto& e : h->cg_graphs)
+        if (e.key == key) {
+            *exec = e.exec;
+            return FL_OK;
+        }
+    if (!h->cap_stream) FL_CU(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const uint64_t before = fl_launch_count();
+    cudaGraph_t g = nullptr;
+    FL_CU(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int b = 0; b < CG_BATCH; ++b) enqueue_cg_iteration(w, n, dtype, M, ldm, dinv, d, pf, h->cap_stream);
+    cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, h->cap_stream);
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &g);
+    fl::count_launch(-(int)(fl_launch_count() - before));  // captured, not launched
+    if (ec != cudaSuccess) return set_err(h, FL_ECUDA, std::string("CG graph capture: ") + cudaGetErrorString(ec));
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return set_err(h, FL_ECUDA, std::string("CG graph instantiate: ") + cudaGetErrorString(ei));
+    h->cg_graphs.push_back({key, ex});
+    *exec = ex;
+    return FL_OK;
+}
+
 static int pcg(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int64_t ldm, const double* dinv,
                const double* rhs, double* d, double tol, int maxit, int* its, double* relres, cudaStream_t st) {
     const unsigned g = (unsigned)((n + 255) / 256);
@@ -424,41 +483,27 @@ static int pcg(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int
     residual_kernel<<<g, 256, 0, st>>>(n, rhs, nullptr, w.r); fl::count_launch();
     float* pf = (dtype == FL_F64) ? nullptr : w.xf;
     cg_start_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.r, dinv, w.z, w.p, pf, w.prz, w.prr); fl::count_launch();
-    cg_init_scalars_kernel<<<1, 256, 0, st>>>(w.prz, w.prr, RED_BLOCKS, w.s); fl::count_launch();
+    cg_init_scalars_kernel<<<1, 256, 0, st>>>(w.prz, w.prr, RED_BLOCKS, w.s, tol, maxit); fl::count_launch();
     FL_CU(h, cudaGetLastError());
     FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
     FL_CU(h, cudaStreamSynchronize(st));
     const double rr0 = w.s_host->rr;
     *its = 0;
-    if (rr0 == 0.0) {
-        *relres = 0.0;
-        return FL_OK;
-    }
-    const double stop = tol * tol * rr0;
-    int it = 0;
-    double rr = rr0;
-    while (it < maxit) {
-        FL_CU(h, gemv(dtype, M, ldm, n, w.p, 1, w.q, 1, w.xf, st, pf != nullptr));
-        dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.p, w.q, w.ppq); fl::count_launch();
-        cg_alpha_kernel<<<1, 256, 0, st>>>(w.ppq, RED_BLOCKS, w.s); fl::count_launch();
-        cg_update_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, d, w.r, w.z, w.p, w.q, dinv, w.prz, w.prr); fl::count_launch();
-        cg_beta_kernel<<<1, 256, 0, st>>>(w.prz, w.prr, RED_BLOCKS, w.s); fl::count_launch();
-        cg_p_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, w.s, w.z, w.p, pf); fl::count_launch();
-        FL_CU(h, cudaGetLastError());
-        ++it;
-        FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    *relres = 0.0;
+    if (rr0 == 0.0) return FL_OK;
+    cudaGraphExec_t ex = nullptr;
+    int r = cg_graph(h, w, n, dtype, M, ldm, dinv, d, pf, &ex);
+    if (r != FL_OK) return r;
+    const int per_iter = (dtype == FL_F64) ? 6 : 6;  // gemv + 5 (the float copy of p comes from cg_p)
+    while (!w.s_host->done) {
+        FL_CU(h, cudaGraphLaunch(ex, st));
+        fl::count_launch(CG_BATCH * per_iter);
         FL_CU(h, cudaStreamSynchronize(st));
-        if (w.s_host->breakdown) {
-            *its = it;
-            *relres = std::sqrt(rr / rr0);
-            return set_err(h, FL_ENOTSPD, "CG breakdown: p^T A p <= 0");
-        }
-        rr = w.s_host->rr;
-        if (rr <= stop) break;
     }
-    *its = it;
-    *relres = std::sqrt(rr / rr0);
-    return (rr <= stop) ? FL_OK : FL_ENOTCONV;
+    *its = w.s_host->it;
+    *relres = std::sqrt(w.s_host->rr / rr0);
+    if (w.s_host->breakdown) return set_err(h, FL_ENOTSPD, "CG breakdown: p^T A p <= 0");
+    return (w.s_host->rr <= w.s_host->stop) ? FL_OK : FL_ENOTCONV;
 }
 
 }  // namespace fl

@@ -37,7 +37,7 @@ class FlError(RuntimeError):
 
 class fl_options(ctypes.Structure):
     _fields_ = [("k_far", ctypes.c_int), ("k_near", ctypes.c_int), ("k_touch", ctypes.c_int),
-                ("k_bnd", ctypes.c_int), ("regional", ctypes.c_int)]
+                ("k_bnd", ctypes.c_int), ("regional", ctypes.c_int), ("k_vertex", ctypes.c_int)]
 
 
 class fl_solve_opts(ctypes.Structure):
@@ -234,9 +234,11 @@ def fl_matvec_f32_static(A32, x, y, stream=None):
 class Mesh:
     """Owns one fl_handle.  Orders and the DOF rule are fixed at creation."""
 
-    def __init__(self, vertices, cells, dof_mode="interior", k_far=4, k_near=6, k_touch=8, k_bnd=8, regional=False):
+    def __init__(self, vertices, cells, dof_mode="interior", k_far=4, k_near=6, k_touch=8, k_bnd=8, regional=False,
+                 k_vertex=6):
         o = fl_default_options()
         o.k_far, o.k_near, o.k_touch, o.k_bnd, o.regional = k_far, k_near, k_touch, k_bnd, int(regional)
+        o.k_vertex = k_vertex
         self.h = fl_create(vertices, cells, FL_DOF_PAPER if dof_mode == "paper" else FL_DOF_INTERIOR, o)
         self.dim = 1 if np.asarray(vertices).ndim == 1 else np.asarray(vertices).shape[1]
 

@@ -38,15 +38,24 @@ def graded_interval(n_el: int, mu: float = 2.0):
     return z[:, None].copy(), cells.astype(np.int32)
 
 
-def _zipper(inner, inner_ang, outer, outer_ang):
-    """Triangulate the annulus between two closed rings by walking both in angle."""
+def _zipper(inner, inner_ang, outer, outer_ang, pts):
+    """Triangulate the annulus between two closed rings, walking both rings and
+    closing each step with the shorter of the two candidate diagonals."""
     na, nb = len(inner), len(outer)
     tris = []
     i = j = 0
+
+    def d2(p, q):
+        return (pts[p][0] - pts[q][0]) ** 2 + (pts[p][1] - pts[q][1]) ** 2
+
     while i < na or j < nb:
-        a_next = inner_ang[0] + 2 * math.pi * (i + 1) / na
-        b_next = outer_ang[0] + 2 * math.pi * (j + 1) / nb
-        if j == nb or (i < na and a_next < b_next):
+        if j == nb:
+            adv_inner = True
+        elif i == na:
+            adv_inner = False
+        else:
+            adv_inner = d2(inner[(i + 1) % na], outer[j % nb]) < d2(inner[i % na], outer[(j + 1) % nb])
+        if adv_inner:
             tris.append((inner[i % na], outer[j % nb], inner[(i + 1) % na]))
             i += 1
         else:
@@ -59,8 +68,9 @@ def disc(M: int, mu: float = 1.0):
     """Unit-disc mesh of M concentric rings with radii r_i = 1 - (1 - i/M)^mu.
 
     Ring i carries round(2*pi*r_i/h_i) equally spaced points (h_i = r_i - r_{i-1}),
-    odd rings shifted by half a step; consecutive rings are joined by an angular
-    walk and the first ring by a fan around the centre.  mu = 1 gives the
+    odd rings shifted by half a step; consecutive rings are joined by a walk that
+    closes each step with the shorter diagonal, the first ring by a fan around the
+    centre.  mu = 1 gives the
     quasi-uniform disc, mu = 2 the boundary-graded disc.  All boundary vertices lie
     on the unit circle, so the polygon is inscribed in the disc.
     """
@@ -80,7 +90,7 @@ def disc(M: int, mu: float = 1.0):
     for k in range(len(idx0)):
         tris.append((0, idx0[k], idx0[(k + 1) % len(idx0)]))
     for (ia, aa), (ib, ab) in zip(rings[:-1], rings[1:]):
-        tris.extend(_zipper(ia, aa, ib, ab))
+        tris.extend(_zipper(ia, aa, ib, ab, pts))
     return np.array(pts, dtype=np.float64), np.array(tris, dtype=np.int32)
 
 

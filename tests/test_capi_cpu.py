@@ -72,6 +72,6 @@ def test_create_rejects_bad_input():
 def test_default_options():
     _lib_or_skip()
     o = F.fl_default_options()
-    assert (o.k_far, o.k_near, o.k_touch, o.k_bnd, o.regional) == (4, 6, 8, 8, 0)
+    assert (o.k_far, o.k_near, o.k_touch, o.k_bnd, o.regional, o.k_vertex) == (4, 6, 8, 8, 0, 6)
     so = F.fl_default_solve_opts()
     assert so.tol == 1e-8 and so.inner_dtype == F.FL_F64

@@ -58,9 +58,9 @@ def test_2d_parity_lshape_and_square():
 
 def test_orders_and_regional():
     V, T = synth.square(5, 0.2)
-    o = QuadOrders(k_far=3, k_near=5, k_touch=6, k_bnd=5)
+    o = QuadOrders(k_far=3, k_near=5, k_touch=6, k_bnd=5, k_vertex=4)
     Ao, _ = assemble_matrix(OracleMesh(V, T), 0.4, o)
-    Ag = gpu_matrix(V, T, 0.4, k_far=3, k_near=5, k_touch=6, k_bnd=5)
+    Ag = gpu_matrix(V, T, 0.4, k_far=3, k_near=5, k_touch=6, k_bnd=5, k_vertex=4)
     assert scaled(Ag, Ao) < TOL64
     Ao, _ = assemble_matrix(OracleMesh(V, T), 0.4, dof_mode="paper", regional=True)
     Ag = gpu_matrix(V, T, 0.4, dof_mode="paper", regional=True)
@@ -75,7 +75,7 @@ def test_exact_golden_high_orders():
     gold = json.load(open(os.path.join(GOLD, "square4_exact.json")))
     V, T = synth.square(4, 0.2)
     for s, E in gold["matrices"].items():
-        Ag = gpu_matrix(V, T, float(s), k_far=6, k_near=12, k_touch=20, k_bnd=20)
+        Ag = gpu_matrix(V, T, float(s), k_far=6, k_near=12, k_touch=20, k_bnd=20, k_vertex=16)
         assert scaled(Ag, np.array(E)) < 1e-8
     gold = json.load(open(os.path.join(GOLD, "interval16_exact.json")))
     V, T = synth.interval(16)

@@ -14,7 +14,7 @@ from oracle.assemble import frac_constant
 from paper_1708_03912_gb300 import synth
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
-HIGH = QuadOrders(k_far=10, k_near=14, k_touch=20, k_bnd=20)
+HIGH = QuadOrders(k_far=10, k_near=14, k_touch=20, k_bnd=20, k_vertex=20)
 
 
 def scaled_err(A, E):
@@ -91,7 +91,7 @@ def test_2d_matches_exact_matrix_disc(s):
     m = OracleMesh(V, T)
     E = exact.exact_matrix_2d(m, s)
     errs = []
-    for orders in (QuadOrders(), QuadOrders(6, 8, 12, 12), HIGH):
+    for orders in (QuadOrders(), QuadOrders(6, 8, 12, 12, 10), HIGH):
         A, _ = assemble_matrix(m, s, orders)
         errs.append(scaled_err(A, E))
     assert errs[0] < 5e-5 and errs[1] < errs[0] / 20 and errs[2] < 1e-10
