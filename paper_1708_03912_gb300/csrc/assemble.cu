@@ -522,18 +522,48 @@ __global__ void touch_pair_kernel(int ntp, int dim, const int* tp_type, const in
 }
 
 // ------------------------------------------------------ boundary, far facets --
-// 2D: for each cell (lane) the sums B_a = Σ_e Σ_b w_b n_e·(x_a - y_b) |x_a - y_b|^{-2-2s}
-// over all boundary facets not listed as touching/near for that cell.
+// 2D: for each cell the sums B_a = Σ_e Σ_b w_b n_e·(x_a - y_b) |x_a - y_b|^{-2-2s}
+// over all boundary facets not listed as touching/near for that cell.  A block of
+// BND_WARPS warps serves 32 cells (lane = cell); warp w takes the facets f = w, w +
+// BND_WARPS, ...; the per-warp sums are added in warp order.  Facet data come from a
+// compact per-facet record (start point, edge, normal and length, float64).
+constexpr int BND_WARPS = 4;
+
+struct FacetRec {
+    double e0x, e0y;   // start point
+    double ex, ey;     // edge vector E1 - E0
+    double nx, ny;     // inward unit normal
+    double len, pad;
+};
+
+__global__ void facet_records_kernel(int64_t nf, const int* F, const double* FN, const double* FLEN, const double* V,
+                                     FacetRec* out) {
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const double* E0 = V + 2 * F[2 * f];
+    const double* E1 = V + 2 * F[2 * f + 1];
+    FacetRec r;
+    r.e0x = E0[0];
+    r.e0y = E0[1];
+    r.ex = E1[0] - E0[0];
+    r.ey = E1[1] - E0[1];
+    r.nx = FN[2 * f];
+    r.ny = FN[2 * f + 1];
+    r.len = FLEN[f];
+    r.pad = 0.0;
+    out[f] = r;
+}
+
 template <typename T, int Q, int PW>
-__global__ void __launch_bounds__(32) bnd_far_kernel(int64_t nc, int64_t nf, const double* cen, const T* pts,
-                                                      const char* hasdof, const int* ef_ptr, const int* ef_fac,
-                                                      const int* F, const double* FN, const double* FLEN,
-                                                      const double* V, const double* rule, RuleOffsets ro, T expo,
-                                                      double* Bf) {
-    const int lane = threadIdx.x;
+__global__ void __launch_bounds__(32 * BND_WARPS) bnd_far_kernel(int64_t nc, int64_t nf, const double* cen, const T* pts,
+                                                                  const char* hasdof, const int* ef_ptr,
+                                                                  const int* ef_fac, const FacetRec* FR,
+                                                                  const double* F64, const double* rule, RuleOffsets ro,
+                                                                  T expo, double* Bf) {
+    __shared__ double part[BND_WARPS][Q][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t k = (int64_t)blockIdx.x * 32 + lane;
     const bool valid = k < nc && hasdof[k];
-    if (!__any_sync(0xffffffffu, valid)) return;
     T xa[Q][2];
     double c[2] = {0.0, 0.0};
     int ep = 0, ee = 0;
@@ -556,26 +586,28 @@ __global__ void __launch_bounds__(32) bnd_far_kernel(int64_t nc, int64_t nf, con
     T Bp[Q];
     for (int a = 0; a < Q; ++a) B[a] = 0.0, Bp[a] = T(0);
     int since = 0;
-    for (int64_t f = 0; f < nf; ++f) {
+    const bool any = __any_sync(0xffffffffu, valid);
+    for (int64_t f = wid; any && f < nf; f += BND_WARPS) {
         bool act = valid;
         if (act) {
             while (ep < ee && ef_fac[ep] < f) ++ep;
             if (ep < ee && ef_fac[ep] == f) act = false;
         }
-        const double* E0 = V + 2 * F[2 * f];
-        const double* E1 = V + 2 * F[2 * f + 1];
-        const T ex = (T)(E1[0] - E0[0]), ey = (T)(E1[1] - E0[1]);
-        const T nx = (T)FN[2 * f], ny = (T)FN[2 * f + 1];
-        const T dcx = (T)(c[0] - E0[0]), dcy = (T)(c[1] - E0[1]);
-        const T L = (T)FLEN[f];
+        const FacetRec r = FR[f];
+        const T ex = (T)r.ex, ey = (T)r.ey, nx = (T)r.nx, ny = (T)r.ny;
+        T dcx = (T)(c[0] - r.e0x), dcy = (T)(c[1] - r.e0y);
+        if (!act) {  // far away and zero-weighted: every value stays finite
+            dcx = T(1.0e3);
+            dcy = T(1.0e3);
+        }
+        const T L = act ? (T)r.len : T(0);
         for (int b = 0; b < kf; ++b) {
             const T tb = (T)gt[b], wb = (T)gw[b] * L;
             const T yx = tb * ex, yy = tb * ey;
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const T dx = dcx + xa[a][0] - yx, dy = dcy + xa[a][1] - yy;
-                T kv = kpow<PW>(fma(dx, dx, dy * dy), expo);
-                kv = act ? kv : T(0);
+                const T kv = kpow<PW>(fma(dx, dx, dy * dy), expo);
                 Bp[a] = fma(wb * (nx * dx + ny * dy), kv, Bp[a]);
             }
         }
@@ -584,8 +616,14 @@ __global__ void __launch_bounds__(32) bnd_far_kernel(int64_t nc, int64_t nf, con
             since = 0;
         }
     }
-    if (valid)
-        for (int a = 0; a < Q; ++a) Bf[k * Q + a] = B[a] + (double)Bp[a];
+    for (int a = 0; a < Q; ++a) part[wid][a][lane] = B[a] + (double)Bp[a];
+    __syncthreads();
+    if (wid == 0 && valid)
+        for (int a = 0; a < Q; ++a) {
+            double acc = 0.0;
+            for (int w = 0; w < BND_WARPS; ++w) acc += part[w][a][lane];
+            Bf[k * Q + a] = acc;
+        }
 }
 
 // ------------------------------------------------------------- per element --
@@ -638,23 +676,48 @@ __global__ void element_kernel(ElemArgs A) {
     const double jk = A.jac[k];
     double blk[6] = {};
     const int qf = ro.qf, qn = ro.qn;
-    // diagonal block from the far row sums (fixed order over partner blocks) and far facets
+    // diagonal block from the far row sums and far facets.  Lanes own (point a, half h)
+    // and add the partner blocks B = h, h+2, h+4, ... in a fixed order with four
+    // independent accumulators; the two halves are then added.
     {
         const double* w = rule + ro.far_w;
         const double* phi = rule + ro.far_phi;
-        for (int a = lane; a < qf; a += 32) {
+        const int npass = (qf + 15) / 16;
+        for (int pass = 0; pass < npass; ++pass) {
+            const int a = pass * 16 + (lane & 15), hb = lane >> 4;
             double Dk = 0.0;
-            if (A.pd_is_float) {
-                const float* Pd = (const float*)A.Pd + k * A.nblk * qf + a;
-                for (int64_t B = 0; B < A.nblk; ++B) Dk += (double)Pd[B * qf];
-            } else {
-                const double* Pd = (const double*)A.Pd + k * A.nblk * qf + a;
-                for (int64_t B = 0; B < A.nblk; ++B) Dk += Pd[B * qf];
+            if (a < qf) {
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                int64_t B = hb;
+                if (A.pd_is_float) {
+                    const float* Pd = (const float*)A.Pd + k * A.nblk * qf + a;
+                    for (; B + 6 < A.nblk; B += 8) {
+                        s0 += (double)Pd[B * qf];
+                        s1 += (double)Pd[(B + 2) * qf];
+                        s2 += (double)Pd[(B + 4) * qf];
+                        s3 += (double)Pd[(B + 6) * qf];
+                    }
+                    for (; B < A.nblk; B += 2) s0 += (double)Pd[B * qf];
+                } else {
+                    const double* Pd = (const double*)A.Pd + k * A.nblk * qf + a;
+                    for (; B + 6 < A.nblk; B += 8) {
+                        s0 += Pd[B * qf];
+                        s1 += Pd[(B + 2) * qf];
+                        s2 += Pd[(B + 4) * qf];
+                        s3 += Pd[(B + 6) * qf];
+                    }
+                    for (; B < A.nblk; B += 2) s0 += Pd[B * qf];
+                }
+                Dk = (s0 + s1) + (s2 + s3);
             }
-            const double bf = (D == 2 && !A.regional) ? A.Bf[k * qf + a] : 0.0;
-            const double f = jk * w[a] * (C * Dk + C / (2.0 * s) * bf);
-            for (int i = 0; i < NV; ++i)
-                for (int j = i; j < NV; ++j) blk[tri_index(i, j, NV)] += f * phi[a * NV + i] * phi[a * NV + j];
+            const double other = __shfl_xor_sync(0xffffffffu, Dk, 16);
+            Dk = (hb == 0) ? Dk + other : other + Dk;
+            if (hb == 0 && a < qf) {
+                const double bf = (D == 2 && !A.regional) ? A.Bf[k * qf + a] : 0.0;
+                const double f = jk * w[a] * (C * Dk + C / (2.0 * s) * bf);
+                for (int i = 0; i < NV; ++i)
+                    for (int j = i; j < NV; ++j) blk[tri_index(i, j, NV)] += f * phi[a * NV + i] * phi[a * NV + j];
+            }
         }
     }
     // near pairs (both roles) and near boundary facets, order-k_near points
@@ -663,8 +726,15 @@ __global__ void element_kernel(ElemArgs A) {
         const double* phi = rule + ro.near_phi;
         const double* lam = rule + ro.near_lam;
         for (int a = lane; a < qn; a += 32) {
-            double Dk = 0.0;
-            for (int q = A.enp_ptr[k]; q < A.enp_ptr[k + 1]; ++q) Dk += A.Dn[(int64_t)A.enp_ent[q] * qn + a];
+            double Dk = 0.0, D1 = 0.0;
+            const int q0 = A.enp_ptr[k], q1 = A.enp_ptr[k + 1];
+            int q = q0;
+            for (; q + 1 < q1; q += 2) {
+                Dk += A.Dn[(int64_t)A.enp_ent[q] * qn + a];
+                D1 += A.Dn[(int64_t)A.enp_ent[q + 1] * qn + a];
+            }
+            if (q < q1) Dk += A.Dn[(int64_t)A.enp_ent[q] * qn + a];
+            Dk += D1;
             double Bn = 0.0;
             if (!A.regional) {
                 double xa[2] = {0.0, 0.0};
@@ -1013,6 +1083,13 @@ int ensure_device(fl_ctx* h, int pi) {
     FL_TRY(alloc(h, (void**)&t.Bf, (size_t)nc * qf * sizeof(double)));
     FL_TRY(alloc(h, (void**)&t.contrib, (size_t)P.nslots * sizeof(double)));
     FL_TRY(alloc(h, (void**)&t.csr_val, P.csr_col.size() * sizeof(double)));
+    FL_TRY(alloc(h, &t.facet_rec, (size_t)std::max<int64_t>(P.nf, 1) * sizeof(FacetRec)));
+    if (P.dim == 2 && P.nf > 0) {
+        facet_records_kernel<<<(unsigned)((P.nf + 127) / 128), 128>>>(P.nf, t.F, t.FN, t.FLEN, t.V,
+                                                                      (FacetRec*)t.facet_rec);
+        fl::count_launch();
+        FL_CUDA_TRY(h, cudaDeviceSynchronize());
+    }
     t.ready = true;
     return FL_OK;
 }
@@ -1208,9 +1285,9 @@ int launch_far_t(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<doubl
     const int maxL = std::max(1, P.maxL);
     size_t smem = 32 * D * sizeof(double) + 32 * sizeof(double) + 32 * Q * D * sizeof(T) + 32 * Q * sizeof(T) +
                   (size_t)NV * maxL * 32 * sizeof(T) + 32 * NV * sizeof(int) + 32 * sizeof(int);
+    const int64_t ntiles = (int64_t)P.tiles.size() / 2;
     auto kern = far_tile_kernel<D, T, Q, PW>;
     FL_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int64_t ntiles = (int64_t)P.tiles.size() / 2;
     kern<<<(unsigned)ntiles, 32, smem, st>>>(A, R, maxL); fl::count_launch();
     FL_CUDA_TRY(h, cudaGetLastError());
     return FL_OK;
@@ -1267,19 +1344,16 @@ int launch_far(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>
 template <typename T, int Q>
 int launch_bnd_q(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, double expo, int pw, cudaStream_t st) {
     const unsigned nb = (unsigned)((P.nc + 31) / 32);
-    if (Q == 16 && pw == 6) {
-        bnd_far_kernel<T, Q, 6><<<nb, 32, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, t.ef_fac, t.F,
-                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf); fl::count_launch();
-    } else if (Q == 16 && pw == 5) {
-        bnd_far_kernel<T, Q, 5><<<nb, 32, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, t.ef_fac, t.F,
-                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf); fl::count_launch();
-    } else if (Q == 16 && pw == 7) {
-        bnd_far_kernel<T, Q, 7><<<nb, 32, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, t.ef_fac, t.F,
-                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf); fl::count_launch();
-    } else {
-        bnd_far_kernel<T, Q, 0><<<nb, 32, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, t.ef_fac, t.F,
-                                                   t.FN, t.FLEN, t.V, t.rule, ro, (T)expo, t.Bf); fl::count_launch();
-    }
+    const FacetRec* FR = (const FacetRec*)t.facet_rec;
+#define FL_BND(PWV)                                                                                                  \
+    bnd_far_kernel<T, Q, PWV><<<nb, 32 * BND_WARPS, 0, st>>>(P.nc, P.nf, t.cen, (const T*)t.pts, t.hasdof, t.ef_ptr, \
+                                                              t.ef_fac, FR, nullptr, t.rule, ro, (T)expo, t.Bf)
+    if (Q == 16 && pw == 6) FL_BND(6);
+    else if (Q == 16 && pw == 5) FL_BND(5);
+    else if (Q == 16 && pw == 7) FL_BND(7);
+    else FL_BND(0);
+#undef FL_BND
+    fl::count_launch();
     FL_CUDA_TRY(h, cudaGetLastError());
     return FL_OK;
 }

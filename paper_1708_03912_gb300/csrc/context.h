@@ -75,6 +75,7 @@ struct DevTables {
     double* Bf = nullptr;   // nc * Qf boundary sums (far facets)
     double* contrib = nullptr;
     double* csr_val = nullptr;
+    void* facet_rec = nullptr;  // compact boundary-facet records (2D)
     double* rule = nullptr; // per-s rule tables (see assemble.cu)
     size_t rule_len = 0;
 };
@@ -92,6 +93,7 @@ struct fl_ctx {
     fl::DevTables dev[2];
     std::vector<fl::DBuf> bufs;
     int profiling = 0;
+    int no_persistent = 0;  // 1: run CG as captured kernel batches instead of one cooperative launch
     cudaEvent_t ev[2 * FL_NSTAGES] = {};
     bool ev_made = false;
     bool ev_recorded = false;

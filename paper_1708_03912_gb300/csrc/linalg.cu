@@ -2,6 +2,7 @@
 // matrix-vector product, whose cost is n^2 per product, and diagonally
 // preconditioned conjugate gradients, whose iteration count grows like n^{s/d}.
 // Also the float32 / bfloat16 copies used by the mixed-precision refinement.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -222,6 +223,10 @@ __global__ void sum_partials_kernel(const double* partial, int nb, double* out) 
 }
 
 // ------------------------------------------------------------- PCG parts --
+struct TAVoid {
+    const void* p;
+};
+
 struct CgScalars {
     double rz, rz_new, pq, rr, bb, alpha, beta, stop;
     int breakdown;
@@ -373,7 +378,7 @@ __global__ void zero_kernel(int64_t n, double* x) {
 
 // ------------------------------------------------------- solver workspace --
 struct SolveWork {
-    double *r, *z, *p, *q, *dinv, *dinv_lo, *d, *t, *prz, *prr, *ppq;
+    double *r, *z, *p, *q, *dinv, *dinv_lo, *d, *t, *prz, *prr, *ppq, *part;
     float* xf;
     CgScalars* s;
     CgScalars* s_host;
@@ -386,7 +391,7 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
     // (eight float64 vectors, three reduction buffers, one float32 vector, scalars)
     // is carved with the same 256-byte rounding that sizes it
     const size_t need = 8 * round256(n * sizeof(double)) + 3 * round256(RED_BLOCKS * sizeof(double)) +
-                        round256(n * sizeof(float)) + round256(sizeof(CgScalars));
+                        round256(2 * 1024 * sizeof(double)) + round256(n * sizeof(float)) + round256(sizeof(CgScalars));
     void* base = nullptr;
     if (h->solve_ws_bytes < need) {
         for (auto& g : h->cg_graphs) cudaGraphExecDestroy(g.exec);
@@ -421,6 +426,7 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
     w.prz = (double*)take(RED_BLOCKS * sizeof(double));
     w.prr = (double*)take(RED_BLOCKS * sizeof(double));
     w.ppq = (double*)take(RED_BLOCKS * sizeof(double));
+    w.part = (double*)take(2 * 1024 * sizeof(double));
     w.xf = (float*)take(n * sizeof(float));
     w.s = (CgScalars*)take(sizeof(CgScalars));
     w.s_host = (CgScalars*)h->solve_host;
@@ -433,6 +439,188 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
         cudaError_t e_ = (x);                                                                              \
         if (e_ != cudaSuccess) return set_err(h, FL_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
     } while (0)
+
+// ---------------------------------------------------- persistent Jacobi-PCG --
+// The whole iteration in one cooperative launch: rows of the matrix-vector product and
+// vector entries are split over a fixed grid; after each phase every block adds the
+// per-block partial sums in the same order, so all blocks hold bitwise identical
+// scalars and take the same branch (no block can leave while others wait).
+constexpr int PCG_THREADS = 256;
+constexpr int PCG_MAX_BLOCKS = 1024;
+
+__device__ __forceinline__ double block_total(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+    return t;  // same value in every thread
+}
+
+// sum of part[0..nb) in index order, computed by every thread (identical results)
+__device__ __forceinline__ double grid_total(const double* part, int nb, int stride, double* sh) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += part[(int64_t)i * stride];
+    return block_total(acc, sh);
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(PCG_THREADS) pcg_persistent_kernel(int64_t n, const TA* __restrict__ A, int64_t lda,
+                                                                      const double* __restrict__ dinv,
+                                                                      const double* __restrict__ rhs, double* u, double* r,
+                                                                      double* z, double* p, double* q, float* pf,
+                                                                      double* part, CgScalars* S, double tol, int maxit) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double sh[PCG_THREADS / 32];
+    const int nb = gridDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)nb * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
+    // start: u = 0, r = rhs, z = D^-1 r, p = z
+    double a0 = 0.0, c0 = 0.0;
+    for (int64_t i = tid; i < n; i += nthreads) {
+        const double ri = rhs[i];
+        const double zi = dinv[i] * ri;
+        u[i] = 0.0;
+        r[i] = ri;
+        z[i] = zi;
+        p[i] = zi;
+        if (pf) pf[i] = (float)zi;
+        a0 = fma(ri, zi, a0);
+        c0 = fma(ri, ri, c0);
+    }
+    a0 = block_total(a0, sh);
+    c0 = block_total(c0, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a0;
+        part[2 * blockIdx.x + 1] = c0;
+    }
+    grid.sync();
+    double rz = grid_total(part, nb, 2, sh);
+    const double rr0 = grid_total(part + 1, nb, 2, sh);
+    const double stop = tol * tol * rr0;
+    double rr = rr0;
+    int it = 0, breakdown = 0;
+    grid.sync();  // every block has read part before it is rewritten
+    while (rr > stop && it < maxit) {
+        // q = A p and the partial p.q (one warp per row)
+        double pq = 0.0;
+        for (int64_t row = warp; row < n; row += nwarps) {
+            const TA* a = A + row * lda;
+            double acc;
+            // four independent accumulators keep four loads per lane in flight
+            if constexpr (sizeof(TA) == 8) {
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                int64_t j = lane;
+                for (; j + 96 < n; j += 128) {
+                    s0 = fma((double)a[j], p[j], s0);
+                    s1 = fma((double)a[j + 32], p[j + 32], s1);
+                    s2 = fma((double)a[j + 64], p[j + 64], s2);
+                    s3 = fma((double)a[j + 96], p[j + 96], s3);
+                }
+                for (; j < n; j += 32) s0 = fma((double)a[j], p[j], s0);
+                acc = warp_sum((s0 + s1) + (s2 + s3));
+            } else {
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                int64_t j = lane;
+                for (; j + 96 < n; j += 128) {
+                    s0 = fmaf((float)a[j], pf[j], s0);
+                    s1 = fmaf((float)a[j + 32], pf[j + 32], s1);
+                    s2 = fmaf((float)a[j + 64], pf[j + 64], s2);
+                    s3 = fmaf((float)a[j + 96], pf[j + 96], s3);
+                }
+                for (; j < n; j += 32) s0 = fmaf((float)a[j], pf[j], s0);
+                acc = warp_sum((double)s0 + (double)s1 + ((double)s2 + (double)s3));
+            }
+            if (lane == 0) {
+                q[row] = acc;
+                pq = fma(p[row], acc, pq);
+            }
+        }
+        pq = block_total(pq, sh);
+        if (threadIdx.x == 0) part[2 * blockIdx.x] = pq;
+        grid.sync();
+        pq = grid_total(part, nb, 2, sh);
+        if (!(pq > 0.0)) {
+            breakdown = 1;
+            break;
+        }
+        const double alpha = rz / pq;
+        grid.sync();
+        double a1 = 0.0, c1 = 0.0;
+        for (int64_t i = tid; i < n; i += nthreads) {
+            u[i] = fma(alpha, p[i], u[i]);
+            const double ri = fma(-alpha, q[i], r[i]);
+            r[i] = ri;
+            const double zi = dinv[i] * ri;
+            z[i] = zi;
+            a1 = fma(ri, zi, a1);
+            c1 = fma(ri, ri, c1);
+        }
+        a1 = block_total(a1, sh);
+        c1 = block_total(c1, sh);
+        if (threadIdx.x == 0) {
+            part[2 * blockIdx.x] = a1;
+            part[2 * blockIdx.x + 1] = c1;
+        }
+        grid.sync();
+        const double rz_new = grid_total(part, nb, 2, sh);
+        rr = grid_total(part + 1, nb, 2, sh);
+        const double beta = rz_new / rz;
+        rz = rz_new;
+        ++it;
+        for (int64_t i = tid; i < n; i += nthreads) {
+            const double pi = fma(beta, p[i], z[i]);
+            p[i] = pi;
+            if (pf) pf[i] = (float)pi;
+        }
+        grid.sync();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S->rr = rr;
+        S->stop = stop;
+        S->it = it;
+        S->breakdown = breakdown;
+        S->done = 1;
+        S->rz = rr0;  // initial residual norm^2, read back by the host
+    }
+}
+
+// Launch the persistent solver if the device supports cooperative launches and the grid
+// fits; returns false (nothing launched) otherwise.
+static bool pcg_persistent(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int64_t ldm,
+                           const double* dinv, const double* rhs, double* d, double tol, int maxit, cudaStream_t st,
+                           int* status) {
+    if (dtype == FL_BF16 || h->no_persistent) return false;
+    int dev = 0, coop = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop) return false;
+    int per_sm = 0;
+    const void* fn = (dtype == FL_F64) ? (const void*)pcg_persistent_kernel<double> : (const void*)pcg_persistent_kernel<float>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_THREADS, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    const int blocks = std::min(sms * std::min(per_sm, 2), PCG_MAX_BLOCKS);
+    float* pf = (dtype == FL_F64) ? nullptr : w.xf;
+    const TAVoid Mv{M};
+    void* args[] = {(void*)&n, (void*)&Mv.p, (void*)&ldm, (void*)&dinv, (void*)&rhs, (void*)&d, (void*)&w.r, (void*)&w.z,
+                    (void*)&w.p, (void*)&w.q, (void*)&pf, (void*)&w.part, (void*)&w.s, (void*)&tol, (void*)&maxit};
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(PCG_THREADS), args, 0, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    fl::count_launch();
+    *status = FL_OK;
+    return true;
+}
 
 // Jacobi-PCG on y = M x (M of type dtype) for M d = rhs from d = 0, relative tolerance tol
 // (||rhs - M d|| by the recursion).  The iterations run in batches of CG_BATCH captured in a
@@ -478,6 +666,16 @@ static int cg_graph(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M
 
 static int pcg(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int64_t ldm, const double* dinv,
                const double* rhs, double* d, double tol, int maxit, int* its, double* relres, cudaStream_t st) {
+    int pst = FL_OK;
+    if (pcg_persistent(h, w, n, dtype, M, ldm, dinv, rhs, d, tol, maxit, st, &pst)) {
+        FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+        FL_CU(h, cudaStreamSynchronize(st));
+        const CgScalars& S = *w.s_host;
+        *its = S.it;
+        *relres = (S.rz > 0.0) ? std::sqrt(S.rr / S.rz) : 0.0;
+        if (S.breakdown) return set_err(h, FL_ENOTSPD, "CG breakdown: p^T A p <= 0");
+        return (S.rr <= S.stop) ? FL_OK : FL_ENOTCONV;
+    }
     const unsigned g = (unsigned)((n + 255) / 256);
     zero_kernel<<<g, 256, 0, st>>>(n, d); fl::count_launch();
     residual_kernel<<<g, 256, 0, st>>>(n, rhs, nullptr, w.r); fl::count_launch();

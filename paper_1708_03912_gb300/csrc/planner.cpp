@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
 #include <unordered_map>
 
 #include "internal.h"
@@ -244,13 +245,6 @@ int plan_mesh(Plan& P, int dim, int64_t nv, const double* V, int64_t nc, const i
     return FL_OK;
 }
 
-namespace {
-struct Entry {
-    int j;
-    int64_t slot;
-};
-}  // namespace
-
 int plan_dofs(Plan& P, int paper_all, std::string& err) {
     const int m = P.nvpc, dim = P.dim;
     const int64_t nc = P.nc, nv = P.nv;
@@ -330,146 +324,212 @@ int plan_dofs(Plan& P, int paper_all, std::string& err) {
         std::vector<int> tmp;
         csr_from_lists(ol, tmp, P.occ_loc);
     }
-    // pair classes
-    std::vector<std::vector<int>> ex(nc), enp(nc);
-    std::vector<std::vector<std::pair<int, int>>> ef(nc);
+    // pair classes, in parallel over ranges of original cells.  Per-range outputs are
+    // concatenated in cell order, so nothing depends on the number of threads.
+    const int nthr = (int)std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
+    const int64_t chunk = (nc + nthr - 1) / nthr;
+    struct Part {
+        std::vector<int> ex, ef_f, ef_c, tp_type, tp_vert, tp_cell, np_a, np_b;
+    };
+    std::vector<Part> parts(nthr);
+    std::vector<int64_t> ex_off(nc), ef_off(nc);
+    std::vector<int> ex_len(nc), ef_len(nc, 0);
+    auto classify = [&](int t) {
+        Part& o = parts[t];
+        const int64_t K0 = (int64_t)t * chunk, K1 = std::min(nc, K0 + chunk);
+        if (K0 >= K1) return;
+        std::vector<int64_t> vs0(nv, -1), vs1(nv, -1), cs(nc, -1), fs(std::max<int64_t>(P.nf, 1), -1);
+        std::vector<int> n1, touch, nearc;
+        std::vector<std::pair<int, int>> efl;
+        for (int64_t K = K0; K < K1; ++K) {
+            const int* c = &P.C[K * m];
+            const int k = P.iperm[K];
+            n1.clear();
+            for (int a = 0; a < m; ++a) {
+                vs0[c[a]] = K;
+                vs1[c[a]] = K;
+                n1.push_back(c[a]);
+            }
+            for (int a = 0; a < m; ++a)
+                for (int q = P.nbr_ptr[c[a]]; q < P.nbr_ptr[c[a] + 1]; ++q) {
+                    const int u = P.nbr[q];
+                    if (vs1[u] != K) {
+                        vs1[u] = K;
+                        n1.push_back(u);
+                    }
+                }
+            touch.clear();
+            nearc.clear();
+            cs[K] = K;
+            for (int a = 0; a < m; ++a)
+                for (int q = P.v2c_ptr[c[a]]; q < P.v2c_ptr[c[a] + 1]; ++q) {
+                    const int M = P.v2c[q];
+                    if (cs[M] != K) {
+                        cs[M] = K;
+                        touch.push_back(M);
+                    }
+                }
+            for (int u : n1) {
+                if (vs0[u] == K) continue;
+                for (int q = P.v2c_ptr[u]; q < P.v2c_ptr[u + 1]; ++q) {
+                    const int M = P.v2c[q];
+                    if (cs[M] != K) {
+                        cs[M] = K;
+                        nearc.push_back(M);
+                    }
+                }
+            }
+            std::sort(touch.begin(), touch.end());
+            std::sort(nearc.begin(), nearc.end());
+            // exclusion list of the far-field kernel (internal indices)
+            const size_t e0 = o.ex.size();
+            ex_off[K] = (int64_t)e0;
+            o.ex.push_back(k);
+            for (int M : touch) o.ex.push_back(P.iperm[M]);
+            for (int M : nearc) o.ex.push_back(P.iperm[M]);
+            std::sort(o.ex.begin() + e0, o.ex.end());
+            ex_len[K] = (int)(o.ex.size() - e0);
+            // touching pairs, canonical: lower original index plays K
+            for (int M : touch) {
+                if (M < K) continue;
+                const int km = P.iperm[M];
+                if (!P.hasdof[k] && !P.hasdof[km]) continue;
+                const int* d = &P.C[(int64_t)M * m];
+                int sv[3], ns = 0;
+                for (int a = 0; a < m; ++a)
+                    for (int b = 0; b < m; ++b)
+                        if (c[a] == d[b]) sv[ns++] = c[a];
+                int tv[5] = {-1, -1, -1, -1, -1};
+                int type;
+                if (dim == 1) {
+                    // left interval has the shared vertex as its right end
+                    const int left = (c[1] == sv[0]) ? (int)K : M, right = (left == K) ? M : (int)K;
+                    tv[0] = P.C[(int64_t)left * 2];
+                    tv[1] = sv[0];
+                    tv[2] = P.C[(int64_t)right * 2 + 1];
+                    type = 2;
+                    o.tp_cell.push_back(left);
+                    o.tp_cell.push_back(right);
+                } else if (ns == 2) {
+                    type = 0;
+                    tv[0] = sv[0];
+                    tv[1] = sv[1];
+                    for (int a = 0; a < 3; ++a)
+                        if (c[a] != sv[0] && c[a] != sv[1]) tv[2] = c[a];
+                    for (int a = 0; a < 3; ++a)
+                        if (d[a] != sv[0] && d[a] != sv[1]) tv[3] = d[a];
+                    o.tp_cell.push_back((int)K);
+                    o.tp_cell.push_back(M);
+                } else {
+                    type = 1;
+                    int ia = 0, ib = 0;
+                    for (int a = 0; a < 3; ++a) {
+                        if (c[a] == sv[0]) ia = a;
+                        if (d[a] == sv[0]) ib = a;
+                    }
+                    tv[0] = sv[0];
+                    tv[1] = c[(ia + 1) % 3];
+                    tv[2] = c[(ia + 2) % 3];
+                    tv[3] = d[(ib + 1) % 3];
+                    tv[4] = d[(ib + 2) % 3];
+                    o.tp_cell.push_back((int)K);
+                    o.tp_cell.push_back(M);
+                }
+                o.tp_type.push_back(type);
+                for (int a = 0; a < 5; ++a) o.tp_vert.push_back(tv[a]);
+            }
+            // near separated pairs, unordered by internal index
+            for (int M : nearc) {
+                const int km = P.iperm[M];
+                if (km < k) continue;
+                if (!P.hasdof[k] && !P.hasdof[km]) continue;
+                o.np_a.push_back(k);
+                o.np_b.push_back(km);
+            }
+            // boundary facets handled individually (touching or at distance 1)
+            if (P.hasdof[k]) {
+                efl.clear();
+                for (int v : n1)
+                    for (int q = P.v2f_ptr[v]; q < P.v2f_ptr[v + 1]; ++q) {
+                        const int f = P.v2f[q];
+                        if (fs[f] == K) continue;
+                        fs[f] = K;
+                        int sh = 0;
+                        for (int a = 0; a < dim; ++a) sh += (vs0[P.F[(int64_t)f * dim + a]] == K) ? 1 : 0;
+                        const int cls = (sh == 0) ? 1 : (dim == 1 ? 2 : (sh == 2 ? 2 : 3));
+                        efl.push_back({f, cls});
+                    }
+                std::sort(efl.begin(), efl.end());
+                ef_off[K] = (int64_t)o.ef_f.size();
+                ef_len[K] = (int)efl.size();
+                for (auto& pr : efl) {
+                    o.ef_f.push_back(pr.first);
+                    o.ef_c.push_back(pr.second);
+                }
+            }
+        }
+    };
+    {
+        std::vector<std::thread> th;
+        for (int t = 1; t < nthr; ++t) th.emplace_back(classify, t);
+        classify(0);
+        for (auto& x : th) x.join();
+    }
     P.np_a.clear();
     P.np_b.clear();
     P.tp_type.clear();
     P.tp_vert.clear();
     P.tp_cell.clear();
-    std::vector<char> mark0(nv, 0), mark1(nv, 0);
-    std::vector<int> touch, nearc, n1;
-    for (int64_t K = 0; K < nc; ++K) {  // original order
-        const int* c = &P.C[K * m];
-        int k = P.iperm[K];
-        n1.clear();
-        for (int a = 0; a < m; ++a) {
-            mark0[c[a]] = 1;
-            n1.push_back(c[a]);
-            for (int q = P.nbr_ptr[c[a]]; q < P.nbr_ptr[c[a] + 1]; ++q) n1.push_back(P.nbr[q]);
-        }
-        std::sort(n1.begin(), n1.end());
-        n1.erase(std::unique(n1.begin(), n1.end()), n1.end());
-        for (int v : n1) mark1[v] = 1;
-        touch.clear();
-        nearc.clear();
-        for (int v : n1) {
-            for (int q = P.v2c_ptr[v]; q < P.v2c_ptr[v + 1]; ++q) {
-                int M = P.v2c[q];
-                if (M == K) continue;
-                if (mark0[v]) touch.push_back(M);
-                else nearc.push_back(M);
-            }
-        }
-        std::sort(touch.begin(), touch.end());
-        touch.erase(std::unique(touch.begin(), touch.end()), touch.end());
-        std::sort(nearc.begin(), nearc.end());
-        nearc.erase(std::unique(nearc.begin(), nearc.end()), nearc.end());
-        std::vector<int> nearonly;
-        std::set_difference(nearc.begin(), nearc.end(), touch.begin(), touch.end(), std::back_inserter(nearonly));
-        // exclusion list of the far-field kernel (internal indices)
-        auto& E = ex[k];
-        E.push_back(k);
-        for (int M : touch) E.push_back(P.iperm[M]);
-        for (int M : nearonly) E.push_back(P.iperm[M]);
-        std::sort(E.begin(), E.end());
-        // touching pairs, canonical: lower original index plays K
-        for (int M : touch) {
-            if (M < K) continue;
-            int km = P.iperm[M];
-            if (!P.hasdof[k] && !P.hasdof[km]) continue;
-            const int* d = &P.C[(int64_t)M * m];
-            int sv[3], ns = 0;
-            for (int a = 0; a < m; ++a)
-                for (int b = 0; b < m; ++b)
-                    if (c[a] == d[b]) sv[ns++] = c[a];
-            int tv[5] = {-1, -1, -1, -1, -1};
-            int type;
-            if (dim == 1) {
-                // left interval has the shared vertex as its right end
-                int left = (c[1] == sv[0]) ? (int)K : M, right = (left == K) ? M : (int)K;
-                tv[0] = P.C[(int64_t)left * 2];
-                tv[1] = sv[0];
-                tv[2] = P.C[(int64_t)right * 2 + 1];
-                type = 2;
-                P.tp_cell.push_back(left);
-                P.tp_cell.push_back(right);
-            } else if (ns == 2) {
-                type = 0;
-                tv[0] = sv[0];
-                tv[1] = sv[1];
-                for (int a = 0; a < 3; ++a)
-                    if (c[a] != sv[0] && c[a] != sv[1]) tv[2] = c[a];
-                for (int a = 0; a < 3; ++a)
-                    if (d[a] != sv[0] && d[a] != sv[1]) tv[3] = d[a];
-                P.tp_cell.push_back((int)K);
-                P.tp_cell.push_back(M);
-            } else {
-                type = 1;
-                int ia = 0, ib = 0;
-                for (int a = 0; a < 3; ++a) {
-                    if (c[a] == sv[0]) ia = a;
-                    if (d[a] == sv[0]) ib = a;
-                }
-                tv[0] = sv[0];
-                tv[1] = c[(ia + 1) % 3];
-                tv[2] = c[(ia + 2) % 3];
-                tv[3] = d[(ib + 1) % 3];
-                tv[4] = d[(ib + 2) % 3];
-                P.tp_cell.push_back((int)K);
-                P.tp_cell.push_back(M);
-            }
-            P.tp_type.push_back(type);
-            for (int a = 0; a < 5; ++a) P.tp_vert.push_back(tv[a]);
-        }
-        // near separated pairs, unordered by internal index
-        for (int M : nearonly) {
-            int km = P.iperm[M];
-            if (km < k) continue;
-            if (!P.hasdof[k] && !P.hasdof[km]) continue;
-            int p = (int)P.np_a.size();
-            P.np_a.push_back(k);
-            P.np_b.push_back(km);
-            enp[k].push_back(2 * p);
-            enp[km].push_back(2 * p + 1);
-        }
-        // boundary facets handled individually (touching or at distance 1)
-        if (P.hasdof[k]) {
-            for (int v : n1)
-                for (int q = P.v2f_ptr[v]; q < P.v2f_ptr[v + 1]; ++q) {
-                    int f = P.v2f[q];
-                    int sh = 0;
-                    for (int a = 0; a < dim; ++a) sh += mark0[P.F[(int64_t)f * dim + a]];
-                    int cls = (sh == 0) ? 1 : (dim == 1 ? 2 : (sh == 2 ? 2 : 3));
-                    ef[k].push_back({f, cls});
-                }
-            auto& l = ef[k];
-            std::sort(l.begin(), l.end());
-            l.erase(std::unique(l.begin(), l.end()), l.end());
-        }
-        for (int a = 0; a < m; ++a) mark0[c[a]] = 0;
-        for (int v : n1) mark1[v] = 0;
+    for (auto& o : parts) {
+        P.np_a.insert(P.np_a.end(), o.np_a.begin(), o.np_a.end());
+        P.np_b.insert(P.np_b.end(), o.np_b.begin(), o.np_b.end());
+        P.tp_type.insert(P.tp_type.end(), o.tp_type.begin(), o.tp_type.end());
+        P.tp_vert.insert(P.tp_vert.end(), o.tp_vert.begin(), o.tp_vert.end());
+        P.tp_cell.insert(P.tp_cell.end(), o.tp_cell.begin(), o.tp_cell.end());
     }
-    csr_from_lists(ex, P.ex_ptr, P.ex_idx);
-    for (auto& l : enp) std::sort(l.begin(), l.end());
-    csr_from_lists(enp, P.enp_ptr, P.enp_ent);
+    // exclusion and facet lists in internal order
+    P.ex_ptr.assign(nc + 1, 0);
     P.ef_ptr.assign(nc + 1, 0);
-    P.ef_fac.clear();
-    P.ef_cls.clear();
     for (int64_t k = 0; k < nc; ++k) {
-        for (auto& pr : ef[k]) {
-            P.ef_fac.push_back(pr.first);
-            P.ef_cls.push_back(pr.second);
+        const int K = P.perm[k];
+        P.ex_ptr[k + 1] = P.ex_ptr[k] + ex_len[K];
+        P.ef_ptr[k + 1] = P.ef_ptr[k] + ef_len[K];
+    }
+    P.ex_idx.resize(P.ex_ptr[nc]);
+    P.ef_fac.resize(P.ef_ptr[nc]);
+    P.ef_cls.resize(P.ef_ptr[nc]);
+    for (int64_t k = 0; k < nc; ++k) {
+        const int K = P.perm[k];
+        const Part& o = parts[K / chunk];
+        std::copy(o.ex.begin() + ex_off[K], o.ex.begin() + ex_off[K] + ex_len[K], P.ex_idx.begin() + P.ex_ptr[k]);
+        if (ef_len[K]) {
+            std::copy(o.ef_f.begin() + ef_off[K], o.ef_f.begin() + ef_off[K] + ef_len[K], P.ef_fac.begin() + P.ef_ptr[k]);
+            std::copy(o.ef_c.begin() + ef_off[K], o.ef_c.begin() + ef_off[K] + ef_len[K], P.ef_cls.begin() + P.ef_ptr[k]);
         }
-        P.ef_ptr[k + 1] = (int)P.ef_fac.size();
+    }
+    std::vector<Part>().swap(parts);
+    // element -> (near pair, role), pairs in increasing order
+    {
+        std::vector<int> cnt(nc + 1, 0);
+        for (size_t p = 0; p < P.np_a.size(); ++p) {
+            cnt[P.np_a[p] + 1]++;
+            cnt[P.np_b[p] + 1]++;
+        }
+        for (int64_t k = 0; k < nc; ++k) cnt[k + 1] += cnt[k];
+        P.enp_ptr = cnt;
+        P.enp_ent.assign(cnt[nc], 0);
+        std::vector<int> cur(cnt.begin(), cnt.end() - 1);
+        for (size_t p = 0; p < P.np_a.size(); ++p) {
+            P.enp_ent[cur[P.np_a[p]]++] = (int)(2 * p);
+            P.enp_ent[cur[P.np_b[p]]++] = (int)(2 * p + 1);
+        }
     }
     // contribution slots and the sparse near-field pattern with its gather lists
     const int64_t ntp = (int64_t)P.tp_type.size(), nnp = (int64_t)P.np_a.size();
     P.tp_slot.resize(ntp);
     int64_t cur = 0;
     for (int64_t p = 0; p < ntp; ++p) {
-        int nl = (P.tp_type[p] == 0) ? 4 : (P.tp_type[p] == 1 ? 5 : 3);
+        const int nl = (P.tp_type[p] == 0) ? 4 : (P.tp_type[p] == 1 ? 5 : 3);
         P.tp_slot[p] = cur;
         cur += nl * nl;
     }
@@ -478,59 +538,140 @@ int plan_dofs(Plan& P, int paper_all, std::string& err) {
     P.el_slot0 = cur;
     cur += nc * m * m;
     P.nslots = cur;
-    std::vector<std::vector<Entry>> rows(P.n);
+    // Rows of the sparse near-field part are generated row by row from inverse incidence
+    // maps (dof -> cells -> element block / touching pairs / near pairs), sorted on
+    // (column, slot) and turned into CSR pieces; threads own contiguous row ranges and
+    // their pieces are concatenated in row order.
+    std::vector<int> c2t_ptr(nc + 1, 0), c2t;  // original cell -> touching pairs
     for (int64_t p = 0; p < ntp; ++p) {
-        int nl = (P.tp_type[p] == 0) ? 4 : (P.tp_type[p] == 1 ? 5 : 3);
-        const int* tv = &P.tp_vert[5 * p];
-        for (int a = 0; a < nl; ++a) {
-            int i = P.dov[tv[a]];
-            if (i < 0) continue;
-            for (int b = 0; b < nl; ++b) {
-                int j = P.dov[tv[b]];
-                if (j >= 0) rows[i].push_back({j, P.tp_slot[p] + a * nl + b});
-            }
+        c2t_ptr[P.tp_cell[2 * p] + 1]++;
+        c2t_ptr[P.tp_cell[2 * p + 1] + 1]++;
+    }
+    for (int64_t K = 0; K < nc; ++K) c2t_ptr[K + 1] += c2t_ptr[K];
+    c2t.resize(c2t_ptr[nc]);
+    {
+        std::vector<int> cur(c2t_ptr.begin(), c2t_ptr.end() - 1);
+        for (int64_t p = 0; p < ntp; ++p) {
+            c2t[cur[P.tp_cell[2 * p]]++] = (int)p;
+            c2t[cur[P.tp_cell[2 * p + 1]]++] = (int)p;
         }
     }
-    for (int64_t p = 0; p < nnp; ++p) {
-        int ka = P.np_a[p], kb = P.np_b[p];
-        for (int a = 0; a < m; ++a) {
-            int i = P.cdof[(int64_t)ka * m + a];
-            for (int b = 0; b < m; ++b) {
-                int j = P.cdof[(int64_t)kb * m + b];
-                if (i < 0 || j < 0) continue;
-                int64_t s = P.np_slot0 + p * m * m + a * m + b;
-                rows[i].push_back({j, s});
-                rows[j].push_back({i, s});
+    struct RowPart {
+        std::vector<int> cnt, col;           // per row: number of distinct columns; columns
+        std::vector<int64_t> gcnt, slot;     // per distinct column: number of slots; slots
+    };
+    std::vector<RowPart> rparts(nthr);
+    const int64_t rchunk = (P.n + nthr - 1) / nthr;
+    auto build_rows = [&](int t) {
+        RowPart& o = rparts[t];
+        const int64_t i0 = (int64_t)t * rchunk, i1 = std::min(P.n, i0 + rchunk);
+        std::vector<std::pair<int, int64_t>> e;
+        std::vector<int> tps;
+        e.reserve(4096);
+        const int64_t rows_here = std::max<int64_t>(0, i1 - i0);
+        o.cnt.reserve(rows_here);
+        o.col.reserve(rows_here * 48);
+        o.gcnt.reserve(rows_here * 48);
+        o.slot.reserve(rows_here * 160);
+        for (int64_t i = i0; i < i1; ++i) {
+            const int v = P.vod[i];
+            e.clear();
+            tps.clear();
+            for (int q = P.v2c_ptr[v]; q < P.v2c_ptr[v + 1]; ++q) {
+                const int K = P.v2c[q];
+                const int k = P.iperm[K];
+                int a = 0;
+                for (int x = 0; x < m; ++x)
+                    if (P.C[(int64_t)K * m + x] == v) a = x;
+                // element block, row a (internal slots follow the oriented cell order)
+                for (int b = 0; b < m; ++b) {
+                    const int j = P.cdof[(int64_t)k * m + b];
+                    if (j >= 0) e.push_back({j, P.el_slot0 + (int64_t)k * m * m + a * m + b});
+                }
+                for (int q2 = c2t_ptr[K]; q2 < c2t_ptr[K + 1]; ++q2) tps.push_back(c2t[q2]);
+                // near pairs of cell k in either role
+                for (int q2 = P.enp_ptr[k]; q2 < P.enp_ptr[k + 1]; ++q2) {
+                    const int ent = P.enp_ent[q2];
+                    const int64_t pp = ent >> 1;
+                    const int role = ent & 1;
+                    const int other = role ? P.np_a[pp] : P.np_b[pp];
+                    for (int b = 0; b < m; ++b) {
+                        const int j = P.cdof[(int64_t)other * m + b];
+                        if (j < 0) continue;
+                        const int64_t sl = role ? P.np_slot0 + pp * m * m + b * m + a : P.np_slot0 + pp * m * m + a * m + b;
+                        e.push_back({j, sl});
+                    }
+                }
             }
+            std::sort(tps.begin(), tps.end());
+            tps.erase(std::unique(tps.begin(), tps.end()), tps.end());
+            for (int p2 : tps) {
+                const int nl = (P.tp_type[p2] == 0) ? 4 : (P.tp_type[p2] == 1 ? 5 : 3);
+                const int* tv = &P.tp_vert[5 * (int64_t)p2];
+                int a = -1;
+                for (int x = 0; x < nl; ++x)
+                    if (tv[x] == v) a = x;
+                if (a < 0) continue;
+                for (int b = 0; b < nl; ++b) {
+                    const int j = P.dov[tv[b]];
+                    if (j >= 0) e.push_back({j, P.tp_slot[p2] + a * nl + b});
+                }
+            }
+            std::sort(e.begin(), e.end());
+            int ncol = 0;
+            for (size_t q = 0; q < e.size(); ++q) {
+                if (q == 0 || e[q].first != e[q - 1].first) {
+                    o.col.push_back(e[q].first);
+                    o.gcnt.push_back(0);
+                    ++ncol;
+                }
+                o.gcnt.back()++;
+                o.slot.push_back(e[q].second);
+            }
+            o.cnt.push_back(ncol);
         }
+    };
+    {
+        std::vector<std::thread> th;
+        for (int t = 1; t < nthr; ++t) th.emplace_back(build_rows, t);
+        build_rows(0);
+        for (auto& x : th) x.join();
     }
-    for (int64_t k = 0; k < nc; ++k)
-        for (int a = 0; a < m; ++a) {
-            int i = P.cdof[k * m + a];
-            if (i < 0) continue;
-            for (int b = 0; b < m; ++b) {
-                int j = P.cdof[k * m + b];
-                if (j >= 0) rows[i].push_back({j, P.el_slot0 + k * m * m + a * m + b});
-            }
-        }
+    // concatenate: offsets per part first, then the copies in parallel
+    std::vector<int64_t> coff(nthr + 1, 0), soff(nthr + 1, 0);
+    for (int t = 0; t < nthr; ++t) {
+        coff[t + 1] = coff[t] + (int64_t)rparts[t].col.size();
+        soff[t + 1] = soff[t] + (int64_t)rparts[t].slot.size();
+    }
     P.csr_ptr.assign(P.n + 1, 0);
-    P.csr_col.clear();
-    P.g_ptr.clear();
-    P.g_slot.clear();
-    for (int64_t i = 0; i < P.n; ++i) {
-        auto& r = rows[i];
-        std::sort(r.begin(), r.end(), [](const Entry& x, const Entry& y) { return x.j < y.j || (x.j == y.j && x.slot < y.slot); });
-        for (size_t q = 0; q < r.size(); ++q) {
-            if (q == 0 || r[q].j != r[q - 1].j) {
-                P.csr_col.push_back(r[q].j);
-                P.g_ptr.push_back((int64_t)P.g_slot.size());
+    {
+        int64_t row = 0;
+        for (auto& o : rparts)
+            for (int c : o.cnt) {
+                P.csr_ptr[row + 1] = P.csr_ptr[row] + c;
+                ++row;
             }
-            P.g_slot.push_back(r[q].slot);
-        }
-        P.csr_ptr[i + 1] = (int)P.csr_col.size();
-        std::vector<Entry>().swap(r);
     }
-    P.g_ptr.push_back((int64_t)P.g_slot.size());
+    P.csr_col.resize(coff[nthr]);
+    P.g_ptr.resize(coff[nthr] + 1);
+    P.g_slot.resize(soff[nthr]);
+    P.g_ptr[coff[nthr]] = soff[nthr];
+    {
+        auto copy_part = [&](int t) {
+            const RowPart& o = rparts[t];
+            std::copy(o.col.begin(), o.col.end(), P.csr_col.begin() + coff[t]);
+            std::copy(o.slot.begin(), o.slot.end(), P.g_slot.begin() + soff[t]);
+            int64_t acc = soff[t];
+            for (size_t z = 0; z < o.gcnt.size(); ++z) {
+                P.g_ptr[coff[t] + z] = acc;
+                acc += o.gcnt[z];
+            }
+        };
+        std::vector<std::thread> th;
+        for (int t = 1; t < nthr; ++t) th.emplace_back(copy_part, t);
+        copy_part(0);
+        for (auto& x : th) x.join();
+    }
     return FL_OK;
 }
 
