@@ -176,6 +176,92 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
              const fl_solve_opts* o, fl_solve_info* info, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Batched solves (no counterpart in the paper, which solves one system at a
+ * time with the Jacobi-preconditioned CG of Section 5): several matrices A^s
+ * (one per order s, or per mesh) with many right-hand sides each, solved
+ * together.  The inner iteration is CG on the Jacobi-scaled matrix
+ * Ã = D A D, D = diag(A)^{-1/2}, held as bfloat16 slices, whose product with
+ * the block of search directions runs on the tensor cores; float64 iterative
+ * refinement with the float64 residual B - A U decides convergence.
+ * ------------------------------------------------------------------------ */
+#define FL_BATCH_MAXPROB 8
+
+/*
+ * d = diag(A)^{-1/2} into dscale_dev[n] (float64), and the bfloat16 slices of
+ * Ã_ij = (d_i d_j) a_ij (exactly symmetric): S_0 = bf16(Ã), and for nslices = 2 also
+ * S_1 = bf16(Ã - S_0), each rounded to nearest (ties to even) in one rounding
+ * from float64; magnitudes below 2^-126 become zero.  S_dev holds the slices
+ * one after the other, each n rows of lds elements (slice k at element
+ * offset k*n*lds); lds >= n, a multiple of 8; S_dev 16-byte aligned.
+ * n <= 65536.  Errors: FL_EINVAL, FL_ECUDA.
+ */
+int fl_split_bf16(const double* A_dev, int64_t lda, int64_t n, int nslices, void* S_dev, int64_t lds,
+                  double* dscale_dev, void* stream);
+
+/*
+ * Y = S_0 (X_hi + X_lo) + S_1 X_hi on the tensor cores, where X_hi = bf16(X),
+ * X_lo = bf16(X - X_hi) per entry, operands bfloat16 and float32
+ * accumulation (relative accuracy about 2^-16 of |S||X| with two slices).
+ * X_dev, Y_dev: float32, column j of X at X_dev + j*ldx (n entries), same for Y.
+ * nrhs a multiple of 16 in [16, 128].  The S_dev layout is that of
+ * fl_split_bf16.  Allocates its scratch on `stream` (stream-ordered) and
+ * synchronises it.  Errors: FL_EINVAL, FL_ENOMEM, FL_ECUDA, FL_ETIMEOUT (a
+ * bounded device wait gave up).
+ */
+int fl_matmul_bf16(const void* S_dev, int64_t lds, int64_t n, int nslices, int nrhs, const float* X_dev,
+                   int64_t ldx, float* Y_dev, int64_t ldy, void* stream);
+
+typedef struct fl_batch_problem {
+    int64_t n;                 /* unknowns */
+    const double* A_dev;       /* float64 matrix, n x n, row pitch lda: judges the residual */
+    int64_t lda;
+    const void* S_dev;         /* its bfloat16 slices and scaling from fl_split_bf16 */
+    int64_t lds;
+    int nslices;               /* 1 or 2 */
+    const double* dscale_dev;  /* [n] */
+    int nrhs;                  /* right-hand sides, 1..128 */
+    const double* B_dev;       /* [n][ldb] float64, right-hand side j in column j */
+    int64_t ldb;
+    double* U_dev;             /* [n][ldu] float64 solutions (overwritten; start from 0) */
+    int64_t ldu;
+} fl_batch_problem;
+
+typedef struct fl_batch_opts {
+    double tol;        /* stop column j at ||b_j - A u_j|| <= tol ||b_j|| (default 1e-8) */
+    int max_outer;     /* refinement steps (default 8) */
+    double inner_tol;  /* relative r.r reduction of each inner CG solve (default 1e-5) */
+    int inner_maxit;   /* default 5000 */
+    int ctas;          /* CTAs of the persistent kernel (0: one per SM) */
+    int stages;        /* TMA pipeline depth (0: as many as shared memory holds) */
+} fl_batch_opts;
+
+typedef struct fl_batch_info {
+    int outer_iterations;  /* refinement steps taken */
+    int inner_iterations;  /* CG steps summed over the refinement steps */
+    int status;            /* FL_OK when every column converged */
+    int ctas, stages;      /* launch shape used */
+} fl_batch_info;
+
+void fl_default_batch_opts(fl_batch_opts* o);
+
+/*
+ * Solve A_p U_p = B_p for p < nprob (nprob <= FL_BATCH_MAXPROB), all columns
+ * together: each refinement step computes R = B - A U in float64, then runs one
+ * persistent cooperative kernel that iterates CG on D R for every unfinished
+ * column of every problem at once (per step: one tensor-core product
+ * Ã [P_hi P_lo] per problem, then the vector updates), then U += D Z.
+ * rel_residual_host / status_host (host, optional): per column, problems in
+ * order, the final ||b - A u|| / ||b|| and FL_OK / FL_ENOTCONV / FL_ENOTSPD.
+ * h supplies the workspace (grown on demand) and the error message; the
+ * problems need not belong to h's mesh.  Synchronises `stream`.
+ * Returns FL_OK if every column converged, else the first failing status;
+ * FL_EINVAL, FL_ENOMEM, FL_ECUDA, FL_ETIMEOUT (a bounded device wait gave up),
+ * FL_ENOTIMPL (no cooperative launch).
+ */
+int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const fl_batch_opts* o,
+                   fl_batch_info* info, double* rel_residual_host, int* status_host, void* stream);
+
+/* ------------------------------------------------------------------------
  * Measurement hooks (no counterpart in the paper): plan statistics, per-stage
  * device times of fl_assemble, and a count of kernel launches.
  * ------------------------------------------------------------------------ */

@@ -110,7 +110,7 @@ int fl_create(fl_handle* out, int dim, int64_t n_vertices, const double* vertice
 
 void fl_destroy(fl_handle h) {
     if (!h) return;
-    if (!h->bufs.empty() || h->solve_ws) {
+    if (!h->bufs.empty() || h->solve_ws || h->batch_ws || h->batch_host) {
         cudaSetDevice(h->device);
         cudaDeviceSynchronize();
         for (auto& b : h->bufs) cudaFree(b.p);
@@ -118,6 +118,8 @@ void fl_destroy(fl_handle h) {
             for (int k = 0; k < 2 * FL_NSTAGES; ++k) cudaEventDestroy(h->ev[k]);
         if (h->solve_ws) cudaFree(h->solve_ws);
         if (h->solve_host) cudaFreeHost(h->solve_host);
+        if (h->batch_ws) cudaFree(h->batch_ws);
+        if (h->batch_host) cudaFreeHost(h->batch_host);
     }
     for (auto& g : h->cg_graphs) cudaGraphExecDestroy(g.exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -181,7 +183,7 @@ int fl_get_stats(fl_handle h, double s, fl_stats* st) {
     o.n_far_pairs = all - o.n_touch_pairs - o.n_near_pairs;
     o.nnz_nearfield = (int64_t)P.csr_col.size();
     o.h2d_bytes = h->h2d_bytes;
-    o.workspace_bytes = h->ws_bytes + (int64_t)h->solve_ws_bytes;
+    o.workspace_bytes = h->ws_bytes + (int64_t)h->solve_ws_bytes + (int64_t)h->batch_ws_bytes;
     *st = o;
     return FL_OK;
 }

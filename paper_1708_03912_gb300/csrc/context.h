@@ -104,6 +104,9 @@ struct fl_ctx {
     void* solve_ws = nullptr;     // solver workspace (device), grown on demand
     void* solve_host = nullptr;   // pinned scalars read back by the solver
     size_t solve_ws_bytes = 0;
+    void* batch_ws = nullptr;     // batched-solver workspace (device), grown on demand
+    size_t batch_ws_bytes = 0;
+    void* batch_host = nullptr;   // pinned scalars of the batched solver
 };
 
 namespace fl {

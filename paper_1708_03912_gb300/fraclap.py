@@ -24,8 +24,10 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
 
 EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
            "fl_assemble", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
-           "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_matvec_f32_static"]
+           "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_matvec_f32_static",
+           "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve"]
 FL_STATIC_MAX_N = 65536
+FL_BATCH_MAXPROB = 8
 STAGES = ["prep", "far", "near", "touch", "bnd", "element", "compose"]
 
 
@@ -55,6 +57,23 @@ class fl_stats(ctypes.Structure):
 class fl_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("status", ctypes.c_int)]
+
+
+class fl_batch_problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("A_dev", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("S_dev", ctypes.c_void_p), ("lds", ctypes.c_int64), ("nslices", ctypes.c_int),
+                ("dscale_dev", ctypes.c_void_p), ("nrhs", ctypes.c_int), ("B_dev", ctypes.c_void_p),
+                ("ldb", ctypes.c_int64), ("U_dev", ctypes.c_void_p), ("ldu", ctypes.c_int64)]
+
+
+class fl_batch_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("inner_maxit", ctypes.c_int), ("ctas", ctypes.c_int), ("stages", ctypes.c_int)]
+
+
+class fl_batch_info(ctypes.Structure):
+    _fields_ = [("outer_iterations", ctypes.c_int), ("inner_iterations", ctypes.c_int), ("status", ctypes.c_int),
+                ("ctas", ctypes.c_int), ("stages", ctypes.c_int)]
 
 
 _lib = None
@@ -103,6 +122,15 @@ def lib():
     L.fl_launch_count.restype = ctypes.c_uint64
     L.fl_matvec_f32_static.argtypes = [vp, i64, i64, vp, vp, vp]
     L.fl_matvec_f32_static.restype = ci
+    L.fl_split_bf16.argtypes = [vp, i64, i64, ci, vp, i64, vp, vp]
+    L.fl_split_bf16.restype = ci
+    L.fl_matmul_bf16.argtypes = [vp, i64, i64, ci, ci, vp, i64, vp, i64, vp]
+    L.fl_matmul_bf16.restype = ci
+    L.fl_default_batch_opts.argtypes = [ctypes.POINTER(fl_batch_opts)]
+    L.fl_default_batch_opts.restype = None
+    L.fl_batch_solve.argtypes = [vp, ci, ctypes.POINTER(fl_batch_problem), ctypes.POINTER(fl_batch_opts),
+                                 ctypes.POINTER(fl_batch_info), vp, vp, vp]
+    L.fl_batch_solve.restype = ci
     _ = i32
     _lib = L
     return L
@@ -228,6 +256,49 @@ def fl_matvec_f32_static(A32, x, y, stream=None):
     """y = A32 x without any device allocation (for callers that cannot allocate);
     n <= FL_STATIC_MAX_N.  Returns the status code (0 = FL_OK) instead of raising."""
     return lib().fl_matvec_f32_static(_ptr(A32), A32.stride(0), A32.shape[0], _ptr(x), _ptr(y), _stream(stream))
+
+
+def fl_split_bf16(A, nslices, S, dscale, stream=None):
+    """A: float64 [n, lda]; S: bf16 CUDA tensor [nslices * n, lds] (slices stacked by rows);
+    dscale: float64 [n]."""
+    n = A.shape[0]
+    _check(lib().fl_split_bf16(_ptr(A), A.stride(0), n, nslices, _ptr(S), S.stride(0), _ptr(dscale),
+                               _stream(stream)))
+
+
+def fl_matmul_bf16(S, n, nslices, X, Y, stream=None):
+    """S from fl_split_bf16; X, Y: float32 CUDA tensors [nrhs, n] (one right-hand side per row)."""
+    _check(lib().fl_matmul_bf16(_ptr(S), S.stride(0), n, nslices, X.shape[0], _ptr(X), X.stride(0), _ptr(Y),
+                                Y.stride(0), _stream(stream)))
+
+
+def fl_default_batch_opts():
+    o = fl_batch_opts()
+    lib().fl_default_batch_opts(ctypes.byref(o))
+    return o
+
+
+def fl_batch_solve(h, problems, opts=None, stream=None):
+    """problems: list of dicts with keys A (float64 [n, n]), S, nslices, dscale, B (float64 [n, nrhs]),
+    U (float64 [n, nrhs], overwritten).  Returns (status, fl_batch_info, rel_residuals, statuses);
+    raises on FL_EINVAL / FL_ENOMEM / FL_ECUDA / FL_ETIMEOUT / FL_ENOTIMPL."""
+    arr = (fl_batch_problem * len(problems))()
+    total = 0
+    for k, q in enumerate(problems):
+        A, S, B, U = q["A"], q["S"], q["B"], q["U"]
+        arr[k] = fl_batch_problem(A.shape[0], A.data_ptr(), A.stride(0), S.data_ptr(), S.stride(0), q["nslices"],
+                                  q["dscale"].data_ptr(), B.shape[1], B.data_ptr(), B.stride(0), U.data_ptr(),
+                                  U.stride(0))
+        total += B.shape[1]
+    o = opts if opts is not None else fl_default_batch_opts()
+    info = fl_batch_info()
+    rel = np.zeros(total, dtype=np.float64)
+    st = np.zeros(total, dtype=np.int32)
+    r = lib().fl_batch_solve(h, len(problems), arr, ctypes.byref(o), ctypes.byref(info), rel.ctypes.data,
+                             st.ctypes.data, _stream(stream))
+    if r not in (FL_OK, FL_ENOTCONV, FL_ENOTSPD):
+        _check(r, h)
+    return r, info, rel, st
 
 
 # ------------------------------------------------------------- convenience --
