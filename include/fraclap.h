@@ -185,6 +185,8 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
  * refinement with the float64 residual B - A U decides convergence.
  * ------------------------------------------------------------------------ */
 #define FL_BATCH_MAXPROB 8
+#define FL_RESID_F64 0
+#define FL_RESID_DF  1
 
 /*
  * d = diag(A)^{-1/2} into dscale_dev[n] (float64), and the bfloat16 slices of
@@ -233,6 +235,8 @@ typedef struct fl_batch_opts {
     int inner_maxit;   /* default 5000 */
     int ctas;          /* CTAs of the persistent kernel (0: one per SM) */
     int stages;        /* TMA pipeline depth (0: as many as shared memory holds) */
+    int residual;      /* FL_RESID_DF (default): B - A U in double-float arithmetic on the float32
+                          pipe (about 2^-48 relative per operation); FL_RESID_F64: float64 FMA */
 } fl_batch_opts;
 
 typedef struct fl_batch_info {

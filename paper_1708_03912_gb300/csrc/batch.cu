@@ -643,6 +643,191 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(const __grid_cons
     }
 }
 
+// ------------------------------------------------- double-float residual --
+// R = B - A U with A and U in float64, evaluated on the float32 pipe in
+// double-float arithmetic: every float64 operand is split into hi + lo float32
+// parts (hi = fl32(x), lo = fl32(x - hi)), the product a_hi u_hi is formed
+// exactly (hi part by a float32 multiply, its rounding error by an FMA), the
+// cross terms a_hi u_lo + a_lo u_hi are added to it in float32, and the running
+// sum is kept as an unevaluated pair (s_hi, s_lo) updated with the error-free
+// two-sum.  Relative accuracy of each product and addition is about 2^-48.
+// Work items are (column tile, 128-row block, 32-wide K chunk); contiguous ranges
+// of them go to the CTAs (balanced to one chunk; never more CTAs than items, so no
+// range is empty), and every CTA writes one partial (s_hi, s_lo) tile per row
+// block it touched.
+constexpr int DF_ROWS = 128, DF_COLS = 64, DF_K = 32, DF_THREADS = 256;
+constexpr size_t DF_SMEM = (size_t)DF_K * (DF_ROWS + 1) * sizeof(float2) + (size_t)DF_K * DF_COLS * sizeof(float2);
+
+struct DfProb {
+    int n, nrhs, nrp, rblocks, kch, ctiles;
+    const double* A;
+    int64_t lda;
+    const double* U;
+    int64_t ldu;
+};
+struct DfParams {
+    DfProb prob[MAXP];
+    int na, rmax;
+    int act[MAXP];
+    long long ubase[MAXP + 1], tbase[MAXP + 1];
+    float2* slots;  // [G][rmax][DF_COLS][DF_ROWS]
+    int* err;
+};
+
+struct DfUnit {
+    int k, p, ct, rb, kc;
+};
+__device__ __forceinline__ DfUnit df_decode(const DfParams& D, long long g) {
+    int k = 0;
+    while (k + 1 < D.na && g >= D.ubase[k + 1]) ++k;
+    const int p = D.act[k];
+    const DfProb& pr = D.prob[p];
+    long long l = g - D.ubase[k];
+    const int kc = (int)(l % pr.kch);
+    l /= pr.kch;
+    return {k, p, (int)(l / pr.rblocks), (int)(l % pr.rblocks), kc};
+}
+__device__ __forceinline__ long long df_tile(const DfParams& D, long long g) {
+    const DfUnit u = df_decode(D, g);
+    return D.tbase[u.k] + (long long)u.ct * D.prob[u.p].rblocks + u.rb;
+}
+
+__device__ __forceinline__ void df_split(double x, float2& v) {
+    const float hi = __double2float_rn(x);
+    v = make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
+// (sh, sl) += (ah + al)(uh + ul), dropping al ul
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al, float uh, float ul) {
+    const float p = __fmul_rn(ah, uh);
+    const float e = __fmaf_rn(ah, uh, -p);
+    const float l = __fmaf_rn(ah, ul, __fmaf_rn(al, uh, e));
+    const float t = __fadd_rn(sh, p);
+    const float z = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, l));
+}
+
+__global__ void __launch_bounds__(DF_THREADS, 2) residual_df_kernel(const __grid_constant__ DfParams D) {
+    extern __shared__ float2 df_smem[];
+    float2(*As)[DF_ROWS + 1] = reinterpret_cast<float2(*)[DF_ROWS + 1]>(df_smem);
+    float2(*Us)[DF_COLS] = reinterpret_cast<float2(*)[DF_COLS]>(df_smem + DF_K * (DF_ROWS + 1));
+    const int b = blockIdx.x, G = gridDim.x;
+    const long long Utot = D.ubase[D.na];
+    const long long u0 = range_start(Utot, G, b), u1 = range_start(Utot, G, b + 1);
+    const int t = threadIdx.x, rg = t & 15, cg = t >> 4;
+    float sh[8][4], sl[8][4];
+    int r = 0;
+    for (long long g = u0; g < u1; ++g) {
+        const DfUnit u = df_decode(D, g);
+        const DfProb& pr = D.prob[u.p];
+        if (g == u0 || u.kc == 0) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
+        }
+        const int r0 = u.rb * DF_ROWS, k0 = u.kc * DF_K, c0 = u.ct * DF_COLS;
+        for (int e = t; e < DF_ROWS * DF_K; e += DF_THREADS) {
+            const int row = e >> 5, kk = e & 31;
+            const int i = r0 + row, kcol = k0 + kk;
+            df_split((i < pr.n && kcol < pr.n) ? pr.A[(int64_t)i * pr.lda + kcol] : 0.0, As[kk][row]);
+        }
+        for (int e = t; e < DF_K * DF_COLS; e += DF_THREADS) {
+            const int kk = e >> 6, c = e & 63;
+            const int krow = k0 + kk, col = c0 + c;
+            df_split((krow < pr.n && col < pr.nrhs) ? pr.U[(int64_t)krow * pr.ldu + col] : 0.0, Us[kk][c]);
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int kk = 0; kk < DF_K; ++kk) {
+            float2 a[8], v[4];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = As[kk][rg + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = Us[kk][cg + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) df_fma(sh[i][j], sl[i][j], a[i].x, a[i].y, v[j].x, v[j].y);
+        }
+        __syncthreads();
+        if (g == u1 - 1 || u.kc == pr.kch - 1) {
+            if (r < D.rmax) {
+                float2* slot = D.slots + (size_t)(b * D.rmax + r) * DF_COLS * DF_ROWS;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        slot[(cg + 16 * j) * DF_ROWS + rg + 16 * i] = make_float2(sh[i][j], sl[i][j]);
+            } else if (t == 0) {
+                atomicOr(D.err, 2);
+            }
+            ++r;
+        }
+    }
+}
+
+// Sum the partial tiles of each (problem, column tile, row block) in a fixed order:
+// R = B - sum (float64), and the column sums of R^2 per 16-row block.
+// Block (row block, column tile, active problem index).
+__global__ void __launch_bounds__(256) residual_df_reduce_kernel(const __grid_constant__ DfParams D,
+                                                                 const __grid_constant__ RefParams RP, int G) {
+    const int k = blockIdx.z;
+    if (k >= D.na) return;
+    const int p = D.act[k];
+    const DfProb& pr = D.prob[p];
+    const RefProb& rp = RP.prob[p];
+    const int rb = blockIdx.x, ct = blockIdx.y;
+    if (rb >= pr.rblocks || ct >= pr.ctiles) return;
+    __shared__ double Rs[DF_ROWS][DF_COLS / 2 + 1];
+    __shared__ int own[3];
+    const long long Utot = D.ubase[D.na];
+    if (threadIdx.x == 0) {
+        const long long g0 = D.ubase[k] + ((long long)ct * pr.rblocks + rb) * pr.kch, g1 = g0 + pr.kch - 1;
+        const int bf = owner(g0, Utot, G), bl = owner(g1, Utot, G);
+        own[0] = bf;
+        own[1] = bl - bf + 1;
+        own[2] = (int)(df_tile(D, g0) - df_tile(D, range_start(Utot, G, bf)));
+    }
+    __syncthreads();
+    constexpr int HC = DF_COLS / 2;  // columns per half
+    const int row = threadIdx.x & 127, sub = threadIdx.x >> 7;
+    const int i = rb * DF_ROWS + row;
+    for (int half = 0; half < 2; ++half) {
+        for (int cc = sub; cc < HC; cc += 2) {
+            const int c = half * HC + cc;
+            double sum = 0.0;
+            for (int o = 0; o < own[1]; ++o) {
+                const int sl = (o == 0) ? (own[0] * D.rmax + own[2]) : ((own[0] + o) * D.rmax);
+                const float2 v = D.slots[((size_t)sl * DF_COLS + c) * DF_ROWS + row];
+                sum += (double)v.x + (double)v.y;
+            }
+            const int col = ct * DF_COLS + c;
+            double rv = 0.0;
+            if (i < pr.n && col < pr.nrhs) rv = rp.B[(int64_t)i * rp.ldb + col] - sum;
+            Rs[row][cc] = rv;
+        }
+        __syncthreads();
+        // coalesced row-major store of R, then per 16-row block column sums of squares
+        for (int e = threadIdx.x; e < DF_ROWS * HC; e += blockDim.x) {
+            const int rr = e / HC, c = e % HC;
+            const int ii = rb * DF_ROWS + rr, col = ct * DF_COLS + half * HC + c;
+            if (ii < pr.n && col < pr.nrp) rp.R[(int64_t)ii * pr.nrp + col] = Rs[rr][c];
+        }
+        for (int e = threadIdx.x; e < (DF_ROWS / RES_ROWS) * HC; e += blockDim.x) {
+            const int sb = e / HC, c = e % HC;
+            const int col = ct * DF_COLS + half * HC + c, blk = rb * (DF_ROWS / RES_ROWS) + sb;
+            if (col >= pr.nrp || blk * RES_ROWS >= pr.n) continue;
+            double ss = 0.0;
+            for (int rr = 0; rr < RES_ROWS; ++rr) ss += Rs[sb * RES_ROWS + rr][c] * Rs[sb * RES_ROWS + rr][c];
+            rp.rpart[(int64_t)blk * pr.nrp + col] = ss;
+        }
+        __syncthreads();
+    }
+}
+
 // Per column: relative residual, convergence, and the start of the next inner solve
 // (r = D R_j in float32, z = 0, p = r, P = split(p)).  Block (j, problem).
 __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ RefParams RP,
@@ -944,6 +1129,7 @@ void fl_default_batch_opts(fl_batch_opts* o) {
     o->inner_maxit = 5000;
     o->ctas = 0;
     o->stages = 0;
+    o->residual = FL_RESID_DF;
 }
 
 int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const fl_batch_opts* o_in,
@@ -954,7 +1140,8 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
     fl_batch_opts o;
     fl_default_batch_opts(&o);
     if (o_in) o = *o_in;
-    if (!(o.tol > 0) || !(o.inner_tol > 0) || o.max_outer < 1 || o.inner_maxit < 1)
+    if (!(o.tol > 0) || !(o.inner_tol > 0) || o.max_outer < 1 || o.inner_maxit < 1 ||
+        (o.residual != FL_RESID_F64 && o.residual != FL_RESID_DF))
         return set_err(h, FL_EINVAL, "bad batch options");
     for (int p = 0; p < nprob; ++p) {
         const fl_batch_problem& q = probs[p];
@@ -1012,6 +1199,30 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
     }
     const size_t off_slots = take((size_t)g.G * g.rmax * g.nrmax * BM * sizeof(float));
     const size_t off_flags = take(256);
+    // double-float residual: grid, run bound and partial tiles
+    int df_G = 0, df_rmax = 0;
+    size_t off_df = 0;
+    if (o.residual == FL_RESID_DF) {
+        int occ = 0;
+        if (cudaFuncSetAttribute((const void*)residual_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)DF_SMEM) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)residual_df_kernel, DF_THREADS,
+                                                          DF_SMEM) != cudaSuccess ||
+            occ < 1) {
+            cudaGetLastError();
+            return set_err(h, FL_ECUDA, "double-float residual kernel does not fit on an SM");
+        }
+        df_G = sms * std::min(occ, 2);
+        long long Uall = 0;
+        int kmin = 1 << 30;
+        for (const ProbDev& d : pd) {
+            const int kch = (d.n + DF_K - 1) / DF_K;
+            Uall += (long long)((d.nr + DF_COLS - 1) / DF_COLS) * ((d.n + DF_ROWS - 1) / DF_ROWS) * kch;
+            kmin = std::min(kmin, kch);
+        }
+        df_rmax = (int)(((Uall + df_G - 1) / df_G + kmin - 1) / kmin) + 2;
+        off_df = take((size_t)df_G * df_rmax * DF_COLS * DF_ROWS * sizeof(float2));
+    }
     if (total > h->batch_ws_bytes) {
         if (h->batch_ws) cudaFree(h->batch_ws);
         h->batch_ws = nullptr;
@@ -1098,19 +1309,62 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
     int total_rhs = 0;
     for (int p = 0; p < nprob; ++p) total_rhs += probs[p].nrhs;
     int* hs = (int*)h->batch_host;
+    memset(hs, 0, 256);
     int outer = 0, inner_total = 0;
     bool all_done = false;
     for (int pass = 0; pass <= o.max_outer; ++pass) {
         const bool last = (pass == o.max_outer);
-        residual_kernel<<<dim3((nmax + RES_ROWS - 1) / RES_ROWS, (nrmax + RES_COLS - 1) / RES_COLS, nprob),
-                          RES_THREADS, 0, st>>>(RP, pass == 0 ? 1 : 0);
-        fl::count_launch();
+        if (pass == 0 || o.residual == FL_RESID_F64) {
+            residual_kernel<<<dim3((nmax + RES_ROWS - 1) / RES_ROWS, (nrmax + RES_COLS - 1) / RES_COLS, nprob),
+                              RES_THREADS, 0, st>>>(RP, pass == 0 ? 1 : 0);
+            fl::count_launch();
+        } else {
+            DfParams D;
+            memset(&D, 0, sizeof(D));
+            long long u = 0, tt = 0;
+            int rbmax = 0, ctmax = 0;
+            for (int p = 0; p < nprob; ++p) {
+                DfProb& q = D.prob[p];
+                q.n = pd[p].n;
+                q.nrhs = probs[p].nrhs;
+                q.nrp = pd[p].nr;
+                q.rblocks = (q.n + DF_ROWS - 1) / DF_ROWS;
+                q.kch = (q.n + DF_K - 1) / DF_K;
+                q.ctiles = (q.nrp + DF_COLS - 1) / DF_COLS;
+                q.A = probs[p].A_dev;
+                q.lda = probs[p].lda;
+                q.U = probs[p].U_dev;
+                q.ldu = probs[p].ldu;
+                if (hs[16 + p] >= probs[p].nrhs) continue;  // every column finished
+                D.act[D.na] = p;
+                D.ubase[D.na] = u;
+                D.tbase[D.na] = tt;
+                u += (long long)q.ctiles * q.rblocks * q.kch;
+                tt += (long long)q.ctiles * q.rblocks;
+                rbmax = std::max(rbmax, q.rblocks);
+                ctmax = std::max(ctmax, q.ctiles);
+                ++D.na;
+            }
+            D.ubase[D.na] = u;
+            D.tbase[D.na] = tt;
+            D.rmax = df_rmax;
+            D.slots = (float2*)(W + off_df);
+            D.err = flags;
+            if (D.na > 0) {
+                // at most one CTA per work item, so that every CTA's range is non-empty and
+                // the CTAs covering a row block are consecutive
+                const int G = (int)std::min<long long>(df_G, u);
+                residual_df_kernel<<<G, DF_THREADS, DF_SMEM, st>>>(D);
+                residual_df_reduce_kernel<<<dim3(rbmax, ctmax, D.na), 256, 0, st>>>(D, RP, G);
+                fl::count_launch(2);
+            }
+        }
         if (cudaMemsetAsync(P.ndone, 0, MAXP * sizeof(int), st) != cudaSuccess)
             return set_err(h, FL_ECUDA, "memset");
         prep_kernel<<<dim3(nrmax, nprob), 256, 0, st>>>(RP, P, pass == 0 ? 1 : 0, o.tol, last ? 1 : 0, flags + 1);
         fl::count_launch();
         if (cudaGetLastError() != cudaSuccess) return set_err(h, FL_ECUDA, "refinement kernels");
-        if (cudaMemcpyAsync(hs, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        if (cudaMemcpyAsync(hs, flags, 256, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return set_err(h, FL_ECUDA, "batch scalars");
         if (hs[1] >= total_rhs) {
@@ -1129,7 +1383,7 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
         update_kernel<<<dim3(nrmax, nprob), 256, 0, st>>>(RP, P);
         fl::count_launch();
         ++outer;
-        if (cudaMemcpyAsync(hs, flags, 5 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        if (cudaMemcpyAsync(hs, flags, 256, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return set_err(h, FL_ECUDA, "batch scalars");
         inner_total += hs[4];

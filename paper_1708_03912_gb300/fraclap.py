@@ -28,6 +28,7 @@ EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl
            "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve"]
 FL_STATIC_MAX_N = 65536
 FL_BATCH_MAXPROB = 8
+FL_RESID_F64, FL_RESID_DF = 0, 1
 STAGES = ["prep", "far", "near", "touch", "bnd", "element", "compose"]
 
 
@@ -68,7 +69,8 @@ class fl_batch_problem(ctypes.Structure):
 
 class fl_batch_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("inner_maxit", ctypes.c_int), ("ctas", ctypes.c_int), ("stages", ctypes.c_int)]
+                ("inner_maxit", ctypes.c_int), ("ctas", ctypes.c_int), ("stages", ctypes.c_int),
+                ("residual", ctypes.c_int)]
 
 
 class fl_batch_info(ctypes.Structure):

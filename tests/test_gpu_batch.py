@@ -169,3 +169,30 @@ def test_batched_solve_rejects_bad_input():
         F.fl_matmul_bf16(q["S"], A.shape[0], 2, torch.zeros((20, A.shape[0]), device="cuda"),
                          torch.zeros((20, A.shape[0]), device="cuda"))
     F.fl_destroy(h)
+
+
+@pytest.mark.parametrize("mode", ["df", "f64"])
+def test_reported_residual_matches_float64(disc10, mode):
+    # the residual that decides convergence (double-float or float64 FMA) agrees with a
+    # float64 recomputation of B - A U on the host
+    V, T, A = disc10
+    rng = np.random.default_rng(2)
+    B = rng.standard_normal((A.shape[0], 70))  # two column tiles of the residual
+    q = _problem(A, B, 2)
+    o = F.fl_default_batch_opts()
+    o.tol = 1e-10
+    o.residual = F.FL_RESID_DF if mode == "df" else F.FL_RESID_F64
+    h = F.fl_create(V, T)
+    r, info, rel, st = F.fl_batch_solve(h, [q], o)
+    F.fl_destroy(h)
+    assert r == F.FL_OK
+    U = q["U"].cpu().numpy()
+    nb = np.linalg.norm(B, axis=0)
+    rel_host = np.linalg.norm(B - A @ U, axis=0) / nb
+    assert np.all(rel <= 1e-10)
+    # operands carried to 2^-48 (double-float) or 2^-53 (float64): the residual of column j
+    # is exact to about 2^-46 || |A| |u_j| || (random right-hand sides make |A||u| >> |b|)
+    floor = 2.0 ** -46 * np.linalg.norm(np.abs(A) @ np.abs(U), axis=0) / nb
+    dev = np.abs(rel - rel_host)
+    print(f"{mode}: max |rel - rel_host| = {dev.max():.2e}, max floor {floor.max():.2e}")
+    assert np.all(dev <= 1e-3 * rel_host + floor)
