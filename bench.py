@@ -30,6 +30,8 @@ WORKLOAD = {"workload": "disc-quasi-uniform-25-rings", "domain": "unit disc", "r
             "dofs": 1887, "s": 0.75, "f": "1", "dtype_assembly": "f32 separated pairs + f64 near/boundary",
             "solve": "f64-refined Jacobi-PCG on f32 copy to 1e-8", "l2": "flushed between timed steps (512 MiB write)"}
 METRIC = "element pairs/s assembled; matvec HBM GB/s; solve time to 1e-8 vs plain FP64"
+# the batched workload: 4 orders x 64 loads on the disc graded toward the boundary
+BATCH = {"rings": 30, "mu": 2.0, "s": [0.25, 0.5, 0.75, 0.9], "nrhs": 64}
 # DRAM bytes (read 1.433 MB + write 2.119 MB) per launch of far_tile_kernel<2,float,16,0> on this
 # workload, from one ncu capture of the current kernel; reset to None whenever that kernel changes.
 FAR_KERNEL_DRAM_BYTES = 3.552e6
@@ -275,6 +277,52 @@ def main():
     _, inf64 = m.solve(A, b, tol=1e-8)
     _, infmx = m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3)
 
+    # ---- batched: 4 orders x 64 right-hand sides on the graded disc (n = 8195) ----
+    from paper_1708_03912_gb300.profile_batch import build_problems
+
+    Vg, Tg = synth.disc(BATCH["rings"], BATCH["mu"])
+    mg = F.Mesh(Vg, Tg)
+    probs = build_problems(mg, BATCH["s"], BATCH["nrhs"], 2, Vg)
+    ob = F.fl_default_batch_opts()
+    ob.inner_tol = 1e-4
+    binfo = {}
+
+    def batched():
+        r_, inf_, rel_, st_ = F.fl_batch_solve(mg.h, probs, ob)
+        binfo.update(status=int(r_), outer=inf_.outer_iterations, inner=inf_.inner_iterations,
+                     max_rel=float(rel_.max()), ctas=inf_.ctas, stages=inf_.stages)
+
+    batched()
+    batch_ms = timed(batched, reps=3)
+    # plain float64 Jacobi-PCG on the same systems: f = 1 and the first Gaussian load for every s,
+    # the per-column mean extrapolated to all columns
+    plain_cols = []
+    for q in probs:
+        for j in (0, 1):
+            bj = q["B"][:, j].contiguous()
+            mg.solve(q["A"], bj)
+            plain_cols.append(timed(lambda: mg.solve(q["A"], bj), reps=1, flush_between=True))
+    plain_total = statistics.mean(plain_cols) * BATCH["nrhs"] * len(BATCH["s"])
+    # the tensor-core product alone: S (two bf16 slices of A^{3/4}) times 64 columns
+    nbg = probs[2]["A"].shape[0]
+    Xg = torch.randn(BATCH["nrhs"], nbg, dtype=torch.float32, device=dev)
+    Yg = torch.empty_like(Xg)
+    gemm_ms = timed(lambda: F.fl_matmul_bf16(probs[2]["S"], nbg, 2, Xg, Yg), reps=5)
+    gemm_bytes = 2 * nbg * nbg * 2
+    batch_line = {
+        "workload": f"graded disc {BATCH['rings']} rings mu {BATCH['mu']}, n = {nbg}, s = {BATCH['s']}, "
+                    f"{BATCH['nrhs']} right-hand sides (f = 1 and seeded Gaussian nodal loads)",
+        "ms_to_1e-8": batch_ms, "systems": BATCH["nrhs"] * len(BATCH["s"]),
+        "plain_f64_ms_extrapolated": plain_total,
+        "plain_f64_note": "mean of 2 timed single-column float64 Jacobi-PCG solves per s, times 64 columns",
+        "speedup_vs_plain_f64": plain_total / batch_ms, **binfo,
+        "tc_gemm": {"ms": gemm_ms, "gbs": gemm_bytes / (gemm_ms / 1000) / 1e9,
+                    "tflops": 2 * 3 * nbg * nbg * BATCH["nrhs"] / (gemm_ms / 1000) / 1e12,
+                    "note": "fl_matmul_bf16, 2 slices x 64 columns (3 bf16 products), bytes = slices read once"},
+    }
+    del probs
+    mg.close()
+
     # ---- end to end through the public API with host buffers ----
     def e2e_step():
         mm = F.Mesh(V, T)
@@ -322,6 +370,7 @@ def main():
                    "note": "bytes of A per product / device time; L2 flushed; f32 through fl_matvec_f32_static"},
         "solve_ms_to_1e-8": {"f32_refined": sol_mixed, "plain_f64": sol_fp64, "iters_f64": inf64.iterations,
                              "iters_refined": infmx.iterations, "outer": infmx.outer_iterations},
+        "batched": batch_line,
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": {"value": n_el * n_el / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -189,36 +189,45 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
 #define FL_RESID_DF  1
 
 /*
+ * Bytes of the slice storage fl_split_bf16 writes for order n and nslices slices:
+ * nslices * ceil(n/128) * ceil(n/64) * 16384 (0 for invalid arguments).
+ */
+int64_t fl_split_bf16_bytes(int64_t n, int nslices);
+
+/*
  * d = diag(A)^{-1/2} into dscale_dev[n] (float64), and the bfloat16 slices of
  * Ã_ij = (d_i d_j) a_ij (exactly symmetric): S_0 = bf16(Ã), and for nslices = 2 also
  * S_1 = bf16(Ã - S_0), each rounded to nearest (ties to even) in one rounding
- * from float64; magnitudes below 2^-126 become zero.  S_dev holds the slices
- * one after the other, each n rows of lds elements (slice k at element
- * offset k*n*lds); lds >= n, a multiple of 8; S_dev 16-byte aligned.
+ * from float64; magnitudes below 2^-126 become zero.
+ * Layout of S_dev (fl_split_bf16_bytes(n, nslices) bytes, 16-byte aligned): the
+ * tiles the tensor cores read, one contiguous 16 KiB block per (slice k, row
+ * tile t < ceil(n/128), column chunk c < ceil(n/64)) at byte offset
+ * ((k ceil(n/128) + t) ceil(n/64) + c) 16384; inside a block, entry
+ * (row r < 128, column q < 64) is at byte r 128 + 16 ((q/8) XOR (r mod 8))
+ * + 2 (q mod 8) (the 128-byte swizzle); entries outside n x n are zero.
  * n <= 65536.  Errors: FL_EINVAL, FL_ECUDA.
  */
-int fl_split_bf16(const double* A_dev, int64_t lda, int64_t n, int nslices, void* S_dev, int64_t lds,
-                  double* dscale_dev, void* stream);
+int fl_split_bf16(const double* A_dev, int64_t lda, int64_t n, int nslices, void* S_dev, double* dscale_dev,
+                  void* stream);
 
 /*
  * Y = S_0 (X_hi + X_lo) + S_1 X_hi on the tensor cores, where X_hi = bf16(X),
  * X_lo = bf16(X - X_hi) per entry, operands bfloat16 and float32
  * accumulation (relative accuracy about 2^-16 of |S||X| with two slices).
  * X_dev, Y_dev: float32, column j of X at X_dev + j*ldx (n entries), same for Y.
- * nrhs a multiple of 16 in [16, 128].  The S_dev layout is that of
- * fl_split_bf16.  Allocates its scratch on `stream` (stream-ordered) and
- * synchronises it.  Errors: FL_EINVAL, FL_ENOMEM, FL_ECUDA, FL_ETIMEOUT (a
- * bounded device wait gave up).
+ * nrhs a multiple of 16 in [16, 128].  S_dev as written by fl_split_bf16.
+ * Allocates its scratch on `stream` (stream-ordered) and synchronises it.
+ * Errors: FL_EINVAL, FL_ENOMEM, FL_ECUDA, FL_ETIMEOUT (a bounded device wait
+ * gave up).
  */
-int fl_matmul_bf16(const void* S_dev, int64_t lds, int64_t n, int nslices, int nrhs, const float* X_dev,
-                   int64_t ldx, float* Y_dev, int64_t ldy, void* stream);
+int fl_matmul_bf16(const void* S_dev, int64_t n, int nslices, int nrhs, const float* X_dev, int64_t ldx,
+                   float* Y_dev, int64_t ldy, void* stream);
 
 typedef struct fl_batch_problem {
     int64_t n;                 /* unknowns */
     const double* A_dev;       /* float64 matrix, n x n, row pitch lda: judges the residual */
     int64_t lda;
     const void* S_dev;         /* its bfloat16 slices and scaling from fl_split_bf16 */
-    int64_t lds;
     int nslices;               /* 1 or 2 */
     const double* dscale_dev;  /* [n] */
     int nrhs;                  /* right-hand sides, 1..128 */
@@ -236,7 +245,9 @@ typedef struct fl_batch_opts {
     int ctas;          /* CTAs of the persistent kernel (0: one per SM) */
     int stages;        /* TMA pipeline depth (0: as many as shared memory holds) */
     int residual;      /* FL_RESID_DF (default): B - A U in double-float arithmetic on the float32
-                          pipe (about 2^-48 relative per operation); FL_RESID_F64: float64 FMA */
+                          pipe (about 2^-47 relative per operand and operation, so each residual
+                          entry is exact to about 2^-46 (|A||u|)_i); FL_RESID_F64: float64 FMA,
+                          for tolerances near or below 2^-46 || |A||u| || / ||b|| */
 } fl_batch_opts;
 
 typedef struct fl_batch_info {

@@ -16,10 +16,8 @@
 // S_0 (p_hi + p_lo) + S_1 p_hi with float32 accumulation, relative accuracy about
 // 2^-16 with two slices and 2^-8 with one.  The refinement residual and the
 // solution update are float64.
-#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
-#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -41,11 +39,12 @@ constexpr int THREADS = 256;       // warp 0: TMA producer, warp 1: MMA issuer, 
 constexpr int MAXP = FL_BATCH_MAXPROB;
 constexpr int A_TILE = BM * BK * 2;  // bytes of one matrix tile (16 KiB)
 constexpr int MAX_STAGES = 8;
-constexpr int MAX_TILES = 512;     // n <= 65536
 constexpr int UMIN = 8;            // fewest chunks a CTA takes in a GEMM phase
 
 struct ColState {
-    double rr, rr0;  // current and initial r.r of the inner iteration
+    double gam[2], alp[2];  // gamma = r.r and alpha of the step of even / odd parity (a step reads
+                            // the previous step's pair and writes its own)
+    double rr0;             // r.r at the start of the inner solve
     int done, its, status, pad;
 };
 struct ColOuter {
@@ -53,25 +52,38 @@ struct ColOuter {
     int odone, status;
 };
 
+// Operand tiles in global memory are stored exactly as the MMA reads them from
+// shared memory: 128-byte rows (64 bf16 along K) with the 128-byte swizzle (the
+// 16-byte unit u of row r sits at unit position u XOR (r mod 8)), so that one
+// contiguous bulk copy moves a whole tile.  Byte offset of element (r, q):
+__host__ __device__ constexpr uint32_t sw128(uint32_t r, uint32_t q) {
+    return r * 128u + ((((q >> 3) ^ (r & 7u)) << 4)) + (q & 7u) * 2u;
+}
+
 struct ProbDev {
     int n, nr, nslices, mtiles, chunks, ldv;
-    float *r, *z, *p, *q;  // [nr][ldv]
-    __nv_bfloat16* P;      // [2 nr][ldv]: p_hi rows then p_lo rows (TMA source)
+    const uint8_t* S;      // slices: [nslices][mtiles][chunks] tiles of 128 x 64 (16 KiB)
+    float *r, *z, *p, *q, *sv;  // [nr][ldv]: residual, solution, direction, w = Ã r, s = Ã p
+    __nv_bfloat16* P;      // [2 mtiles] tiles of 2 nr x 64: p_hi rows then p_lo rows (the GEMM reads
+                           // the first `chunks`; the vector phases write all mtiles * 128 rows)
     ColState* col;         // [nr]
+    float *pq, *rq;        // [nr][ngroups] partial r.w and r.r per group of VT row tiles
+    int ngroups;
 };
 
 struct Params {
-    CUtensorMap tmA[MAXP][2];  // bf16 slices S_0, S_1 (box 64 x 128)
-    CUtensorMap tmP[MAXP];     // P (box 64 x 2 nr)
     ProbDev prob[MAXP];
     int nprob, stages, rmax, nrmax, maxit, tmem_cols, nsmax;
+    int nacc;  // independent TMEM accumulators the K steps of a chunk rotate over (1, 2 or 4)
     double tol2;
     float* slots;    // [G][rmax][nrmax][128] per-run partial products
-    unsigned* gbar;  // grid barrier state (2 words)
+    unsigned* gbar;  // grid barrier arrival counter (own cache line, zero at launch)
     int* err;        // bit 0: mbarrier timeout, 1: run-slot overflow, 2: grid barrier timeout
     int* ndone;      // [MAXP] finished columns per problem
     int* active;     // [MAXP] (GEMM-only launches): problem takes part
     int* iters;      // CG steps taken by the last persistent launch
+    int4* owners;    // per row tile (ordinal over the active problems) of the current GEMM phase:
+                     // x = first CTA, y = its run index for the tile, z = last CTA
 };
 
 struct Ctl {
@@ -83,7 +95,7 @@ struct Ctl {
     long long ubase[MAXP + 1];
     int tbase[MAXP + 1];
     long long U;
-    int own_first[MAX_TILES], own_r[MAX_TILES], own_cnt[MAX_TILES];
+    long long vbase[MAXP + 1];  // vector work items (column, group of row tiles) per active problem
     double red[THREADS / 32];
     int flag;
 };
@@ -107,10 +119,6 @@ __device__ __forceinline__ int owner(long long g, long long U, int G) {
     while (b > 0 && range_start(U, G, b) > g) --b;
     return b;
 }
-__device__ __forceinline__ long long tile_ordinal(const Ctl& s, const Params& P, long long g) {
-    const Unit u = decode(s, P, g);
-    return s.tbase[u.k] + u.t;
-}
 
 // Active problems of this phase, the unit (chunk) numbering over them and the
 // number of CTAs that take part in the GEMM.  Run by every CTA on data that no
@@ -118,19 +126,22 @@ __device__ __forceinline__ long long tile_ordinal(const Ctl& s, const Params& P,
 __device__ void plan_phase(Ctl& s, const Params& P, int G, bool cg_mode) {
     if (threadIdx.x == 0) {
         int na = 0, tt = 0;
-        long long u = 0;
+        long long u = 0, vi = 0;
         for (int p = 0; p < P.nprob; ++p) {
             const bool on = cg_mode ? (__ldcg(P.ndone + p) < P.prob[p].nr) : (__ldcg(P.active + p) != 0);
             if (!on) continue;
             s.act[na] = p;
             s.ubase[na] = u;
             s.tbase[na] = tt;
+            s.vbase[na] = vi;
             u += (long long)P.prob[p].mtiles * P.prob[p].chunks;
             tt += P.prob[p].mtiles;
+            vi += (long long)P.prob[p].nr * P.prob[p].ngroups;
             ++na;
         }
         s.ubase[na] = u;
         s.tbase[na] = tt;
+        s.vbase[na] = vi;
         s.na = na;
         s.U = u;
         s.geff = (int)std::max<long long>(1, std::min<long long>(G, u / UMIN));
@@ -146,54 +157,85 @@ __device__ __forceinline__ uint8_t* stage_base(int stages) {
 
 // Pipeline counters of the role threads, kept in registers across phases.
 struct Roles {
-    uint32_t pc = 0;  // chunks issued (producer) / consumed (MMA)
-    uint32_t rc = 0;  // runs accumulated (MMA) / drained (epilogue)
+    uint32_t pc = 0;   // chunks issued (producer) / consumed (MMA)
+    uint32_t st = 0;   // stage of chunk pc
+    uint32_t ph = 0;   // parity of the ring pass of chunk pc
+    uint32_t rc = 0;   // runs accumulated (MMA) / drained (epilogue)
     int last_issued = -1;
+    __device__ __forceinline__ void next(int S) {
+        ++pc;
+        if (++st == (uint32_t)S) {
+            st = 0;
+            ph ^= 1u;
+        }
+    }
 };
 
 // One GEMM phase: for every active problem, Y = Ã P over its row tiles, the
 // chunks (64-wide K slices) of all tiles split into G_eff contiguous ranges, one
 // per CTA.  A CTA accumulates consecutive chunks of one tile in tensor memory
-// (a "run") and writes each run's 128 x nr product to its slot.
+// (a "run") and writes each run's 128 x nr product to its slot.  The producer and
+// the MMA issuer walk their range with running indices (one division per phase).
 __device__ void gemm_phase(Ctl& s, const Params& P, int b, Roles& ro) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (s.U == 0 || b >= s.geff) return;
     const long long u0 = range_start(s.U, s.geff, b), u1 = range_start(s.U, s.geff, b + 1);
     if (u0 >= u1) return;
     const int S = P.stages;
-    const int stage_bytes = A_TILE * P.nsmax + P.nrmax * 2 * BK * 2;
+    const uint32_t stage_bytes = A_TILE * P.nsmax + P.nrmax * 2 * BK * 2;
     uint8_t* base = stage_base(S);
+    const int nitems = (int)(u1 - u0);
 
     if (warp == 0) {
         if (lane == 0) {
             const uint64_t pol_a = tc::policy_evict_first(), pol_b = tc::policy_evict_last();
             tc::fence_proxy_async_global();
-            for (long long g = u0; g < u1; ++g) {
-                const Unit u = decode(s, P, g);
-                const ProbDev& pr = P.prob[u.p];
-                const int st = ro.pc % S;
-                const uint32_t ph = (ro.pc / S) & 1;
-                if (!tc::mbar_wait(&s.empty[st], ph ^ 1)) {
+            const Unit u = decode(s, P, u0);
+            int k = u.k, t = u.t, c = u.c;
+            const ProbDev* pr = &P.prob[u.p];
+            uint32_t pbytes = pr->nr * 2 * BK * 2;
+            size_t sstride = (size_t)pr->mtiles * pr->chunks * A_TILE;
+            const uint8_t* ga = pr->S + ((size_t)t * pr->chunks + c) * A_TILE;
+            const uint8_t* gp = reinterpret_cast<const uint8_t*>(pr->P) + (size_t)c * pbytes;
+            for (int it = 0; it < nitems; ++it) {
+                if (!tc::mbar_wait(&s.empty[ro.st], ro.ph ^ 1)) {
                     atomicOr(P.err, 1);
                     break;
                 }
-                const uint32_t bytes = A_TILE * pr.nslices + pr.nr * 2 * BK * 2;
-                tc::mbar_arrive_expect_tx(&s.full[st], bytes);
-                uint8_t* sa = base + (size_t)st * stage_bytes;
-                tc::tma_load_2d(sa, &P.tmA[u.p][0], u.c * BK, u.t * BM, &s.full[st], pol_a);
-                if (pr.nslices > 1) tc::tma_load_2d(sa + A_TILE, &P.tmA[u.p][1], u.c * BK, u.t * BM, &s.full[st], pol_a);
-                tc::tma_load_2d(sa + (size_t)A_TILE * P.nsmax, &P.tmP[u.p], u.c * BK, 0, &s.full[st], pol_b);
+                tc::mbar_arrive_expect_tx(&s.full[ro.st], A_TILE * pr->nslices + pbytes);
+                uint8_t* sa = base + ro.st * stage_bytes;
+                tc::bulk_load(sa, ga, A_TILE, &s.full[ro.st], pol_a);
+                if (pr->nslices > 1) tc::bulk_load(sa + A_TILE, ga + sstride, A_TILE, &s.full[ro.st], pol_a);
+                tc::bulk_load(sa + A_TILE * P.nsmax, gp, pbytes, &s.full[ro.st], pol_b);
                 ro.last_issued = (int)ro.pc;
-                ++ro.pc;
+                ro.next(S);
+                // next chunk: tiles of a problem are consecutive blocks, chunk-major within a tile
+                ga += A_TILE;
+                gp += pbytes;
+                if (++c == pr->chunks) {
+                    c = 0;
+                    gp = reinterpret_cast<const uint8_t*>(pr->P);
+                    if (++t == pr->mtiles && ++k < s.na) {
+                        t = 0;
+                        pr = &P.prob[s.act[k]];
+                        pbytes = pr->nr * 2 * BK * 2;
+                        sstride = (size_t)pr->mtiles * pr->chunks * A_TILE;
+                        ga = pr->S;
+                        gp = reinterpret_cast<const uint8_t*>(pr->P);
+                    }
+                }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            for (long long g = u0; g < u1; ++g) {
-                const Unit u = decode(s, P, g);
-                const ProbDev& pr = P.prob[u.p];
-                const bool first = (g == u0) || (u.c == 0);
-                const bool last = (g == u1 - 1) || (u.c == pr.chunks - 1);
+            const Unit u = decode(s, P, u0);
+            int k = u.k, c = u.c, t = u.t;
+            const ProbDev* pr = &P.prob[u.p];
+            uint32_t id_all = tc::idesc_bf16_f32(BM, 2 * pr->nr), id_hi = tc::idesc_bf16_f32(BM, pr->nr);
+            const uint64_t dbase = tc::sdesc_sw128(tc::smem_addr(base));
+            bool first = true;
+            for (int it = 0; it < nitems; ++it) {
+                const bool last = (it == nitems - 1) || (c == pr->chunks - 1);
                 if (first) {
                     if (!tc::mbar_wait(&s.acc_empty, (ro.rc & 1) ^ 1)) {
                         atomicOr(P.err, 1);
@@ -201,31 +243,48 @@ __device__ void gemm_phase(Ctl& s, const Params& P, int b, Roles& ro) {
                     }
                     tc::tc_fence_after();
                 }
-                const int st = ro.pc % S;
-                const uint32_t ph = (ro.pc / S) & 1;
-                if (!tc::mbar_wait(&s.full[st], ph)) {
+                if (!tc::mbar_wait(&s.full[ro.st], ro.ph)) {
                     atomicOr(P.err, 1);
                     break;
                 }
                 tc::tc_fence_after();
-                const uint32_t sa = tc::smem_addr(base + (size_t)st * stage_bytes);
-                const uint32_t sb = sa + A_TILE * P.nsmax;
-                const uint32_t id_all = tc::idesc_bf16_f32(BM, 2 * pr.nr);
-                const uint32_t id_hi = tc::idesc_bf16_f32(BM, pr.nr);
+                // descriptors of this stage: start address field advanced by (offset >> 4)
+                const uint64_t da = dbase + ((ro.st * stage_bytes) >> 4);
+                const uint64_t db = da + ((A_TILE * P.nsmax) >> 4);
+                // K step kk accumulates into accumulator kk mod nacc, so consecutive MMAs do not
+                // wait on each other's result; the S_1 products follow all S_0 products of the chunk
+                const uint32_t acc_cols = 2 * pr->nr;
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk) {
-                    tc::mma_bf16(s.tmem_base, tc::sdesc_sw128(sa + kk * 32), tc::sdesc_sw128(sb + kk * 32), id_all,
-                                 (first && kk == 0) ? 0u : 1u);
-                    if (pr.nslices > 1)
-                        tc::mma_bf16(s.tmem_base + pr.nr, tc::sdesc_sw128(sa + A_TILE + kk * 32),
-                                     tc::sdesc_sw128(sb + kk * 32), id_hi, 1u);
+                    const uint32_t a = kk & (P.nacc - 1);
+                    tc::mma_bf16(s.tmem_base + a * acc_cols, da + 2 * kk, db + 2 * kk, id_all,
+                                 (first && kk < P.nacc) ? 0u : 1u);
                 }
-                tc::mma_commit(&s.empty[st]);
+                if (pr->nslices > 1) {
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t a = kk & (P.nacc - 1);
+                        tc::mma_bf16(s.tmem_base + a * acc_cols + pr->nr, da + (A_TILE >> 4) + 2 * kk, db + 2 * kk,
+                                     id_hi, 1u);
+                    }
+                }
+                tc::mma_commit(&s.empty[ro.st]);
+                first = false;
                 if (last) {
                     tc::mma_commit(&s.acc_full);
                     ++ro.rc;
+                    first = true;
                 }
-                ++ro.pc;
+                ro.next(S);
+                if (++c == pr->chunks) {
+                    c = 0;
+                    if (++t == pr->mtiles && ++k < s.na) {
+                        t = 0;
+                        pr = &P.prob[s.act[k]];
+                        id_all = tc::idesc_bf16_f32(BM, 2 * pr->nr);
+                        id_hi = tc::idesc_bf16_f32(BM, pr->nr);
+                    }
+                }
             }
         }
     } else if (warp >= 4) {
@@ -237,6 +296,14 @@ __device__ void gemm_phase(Ctl& s, const Params& P, int b, Roles& ro) {
             const Unit u = decode(s, P, g);
             const ProbDev& pr = P.prob[u.p];
             const long long gend = std::min<long long>(u1, g + (pr.chunks - u.c));
+            if (quarter == 0 && lane == 0) {
+                int4* ow = P.owners + (s.tbase[u.k] + u.t);
+                if (u.c == 0) {
+                    __stcg(&ow->x, b);
+                    __stcg(&ow->y, r);
+                }
+                if (u.c + (int)(gend - g) == pr.chunks) __stcg(&ow->z, b);
+            }
             int ok = 1;
             if (lane == 0) ok = tc::mbar_wait(&s.acc_full, ro.rc & 1) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -250,12 +317,20 @@ __device__ void gemm_phase(Ctl& s, const Params& P, int b, Roles& ro) {
                 float* slot = P.slots + ((size_t)(b * P.rmax + r) * P.nrmax) * BM;
                 const uint32_t ta = s.tmem_base + ((uint32_t)(quarter * 32) << 16);
                 for (int jc = 0; jc < pr.nr; jc += 16) {
-                    float a[16], c[16];
-                    tc::tmem_ld16(ta + jc, a);
-                    tc::tmem_ld16(ta + pr.nr + jc, c);
-                    tc::tmem_wait_ld();
+                    float y[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) __stcg(slot + (size_t)(jc + i) * BM + row, a[i] + c[i]);
+                    for (int i = 0; i < 16; ++i) y[i] = 0.f;
+                    for (int acc = 0; acc < P.nacc; ++acc) {
+                        float a[16], c[16];
+                        const uint32_t tacc = ta + acc * 2 * pr.nr;
+                        tc::tmem_ld16(tacc + jc, a);
+                        tc::tmem_ld16(tacc + pr.nr + jc, c);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) y[i] += a[i] + c[i];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) __stcg(slot + (size_t)(jc + i) * BM + row, y[i]);
                 }
             } else if (lane == 0) {
                 atomicOr(P.err, 2);
@@ -270,29 +345,25 @@ __device__ void gemm_phase(Ctl& s, const Params& P, int b, Roles& ro) {
     }
 }
 
-// For every row tile of active problem k: the first CTA whose run covers it, that
-// run's index, and the number of CTAs contributing (later ones use run 0).
-__device__ void owner_table(Ctl& s, const Params& P, int k) {
-    __syncthreads();  // earlier readers of the table are done
-    const int p = s.act[k];
-    const ProbDev& pr = P.prob[p];
-    for (int t = threadIdx.x; t < pr.mtiles; t += blockDim.x) {
-        const long long g0 = s.ubase[k] + (long long)t * pr.chunks, g1 = g0 + pr.chunks - 1;
-        const int bf = owner(g0, s.U, s.geff), bl = owner(g1, s.U, s.geff);
-        s.own_first[t] = bf;
-        s.own_cnt[t] = bl - bf + 1;
-        s.own_r[t] = (int)(tile_ordinal(s, P, g0) - tile_ordinal(s, P, range_start(s.U, s.geff, bf)));
-    }
-    __syncthreads();
+// The CTAs whose runs cover row tile t of active problem k: the first one, the
+// index of its run for that tile, and how many consecutive CTAs contribute (the
+// later ones through their run 0).
+struct Owners {
+    int first, count, r;
+};
+__device__ __forceinline__ Owners tile_owners(const Ctl& s, const Params& P, int k, int t) {
+    const int4 o = __ldcg(P.owners + (s.tbase[k] + t));
+    // entries are written by the GEMM epilogues; anything out of range means a phase did
+    // not complete: contribute nothing (the error flag is already set by the waits)
+    if (o.x < 0 || o.z < o.x || o.z >= s.geff || o.y < 0 || o.y >= P.rmax) return {0, 0, 0};
+    return {o.x, o.z - o.x + 1, o.y};
 }
 
-// y[i .. i+3] of column j: the sum of the run slots that cover row tile i / 128
-__device__ __forceinline__ float4 gather_q(const Ctl& s, const Params& P, int j, int i) {
-    const int t = i >> 7, off = i & 127;
-    const int bf = s.own_first[t], cnt = s.own_cnt[t];
+// q[off .. off+3] of column j in a row tile: the sum of the run slots covering it
+__device__ __forceinline__ float4 gather_q(const Params& P, const Owners& ow, int j, int off) {
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int o = 0; o < cnt; ++o) {
-        const int sl = (o == 0) ? ((bf)*P.rmax + s.own_r[t]) : ((bf + o) * P.rmax);
+    for (int o = 0; o < ow.count; ++o) {
+        const int sl = (o == 0) ? (ow.first * P.rmax + ow.r) : ((ow.first + o) * P.rmax);
         const float4 v = __ldcg(reinterpret_cast<const float4*>(P.slots + ((size_t)sl * P.nrmax + j) * BM + off));
         q.x += v.x;
         q.y += v.y;
@@ -302,122 +373,213 @@ __device__ __forceinline__ float4 gather_q(const Ctl& s, const Params& P, int j,
     return q;
 }
 
-__device__ __forceinline__ double block_sum(double v, Ctl& s) {
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) s.red[w] = v;
-    __syncthreads();
-    double t = 0.0;
-#pragma unroll
-    for (int i = 0; i < THREADS / 32; ++i) t += s.red[i];
-    return t;
-}
-
 __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo, float v) {
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
     *hi = h;
     *lo = l;
 }
+// entry i of column j of P (hi at row j, lo at row nr + j of the 2 nr-row tiles)
+__device__ __forceinline__ void p_store(__nv_bfloat16* P, int nr, int j, int i, float v) {
+    uint8_t* Pt = reinterpret_cast<uint8_t*>(P);
+    const size_t tb = (size_t)(i >> 6) * (2 * nr) * 128;
+    split_store(reinterpret_cast<__nv_bfloat16*>(Pt + tb + sw128(j, i & 63)),
+                reinterpret_cast<__nv_bfloat16*>(Pt + tb + sw128(nr + j, i & 63)), v);
+}
 
-// One CG step for every unfinished column of the active problems, a CTA per column.
-__device__ void vector_phase(Ctl& s, const Params& P, int b, int G) {
-    int total = 0;
-    for (int k = 0; k < s.na; ++k) total += P.prob[s.act[k]].nr;
-    int cached_k = -1;
-    for (int ci = b; ci < total; ci += G) {
-        int k = 0, j = ci;
-        while (j >= P.prob[s.act[k]].nr) j -= P.prob[s.act[k++]].nr;
-        const int p = s.act[k];
-        const ProbDev& pr = P.prob[p];
-        ColState* cs = pr.col + j;
+// Vector work is split into items (active problem, column j, group of VT row tiles =
+// VT * 128 rows); each warp of the grid takes a contiguous range of items, each lane
+// four consecutive rows of every tile of the group.  Dot products are summed per item
+// and written as partials; a column's total is the sum of its partials in group
+// order, computed identically by every warp that needs it.
+constexpr int VT = 4;
+
+struct VItem {
+    int k, p, j, g;
+};
+__device__ __forceinline__ VItem vdecode(const Ctl& s, const Params& P, long long i) {
+    int k = 0;
+    while (k + 1 < s.na && i >= s.vbase[k + 1]) ++k;
+    const int p = s.act[k];
+    const long long l = i - s.vbase[k];
+    const int ng = P.prob[p].ngroups;
+    return {k, p, (int)(l / ng), (int)(l % ng)};
+}
+
+// sum of part[0 .. m) in index order within each lane's stride, then across lanes.
+// The inner iteration keeps its inner products in float32: its vectors are float32,
+// and the float64 pipe of this part is too slow to spend on them.
+__device__ __forceinline__ float column_total(const float* part, int m) {
+    const int lane = threadIdx.x & 31;
+    float a = 0.f;
+    for (int i = lane; i < m; i += 32) a += __ldcg(part + i);
+    return warp_sum(a);
+}
+
+__device__ __forceinline__ float dot4(const float4& a, const float4& b) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+
+// The inner iteration is conjugate gradients in the Chronopoulos-Gear arrangement:
+// the product is taken of the residual (w = Ã r) and s = Ã p is carried by
+// recurrence, so that both inner products of a step (gamma = r.r, delta = r.w) come
+// from one pass, and a step needs two vector phases:
+//   X: w = Ã r (sum of the run slots); partial gamma and delta per item.
+//   Y: beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev)
+//      (beta = 0, alpha = gamma / delta on the first step); p = r + beta p,
+//      s = w + beta s, z += alpha p, r -= alpha s; bf16 split of the new r.
+// In exact arithmetic this is the same sequence of iterates as the textbook form.
+
+// Phase X
+__device__ void vec_phase_x(const Ctl& s, const Params& P, int gw, int W) {
+    const long long I = s.vbase[s.na];
+    const long long i0 = range_start(I, W, gw), i1 = range_start(I, W, gw + 1);
+    const int lane = threadIdx.x & 31;
+    for (long long i = i0; i < i1; ++i) {
+        const VItem v = vdecode(s, P, i);
+        const ProbDev& pr = P.prob[v.p];
+        const int done = __ldcg(&pr.col[v.j].done);
+        const size_t base = (size_t)v.j * pr.ldv;
+        const int tn = min(VT, pr.mtiles - v.g * VT);
+        Owners ow[VT];
+        float4 rv[VT];
+#pragma unroll
+        for (int u = 0; u < VT; ++u) {
+            if (u < tn) {
+                ow[u] = tile_owners(s, P, v.k, v.g * VT + u);
+                rv[u] = __ldcg(reinterpret_cast<const float4*>(pr.r + base + (v.g * VT + u) * BM + lane * 4));
+            }
+        }
+        if (done) continue;
+        float d = 0.f, g = 0.f;
+#pragma unroll
+        for (int u = 0; u < VT; ++u) {
+            if (u < tn) {
+                const float4 w = gather_q(P, ow[u], v.j, lane * 4);
+                __stcg(reinterpret_cast<float4*>(pr.q + base + (v.g * VT + u) * BM + lane * 4), w);
+                d += dot4(rv[u], w);
+                g += dot4(rv[u], rv[u]);
+            }
+        }
+        d = warp_sum(d);
+        g = warp_sum(g);
+        if (lane == 0) {
+            __stcg(pr.pq + (size_t)v.j * pr.ngroups + v.g, d);
+            __stcg(pr.rq + (size_t)v.j * pr.ngroups + v.g, g);
+        }
+    }
+}
+
+// Phase Y
+__device__ void vec_phase_y(const Ctl& s, const Params& P, int gw, int W, int it) {
+    const long long I = s.vbase[s.na];
+    const long long i0 = range_start(I, W, gw), i1 = range_start(I, W, gw + 1);
+    const int lane = threadIdx.x & 31;
+    int cp = -1, cj = -1;
+    float gam = 0.f, del = 0.f;
+    for (long long i = i0; i < i1; ++i) {
+        const VItem v = vdecode(s, P, i);
+        const ProbDev& pr = P.prob[v.p];
+        ColState* cs = pr.col + v.j;
+        const size_t base = (size_t)v.j * pr.ldv;
+        const int tn = min(VT, pr.mtiles - v.g * VT);
+        // every load of the item is independent of the step scalars: issue them all first
+        float4 w[VT], r[VT], pp[VT], sv[VT], z[VT];
+#pragma unroll
+        for (int u = 0; u < VT; ++u) {
+            if (u < tn) {
+                const size_t o = base + (v.g * VT + u) * BM + lane * 4;
+                w[u] = __ldcg(reinterpret_cast<const float4*>(pr.q + o));
+                r[u] = __ldcg(reinterpret_cast<const float4*>(pr.r + o));
+                pp[u] = __ldcg(reinterpret_cast<const float4*>(pr.p + o));
+                sv[u] = __ldcg(reinterpret_cast<const float4*>(pr.sv + o));
+                z[u] = __ldcg(reinterpret_cast<const float4*>(pr.z + o));
+            }
+        }
+        const float gprev = (float)__ldcg(&cs->gam[it & 1]), aprev = (float)__ldcg(&cs->alp[it & 1]);
+        const float rr0 = (float)__ldcg(&cs->rr0);
         if (__ldcg(&cs->done)) continue;
-        // column state, read before any thread of the block can update it
-        const double rr = __ldcg(&cs->rr), rr0 = __ldcg(&cs->rr0);
-        const int its = __ldcg(&cs->its) + 1;
-        if (k != cached_k) {
-            owner_table(s, P, k);
-            cached_k = k;
+        if (v.p != cp || v.j != cj) {
+            gam = column_total(pr.rq + (size_t)v.j * pr.ngroups, pr.ngroups);
+            del = column_total(pr.pq + (size_t)v.j * pr.ngroups, pr.ngroups);
+            cp = v.p;
+            cj = v.j;
         }
-        const int rows = pr.mtiles * BM;
-        float* pv = pr.p + (size_t)j * pr.ldv;
-        float* qv = pr.q + (size_t)j * pr.ldv;
-        float* rv = pr.r + (size_t)j * pr.ldv;
-        float* zv = pr.z + (size_t)j * pr.ldv;
-        // q = Ã p from the run slots; p.q
-        double pq = 0.0;
-        for (int i = threadIdx.x * 4; i < rows; i += THREADS * 4) {
-            const float4 q = gather_q(s, P, j, i);
-            const float4 pp = __ldcg(reinterpret_cast<const float4*>(pv + i));
-            pq += (double)pp.x * q.x + (double)pp.y * q.y + (double)pp.z * q.z + (double)pp.w * q.w;
-            __stcg(reinterpret_cast<float4*>(qv + i), q);
-        }
-        pq = block_sum(pq, s);
-        if (!(pq > 0.0)) {
-            if (threadIdx.x == 0) {
+        // every warp of the column computes the same totals and takes the same branch
+        if (gam <= (float)P.tol2 * rr0) {
+            if (v.g == 0 && lane == 0) {
+                __stcg(&cs->its, it);
+                __stcg(&cs->status, (int)FL_OK);
                 __stcg(&cs->done, 1);
+                atomicAdd(P.ndone + v.p, 1);
+            }
+            continue;
+        }
+        float beta = 0.f, alpha;
+        if (it == 0) {
+            alpha = gam / del;
+        } else {
+            beta = gam / gprev;
+            alpha = gam / (del - beta * gam / aprev);
+        }
+        if (!(alpha > 0.f) || !isfinite(alpha)) {  // loss of positive definiteness
+            if (v.g == 0 && lane == 0) {
                 __stcg(&cs->status, (int)FL_ENOTSPD);
-                atomicAdd(P.ndone + p, 1);
-            }
-            continue;
-        }
-        const float alpha = (float)(rr / pq);
-        double rn = 0.0;
-        for (int i = threadIdx.x * 4; i < rows; i += THREADS * 4) {
-            const float4 pp = __ldcg(reinterpret_cast<const float4*>(pv + i));
-            const float4 q = __ldcg(reinterpret_cast<const float4*>(qv + i));
-            float4 z = __ldcg(reinterpret_cast<const float4*>(zv + i));
-            float4 r = __ldcg(reinterpret_cast<const float4*>(rv + i));
-            z.x = fmaf(alpha, pp.x, z.x);
-            z.y = fmaf(alpha, pp.y, z.y);
-            z.z = fmaf(alpha, pp.z, z.z);
-            z.w = fmaf(alpha, pp.w, z.w);
-            r.x = fmaf(-alpha, q.x, r.x);
-            r.y = fmaf(-alpha, q.y, r.y);
-            r.z = fmaf(-alpha, q.z, r.z);
-            r.w = fmaf(-alpha, q.w, r.w);
-            rn += (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z + (double)r.w * r.w;
-            __stcg(reinterpret_cast<float4*>(zv + i), z);
-            __stcg(reinterpret_cast<float4*>(rv + i), r);
-        }
-        rn = block_sum(rn, s);
-        const bool conv = rn <= P.tol2 * rr0;
-        if (conv || its >= P.maxit) {
-            if (threadIdx.x == 0) {
-                __stcg(&cs->its, its);
-                __stcg(&cs->rr, rn);
+                __stcg(&cs->its, it + 1);
                 __stcg(&cs->done, 1);
-                __stcg(&cs->status, conv ? (int)FL_OK : (int)FL_ENOTCONV);
-                atomicAdd(P.ndone + p, 1);
+                atomicAdd(P.ndone + v.p, 1);
             }
             continue;
         }
-        const float beta = (float)(rn / rr);
-        __nv_bfloat16* Ph = pr.P + (size_t)j * pr.ldv;
-        __nv_bfloat16* Pl = pr.P + (size_t)(pr.nr + j) * pr.ldv;
-        for (int i = threadIdx.x * 4; i < rows; i += THREADS * 4) {
-            const float4 r = __ldcg(reinterpret_cast<const float4*>(rv + i));
-            float4 pp = __ldcg(reinterpret_cast<const float4*>(pv + i));
-            pp.x = fmaf(beta, pp.x, r.x);
-            pp.y = fmaf(beta, pp.y, r.y);
-            pp.z = fmaf(beta, pp.z, r.z);
-            pp.w = fmaf(beta, pp.w, r.w);
-            __stcg(reinterpret_cast<float4*>(pv + i), pp);
+        const float a = alpha, bt = beta;
+        uint8_t* Pt = reinterpret_cast<uint8_t*>(pr.P);
+        const int nr2 = 2 * pr.nr;
+#pragma unroll
+        for (int u = 0; u < VT; ++u) {
+            if (u >= tn) break;
+            const int row = (v.g * VT + u) * BM + lane * 4;
+            const size_t o = base + row;
+            pp[u].x = fmaf(bt, pp[u].x, r[u].x);
+            pp[u].y = fmaf(bt, pp[u].y, r[u].y);
+            pp[u].z = fmaf(bt, pp[u].z, r[u].z);
+            pp[u].w = fmaf(bt, pp[u].w, r[u].w);
+            sv[u].x = fmaf(bt, sv[u].x, w[u].x);
+            sv[u].y = fmaf(bt, sv[u].y, w[u].y);
+            sv[u].z = fmaf(bt, sv[u].z, w[u].z);
+            sv[u].w = fmaf(bt, sv[u].w, w[u].w);
+            z[u].x = fmaf(a, pp[u].x, z[u].x);
+            z[u].y = fmaf(a, pp[u].y, z[u].y);
+            z[u].z = fmaf(a, pp[u].z, z[u].z);
+            z[u].w = fmaf(a, pp[u].w, z[u].w);
+            r[u].x = fmaf(-a, sv[u].x, r[u].x);
+            r[u].y = fmaf(-a, sv[u].y, r[u].y);
+            r[u].z = fmaf(-a, sv[u].z, r[u].z);
+            r[u].w = fmaf(-a, sv[u].w, r[u].w);
+            __stcg(reinterpret_cast<float4*>(pr.p + o), pp[u]);
+            __stcg(reinterpret_cast<float4*>(pr.sv + o), sv[u]);
+            __stcg(reinterpret_cast<float4*>(pr.z + o), z[u]);
+            __stcg(reinterpret_cast<float4*>(pr.r + o), r[u]);
             __nv_bfloat16 h[4], l[4];
-            split_store(&h[0], &l[0], pp.x);
-            split_store(&h[1], &l[1], pp.y);
-            split_store(&h[2], &l[2], pp.z);
-            split_store(&h[3], &l[3], pp.w);
+            split_store(&h[0], &l[0], r[u].x);
+            split_store(&h[1], &l[1], r[u].y);
+            split_store(&h[2], &l[2], r[u].z);
+            split_store(&h[3], &l[3], r[u].w);
             uint2 hv, lv;
             memcpy(&hv, h, 8);
             memcpy(&lv, l, 8);
-            __stcg(reinterpret_cast<uint2*>(Ph + i), hv);
-            __stcg(reinterpret_cast<uint2*>(Pl + i), lv);
+            const size_t tb = (size_t)(row >> 6) * nr2 * 128;
+            __stcg(reinterpret_cast<uint2*>(Pt + tb + sw128(v.j, row & 63)), hv);
+            __stcg(reinterpret_cast<uint2*>(Pt + tb + sw128(pr.nr + v.j, row & 63)), lv);
         }
-        if (threadIdx.x == 0) {
-            __stcg(&cs->its, its);
-            __stcg(&cs->rr, rn);
+        if (v.g == 0 && lane == 0) {
+            __stcg(&cs->gam[(it + 1) & 1], gam);
+            __stcg(&cs->alp[(it + 1) & 1], alpha);
+            __stcg(&cs->its, it + 1);
+            if (it + 1 >= P.maxit) {
+                __stcg(&cs->status, (int)FL_ENOTCONV);
+                __stcg(&cs->done, 1);
+                atomicAdd(P.ndone + v.p, 1);
+            }
         }
     }
     tc::fence_proxy_async_global();
@@ -434,11 +596,6 @@ __device__ void setup(Ctl& s, const Params& P) {
         tc::mbar_init(&s.acc_empty, 4);
         tc::mbar_init(&s.drain, 1);
         tc::mbar_fence_init();
-        for (int p = 0; p < P.nprob; ++p) {
-            tc::tma_prefetch(&P.tmA[p][0]);
-            if (P.prob[p].nslices > 1) tc::tma_prefetch(&P.tmA[p][1]);
-            tc::tma_prefetch(&P.tmP[p]);
-        }
     }
     if (warp == 1) {
         tc::tmem_alloc(&s.tmem_base, (uint32_t)P.tmem_cols);
@@ -488,16 +645,18 @@ __global__ void __launch_bounds__(THREADS, 1) cg_kernel(const __grid_constant__ 
     setup(s, P);
     Roles ro;
     const int G = gridDim.x;
+    unsigned epoch = 0;
     int it = 0;
     for (; it < P.maxit; ++it) {
         plan_phase(s, P, G, true);
         if (s.na == 0) break;
         gemm_phase(s, P, blockIdx.x, ro);
-        if (!tc::grid_barrier(P.gbar, G, P.err)) break;
-        if (__ldcg(P.err) != 0) break;
-        vector_phase(s, P, blockIdx.x, G);
-        if (!tc::grid_barrier(P.gbar, G, P.err)) break;
-        if (__ldcg(P.err) != 0) break;
+        if (!tc::grid_barrier(P.gbar, epoch, G, P.err) || __ldcg(P.err) != 0) break;
+        const int W = G * (THREADS / 32), gw = blockIdx.x * (THREADS / 32) + (threadIdx.x >> 5);
+        vec_phase_x(s, P, gw, W);
+        if (!tc::grid_barrier(P.gbar, epoch, G, P.err) || __ldcg(P.err) != 0) break;
+        vec_phase_y(s, P, gw, W, it);
+        if (!tc::grid_barrier(P.gbar, epoch, G, P.err) || __ldcg(P.err) != 0) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *P.iters = it;
     __syncthreads();
@@ -510,24 +669,21 @@ __global__ void slots_reduce_kernel(const __grid_constant__ Params P, int G, flo
     __shared__ Ctl s;
     plan_phase(s, P, G, false);
     const int j = blockIdx.x;
-    owner_table(s, P, 0);
     const ProbDev& pr = P.prob[s.act[0]];
     for (int i = threadIdx.x * 4; i < pr.mtiles * BM; i += blockDim.x * 4) {
-        const float4 q = gather_q(s, P, j, i);
+        const Owners ow = tile_owners(s, P, 0, i / BM);
+        const float4 q = gather_q(P, ow, j, i % BM);
         const float v[4] = {q.x, q.y, q.z, q.w};
         for (int e = 0; e < 4; ++e)
             if (i + e < pr.n) Y[(size_t)j * ldy + i + e] = v[e];
     }
 }
 
-// X (float32, [nr][ldx]) -> P = [x_hi ; x_lo] (bf16, [2 nr][ldv]), zero beyond n.
-__global__ void split_vec_kernel(int n, int nr, int ldv, int rows, const float* X, int64_t ldx,
-                                 __nv_bfloat16* Pb) {
+// X (float32, column j at X + j ldx) -> P tiles (x_hi, x_lo), zero beyond n.
+__global__ void split_vec_kernel(int n, int nr, int rows, const float* X, int64_t ldx, __nv_bfloat16* Pb) {
     const int j = blockIdx.y;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
-        const float v = (i < n) ? X[(size_t)j * ldx + i] : 0.f;
-        split_store(Pb + (size_t)j * ldv + i, Pb + (size_t)(nr + j) * ldv + i, v);
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x)
+        p_store(Pb, nr, j, i, (i < n) ? X[(size_t)j * ldx + i] : 0.f);
 }
 
 // ------------------------------------------------- slices of the matrix --
@@ -557,17 +713,32 @@ __global__ void dscale_kernel(int64_t n, const double* A, int64_t lda, double* d
     if (i < n) d[i] = 1.0 / sqrt(A[i * lda + i]);
 }
 
-// S_0 = bf16(Ã), S_1 = bf16(Ã - S_0) with Ã_ij = (d_i d_j) a_ij (exactly symmetric)
+// S_0 = bf16(Ã), S_1 = bf16(Ã - S_0) with Ã_ij = (d_i d_j) a_ij (exactly symmetric),
+// written as swizzled 128 x 64 tiles (zero outside n x n).  Block per tile; each
+// thread converts 8 consecutive entries of a row into one 16-byte unit.
 __global__ void split_matrix_kernel(int64_t n, const double* A, int64_t lda, const double* d, int nslices,
-                                    uint16_t* S, int64_t lds) {
-    for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
-        const double di = d[i];
-        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-             j += (int64_t)gridDim.x * blockDim.x) {
-            const double a = A[i * lda + j] * (di * d[j]);
-            const uint16_t h = bf16_bits_rn(a);
-            S[i * lds + j] = h;
-            if (nslices > 1) S[n * lds + i * lds + j] = bf16_bits_rn(a - bf16_value(h));
+                                    uint8_t* S, int mtiles, int chunks) {
+    for (int64_t blk = blockIdx.x; blk < (int64_t)mtiles * chunks; blk += gridDim.x) {
+        const int t = (int)(blk / chunks), c = (int)(blk % chunks);
+        uint8_t* T0 = S + (size_t)blk * A_TILE;
+        uint8_t* T1 = S + ((size_t)mtiles * chunks + blk) * A_TILE;
+        for (int e = threadIdx.x; e < BM * 8; e += blockDim.x) {
+            const int r = e >> 3, u = e & 7;
+            const int64_t i = (int64_t)t * BM + r;
+            uint16_t h[8], l[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int64_t j = (int64_t)c * BK + u * 8 + q;
+                double a = 0.0;
+                if (i < n && j < n) a = A[i * lda + j] * (d[i] * d[j]);
+                h[q] = bf16_bits_rn(a);
+                l[q] = bf16_bits_rn(a - bf16_value(h[q]));
+            }
+            uint4 hv, lv;
+            memcpy(&hv, h, 16);
+            memcpy(&lv, l, 16);
+            *reinterpret_cast<uint4*>(T0 + sw128(r, u * 8)) = hv;
+            if (nslices > 1) *reinterpret_cast<uint4*>(T1 + sw128(r, u * 8)) = lv;
         }
     }
 }
@@ -656,7 +827,8 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(const __grid_cons
 // range is empty), and every CTA writes one partial (s_hi, s_lo) tile per row
 // block it touched.
 constexpr int DF_ROWS = 128, DF_COLS = 64, DF_K = 32, DF_THREADS = 256;
-constexpr size_t DF_SMEM = (size_t)DF_K * (DF_ROWS + 1) * sizeof(float2) + (size_t)DF_K * DF_COLS * sizeof(float2);
+constexpr size_t DF_SMEM = (size_t)DF_K * (DF_ROWS + 1) * sizeof(float2) + (size_t)DF_K * DF_COLS * sizeof(float2) +
+                          (size_t)(DF_ROWS * DF_K + DF_K * DF_COLS) * sizeof(double);
 
 struct DfProb {
     int n, nrhs, nrp, rblocks, kch, ctiles;
@@ -692,9 +864,31 @@ __device__ __forceinline__ long long df_tile(const DfParams& D, long long g) {
     return D.tbase[u.k] + (long long)u.ct * D.prob[u.p].rblocks + u.rb;
 }
 
+// x = hi + lo + O(2^-47 |x|) with integer operations only (no float64 pipe): hi keeps
+// the leading 24 significand bits (truncated), lo is the float32 value of the 29 bits
+// dropped.  |x| < 2^-126 gives (0, 0); lo is dropped below 2^-74 |x|'s scale.
 __device__ __forceinline__ void df_split(double x, float2& v) {
-    const float hi = __double2float_rn(x);
-    v = make_float2(hi, __double2float_rn(x - (double)hi));
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((u >> 52) & 0x7ff);
+    if (e <= 1023 - 127) {
+        v = make_float2(0.f, 0.f);
+        return;
+    }
+    const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+    if (e >= 1023 + 128) {  // beyond float32: an infinity that poisons the residual visibly
+        v = make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+        return;
+    }
+    const unsigned long long m = u & ((1ull << 52) - 1);
+    const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(m >> 29));
+    // dropped bits have weight 2^(e - 1023 - 52); as a float32 scale that needs e >= 949
+    float lo = 0.f;
+    if (e >= 1023 - 74) {
+        const float scale = __uint_as_float((unsigned)(e - 1023 - 52 + 127) << 23);
+        lo = __uint2float_rn((unsigned)(m & 0x1FFFFFFFu)) * scale;
+        if (sign) lo = -lo;
+    }
+    v = make_float2(hi, lo);
 }
 
 // (sh, sl) += (ah + al)(uh + ul), dropping al ul
@@ -709,16 +903,48 @@ __device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al,
     sl = __fadd_rn(sl, __fadd_rn(err, l));
 }
 
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(tc::smem_addr(dst)),
+                 "l"((uint64_t)__cvta_generic_to_global(src)), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Raw float64 tiles of work item g into shared memory (asynchronous, zero-filled
+// outside the matrix): A rows r0.., columns k0.. and U rows k0.., columns c0..
+__device__ __forceinline__ void df_fetch(const DfParams& D, long long g, double* Araw, double* Uraw) {
+    const DfUnit u = df_decode(D, g);
+    const DfProb& pr = D.prob[u.p];
+    const int r0 = u.rb * DF_ROWS, k0 = u.kc * DF_K, c0 = u.ct * DF_COLS;
+    for (int e = threadIdx.x; e < DF_ROWS * DF_K; e += DF_THREADS) {
+        const int row = e >> 5, kk = e & 31;
+        const int i = r0 + row, kcol = k0 + kk;
+        const bool ok = i < pr.n && kcol < pr.n;
+        cp_async8(Araw + e, ok ? pr.A + (int64_t)i * pr.lda + kcol : pr.A, ok ? 8u : 0u);
+    }
+    for (int e = threadIdx.x; e < DF_K * DF_COLS; e += DF_THREADS) {
+        const int kk = e >> 6, c = e & 63;
+        const int krow = k0 + kk, col = c0 + c;
+        const bool ok = krow < pr.n && col < pr.nrhs;
+        cp_async8(Uraw + e, ok ? pr.U + (int64_t)krow * pr.ldu + col : pr.U, ok ? 8u : 0u);
+    }
+    cp_async_commit();
+}
+
 __global__ void __launch_bounds__(DF_THREADS, 2) residual_df_kernel(const __grid_constant__ DfParams D) {
     extern __shared__ float2 df_smem[];
     float2(*As)[DF_ROWS + 1] = reinterpret_cast<float2(*)[DF_ROWS + 1]>(df_smem);
     float2(*Us)[DF_COLS] = reinterpret_cast<float2(*)[DF_COLS]>(df_smem + DF_K * (DF_ROWS + 1));
+    double* Araw = reinterpret_cast<double*>(df_smem + DF_K * (DF_ROWS + 1) + DF_K * DF_COLS);
+    double* Uraw = Araw + DF_ROWS * DF_K;
     const int b = blockIdx.x, G = gridDim.x;
     const long long Utot = D.ubase[D.na];
     const long long u0 = range_start(Utot, G, b), u1 = range_start(Utot, G, b + 1);
     const int t = threadIdx.x, rg = t & 15, cg = t >> 4;
     float sh[8][4], sl[8][4];
     int r = 0;
+    if (u0 < u1) df_fetch(D, u0, Araw, Uraw);
     for (long long g = u0; g < u1; ++g) {
         const DfUnit u = df_decode(D, g);
         const DfProb& pr = D.prob[u.p];
@@ -728,18 +954,12 @@ __global__ void __launch_bounds__(DF_THREADS, 2) residual_df_kernel(const __grid
 #pragma unroll
                 for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
         }
-        const int r0 = u.rb * DF_ROWS, k0 = u.kc * DF_K, c0 = u.ct * DF_COLS;
-        for (int e = t; e < DF_ROWS * DF_K; e += DF_THREADS) {
-            const int row = e >> 5, kk = e & 31;
-            const int i = r0 + row, kcol = k0 + kk;
-            df_split((i < pr.n && kcol < pr.n) ? pr.A[(int64_t)i * pr.lda + kcol] : 0.0, As[kk][row]);
-        }
-        for (int e = t; e < DF_K * DF_COLS; e += DF_THREADS) {
-            const int kk = e >> 6, c = e & 63;
-            const int krow = k0 + kk, col = c0 + c;
-            df_split((krow < pr.n && col < pr.nrhs) ? pr.U[(int64_t)krow * pr.ldu + col] : 0.0, Us[kk][c]);
-        }
-        __syncthreads();
+        cp_async_wait_all();
+        __syncthreads();  // raw tiles of g landed; every thread is done with the previous split tiles
+        for (int e = t; e < DF_ROWS * DF_K; e += DF_THREADS) df_split(Araw[e], As[e & 31][e >> 5]);
+        for (int e = t; e < DF_K * DF_COLS; e += DF_THREADS) df_split(Uraw[e], Us[e >> 6][e & 63]);
+        __syncthreads();  // split tiles ready; raw buffer free
+        if (g + 1 < u1) df_fetch(D, g + 1, Araw, Uraw);  // overlaps the products below
 #pragma unroll 1
         for (int kk = 0; kk < DF_K; ++kk) {
             float2 a[8], v[4];
@@ -752,7 +972,6 @@ __global__ void __launch_bounds__(DF_THREADS, 2) residual_df_kernel(const __grid
 #pragma unroll
                 for (int j = 0; j < 4; ++j) df_fma(sh[i][j], sl[i][j], a[i].x, a[i].y, v[j].x, v[j].y);
         }
-        __syncthreads();
         if (g == u1 - 1 || u.kc == pr.kch - 1) {
             if (r < D.rmax) {
                 float2* slot = D.slots + (size_t)(b * D.rmax + r) * DF_COLS * DF_ROWS;
@@ -767,6 +986,7 @@ __global__ void __launch_bounds__(DF_THREADS, 2) residual_df_kernel(const __grid
             ++r;
         }
     }
+    cp_async_wait_all();
 }
 
 // Sum the partial tiles of each (problem, column tile, row block) in a fixed order:
@@ -896,9 +1116,10 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ RefPa
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
         const float v = (i < pr.n) ? (float)(rp.d[i] * rp.R[(int64_t)i * rp.nrp + j]) : 0.f;
         pr.r[(size_t)j * pr.ldv + i] = v;
-        pr.p[(size_t)j * pr.ldv + i] = v;
+        pr.p[(size_t)j * pr.ldv + i] = 0.f;
+        pr.sv[(size_t)j * pr.ldv + i] = 0.f;
         pr.z[(size_t)j * pr.ldv + i] = 0.f;
-        split_store(pr.P + (size_t)j * pr.ldv + i, pr.P + (size_t)(pr.nr + j) * pr.ldv + i, v);
+        p_store(pr.P, pr.nr, j, i, v);
         rr += (double)v * v;
     }
     rr = warp_sum(rr);
@@ -908,7 +1129,8 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ RefPa
     if (threadIdx.x == 0) {
         double tot = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-        cs->rr = tot;
+        cs->gam[0] = tot;
+        cs->alp[0] = 1.0;
         cs->rr0 = tot;
         cs->its = 0;
         cs->status = FL_OK;
@@ -936,41 +1158,10 @@ __global__ void zero_u_kernel(const __grid_constant__ RefParams RP) {
 }
 
 // ------------------------------------------------------------------ host --
-using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
-
-static EncodeFn encode_fn() {
-    static EncodeFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeFn)p;
-    });
-    return fn;
-}
-
-// 2D bf16 tensor [rows][cols] with row pitch ld elements, tile box (64 x box_rows),
-// 128-byte swizzle, zero fill outside.
-static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
-    EncodeFn fn = encode_fn();
-    if (!fn) return false;
-    if (((uintptr_t)base & 15) != 0 || (ld * 2) % 16 != 0) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
-    cuuint32_t es[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 static int round_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b * b); }
 
 struct Geometry {
-    int G = 0, stages = 0, rmax = 0, nrmax = 0, nsmax = 0, tmem_cols = 0;
+    int G = 0, stages = 0, rmax = 0, nrmax = 0, nsmax = 0, tmem_cols = 0, nacc = 1;
     size_t smem = 0;
 };
 
@@ -1002,7 +1193,10 @@ static bool geometry(const std::vector<ProbDev>& pr, int sms, int want_ctas, int
     // within one tile; U / G_eff <= max(U / G, 2 UMIN) for any subset of problems
     const long long per = std::max<long long>((U + g.G - 1) / g.G, 2 * UMIN) + 1;
     g.rmax = (int)((per + chmin - 1) / chmin) + 1;
-    g.tmem_cols = tmem_cols_for(g.nrmax);
+    // as many accumulators (up to one per K step of a chunk) as tensor memory holds
+    g.nacc = 4;
+    while (g.nacc > 1 && g.nacc * 2 * g.nrmax > 512) g.nacc >>= 1;
+    g.tmem_cols = tmem_cols_for(g.nacc * g.nrmax);
     return true;
 }
 
@@ -1018,23 +1212,29 @@ using namespace fl::bt;
 
 extern "C" {
 
-int fl_split_bf16(const double* A_dev, int64_t lda, int64_t n, int nslices, void* S_dev, int64_t lds,
-                  double* dscale_dev, void* stream) {
-    if (!A_dev || !S_dev || !dscale_dev || n < 1 || n > 65536 || lda < n || lds < n || (lds % 8) != 0 ||
-        (nslices != 1 && nslices != 2) || ((uintptr_t)S_dev & 15) != 0)
+int64_t fl_split_bf16_bytes(int64_t n, int nslices) {
+    if (n < 1 || n > 65536 || (nslices != 1 && nslices != 2)) return 0;
+    return (int64_t)nslices * ((n + BM - 1) / BM) * ((n + BK - 1) / BK) * A_TILE;
+}
+
+int fl_split_bf16(const double* A_dev, int64_t lda, int64_t n, int nslices, void* S_dev, double* dscale_dev,
+                  void* stream) {
+    if (!A_dev || !S_dev || !dscale_dev || n < 1 || n > 65536 || lda < n || (nslices != 1 && nslices != 2) ||
+        ((uintptr_t)S_dev & 15) != 0)
         return FL_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     dscale_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, A_dev, lda, dscale_dev);
     fl::count_launch();
-    dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 32), (unsigned)std::min<int64_t>(n, 65535));
-    split_matrix_kernel<<<grid, 256, 0, st>>>(n, A_dev, lda, dscale_dev, nslices, (uint16_t*)S_dev, lds);
+    const int mt = (int)((n + BM - 1) / BM), ch = (int)((n + BK - 1) / BK);
+    split_matrix_kernel<<<(unsigned)std::min<int64_t>((int64_t)mt * ch, 8192), 256, 0, st>>>(
+        n, A_dev, lda, dscale_dev, nslices, (uint8_t*)S_dev, mt, ch);
     fl::count_launch();
     return cudaGetLastError() == cudaSuccess ? FL_OK : FL_ECUDA;
 }
 
-int fl_matmul_bf16(const void* S_dev, int64_t lds, int64_t n, int nslices, int nrhs, const float* X_dev,
-                   int64_t ldx, float* Y_dev, int64_t ldy, void* stream) {
-    if (!S_dev || !X_dev || !Y_dev || n < 1 || n > 65536 || lds < n || (lds % 8) != 0 || ldx < n || ldy < n ||
+int fl_matmul_bf16(const void* S_dev, int64_t n, int nslices, int nrhs, const float* X_dev, int64_t ldx,
+                   float* Y_dev, int64_t ldy, void* stream) {
+    if (!S_dev || !X_dev || !Y_dev || n < 1 || n > 65536 || ldx < n || ldy < n ||
         nrhs < 16 || nrhs > 128 || (nrhs % 16) != 0 || (nslices != 1 && nslices != 2) ||
         ((uintptr_t)S_dev & 15) != 0)
         return FL_EINVAL;
@@ -1049,6 +1249,7 @@ int fl_matmul_bf16(const void* S_dev, int64_t lds, int64_t n, int nslices, int n
     pd.mtiles = (int)((n + BM - 1) / BM);
     pd.chunks = (int)((n + BK - 1) / BK);
     pd.ldv = round_up(pd.mtiles * BM, 64);
+    pd.S = (const uint8_t*)S_dev;
     Geometry g;
     if (!geometry({pd}, sms, 0, 0, g)) return FL_EINVAL;
     // G: enough CTAs that each takes at least 2 UMIN chunks
@@ -1058,7 +1259,7 @@ int fl_matmul_bf16(const void* S_dev, int64_t lds, int64_t n, int nslices, int n
         const long long per = std::max<long long>((U + g.G - 1) / g.G, 2 * UMIN) + 1;
         g.rmax = (int)((per + pd.chunks - 1) / pd.chunks) + 1;
     }
-    const size_t pbytes = (size_t)2 * nrhs * pd.ldv * sizeof(__nv_bfloat16);
+    const size_t pbytes = (size_t)2 * pd.mtiles * 2 * nrhs * BK * sizeof(__nv_bfloat16);
     const size_t sbytes = (size_t)g.G * g.rmax * g.nrmax * BM * sizeof(float);
     void* ws = nullptr;
     if (cudaMallocAsync(&ws, pbytes + sbytes + 256, st) != cudaSuccess) return FL_ENOMEM;
@@ -1066,7 +1267,7 @@ int fl_matmul_bf16(const void* S_dev, int64_t lds, int64_t n, int nslices, int n
     pd.P = (__nv_bfloat16*)c;
     float* slots = (float*)(c + ((pbytes + 255) & ~size_t(255)));
     int* flags = nullptr;
-    if (cudaMallocAsync((void**)&flags, 256, st) != cudaSuccess) {
+    if (cudaMallocAsync((void**)&flags, 256 + (size_t)pd.mtiles * sizeof(int4), st) != cudaSuccess) {
         cudaFreeAsync(ws, st);
         return FL_ENOMEM;
     }
@@ -1081,22 +1282,20 @@ int fl_matmul_bf16(const void* S_dev, int64_t lds, int64_t n, int nslices, int n
     P.nrmax = g.nrmax;
     P.nsmax = g.nsmax;
     P.tmem_cols = g.tmem_cols;
+    P.nacc = g.nacc;
     P.maxit = 1;
     P.slots = slots;
     P.err = flags;
     P.active = flags + 16;
     P.ndone = flags + 32;
     P.iters = flags + 48;
+    P.owners = reinterpret_cast<int4*>(flags + 64);
     int rc = FL_OK;
-    if (!make_map(&P.tmA[0][0], S_dev, n, n, lds, BM) ||
-        (nslices > 1 && !make_map(&P.tmA[0][1], (const uint16_t*)S_dev + n * lds, n, n, lds, BM)) ||
-        !make_map(&P.tmP[0], pd.P, 2 * nrhs, n, pd.ldv, 2 * nrhs)) {
-        rc = FL_EINVAL;
-    } else {
+    {
         const int one = 1;
-        cudaMemsetAsync(flags, 0, 256, st);
+        cudaMemsetAsync(flags, 0, 256 + (size_t)pd.mtiles * sizeof(int4), st);
         cudaMemcpyAsync(P.active, &one, sizeof(int), cudaMemcpyHostToDevice, st);
-        split_vec_kernel<<<dim3(16, nrhs), 256, 0, st>>>((int)n, nrhs, pd.ldv, pd.mtiles * BM, X_dev, ldx, pd.P);
+        split_vec_kernel<<<dim3(16, nrhs), 256, 0, st>>>((int)n, nrhs, pd.chunks * BK, X_dev, ldx, pd.P);
         fl::count_launch();
         if (!launch_cfg((const void*)gemm_kernel, g.smem)) {
             rc = FL_ECUDA;
@@ -1145,7 +1344,7 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
         return set_err(h, FL_EINVAL, "bad batch options");
     for (int p = 0; p < nprob; ++p) {
         const fl_batch_problem& q = probs[p];
-        if (q.n < 1 || q.n > 65536 || !q.A_dev || q.lda < q.n || !q.S_dev || q.lds < q.n || (q.lds % 8) != 0 ||
+        if (q.n < 1 || q.n > 65536 || !q.A_dev || q.lda < q.n || !q.S_dev ||
             (q.nslices != 1 && q.nslices != 2) || !q.dscale_dev || q.nrhs < 1 || q.nrhs > 128 || !q.B_dev ||
             q.ldb < q.nrhs || !q.U_dev || q.ldu < q.nrhs || ((uintptr_t)q.S_dev & 15) != 0)
             return set_err(h, FL_EINVAL, "bad batch problem " + std::to_string(p));
@@ -1167,6 +1366,7 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
         d.mtiles = (d.n + BM - 1) / BM;
         d.chunks = (d.n + BK - 1) / BK;
         d.ldv = round_up((int64_t)d.mtiles * BM, 64);
+        d.ngroups = (d.mtiles + VT - 1) / VT;
     }
     Geometry g;
     if (!geometry(pd, sms, o.ctas, o.stages, g)) return set_err(h, FL_EINVAL, "no pipeline fits shared memory");
@@ -1181,7 +1381,8 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
     g.G = std::min(g.G, sms * per_sm);
 
     // workspace layout
-    std::vector<size_t> off_vec(nprob), off_P(nprob), off_col(nprob), off_R(nprob), off_rp(nprob), off_co(nprob);
+    std::vector<size_t> off_vec(nprob), off_P(nprob), off_col(nprob), off_R(nprob), off_rp(nprob), off_co(nprob),
+        off_part(nprob);
     size_t total = 0;
     auto take = [&](size_t bytes) {
         const size_t at = total;
@@ -1190,15 +1391,21 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
     };
     for (int p = 0; p < nprob; ++p) {
         const ProbDev& d = pd[p];
-        off_vec[p] = take((size_t)4 * d.nr * d.ldv * sizeof(float));
-        off_P[p] = take((size_t)2 * d.nr * d.ldv * sizeof(__nv_bfloat16));
+        off_vec[p] = take((size_t)5 * d.nr * d.ldv * sizeof(float));
+        // P tiles for every row the vector phases write (mtiles * 128 rows = 2 mtiles chunks)
+        off_P[p] = take((size_t)2 * d.mtiles * 2 * d.nr * BK * sizeof(__nv_bfloat16));
         off_col[p] = take((size_t)d.nr * sizeof(ColState));
         off_R[p] = take((size_t)d.n * d.nr * sizeof(double));
         off_rp[p] = take((size_t)((d.n + RES_ROWS - 1) / RES_ROWS) * d.nr * sizeof(double));
         off_co[p] = take((size_t)d.nr * sizeof(ColOuter));
+        off_part[p] = take((size_t)2 * d.nr * d.ngroups * sizeof(float));
     }
     const size_t off_slots = take((size_t)g.G * g.rmax * g.nrmax * BM * sizeof(float));
     const size_t off_flags = take(256);
+    const size_t off_bar = take(256);
+    int ntiles = 0;
+    for (const ProbDev& d : pd) ntiles += d.mtiles;
+    const size_t off_owners = take((size_t)ntiles * sizeof(int4));
     // double-float residual: grid, run bound and partial tiles
     int df_G = 0, df_rmax = 0;
     size_t off_df = 0;
@@ -1251,14 +1458,16 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
     P.nrmax = g.nrmax;
     P.nsmax = g.nsmax;
     P.tmem_cols = g.tmem_cols;
+    P.nacc = g.nacc;
     P.maxit = o.inner_maxit;
     P.tol2 = o.inner_tol * o.inner_tol;
     P.slots = (float*)(W + off_slots);
     P.err = flags;
-    P.gbar = (unsigned*)(flags + 2);
+    P.gbar = (unsigned*)(W + off_bar);
     P.ndone = flags + 8;
     P.active = flags + 24;
     P.iters = flags + 4;
+    P.owners = reinterpret_cast<int4*>(W + off_owners);
     RP.nprob = nprob;
     for (int p = 0; p < nprob; ++p) {
         ProbDev& d = pd[p];
@@ -1267,14 +1476,14 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
         d.z = v + (size_t)d.nr * d.ldv;
         d.p = v + (size_t)2 * d.nr * d.ldv;
         d.q = v + (size_t)3 * d.nr * d.ldv;
+        d.sv = v + (size_t)4 * d.nr * d.ldv;
         d.P = (__nv_bfloat16*)(W + off_P[p]);
+        d.S = (const uint8_t*)probs[p].S_dev;
         d.col = (ColState*)(W + off_col[p]);
+        d.pq = (float*)(W + off_part[p]);
+        d.rq = d.pq + (size_t)d.nr * d.ngroups;
         P.prob[p] = d;
         const fl_batch_problem& q = probs[p];
-        if (!make_map(&P.tmA[p][0], q.S_dev, q.n, q.n, q.lds, BM) ||
-            (q.nslices > 1 && !make_map(&P.tmA[p][1], (const uint16_t*)q.S_dev + q.n * q.lds, q.n, q.n, q.lds, BM)) ||
-            !make_map(&P.tmP[p], d.P, 2 * d.nr, d.n, d.ldv, 2 * d.nr))
-            return set_err(h, FL_EINVAL, "tensor map of problem " + std::to_string(p));
         RefProb& r = RP.prob[p];
         r.n = d.n;
         r.nrhs = q.nrhs;
@@ -1372,6 +1581,7 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
             break;
         }
         if (last) break;
+        if (cudaMemsetAsync(P.gbar, 0, sizeof(unsigned), st) != cudaSuccess) return set_err(h, FL_ECUDA, "memset");
         void* args[] = {(void*)&P};
         const cudaError_t e =
             cudaLaunchCooperativeKernel((const void*)cg_kernel, dim3(g.G), dim3(THREADS), args, g.smem, st);

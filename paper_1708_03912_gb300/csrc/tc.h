@@ -1,9 +1,8 @@
-// Blackwell (sm_103a) primitives written as inline PTX: mbarriers, TMA tile loads,
-// tensor-memory allocation and the tcgen05 matrix-multiply-accumulate with its
+// Blackwell (sm_103a) primitives written as inline PTX: mbarriers, bulk (TMA)
+// copies, tensor-memory allocation and the tcgen05 matrix-multiply-accumulate with its
 // shared-memory and instruction descriptors.  Every wait is bounded by the
 // global timer and reports a timeout instead of spinning forever.
 #pragma once
-#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -59,19 +58,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return true;
 }
 
-// --------------------------------------------------------------------- TMA --
-__device__ __forceinline__ void tma_prefetch(const CUtensorMap* tm) {
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
-}
-// 2D tile load: box at element coordinates (x = inner, y = outer) into shared memory,
-// completion signalled as transaction bytes on `bar`.  x * element size must be a
-// multiple of 16 bytes.
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar,
-                                            uint64_t policy) {
+// -------------------------------------------------------------- bulk copy --
+// Contiguous bulk copy global -> shared (16-byte aligned addresses, size a multiple
+// of 16), completion signalled as transaction bytes on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                          uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_addr(bar)), "l"(policy)
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_addr(dst)),
+        "l"((uint64_t)__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
         : "memory");
 }
 __device__ __forceinline__ uint64_t policy_evict_first() {
@@ -84,7 +79,7 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
-// order this thread's earlier generic-proxy global writes before later async-proxy (TMA) reads
+// order this thread's earlier generic-proxy global writes before later async-proxy (bulk copy) reads
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
@@ -117,8 +112,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 // Shared-memory matrix descriptor of a K-major operand tile stored as rows of
-// 128 bytes with the 128-byte swizzle (as written by a TMA load with
-// CU_TENSOR_MAP_SWIZZLE_128B): start address >> 4 in [0,14), leading offset
+// 128 bytes with the 128-byte swizzle (16-byte unit u of row r at unit position
+// u XOR (r mod 8)): start address >> 4 in [0,14), leading offset
 // (unused for this layout, 16 bytes) in [16,30), stride between 8-row groups
 // (1024 bytes) >> 4 in [32,46), descriptor version 1 at bit 46, swizzle mode 2
 // (128 B) in [61,64).  The tile must start on a 1024-byte boundary; the k-th
@@ -160,31 +155,32 @@ __device__ __forceinline__ void tmem_wait_ld() {
 }
 
 // ------------------------------------------------------------ grid barrier --
-// Sense-counting barrier over all blocks of a co-resident (cooperative) grid.
-// bar[0] counts arrivals, bar[1] is the generation.  Bounded: on timeout sets
-// bit 2 of *err and returns false (the caller then winds down).
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+// Barrier over all blocks of a co-resident (cooperative) grid on a monotone arrival
+// counter (zero at launch, on a cache line of its own): barrier number `epoch` is
+// passed when the counter reaches epoch * nblocks.  Arrival is a fire-and-forget
+// release add; the wait polls with acquire loads.  Bounded: on timeout sets bit 2 of
+// *err and returns false (the caller then winds down).
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& epoch, unsigned nblocks, int* err) {
     __syncthreads();
     __shared__ int ok_s;
+    ++epoch;
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned* vgen = bar + 1;
-        const unsigned gen = *vgen;
         __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+        const unsigned target = epoch * nblocks;
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+        if ((int)(v - target) < 0) {
             const uint64_t t0 = globaltimer();
-            while (*vgen == gen) {
+            do {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
                 if (globaltimer() - t0 > WAIT_LIMIT_NS) {
                     atomicOr(err, 4);
                     ok = 0;
                     break;
                 }
-            }
+            } while ((int)(v - target) < 0);
         }
         __threadfence();
         ok_s = ok;

@@ -25,7 +25,7 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
 EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
            "fl_assemble", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
            "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_matvec_f32_static",
-           "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve"]
+           "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve"]
 FL_STATIC_MAX_N = 65536
 FL_BATCH_MAXPROB = 8
 FL_RESID_F64, FL_RESID_DF = 0, 1
@@ -62,7 +62,7 @@ class fl_solve_info(ctypes.Structure):
 
 class fl_batch_problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("A_dev", ctypes.c_void_p), ("lda", ctypes.c_int64),
-                ("S_dev", ctypes.c_void_p), ("lds", ctypes.c_int64), ("nslices", ctypes.c_int),
+                ("S_dev", ctypes.c_void_p), ("nslices", ctypes.c_int),
                 ("dscale_dev", ctypes.c_void_p), ("nrhs", ctypes.c_int), ("B_dev", ctypes.c_void_p),
                 ("ldb", ctypes.c_int64), ("U_dev", ctypes.c_void_p), ("ldu", ctypes.c_int64)]
 
@@ -124,9 +124,11 @@ def lib():
     L.fl_launch_count.restype = ctypes.c_uint64
     L.fl_matvec_f32_static.argtypes = [vp, i64, i64, vp, vp, vp]
     L.fl_matvec_f32_static.restype = ci
-    L.fl_split_bf16.argtypes = [vp, i64, i64, ci, vp, i64, vp, vp]
+    L.fl_split_bf16_bytes.argtypes = [i64, ci]
+    L.fl_split_bf16_bytes.restype = i64
+    L.fl_split_bf16.argtypes = [vp, i64, i64, ci, vp, vp, vp]
     L.fl_split_bf16.restype = ci
-    L.fl_matmul_bf16.argtypes = [vp, i64, i64, ci, ci, vp, i64, vp, i64, vp]
+    L.fl_matmul_bf16.argtypes = [vp, i64, ci, ci, vp, i64, vp, i64, vp]
     L.fl_matmul_bf16.restype = ci
     L.fl_default_batch_opts.argtypes = [ctypes.POINTER(fl_batch_opts)]
     L.fl_default_batch_opts.restype = None
@@ -260,18 +262,33 @@ def fl_matvec_f32_static(A32, x, y, stream=None):
     return lib().fl_matvec_f32_static(_ptr(A32), A32.stride(0), A32.shape[0], _ptr(x), _ptr(y), _stream(stream))
 
 
+def fl_split_bf16_bytes(n, nslices):
+    return int(lib().fl_split_bf16_bytes(n, nslices))
+
+
 def fl_split_bf16(A, nslices, S, dscale, stream=None):
-    """A: float64 [n, lda]; S: bf16 CUDA tensor [nslices * n, lds] (slices stacked by rows);
-    dscale: float64 [n]."""
+    """A: float64 [n, lda]; S: CUDA tensor of at least fl_split_bf16_bytes(n, nslices) bytes
+    (tiled layout, see fraclap.h); dscale: float64 [n]."""
     n = A.shape[0]
-    _check(lib().fl_split_bf16(_ptr(A), A.stride(0), n, nslices, _ptr(S), S.stride(0), _ptr(dscale),
-                               _stream(stream)))
+    assert S.numel() * S.element_size() >= fl_split_bf16_bytes(n, nslices)
+    _check(lib().fl_split_bf16(_ptr(A), A.stride(0), n, nslices, _ptr(S), _ptr(dscale), _stream(stream)))
+
+
+def split_bf16(A, nslices=2, stream=None):
+    """Allocate and fill the slices of A: returns (S as a uint8 CUDA tensor, dscale)."""
+    import torch
+
+    n = A.shape[0]
+    S = torch.empty(fl_split_bf16_bytes(n, nslices), dtype=torch.uint8, device=A.device)
+    d = torch.empty(n, dtype=torch.float64, device=A.device)
+    fl_split_bf16(A, nslices, S, d, stream)
+    return S, d
 
 
 def fl_matmul_bf16(S, n, nslices, X, Y, stream=None):
     """S from fl_split_bf16; X, Y: float32 CUDA tensors [nrhs, n] (one right-hand side per row)."""
-    _check(lib().fl_matmul_bf16(_ptr(S), S.stride(0), n, nslices, X.shape[0], _ptr(X), X.stride(0), _ptr(Y),
-                                Y.stride(0), _stream(stream)))
+    _check(lib().fl_matmul_bf16(_ptr(S), n, nslices, X.shape[0], _ptr(X), X.stride(0), _ptr(Y), Y.stride(0),
+                                _stream(stream)))
 
 
 def fl_default_batch_opts():
@@ -288,7 +305,7 @@ def fl_batch_solve(h, problems, opts=None, stream=None):
     total = 0
     for k, q in enumerate(problems):
         A, S, B, U = q["A"], q["S"], q["B"], q["U"]
-        arr[k] = fl_batch_problem(A.shape[0], A.data_ptr(), A.stride(0), S.data_ptr(), S.stride(0), q["nslices"],
+        arr[k] = fl_batch_problem(A.shape[0], A.data_ptr(), A.stride(0), S.data_ptr(), q["nslices"],
                                   q["dscale"].data_ptr(), B.shape[1], B.data_ptr(), B.stride(0), U.data_ptr(),
                                   U.stride(0))
         total += B.shape[1]
