@@ -277,6 +277,38 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
                    fl_batch_info* info, double* rel_residual_host, int* status_host, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Autotuning (no counterpart in the paper): launch shapes measured on the
+ * running device, kept in a process-wide table keyed by (kernel, n, nrhs,
+ * nslices) and the device name, consulted when a launch parameter is left at
+ * 0, persisted as JSON.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Sweep the pipeline depth (2 .. what shared memory holds) and the CTA count
+ * (the SM count and a few smaller grids) of the tensor-core product of
+ * fl_batch_solve on these problems' slices (timed with CUDA events, median of
+ * `reps` launches after one warm-up, inputs of zero), record the fastest as
+ * kernel "batch_gemm" with p0 = stages, p1 = CTAs under key (max n, max nrhs
+ * rounded up to 16, max nslices), and return it in *best (other fields at
+ * their defaults) and its time in *best_ms.  Only S_dev, n, nslices and nrhs of
+ * the problems are used.  Synchronous.  Errors: FL_EINVAL, FL_ENOMEM,
+ * FL_ECUDA, FL_ETIMEOUT.
+ */
+int fl_tune_batch(fl_handle h, int nprob, const fl_batch_problem* probs, int reps, fl_batch_opts* best,
+                  double* best_ms);
+
+/* Add or replace a table entry for the current device (p0, p1: the kernel's two parameters). */
+int fl_tune_record(const char* kernel, int64_t n, int nrhs, int nslices, int p0, int p1, double ms);
+/* FL_OK and the parameters if the current device has an entry, else FL_ENOTIMPL. */
+int fl_tune_lookup(const char* kernel, int64_t n, int nrhs, int nslices, int* p0, int* p1);
+void fl_tune_clear(void);
+int fl_tune_count(void);
+/* Write / merge the table as JSON: {"entries": [{"device", "kernel", "n", "nrhs", "nslices",
+   "p0", "p1", "ms"}, ...]}.  FL_EINVAL on I/O or format errors. */
+int fl_tune_save(const char* path);
+int fl_tune_load(const char* path);
+
+/* ------------------------------------------------------------------------
  * Measurement hooks (no counterpart in the paper): plan statistics, per-stage
  * device times of fl_assemble, and a count of kernel launches.
  * ------------------------------------------------------------------------ */

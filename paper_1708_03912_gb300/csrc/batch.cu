@@ -1320,6 +1320,140 @@ int fl_matmul_bf16(const void* S_dev, int64_t n, int nslices, int nrhs, const fl
     return rc;
 }
 
+int fl_tune_batch(fl_handle h, int nprob, const fl_batch_problem* probs, int reps, fl_batch_opts* best,
+                  double* best_ms) {
+    if (!h) return FL_EINVAL;
+    h->err.clear();
+    if (nprob < 1 || nprob > MAXP || !probs || reps < 1) return set_err(h, FL_EINVAL, "bad tuning arguments");
+    int sms = 0;
+    if (cudaSetDevice(h->device) != cudaSuccess) return set_err(h, FL_ECUDA, "cudaSetDevice");
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    std::vector<ProbDev> pd(nprob);
+    size_t pbytes_total = 0;
+    int nmx = 0, nrx = 0, nsx = 0;
+    for (int p = 0; p < nprob; ++p) {
+        const fl_batch_problem& q = probs[p];
+        if (q.n < 1 || q.n > 65536 || !q.S_dev || (q.nslices != 1 && q.nslices != 2) || q.nrhs < 1 || q.nrhs > 128)
+            return set_err(h, FL_EINVAL, "bad batch problem " + std::to_string(p));
+        ProbDev& d = pd[p];
+        d.n = (int)q.n;
+        d.nr = round_up(q.nrhs, 16);
+        d.nslices = q.nslices;
+        d.mtiles = (d.n + BM - 1) / BM;
+        d.chunks = (d.n + BK - 1) / BK;
+        d.S = (const uint8_t*)q.S_dev;
+        pbytes_total += (size_t)2 * d.mtiles * 2 * d.nr * BK * 2;
+        nmx = std::max(nmx, d.n);
+        nrx = std::max(nrx, d.nr);
+        nsx = std::max(nsx, d.nslices);
+    }
+    Geometry g0;
+    if (!geometry(pd, sms, 0, 0, g0)) return set_err(h, FL_EINVAL, "no pipeline fits shared memory");
+    int ntiles = 0;
+    for (const ProbDev& d : pd) ntiles += d.mtiles;
+    // scratch: P tiles (zero), run slots for the largest grid, flags and owner table
+    const size_t slot_bytes = (size_t)sms * (g0.rmax + 2) * g0.nrmax * BM * sizeof(float);
+    const size_t flag_bytes = 256 + (size_t)ntiles * sizeof(int4);
+    char* ws = nullptr;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return set_err(h, FL_ECUDA, "stream");
+    if (cudaMalloc((void**)&ws, pbytes_total + slot_bytes + flag_bytes + 1024) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamDestroy(st);
+        return set_err(h, FL_ENOMEM, "tuning scratch");
+    }
+    cudaMemsetAsync(ws, 0, pbytes_total + slot_bytes + flag_bytes + 1024, st);
+    char* c = ws;
+    for (ProbDev& d : pd) {
+        d.P = (__nv_bfloat16*)c;
+        c += ((size_t)2 * d.mtiles * 2 * d.nr * BK * 2 + 255) & ~size_t(255);
+    }
+    float* slots = (float*)c;
+    int* flags = (int*)(c + ((slot_bytes + 255) & ~size_t(255)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<int> ctas = {sms, sms - 4, sms - 8, sms - 16, (3 * sms) / 4, sms / 2};
+    int best_st = g0.stages, best_ct = sms, rc = FL_OK;
+    float best_t = 1e30f;
+    static Params P;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int stg = 2; stg <= g0.stages && rc == FL_OK; ++stg) {
+        for (int ct : ctas) {
+            if (ct < 1) continue;
+            Geometry g;
+            if (!geometry(pd, sms, ct, stg, g)) continue;
+            if (g.rmax > g0.rmax + 2) continue;  // slot scratch sized for the default grid
+            memset(&P, 0, sizeof(P));
+            P.nprob = nprob;
+            for (int p = 0; p < nprob; ++p) P.prob[p] = pd[p];
+            P.stages = g.stages;
+            P.rmax = g.rmax;
+            P.nrmax = g.nrmax;
+            P.nsmax = g.nsmax;
+            P.tmem_cols = g.tmem_cols;
+            P.nacc = g.nacc;
+            P.maxit = 1;
+            P.slots = slots;
+            P.err = flags;
+            P.active = flags + 16;
+            P.ndone = flags + 32;
+            P.iters = flags + 48;
+            P.owners = reinterpret_cast<int4*>(flags + 64);
+            std::vector<int> one(MAXP, 0);
+            for (int p = 0; p < nprob; ++p) one[p] = 1;
+            cudaMemcpyAsync(P.active, one.data(), MAXP * sizeof(int), cudaMemcpyHostToDevice, st);
+            if (!launch_cfg((const void*)gemm_kernel, g.smem)) {
+                rc = FL_ECUDA;
+                break;
+            }
+            std::vector<float> ts;
+            for (int r = 0; r <= reps; ++r) {
+                cudaEventRecord(e0, st);
+                gemm_kernel<<<g.G, THREADS, g.smem, st>>>(P);
+                cudaEventRecord(e1, st);
+                fl::count_launch();
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = FL_ECUDA;
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0) ts.push_back(ms);  // the first launch warms up
+            }
+            if (rc != FL_OK) break;
+            int err = 0;
+            cudaMemcpyAsync(&err, flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+            cudaStreamSynchronize(st);
+            if (err != 0) {
+                rc = FL_ETIMEOUT;
+                break;
+            }
+            std::sort(ts.begin(), ts.end());
+            const float med = ts[ts.size() / 2];
+            if (med < best_t) {
+                best_t = med;
+                best_st = g.stages;
+                best_ct = g.G;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(ws);
+    cudaStreamDestroy(st);
+    if (rc != FL_OK) return set_err(h, rc, "tuning launch failed");
+    tune_record(device_name(), "batch_gemm", nmx, nrx, nsx, best_st, best_ct, best_t);
+    if (best) {
+        fl_default_batch_opts(best);
+        best->stages = best_st;
+        best->ctas = best_ct;
+    }
+    if (best_ms) *best_ms = best_t;
+    return FL_OK;
+}
+
 void fl_default_batch_opts(fl_batch_opts* o) {
     if (!o) return;
     o->tol = 1e-8;
@@ -1368,8 +1502,21 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
         d.ldv = round_up((int64_t)d.mtiles * BM, 64);
         d.ngroups = (d.mtiles + VT - 1) / VT;
     }
+    int want_ctas = o.ctas, want_stages = o.stages;
+    if (want_ctas == 0 && want_stages == 0) {  // launch shape from the tuning table, if measured
+        int nmx = 0, nrx = 0, nsx = 0, st0 = 0, ct0 = 0;
+        for (const ProbDev& d : pd) {
+            nmx = std::max(nmx, d.n);
+            nrx = std::max(nrx, d.nr);
+            nsx = std::max(nsx, d.nslices);
+        }
+        if (tune_lookup(device_name(), "batch_gemm", nmx, nrx, nsx, &st0, &ct0)) {
+            want_stages = st0;
+            want_ctas = ct0;
+        }
+    }
     Geometry g;
-    if (!geometry(pd, sms, o.ctas, o.stages, g)) return set_err(h, FL_EINVAL, "no pipeline fits shared memory");
+    if (!geometry(pd, sms, want_ctas, want_stages, g)) return set_err(h, FL_EINVAL, "no pipeline fits shared memory");
     int per_sm = 0;
     if (!launch_cfg((const void*)cg_kernel, g.smem) ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)cg_kernel, THREADS, g.smem) !=

@@ -115,4 +115,10 @@ void count_launch(int n = 1);
 // returns plan index for order s (building it on demand); -1 on error (h->err set)
 int plan_for(fl_ctx* h, double s);
 int set_err(fl_ctx* h, int code, const std::string& msg);
+// tuning table (tune.cpp)
+std::string device_name();
+void tune_record(const std::string& device, const std::string& kernel, int64_t n, int nrhs, int nslices, int p0,
+                 int p1, double ms);
+bool tune_lookup(const std::string& device, const std::string& kernel, int64_t n, int nrhs, int nslices, int* p0,
+                 int* p1);
 }  // namespace fl

@@ -25,7 +25,9 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
 EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
            "fl_assemble", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
            "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_matvec_f32_static",
-           "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve"]
+           "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
+           "fl_tune_batch", "fl_tune_record", "fl_tune_lookup", "fl_tune_clear", "fl_tune_count", "fl_tune_save",
+           "fl_tune_load"]
 FL_STATIC_MAX_N = 65536
 FL_BATCH_MAXPROB = 8
 FL_RESID_F64, FL_RESID_DF = 0, 1
@@ -135,6 +137,21 @@ def lib():
     L.fl_batch_solve.argtypes = [vp, ci, ctypes.POINTER(fl_batch_problem), ctypes.POINTER(fl_batch_opts),
                                  ctypes.POINTER(fl_batch_info), vp, vp, vp]
     L.fl_batch_solve.restype = ci
+    L.fl_tune_batch.argtypes = [vp, ci, ctypes.POINTER(fl_batch_problem), ci, ctypes.POINTER(fl_batch_opts),
+                                ctypes.POINTER(dbl)]
+    L.fl_tune_batch.restype = ci
+    L.fl_tune_record.argtypes = [ctypes.c_char_p, i64, ci, ci, ci, ci, dbl]
+    L.fl_tune_record.restype = ci
+    L.fl_tune_lookup.argtypes = [ctypes.c_char_p, i64, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    L.fl_tune_lookup.restype = ci
+    L.fl_tune_clear.argtypes = []
+    L.fl_tune_clear.restype = None
+    L.fl_tune_count.argtypes = []
+    L.fl_tune_count.restype = ci
+    L.fl_tune_save.argtypes = [ctypes.c_char_p]
+    L.fl_tune_save.restype = ci
+    L.fl_tune_load.argtypes = [ctypes.c_char_p]
+    L.fl_tune_load.restype = ci
     _ = i32
     _lib = L
     return L
@@ -295,6 +312,54 @@ def fl_default_batch_opts():
     o = fl_batch_opts()
     lib().fl_default_batch_opts(ctypes.byref(o))
     return o
+
+
+def _batch_array(problems):
+    arr = (fl_batch_problem * len(problems))()
+    for k, q in enumerate(problems):
+        A, S, B, U = q.get("A"), q["S"], q["B"], q.get("U")
+        arr[k] = fl_batch_problem(A.shape[0] if A is not None else q["n"],
+                                  A.data_ptr() if A is not None else None, A.stride(0) if A is not None else 0,
+                                  S.data_ptr(), q["nslices"], q["dscale"].data_ptr() if "dscale" in q else None,
+                                  B.shape[1], B.data_ptr(), B.stride(0), U.data_ptr() if U is not None else None,
+                                  U.stride(0) if U is not None else 0)
+    return arr
+
+
+def fl_tune_batch(h, problems, reps=5):
+    """Autotune the batched tensor-core product on these problems; returns (fl_batch_opts, ms)."""
+    arr = _batch_array(problems)
+    best = fl_batch_opts()
+    ms = ctypes.c_double()
+    _check(lib().fl_tune_batch(h, len(problems), arr, reps, ctypes.byref(best), ctypes.byref(ms)), h)
+    return best, ms.value
+
+
+def fl_tune_record(kernel, n, nrhs, nslices, p0, p1, ms):
+    _check(lib().fl_tune_record(kernel.encode(), n, nrhs, nslices, p0, p1, ms))
+
+
+def fl_tune_lookup(kernel, n, nrhs, nslices):
+    """(p0, p1) or None."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    r = lib().fl_tune_lookup(kernel.encode(), n, nrhs, nslices, ctypes.byref(a), ctypes.byref(b))
+    return (a.value, b.value) if r == FL_OK else None
+
+
+def fl_tune_clear():
+    lib().fl_tune_clear()
+
+
+def fl_tune_count():
+    return int(lib().fl_tune_count())
+
+
+def fl_tune_save(path):
+    _check(lib().fl_tune_save(os.fspath(path).encode()))
+
+
+def fl_tune_load(path):
+    _check(lib().fl_tune_load(os.fspath(path).encode()))
 
 
 def fl_batch_solve(h, problems, opts=None, stream=None):

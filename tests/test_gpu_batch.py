@@ -207,3 +207,20 @@ def test_reported_residual_matches_float64(disc10, mode):
     dev = np.abs(rel - rel_host)
     print(f"{mode}: max |rel - rel_host| = {dev.max():.2e}, max floor {floor.max():.2e}")
     assert np.all(dev <= 1e-3 * rel_host + floor)
+
+
+def test_autotuner_feeds_the_solver(disc10):
+    V, T, A = disc10
+    rng = np.random.default_rng(4)
+    q = _problem(A, rng.standard_normal((A.shape[0], 32)), 2)
+    h = F.fl_create(V, T)
+    F.fl_tune_clear()
+    best, ms = F.fl_tune_batch(h, [q], reps=3)
+    assert 2 <= best.stages <= 8 and 1 <= best.ctas and ms > 0
+    assert F.fl_tune_lookup("batch_gemm", A.shape[0], 32, 2) == (best.stages, best.ctas)
+    o = F.fl_default_batch_opts()
+    o.tol = 1e-10
+    r, info, rel, st = F.fl_batch_solve(h, [q], o)
+    assert r == F.FL_OK and (info.stages, info.ctas) == (best.stages, best.ctas)
+    F.fl_tune_clear()
+    F.fl_destroy(h)
