@@ -192,6 +192,18 @@ def _nvb_refine(V, T, marked):
     return np.array(V, dtype=np.float64), np.array(T2, dtype=np.int64)
 
 
+def bisect_all(V, T, rounds: int = 1):
+    """Nested refinement: every triangle bisected by newest-vertex bisection, `rounds` times
+    (two rounds halve the mesh size)."""
+    V = np.asarray(V, dtype=np.float64)
+    T = np.asarray(T)
+    for _ in range(rounds):
+        V, T = _nvb_refine(V, T, list(range(len(T))))
+        V = np.asarray(V, dtype=np.float64)
+        T = np.asarray(T)
+    return V, T.astype(np.int32)
+
+
 def lshape(h0: float = 0.25, levels: int = 0):
     """L-shaped domain [0,2]^2 minus [1,2]^2 (Section 7.3), refined towards the
     re-entrant corner (1,1) and the boundary by newest-vertex bisection.
