@@ -277,6 +277,52 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
                    fl_batch_info* info, double* rel_residual_host, int* status_host, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Multigrid (Section 5 proposes multigrid for these dense systems; no algorithm is
+ * given, this is the Galerkin V-cycle on nested meshes).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Prolongation from the coarse mesh's DOFs to the fine mesh's DOFs for order s:
+ * P_ij = (coarse hat function j)(fine DOF vertex i), exact when the fine mesh is a
+ * refinement of the coarse one.  Host CSR (rows = fine DOFs): call first with
+ * rowptr = col = val = NULL to get *nnz, then with arrays of n_fine + 1, nnz, nnz.
+ * Errors: FL_EINVAL (dimensions differ, a fine vertex outside the coarse mesh).
+ */
+int fl_prolongation(fl_handle fine, fl_handle coarse, double s, int64_t* nnz, int32_t* rowptr, int32_t* col,
+                    double* val);
+
+typedef struct fl_mg* fl_mg_handle;
+
+/* Start a hierarchy on the finest operator A_dev (float64, n x n, row pitch lda; not
+   copied: it must outlive the handle). */
+int fl_mg_create(fl_mg_handle* mg, const double* A_dev, int64_t lda, int64_t n);
+/* Add a coarser level: P (host CSR, rows = DOFs of the current coarsest level, nc
+   columns) from fl_prolongation; forms A_c = P^T A P on the device in float64.
+   Synchronises `stream`. */
+int fl_mg_add_level(fl_mg_handle mg, int64_t nc, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                    const double* val, void* stream);
+/* Float32 level copies, Jacobi weights w = 4 / (3 lambda) (lambda: ten power-iteration
+   steps on D^-1 A from (1, ..., 1), then |D^-1 A x| / |x|), the explicit inverse of the
+   coarsest operator (Gauss-Jordan, float64); nu smoothing steps before and after the
+   coarse correction.  Synchronises `stream`. */
+int fl_mg_setup(fl_mg_handle mg, int nu, void* stream);
+/* Order, float64 operator (device, owned by mg for level > 0) and its row pitch of a level. */
+int fl_mg_level(fl_mg_handle mg, int level, int64_t* n, const double** A_dev, int64_t* lda);
+/* Copy a level's float64 operator into dst_dev[n][ldd] (device). */
+int fl_mg_level_copy(fl_mg_handle mg, int level, double* dst_dev, int64_t ldd, void* stream);
+/* The Jacobi weight of a level (after fl_mg_setup). */
+int fl_mg_omega(fl_mg_handle mg, int level, float* omega);
+/* z = V(r): one V-cycle from zero on the finest level, float32 device vectors [n]. */
+int fl_mg_vcycle(fl_mg_handle mg, const float* r_dev, float* z_dev, void* stream);
+/* Conjugate gradients on the finest operator preconditioned by one V-cycle per step,
+   from u = 0, until ||b - A u|| <= tol ||b|| (recursive residual, float64).
+   Returns FL_OK, FL_ENOTCONV or FL_ENOTSPD; info as for fl_solve. */
+int fl_mg_solve(fl_mg_handle mg, const double* b_dev, double* u_dev, double tol, int maxit, fl_solve_info* info,
+                void* stream);
+const char* fl_mg_last_error(fl_mg_handle mg);
+void fl_mg_destroy(fl_mg_handle mg);
+
+/* ------------------------------------------------------------------------
  * Autotuning (no counterpart in the paper): launch shapes measured on the
  * running device, kept in a process-wide table keyed by (kernel, n, nrhs,
  * nslices) and the device name, consulted when a launch parameter is left at

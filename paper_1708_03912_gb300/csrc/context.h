@@ -115,6 +115,10 @@ void count_launch(int n = 1);
 // returns plan index for order s (building it on demand); -1 on error (h->err set)
 int plan_for(fl_ctx* h, double s);
 int set_err(fl_ctx* h, int code, const std::string& msg);
+// y = A x for a dense matrix of type dtype (linalg.cu); x, y float64 with strides; xf: n floats of
+// scratch for the float32 copy of x (unused for FL_F64)
+cudaError_t gemv(int dtype, const void* A, int64_t lda, int64_t n, const double* x, int64_t incx, double* y,
+                 int64_t incy, float* xf, cudaStream_t st, bool xf_ready = false);
 // tuning table (tune.cpp)
 std::string device_name();
 void tune_record(const std::string& device, const std::string& kernel, int64_t n, int nrhs, int nslices, int p0,

@@ -167,8 +167,8 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 // y = A x for one right-hand side; xf is a float32 scratch copy of x (n) for low-precision A
 // xf_ready: xf already holds x rounded to float32 (the CG keeps such a copy of p)
-static cudaError_t gemv(int dtype, const void* A, int64_t lda, int64_t n, const double* x, int64_t incx, double* y,
-                        int64_t incy, float* xf, cudaStream_t st, bool xf_ready = false) {
+cudaError_t gemv(int dtype, const void* A, int64_t lda, int64_t n, const double* x, int64_t incx, double* y,
+                 int64_t incy, float* xf, cudaStream_t st, bool xf_ready) {
     const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
     if (dtype == FL_F64) {
         const int vec = (((uintptr_t)A & 7u) == 0) && aligned16(x);

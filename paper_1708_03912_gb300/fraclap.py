@@ -27,7 +27,8 @@ EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl
            "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_matvec_f32_static",
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
            "fl_tune_batch", "fl_tune_record", "fl_tune_lookup", "fl_tune_clear", "fl_tune_count", "fl_tune_save",
-           "fl_tune_load"]
+           "fl_tune_load", "fl_prolongation", "fl_mg_create", "fl_mg_add_level", "fl_mg_setup", "fl_mg_level", "fl_mg_level_copy",
+           "fl_mg_omega", "fl_mg_vcycle", "fl_mg_solve", "fl_mg_last_error", "fl_mg_destroy"]
 FL_STATIC_MAX_N = 65536
 FL_BATCH_MAXPROB = 8
 FL_RESID_F64, FL_RESID_DF = 0, 1
@@ -152,6 +153,28 @@ def lib():
     L.fl_tune_save.restype = ci
     L.fl_tune_load.argtypes = [ctypes.c_char_p]
     L.fl_tune_load.restype = ci
+    L.fl_prolongation.argtypes = [vp, vp, dbl, ctypes.POINTER(i64), vp, vp, vp]
+    L.fl_prolongation.restype = ci
+    L.fl_mg_create.argtypes = [ctypes.POINTER(vp), vp, i64, i64]
+    L.fl_mg_create.restype = ci
+    L.fl_mg_add_level.argtypes = [vp, i64, i64, vp, vp, vp, vp]
+    L.fl_mg_add_level.restype = ci
+    L.fl_mg_setup.argtypes = [vp, ci, vp]
+    L.fl_mg_setup.restype = ci
+    L.fl_mg_level.argtypes = [vp, ci, ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.POINTER(i64)]
+    L.fl_mg_level.restype = ci
+    L.fl_mg_level_copy.argtypes = [vp, ci, vp, i64, vp]
+    L.fl_mg_level_copy.restype = ci
+    L.fl_mg_omega.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_float)]
+    L.fl_mg_omega.restype = ci
+    L.fl_mg_vcycle.argtypes = [vp, vp, vp, vp]
+    L.fl_mg_vcycle.restype = ci
+    L.fl_mg_solve.argtypes = [vp, vp, vp, dbl, ci, ctypes.POINTER(fl_solve_info), vp]
+    L.fl_mg_solve.restype = ci
+    L.fl_mg_last_error.argtypes = [vp]
+    L.fl_mg_last_error.restype = ctypes.c_char_p
+    L.fl_mg_destroy.argtypes = [vp]
+    L.fl_mg_destroy.restype = None
     _ = i32
     _lib = L
     return L
@@ -360,6 +383,85 @@ def fl_tune_save(path):
 
 def fl_tune_load(path):
     _check(lib().fl_tune_load(os.fspath(path).encode()))
+
+
+def fl_prolongation(fine, coarse, s):
+    """Host CSR (rowptr, col, val) of the prolongation from coarse to fine DOFs."""
+    nnz = ctypes.c_int64()
+    _check(lib().fl_prolongation(fine, coarse, s, ctypes.byref(nnz), None, None, None), fine)
+    n = fl_num_dofs(fine, s)
+    ptr = np.zeros(n + 1, dtype=np.int32)
+    col = np.zeros(nnz.value, dtype=np.int32)
+    val = np.zeros(nnz.value, dtype=np.float64)
+    _check(lib().fl_prolongation(fine, coarse, s, ctypes.byref(nnz), ptr.ctypes.data, col.ctypes.data,
+                                 val.ctypes.data), fine)
+    return ptr, col, val
+
+
+class Multigrid:
+    """Galerkin V-cycle hierarchy (fl_mg_*) on a finest float64 operator A (kept alive here)."""
+
+    def __init__(self, A):
+        self.A = A
+        self.m = ctypes.c_void_p()
+        r = lib().fl_mg_create(ctypes.byref(self.m), _ptr(A), A.stride(0), A.shape[0])
+        if r != FL_OK:
+            raise FlError(r, "fl_mg_create")
+
+    def _check(self, r):
+        if r != FL_OK:
+            raise FlError(r, lib().fl_mg_last_error(self.m).decode(errors="replace"))
+
+    def add_level(self, ptr, col, val, nc, stream=None):
+        ptr = np.ascontiguousarray(ptr, dtype=np.int32)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        self._check(lib().fl_mg_add_level(self.m, nc, len(col), ptr.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                          _stream(stream)))
+
+    def setup(self, nu=2, stream=None):
+        self._check(lib().fl_mg_setup(self.m, nu, _stream(stream)))
+
+    def level(self, k):
+        """(n, device pointer, lda) of level k."""
+        n, p, ld = ctypes.c_int64(), ctypes.c_void_p(), ctypes.c_int64()
+        self._check(lib().fl_mg_level(self.m, k, ctypes.byref(n), ctypes.byref(p), ctypes.byref(ld)))
+        return n.value, p.value, ld.value
+
+    def level_matrix(self, k, stream=None):
+        """A copy of level k's float64 operator as a CUDA tensor."""
+        import torch
+
+        n = self.level(k)[0]
+        out = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        self._check(lib().fl_mg_level_copy(self.m, k, _ptr(out), n, _stream(stream)))
+        return out
+
+    def omega(self, k):
+        w = ctypes.c_float()
+        self._check(lib().fl_mg_omega(self.m, k, ctypes.byref(w)))
+        return w.value
+
+    def vcycle(self, r32, z32, stream=None):
+        self._check(lib().fl_mg_vcycle(self.m, _ptr(r32), _ptr(z32), _stream(stream)))
+
+    def solve(self, b, u, tol=1e-8, maxit=1000, stream=None):
+        info = fl_solve_info()
+        r = lib().fl_mg_solve(self.m, _ptr(b), _ptr(u), tol, maxit, ctypes.byref(info), _stream(stream))
+        if r not in (FL_OK, FL_ENOTCONV, FL_ENOTSPD):
+            self._check(r)
+        return info
+
+    def close(self):
+        if self.m:
+            lib().fl_mg_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fl_batch_solve(h, problems, opts=None, stream=None):

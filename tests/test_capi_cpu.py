@@ -75,3 +75,27 @@ def test_default_options():
     assert (o.k_far, o.k_near, o.k_touch, o.k_bnd, o.regional, o.k_vertex) == (4, 6, 8, 8, 0, 6)
     so = F.fl_default_solve_opts()
     assert so.tol == 1e-8 and so.inner_dtype == F.FL_F64
+
+
+def test_prolongation_matches_oracle():
+    _lib_or_skip()
+    from oracle.multigrid import prolongation
+
+    Vc, Tc = synth.square(3, 0.15)
+    Vf, Tf = synth.bisect_all(Vc, Tc, 2)
+    hc, hf = F.fl_create(Vc, Tc), F.fl_create(Vf, Tf)
+    for s in (0.3, 0.8):
+        ptr, col, val = F.fl_prolongation(hf, hc, s)
+        n, nc = F.fl_num_dofs(hf, s), F.fl_num_dofs(hc, s)
+        P = np.zeros((n, nc))
+        for i in range(n):
+            P[i, col[ptr[i]:ptr[i + 1]]] = val[ptr[i]:ptr[i + 1]]
+        Po = prolongation(Vf, OracleMesh(Vf, Tf).dofs(s)[0], Vc, Tc, OracleMesh(Vc, Tc).dofs(s)[0])
+        assert np.allclose(P, Po, rtol=0, atol=1e-14)
+    # a point outside the coarse mesh is an error, not a silent zero row
+    Vo, To = synth.square(2, 0.0, lo=0.0, hi=3.0)
+    ho = F.fl_create(Vo, To)
+    with pytest.raises(F.FlError):
+        F.fl_prolongation(ho, hc, 0.5)
+    for h in (hc, hf, ho):
+        F.fl_destroy(h)
