@@ -1,25 +1,28 @@
 """Learned patch preconditioner (oracle; test infrastructure only).
 
-No part of this is in the paper: the preconditioner M(r) maps the residual r of a
-conjugate-gradient iterate to an estimate of its error e = A⁻¹ r, one DOF at a time,
-from the residual on a small patch of nearby DOFs.  Definitions (the GPU path states
-the same ones):
+No part of this is in the paper.  The preconditioner is linear in the residual, with
+coefficients that a small network computes from the mesh geometry around each DOF:
 
 * Patch of DOF i: the K nearest other DOFs among the vertices within two mesh edges
   of vertex i, ordered by (distance, vertex index); missing entries padded with -1.
-* h_i: mean length of the mesh edges at vertex i; hop_i: number of mesh edges from
-  vertex i to the nearest boundary vertex, capped at 8.
-* Features x_i (length 1 + 3K + 3):
-  σ_i = sqrt((r_i² + Σ_k r_{j_k}²) / (1 + K_i) + 1e-30) over the K_i present neighbours,
-  x = [r_i/σ_i, (r_{j_k}/σ_i, (x_{j_k} - x_i)/h_i, (y_{j_k} - y_i)/h_i) for k < K
-  (zeros where padded), log(h_i), hop_i/8, s].
-* Network: y = x_0 + w3·tanh(W2ᵀ tanh(W1ᵀ x + b1) + b2) + b3 (hidden widths H, H);
-  M(r)_i = σ_i y_i / A_ii.  With w3 = b3 = 0 this is the Jacobi preconditioner.
-* Training loss on samples (x_n, t_n) with t_n = e_i A_ii / σ_i:  mean_n (y_n - t_n)².
+* h_i: mean length of the mesh edges at vertex i; hop_i: mesh edges from vertex i to
+  the nearest boundary vertex, capped at 8.
+* Geometry features g_i (2K + 3): ((x_{j_k} - x_i)/h_i, (y_{j_k} - y_i)/h_i) for k < K
+  (zeros where padded), log h_i, hop_i/8, s.
+* Network: o_i = W3ᵀ tanh(W2ᵀ tanh(W1ᵀ g_i + b1) + b2) + b3 (K + 1 outputs, hidden
+  widths H, H); stencil c_i = o_i + (1, 0, ..., 0).
+* M r: (M r)_i = (c_i0 r_i + Σ_k c_ik r_{j_k}) / A_ii; the preconditioner applied is the
+  symmetric part ½ (M + Mᵀ) r.  With W3 = 0, b3 = 0 it is the Jacobi preconditioner.
+* Training samples pair the normalised residual patch of one DOF,
+  x_i = (r_i, r_{j_0}, ..., r_{j_{K-1}}) / σ_i (zeros where padded),
+  σ_i = sqrt((r_i² + Σ_k r_{j_k}²) / (1 + K_i) + 1e-30), with the target t_i = e_i A_ii / σ_i
+  of an error/residual pair (r = A e); prediction y = c_i · x_i; loss mean (y - t)².
+  For white-noise errors this is the least-squares (Frobenius) fit of M to A⁻¹ on the
+  patch pattern.
 
-Parity status: the gradients are pinned against central finite differences of the
-loss (tests/test_oracle_mlp.py); the patch table against brute-force distances; the
-features against their definition on a hand-checked mesh.
+Parity status: gradients pinned against central finite differences
+(tests/test_oracle_mlp.py); patch table against brute-force distances; the Jacobi
+limit and the symmetric apply against their definitions.
 """
 from __future__ import annotations
 
@@ -37,9 +40,7 @@ def patches(mesh, s, K=12):
             for b in range(3):
                 if a != b:
                     adj[c[a]].add(int(c[b]))
-    # h: mean incident edge length
     h = np.array([np.mean([np.linalg.norm(V[v] - V[w]) for w in adj[v]]) for v in range(nv)])
-    # hops to the boundary (breadth-first from the boundary vertices)
     onb = mesh.on_boundary
     hop = np.full(nv, 8, dtype=np.int64)
     frontier = [v for v in range(nv) if onb[v]]
@@ -69,54 +70,80 @@ def patches(mesh, s, K=12):
     return nbr, h[dofs], hop[dofs]
 
 
-def features(mesh, s, r, nbr, h, hop):
+def geometry(mesh, s, nbr, h, hop):
     dofs, _ = mesh.dofs(s)
     X = mesh.V[dofs]
     n, K = nbr.shape
-    F = np.zeros((n, 1 + 3 * K + 3))
+    G = np.zeros((n, 2 * K + 3))
+    for i in range(n):
+        for k in range(K):
+            j = nbr[i, k]
+            if j >= 0:
+                G[i, 2 * k] = (X[j, 0] - X[i, 0]) / h[i]
+                G[i, 2 * k + 1] = (X[j, 1] - X[i, 1]) / h[i]
+        G[i, 2 * K] = np.log(h[i])
+        G[i, 2 * K + 1] = hop[i] / 8.0
+        G[i, 2 * K + 2] = s
+    return G
+
+
+def residual_patch(r, nbr):
+    """(x [n, K+1], sigma [n]) of a residual."""
+    n, K = nbr.shape
+    x = np.zeros((n, K + 1))
     sig = np.zeros(n)
     for i in range(n):
         present = nbr[i][nbr[i] >= 0]
-        ss = r[i] ** 2 + np.sum(r[present] ** 2)
-        sig[i] = np.sqrt(ss / (1 + len(present)) + 1e-30)
-        F[i, 0] = r[i] / sig[i]
+        sig[i] = np.sqrt((r[i] ** 2 + np.sum(r[present] ** 2)) / (1 + len(present)) + 1e-30)
+        x[i, 0] = r[i] / sig[i]
         for k in range(K):
-            j = nbr[i, k]
-            if j < 0:
-                continue
-            F[i, 1 + 3 * k] = r[j] / sig[i]
-            F[i, 2 + 3 * k] = (X[j, 0] - X[i, 0]) / h[i]
-            F[i, 3 + 3 * k] = (X[j, 1] - X[i, 1]) / h[i]
-        F[i, 1 + 3 * K] = np.log(h[i])
-        F[i, 2 + 3 * K] = hop[i] / 8.0
-        F[i, 3 + 3 * K] = s
-    return F, sig
+            if nbr[i, k] >= 0:
+                x[i, 1 + k] = r[nbr[i, k]] / sig[i]
+    return x, sig
 
 
-def forward(Wts, X):
-    W1, b1, W2, b2, w3, b3 = Wts
-    H1 = np.tanh(X @ W1 + b1)
+def coefficients(Wts, G):
+    W1, b1, W2, b2, W3, b3 = Wts
+    H1 = np.tanh(G @ W1 + b1)
     H2 = np.tanh(H1 @ W2 + b2)
-    return X[:, 0] + H2 @ w3 + b3, (H1, H2)
+    C = H2 @ W3 + b3
+    C[:, 0] += 1.0
+    return C, (H1, H2)
 
 
-def loss_grad(Wts, X, t):
-    """Loss mean (y - t)² and its gradient with respect to (W1, b1, W2, b2, w3, b3)."""
-    W1, b1, W2, b2, w3, b3 = Wts
-    y, (H1, H2) = forward(Wts, X)
-    B = X.shape[0]
+def loss_grad(Wts, G, X, t):
+    """Loss mean (c(g) · x - t)² and its gradient with respect to (W1, b1, W2, b2, W3, b3)."""
+    W1, b1, W2, b2, W3, b3 = Wts
+    C, (H1, H2) = coefficients(Wts, G)
+    y = np.sum(C * X, axis=1)
+    B = G.shape[0]
     dy = 2.0 * (y - t) / B
-    gw3 = H2.T @ dy
-    gb3 = np.sum(dy)
-    dA2 = np.outer(dy, w3) * (1.0 - H2 ** 2)
+    dO = dy[:, None] * X
+    gW3 = H2.T @ dO
+    gb3 = dO.sum(axis=0)
+    dA2 = (dO @ W3.T) * (1.0 - H2 ** 2)
     gW2 = H1.T @ dA2
     gb2 = dA2.sum(axis=0)
     dA1 = (dA2 @ W2.T) * (1.0 - H1 ** 2)
-    gW1 = X.T @ dA1
+    gW1 = G.T @ dA1
     gb1 = dA1.sum(axis=0)
-    return float(np.mean((y - t) ** 2)), (gW1, gb1, gW2, gb2, gw3, np.array(gb3))
+    return float(np.mean((y - t) ** 2)), (gW1, gb1, gW2, gb2, gW3, gb3)
 
 
-def apply(Wts, F, sig, diag):
-    y, _ = forward(Wts, F)
-    return sig * y / diag
+def stencil_matrix(C, nbr, diag):
+    """M with M_ii = c_i0 / A_ii, M_{i j_k} = c_ik / A_ii."""
+    n, K = nbr.shape
+    M = np.zeros((n, n))
+    for i in range(n):
+        M[i, i] += C[i, 0] / diag[i]
+        for k in range(K):
+            if nbr[i, k] >= 0:
+                M[i, nbr[i, k]] += C[i, 1 + k] / diag[i]
+    return M
+
+
+def apply(Wts, G, nbr, diag, r):
+    """½ (M + Mᵀ) r."""
+    C, _ = coefficients(Wts, G)
+    M = stencil_matrix(C, nbr, diag)
+    return 0.5 * (M @ r + M.T @ r)
