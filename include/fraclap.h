@@ -323,6 +323,85 @@ const char* fl_mg_last_error(fl_mg_handle mg);
 void fl_mg_destroy(fl_mg_handle mg);
 
 /* ------------------------------------------------------------------------
+ * Learned patch preconditioner and flexible CG (not in the paper).  A linear
+ * preconditioner whose stencil over each DOF's patch (the K = 12 nearest DOFs within
+ * two mesh edges) a small network (hidden width 64, tanh) computes from the patch
+ * geometry; applied as the symmetric part (M + M^T)/2; see learned.cu for the exact
+ * definition.  The network starts as the Jacobi preconditioner.
+ * ------------------------------------------------------------------------ */
+
+/* Patch table of the mesh's DOFs at order s (host, 2D): nbr_host[n][K] DOF indices
+   ordered by (distance, vertex index), -1 padded; hlen_host[n] mean edge length at the
+   vertex; hop_host[n] mesh edges to the boundary (capped at 8).  Either of the last two
+   may be NULL. */
+int fl_patches(fl_handle h, double s, int K, int32_t* nbr_host, double* hlen_host, int32_t* hop_host);
+
+typedef struct fl_lp* fl_lp_handle;
+/* A network for the mesh's DOFs at order s: K = 12, hidden = 64 (FL_ENOTIMPL otherwise),
+   hidden layers seeded (splitmix64 / Box-Muller, variance 1/fan-in), output layer zero
+   (the Jacobi preconditioner).  `mesh` must outlive the handle. */
+int fl_lp_create(fl_lp_handle* lp, fl_handle mesh, double s, int K, int hidden, uint64_t seed);
+int64_t fl_lp_num_params(fl_lp_handle lp);
+int fl_lp_num_features(fl_lp_handle lp);
+int64_t fl_lp_num_samples(fl_lp_handle lp);
+/* Parameters [W1 (G x H) | b1 | W2 (H x H) | b2 | W3 (H x (K+1)) | b3], G = 2K + 3, float32 host
+   arrays; fl_lp_set_params also recomputes the stencil table. */
+int fl_lp_get_params(fl_lp_handle lp, float* host);
+int fl_lp_set_params(fl_lp_handle lp, const float* host);
+/* Take the diagonal of A (device, float64) as the scale of the preconditioner. */
+int fl_lp_bind(fl_lp_handle lp, const double* A_dev, int64_t lda, void* stream);
+/* Training-sample rows X_dev[n][F] = [geometry (2K + 3) | residual patch / sigma (K + 1)] and
+   sigma_dev[n] of a residual r_dev[n] (float64). */
+int fl_lp_features(fl_lp_handle lp, const double* r_dev, float* X_dev, float* sigma_dev, void* stream);
+/* Stencil table c [n][K + 1] (host) computed with the float16 network. */
+int fl_lp_stencil(fl_lp_handle lp, float* host);
+/* z = (M + M^T) r / 2, float64 device vectors. */
+int fl_lp_apply(fl_lp_handle lp, const double* r_dev, double* z_dev, void* stream);
+/* Loss mean (c(g) . x - t)^2 and its gradient (host, fl_lp_num_params floats) on a batch of
+   sample rows X_dev[B][F] and targets T_dev[B] (float32, device). */
+int fl_lp_loss_grad(fl_lp_handle lp, int64_t B, const float* X_dev, const float* T_dev, float* loss_host,
+                    float* grad_host, void* stream);
+/* Training pairs from error vectors E (column c at E_dev + c*lde): r = A e, features of r,
+   targets e_i A_ii / sigma_i, appended to the handle's training set. */
+int fl_lp_add_pairs(fl_lp_handle lp, const double* A_dev, int64_t lda, const double* E_dev, int64_t lde,
+                    int count, void* stream);
+/* Pairs from the method's own Jacobi-PCG: u = A^-1 b (to 1e-11), then for each k in ks
+   the iterate x_k from 0 and the pair (A (u - x_k), u - x_k). */
+int fl_lp_collect(fl_lp_handle lp, const double* A_dev, int64_t lda, const double* b_dev, int nk, const int* ks,
+                  void* stream);
+/* Pairs from Jacobi-PCG on A x = 0 started at seeded white noise x0 (splitmix64 / Box-Muller
+   of (seed + c, i)), c < count: for each k in ks the iterate x_k (k = 0: x0) and the pair
+   (A e, e) with the exact error e = -x_k.  For k = 0 the loss is the Frobenius fit of M to
+   A^-1 on the stencil pattern; larger k weights the error components CG leaves behind. */
+int fl_lp_collect_noise(fl_lp_handle lp, const double* A_dev, int64_t lda, int count, int nk, const int* ks,
+                        uint64_t seed, void* stream);
+/* Adam (0.9, 0.999, 1e-8) on mini-batches drawn from the training set with splitmix64(seed,
+   step, slot); *loss_host = loss of the last batch. */
+int fl_lp_train(fl_lp_handle lp, int steps, int64_t batch, float lr, uint64_t seed, float* loss_host, void* stream);
+const char* fl_lp_last_error(fl_lp_handle lp);
+void fl_lp_destroy(fl_lp_handle lp);
+
+typedef struct fl_fcg_info {
+    int iterations;
+    int fallback_at;           /* iteration at which the fallback preconditioner took over, -1: none */
+    int final_preconditioner;  /* 2 learned, 1 multigrid, 0 Jacobi */
+    double rel_residual;       /* ||b - A u|| / ||b||, recomputed in float64 at the end */
+    int status;
+} fl_fcg_info;
+
+/*
+ * Flexible CG (one-step orthogonalisation, alpha = p.r / p.Ap) on the float64 matrix,
+ * preconditioned by the learned map lp if given, else the multigrid V-cycle mg if
+ * given, else Jacobi.  When the learned (or, after it, the multigrid) preconditioner
+ * gives a non-descent direction or the residual falls by less than 10 % over 10 steps,
+ * the next one in the order learned -> multigrid -> Jacobi takes over and the
+ * directions restart.  Converged when the recursive residual meets tol and the
+ * float64 residual recomputed at the end agrees.  h supplies the error message.
+ */
+int fl_fcg_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const double* b_dev, double* u_dev,
+                 fl_lp_handle lp, fl_mg_handle mg, double tol, int maxit, fl_fcg_info* info, void* stream);
+
+/* ------------------------------------------------------------------------
  * Autotuning (no counterpart in the paper): launch shapes measured on the
  * running device, kept in a process-wide table keyed by (kernel, n, nrhs,
  * nslices) and the device name, consulted when a launch parameter is left at

@@ -119,6 +119,8 @@ int set_err(fl_ctx* h, int code, const std::string& msg);
 // scratch for the float32 copy of x (unused for FL_F64)
 cudaError_t gemv(int dtype, const void* A, int64_t lda, int64_t n, const double* x, int64_t incx, double* y,
                  int64_t incy, float* xf, cudaStream_t st, bool xf_ready = false);
+// z = V(r), float64 vectors on the finest level of a multigrid hierarchy (mg.cu)
+int mg_precondition(fl_mg_handle m, const double* r, double* z, cudaStream_t st);
 // tuning table (tune.cpp)
 std::string device_name();
 void tune_record(const std::string& device, const std::string& kernel, int64_t n, int nrhs, int nslices, int p0,

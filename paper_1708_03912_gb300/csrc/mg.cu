@@ -399,6 +399,20 @@ struct Locator {
 }  // namespace mg
 }  // namespace fl
 
+namespace fl {
+// z = V(r) for float64 vectors on the finest level (used by the flexible CG)
+int mg_precondition(fl_mg_handle m, const double* r, double* z, cudaStream_t st) {
+    if (!m || !m->ready) return FL_EINVAL;
+    mg::Level& L = m->lv[0];
+    const unsigned g = mg::nb(L.n);
+    mg::d2f_kernel<<<g, 256, 0, st>>>(L.n, r, L.r);
+    mg::vcycle(m, 0, st);
+    mg::f2d_kernel<<<g, 256, 0, st>>>(L.n, L.x, z);
+    fl::count_launch(2);
+    return cudaGetLastError() == cudaSuccess ? FL_OK : FL_ECUDA;
+}
+}  // namespace fl
+
 using namespace fl;
 using namespace fl::mg;
 

@@ -28,7 +28,10 @@ EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
            "fl_tune_batch", "fl_tune_record", "fl_tune_lookup", "fl_tune_clear", "fl_tune_count", "fl_tune_save",
            "fl_tune_load", "fl_prolongation", "fl_mg_create", "fl_mg_add_level", "fl_mg_setup", "fl_mg_level", "fl_mg_level_copy",
-           "fl_mg_omega", "fl_mg_vcycle", "fl_mg_solve", "fl_mg_last_error", "fl_mg_destroy"]
+           "fl_mg_omega", "fl_mg_vcycle", "fl_mg_solve", "fl_mg_last_error", "fl_mg_destroy",
+           "fl_patches", "fl_lp_create", "fl_lp_num_params", "fl_lp_num_features", "fl_lp_num_samples",
+           "fl_lp_get_params", "fl_lp_set_params", "fl_lp_stencil", "fl_lp_bind", "fl_lp_features", "fl_lp_apply", "fl_lp_loss_grad",
+           "fl_lp_add_pairs", "fl_lp_collect", "fl_lp_collect_noise", "fl_lp_train", "fl_lp_last_error", "fl_lp_destroy", "fl_fcg_solve"]
 FL_STATIC_MAX_N = 65536
 FL_BATCH_MAXPROB = 8
 FL_RESID_F64, FL_RESID_DF = 0, 1
@@ -61,6 +64,11 @@ class fl_stats(ctypes.Structure):
 class fl_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("status", ctypes.c_int)]
+
+
+class fl_fcg_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("fallback_at", ctypes.c_int), ("final_preconditioner", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("status", ctypes.c_int)]
 
 
 class fl_batch_problem(ctypes.Structure):
@@ -175,6 +183,41 @@ def lib():
     L.fl_mg_last_error.restype = ctypes.c_char_p
     L.fl_mg_destroy.argtypes = [vp]
     L.fl_mg_destroy.restype = None
+    L.fl_patches.argtypes = [vp, dbl, ci, vp, vp, vp]
+    L.fl_patches.restype = ci
+    L.fl_lp_create.argtypes = [ctypes.POINTER(vp), vp, dbl, ci, ci, ctypes.c_uint64]
+    L.fl_lp_create.restype = ci
+    for nm, rt in (("fl_lp_num_params", i64), ("fl_lp_num_features", ci), ("fl_lp_num_samples", i64)):
+        getattr(L, nm).argtypes = [vp]
+        getattr(L, nm).restype = rt
+    L.fl_lp_get_params.argtypes = [vp, vp]
+    L.fl_lp_get_params.restype = ci
+    L.fl_lp_set_params.argtypes = [vp, vp]
+    L.fl_lp_set_params.restype = ci
+    L.fl_lp_stencil.argtypes = [vp, vp]
+    L.fl_lp_stencil.restype = ci
+    L.fl_lp_bind.argtypes = [vp, vp, i64, vp]
+    L.fl_lp_bind.restype = ci
+    L.fl_lp_features.argtypes = [vp, vp, vp, vp, vp]
+    L.fl_lp_features.restype = ci
+    L.fl_lp_apply.argtypes = [vp, vp, vp, vp]
+    L.fl_lp_apply.restype = ci
+    L.fl_lp_loss_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    L.fl_lp_loss_grad.restype = ci
+    L.fl_lp_add_pairs.argtypes = [vp, vp, i64, vp, i64, ci, vp]
+    L.fl_lp_add_pairs.restype = ci
+    L.fl_lp_collect.argtypes = [vp, vp, i64, vp, ci, vp, vp]
+    L.fl_lp_collect.restype = ci
+    L.fl_lp_collect_noise.argtypes = [vp, vp, i64, ci, ci, vp, ctypes.c_uint64, vp]
+    L.fl_lp_collect_noise.restype = ci
+    L.fl_lp_train.argtypes = [vp, ci, i64, ctypes.c_float, ctypes.c_uint64, vp, vp]
+    L.fl_lp_train.restype = ci
+    L.fl_lp_last_error.argtypes = [vp]
+    L.fl_lp_last_error.restype = ctypes.c_char_p
+    L.fl_lp_destroy.argtypes = [vp]
+    L.fl_lp_destroy.restype = None
+    L.fl_fcg_solve.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, dbl, ci, ctypes.POINTER(fl_fcg_info), vp]
+    L.fl_fcg_solve.restype = ci
     _ = i32
     _lib = L
     return L
@@ -462,6 +505,113 @@ class Multigrid:
             self.close()
         except Exception:
             pass
+
+
+def fl_patches(h, s, K=12):
+    """(nbr [n, K] int32, h [n] float64, hop [n] int32) of the mesh's DOFs (host)."""
+    n = fl_num_dofs(h, s)
+    nbr = np.zeros((n, K), dtype=np.int32)
+    hl = np.zeros(n, dtype=np.float64)
+    hop = np.zeros(n, dtype=np.int32)
+    _check(lib().fl_patches(h, s, K, nbr.ctypes.data, hl.ctypes.data, hop.ctypes.data), h)
+    return nbr, hl, hop
+
+
+class LearnedPreconditioner:
+    """fl_lp_* handle: patch-MLP preconditioner for one mesh (which must stay alive)."""
+
+    def __init__(self, mesh_handle, s, seed=1, K=12, hidden=64):
+        self.m = ctypes.c_void_p()
+        r = lib().fl_lp_create(ctypes.byref(self.m), mesh_handle, s, K, hidden, seed)
+        if r != FL_OK:
+            raise FlError(r, "fl_lp_create")
+        self.n = fl_num_dofs(mesh_handle, s)
+        self.nw = int(lib().fl_lp_num_params(self.m))
+        self.F = int(lib().fl_lp_num_features(self.m))
+
+    def _check(self, r):
+        if r != FL_OK:
+            raise FlError(r, lib().fl_lp_last_error(self.m).decode(errors="replace"))
+
+    def params(self):
+        out = np.zeros(self.nw, dtype=np.float32)
+        self._check(lib().fl_lp_get_params(self.m, out.ctypes.data))
+        return out
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == self.nw
+        self._check(lib().fl_lp_set_params(self.m, w.ctypes.data))
+
+    def stencil(self):
+        out = np.zeros((self.n, 13), dtype=np.float32)
+        self._check(lib().fl_lp_stencil(self.m, out.ctypes.data))
+        return out
+
+    def bind(self, A, stream=None):
+        self._check(lib().fl_lp_bind(self.m, _ptr(A), A.stride(0), _stream(stream)))
+
+    def features(self, r, stream=None):
+        import torch
+
+        X = torch.empty((self.n, self.F), dtype=torch.float32, device="cuda")
+        sig = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        self._check(lib().fl_lp_features(self.m, _ptr(r), _ptr(X), _ptr(sig), _stream(stream)))
+        return X, sig
+
+    def apply(self, r, z, stream=None):
+        self._check(lib().fl_lp_apply(self.m, _ptr(r), _ptr(z), _stream(stream)))
+
+    def loss_grad(self, X, T, stream=None):
+        loss = ctypes.c_float()
+        g = np.zeros(self.nw, dtype=np.float32)
+        self._check(lib().fl_lp_loss_grad(self.m, X.shape[0], _ptr(X), _ptr(T), ctypes.byref(loss), g.ctypes.data,
+                                          _stream(stream)))
+        return loss.value, g
+
+    def add_pairs(self, A, E, stream=None):
+        """E: float64 [count, n] (one error vector per row)."""
+        self._check(lib().fl_lp_add_pairs(self.m, _ptr(A), A.stride(0), _ptr(E), E.stride(0), E.shape[0],
+                                          _stream(stream)))
+
+    def collect(self, A, b, ks, stream=None):
+        k = np.ascontiguousarray(ks, dtype=np.int32)
+        self._check(lib().fl_lp_collect(self.m, _ptr(A), A.stride(0), _ptr(b), len(k), k.ctypes.data,
+                                        _stream(stream)))
+
+    def collect_noise(self, A, count, ks, seed=20170813, stream=None):
+        k = np.ascontiguousarray(ks, dtype=np.int32)
+        self._check(lib().fl_lp_collect_noise(self.m, _ptr(A), A.stride(0), count, len(k), k.ctypes.data, seed,
+                                              _stream(stream)))
+
+    def num_samples(self):
+        return int(lib().fl_lp_num_samples(self.m))
+
+    def train(self, steps, batch=4096, lr=1e-3, seed=7, stream=None):
+        loss = ctypes.c_float()
+        self._check(lib().fl_lp_train(self.m, steps, batch, lr, seed, ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def close(self):
+        if self.m:
+            lib().fl_lp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fl_fcg_solve(h, A, b, u, lp=None, mg=None, tol=1e-8, maxit=2000, stream=None):
+    """Flexible CG; returns fl_fcg_info (raises on argument / device errors)."""
+    info = fl_fcg_info()
+    r = lib().fl_fcg_solve(h, A.shape[0], _ptr(A), A.stride(0), _ptr(b), _ptr(u), lp.m if lp is not None else None,
+                           mg.m if mg is not None else None, tol, maxit, ctypes.byref(info), _stream(stream))
+    if r not in (FL_OK, FL_ENOTCONV, FL_ENOTSPD):
+        _check(r, h)
+    return info
 
 
 def fl_batch_solve(h, problems, opts=None, stream=None):

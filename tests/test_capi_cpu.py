@@ -99,3 +99,18 @@ def test_prolongation_matches_oracle():
         F.fl_prolongation(ho, hc, 0.5)
     for h in (hc, hf, ho):
         F.fl_destroy(h)
+
+
+def test_patch_table_matches_oracle():
+    _lib_or_skip()
+    from oracle.mlp import patches
+
+    for V, T in (synth.square(6, 0.2), synth.lshape(0.25, 0)):
+        h = F.fl_create(V, T)
+        for s in (0.4, 0.7):
+            nbr, hl, hop = F.fl_patches(h, s, 12)
+            on, oh, ohop = patches(OracleMesh(V, T), s, 12)
+            assert np.array_equal(nbr, on)
+            assert np.allclose(hl, oh, rtol=1e-13, atol=0)
+            assert np.array_equal(hop, ohop)
+        F.fl_destroy(h)
