@@ -30,6 +30,8 @@ WORKLOAD = {"workload": "disc-quasi-uniform-25-rings", "domain": "unit disc", "r
             "dofs": 1887, "s": 0.75, "f": "1", "dtype_assembly": "f32 separated pairs + f64 near/boundary",
             "solve": "f64-refined Jacobi-PCG on f32 copy to 1e-8", "l2": "flushed between timed steps (512 MiB write)"}
 METRIC = "element pairs/s assembled; matvec HBM GB/s; solve time to 1e-8 vs plain FP64"
+# the L-shape workload: nested levels 1..4 of the corner- and boundary-refined L-shape
+LSHAPE = {"level": 4, "s": 0.5}
 # the batched workload: 4 orders x 64 loads on the disc graded toward the boundary
 BATCH = {"rings": 30, "mu": 2.0, "s": [0.25, 0.5, 0.75, 0.9], "nrhs": 64}
 # DRAM bytes (read 1.433 MB + write 2.119 MB) per launch of far_tile_kernel<2,float,16,0> on this
@@ -144,6 +146,67 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def lshape_section(F, synth, timed, dev):
+    """L-shape level LSHAPE["level"] (s = 1/2): Jacobi-PCG, multigrid-preconditioned CG on the nested
+    levels below it, and flexible CG with the learned stencil trained on a coarser level."""
+    import torch
+
+    s = LSHAPE["s"]
+    lev = LSHAPE["level"]
+    meshes = [synth.lshape(0.25, l) for l in range(lev, 0, -1)]  # fine to coarse
+    hs = [F.fl_create(V, T) for V, T in meshes]
+    mf = F.Mesh(*meshes[0])
+    A = mf.assemble(s, "mixed")
+    n = A.shape[0]
+    b = mf.load_vector(s)
+    u = torch.empty_like(b)
+    out = {"workload": f"L-shape [0,2]^2 minus [1,2]^2, level {lev} (refined towards (1,1) and the boundary), "
+                       f"n = {n}, s = {s}, f = 1, tol 1e-8, float64 matvec", "n": n}
+    _, ij = mf.solve(A, b, tol=1e-8)
+    out["jacobi_pcg"] = {"ms": timed(lambda: mf.solve(A, b, tol=1e-8), reps=2), "iterations": ij.iterations}
+    # multigrid on the nested levels
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mg = F.Multigrid(A)
+    for k in range(len(hs) - 1):
+        ptr, col, val = F.fl_prolongation(hs[k], hs[k + 1], s)
+        mg.add_level(ptr, col, val, F.fl_num_dofs(hs[k + 1], s))
+    mg.setup(nu=2)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1000
+    im = mg.solve(b, u, tol=1e-8, maxit=500)
+    out["mg_pcg"] = {"ms": timed(lambda: mg.solve(b, u, tol=1e-8, maxit=500), reps=2), "iterations": im.iterations,
+                     "setup_ms": setup_ms, "levels": [F.fl_num_dofs(h, s) for h in hs]}
+    # learned stencil: trained on level 2 from noise-started CG pairs, transferred to this level
+    V2, T2 = synth.lshape(0.25, 2)
+    m2 = F.Mesh(V2, T2)
+    A2 = m2.assemble(s, "mixed")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lp2 = F.LearnedPreconditioner(m2.h, s, seed=1)
+    lp2.collect_noise(A2, 8, [0, 1, 2, 4])
+    loss = lp2.train(2000, batch=8192, lr=1e-3)
+    torch.cuda.synchronize()
+    train_ms = (time.perf_counter() - t0) * 1000
+    lp = F.LearnedPreconditioner(mf.h, s, seed=1)
+    lp.set_params(lp2.params())
+    il = F.fl_fcg_solve(mf.h, A, b, u, lp=lp, mg=mg, tol=1e-8)
+    out["learned_fcg"] = {"ms": timed(lambda: F.fl_fcg_solve(mf.h, A, b, u, lp=lp, mg=mg, tol=1e-8), reps=2),
+                          "iterations": il.iterations, "fallback_at": il.fallback_at,
+                          "rel_residual_f64": il.rel_residual, "train_ms": train_ms, "train_loss": loss,
+                          "note": "stencil network trained on level 2 (2000 Adam steps, batch 8192), weights "
+                                  "transferred; multigrid as fallback"}
+    ij2 = F.fl_fcg_solve(mf.h, A, b, u, mg=mg, tol=1e-8)
+    out["mg_fcg_iterations"] = ij2.iterations
+    for obj in (lp, lp2, mg):
+        obj.close()
+    m2.close()
+    mf.close()
+    for h in hs:
+        F.fl_destroy(h)
+    return out
 
 
 def main():
@@ -333,6 +396,9 @@ def main():
     del probs
     mg.close()
 
+    # ---- L-shape refined towards the corner and the boundary: preconditioners, time to 1e-8 ----
+    lsh = lshape_section(F, synth, timed, dev)
+
     # ---- end to end through the public API with host buffers ----
     def e2e_step():
         mm = F.Mesh(V, T)
@@ -381,6 +447,7 @@ def main():
         "solve_ms_to_1e-8": {"f32_refined": sol_mixed, "plain_f64": sol_fp64, "iters_f64": inf64.iterations,
                              "iters_refined": infmx.iterations, "outer": infmx.outer_iterations},
         "batched": batch_line,
+        "lshape": lsh,
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": {"value": n_el * n_el / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
