@@ -7,11 +7,13 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 #include <string>
 #include <vector>
 
 #include "context.h"
 #include "device.h"
+#include "tc.h"
 
 namespace fl {
 
@@ -378,7 +380,8 @@ __global__ void zero_kernel(int64_t n, double* x) {
 
 // ------------------------------------------------------- solver workspace --
 struct SolveWork {
-    double *r, *z, *p, *q, *dinv, *dinv_lo, *d, *t, *prz, *prr, *ppq, *part;
+    double *r, *z, *p, *q, *dinv, *dinv_lo, *d, *t, *sv, *prz, *prr, *ppq, *part;
+    unsigned* gbar;  // grid-barrier counter of the persistent solver (own cache line)
     float* xf;
     CgScalars* s;
     CgScalars* s_host;
@@ -390,8 +393,9 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
     // one contiguous device block per handle, grown on demand; the layout below
     // (eight float64 vectors, three reduction buffers, one float32 vector, scalars)
     // is carved with the same 256-byte rounding that sizes it
-    const size_t need = 8 * round256(n * sizeof(double)) + 3 * round256(RED_BLOCKS * sizeof(double)) +
-                        round256(2 * 1024 * sizeof(double)) + round256(n * sizeof(float)) + round256(sizeof(CgScalars));
+    const size_t need = 9 * round256(n * sizeof(double)) + 3 * round256(RED_BLOCKS * sizeof(double)) +
+                        round256(4 * 1024 * sizeof(double)) + round256(256) + round256(n * sizeof(float)) +
+                        round256(sizeof(CgScalars));
     void* base = nullptr;
     if (h->solve_ws_bytes < need) {
         for (auto& g : h->cg_graphs) cudaGraphExecDestroy(g.exec);
@@ -423,10 +427,12 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
     w.dinv_lo = (double*)take(n * sizeof(double));
     w.d = (double*)take(n * sizeof(double));
     w.t = (double*)take(n * sizeof(double));
+    w.sv = (double*)take(n * sizeof(double));
     w.prz = (double*)take(RED_BLOCKS * sizeof(double));
     w.prr = (double*)take(RED_BLOCKS * sizeof(double));
     w.ppq = (double*)take(RED_BLOCKS * sizeof(double));
-    w.part = (double*)take(2 * 1024 * sizeof(double));
+    w.part = (double*)take(4 * 1024 * sizeof(double));
+    w.gbar = (unsigned*)take(256);
     w.xf = (float*)take(n * sizeof(float));
     w.s = (CgScalars*)take(sizeof(CgScalars));
     w.s_host = (CgScalars*)h->solve_host;
@@ -466,119 +472,166 @@ __device__ __forceinline__ double grid_total(const double* part, int nb, int str
     return block_total(acc, sh);
 }
 
+// Row `row` of A times x (float64 or float32 entries), one warp: 16-byte loads of A after
+// peeling to an aligned start, four loads per lane in flight, x read through the cache.
+template <bool SH, typename TX>
+__device__ __forceinline__ TX xload(const TX* p) {
+    if constexpr (SH) return *p;  // shared-memory copy
+    else return __ldcg(p);
+}
+template <typename TA, typename TX, typename TS, bool SH>
+__device__ __forceinline__ TS row_dot(const TA* __restrict__ a, const TX* __restrict__ x, int64_t n, int lane) {
+    constexpr int V = 16 / sizeof(TA);  // entries per 16-byte load
+    const int peel = (int)((V - (((uintptr_t)a / sizeof(TA)) & (V - 1))) & (V - 1));
+    TS s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    const int head = (int)((int64_t)peel < n ? (int64_t)peel : n);
+    if (lane < head) s0 = (TS)a[lane] * (TS)xload<SH>(x + lane);
+    const int64_t nv = (n - head) / V;  // whole vectors after the peel
+    const TA* av = a + head;
+    const TX* xv = x + head;
+    int64_t k = lane;
+    for (; k + 96 < nv; k += 128) {
+        const uint4 u0 = __ldcs(reinterpret_cast<const uint4*>(av) + k);
+        const uint4 u1 = __ldcs(reinterpret_cast<const uint4*>(av) + k + 32);
+        const uint4 u2 = __ldcs(reinterpret_cast<const uint4*>(av) + k + 64);
+        const uint4 u3 = __ldcs(reinterpret_cast<const uint4*>(av) + k + 96);
+        const TA* e0 = reinterpret_cast<const TA*>(&u0);
+        const TA* e1 = reinterpret_cast<const TA*>(&u1);
+        const TA* e2 = reinterpret_cast<const TA*>(&u2);
+        const TA* e3 = reinterpret_cast<const TA*>(&u3);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            s0 += (TS)e0[v] * (TS)xload<SH>(xv + k * V + v);
+            s1 += (TS)e1[v] * (TS)xload<SH>(xv + (k + 32) * V + v);
+            s2 += (TS)e2[v] * (TS)xload<SH>(xv + (k + 64) * V + v);
+            s3 += (TS)e3[v] * (TS)xload<SH>(xv + (k + 96) * V + v);
+        }
+    }
+    for (; k < nv; k += 32) {
+        const uint4 u0 = __ldcs(reinterpret_cast<const uint4*>(av) + k);
+        const TA* e0 = reinterpret_cast<const TA*>(&u0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) s0 += (TS)e0[v] * (TS)xload<SH>(xv + k * V + v);
+    }
+    for (int64_t j = head + nv * V + lane; j < n; j += 32) s1 += (TS)a[j] * (TS)xload<SH>(x + j);
+    return warp_sum((s0 + s1) + (s2 + s3));
+}
+
+// Persistent Jacobi-PCG in the Chronopoulos-Gear arrangement (one cooperative launch):
+// the product is taken of the preconditioned residual, w = A z, and s = A p is carried by
+// recurrence, so both inner products of a step come from one pass and a step needs two
+// grid barriers:
+//   M: w = A z, partial delta = z.w
+//   U: beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev)
+//      (beta = 0, alpha = gamma / delta first); p = z + beta p, s = w + beta s, u += alpha p,
+//      r -= alpha s, z = D^-1 r; partial gamma = r.z and r.r
+// Every block sums the per-block partials in the same order, so all blocks hold the same
+// scalars and take the same branch.  A float32 matrix (the inner solver of the refinement)
+// multiplies a float32 copy of z with float32 row sums.  Breakdown: a non-positive
+// denominator (p.Ap <= 0).
 template <typename TA>
 __global__ void __launch_bounds__(PCG_THREADS) pcg_persistent_kernel(int64_t n, const TA* __restrict__ A, int64_t lda,
                                                                       const double* __restrict__ dinv,
                                                                       const double* __restrict__ rhs, double* u, double* r,
-                                                                      double* z, double* p, double* q, float* pf,
-                                                                      double* part, CgScalars* S, double tol, int maxit) {
-    namespace cg = cooperative_groups;
-    cg::grid_group grid = cg::this_grid();
+                                                                      double* z, double* p, double* w, double* sv,
+                                                                      float* zf, double* part, unsigned* gbar,
+                                                                      CgScalars* S, double tol, int maxit, int* err,
+                                                                      int stage_x) {
     __shared__ double sh[PCG_THREADS / 32];
+    extern __shared__ __align__(16) unsigned char xs_raw[];  // copy of z (or zf) when it fits
     const int nb = gridDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)nb * blockDim.x;
     const int lane = threadIdx.x & 31;
     const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
-    // start: u = 0, r = rhs, z = D^-1 r, p = z
-    double a0 = 0.0, c0 = 0.0;
+    double* partD = part;
+    double* partG = part + 1024;
+    double* partR = part + 2048;
+    unsigned epoch = 0;
+    // start: u = 0, r = rhs, z = D^-1 r, p = s = 0
+    double g0 = 0.0, c0 = 0.0;
     for (int64_t i = tid; i < n; i += nthreads) {
         const double ri = rhs[i];
         const double zi = dinv[i] * ri;
         u[i] = 0.0;
         r[i] = ri;
         z[i] = zi;
-        p[i] = zi;
-        if (pf) pf[i] = (float)zi;
-        a0 = fma(ri, zi, a0);
+        p[i] = 0.0;
+        sv[i] = 0.0;
+        if (zf) zf[i] = (float)zi;
+        g0 = fma(ri, zi, g0);
         c0 = fma(ri, ri, c0);
     }
-    a0 = block_total(a0, sh);
+    g0 = block_total(g0, sh);
     c0 = block_total(c0, sh);
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = a0;
-        part[2 * blockIdx.x + 1] = c0;
+        partG[blockIdx.x] = g0;
+        partR[blockIdx.x] = c0;
     }
-    grid.sync();
-    double rz = grid_total(part, nb, 2, sh);
-    const double rr0 = grid_total(part + 1, nb, 2, sh);
+    if (!tc::grid_barrier(gbar, epoch, nb, err)) return;
+    double gamma = grid_total(partG, nb, 1, sh);
+    const double rr0 = grid_total(partR, nb, 1, sh);
     const double stop = tol * tol * rr0;
-    double rr = rr0;
+    double rr = rr0, gamma_prev = 1.0, alpha_prev = 1.0;
     int it = 0, breakdown = 0;
-    grid.sync();  // every block has read part before it is rewritten
     while (rr > stop && it < maxit) {
-        // q = A p and the partial p.q (one warp per row)
-        double pq = 0.0;
+        // M: w = A z and the partial z.w
+        double dl = 0.0;
+        using TX = typename std::conditional<sizeof(TA) == 8, double, float>::type;
+        const TX* xg = (sizeof(TA) == 8) ? reinterpret_cast<const TX*>(z) : reinterpret_cast<const TX*>(zf);
+        TX* xs = reinterpret_cast<TX*>(xs_raw);
+        if (stage_x) {
+            for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xs[i] = __ldcg(xg + i);
+            __syncthreads();
+        }
         for (int64_t row = warp; row < n; row += nwarps) {
-            const TA* a = A + row * lda;
             double acc;
-            // four independent accumulators keep four loads per lane in flight
-            if constexpr (sizeof(TA) == 8) {
-                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                int64_t j = lane;
-                for (; j + 96 < n; j += 128) {
-                    s0 = fma((double)a[j], p[j], s0);
-                    s1 = fma((double)a[j + 32], p[j + 32], s1);
-                    s2 = fma((double)a[j + 64], p[j + 64], s2);
-                    s3 = fma((double)a[j + 96], p[j + 96], s3);
-                }
-                for (; j < n; j += 32) s0 = fma((double)a[j], p[j], s0);
-                acc = warp_sum((s0 + s1) + (s2 + s3));
-            } else {
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-                int64_t j = lane;
-                for (; j + 96 < n; j += 128) {
-                    s0 = fmaf((float)a[j], pf[j], s0);
-                    s1 = fmaf((float)a[j + 32], pf[j + 32], s1);
-                    s2 = fmaf((float)a[j + 64], pf[j + 64], s2);
-                    s3 = fmaf((float)a[j + 96], pf[j + 96], s3);
-                }
-                for (; j < n; j += 32) s0 = fmaf((float)a[j], pf[j], s0);
-                acc = warp_sum((double)s0 + (double)s1 + ((double)s2 + (double)s3));
-            }
+            if (stage_x) acc = (double)row_dot<TA, TX, TX, true>(A + row * lda, xs, n, lane);
+            else acc = (double)row_dot<TA, TX, TX, false>(A + row * lda, xg, n, lane);
             if (lane == 0) {
-                q[row] = acc;
-                pq = fma(p[row], acc, pq);
+                w[row] = acc;
+                dl = fma(__ldcg(z + row), acc, dl);
             }
         }
-        pq = block_total(pq, sh);
-        if (threadIdx.x == 0) part[2 * blockIdx.x] = pq;
-        grid.sync();
-        pq = grid_total(part, nb, 2, sh);
-        if (!(pq > 0.0)) {
+        dl = block_total(dl, sh);
+        if (threadIdx.x == 0) partD[blockIdx.x] = dl;
+        if (!tc::grid_barrier(gbar, epoch, nb, err)) return;
+        // U
+        const double delta = grid_total(partD, nb, 1, sh);
+        const double beta = (it == 0) ? 0.0 : gamma / gamma_prev;
+        const double den = (it == 0) ? delta : delta - beta * gamma / alpha_prev;
+        if (!(den > 0.0)) {
             breakdown = 1;
             break;
         }
-        const double alpha = rz / pq;
-        grid.sync();
-        double a1 = 0.0, c1 = 0.0;
+        const double alpha = gamma / den;
+        double g1 = 0.0, c1 = 0.0;
         for (int64_t i = tid; i < n; i += nthreads) {
-            u[i] = fma(alpha, p[i], u[i]);
-            const double ri = fma(-alpha, q[i], r[i]);
+            const double pi = fma(beta, p[i], z[i]);
+            const double si = fma(beta, sv[i], __ldcg(w + i));
+            p[i] = pi;
+            sv[i] = si;
+            u[i] = fma(alpha, pi, u[i]);
+            const double ri = fma(-alpha, si, r[i]);
             r[i] = ri;
             const double zi = dinv[i] * ri;
             z[i] = zi;
-            a1 = fma(ri, zi, a1);
+            if (zf) zf[i] = (float)zi;
+            g1 = fma(ri, zi, g1);
             c1 = fma(ri, ri, c1);
         }
-        a1 = block_total(a1, sh);
+        g1 = block_total(g1, sh);
         c1 = block_total(c1, sh);
         if (threadIdx.x == 0) {
-            part[2 * blockIdx.x] = a1;
-            part[2 * blockIdx.x + 1] = c1;
+            partG[blockIdx.x] = g1;
+            partR[blockIdx.x] = c1;
         }
-        grid.sync();
-        const double rz_new = grid_total(part, nb, 2, sh);
-        rr = grid_total(part + 1, nb, 2, sh);
-        const double beta = rz_new / rz;
-        rz = rz_new;
+        if (!tc::grid_barrier(gbar, epoch, nb, err)) return;
+        gamma_prev = gamma;
+        alpha_prev = alpha;
+        gamma = grid_total(partG, nb, 1, sh);
+        rr = grid_total(partR, nb, 1, sh);
         ++it;
-        for (int64_t i = tid; i < n; i += nthreads) {
-            const double pi = fma(beta, p[i], z[i]);
-            p[i] = pi;
-            if (pf) pf[i] = (float)pi;
-        }
-        grid.sync();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         S->rr = rr;
@@ -603,16 +656,30 @@ static bool pcg_persistent(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const 
     if (!coop) return false;
     int per_sm = 0;
     const void* fn = (dtype == FL_F64) ? (const void*)pcg_persistent_kernel<double> : (const void*)pcg_persistent_kernel<float>;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_THREADS, 0) != cudaSuccess || per_sm < 1) {
+    // every block keeps a shared-memory copy of the multiplied vector when it fits in 96 KiB
+    const size_t xbytes = (size_t)n * (dtype == FL_F64 ? sizeof(double) : sizeof(float));
+    int stage_x = xbytes <= 96 * 1024 ? 1 : 0;
+    const size_t smem = stage_x ? xbytes : 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_THREADS, smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return false;
     }
     const int blocks = std::min(sms * std::min(per_sm, 2), PCG_MAX_BLOCKS);
-    float* pf = (dtype == FL_F64) ? nullptr : w.xf;
+    float* zf = (dtype == FL_F64) ? nullptr : w.xf;
     const TAVoid Mv{M};
-    void* args[] = {(void*)&n, (void*)&Mv.p, (void*)&ldm, (void*)&dinv, (void*)&rhs, (void*)&d, (void*)&w.r, (void*)&w.z,
-                    (void*)&w.p, (void*)&w.q, (void*)&pf, (void*)&w.part, (void*)&w.s, (void*)&tol, (void*)&maxit};
-    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(PCG_THREADS), args, 0, st);
+    int* err = reinterpret_cast<int*>(w.part + 3 * 1024);
+    if (cudaMemsetAsync(w.gbar, 0, sizeof(unsigned), st) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    void* args[] = {(void*)&n,   (void*)&Mv.p,   (void*)&ldm,  (void*)&dinv, (void*)&rhs, (void*)&d,
+                    (void*)&w.r, (void*)&w.z,    (void*)&w.p,  (void*)&w.q,  (void*)&w.sv, (void*)&zf,
+                    (void*)&w.part, (void*)&w.gbar, (void*)&w.s, (void*)&tol, (void*)&maxit, (void*)&err,
+                    (void*)&stage_x};
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(PCG_THREADS), args, smem, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -668,8 +735,11 @@ static int pcg(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int
                const double* rhs, double* d, double tol, int maxit, int* its, double* relres, cudaStream_t st) {
     int pst = FL_OK;
     if (pcg_persistent(h, w, n, dtype, M, ldm, dinv, rhs, d, tol, maxit, st, &pst)) {
+        int err = 0;
         FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+        FL_CU(h, cudaMemcpyAsync(&err, w.part + 3 * 1024, sizeof(int), cudaMemcpyDeviceToHost, st));
         FL_CU(h, cudaStreamSynchronize(st));
+        if (err != 0) return set_err(h, FL_ETIMEOUT, "a grid barrier of the persistent solver gave up");
         const CgScalars& S = *w.s_host;
         *its = S.it;
         *relres = (S.rz > 0.0) ? std::sqrt(S.rr / S.rz) : 0.0;
