@@ -472,49 +472,50 @@ __device__ __forceinline__ double grid_total(const double* part, int nb, int str
     return block_total(acc, sh);
 }
 
-// Row `row` of A times x (float64 or float32 entries), one warp: 16-byte loads of A after
-// peeling to an aligned start, four loads per lane in flight, x read through the cache.
+// Entry v of a 16-byte vector of float64 (v < 2) or float32 (v < 4) values.
+template <typename TA>
+__device__ __forceinline__ TA vec_elem(const uint4& u, int v) {
+    if constexpr (sizeof(TA) == 8) return v == 0 ? __hiloint2double((int)u.y, (int)u.x) : __hiloint2double((int)u.w, (int)u.z);
+    else return __uint_as_float(v == 0 ? u.x : v == 1 ? u.y : v == 2 ? u.z : u.w);
+}
+
 template <bool SH, typename TX>
 __device__ __forceinline__ TX xload(const TX* p) {
     if constexpr (SH) return *p;  // shared-memory copy
     else return __ldcg(p);
 }
+
+// Row `row` of A times x (float64 or float32 entries), one warp: 16-byte loads of A after
+// peeling to an aligned start, six loads per lane in flight (the last round predicated,
+// masked entries multiply zero); x is the block's shared-memory copy (SH) or, when it does
+// not fit, read through L2 (other blocks rewrite it between products).
 template <typename TA, typename TX, typename TS, bool SH>
 __device__ __forceinline__ TS row_dot(const TA* __restrict__ a, const TX* __restrict__ x, int64_t n, int lane) {
     constexpr int V = 16 / sizeof(TA);  // entries per 16-byte load
+    constexpr int U = 6;                // loads in flight per lane
     const int peel = (int)((V - (((uintptr_t)a / sizeof(TA)) & (V - 1))) & (V - 1));
-    TS s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    TS s[4] = {0, 0, 0, 0};
     const int head = (int)((int64_t)peel < n ? (int64_t)peel : n);
-    if (lane < head) s0 = (TS)a[lane] * (TS)xload<SH>(x + lane);
+    if (lane < head) s[0] = (TS)a[lane] * (TS)xload<SH>(x + lane);
     const int64_t nv = (n - head) / V;  // whole vectors after the peel
-    const TA* av = a + head;
+    const uint4* av = reinterpret_cast<const uint4*>(a + head);
     const TX* xv = x + head;
-    int64_t k = lane;
-    for (; k + 96 < nv; k += 128) {
-        const uint4 u0 = __ldcs(reinterpret_cast<const uint4*>(av) + k);
-        const uint4 u1 = __ldcs(reinterpret_cast<const uint4*>(av) + k + 32);
-        const uint4 u2 = __ldcs(reinterpret_cast<const uint4*>(av) + k + 64);
-        const uint4 u3 = __ldcs(reinterpret_cast<const uint4*>(av) + k + 96);
-        const TA* e0 = reinterpret_cast<const TA*>(&u0);
-        const TA* e1 = reinterpret_cast<const TA*>(&u1);
-        const TA* e2 = reinterpret_cast<const TA*>(&u2);
-        const TA* e3 = reinterpret_cast<const TA*>(&u3);
+    for (int64_t k0 = lane; k0 < nv; k0 += 32 * U) {
+        uint4 u[U];
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            s0 += (TS)e0[v] * (TS)xload<SH>(xv + k * V + v);
-            s1 += (TS)e1[v] * (TS)xload<SH>(xv + (k + 32) * V + v);
-            s2 += (TS)e2[v] * (TS)xload<SH>(xv + (k + 64) * V + v);
-            s3 += (TS)e3[v] * (TS)xload<SH>(xv + (k + 96) * V + v);
+        for (int j = 0; j < U; ++j) {
+            const int64_t k = k0 + 32 * j;
+            u[j] = k < nv ? __ldcs(av + k) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const int64_t k = k0 + 32 * j < nv ? k0 + 32 * j : nv - 1;  // masked: a zero times a valid x
+#pragma unroll
+            for (int v = 0; v < V; ++v) s[j & 3] += (TS)vec_elem<TA>(u[j], v) * (TS)xload<SH>(xv + k * V + v);
         }
     }
-    for (; k < nv; k += 32) {
-        const uint4 u0 = __ldcs(reinterpret_cast<const uint4*>(av) + k);
-        const TA* e0 = reinterpret_cast<const TA*>(&u0);
-#pragma unroll
-        for (int v = 0; v < V; ++v) s0 += (TS)e0[v] * (TS)xload<SH>(xv + k * V + v);
-    }
-    for (int64_t j = head + nv * V + lane; j < n; j += 32) s1 += (TS)a[j] * (TS)xload<SH>(x + j);
-    return warp_sum((s0 + s1) + (s2 + s3));
+    for (int64_t j = head + nv * V + lane; j < n; j += 32) s[1] += (TS)a[j] * (TS)xload<SH>(x + j);
+    return warp_sum((s[0] + s[1]) + (s[2] + s[3]));
 }
 
 // Persistent Jacobi-PCG in the Chronopoulos-Gear arrangement (one cooperative launch):
@@ -529,14 +530,14 @@ __device__ __forceinline__ TS row_dot(const TA* __restrict__ a, const TX* __rest
 // scalars and take the same branch.  A float32 matrix (the inner solver of the refinement)
 // multiplies a float32 copy of z with float32 row sums.  Breakdown: a non-positive
 // denominator (p.Ap <= 0).
-template <typename TA>
-__global__ void __launch_bounds__(PCG_THREADS) pcg_persistent_kernel(int64_t n, const TA* __restrict__ A, int64_t lda,
+template <typename TA, bool SH>
+__global__ void __launch_bounds__(PCG_THREADS, 2) pcg_persistent_kernel(int64_t n, const TA* __restrict__ A, int64_t lda,
                                                                       const double* __restrict__ dinv,
                                                                       const double* __restrict__ rhs, double* u, double* r,
                                                                       double* z, double* p, double* w, double* sv,
                                                                       float* zf, double* part, unsigned* gbar,
-                                                                      CgScalars* S, double tol, int maxit, int* err,
-                                                                      int stage_x) {
+                                                                      CgScalars* S, double tol, int maxit, int* err) {
+    constexpr bool stage_x = SH;
     __shared__ double sh[PCG_THREADS / 32];
     extern __shared__ __align__(16) unsigned char xs_raw[];  // copy of z (or zf) when it fits
     const int nb = gridDim.x;
@@ -580,17 +581,28 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_persistent_kernel(int64_t n, 
         using TX = typename std::conditional<sizeof(TA) == 8, double, float>::type;
         const TX* xg = (sizeof(TA) == 8) ? reinterpret_cast<const TX*>(z) : reinterpret_cast<const TX*>(zf);
         TX* xs = reinterpret_cast<TX*>(xs_raw);
-        if (stage_x) {
-            for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xs[i] = __ldcg(xg + i);
+        if constexpr (SH) {
+            // 16-byte copies, four in flight per thread (the workspace vectors are 256-byte aligned)
+            const int64_t nq = n * (int64_t)sizeof(TX) / 16;
+            const uint4* src = reinterpret_cast<const uint4*>(xg);
+            uint4* dst = reinterpret_cast<uint4*>(xs);
+            for (int64_t i0 = threadIdx.x; i0 < nq; i0 += 4 * blockDim.x) {
+                uint4 v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (i0 + j * blockDim.x < nq) v[j] = __ldcg(src + i0 + j * blockDim.x);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (i0 + j * blockDim.x < nq) dst[i0 + j * blockDim.x] = v[j];
+            }
+            for (int64_t i = nq * 16 / (int64_t)sizeof(TX) + threadIdx.x; i < n; i += blockDim.x) xs[i] = __ldcg(xg + i);
             __syncthreads();
         }
         for (int64_t row = warp; row < n; row += nwarps) {
-            double acc;
-            if (stage_x) acc = (double)row_dot<TA, TX, TX, true>(A + row * lda, xs, n, lane);
-            else acc = (double)row_dot<TA, TX, TX, false>(A + row * lda, xg, n, lane);
+            const double acc = (double)row_dot<TA, TX, TX, SH>(A + row * lda, SH ? xs : xg, n, lane);
             if (lane == 0) {
                 w[row] = acc;
-                dl = fma(__ldcg(z + row), acc, dl);
+                dl = fma((sizeof(TA) == 8 && stage_x) ? (double)xs[row] : __ldcg(z + row), acc, dl);
             }
         }
         dl = block_total(dl, sh);
@@ -655,10 +667,12 @@ static bool pcg_persistent(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (!coop) return false;
     int per_sm = 0;
-    const void* fn = (dtype == FL_F64) ? (const void*)pcg_persistent_kernel<double> : (const void*)pcg_persistent_kernel<float>;
     // every block keeps a shared-memory copy of the multiplied vector when it fits in 96 KiB
     const size_t xbytes = (size_t)n * (dtype == FL_F64 ? sizeof(double) : sizeof(float));
-    int stage_x = xbytes <= 96 * 1024 ? 1 : 0;
+    const bool stage_x = xbytes <= 96 * 1024;
+    const void* fn = (dtype == FL_F64)
+                         ? (stage_x ? (const void*)pcg_persistent_kernel<double, true> : (const void*)pcg_persistent_kernel<double, false>)
+                         : (stage_x ? (const void*)pcg_persistent_kernel<float, true> : (const void*)pcg_persistent_kernel<float, false>);
     const size_t smem = stage_x ? xbytes : 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1)) !=
             cudaSuccess ||
@@ -677,8 +691,7 @@ static bool pcg_persistent(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const 
     }
     void* args[] = {(void*)&n,   (void*)&Mv.p,   (void*)&ldm,  (void*)&dinv, (void*)&rhs, (void*)&d,
                     (void*)&w.r, (void*)&w.z,    (void*)&w.p,  (void*)&w.q,  (void*)&w.sv, (void*)&zf,
-                    (void*)&w.part, (void*)&w.gbar, (void*)&w.s, (void*)&tol, (void*)&maxit, (void*)&err,
-                    (void*)&stage_x};
+                    (void*)&w.part, (void*)&w.gbar, (void*)&w.s, (void*)&tol, (void*)&maxit, (void*)&err};
     const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(PCG_THREADS), args, smem, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
