@@ -451,25 +451,51 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
 // vector entries are split over a fixed grid; after each phase every block adds the
 // per-block partial sums in the same order, so all blocks hold bitwise identical
 // scalars and take the same branch (no block can leave while others wait).
-constexpr int PCG_THREADS = 256;
+constexpr int PCG_THREADS = 512;  // one block of 16 warps per SM
+constexpr int PCG_WARPS = PCG_THREADS / 32;
 constexpr int PCG_MAX_BLOCKS = 1024;
 
-__device__ __forceinline__ double block_total(double v, double* sh) {
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
-    return t;  // same value in every thread
+template <typename T>
+__device__ __forceinline__ T warp_total(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-// sum of part[0..nb) in index order, computed by every thread (identical results)
-__device__ __forceinline__ double grid_total(const double* part, int nb, int stride, double* sh) {
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += part[(int64_t)i * stride];
-    return block_total(acc, sh);
+// Block sums of NV values, identical in every thread: warp sums, then warp 0 sums the
+// per-warp results in warp order.  sh holds NV * 33 values.
+template <typename T, int NV>
+__device__ __forceinline__ void block_totals(T (&v)[NV], T* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_total(v[k]);
+    __syncthreads();  // sh may still be read from the previous call
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k * 32 + w] = v[k];
+    __syncthreads();
+    if (w == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const T t = warp_total(lane < PCG_WARPS ? sh[k * 32 + lane] : T(0));
+            if (lane == 0) sh[NV * 32 + k] = t;
+        }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = sh[NV * 32 + k];
+}
+
+// Sums over the blocks' partials part[k * 1024 + b], b < nb, in a fixed order (the same
+// result in every block, so that all blocks take the same branch).
+template <typename T, int NV>
+__device__ __forceinline__ void grid_totals(T (&v)[NV], const T* part, const int (&slot)[NV], int nb, T* sh) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        T a = 0;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) a += __ldcg(part + slot[k] * 1024 + i);
+        v[k] = a;
+    }
+    block_totals<T, NV>(v, sh);
 }
 
 // Entry v of a 16-byte vector of float64 (v < 2) or float32 (v < 4) values.
@@ -522,176 +548,241 @@ __device__ __forceinline__ TS row_dot(const TA* __restrict__ a, const TX* __rest
 // the product is taken of the preconditioned residual, w = A z, and s = A p is carried by
 // recurrence, so both inner products of a step come from one pass and a step needs two
 // grid barriers:
-//   M: w = A z, partial delta = z.w
+//   M: w = A z for the block's own rows, partial delta = z.w
 //   U: beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev)
 //      (beta = 0, alpha = gamma / delta first); p = z + beta p, s = w + beta s, u += alpha p,
 //      r -= alpha s, z = D^-1 r; partial gamma = r.z and r.r
-// Every block sums the per-block partials in the same order, so all blocks hold the same
-// scalars and take the same branch.  A float32 matrix (the inner solver of the refinement)
-// multiplies a float32 copy of z with float32 row sums.  Breakdown: a non-positive
-// denominator (p.Ap <= 0).
-template <typename TA, bool SH>
-__global__ void __launch_bounds__(PCG_THREADS, 2) pcg_persistent_kernel(int64_t n, const TA* __restrict__ A, int64_t lda,
-                                                                      const double* __restrict__ dinv,
-                                                                      const double* __restrict__ rhs, double* u, double* r,
-                                                                      double* z, double* p, double* w, double* sv,
-                                                                      float* zf, double* part, unsigned* gbar,
-                                                                      CgScalars* S, double tol, int maxit, int* err) {
-    constexpr bool stage_x = SH;
-    __shared__ double sh[PCG_THREADS / 32];
-    extern __shared__ __align__(16) unsigned char xs_raw[];  // copy of z (or zf) when it fits
+// Block b owns rows [b rpb, (b + 1) rpb) of the product and of every vector, so w never
+// leaves shared memory.  T is the type of the matrix, the vectors and the scalars: float64
+// for the plain solve, float32 for the inner solve of the refinement (whose float64
+// residual corrects it), so that no float64 arithmetic (a slow pipe on this part) sits on
+// the float32 iteration's critical path.  Every block sums the per-block partials in the
+// same order, so all blocks hold the same scalars and take the same branch.
+// MODE 2: the block's rows of A stay in shared memory for the whole solve (and z is
+// staged there each step); MODE 1: z staged, A streamed; MODE 0: both streamed.
+// Breakdown: a non-positive denominator (p.Ap <= 0).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(PCG_THREADS, 1)
+    pcg_persistent_kernel(int64_t n, int64_t rpb, int64_t lds, const T* __restrict__ A, int64_t lda,
+                          const double* __restrict__ dinv, const double* __restrict__ rhs, double* d, T* u, T* r,
+                          T* z, T* p, T* sv, T* dv, T* part, unsigned* gbar, CgScalars* S, double tol, int maxit,
+                          int* err) {
+    constexpr int V = 16 / sizeof(T);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T sh[2 * 33];
+    T* xs = reinterpret_cast<T*>(smem_raw);  // [lds] copy of z (MODE >= 1)
+    const int64_t rpb_pad = (rpb + V - 1) / V * V;
+    T* ws = xs + (MODE >= 1 ? lds : 0);  // [rpb] products of the own rows
+    T* As = ws + rpb_pad;                 // [rpb][lds] own rows of A (MODE 2)
     const int nb = gridDim.x;
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t nthreads = (int64_t)nb * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
-    double* partD = part;
-    double* partG = part + 1024;
-    double* partR = part + 2048;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r0 = blockIdx.x * rpb;
+    const int64_t r1 = (r0 + rpb < n) ? r0 + rpb : n;
+    constexpr int D_ = 0, G_ = 1, R_ = 2;
     unsigned epoch = 0;
-    // start: u = 0, r = rhs, z = D^-1 r, p = s = 0
-    double g0 = 0.0, c0 = 0.0;
-    for (int64_t i = tid; i < n; i += nthreads) {
-        const double ri = rhs[i];
-        const double zi = dinv[i] * ri;
-        u[i] = 0.0;
-        r[i] = ri;
-        z[i] = zi;
-        p[i] = 0.0;
-        sv[i] = 0.0;
-        if (zf) zf[i] = (float)zi;
-        g0 = fma(ri, zi, g0);
-        c0 = fma(ri, ri, c0);
+    if constexpr (MODE == 2) {
+        for (int64_t row = r0; row < r1; ++row)
+            for (int64_t j = threadIdx.x; j < lds; j += blockDim.x)
+                As[(row - r0) * lds + j] = j < n ? A[row * lda + j] : T(0);
     }
-    g0 = block_total(g0, sh);
-    c0 = block_total(c0, sh);
-    if (threadIdx.x == 0) {
-        partG[blockIdx.x] = g0;
-        partR[blockIdx.x] = c0;
+    if constexpr (MODE >= 1)
+        for (int64_t j = n + threadIdx.x; j < lds; j += blockDim.x) xs[j] = T(0);
+    // start: u = 0, r = rhs, z = D^-1 r, p = s = 0
+    {
+        T v[2] = {0, 0};
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const T ri = (T)rhs[i];
+            T di;
+            if constexpr (sizeof(T) == 4) {
+                di = (T)dinv[i];
+                dv[i] = di;
+            } else {
+                di = dinv[i];
+            }
+            const T zi = di * ri;
+            u[i] = 0;
+            r[i] = ri;
+            z[i] = zi;
+            p[i] = 0;
+            sv[i] = 0;
+            v[0] += ri * zi;
+            v[1] += ri * ri;
+        }
+        block_totals<T, 2>(v, sh);
+        if (threadIdx.x == 0) {
+            part[G_ * 1024 + blockIdx.x] = v[0];
+            part[R_ * 1024 + blockIdx.x] = v[1];
+        }
     }
     if (!tc::grid_barrier(gbar, epoch, nb, err)) return;
-    double gamma = grid_total(partG, nb, 1, sh);
-    const double rr0 = grid_total(partR, nb, 1, sh);
-    const double stop = tol * tol * rr0;
-    double rr = rr0, gamma_prev = 1.0, alpha_prev = 1.0;
+    T gamma, rr0;
+    {
+        T v[2];
+        grid_totals<T, 2>(v, part, {G_, R_}, nb, sh);
+        gamma = v[0];
+        rr0 = v[1];
+    }
+    const T stop = (T)(tol * tol) * rr0;
+    T rr = rr0, gamma_prev = 1, alpha_prev = 1;
     int it = 0, breakdown = 0;
     while (rr > stop && it < maxit) {
-        // M: w = A z and the partial z.w
-        double dl = 0.0;
-        using TX = typename std::conditional<sizeof(TA) == 8, double, float>::type;
-        const TX* xg = (sizeof(TA) == 8) ? reinterpret_cast<const TX*>(z) : reinterpret_cast<const TX*>(zf);
-        TX* xs = reinterpret_cast<TX*>(xs_raw);
-        if constexpr (SH) {
-            // 16-byte copies, four in flight per thread (the workspace vectors are 256-byte aligned)
-            const int64_t nq = n * (int64_t)sizeof(TX) / 16;
-            const uint4* src = reinterpret_cast<const uint4*>(xg);
+        // M: w = A z on the own rows, partial z.w
+        if constexpr (MODE >= 1) {
+            const int64_t nq = n * (int64_t)sizeof(T) / 16;  // z is 256-byte aligned
+            const uint4* src = reinterpret_cast<const uint4*>(z);
             uint4* dst = reinterpret_cast<uint4*>(xs);
             for (int64_t i0 = threadIdx.x; i0 < nq; i0 += 4 * blockDim.x) {
-                uint4 v[4];
+                uint4 q[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (i0 + j * blockDim.x < nq) v[j] = __ldcg(src + i0 + j * blockDim.x);
+                    if (i0 + j * blockDim.x < nq) q[j] = __ldcg(src + i0 + j * blockDim.x);
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (i0 + j * blockDim.x < nq) dst[i0 + j * blockDim.x] = v[j];
+                    if (i0 + j * blockDim.x < nq) dst[i0 + j * blockDim.x] = q[j];
             }
-            for (int64_t i = nq * 16 / (int64_t)sizeof(TX) + threadIdx.x; i < n; i += blockDim.x) xs[i] = __ldcg(xg + i);
+            for (int64_t i = nq * 16 / (int64_t)sizeof(T) + threadIdx.x; i < n; i += blockDim.x) xs[i] = __ldcg(z + i);
             __syncthreads();
         }
-        for (int64_t row = warp; row < n; row += nwarps) {
-            const double acc = (double)row_dot<TA, TX, TX, SH>(A + row * lda, SH ? xs : xg, n, lane);
+        T dl[1] = {0};
+        for (int64_t row = r0 + warp; row < r1; row += PCG_WARPS) {
+            T acc;
+            if constexpr (MODE == 2) {
+                const uint4* a4 = reinterpret_cast<const uint4*>(As + (row - r0) * lds);
+                const uint4* x4 = reinterpret_cast<const uint4*>(xs);
+                T s0 = 0, s1 = 0;
+                for (int64_t q = lane; q < lds / V; q += 32) {
+                    const uint4 av = a4[q], xv = x4[q];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        if (v & 1) s1 = fma(vec_elem<T>(av, v), vec_elem<T>(xv, v), s1);
+                        else s0 = fma(vec_elem<T>(av, v), vec_elem<T>(xv, v), s0);
+                    }
+                }
+                acc = warp_total(s0 + s1);
+            } else {
+                acc = row_dot<T, T, T, (MODE == 1)>(A + row * lda, MODE == 1 ? xs : z, n, lane);
+            }
             if (lane == 0) {
-                w[row] = acc;
-                dl = fma((sizeof(TA) == 8 && stage_x) ? (double)xs[row] : __ldcg(z + row), acc, dl);
+                ws[row - r0] = acc;
+                dl[0] += (MODE >= 1 ? xs[row] : __ldcg(z + row)) * acc;
             }
         }
-        dl = block_total(dl, sh);
-        if (threadIdx.x == 0) partD[blockIdx.x] = dl;
+        block_totals<T, 1>(dl, sh);
+        if (threadIdx.x == 0) part[D_ * 1024 + blockIdx.x] = dl[0];
         if (!tc::grid_barrier(gbar, epoch, nb, err)) return;
         // U
-        const double delta = grid_total(partD, nb, 1, sh);
-        const double beta = (it == 0) ? 0.0 : gamma / gamma_prev;
-        const double den = (it == 0) ? delta : delta - beta * gamma / alpha_prev;
-        if (!(den > 0.0)) {
+        T delta[1];
+        grid_totals<T, 1>(delta, part, {D_}, nb, sh);
+        const T beta = (it == 0) ? T(0) : gamma / gamma_prev;
+        const T den = (it == 0) ? delta[0] : delta[0] - beta * gamma / alpha_prev;
+        if (!(den > T(0))) {
             breakdown = 1;
             break;
         }
-        const double alpha = gamma / den;
-        double g1 = 0.0, c1 = 0.0;
-        for (int64_t i = tid; i < n; i += nthreads) {
-            const double pi = fma(beta, p[i], z[i]);
-            const double si = fma(beta, sv[i], __ldcg(w + i));
+        const T alpha = gamma / den;
+        T v[2] = {0, 0};
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const T pi = fma(beta, p[i], z[i]);
+            const T si = fma(beta, sv[i], ws[i - r0]);
             p[i] = pi;
             sv[i] = si;
             u[i] = fma(alpha, pi, u[i]);
-            const double ri = fma(-alpha, si, r[i]);
+            const T ri = fma(-alpha, si, r[i]);
             r[i] = ri;
-            const double zi = dinv[i] * ri;
+            const T zi = dv[i] * ri;
             z[i] = zi;
-            if (zf) zf[i] = (float)zi;
-            g1 = fma(ri, zi, g1);
-            c1 = fma(ri, ri, c1);
+            v[0] = fma(ri, zi, v[0]);
+            v[1] = fma(ri, ri, v[1]);
         }
-        g1 = block_total(g1, sh);
-        c1 = block_total(c1, sh);
+        block_totals<T, 2>(v, sh);
         if (threadIdx.x == 0) {
-            partG[blockIdx.x] = g1;
-            partR[blockIdx.x] = c1;
+            part[G_ * 1024 + blockIdx.x] = v[0];
+            part[R_ * 1024 + blockIdx.x] = v[1];
         }
         if (!tc::grid_barrier(gbar, epoch, nb, err)) return;
         gamma_prev = gamma;
         alpha_prev = alpha;
-        gamma = grid_total(partG, nb, 1, sh);
-        rr = grid_total(partR, nb, 1, sh);
+        grid_totals<T, 2>(v, part, {G_, R_}, nb, sh);
+        gamma = v[0];
+        rr = v[1];
         ++it;
     }
+    if constexpr (sizeof(T) == 4)
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) d[i] = (double)u[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        S->rr = rr;
-        S->stop = stop;
+        S->rr = (double)rr;
+        S->stop = (double)stop;
         S->it = it;
         S->breakdown = breakdown;
         S->done = 1;
-        S->rz = rr0;  // initial residual norm^2, read back by the host
+        S->rz = (double)rr0;  // initial residual norm^2, read back by the host
     }
 }
 
 // Launch the persistent solver if the device supports cooperative launches and the grid
 // fits; returns false (nothing launched) otherwise.
+template <typename T, int MODE>
+static const void* pcg_fn() {
+    return (const void*)pcg_persistent_kernel<T, MODE>;
+}
+
 static bool pcg_persistent(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int64_t ldm,
                            const double* dinv, const double* rhs, double* d, double tol, int maxit, cudaStream_t st,
                            int* status) {
     if (dtype == FL_BF16 || h->no_persistent) return false;
-    int dev = 0, coop = 0, sms = 0;
+    int dev = 0, coop = 0, sms = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (!coop) return false;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop || sms < 1) return false;
+    const bool f64 = dtype == FL_F64;
+    const size_t es = f64 ? sizeof(double) : sizeof(float);
+    const int64_t V = 16 / (int64_t)es;
+    const int blocks = std::min(sms, PCG_MAX_BLOCKS);
+    const int64_t rpb = (n + blocks - 1) / blocks;
+    const int64_t rpb_pad = (rpb + V - 1) / V * V;
+    const int64_t lds = (n + V - 1) / V * V;
+    const size_t budget = optin > 4096 ? (size_t)optin - 2048 : 0;  // room for the static reduction buffers
+    int mode;
+    size_t smem;
+    if ((size_t)(lds + rpb_pad + rpb * lds) * es <= budget) {
+        mode = 2;
+        smem = (size_t)(lds + rpb_pad + rpb * lds) * es;
+    } else if ((size_t)(lds + rpb_pad) * es <= budget) {
+        mode = 1;
+        smem = (size_t)(lds + rpb_pad) * es;
+    } else if ((size_t)rpb_pad * es <= budget) {
+        mode = 0;
+        smem = (size_t)rpb_pad * es;
+    } else {
+        return false;
+    }
+    const void* fn = f64 ? (mode == 2 ? pcg_fn<double, 2>() : mode == 1 ? pcg_fn<double, 1>() : pcg_fn<double, 0>())
+                         : (mode == 2 ? pcg_fn<float, 2>() : mode == 1 ? pcg_fn<float, 1>() : pcg_fn<float, 0>());
     int per_sm = 0;
-    // every block keeps a shared-memory copy of the multiplied vector when it fits in 96 KiB
-    const size_t xbytes = (size_t)n * (dtype == FL_F64 ? sizeof(double) : sizeof(float));
-    const bool stage_x = xbytes <= 96 * 1024;
-    const void* fn = (dtype == FL_F64)
-                         ? (stage_x ? (const void*)pcg_persistent_kernel<double, true> : (const void*)pcg_persistent_kernel<double, false>)
-                         : (stage_x ? (const void*)pcg_persistent_kernel<float, true> : (const void*)pcg_persistent_kernel<float, false>);
-    const size_t smem = stage_x ? xbytes : 0;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1)) !=
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 16)) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_THREADS, smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return false;
     }
-    const int blocks = std::min(sms * std::min(per_sm, 2), PCG_MAX_BLOCKS);
-    float* zf = (dtype == FL_F64) ? nullptr : w.xf;
-    const TAVoid Mv{M};
     int* err = reinterpret_cast<int*>(w.part + 3 * 1024);
     if (cudaMemsetAsync(w.gbar, 0, sizeof(unsigned), st) != cudaSuccess ||
         cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    void* args[] = {(void*)&n,   (void*)&Mv.p,   (void*)&ldm,  (void*)&dinv, (void*)&rhs, (void*)&d,
-                    (void*)&w.r, (void*)&w.z,    (void*)&w.p,  (void*)&w.q,  (void*)&w.sv, (void*)&zf,
-                    (void*)&w.part, (void*)&w.gbar, (void*)&w.s, (void*)&tol, (void*)&maxit, (void*)&err};
+    // vectors: float64 ones in place (u is d itself); float32 ones in the first halves of the
+    // float64 work vectors (u in q, whose product w stays in shared memory), D^-1 in xf
+    void* u = f64 ? (void*)d : (void*)w.q;
+    void* dv = f64 ? (void*)dinv : (void*)w.xf;
+    void* part = (void*)w.part;
+    const TAVoid Mv{M};
+    void* args[] = {(void*)&n,   (void*)&rpb,  (void*)&lds,  (void*)&Mv.p,  (void*)&ldm,   (void*)&dinv,
+                    (void*)&rhs, (void*)&d,    (void*)&u,    (void*)&w.r,   (void*)&w.z,   (void*)&w.p,
+                    (void*)&w.sv, (void*)&dv,  (void*)&part, (void*)&w.gbar, (void*)&w.s,  (void*)&tol,
+                    (void*)&maxit, (void*)&err};
     const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(PCG_THREADS), args, smem, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
