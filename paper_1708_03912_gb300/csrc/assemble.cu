@@ -421,15 +421,23 @@ __global__ void near_pair_fast(int nnear, const int* np_a, const int* np_b, cons
 }
 
 // ---------------------------------------------------------- touching pairs --
-// Common edge / common vertex pairs (2D) and common vertex pairs (1D), float64,
-// one warp per pair: lanes take the points of the (per-s) table in a strided
-// order, then a butterfly sum gives every lane the same totals.
+// Common edge / common vertex pairs (2D) and common vertex pairs (1D), one warp per
+// pair: lanes take the points of the (per-s) table in a strided order, then a
+// butterfly sum gives every lane the same totals.
 // Tables hold the angular / Duffy points with the exact radial factor folded into
-// their weights.
-template <int PW>
+// their weights.  T is the arithmetic type: float64 in the parity mode; float32 in
+// the mixed mode (float32 tables and relative coordinates, the per-pair scale applied
+// in float64), where the float64 version is bound by the slow float64 pipe.
+template <typename T>
+__device__ __forceinline__ T touch_pow(T x, T e) {
+    if constexpr (sizeof(T) == 8) return pow(x, e);
+    else return kpow<0>(x, e);
+}
+
+template <typename T, int PW>
 __global__ void touch_pair_kernel(int ntp, int dim, const int* tp_type, const int* tp_vert, const int* tp_cell,
                                   const int64_t* tp_slot, const double* V, const double* jac_orig,
-                                  const double* rule, RuleOffsets ro, double s, double C, double* contrib) {
+                                  const T* rule, RuleOffsets ro, double s, double C, double* contrib) {
     const int lane = threadIdx.x & 31;
     const int p = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (p >= ntp) return;
@@ -438,45 +446,45 @@ __global__ void touch_pair_kernel(int ntp, int dim, const int* tp_type, const in
     double* out = contrib + tp_slot[p];
     const double jK = jac_orig[tp_cell[2 * p]], jM = jac_orig[tp_cell[2 * p + 1]];
     if (type == 2) {  // 1D common vertex: [a, v, b], h1 = left, h2 = right
-        const double* tb = rule + ro.t_1d;
-        const double h1 = jK, h2 = jM;
-        const double e = -1.0 - 2.0 * s;
-        double acc[6] = {};
+        const T* tb = rule + ro.t_1d;
+        const T h1 = (T)jK, h2 = (T)jM;
+        const T e = (T)(-1.0 - 2.0 * s);
+        T acc[6] = {};
         for (int m = lane; m < ro.n_1d; m += 32) {
-            const double eta = tb[2 * m], wt = tb[2 * m + 1];
-            const double d1[3] = {1.0, -1.0 + eta, -eta};
-            const double d2[3] = {eta, 1.0 - eta, -1.0};
-            const double k1 = wt * pow(h1 + h2 * eta, e), k2 = wt * pow(h1 * eta + h2, e);
+            const T eta = tb[2 * m], wt = tb[2 * m + 1];
+            const T d1[3] = {T(1), T(-1) + eta, -eta};
+            const T d2[3] = {eta, T(1) - eta, T(-1)};
+            const T k1 = wt * touch_pow<T>(h1 + h2 * eta, e), k2 = wt * touch_pow<T>(h1 * eta + h2, e);
             int q = 0;
             for (int i = 0; i < 3; ++i)
                 for (int j = i; j < 3; ++j) acc[q++] += k1 * d1[i] * d1[j] + k2 * d2[i] * d2[j];
         }
         for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
         if (lane == 0) {
-            const double sc = C * h1 * h2 / (3.0 - 2.0 * s);
+            const double sc = C * jK * jM / (3.0 - 2.0 * s);
             int q = 0;
             for (int i = 0; i < 3; ++i)
-                for (int j = i; j < 3; ++j, ++q) out[i * 3 + j] = out[j * 3 + i] = sc * acc[q];
+                for (int j = i; j < 3; ++j, ++q) out[i * 3 + j] = out[j * 3 + i] = sc * (double)acc[q];
         }
         return;
     }
-    const double e2 = -(1.0 + s);
+    const T e2 = (T)(-(1.0 + s));
     if (type == 0) {  // common edge [P,Q], thirds R (K) and Rt (M)
         const double *P_ = V + 2 * tv[0], *Q_ = V + 2 * tv[1], *R_ = V + 2 * tv[2], *Rt = V + 2 * tv[3];
-        const double a[2] = {Q_[0] - P_[0], Q_[1] - P_[1]};
-        const double b[2] = {R_[0] - Q_[0], R_[1] - Q_[1]};
-        const double c[2] = {-(Rt[0] - Q_[0]), -(Rt[1] - Q_[1])};
-        const double* tb = rule + ro.t_edge;
-        double acc[10] = {};
+        const T a[2] = {(T)(Q_[0] - P_[0]), (T)(Q_[1] - P_[1])};
+        const T b[2] = {(T)(R_[0] - Q_[0]), (T)(R_[1] - Q_[1])};
+        const T c[2] = {(T)(-(Rt[0] - Q_[0])), (T)(-(Rt[1] - Q_[1]))};
+        const T* tb = rule + ro.t_edge;
+        T acc[10] = {};
         for (int m = lane; m < ro.n_edge; m += 32) {
-            const double* r = tb + 8 * m;  // dphi[4], w1, w2, w3, weight
-            const double x = a[0] * r[4] + b[0] * r[5] + c[0] * r[6];
-            const double y = a[1] * r[4] + b[1] * r[5] + c[1] * r[6];
-            const double f = r[7] * kpow<PW>(x * x + y * y, e2);
+            const T* r = tb + 8 * m;  // dphi[4], w1, w2, w3, weight
+            const T x = a[0] * r[4] + b[0] * r[5] + c[0] * r[6];
+            const T y = a[1] * r[4] + b[1] * r[5] + c[1] * r[6];
+            const T f = r[7] * kpow<PW>(x * x + y * y, e2);
             int q = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const double fi = f * r[i];
+                const T fi = f * r[i];
 #pragma unroll
                 for (int j = i; j < 4; ++j) acc[q++] += fi * r[j];
             }
@@ -487,25 +495,25 @@ __global__ void touch_pair_kernel(int ntp, int dim, const int* tp_type, const in
             const double sc = C * jK * jM / ((3.0 - 2.0 * s) * (4.0 - 2.0 * s));
             int q = 0;
             for (int i = 0; i < 4; ++i)
-                for (int j = i; j < 4; ++j, ++q) out[i * 4 + j] = out[j * 4 + i] = sc * acc[q];
+                for (int j = i; j < 4; ++j, ++q) out[i * 4 + j] = out[j * 4 + i] = sc * (double)acc[q];
         }
     } else {  // common vertex P: K = (P,Q,R), M = (P,Qt,Rt)
         const double *P_ = V + 2 * tv[0], *Q_ = V + 2 * tv[1], *R_ = V + 2 * tv[2], *Qt = V + 2 * tv[3], *Rt = V + 2 * tv[4];
-        const double a1[2] = {Q_[0] - P_[0], Q_[1] - P_[1]};
-        const double a2[2] = {R_[0] - Q_[0], R_[1] - Q_[1]};
-        const double a3[2] = {-(Qt[0] - P_[0]), -(Qt[1] - P_[1])};
-        const double a4[2] = {-(Rt[0] - Qt[0]), -(Rt[1] - Qt[1])};
-        const double* tb = rule + ro.t_vert;
-        double acc[15] = {};
+        const T a1[2] = {(T)(Q_[0] - P_[0]), (T)(Q_[1] - P_[1])};
+        const T a2[2] = {(T)(R_[0] - Q_[0]), (T)(R_[1] - Q_[1])};
+        const T a3[2] = {(T)(-(Qt[0] - P_[0])), (T)(-(Qt[1] - P_[1]))};
+        const T a4[2] = {(T)(-(Rt[0] - Qt[0])), (T)(-(Rt[1] - Qt[1]))};
+        const T* tb = rule + ro.t_vert;
+        T acc[15] = {};
         for (int m = lane; m < ro.n_vert; m += 32) {
-            const double* r = tb + 10 * m;  // dphi[5], x1, x2, y1, y2, weight
-            const double x = a1[0] * r[5] + a2[0] * r[6] + a3[0] * r[7] + a4[0] * r[8];
-            const double y = a1[1] * r[5] + a2[1] * r[6] + a3[1] * r[7] + a4[1] * r[8];
-            const double f = r[9] * kpow<PW>(x * x + y * y, e2);
+            const T* r = tb + 10 * m;  // dphi[5], x1, x2, y1, y2, weight
+            const T x = a1[0] * r[5] + a2[0] * r[6] + a3[0] * r[7] + a4[0] * r[8];
+            const T y = a1[1] * r[5] + a2[1] * r[6] + a3[1] * r[7] + a4[1] * r[8];
+            const T f = r[9] * kpow<PW>(x * x + y * y, e2);
             int q = 0;
 #pragma unroll
             for (int i = 0; i < 5; ++i) {
-                const double fi = f * r[i];
+                const T fi = f * r[i];
 #pragma unroll
                 for (int j = i; j < 5; ++j) acc[q++] += fi * r[j];
             }
@@ -516,7 +524,7 @@ __global__ void touch_pair_kernel(int ntp, int dim, const int* tp_type, const in
             const double sc = C * jK * jM / (4.0 - 2.0 * s);
             int q = 0;
             for (int i = 0; i < 5; ++i)
-                for (int j = i; j < 5; ++j, ++q) out[i * 5 + j] = out[j * 5 + i] = sc * acc[q];
+                for (int j = i; j < 5; ++j, ++q) out[i * 5 + j] = out[j * 5 + i] = sc * (double)acc[q];
         }
     }
 }
@@ -1440,10 +1448,21 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
         t.rule_len = rb.size();
     }
     FL_CUDA_TRY(h, cudaMemcpyAsync(t.rule, rb.data(), rb.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    const bool f32 = precision == FL_MIXED;
+    std::vector<float> rb32;
+    if (f32) {  // float32 copy of the tables for the mixed-mode touching pairs
+        if (t.rule32_len < rb.size()) {
+            void* p = nullptr;
+            FL_TRY(alloc(h, &p, rb.size() * sizeof(float)));
+            t.rule32 = (float*)p;
+            t.rule32_len = rb.size();
+        }
+        rb32.assign(rb.begin(), rb.end());
+        FL_CUDA_TRY(h, cudaMemcpyAsync(t.rule32, rb32.data(), rb32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    }
     const double C = frac_constant(D, s);
     const double expo = -(D + 2.0 * s) / 2.0;
     const int pw = pw_mode(D, s);
-    const bool f32 = precision == FL_MIXED;
     const int64_t nc = P.nc;
     const unsigned gb = (unsigned)((nc + 127) / 128);
     // far rule offsets
@@ -1493,17 +1512,20 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
         FL_CUDA_TRY(h, cudaGetLastError());
     }
     stage_mark(h, st, FL_STAGE_NEAR, 1);
-    // touching pairs (float64)
+    // touching pairs (float64; float32 in the mixed mode)
     stage_mark(h, st, FL_STAGE_TOUCH, 0);
     const int ntp = (int)P.tp_type.size();
     if (ntp > 0) {
         const unsigned g = (unsigned)(((int64_t)ntp * 32 + 127) / 128);  // one warp per pair
-#define FL_TOUCH(PWV) \
-    touch_pair_kernel<PWV><<<g, 128, 0, st>>>(ntp, D, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, t.rule, ro, s, C, t.contrib)
-        if (D == 2 && pw == 5) FL_TOUCH(5);
-        else if (D == 2 && pw == 6) FL_TOUCH(6);
-        else if (D == 2 && pw == 7) FL_TOUCH(7);
-        else FL_TOUCH(0);
+#define FL_TOUCH(TT, RULE, PWV) \
+    touch_pair_kernel<TT, PWV><<<g, 128, 0, st>>>(ntp, D, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, RULE, ro, s, C, t.contrib)
+        if (f32) {
+            if (D == 2 && pw == 6) FL_TOUCH(float, t.rule32, 6);
+            else FL_TOUCH(float, t.rule32, 0);
+        } else if (D == 2 && pw == 5) FL_TOUCH(double, t.rule, 5);
+        else if (D == 2 && pw == 6) FL_TOUCH(double, t.rule, 6);
+        else if (D == 2 && pw == 7) FL_TOUCH(double, t.rule, 7);
+        else FL_TOUCH(double, t.rule, 0);
 #undef FL_TOUCH
         fl::count_launch();
         FL_CUDA_TRY(h, cudaGetLastError());

@@ -78,6 +78,8 @@ struct DevTables {
     void* facet_rec = nullptr;  // compact boundary-facet records (2D)
     double* rule = nullptr; // per-s rule tables (see assemble.cu)
     size_t rule_len = 0;
+    float* rule32 = nullptr;  // their float32 copy (mixed-mode touching pairs)
+    size_t rule32_len = 0;
 };
 
 }  // namespace fl
