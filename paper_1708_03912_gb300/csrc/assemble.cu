@@ -153,8 +153,18 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
         for (int d = 0; d < D; ++d) cj[d] = 0.0;
     }
     T S[Q];
+    T pn[Q];  // |y_b - c_J|^2
 #pragma unroll
-    for (int b = 0; b < Q; ++b) S[b] = T(0);
+    for (int b = 0; b < Q; ++b) {
+        S[b] = T(0);
+        T q = T(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) q = fma(pj[b][d], pj[b][d], q);
+        pn[b] = q;
+    }
+    // an inactive lane's row cell is moved so far that |x - y|^2 overflows to +inf and the
+    // kernel value is exactly 0 (no per-evaluation select)
+    const T far_away = sizeof(T) == 8 ? T(1e200) : T(1e30);
 
     for (int kk = 0; kk < nI; ++kk) {
         const int64_t K = K0 + kk;
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
         if (any) {
             T dct[D];
 #pragma unroll
-            for (int d = 0; d < D; ++d) dct[d] = (T)(sCen[kk * D + d] - cj[d]);
+            for (int d = 0; d < D; ++d) dct[d] = act ? (T)(sCen[kk * D + d] - cj[d]) : far_away;
             const T wK = (T)sJac[kk];
             T off[NV][NV];
 #pragma unroll
@@ -180,23 +190,26 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
                 for (int j = 0; j < NV; ++j) off[i][j] = T(0);
 #pragma unroll 1
             for (int a = 0; a < Q; ++a) {
-                T xa[D];
+                // |x_a - y_b|^2 = |x_a|^2 + |y_b|^2 - 2 x_a.y_b, offsets from c_J (|x_a| and
+                // |y_b| are within a few cell diameters of |x_a - y_b| for separated pairs)
+                T xm[D];
+                T xn = T(0);
 #pragma unroll
-                for (int d = 0; d < D; ++d) xa[d] = dct[d] + sPts[(kk * Q + a) * D + d];
+                for (int d = 0; d < D; ++d) {
+                    const T x = dct[d] + sPts[(kk * Q + a) * D + d];
+                    xn = fma(x, x, xn);
+                    xm[d] = T(-2) * x;
+                }
                 T t[NV];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) t[v] = T(0);
                 const T wa = R.w[a] * wK;
 #pragma unroll
                 for (int b = 0; b < Q; ++b) {
-                    T r2 = T(0);
+                    T r2 = xn + pn[b];
 #pragma unroll
-                    for (int d = 0; d < D; ++d) {
-                        T df = xa[d] - pj[b][d];
-                        r2 = fma(df, df, r2);
-                    }
-                    T kv = kpow<PW>(r2, A.expo);
-                    kv = act ? kv : T(0);
+                    for (int d = 0; d < D; ++d) r2 = fma(xm[d], pj[b][d], r2);
+                    const T kv = kpow<PW>(r2, A.expo);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) t[v] = fma(R.wphi[b * NV + v], kv, t[v]);
                     S[b] = fma(wa, kv, S[b]);
@@ -657,8 +670,11 @@ struct ElemArgs {
     const double* V;
     const int* corner;  // nc*nvpc original vertex ids in internal order
     const double* rule;
+    const float* rule32;  // float32 tables in the mixed mode (identical pair and 2D facet powers in float32), else null
     RuleOffsets ro;
     double s, C;
+    double C2s;             // C / (2s)
+    double r2s, r3s, r4s;   // 1 / (2 - 2s), 1 / (3 - 2s), 1 / (4 - 2s)
     int regional;
     double* contrib;
     int64_t slot0;
@@ -669,6 +685,25 @@ struct ElemArgs {
 // with a butterfly at the end.
 __device__ __forceinline__ int tri_index(int i, int j, int NV) {  // i <= j
     return i * NV - i * (i - 1) / 2 + (j - i);
+}
+
+// s += x with the running compensation c (Kahan); no reassociation is applied to it.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// |x - y|^{2e} from r2 = |x - y|^2 for the 2D boundary facets: float64, or in the mixed
+// mode float32 (the float64 power is the slow pipe's work; the geometry stays float64).
+template <int PW>
+__device__ __forceinline__ double facet_pow(double r2, double e, bool f32) {
+    if (f32) {
+        constexpr int PWF = (PW == 4 || PW == 6) ? PW : 0;
+        return (double)kpow<PWF>((float)r2, (float)e);
+    }
+    return kpow<PW>(r2, e);
 }
 
 template <int PW>
@@ -698,14 +733,20 @@ __global__ void element_kernel(ElemArgs A) {
                 double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
                 int64_t B = hb;
                 if (A.pd_is_float) {
+                    // compensated (Kahan) float32 sums: float64 accuracy without the slow pipe
                     const float* Pd = (const float*)A.Pd + k * A.nblk * qf + a;
+                    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
                     for (; B + 6 < A.nblk; B += 8) {
-                        s0 += (double)Pd[B * qf];
-                        s1 += (double)Pd[(B + 2) * qf];
-                        s2 += (double)Pd[(B + 4) * qf];
-                        s3 += (double)Pd[(B + 6) * qf];
+                        kahan_add(f0, c0, Pd[B * qf]);
+                        kahan_add(f1, c1, Pd[(B + 2) * qf]);
+                        kahan_add(f2, c2, Pd[(B + 4) * qf]);
+                        kahan_add(f3, c3, Pd[(B + 6) * qf]);
                     }
-                    for (; B < A.nblk; B += 2) s0 += (double)Pd[B * qf];
+                    for (; B < A.nblk; B += 2) kahan_add(f0, c0, Pd[B * qf]);
+                    s0 = (double)f0 - (double)c0;
+                    s1 = (double)f1 - (double)c1;
+                    s2 = (double)f2 - (double)c2;
+                    s3 = (double)f3 - (double)c3;
                 } else {
                     const double* Pd = (const double*)A.Pd + k * A.nblk * qf + a;
                     for (; B + 6 < A.nblk; B += 8) {
@@ -722,7 +763,7 @@ __global__ void element_kernel(ElemArgs A) {
             Dk = (hb == 0) ? Dk + other : other + Dk;
             if (hb == 0 && a < qf) {
                 const double bf = (D == 2 && !A.regional) ? A.Bf[k * qf + a] : 0.0;
-                const double f = jk * w[a] * (C * Dk + C / (2.0 * s) * bf);
+                const double f = jk * w[a] * (C * Dk + A.C2s * bf);
                 for (int i = 0; i < NV; ++i)
                     for (int j = i; j < NV; ++j) blk[tri_index(i, j, NV)] += f * phi[a * NV + i] * phi[a * NV + j];
             }
@@ -766,13 +807,13 @@ __global__ void element_kernel(ElemArgs A) {
                             const double dx = xa[0] - (E0[0] + gt[b] * (E1[0] - E0[0]));
                             const double dy = xa[1] - (E0[1] + gt[b] * (E1[1] - E0[1]));
                             acc += gw[b] * A.FLEN[f] * (A.FN[2 * f] * dx + A.FN[2 * f + 1] * dy) *
-                                   kpow<PW>(dx * dx + dy * dy, -(1.0 + s));
+                                   facet_pow<PW>(dx * dx + dy * dy, -(1.0 + s), A.rule32 != nullptr);
                         }
                         Bn += acc;
                     }
                 }
             }
-            const double f = jk * w[a] * (C * Dk + C / (2.0 * s) * Bn);
+            const double f = jk * w[a] * (C * Dk + A.C2s * Bn);
             for (int i = 0; i < NV; ++i)
                 for (int j = i; j < NV; ++j) blk[tri_index(i, j, NV)] += f * phi[a * NV + i] * phi[a * NV + j];
         }
@@ -785,6 +826,25 @@ __global__ void element_kernel(ElemArgs A) {
             blk[1] -= val;
             blk[2] += val;
         }
+    } else if (A.rule32) {
+        // mixed mode: the same sum in float32 (float64 pow is the slow pipe's work here)
+        constexpr int PWF = (PW == 4 || PW == 6) ? PW : 0;
+        const float J00 = (float)(v[2] - v[0]), J10 = (float)(v[3] - v[1]);
+        const float J01 = (float)(v[4] - v[0]), J11 = (float)(v[5] - v[1]);
+        const float* tb = A.rule32 + ro.t_ident;
+        const float e2 = (float)(-(1.0 + s));
+        float bf[6] = {};
+        for (int m = lane; m < ro.n_ident; m += 32) {
+            const float u0 = tb[3 * m], u1 = tb[3 * m + 1], f0 = tb[3 * m + 2];
+            const float jx = J00 * u0 + J01 * u1, jy = J10 * u0 + J11 * u1;
+            const float f = f0 * kpow<PWF>(jx * jx + jy * jy, e2);
+            const float g[3] = {-u0 - u1, u0, u1};
+            for (int i = 0; i < 3; ++i)
+                for (int j = i; j < 3; ++j) bf[tri_index(i, j, 3)] += f * g[i] * g[j];
+        }
+        const double beta = 2.0 * A.r2s * A.r3s * A.r4s;
+        const double sc = 0.5 * C * jk * jk * beta;
+        for (int q = 0; q < 6; ++q) blk[q] += sc * (double)bf[q];
     } else {
         const double J00 = v[2] - v[0], J10 = v[3] - v[1], J01 = v[4] - v[0], J11 = v[5] - v[1];
         const double* tb = rule + ro.t_ident;
@@ -857,11 +917,12 @@ __global__ void element_kernel(ElemArgs A) {
                     const double ax = pE1[0] - pE0[0], ay = pE1[1] - pE0[1];
                     const double bx = pR[0] - pE1[0], by = pR[1] - pE1[1];
                     const double* tb = rule + ro.b_own;
-                    const double sc = C / (2.0 * s) * jk * A.FLEN[f] / ((3.0 - 2.0 * s) * (4.0 - 2.0 * s));
+                    const double sc = A.C2s * jk * A.FLEN[f] * A.r3s * A.r4s;
                     for (int m = lane; m < ro.n_own; m += 32) {
                         const double o1 = tb[3 * m], o2 = tb[3 * m + 1], wt = tb[3 * m + 2];
                         const double x = ax * o1 + bx * o2, y = ay * o1 + by * o2;
-                        blk[tri_index(r, r, 3)] += sc * wt * H * o2 * kpow<PW>(x * x + y * y, -(1.0 + s)) * o2 * o2;
+                        blk[tri_index(r, r, 3)] +=
+                            sc * wt * H * o2 * facet_pow<PW>(x * x + y * y, -(1.0 + s), A.rule32 != nullptr) * o2 * o2;
                     }
                 } else if (cls == 3) {
                     // facet and K share one vertex P
@@ -880,7 +941,7 @@ __global__ void element_kernel(ElemArgs A) {
                     const double gr[2] = {pR[0] - pQ[0], pR[1] - pQ[1]};
                     const double ge[2] = {pE[0] - pP[0], pE[1] - pP[1]};
                     const double* tb = rule + ro.b_vert;
-                    const double sc = C / (2.0 * s) * jk * A.FLEN[f];
+                    const double sc = A.C2s * jk * A.FLEN[f];
                     const int idx[3] = {ip, iq, ir};
                     // local order (P, Q, R): a = e_P, bh = (e_Q - e_P) x1 + (e_R - e_Q) x2
                     for (int m = lane; m < ro.n_bvert; m += 32) {
@@ -888,13 +949,13 @@ __global__ void element_kernel(ElemArgs A) {
                         const double xpx = gq[0] * x1 + gr[0] * x2, xpy = gq[1] * x1 + gr[1] * x2;
                         const double N = xpx * nx + xpy * ny;
                         const double dx = xpx - t * ge[0], dy = xpy - t * ge[1];
-                        const double g = sc * wt * N * kpow<PW>(dx * dx + dy * dy, -(1.0 + s));
+                        const double g = sc * wt * N * facet_pow<PW>(dx * dx + dy * dy, -(1.0 + s), A.rule32 != nullptr);
                         const double bh[3] = {-x1, x1 - x2, x2};
                         for (int i = 0; i < 3; ++i)
                             for (int j = i; j < 3; ++j) {
                                 const double ai = (i == 0) ? 1.0 : 0.0, aj = (j == 0) ? 1.0 : 0.0;
-                                double val = g * bh[i] * bh[j] / (4.0 - 2.0 * s) + g * (ai * bh[j] + aj * bh[i]) / (3.0 - 2.0 * s);
-                                if (ai * aj != 0.0) val += g / (2.0 - 2.0 * s);
+                                double val = g * bh[i] * bh[j] * A.r4s + g * (ai * bh[j] + aj * bh[i]) * A.r3s;
+                                if (ai * aj != 0.0) val += g * A.r2s;
                                 int I_ = idx[i], J_ = idx[j];
                                 if (I_ > J_) { const int tmp = I_; I_ = J_; J_ = tmp; }
                                 blk[tri_index(I_, J_, 3)] += val;
@@ -1566,6 +1627,11 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
         E.V = t.V;
         E.corner = t.corig;
         E.rule = t.rule;
+        E.C2s = C / (2.0 * s);
+        E.r2s = 1.0 / (2.0 - 2.0 * s);
+        E.r3s = 1.0 / (3.0 - 2.0 * s);
+        E.r4s = 1.0 / (4.0 - 2.0 * s);
+        E.rule32 = f32 ? t.rule32 : nullptr;
         E.ro = ro;
         E.s = s;
         E.C = C;
