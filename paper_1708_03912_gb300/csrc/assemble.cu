@@ -93,10 +93,35 @@ __global__ void prep_points(const double* cvx, const double* cen, const double* 
     }
 }
 
+// Sum of 16 values over the 32 lanes of a warp, scattered: halving exchanges (16, 8,
+// 4, 2 lanes apart) leave lane l with the partial total of point point_of_lane16(l) over
+// its half, quarter, ... of the warp; a last exchange with lane l ^ 1 completes it (lanes
+// l and l ^ 1 then hold the same total).  16 shuffles in all, in a fixed order.
+__device__ __forceinline__ int point_of_lane16(int lane) {
+    return (((lane >> 4) & 1) << 3) | (((lane >> 3) & 1) << 2) | (((lane >> 2) & 1) << 1) | ((lane >> 1) & 1);
+}
+template <typename T>
+__device__ __forceinline__ T reduce_scatter16(T (&v)[16], int lane) {
+#pragma unroll
+    for (int h = 8, bit = 16; h >= 1; h >>= 1, bit >>= 1) {
+        const bool upper = (lane & bit) != 0;  // keeps the upper half of the current values
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const T send = upper ? v[k] : v[k + h];
+            const T keep = upper ? v[k + h] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 template <int D, typename T, int Q, int PW>
 __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const FarRule<T, Q, D + 1> R, int maxL) {
     constexpr int NV = D + 1;
     constexpr int QW = (Q + 31) / 32;
+    // Q = 16: the per-point row sums are reduced once per row cell by a 16-value
+    // reduce-scatter across the warp instead of one warp sum per point
+    constexpr bool MR = (Q == 16);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x;
     const int tix = blockIdx.x;
@@ -109,13 +134,15 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
 
     double* sCen = reinterpret_cast<double*>(smem_raw);      // 32*D
     double* sJac = sCen + 32 * D;                             // 32
-    T* sPts = reinterpret_cast<T*>(sJac + 32);                // 32*Q*D
-    T* sD = sPts + 32 * Q * D;                                // 32*Q (diagonal tile)
+    T* sPts = reinterpret_cast<T*>(sJac + 32);                // 32*Q*D (MR: sU[a][lane], Q*32)
+    T* sD = sPts + 32 * Q * (MR ? 1 : D);                     // 32*Q (diagonal tile)
     T* priv = sD + 32 * Q;                                    // NV*maxL*32
     int* sLoc = reinterpret_cast<int*>(priv + NV * maxL * 32);  // 32*NV
     int* sHas = sLoc + 32 * NV;                               // 32
 
-    for (int i = lane; i < nI * Q * D; i += 32) sPts[i] = A.pts[K0 * Q * D + i];
+    if constexpr (!MR)
+        for (int i = lane; i < nI * Q * D; i += 32) sPts[i] = A.pts[K0 * Q * D + i];
+    T* sU = sPts;
     for (int i = lane; i < nI * D; i += 32) sCen[i] = A.cen[K0 * D + i];
     for (int i = lane; i < nI * NV; i += 32) sLoc[i] = A.loc[K0 * NV + i];
     if (lane < nI) {
@@ -178,6 +205,7 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
         T myD[QW];
 #pragma unroll
         for (int w = 0; w < QW; ++w) myD[w] = T(0);
+        T myDa = T(0);  // MR: the row sum of point a_of_lane (lanes with bit 0 clear)
         if (any) {
             T dct[D];
 #pragma unroll
@@ -196,7 +224,7 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
                 T xn = T(0);
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
-                    const T x = dct[d] + sPts[(kk * Q + a) * D + d];
+                    const T x = dct[d] + (MR ? __ldg(A.pts + (K * Q + a) * D + d) : sPts[(kk * Q + a) * D + d]);
                     xn = fma(x, x, xn);
                     xm[d] = T(-2) * x;
                 }
@@ -217,14 +245,25 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
                 T u = t[0];
 #pragma unroll
                 for (int v = 1; v < NV; ++v) u += t[v];
-                u = warp_sum(u * wj);
+                if constexpr (MR) {
+                    sU[a * 32 + lane] = u * wj;
+                } else {
+                    u = warp_sum(u * wj);
 #pragma unroll
-                for (int w = 0; w < QW; ++w)
-                    if (a == w * 32 + lane) myD[w] = u;
+                    for (int w = 0; w < QW; ++w)
+                        if (a == w * 32 + lane) myD[w] = u;
+                }
 #pragma unroll
                 for (int i = 0; i < NV; ++i)
 #pragma unroll
                     for (int j = 0; j < NV; ++j) off[i][j] = fma(R.wphi[a * NV + i], t[j], off[i][j]);
+            }
+            if constexpr (MR) {
+                __syncwarp();
+                T v16[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v16[q] = sU[q * 32 + lane];
+                myDa = reduce_scatter16(v16, lane);
             }
             if (act) {
                 const T sc = wK * wj;
@@ -239,6 +278,15 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
             }
         }
         // row sums of cell K from this tile's columns
+        if constexpr (MR) {
+            if ((lane & 1) == 0) {
+                const int a = point_of_lane16(lane);
+                if (I == J) sD[kk * Q + a] += myDa;
+                else A.Pd[((int64_t)K * A.nblk + J) * Q + a] = myDa;
+            }
+            __syncwarp();  // sU is rewritten by the next row cell
+            continue;
+        }
 #pragma unroll
         for (int w = 0; w < QW; ++w) {
             const int a = w * 32 + lane;
@@ -1352,7 +1400,7 @@ int launch_far_t(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<doubl
     A.nblk = P.nblk;
     A.expo = (T)expo;
     const int maxL = std::max(1, P.maxL);
-    size_t smem = 32 * D * sizeof(double) + 32 * sizeof(double) + 32 * Q * D * sizeof(T) + 32 * Q * sizeof(T) +
+    size_t smem = 32 * D * sizeof(double) + 32 * sizeof(double) + 32 * Q * (Q == 16 ? 1 : D) * sizeof(T) + 32 * Q * sizeof(T) +
                   (size_t)NV * maxL * 32 * sizeof(T) + 32 * NV * sizeof(int) + 32 * sizeof(int);
     const int64_t ntiles = (int64_t)P.tiles.size() / 2;
     auto kern = far_tile_kernel<D, T, Q, PW>;
