@@ -51,8 +51,9 @@ struct RuleOffsets {
 
 template <typename T, int Q, int NV>
 struct FarRule {
-    T w[Q];          // reference weights
-    T wphi[Q * NV];  // reference weight x shape value
+    T w[Q];           // reference weights
+    T wphi[Q * NV];   // reference weight x shape value
+    T wpair[Q * NV];  // the same, as [b / 2][v][b % 2] (pairs of points for packed float32)
 };
 
 // ------------------------------------------------------------- far field --
@@ -93,6 +94,20 @@ __global__ void prep_points(const double* cvx, const double* cen, const double* 
     }
 }
 
+// |x - y|^{2e} for two squared distances at once (packed float32 multiplies).
+template <int PW>
+__device__ __forceinline__ float2 kpow2(float2 r2, float2 e) {
+    if constexpr (PW == 4 || PW == 6) {
+        const float2 t = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        const float2 t2 = __fmul2_rn(t, t);
+        if constexpr (PW == 4) return t2;
+        else return __fmul2_rn(t2, t);
+    } else {
+        const float2 l = __fmul2_rn(make_float2(lg2_approx(r2.x), lg2_approx(r2.y)), e);
+        return make_float2(ex2_approx(l.x), ex2_approx(l.y));
+    }
+}
+
 // Sum of 16 values over the 32 lanes of a warp, scattered: halving exchanges (16, 8,
 // 4, 2 lanes apart) leave lane l with the partial total of point point_of_lane16(l) over
 // its half, quarter, ... of the warp; a last exchange with lane l ^ 1 completes it (lanes
@@ -122,6 +137,8 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
     // Q = 16: the per-point row sums are reduced once per row cell by a 16-value
     // reduce-scatter across the warp instead of one warp sum per point
     constexpr bool MR = (Q == 16);
+    // float32, 2D, 16 points, PW in {0, 4, 6}: points b and b + 1 evaluated as one packed pair
+    constexpr bool PK = MR && D == 2 && sizeof(T) == 4 && (PW == 0 || PW == 4 || PW == 6);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x;
     const int tix = blockIdx.x;
@@ -192,6 +209,20 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
     // an inactive lane's row cell is moved so far that |x - y|^2 overflows to +inf and the
     // kernel value is exactly 0 (no per-evaluation select)
     const T far_away = sizeof(T) == 8 ? T(1e200) : T(1e30);
+    float2 pn2[MR ? Q / 2 : 1], py0[MR ? Q / 2 : 1], py1[MR ? Q / 2 : 1], S2[MR ? Q / 2 : 1];
+    float2 wp[MR ? Q / 2 : 1][NV];
+    if constexpr (PK) {
+#pragma unroll
+        for (int c = 0; c < Q / 2; ++c) {
+            pn2[c] = make_float2((float)pn[2 * c], (float)pn[2 * c + 1]);
+            py0[c] = make_float2((float)pj[2 * c][0], (float)pj[2 * c + 1][0]);
+            py1[c] = make_float2((float)pj[2 * c][D - 1], (float)pj[2 * c + 1][D - 1]);
+            S2[c] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                wp[c][v] = make_float2((float)R.wpair[(c * NV + v) * 2], (float)R.wpair[(c * NV + v) * 2 + 1]);
+        }
+    }
 
     for (int kk = 0; kk < nI; ++kk) {
         const int64_t K = K0 + kk;
@@ -216,6 +247,48 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
             for (int i = 0; i < NV; ++i)
 #pragma unroll
                 for (int j = 0; j < NV; ++j) off[i][j] = T(0);
+            if constexpr (PK) {
+                const float2 e2 = make_float2((float)A.expo, (float)A.expo);
+                const T* px = A.pts + K * Q * D;
+                float nx0 = __ldg(px), nx1 = __ldg(px + 1);  // offsets of point 0, then prefetched
+#pragma unroll 2
+                for (int a = 0; a < Q; ++a) {
+                    const float x0 = (float)dct[0] + nx0, x1 = (float)dct[1] + nx1;
+                    if (a + 1 < Q) {
+                        nx0 = __ldg(px + (a + 1) * D);
+                        nx1 = __ldg(px + (a + 1) * D + 1);
+                    }
+                    const float xn = fmaf(x0, x0, x1 * x1);
+                    const float2 xnn = make_float2(xn, xn);
+                    const float2 xm0 = make_float2(-2.f * x0, -2.f * x0), xm1 = make_float2(-2.f * x1, -2.f * x1);
+                    const float wa = (float)(R.w[a] * wK);
+                    const float2 wa2 = make_float2(wa, wa);
+                    float2 tp[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) tp[v] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int c = 0; c < Q / 2; ++c) {
+                        float2 r2 = __fadd2_rn(xnn, pn2[c]);
+                        r2 = __ffma2_rn(xm0, py0[c], r2);
+                        r2 = __ffma2_rn(xm1, py1[c], r2);
+                        const float2 kv = kpow2<PW>(r2, e2);
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) tp[v] = __ffma2_rn(wp[c][v], kv, tp[v]);
+                        S2[c] = __ffma2_rn(wa2, kv, S2[c]);
+                    }
+                    T t[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) t[v] = (T)(tp[v].x + tp[v].y);
+                    T u = t[0];
+#pragma unroll
+                    for (int v = 1; v < NV; ++v) u += t[v];
+                    sU[a * 32 + lane] = u * wj;
+#pragma unroll
+                    for (int i = 0; i < NV; ++i)
+#pragma unroll
+                        for (int j = 0; j < NV; ++j) off[i][j] = fma(R.wphi[a * NV + i], t[j], off[i][j]);
+                }
+            } else {
 #pragma unroll 1
             for (int a = 0; a < Q; ++a) {
                 // |x_a - y_b|^2 = |x_a|^2 + |y_b|^2 - 2 x_a.y_b, offsets from c_J (|x_a| and
@@ -258,6 +331,7 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
 #pragma unroll
                     for (int j = 0; j < NV; ++j) off[i][j] = fma(R.wphi[a * NV + i], t[j], off[i][j]);
             }
+            }
             if constexpr (MR) {
                 __syncwarp();
                 T v16[16];
@@ -297,6 +371,13 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
         }
     }
     __syncwarp();
+    if constexpr (PK) {
+#pragma unroll
+        for (int c = 0; c < Q / 2; ++c) {
+            S[2 * c] = (T)S2[c].x;
+            S[2 * c + 1] = (T)S2[c].y;
+        }
+    }
     if (valid) {
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
@@ -1381,6 +1462,8 @@ int launch_far_t(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<doubl
         R.w[a] = (T)rb[ro.far_w + a];
         for (int v = 0; v < NV; ++v) R.wphi[a * NV + v] = (T)(rb[ro.far_w + a] * rb[ro.far_phi + a * NV + v]);
     }
+    for (int a = 0; a < Q; ++a)
+        for (int v = 0; v < NV; ++v) R.wpair[((a / 2) * NV + v) * 2 + (a % 2)] = R.wphi[a * NV + v];
     FarArgs<T> A;
     A.cen = t.cen;
     A.pts = (const T*)t.pts;
