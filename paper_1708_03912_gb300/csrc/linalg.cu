@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 #include <string>
 #include <vector>
@@ -561,64 +562,71 @@ __device__ __forceinline__ TS row_dot(const TA* __restrict__ a, const TX* __rest
 // MODE 2: the block's rows of A stay in shared memory for the whole solve (and z is
 // staged there each step); MODE 1: z staged, A streamed; MODE 0: both streamed.
 // Breakdown: a non-positive denominator (p.Ap <= 0).
+// Per-block view of the persistent CG: the block's rows [r0, r1), its shared-memory
+// buffers and the work vectors (all indexed by global row).
+template <typename T>
+struct CgBlock {
+    int64_t n, r0, r1, lds;
+    const T* A;  // global matrix (MODE < 2)
+    int64_t lda;
+    T* xs;  // [lds] staged z (MODE >= 1)
+    T* ws;  // [rpb] products of the own rows
+    T* As;  // [rpb][lds] own rows of A (MODE 2)
+    T *u, *r, *z, *p, *sv, *dv, *part;
+    unsigned* gbar;
+    int* err;
+    T* sh;
+    int nb, lane, warp;
+};
+
+// Copy of the block's rows of A into shared memory (MODE 2), zero padding of the staged vector.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(PCG_THREADS, 1)
-    pcg_persistent_kernel(int64_t n, int64_t rpb, int64_t lds, const T* __restrict__ A, int64_t lda,
-                          const double* __restrict__ dinv, const double* __restrict__ rhs, double* d, T* u, T* r,
-                          T* z, T* p, T* sv, T* dv, T* part, unsigned* gbar, CgScalars* S, double tol, int maxit,
-                          int* err) {
-    constexpr int V = 16 / sizeof(T);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T sh[2 * 33];
-    T* xs = reinterpret_cast<T*>(smem_raw);  // [lds] copy of z (MODE >= 1)
-    const int64_t rpb_pad = (rpb + V - 1) / V * V;
-    T* ws = xs + (MODE >= 1 ? lds : 0);  // [rpb] products of the own rows
-    T* As = ws + rpb_pad;                 // [rpb][lds] own rows of A (MODE 2)
-    const int nb = gridDim.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t r0 = blockIdx.x * rpb;
-    const int64_t r1 = (r0 + rpb < n) ? r0 + rpb : n;
-    constexpr int D_ = 0, G_ = 1, R_ = 2;
-    unsigned epoch = 0;
+__device__ __forceinline__ void cg_block_setup(const CgBlock<T>& c) {
     if constexpr (MODE == 2) {
-        for (int64_t row = r0; row < r1; ++row)
-            for (int64_t j = threadIdx.x; j < lds; j += blockDim.x)
-                As[(row - r0) * lds + j] = j < n ? A[row * lda + j] : T(0);
+        for (int64_t row = c.r0; row < c.r1; ++row)
+            for (int64_t j = threadIdx.x; j < c.lds; j += blockDim.x)
+                c.As[(row - c.r0) * c.lds + j] = j < c.n ? c.A[row * c.lda + j] : T(0);
     }
     if constexpr (MODE >= 1)
-        for (int64_t j = n + threadIdx.x; j < lds; j += blockDim.x) xs[j] = T(0);
+        for (int64_t j = c.n + threadIdx.x; j < c.lds; j += blockDim.x) c.xs[j] = T(0);
+}
+
+// One Jacobi-PCG solve M u = rhs from u = 0 in the Chronopoulos-Gear arrangement, every
+// block on its own rows.  Returns false when a grid barrier gave up (err is set).
+template <typename T, int MODE>
+__device__ __forceinline__ bool cg_block_solve(const CgBlock<T>& c, const double* __restrict__ rhs, double tol,
+                                               int maxit, unsigned& epoch, int& it_out, int& breakdown_out,
+                                               T& rr_out, T& rr0_out) {
+    constexpr int V = 16 / sizeof(T);
+    constexpr int D_ = 0, G_ = 1, R_ = 2;
+    const int64_t n = c.n, r0 = c.r0, r1 = c.r1;
+    const int lane = c.lane, warp = c.warp, nb = c.nb;
+    T* sh = c.sh;
     // start: u = 0, r = rhs, z = D^-1 r, p = s = 0
     {
         T v[2] = {0, 0};
         for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
             const T ri = (T)rhs[i];
-            T di;
-            if constexpr (sizeof(T) == 4) {
-                di = (T)dinv[i];
-                dv[i] = di;
-            } else {
-                di = dinv[i];
-            }
-            const T zi = di * ri;
-            u[i] = 0;
-            r[i] = ri;
-            z[i] = zi;
-            p[i] = 0;
-            sv[i] = 0;
+            const T zi = c.dv[i] * ri;
+            c.u[i] = 0;
+            c.r[i] = ri;
+            c.z[i] = zi;
+            c.p[i] = 0;
+            c.sv[i] = 0;
             v[0] += ri * zi;
             v[1] += ri * ri;
         }
         block_totals<T, 2>(v, sh);
         if (threadIdx.x == 0) {
-            part[G_ * 1024 + blockIdx.x] = v[0];
-            part[R_ * 1024 + blockIdx.x] = v[1];
+            c.part[G_ * 1024 + blockIdx.x] = v[0];
+            c.part[R_ * 1024 + blockIdx.x] = v[1];
         }
     }
-    if (!tc::grid_barrier(gbar, epoch, nb, err)) return;
+    if (!tc::grid_barrier(c.gbar, epoch, nb, c.err)) return false;
     T gamma, rr0;
     {
         T v[2];
-        grid_totals<T, 2>(v, part, {G_, R_}, nb, sh);
+        grid_totals<T, 2>(v, c.part, {G_, R_}, nb, sh);
         gamma = v[0];
         rr0 = v[1];
     }
@@ -629,8 +637,8 @@ __global__ void __launch_bounds__(PCG_THREADS, 1)
         // M: w = A z on the own rows, partial z.w
         if constexpr (MODE >= 1) {
             const int64_t nq = n * (int64_t)sizeof(T) / 16;  // z is 256-byte aligned
-            const uint4* src = reinterpret_cast<const uint4*>(z);
-            uint4* dst = reinterpret_cast<uint4*>(xs);
+            const uint4* src = reinterpret_cast<const uint4*>(c.z);
+            uint4* dst = reinterpret_cast<uint4*>(c.xs);
             for (int64_t i0 = threadIdx.x; i0 < nq; i0 += 4 * blockDim.x) {
                 uint4 q[4];
 #pragma unroll
@@ -640,17 +648,17 @@ __global__ void __launch_bounds__(PCG_THREADS, 1)
                 for (int j = 0; j < 4; ++j)
                     if (i0 + j * blockDim.x < nq) dst[i0 + j * blockDim.x] = q[j];
             }
-            for (int64_t i = nq * 16 / (int64_t)sizeof(T) + threadIdx.x; i < n; i += blockDim.x) xs[i] = __ldcg(z + i);
+            for (int64_t i = nq * 16 / (int64_t)sizeof(T) + threadIdx.x; i < n; i += blockDim.x) c.xs[i] = __ldcg(c.z + i);
             __syncthreads();
         }
         T dl[1] = {0};
         for (int64_t row = r0 + warp; row < r1; row += PCG_WARPS) {
             T acc;
             if constexpr (MODE == 2) {
-                const uint4* a4 = reinterpret_cast<const uint4*>(As + (row - r0) * lds);
-                const uint4* x4 = reinterpret_cast<const uint4*>(xs);
+                const uint4* a4 = reinterpret_cast<const uint4*>(c.As + (row - r0) * c.lds);
+                const uint4* x4 = reinterpret_cast<const uint4*>(c.xs);
                 T s0 = 0, s1 = 0;
-                for (int64_t q = lane; q < lds / V; q += 32) {
+                for (int64_t q = lane; q < c.lds / V; q += 32) {
                     const uint4 av = a4[q], xv = x4[q];
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
@@ -660,19 +668,19 @@ __global__ void __launch_bounds__(PCG_THREADS, 1)
                 }
                 acc = warp_total(s0 + s1);
             } else {
-                acc = row_dot<T, T, T, (MODE == 1)>(A + row * lda, MODE == 1 ? xs : z, n, lane);
+                acc = row_dot<T, T, T, (MODE == 1)>(c.A + row * c.lda, MODE == 1 ? c.xs : c.z, n, lane);
             }
             if (lane == 0) {
-                ws[row - r0] = acc;
-                dl[0] += (MODE >= 1 ? xs[row] : __ldcg(z + row)) * acc;
+                c.ws[row - r0] = acc;
+                dl[0] += (MODE >= 1 ? c.xs[row] : __ldcg(c.z + row)) * acc;
             }
         }
         block_totals<T, 1>(dl, sh);
-        if (threadIdx.x == 0) part[D_ * 1024 + blockIdx.x] = dl[0];
-        if (!tc::grid_barrier(gbar, epoch, nb, err)) return;
+        if (threadIdx.x == 0) c.part[D_ * 1024 + blockIdx.x] = dl[0];
+        if (!tc::grid_barrier(c.gbar, epoch, nb, c.err)) return false;
         // U
         T delta[1];
-        grid_totals<T, 1>(delta, part, {D_}, nb, sh);
+        grid_totals<T, 1>(delta, c.part, {D_}, nb, sh);
         const T beta = (it == 0) ? T(0) : gamma / gamma_prev;
         const T den = (it == 0) ? delta[0] : delta[0] - beta * gamma / alpha_prev;
         if (!(den > T(0))) {
@@ -682,41 +690,193 @@ __global__ void __launch_bounds__(PCG_THREADS, 1)
         const T alpha = gamma / den;
         T v[2] = {0, 0};
         for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-            const T pi = fma(beta, p[i], z[i]);
-            const T si = fma(beta, sv[i], ws[i - r0]);
-            p[i] = pi;
-            sv[i] = si;
-            u[i] = fma(alpha, pi, u[i]);
-            const T ri = fma(-alpha, si, r[i]);
-            r[i] = ri;
-            const T zi = dv[i] * ri;
-            z[i] = zi;
+            const T pi = fma(beta, c.p[i], c.z[i]);
+            const T si = fma(beta, c.sv[i], c.ws[i - r0]);
+            c.p[i] = pi;
+            c.sv[i] = si;
+            c.u[i] = fma(alpha, pi, c.u[i]);
+            const T ri = fma(-alpha, si, c.r[i]);
+            c.r[i] = ri;
+            const T zi = c.dv[i] * ri;
+            c.z[i] = zi;
             v[0] = fma(ri, zi, v[0]);
             v[1] = fma(ri, ri, v[1]);
         }
         block_totals<T, 2>(v, sh);
         if (threadIdx.x == 0) {
-            part[G_ * 1024 + blockIdx.x] = v[0];
-            part[R_ * 1024 + blockIdx.x] = v[1];
+            c.part[G_ * 1024 + blockIdx.x] = v[0];
+            c.part[R_ * 1024 + blockIdx.x] = v[1];
         }
-        if (!tc::grid_barrier(gbar, epoch, nb, err)) return;
+        if (!tc::grid_barrier(c.gbar, epoch, nb, c.err)) return false;
         gamma_prev = gamma;
         alpha_prev = alpha;
-        grid_totals<T, 2>(v, part, {G_, R_}, nb, sh);
+        grid_totals<T, 2>(v, c.part, {G_, R_}, nb, sh);
         gamma = v[0];
         rr = v[1];
         ++it;
     }
+    it_out = it;
+    breakdown_out = breakdown;
+    rr_out = rr;
+    rr0_out = rr0;
+    return true;
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ CgBlock<T> cg_block(int64_t n, int64_t rpb, int64_t lds, const T* A, int64_t lda, T* u,
+                                               T* r, T* z, T* p, T* sv, T* dv, T* part, unsigned* gbar, int* err,
+                                               T* sh, unsigned char* smem_raw) {
+    constexpr int V = 16 / sizeof(T);
+    CgBlock<T> c;
+    c.n = n;
+    c.r0 = blockIdx.x * rpb;
+    c.r1 = (c.r0 + rpb < n) ? c.r0 + rpb : n;
+    c.lds = lds;
+    c.A = A;
+    c.lda = lda;
+    const int64_t rpb_pad = (rpb + V - 1) / V * V;
+    c.xs = reinterpret_cast<T*>(smem_raw);
+    c.ws = c.xs + (MODE >= 1 ? lds : 0);
+    c.As = c.ws + rpb_pad;
+    c.u = u;
+    c.r = r;
+    c.z = z;
+    c.p = p;
+    c.sv = sv;
+    c.dv = dv;
+    c.part = part;
+    c.gbar = gbar;
+    c.err = err;
+    c.sh = sh;
+    c.nb = gridDim.x;
+    c.lane = threadIdx.x & 31;
+    c.warp = threadIdx.x >> 5;
+    return c;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(PCG_THREADS, 1)
+    pcg_persistent_kernel(int64_t n, int64_t rpb, int64_t lds, const T* __restrict__ A, int64_t lda,
+                          const double* __restrict__ dinv, const double* __restrict__ rhs, double* d, T* u, T* r,
+                          T* z, T* p, T* sv, T* dv, T* part, unsigned* gbar, CgScalars* S, double tol, int maxit,
+                          int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T sh[2 * 33];
+    const CgBlock<T> c = cg_block<T, MODE>(n, rpb, lds, A, lda, u, r, z, p, sv, dv, part, gbar, err, sh, smem_raw);
+    cg_block_setup<T, MODE>(c);
     if constexpr (sizeof(T) == 4)
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) d[i] = (double)u[i];
+        for (int64_t i = c.r0 + threadIdx.x; i < c.r1; i += blockDim.x) dv[i] = (T)dinv[i];
+    unsigned epoch = 0;
+    int it = 0, breakdown = 0;
+    T rr = 0, rr0 = 0;
+    if (!cg_block_solve<T, MODE>(c, rhs, tol, maxit, epoch, it, breakdown, rr, rr0)) return;
+    if constexpr (sizeof(T) == 4)
+        for (int64_t i = c.r0 + threadIdx.x; i < c.r1; i += blockDim.x) d[i] = (double)u[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         S->rr = (double)rr;
-        S->stop = (double)stop;
+        S->stop = (double)((T)(tol * tol) * rr0);
         S->it = it;
         S->breakdown = breakdown;
         S->done = 1;
         S->rz = (double)rr0;  // initial residual norm^2, read back by the host
     }
+}
+
+// Float64 iterative refinement around the float32 persistent CG, in one cooperative launch
+// (the host version reads the residual back after every step): per step the float64
+// residual r = b - A u of the own rows (u = 0 first, so r = b), the stopping test
+// ||r|| <= tol ||b|| from the same totals in every block, the float32 solve M d = r, and
+// u += d.  The float32 rows of M are copied into shared memory once for all steps (MODE 2).
+struct RefineOut {
+    double rr, bb;
+    int outer, inner, status;  // status: 0 converged, 1 step limit, 2 breakdown
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(PCG_THREADS, 1)
+    refine_persistent_kernel(int64_t n, int64_t rpb, int64_t lds, const double* __restrict__ A64, int64_t lda,
+                             const float* __restrict__ A32, int64_t ld32, const double* __restrict__ dinv32,
+                             const double* __restrict__ b, double* u, double* r64, float* d, float* r, float* z,
+                             float* p, float* sv, float* dv, float* partf, double* partd, unsigned* gbar,
+                             RefineOut* out, double tol, double inner_tol, int max_outer, int inner_maxit, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float sh[2 * 33];
+    __shared__ double shd[33];
+    const CgBlock<float> c =
+        cg_block<float, MODE>(n, rpb, lds, A32, ld32, d, r, z, p, sv, dv, partf, gbar, err, sh, smem_raw);
+    cg_block_setup<float, MODE>(c);
+    for (int64_t i = c.r0 + threadIdx.x; i < c.r1; i += blockDim.x) {
+        dv[i] = (float)dinv32[i];
+        u[i] = 0.0;
+    }
+    unsigned epoch = 0;
+    double bb = 0.0, rr = 0.0;
+    int outer = 0, inner = 0, status = 1;
+    for (;;) {
+        // float64 residual of the own rows (one warp per row; u is complete after the barrier)
+        double v[1] = {0.0};
+        for (int64_t row = c.r0 + c.warp; row < c.r1; row += PCG_WARPS) {
+            const double acc = outer == 0 ? 0.0 : row_dot<double, double, double, false>(A64 + row * lda, u, n, c.lane);
+            if (c.lane == 0) {
+                const double ri = b[row] - acc;
+                r64[row] = ri;
+                v[0] = fma(ri, ri, v[0]);
+            }
+        }
+        block_totals<double, 1>(v, shd);
+        if (threadIdx.x == 0) partd[blockIdx.x] = v[0];
+        if (!tc::grid_barrier(gbar, epoch, c.nb, err)) return;
+        grid_totals<double, 1>(v, partd, {0}, c.nb, shd);
+        rr = v[0];
+        if (outer == 0) bb = rr;
+        if (rr <= tol * tol * bb) {
+            status = 0;
+            break;
+        }
+        if (outer >= max_outer) break;
+        int it = 0, breakdown = 0;
+        float irr = 0.f, irr0 = 0.f;
+        if (!cg_block_solve<float, MODE>(c, r64, inner_tol, inner_maxit, epoch, it, breakdown, irr, irr0)) return;
+        inner += it;
+        if (breakdown) {
+            status = 2;
+            break;
+        }
+        for (int64_t i = c.r0 + threadIdx.x; i < c.r1; i += blockDim.x) u[i] += (double)d[i];
+        ++outer;
+        if (!tc::grid_barrier(gbar, epoch, c.nb, err)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out->rr = rr;
+        out->bb = bb;
+        out->outer = outer;
+        out->inner = inner;
+        out->status = status;
+    }
+}
+
+// Shared-memory plan of the persistent kernels: MODE 2 (rows of M resident), 1 (z staged)
+// or 0; false if not even the row products fit.
+static bool persistent_plan(int64_t n, size_t es, int blocks, int optin, int* mode, size_t* smem, int64_t* rpb,
+                            int64_t* lds) {
+    const int64_t V = 16 / (int64_t)es;
+    *rpb = (n + blocks - 1) / blocks;
+    const int64_t rpb_pad = (*rpb + V - 1) / V * V;
+    *lds = (n + V - 1) / V * V;
+    const size_t budget = optin > 4096 ? (size_t)optin - 2048 : 0;  // room for the static reduction buffers
+    if ((size_t)(*lds + rpb_pad + *rpb * *lds) * es <= budget) {
+        *mode = 2;
+        *smem = (size_t)(*lds + rpb_pad + *rpb * *lds) * es;
+    } else if ((size_t)(*lds + rpb_pad) * es <= budget) {
+        *mode = 1;
+        *smem = (size_t)(*lds + rpb_pad) * es;
+    } else if ((size_t)rpb_pad * es <= budget) {
+        *mode = 0;
+        *smem = (size_t)rpb_pad * es;
+    } else {
+        return false;
+    }
+    return true;
 }
 
 // Launch the persistent solver if the device supports cooperative launches and the grid
@@ -738,26 +898,11 @@ static bool pcg_persistent(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const 
     if (!coop || sms < 1) return false;
     const bool f64 = dtype == FL_F64;
     const size_t es = f64 ? sizeof(double) : sizeof(float);
-    const int64_t V = 16 / (int64_t)es;
     const int blocks = std::min(sms, PCG_MAX_BLOCKS);
-    const int64_t rpb = (n + blocks - 1) / blocks;
-    const int64_t rpb_pad = (rpb + V - 1) / V * V;
-    const int64_t lds = (n + V - 1) / V * V;
-    const size_t budget = optin > 4096 ? (size_t)optin - 2048 : 0;  // room for the static reduction buffers
-    int mode;
-    size_t smem;
-    if ((size_t)(lds + rpb_pad + rpb * lds) * es <= budget) {
-        mode = 2;
-        smem = (size_t)(lds + rpb_pad + rpb * lds) * es;
-    } else if ((size_t)(lds + rpb_pad) * es <= budget) {
-        mode = 1;
-        smem = (size_t)(lds + rpb_pad) * es;
-    } else if ((size_t)rpb_pad * es <= budget) {
-        mode = 0;
-        smem = (size_t)rpb_pad * es;
-    } else {
-        return false;
-    }
+    int mode = 0;
+    size_t smem = 0;
+    int64_t rpb = 0, lds = 0;
+    if (!persistent_plan(n, es, blocks, optin, &mode, &smem, &rpb, &lds)) return false;
     const void* fn = f64 ? (mode == 2 ? pcg_fn<double, 2>() : mode == 1 ? pcg_fn<double, 1>() : pcg_fn<double, 0>())
                          : (mode == 2 ? pcg_fn<float, 2>() : mode == 1 ? pcg_fn<float, 1>() : pcg_fn<float, 0>());
     int per_sm = 0;
@@ -790,6 +935,61 @@ static bool pcg_persistent(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const 
     }
     fl::count_launch();
     *status = FL_OK;
+    return true;
+}
+
+// Launch the refinement kernel (float32 inner matrix) if cooperative launches are supported
+// and the grid fits; returns false (nothing launched) otherwise.
+static bool refine_persistent(fl_ctx* h, SolveWork& w, int64_t n, const double* A64, int64_t lda, const float* A32,
+                              int64_t ld32, const double* b, double* u, double tol, double inner_tol, int max_outer,
+                              int inner_maxit, cudaStream_t st) {
+    if (h->no_persistent) return false;
+    int dev = 0, coop = 0, sms = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop || sms < 1) return false;
+    const int blocks = std::min(sms, PCG_MAX_BLOCKS);
+    int mode = 0;
+    size_t smem = 0;
+    int64_t rpb = 0, lds = 0;
+    if (!persistent_plan(n, sizeof(float), blocks, optin, &mode, &smem, &rpb, &lds)) return false;
+    const void* fn = mode == 2   ? (const void*)refine_persistent_kernel<2>
+                     : mode == 1 ? (const void*)refine_persistent_kernel<1>
+                                 : (const void*)refine_persistent_kernel<0>;
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 16)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_THREADS, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    int* err = reinterpret_cast<int*>(w.part + 3 * 1024);
+    if (cudaMemsetAsync(w.gbar, 0, sizeof(unsigned), st) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    // float32 vectors in the first halves of the float64 work vectors (d in q), D^-1 in xf;
+    // float partials in the first 12 KiB of part, float64 partials at part + 2048
+    float* partf = reinterpret_cast<float*>(w.part);
+    double* partd = w.part + 2048;
+    RefineOut* out = reinterpret_cast<RefineOut*>(w.s);
+    const double* dinv32 = w.dinv_lo;
+    double* r64 = w.t;
+    float *d = (float*)w.q, *r = (float*)w.r, *z = (float*)w.z, *p = (float*)w.p, *sv = (float*)w.sv, *dv = w.xf;
+    void* args[] = {(void*)&n,     (void*)&rpb,   (void*)&lds,   (void*)&A64,  (void*)&lda,       (void*)&A32,
+                    (void*)&ld32,  (void*)&dinv32, (void*)&b,    (void*)&u,    (void*)&r64,       (void*)&d,
+                    (void*)&r,     (void*)&z,     (void*)&p,     (void*)&sv,   (void*)&dv,        (void*)&partf,
+                    (void*)&partd, (void*)&w.gbar, (void*)&out,  (void*)&tol,  (void*)&inner_tol, (void*)&max_outer,
+                    (void*)&inner_maxit, (void*)&err};
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(PCG_THREADS), args, smem, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    fl::count_launch();
     return true;
 }
 
@@ -953,6 +1153,28 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
         status = pcg(h, w, n, FL_F64, A_dev, lda, w.dinv, b_dev, u_dev, o.tol, o.maxit, &its, &rel, st);
         inf.iterations = its;
         inf.outer_iterations = 1;
+    } else if (o.inner_dtype == FL_F32 && [&] {
+                   diag_inv_kernel<<<g, 256, 0, st>>>(n, FL_F32, o.A_lo_dev, o.ld_lo, w.dinv_lo);
+                   fl::count_launch();
+                   return refine_persistent(h, w, n, A_dev, lda, (const float*)o.A_lo_dev, o.ld_lo, b_dev, u_dev,
+                                            o.tol, o.inner_tol, o.maxit, o.inner_maxit, st);
+               }()) {
+        // the whole refinement ran in one cooperative launch; its last residual is float64 with A
+        int err = 0;
+        FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+        FL_CU(h, cudaMemcpyAsync(&err, w.part + 3 * 1024, sizeof(int), cudaMemcpyDeviceToHost, st));
+        FL_CU(h, cudaStreamSynchronize(st));
+        if (err != 0) return set_err(h, FL_ETIMEOUT, "a grid barrier of the persistent refinement gave up");
+        RefineOut ro;
+        std::memcpy(&ro, w.s_host, sizeof(ro));
+        inf.iterations = ro.inner;
+        inf.outer_iterations = ro.outer;
+        inf.rel_residual = (ro.bb > 0) ? std::sqrt(ro.rr / ro.bb) : 0.0;
+        status = ro.status == 0 ? FL_OK : ro.status == 2 ? FL_ENOTSPD : FL_ENOTCONV;
+        if (status == FL_ENOTSPD) set_err(h, FL_ENOTSPD, "CG breakdown: p^T A p <= 0");
+        inf.status = status;
+        if (info) *info = inf;
+        return status;
     } else {
         // float64 iterative refinement around a low-precision Jacobi-PCG
         diag_inv_kernel<<<g, 256, 0, st>>>(n, o.inner_dtype, o.A_lo_dev, o.ld_lo, w.dinv_lo); fl::count_launch();
