@@ -472,6 +472,19 @@ int fl_stage_ms(fl_handle h, double* ms_out /* [FL_NSTAGES] */);
 /* Number of kernels this library has launched in the process so far. */
 uint64_t fl_launch_count(void);
 
+/*
+ * Caching allocator.  Device tables, workspaces and pinned scalars of handles come from a
+ * process-wide cache (per device, thread-safe): fl_destroy returns a handle's blocks to it
+ * after synchronising the device, and a later handle reuses the smallest cached block of at
+ * least the requested size and at most twice it.  When an allocation fails for lack of
+ * memory the device's cached blocks are released and the allocation retried.
+ * fl_pool_trim releases every cached block (cudaFree / cudaFreeHost) and returns the bytes
+ * released; call it only while no handle's work is in flight.  fl_pool_stats reports the
+ * cached bytes and the hit / miss counts of all requests (any argument may be NULL).
+ */
+int64_t fl_pool_trim(void);
+void fl_pool_stats(int64_t* cached_device_bytes, int64_t* cached_host_bytes, int64_t* hits, int64_t* misses);
+
 /* ------------------------------------------------------------------------
  * Allocation-free float32 matrix-vector product.  The paper has no counterpart;
  * this is a service for callers that cannot allocate device memory: code that

@@ -1159,26 +1159,50 @@ __global__ void add_csr_kernel(int64_t nnz, const int* csr_row, const int* csr_c
 // ---------------------------------------------------------------- host side --
 namespace {
 
-template <typename X>
-int upload(fl_ctx* h, X*& dst, const std::vector<X>& src) {
-    dst = nullptr;
-    size_t bytes = std::max<size_t>(1, src.size()) * sizeof(X);
-    cudaError_t e = cudaMalloc((void**)&dst, bytes);
-    if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    h->bufs.push_back({dst, bytes});
-    h->ws_bytes += (int64_t)bytes;
-    h->h2d_bytes += (int64_t)(src.size() * sizeof(X));
-    if (!src.empty()) {
-        e = cudaMemcpy(dst, src.data(), src.size() * sizeof(X), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return set_err(h, FL_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+// Host tables bound for one device block: each gets a 256-byte aligned range of it.
+struct Uploads {
+    struct Item {
+        void** dst;
+        const void* src;
+        size_t bytes;
+    };
+    std::vector<Item> items;
+    template <typename X>
+    void add(X*& dst, const std::vector<X>& src) {
+        items.push_back({(void**)&dst, src.data(), src.size() * sizeof(X)});
     }
+};
+
+// One pooled device block for all tables, filled from one pinned staging buffer by one copy.
+int upload_all(fl_ctx* h, const Uploads& U, cudaStream_t st) {
+    size_t total = 0;
+    for (const auto& it : U.items) total += (std::max<size_t>(it.bytes, 1) + 255) / 256 * 256;
+    void* base = nullptr;
+    cudaError_t e = pool_dev_alloc(&base, total);
+    if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("device tables: ") + cudaGetErrorString(e));
+    h->bufs.push_back({base, total});
+    h->ws_bytes += (int64_t)total;
+    void* stage = nullptr;
+    e = pool_host_alloc(&stage, total);
+    if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("pinned staging: ") + cudaGetErrorString(e));
+    size_t off = 0;
+    for (const auto& it : U.items) {
+        if (it.bytes) std::memcpy((char*)stage + off, it.src, it.bytes);
+        *it.dst = (char*)base + off;
+        h->h2d_bytes += (int64_t)it.bytes;
+        off += (std::max<size_t>(it.bytes, 1) + 255) / 256 * 256;
+    }
+    e = cudaMemcpyAsync(base, stage, total, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    pool_host_free(stage);
+    if (e != cudaSuccess) return set_err(h, FL_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
     return FL_OK;
 }
 
 int alloc(fl_ctx* h, void** dst, size_t bytes) {
     *dst = nullptr;
-    cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
-    if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+    cudaError_t e = pool_dev_alloc(dst, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("device workspace: ") + cudaGetErrorString(e));
     h->bufs.push_back({*dst, bytes});
     h->ws_bytes += (int64_t)bytes;
     return FL_OK;
@@ -1204,7 +1228,7 @@ void stage_mark(fl_ctx* h, cudaStream_t st, int i, int end) {
 int qf_of(const fl_ctx* h) { return h->dim == 1 ? h->opt.k_far : h->opt.k_far * h->opt.k_far; }
 int qn_of(const fl_ctx* h) { return h->dim == 1 ? h->opt.k_near : h->opt.k_near * h->opt.k_near; }
 
-int ensure_device(fl_ctx* h, int pi) {
+int ensure_device(fl_ctx* h, int pi, cudaStream_t st) {
     DevTables& t = h->dev[pi];
     if (t.ready) return FL_OK;
     const Plan& P = h->plan[pi];
@@ -1230,49 +1254,51 @@ int ensure_device(fl_ctx* h, int pi) {
     std::vector<int> csr_row(P.csr_col.size());
     for (int64_t i = 0; i < P.n; ++i)
         for (int z = P.csr_ptr[i]; z < P.csr_ptr[i + 1]; ++z) csr_row[z] = (int)i;
-    FL_TRY(upload(h, t.V, P.V));
-    FL_TRY(upload(h, t.jac_orig, P.jac));
-    FL_TRY(upload(h, t.F, P.F));
-    FL_TRY(upload(h, t.FN, P.FN));
-    FL_TRY(upload(h, t.FLEN, P.FLEN));
-    FL_TRY(upload(h, t.cvx, cvx));
-    FL_TRY(upload(h, t.cen, cen));
-    FL_TRY(upload(h, t.jac, jac));
-    FL_TRY(upload(h, t.hasdof, P.hasdof));
-    FL_TRY(upload(h, t.loc, P.loc));
-    FL_TRY(upload(h, t.cdof, P.cdof));
-    FL_TRY(upload(h, t.L_ptr, P.L_ptr));
-    FL_TRY(upload(h, t.inc_ptr, P.inc_ptr));
-    FL_TRY(upload(h, t.inc_ent, P.inc_ent));
-    FL_TRY(upload(h, t.tiles, P.tiles));
-    FL_TRY(upload(h, t.toff, P.toff));
-    FL_TRY(upload(h, t.occ_ptr, P.occ_ptr));
-    FL_TRY(upload(h, t.occ_blk, P.occ_blk));
-    FL_TRY(upload(h, t.occ_loc, P.occ_loc));
-    FL_TRY(upload(h, t.ex_ptr, P.ex_ptr));
-    FL_TRY(upload(h, t.ex_idx, P.ex_idx));
-    FL_TRY(upload(h, t.np_a, P.np_a));
-    FL_TRY(upload(h, t.np_b, P.np_b));
-    FL_TRY(upload(h, t.enp_ptr, P.enp_ptr));
-    FL_TRY(upload(h, t.enp_ent, P.enp_ent));
-    FL_TRY(upload(h, t.tp_type, P.tp_type));
-    FL_TRY(upload(h, t.tp_vert, P.tp_vert));
-    FL_TRY(upload(h, t.tp_cell, P.tp_cell));
-    FL_TRY(upload(h, t.tp_slot, P.tp_slot));
-    FL_TRY(upload(h, t.ef_ptr, P.ef_ptr));
-    FL_TRY(upload(h, t.ef_fac, P.ef_fac));
-    FL_TRY(upload(h, t.ef_cls, P.ef_cls));
-    FL_TRY(upload(h, t.csr_ptr, P.csr_ptr));
-    FL_TRY(upload(h, t.csr_col, P.csr_col));
-    FL_TRY(upload(h, t.csr_row, csr_row));
-    FL_TRY(upload(h, t.g_ptr, P.g_ptr));
-    FL_TRY(upload(h, t.g_slot, P.g_slot));
-    FL_TRY(upload(h, t.vod, P.vod));
-    FL_TRY(upload(h, t.corig, corner));
-    FL_TRY(upload(h, t.cells, P.C));
+    Uploads U;
+    U.add(t.V, P.V);
+    U.add(t.jac_orig, P.jac);
+    U.add(t.F, P.F);
+    U.add(t.FN, P.FN);
+    U.add(t.FLEN, P.FLEN);
+    U.add(t.cvx, cvx);
+    U.add(t.cen, cen);
+    U.add(t.jac, jac);
+    U.add(t.hasdof, P.hasdof);
+    U.add(t.loc, P.loc);
+    U.add(t.cdof, P.cdof);
+    U.add(t.L_ptr, P.L_ptr);
+    U.add(t.inc_ptr, P.inc_ptr);
+    U.add(t.inc_ent, P.inc_ent);
+    U.add(t.tiles, P.tiles);
+    U.add(t.toff, P.toff);
+    U.add(t.occ_ptr, P.occ_ptr);
+    U.add(t.occ_blk, P.occ_blk);
+    U.add(t.occ_loc, P.occ_loc);
+    U.add(t.ex_ptr, P.ex_ptr);
+    U.add(t.ex_idx, P.ex_idx);
+    U.add(t.np_a, P.np_a);
+    U.add(t.np_b, P.np_b);
+    U.add(t.enp_ptr, P.enp_ptr);
+    U.add(t.enp_ent, P.enp_ent);
+    U.add(t.tp_type, P.tp_type);
+    U.add(t.tp_vert, P.tp_vert);
+    U.add(t.tp_cell, P.tp_cell);
+    U.add(t.tp_slot, P.tp_slot);
+    U.add(t.ef_ptr, P.ef_ptr);
+    U.add(t.ef_fac, P.ef_fac);
+    U.add(t.ef_cls, P.ef_cls);
+    U.add(t.csr_ptr, P.csr_ptr);
+    U.add(t.csr_col, P.csr_col);
+    U.add(t.csr_row, csr_row);
+    U.add(t.g_ptr, P.g_ptr);
+    U.add(t.g_slot, P.g_slot);
+    U.add(t.vod, P.vod);
+    U.add(t.corig, corner);
+    U.add(t.cells, P.C);
     std::vector<int64_t> v2cp(P.v2c_ptr.begin(), P.v2c_ptr.end());
-    FL_TRY(upload(h, t.v2c_ptr, v2cp));
-    FL_TRY(upload(h, t.v2c, P.v2c));
+    U.add(t.v2c_ptr, v2cp);
+    U.add(t.v2c, P.v2c);
+    FL_TRY(upload_all(h, U, st));
     const int qf = qf_of(h), qn = qn_of(h);
     FL_TRY(alloc(h, &t.P, (size_t)P.toff.back() * sizeof(double)));
     FL_TRY(alloc(h, &t.Pd, (size_t)P.nblk * nc * qf * sizeof(double)));
@@ -1283,10 +1309,10 @@ int ensure_device(fl_ctx* h, int pi) {
     FL_TRY(alloc(h, (void**)&t.csr_val, P.csr_col.size() * sizeof(double)));
     FL_TRY(alloc(h, &t.facet_rec, (size_t)std::max<int64_t>(P.nf, 1) * sizeof(FacetRec)));
     if (P.dim == 2 && P.nf > 0) {
-        facet_records_kernel<<<(unsigned)((P.nf + 127) / 128), 128>>>(P.nf, t.F, t.FN, t.FLEN, t.V,
-                                                                      (FacetRec*)t.facet_rec);
+        facet_records_kernel<<<(unsigned)((P.nf + 127) / 128), 128, 0, st>>>(P.nf, t.F, t.FN, t.FLEN, t.V,
+                                                                             (FacetRec*)t.facet_rec);
         fl::count_launch();
-        FL_CUDA_TRY(h, cudaDeviceSynchronize());
+        FL_CUDA_TRY(h, cudaGetLastError());
     }
     t.ready = true;
     return FL_OK;
@@ -1625,7 +1651,7 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
     if (P.dim == 2 && P.paper_all && !h->opt.regional)
         return set_err(h, FL_ENOTIMPL, "2D boundary DOFs (FL_DOF_PAPER with s < 1/2) are not implemented");
     FL_CUDA_TRY(h, cudaSetDevice(h->device));
-    FL_TRY(ensure_device(h, pi));
+    FL_TRY(ensure_device(h, pi, st));
     DevTables& t = h->dev[pi];
     const int D = P.dim;
     // per-s rule tables
@@ -1841,7 +1867,7 @@ int load_vector(fl_ctx* h, double s, const double* f, int nrhs, double* b, int64
     if (!b || nrhs < 1 || ldb < nrhs) return set_err(h, FL_EINVAL, "bad b / nrhs / ldb");
     if (!f && nrhs != 1) return set_err(h, FL_EINVAL, "f = 1 needs nrhs = 1");
     FL_CUDA_TRY(h, cudaSetDevice(h->device));
-    FL_TRY(ensure_device(h, pi));
+    FL_TRY(ensure_device(h, pi, st));
     DevTables& t = h->dev[pi];
     const unsigned g = (unsigned)((P.n + 127) / 128);
     for (int r = 0; r < nrhs; ++r) {

@@ -1578,17 +1578,20 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
         off_df = take((size_t)df_G * df_rmax * DF_COLS * DF_ROWS * sizeof(float2));
     }
     if (total > h->batch_ws_bytes) {
-        if (h->batch_ws) cudaFree(h->batch_ws);
+        if (h->batch_ws) {
+            cudaDeviceSynchronize();  // the cached block must be idle before another user takes it
+            pool_dev_free(h->batch_ws);
+        }
         h->batch_ws = nullptr;
         h->batch_ws_bytes = 0;
-        if (cudaMalloc(&h->batch_ws, total) != cudaSuccess) {
+        if (pool_dev_alloc(&h->batch_ws, total) != cudaSuccess) {
             cudaGetLastError();
             return set_err(h, FL_ENOMEM, "batch workspace");
         }
         h->batch_ws_bytes = total;
     }
     if (!h->batch_host) {
-        if (cudaMallocHost(&h->batch_host, 4096) != cudaSuccess) return set_err(h, FL_ENOMEM, "pinned scalars");
+        if (pool_host_alloc(&h->batch_host, 4096) != cudaSuccess) return set_err(h, FL_ENOMEM, "pinned scalars");
     }
     char* W = (char*)h->batch_ws;
     int* flags = (int*)(W + off_flags);  // [0] err, [1] outer-done total, [2..] barrier, [8..15] ndone, [16..] odone

@@ -113,13 +113,13 @@ void fl_destroy(fl_handle h) {
     if (!h->bufs.empty() || h->solve_ws || h->batch_ws || h->batch_host) {
         cudaSetDevice(h->device);
         cudaDeviceSynchronize();
-        for (auto& b : h->bufs) cudaFree(b.p);
+        for (auto& b : h->bufs) fl::pool_dev_free(b.p);  // back to the cache (the device is idle)
         if (h->ev_made)
             for (int k = 0; k < 2 * FL_NSTAGES; ++k) cudaEventDestroy(h->ev[k]);
-        if (h->solve_ws) cudaFree(h->solve_ws);
-        if (h->solve_host) cudaFreeHost(h->solve_host);
-        if (h->batch_ws) cudaFree(h->batch_ws);
-        if (h->batch_host) cudaFreeHost(h->batch_host);
+        if (h->solve_ws) fl::pool_dev_free(h->solve_ws);
+        if (h->solve_host) fl::pool_host_free(h->solve_host);
+        if (h->batch_ws) fl::pool_dev_free(h->batch_ws);
+        if (h->batch_host) fl::pool_host_free(h->batch_host);
     }
     for (auto& g : h->cg_graphs) cudaGraphExecDestroy(g.exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);

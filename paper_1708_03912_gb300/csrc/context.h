@@ -116,6 +116,11 @@ namespace fl {
 void count_launch(int n = 1);
 // returns plan index for order s (building it on demand); -1 on error (h->err set)
 int plan_for(fl_ctx* h, double s);
+// caching allocator (pool.cpp): device and pinned host blocks reused across handles
+cudaError_t pool_dev_alloc(void** out, size_t bytes);
+void pool_dev_free(void* p);
+cudaError_t pool_host_alloc(void** out, size_t bytes);
+void pool_host_free(void* p);
 int set_err(fl_ctx* h, int code, const std::string& msg);
 // y = A x for a dense matrix of type dtype (linalg.cu); x, y float64 with strides; xf: n floats of
 // scratch for the float32 copy of x (unused for FL_F64)

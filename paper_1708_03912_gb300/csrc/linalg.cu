@@ -402,15 +402,16 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
         for (auto& g : h->cg_graphs) cudaGraphExecDestroy(g.exec);
         h->cg_graphs.clear();
         if (h->solve_ws) {
-            cudaFree(h->solve_ws);
-            cudaFreeHost(h->solve_host);
+            cudaDeviceSynchronize();  // the cached blocks must be idle before another user takes them
+            pool_dev_free(h->solve_ws);
+            pool_host_free(h->solve_host);
         }
         h->solve_ws = nullptr;
         h->solve_host = nullptr;
         h->solve_ws_bytes = 0;
-        if (cudaMalloc(&h->solve_ws, need) != cudaSuccess) return set_err(h, FL_ENOMEM, "cudaMalloc solver workspace");
-        if (cudaMallocHost(&h->solve_host, sizeof(CgScalars)) != cudaSuccess)
-            return set_err(h, FL_ENOMEM, "cudaMallocHost solver scalars");
+        if (pool_dev_alloc(&h->solve_ws, need) != cudaSuccess) return set_err(h, FL_ENOMEM, "solver workspace");
+        if (pool_host_alloc(&h->solve_host, sizeof(CgScalars)) != cudaSuccess)
+            return set_err(h, FL_ENOMEM, "pinned solver scalars");
         h->solve_ws_bytes = need;
     }
     base = h->solve_ws;

@@ -566,7 +566,12 @@ int plan_dofs(Plan& P, int paper_all, std::string& err) {
         RowPart& o = rparts[t];
         const int64_t i0 = (int64_t)t * rchunk, i1 = std::min(P.n, i0 + rchunk);
         std::vector<std::pair<int, int64_t>> e;
-        std::vector<int> tps;
+        std::vector<int> tps, cols;
+        std::vector<int64_t> placed;
+        // per column: the row that last used it, its slot count and its write position
+        std::vector<int64_t> mark(P.n, -1);
+        std::vector<int> ccount(P.n, 0);
+        std::vector<int64_t> cpos(P.n, 0);
         e.reserve(4096);
         const int64_t rows_here = std::max<int64_t>(0, i1 - i0);
         o.cnt.reserve(rows_here);
@@ -617,18 +622,42 @@ int plan_dofs(Plan& P, int paper_all, std::string& err) {
                     if (j >= 0) e.push_back({j, P.tp_slot[p2] + a * nl + b});
                 }
             }
-            std::sort(e.begin(), e.end());
-            int ncol = 0;
-            for (size_t q = 0; q < e.size(); ++q) {
-                if (q == 0 || e[q].first != e[q - 1].first) {
-                    o.col.push_back(e[q].first);
-                    o.gcnt.push_back(0);
-                    ++ncol;
+            // bucket the entries by column (columns ascending, slots ascending within one)
+            cols.clear();
+            for (const auto& pr : e) {
+                if (mark[pr.first] != i) {
+                    mark[pr.first] = i;
+                    ccount[pr.first] = 0;
+                    cols.push_back(pr.first);
                 }
-                o.gcnt.back()++;
-                o.slot.push_back(e[q].second);
+                ccount[pr.first]++;
             }
-            o.cnt.push_back(ncol);
+            std::sort(cols.begin(), cols.end());
+            int64_t pos = 0;
+            for (int c : cols) {
+                cpos[c] = pos;
+                pos += ccount[c];
+            }
+            placed.resize(pos);
+            for (const auto& pr : e) placed[cpos[pr.first]++] = pr.second;
+            int64_t start = 0;
+            for (int c : cols) {
+                const int64_t end = start + ccount[c];
+                for (int64_t q = start + 1; q < end; ++q) {  // insertion sort of the column's slots
+                    const int64_t x = placed[q];
+                    int64_t r = q - 1;
+                    while (r >= start && placed[r] > x) {
+                        placed[r + 1] = placed[r];
+                        --r;
+                    }
+                    placed[r + 1] = x;
+                }
+                o.col.push_back(c);
+                o.gcnt.push_back(ccount[c]);
+                start = end;
+            }
+            o.slot.insert(o.slot.end(), placed.begin(), placed.end());
+            o.cnt.push_back((int)cols.size());
         }
     };
     {

@@ -24,7 +24,8 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
 
 EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
            "fl_assemble", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
-           "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_matvec_f32_static",
+           "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
+           "fl_matvec_f32_static",
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
            "fl_tune_batch", "fl_tune_record", "fl_tune_lookup", "fl_tune_clear", "fl_tune_count", "fl_tune_save",
            "fl_tune_load", "fl_prolongation", "fl_mg_create", "fl_mg_add_level", "fl_mg_setup", "fl_mg_level", "fl_mg_level_copy",
@@ -133,6 +134,10 @@ def lib():
     L.fl_stage_ms.restype = ci
     L.fl_launch_count.argtypes = []
     L.fl_launch_count.restype = ctypes.c_uint64
+    L.fl_pool_trim.argtypes = []
+    L.fl_pool_trim.restype = i64
+    L.fl_pool_stats.argtypes = [ctypes.POINTER(i64)] * 4
+    L.fl_pool_stats.restype = None
     L.fl_matvec_f32_static.argtypes = [vp, i64, i64, vp, vp, vp]
     L.fl_matvec_f32_static.restype = ci
     L.fl_split_bf16_bytes.argtypes = [i64, ci]
@@ -337,6 +342,18 @@ def fl_stage_ms(h):
 
 def fl_launch_count():
     return int(lib().fl_launch_count())
+
+
+def fl_pool_trim():
+    """Release the allocator's cached device and pinned host blocks; returns the bytes released."""
+    return int(lib().fl_pool_trim())
+
+
+def fl_pool_stats():
+    v = [ctypes.c_int64() for _ in range(4)]
+    lib().fl_pool_stats(*[ctypes.byref(x) for x in v])
+    return {"cached_device_bytes": v[0].value, "cached_host_bytes": v[1].value, "hits": v[2].value,
+            "misses": v[3].value}
 
 
 def fl_matvec_f32_static(A32, x, y, stream=None):

@@ -114,3 +114,10 @@ def test_patch_table_matches_oracle():
             assert np.allclose(hl, oh, rtol=1e-13, atol=0)
             assert np.array_equal(hop, ohop)
         F.fl_destroy(h)
+
+
+def test_pool_stats_without_device_work():
+    # nothing has been allocated in a process without a GPU: the cache is empty
+    st = F.fl_pool_stats()
+    assert st["cached_device_bytes"] == 0 and st["cached_host_bytes"] == 0
+    assert F.fl_pool_trim() == 0
