@@ -40,14 +40,6 @@ int set_err(fl_ctx* h, int code, const std::string& msg) {
 }
 
 // ------------------------------------------------------------------ tables --
-struct RuleOffsets {
-    int qf, qn, kf, kn, kt, kb;
-    int64_t far_lam, far_w, far_phi;
-    int64_t near_lam, near_w, near_phi;
-    int64_t glf_t, glf_w, gln_t, gln_w;   // Gauss points on facets
-    int64_t t_edge, t_vert, t_1d, t_ident, b_own, b_vert;
-    int n_edge, n_vert, n_1d, n_ident, n_own, n_bvert;
-};
 
 template <typename T, int Q, int NV>
 struct FarRule {
@@ -1654,30 +1646,38 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
     FL_TRY(ensure_device(h, pi, st));
     DevTables& t = h->dev[pi];
     const int D = P.dim;
-    // per-s rule tables
-    std::vector<double> rb;
-    RuleOffsets ro;
-    build_rules(h, s, rb, ro);
-    if (ro.qn > MAXQ_NEAR) return set_err(h, FL_ENOTIMPL, "k_near too large");
-    if (t.rule_len < rb.size()) {
-        void* p = nullptr;
-        FL_TRY(alloc(h, &p, rb.size() * sizeof(double)));
-        t.rule = (double*)p;
-        t.rule_len = rb.size();
-    }
-    FL_CUDA_TRY(h, cudaMemcpyAsync(t.rule, rb.data(), rb.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    // per-s rule tables, built and uploaded once per (handle, s): repeated assemblies at the
+    // same s do no host work here and no host-synchronising copy
     const bool f32 = precision == FL_MIXED;
-    std::vector<float> rb32;
-    if (f32) {  // float32 copy of the tables for the mixed-mode touching pairs
+    if (!(t.rule_s == s)) {
+        t.rule_s = std::nan("");
+        t.rule32_ready = false;
+        build_rules(h, s, t.rule_host, t.rule_ro);
+        if (t.rule_ro.qn > MAXQ_NEAR) return set_err(h, FL_ENOTIMPL, "k_near too large");
+        const std::vector<double>& rb = t.rule_host;
+        if (t.rule_len < rb.size()) {
+            void* p = nullptr;
+            FL_TRY(alloc(h, &p, rb.size() * sizeof(double)));
+            t.rule = (double*)p;
+            t.rule_len = rb.size();
+        }
+        FL_CUDA_TRY(h, cudaMemcpyAsync(t.rule, rb.data(), rb.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        t.rule_s = s;
+    }
+    if (f32 && !t.rule32_ready) {  // float32 copy of the tables (mixed-mode touching pairs, identical pair)
+        const std::vector<double>& rb = t.rule_host;
         if (t.rule32_len < rb.size()) {
             void* p = nullptr;
             FL_TRY(alloc(h, &p, rb.size() * sizeof(float)));
             t.rule32 = (float*)p;
             t.rule32_len = rb.size();
         }
-        rb32.assign(rb.begin(), rb.end());
+        const std::vector<float> rb32(rb.begin(), rb.end());
         FL_CUDA_TRY(h, cudaMemcpyAsync(t.rule32, rb32.data(), rb32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        t.rule32_ready = true;
     }
+    const std::vector<double>& rb = t.rule_host;
+    const RuleOffsets& ro = t.rule_ro;
     const double C = frac_constant(D, s);
     const double expo = -(D + 2.0 * s) / 2.0;
     const int pw = pw_mode(D, s);

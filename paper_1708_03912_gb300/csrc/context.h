@@ -29,6 +29,16 @@ struct CgGraph {
     cudaGraphExec_t exec;
 };
 
+// Offsets of the per-s quadrature tables in one float64 buffer (built by build_rules).
+struct RuleOffsets {
+    int qf, qn, kf, kn, kt, kb;
+    int64_t far_lam, far_w, far_phi;
+    int64_t near_lam, near_w, near_phi;
+    int64_t glf_t, glf_w, gln_t, gln_w;   // Gauss points on facets
+    int64_t t_edge, t_vert, t_1d, t_ident, b_own, b_vert;
+    int n_edge, n_vert, n_1d, n_ident, n_own, n_bvert;
+};
+
 // One device allocation owned by a handle.
 struct DBuf {
     void* p = nullptr;
@@ -80,6 +90,10 @@ struct DevTables {
     size_t rule_len = 0;
     float* rule32 = nullptr;  // their float32 copy (mixed-mode touching pairs)
     size_t rule32_len = 0;
+    double rule_s = -1.0;        // the s the device tables hold (NaN while being rebuilt)
+    bool rule32_ready = false;   // the float32 copy matches them
+    std::vector<double> rule_host;
+    RuleOffsets rule_ro{};
 };
 
 }  // namespace fl
