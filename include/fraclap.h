@@ -166,11 +166,16 @@ void fl_default_solve_opts(fl_solve_opts* o);
  * overwritten; the iteration starts from 0).  With inner_dtype = FL_F32 (or
  * FL_BF16) the Jacobi-PCG runs on the low-precision copy o->A_lo_dev inside float64
  * iterative refinement u += d, M d = b - A u, until ||b - A u|| <= tol ||b|| with
- * the float64 A.  The iteration runs on the device; the host reads the scalars
- * once per iteration.  h supplies the workspace (grown on demand) and the error
- * message.  info (host) receives counts and the final residual, computed afresh in
- * float64.  Synchronises `stream`.  Returns FL_OK, FL_ENOTCONV, FL_ENOTSPD,
- * FL_EINVAL, FL_ENOMEM or FL_ECUDA.
+ * the float64 A.  Where cooperative launches are available the plain solve, and
+ * with FL_F32 the whole refinement (float64 residual of each step, stop test,
+ * float32 inner CG, update), run as one cooperative launch whose blocks own row
+ * ranges; the host reads one result block at the end.  Otherwise (and for
+ * FL_BF16) the iterations run as captured kernel batches with the scalars read
+ * once per batch.  h supplies the workspace (grown on demand) and the error
+ * message.  info (host) receives counts and the final residual ||b - A u|| /
+ * ||b||, computed in float64 with A.  Synchronises `stream`.  Returns FL_OK,
+ * FL_ENOTCONV, FL_ENOTSPD, FL_EINVAL, FL_ENOMEM, FL_ECUDA, or FL_ETIMEOUT when a
+ * grid barrier of a cooperative launch waited longer than its bound (2 s).
  */
 int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const double* b_dev, double* u_dev,
              const fl_solve_opts* o, fl_solve_info* info, void* stream);
