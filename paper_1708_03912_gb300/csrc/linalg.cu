@@ -380,10 +380,18 @@ __global__ void zero_kernel(int64_t n, double* x) {
 }
 
 // ------------------------------------------------------- solver workspace --
+// Partial-sum area of the persistent solvers (in doubles): per-block partials of up to three
+// slots of 1024 (float32 pipelined CG: two parity sets of three slots), the float64
+// partials of the refinement at PARTD_OFF, and the error flag at ERR_OFF.
+constexpr int PART_DOUBLES = 8 * 1024;
+constexpr int PARTD_OFF = 4 * 1024;
+constexpr int ERR_OFF = 7 * 1024;
+
 struct SolveWork {
     double *r, *z, *p, *q, *dinv, *dinv_lo, *d, *t, *sv, *prz, *prr, *ppq, *part;
     unsigned* gbar;  // grid-barrier counter of the persistent solver (own cache line)
     float* xf;
+    float* fv[12];  // float32 vectors of the pipelined inner CG
     CgScalars* s;
     CgScalars* s_host;
 };
@@ -395,7 +403,7 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
     // (eight float64 vectors, three reduction buffers, one float32 vector, scalars)
     // is carved with the same 256-byte rounding that sizes it
     const size_t need = 9 * round256(n * sizeof(double)) + 3 * round256(RED_BLOCKS * sizeof(double)) +
-                        round256(4 * 1024 * sizeof(double)) + round256(256) + round256(n * sizeof(float)) +
+                        round256(PART_DOUBLES * sizeof(double)) + round256(256) + 13 * round256(n * sizeof(float)) +
                         round256(sizeof(CgScalars));
     void* base = nullptr;
     if (h->solve_ws_bytes < need) {
@@ -433,9 +441,10 @@ static int get_work(fl_ctx* h, int64_t n, SolveWork& w) {
     w.prz = (double*)take(RED_BLOCKS * sizeof(double));
     w.prr = (double*)take(RED_BLOCKS * sizeof(double));
     w.ppq = (double*)take(RED_BLOCKS * sizeof(double));
-    w.part = (double*)take(4 * 1024 * sizeof(double));
+    w.part = (double*)take(PART_DOUBLES * sizeof(double));
     w.gbar = (unsigned*)take(256);
     w.xf = (float*)take(n * sizeof(float));
+    for (int k = 0; k < 12; ++k) w.fv[k] = (float*)take(n * sizeof(float));
     w.s = (CgScalars*)take(sizeof(CgScalars));
     w.s_host = (CgScalars*)h->solve_host;
     if ((size_t)(c - (char*)base) > need) return set_err(h, FL_EINVAL, "solver workspace layout exceeds its size");
@@ -723,6 +732,171 @@ __device__ __forceinline__ bool cg_block_solve(const CgBlock<T>& c, const double
     return true;
 }
 
+// The product of the block's own rows with xg (all n entries): xg staged in shared memory
+// (MODE >= 1), one warp per row, the results in c.ws; ends with a block barrier.
+template <typename T, int MODE>
+__device__ __forceinline__ void rows_product(const CgBlock<T>& c, const T* __restrict__ xg) {
+    constexpr int V = 16 / sizeof(T);
+    const int64_t n = c.n;
+    if constexpr (MODE >= 1) {
+        const int64_t nq = n * (int64_t)sizeof(T) / 16;  // xg is 256-byte aligned
+        const uint4* src = reinterpret_cast<const uint4*>(xg);
+        uint4* dst = reinterpret_cast<uint4*>(c.xs);
+        for (int64_t i0 = threadIdx.x; i0 < nq; i0 += 4 * blockDim.x) {
+            uint4 q[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (i0 + j * blockDim.x < nq) q[j] = __ldcg(src + i0 + j * blockDim.x);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (i0 + j * blockDim.x < nq) dst[i0 + j * blockDim.x] = q[j];
+        }
+        for (int64_t i = nq * 16 / (int64_t)sizeof(T) + threadIdx.x; i < n; i += blockDim.x) c.xs[i] = __ldcg(xg + i);
+        __syncthreads();
+    }
+    for (int64_t row = c.r0 + c.warp; row < c.r1; row += PCG_WARPS) {
+        T acc;
+        if constexpr (MODE == 2) {
+            const uint4* a4 = reinterpret_cast<const uint4*>(c.As + (row - c.r0) * c.lds);
+            const uint4* x4 = reinterpret_cast<const uint4*>(c.xs);
+            T s0 = 0, s1 = 0;
+            for (int64_t q = c.lane; q < c.lds / V; q += 32) {
+                const uint4 av = a4[q], xv = x4[q];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (v & 1) s1 = fma(vec_elem<T>(av, v), vec_elem<T>(xv, v), s1);
+                    else s0 = fma(vec_elem<T>(av, v), vec_elem<T>(xv, v), s0);
+                }
+            }
+            acc = warp_total(s0 + s1);
+        } else {
+            acc = row_dot<T, T, T, (MODE == 1)>(c.A + row * c.lda, MODE == 1 ? c.xs : xg, n, c.lane);
+        }
+        if (c.lane == 0) c.ws[row - c.r0] = acc;
+    }
+    __syncthreads();
+}
+
+// Float32 work vectors of the pipelined CG (x the solution; m double-buffered by step parity).
+struct PipeVecs {
+    float *x, *r, *u, *w, *z, *q, *s, *p, *m0, *m1, *dv;
+};
+
+// One Jacobi-PCG solve M x = rhs from x = 0 in the pipelined arrangement (one global
+// synchronisation per step, Ghysels & Vanroose): with u = D^-1 r, w = A u, m = D^-1 w and
+// n = A m, a step takes gamma = r.u, delta = w.u (and r.r for the stopping test) from the
+// previous step's partials, forms n = A m for the own rows, updates
+//   z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p,
+//   x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z,
+// and writes m = D^-1 w and the next partials before the step's only grid barrier.  The
+// partials (two sets of three slots) and m alternate by step parity, so a block that runs
+// ahead never overwrites what a slower block still reads.  The recurrences drift from the
+// true residual by a few float32 roundings per step; in the refinement every step is
+// judged and corrected by the float64 residual.  breakdown_out is set for a non-positive
+// p.Ap while ||r|| > 1e-3 ||r_0||; below that it is lost accuracy and just ends the solve.
+template <int MODE>
+__device__ __forceinline__ bool pipe_block_solve(const CgBlock<float>& c, const PipeVecs& v,
+                                                 const double* __restrict__ rhs, double tol, int maxit,
+                                                 unsigned& epoch, int& it_out, int& breakdown_out, float& rr_out,
+                                                 float& rr0_out) {
+    const int64_t r0 = c.r0, r1 = c.r1;
+    const int nb = c.nb;
+    float* sh = c.sh;
+    // start: x = 0, r = rhs, u = D^-1 r, z = q = s = p = 0
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const float ri = (float)rhs[i];
+        v.x[i] = 0.f;
+        v.r[i] = ri;
+        v.u[i] = v.dv[i] * ri;
+        v.z[i] = 0.f;
+        v.q[i] = 0.f;
+        v.s[i] = 0.f;
+        v.p[i] = 0.f;
+    }
+    if (!tc::grid_barrier(c.gbar, epoch, nb, c.err)) return false;
+    // w = A u, m = D^-1 w, partials of r.u, w.u, r.r (set 0)
+    rows_product<float, MODE>(c, v.u);
+    {
+        float t[3] = {0.f, 0.f, 0.f};
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const float ri = v.r[i], ui = v.u[i], wi = c.ws[i - r0];
+            v.w[i] = wi;
+            v.m0[i] = v.dv[i] * wi;
+            t[0] = fmaf(ri, ui, t[0]);
+            t[1] = fmaf(wi, ui, t[1]);
+            t[2] = fmaf(ri, ri, t[2]);
+        }
+        block_totals<float, 3>(t, sh);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 3; ++k) c.part[k * 1024 + blockIdx.x] = t[k];
+    }
+    if (!tc::grid_barrier(c.gbar, epoch, nb, c.err)) return false;
+    float gamma_prev = 1.f, alpha_prev = 1.f, rr0 = 0.f, stop = 0.f, rr = 0.f;
+    int it = 0, breakdown = 0;
+    for (;;) {
+        const int set = it & 1;
+        float tot[3];
+        grid_totals<float, 3>(tot, c.part, {3 * set, 3 * set + 1, 3 * set + 2}, nb, sh);
+        const float gamma = tot[0], delta = tot[1];
+        rr = tot[2];
+        if (it == 0) {
+            rr0 = rr;
+            stop = (float)(tol * tol) * rr0;
+        }
+        if (!(rr > stop) || it >= maxit) break;
+        const float beta = (it == 0) ? 0.f : gamma / gamma_prev;
+        const float den = (it == 0) ? delta : delta - beta * gamma / alpha_prev;
+        if (!(den > 0.f)) {
+            // p.Ap <= 0 while the residual is still above 1e-3 of its start: the matrix is not
+            // SPD.  Below that: the float32 recurrences have lost their accuracy; the solve ends
+            // with the current x (the refinement's float64 residual decides what comes next)
+            breakdown = (it == 0 || rr > 1e-6f * rr0) ? 1 : 0;
+            break;
+        }
+        const float alpha = gamma / den;
+        const float* m_cur = set ? v.m1 : v.m0;
+        float* m_next = set ? v.m0 : v.m1;
+        rows_product<float, MODE>(c, m_cur);
+        float t[3] = {0.f, 0.f, 0.f};
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const float ni = c.ws[i - r0];
+            const float mi = (MODE >= 1) ? c.xs[i] : __ldcg(m_cur + i);
+            const float ui = v.u[i], wi = v.w[i];
+            const float zi = fmaf(beta, v.z[i], ni);
+            const float qi = fmaf(beta, v.q[i], mi);
+            const float si = fmaf(beta, v.s[i], wi);
+            const float pi = fmaf(beta, v.p[i], ui);
+            v.z[i] = zi;
+            v.q[i] = qi;
+            v.s[i] = si;
+            v.p[i] = pi;
+            v.x[i] = fmaf(alpha, pi, v.x[i]);
+            const float rn = fmaf(-alpha, si, v.r[i]);
+            const float un = fmaf(-alpha, qi, ui);
+            const float wn = fmaf(-alpha, zi, wi);
+            v.r[i] = rn;
+            v.u[i] = un;
+            v.w[i] = wn;
+            m_next[i] = v.dv[i] * wn;
+            t[0] = fmaf(rn, un, t[0]);
+            t[1] = fmaf(wn, un, t[1]);
+            t[2] = fmaf(rn, rn, t[2]);
+        }
+        block_totals<float, 3>(t, sh);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 3; ++k) c.part[(3 * (set ^ 1) + k) * 1024 + blockIdx.x] = t[k];
+        if (!tc::grid_barrier(c.gbar, epoch, nb, c.err)) return false;
+        gamma_prev = gamma;
+        alpha_prev = alpha;
+        ++it;
+    }
+    it_out = it;
+    breakdown_out = breakdown;
+    rr_out = rr;
+    rr0_out = rr0;
+    return true;
+}
+
 template <typename T, int MODE>
 __device__ __forceinline__ CgBlock<T> cg_block(int64_t n, int64_t rpb, int64_t lds, const T* A, int64_t lda, T* u,
                                                T* r, T* z, T* p, T* sv, T* dv, T* part, unsigned* gbar, int* err,
@@ -788,6 +962,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1)
 // residual r = b - A u of the own rows (u = 0 first, so r = b), the stopping test
 // ||r|| <= tol ||b|| from the same totals in every block, the float32 solve M d = r, and
 // u += d.  The float32 rows of M are copied into shared memory once for all steps (MODE 2).
+// Stops unconverged after max_outer steps or after three steps without a smaller residual.
 struct RefineOut {
     double rr, bb;
     int outer, inner, status;  // status: 0 converged, 1 step limit, 2 breakdown
@@ -797,53 +972,57 @@ template <int MODE>
 __global__ void __launch_bounds__(PCG_THREADS, 1)
     refine_persistent_kernel(int64_t n, int64_t rpb, int64_t lds, const double* __restrict__ A64, int64_t lda,
                              const float* __restrict__ A32, int64_t ld32, const double* __restrict__ dinv32,
-                             const double* __restrict__ b, double* u, double* r64, float* d, float* r, float* z,
-                             float* p, float* sv, float* dv, float* partf, double* partd, unsigned* gbar,
-                             RefineOut* out, double tol, double inner_tol, int max_outer, int inner_maxit, int* err) {
+                             const double* __restrict__ b, double* u, double* r64, const PipeVecs v,
+                             float* partf, double* partd, unsigned* gbar, RefineOut* out, double tol,
+                             double inner_tol, int max_outer, int inner_maxit, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ float sh[2 * 33];
+    __shared__ float sh[3 * 33];
     __shared__ double shd[33];
-    const CgBlock<float> c =
-        cg_block<float, MODE>(n, rpb, lds, A32, ld32, d, r, z, p, sv, dv, partf, gbar, err, sh, smem_raw);
+    const CgBlock<float> c = cg_block<float, MODE>(n, rpb, lds, A32, ld32, v.x, v.r, v.z, v.p, v.s, v.dv, partf,
+                                                   gbar, err, sh, smem_raw);
     cg_block_setup<float, MODE>(c);
     for (int64_t i = c.r0 + threadIdx.x; i < c.r1; i += blockDim.x) {
-        dv[i] = (float)dinv32[i];
+        v.dv[i] = (float)dinv32[i];
         u[i] = 0.0;
     }
     unsigned epoch = 0;
-    double bb = 0.0, rr = 0.0;
-    int outer = 0, inner = 0, status = 1;
+    double bb = 0.0, rr = 0.0, rr_prev = 0.0;
+    int outer = 0, inner = 0, status = 1, stalled = 0;
     for (;;) {
         // float64 residual of the own rows (one warp per row; u is complete after the barrier)
-        double v[1] = {0.0};
+        double rv[1] = {0.0};
         for (int64_t row = c.r0 + c.warp; row < c.r1; row += PCG_WARPS) {
             const double acc = outer == 0 ? 0.0 : row_dot<double, double, double, false>(A64 + row * lda, u, n, c.lane);
             if (c.lane == 0) {
                 const double ri = b[row] - acc;
                 r64[row] = ri;
-                v[0] = fma(ri, ri, v[0]);
+                rv[0] = fma(ri, ri, rv[0]);
             }
         }
-        block_totals<double, 1>(v, shd);
-        if (threadIdx.x == 0) partd[blockIdx.x] = v[0];
+        block_totals<double, 1>(rv, shd);
+        if (threadIdx.x == 0) partd[blockIdx.x] = rv[0];
         if (!tc::grid_barrier(gbar, epoch, c.nb, err)) return;
-        grid_totals<double, 1>(v, partd, {0}, c.nb, shd);
-        rr = v[0];
+        grid_totals<double, 1>(rv, partd, {0}, c.nb, shd);
+        rr = rv[0];
         if (outer == 0) bb = rr;
         if (rr <= tol * tol * bb) {
             status = 0;
             break;
         }
         if (outer >= max_outer) break;
+        // three steps in a row without a smaller float64 residual: stop (not converged)
+        stalled = (outer > 0 && !(rr < rr_prev)) ? stalled + 1 : 0;
+        if (stalled >= 3) break;
+        rr_prev = rr;
         int it = 0, breakdown = 0;
         float irr = 0.f, irr0 = 0.f;
-        if (!cg_block_solve<float, MODE>(c, r64, inner_tol, inner_maxit, epoch, it, breakdown, irr, irr0)) return;
+        if (!pipe_block_solve<MODE>(c, v, r64, inner_tol, inner_maxit, epoch, it, breakdown, irr, irr0)) return;
         inner += it;
         if (breakdown) {
             status = 2;
             break;
         }
-        for (int64_t i = c.r0 + threadIdx.x; i < c.r1; i += blockDim.x) u[i] += (double)d[i];
+        for (int64_t i = c.r0 + threadIdx.x; i < c.r1; i += blockDim.x) u[i] += (double)v.x[i];
         ++outer;
         if (!tc::grid_barrier(gbar, epoch, c.nb, err)) return;
     }
@@ -913,7 +1092,7 @@ static bool pcg_persistent(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const 
         cudaGetLastError();
         return false;
     }
-    int* err = reinterpret_cast<int*>(w.part + 3 * 1024);
+    int* err = reinterpret_cast<int*>(w.part + ERR_OFF);
     if (cudaMemsetAsync(w.gbar, 0, sizeof(unsigned), st) != cudaSuccess ||
         cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
         cudaGetLastError();
@@ -966,25 +1145,36 @@ static bool refine_persistent(fl_ctx* h, SolveWork& w, int64_t n, const double* 
         cudaGetLastError();
         return false;
     }
-    int* err = reinterpret_cast<int*>(w.part + 3 * 1024);
+    int* err = reinterpret_cast<int*>(w.part + ERR_OFF);
     if (cudaMemsetAsync(w.gbar, 0, sizeof(unsigned), st) != cudaSuccess ||
         cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    // float32 vectors in the first halves of the float64 work vectors (d in q), D^-1 in xf;
-    // float partials in the first 12 KiB of part, float64 partials at part + 2048
+    // float32 vectors of the pipelined CG in fv; float32 partials (two sets of three slots)
+    // at the start of part, float64 partials at PARTD_OFF
     float* partf = reinterpret_cast<float*>(w.part);
-    double* partd = w.part + 2048;
+    double* partd = w.part + PARTD_OFF;
     RefineOut* out = reinterpret_cast<RefineOut*>(w.s);
     const double* dinv32 = w.dinv_lo;
     double* r64 = w.t;
-    float *d = (float*)w.q, *r = (float*)w.r, *z = (float*)w.z, *p = (float*)w.p, *sv = (float*)w.sv, *dv = w.xf;
-    void* args[] = {(void*)&n,     (void*)&rpb,   (void*)&lds,   (void*)&A64,  (void*)&lda,       (void*)&A32,
-                    (void*)&ld32,  (void*)&dinv32, (void*)&b,    (void*)&u,    (void*)&r64,       (void*)&d,
-                    (void*)&r,     (void*)&z,     (void*)&p,     (void*)&sv,   (void*)&dv,        (void*)&partf,
-                    (void*)&partd, (void*)&w.gbar, (void*)&out,  (void*)&tol,  (void*)&inner_tol, (void*)&max_outer,
-                    (void*)&inner_maxit, (void*)&err};
+    PipeVecs v;
+    v.x = w.fv[0];
+    v.r = w.fv[1];
+    v.u = w.fv[2];
+    v.w = w.fv[3];
+    v.z = w.fv[4];
+    v.q = w.fv[5];
+    v.s = w.fv[6];
+    v.p = w.fv[7];
+    v.m0 = w.fv[8];
+    v.m1 = w.fv[9];
+    v.dv = w.fv[10];
+    void* args[] = {(void*)&n,    (void*)&rpb,    (void*)&lds,  (void*)&A64,       (void*)&lda,
+                    (void*)&A32,  (void*)&ld32,   (void*)&dinv32, (void*)&b,       (void*)&u,
+                    (void*)&r64,  (void*)&v,      (void*)&partf, (void*)&partd,    (void*)&w.gbar,
+                    (void*)&out,  (void*)&tol,    (void*)&inner_tol, (void*)&max_outer, (void*)&inner_maxit,
+                    (void*)&err};
     const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(PCG_THREADS), args, smem, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1042,7 +1232,7 @@ static int pcg(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const void* M, int
     if (pcg_persistent(h, w, n, dtype, M, ldm, dinv, rhs, d, tol, maxit, st, &pst)) {
         int err = 0;
         FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
-        FL_CU(h, cudaMemcpyAsync(&err, w.part + 3 * 1024, sizeof(int), cudaMemcpyDeviceToHost, st));
+        FL_CU(h, cudaMemcpyAsync(&err, w.part + ERR_OFF, sizeof(int), cudaMemcpyDeviceToHost, st));
         FL_CU(h, cudaStreamSynchronize(st));
         if (err != 0) return set_err(h, FL_ETIMEOUT, "a grid barrier of the persistent solver gave up");
         const CgScalars& S = *w.s_host;
@@ -1163,7 +1353,7 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
         // the whole refinement ran in one cooperative launch; its last residual is float64 with A
         int err = 0;
         FL_CU(h, cudaMemcpyAsync(w.s_host, w.s, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
-        FL_CU(h, cudaMemcpyAsync(&err, w.part + 3 * 1024, sizeof(int), cudaMemcpyDeviceToHost, st));
+        FL_CU(h, cudaMemcpyAsync(&err, w.part + ERR_OFF, sizeof(int), cudaMemcpyDeviceToHost, st));
         FL_CU(h, cudaStreamSynchronize(st));
         if (err != 0) return set_err(h, FL_ETIMEOUT, "a grid barrier of the persistent refinement gave up");
         RefineOut ro;

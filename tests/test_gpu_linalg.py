@@ -69,6 +69,14 @@ def test_pcg_and_mixed_refinement_2d():
     u2, info2 = m.solve(A, b, tol=1e-10, A_lo=A32, inner_tol=1e-3)
     assert info2.status == F.FL_OK and info2.rel_residual <= 1e-10 and info2.outer_iterations >= 2
     assert np.max(np.abs(u2.cpu().numpy() - uo)) <= 1e-7 * np.max(np.abs(uo))
+    # an inner tolerance below float32 resolution: the float32 recurrences lose accuracy
+    # before reaching it, the inner solve ends there and the refinement still converges
+    u4, info4 = m.solve(A, b, tol=1e-11, A_lo=A32, inner_tol=1e-9, inner_maxit=500)
+    assert info4.status == F.FL_OK and info4.rel_residual <= 1e-11
+    assert np.max(np.abs(u4.cpu().numpy() - uo)) <= 1e-8 * np.max(np.abs(uo))
+    # the refinement's step limit is reported, not raised
+    u5, info5 = m.solve(A, b, tol=1e-14, maxit=1, A_lo=A32, inner_tol=1e-3)
+    assert info5.status == F.FL_ENOTCONV and info5.outer_iterations == 1
     # iteration limit is reported, not raised
     u3, info3 = m.solve(A, b, tol=1e-14, maxit=3)
     assert info3.status == F.FL_ENOTCONV
@@ -87,6 +95,10 @@ def test_pcg_reports_breakdown_on_indefinite_matrix():
     u = torch.empty_like(b)
     info = F.fl_solve(m.h, A, b, u)
     assert info.status == F.FL_ENOTSPD
+    # the same through the refinement with the float32 inner solve
+    A32 = A.to(torch.float32)
+    _, info2 = m.solve(A, b, tol=1e-10, A_lo=A32)
+    assert info2.status == F.FL_ENOTSPD
     m.close()
 
 
