@@ -1105,35 +1105,63 @@ __global__ void gather_csr_kernel(int64_t nnz, const int* csr_row, const int* cs
     val[z] = acc;
 }
 
+// A_ij = -C sum over the block occurrences (Ba, la) of DOF min(i, j) and (Bb, lb) of DOF
+// max(i, j) of the tile partial blocks, in occurrence order (a major, b minor), so A_ij and
+// A_ji are the same sum.  One block per 32 x 32 tile of the upper triangle (tile row
+// IB <= tile column JB): 8 warps, each thread four rows of one column; the tile is written
+// as is and, through shared memory, transposed, both with coalesced stores.
 template <typename T>
-__global__ void compose_far_kernel(int64_t n, int64_t nblk, const int* occ_ptr, const int* occ_blk,
-                                   const int* occ_loc, const int* L_ptr, const int64_t* toff, const T* P,
-                                   double negC, double* A, int64_t lda) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
-    const int64_t lo = min(i, j), hi = max(i, j);
-    double acc = 0.0;
-    for (int a = occ_ptr[lo]; a < occ_ptr[lo + 1]; ++a) {
-        const int64_t Ba = occ_blk[a];
-        const int la = occ_loc[a];
-        for (int b = occ_ptr[hi]; b < occ_ptr[hi + 1]; ++b) {
-            const int64_t Bb = occ_blk[b];
-            const int lb = occ_loc[b];
-            if (Ba < Bb) {
-                const int64_t t = Ba * nblk - Ba * (Ba - 1) / 2 + (Bb - Ba);
-                acc += (double)P[toff[t] + (int64_t)la * (L_ptr[Bb + 1] - L_ptr[Bb]) + lb];
-            } else if (Ba > Bb) {
-                const int64_t t = Bb * nblk - Bb * (Bb - 1) / 2 + (Ba - Bb);
-                acc += (double)P[toff[t] + (int64_t)lb * (L_ptr[Ba + 1] - L_ptr[Ba]) + la];
-            } else {
-                const int64_t t = Ba * nblk - Ba * (Ba - 1) / 2;
-                const int64_t nL = L_ptr[Ba + 1] - L_ptr[Ba];
-                acc += (double)P[toff[t] + (int64_t)la * nL + lb] + (double)P[toff[t] + (int64_t)lb * nL + la];
-            }
-        }
+__global__ void __launch_bounds__(256) compose_far_kernel(int64_t n, int64_t nblk, const int* occ_ptr,
+                                                          const int* occ_blk, const int* occ_loc, const int* L_ptr,
+                                                          const int64_t* toff, const T* P, double negC, double* A,
+                                                          int64_t lda) {
+    __shared__ double tile[32][33];
+    // tile index -> (IB, JB), IB <= JB, in row order of the upper triangle
+    const int64_t nt = (n + 31) / 32;
+    int64_t rem = blockIdx.x, IB = 0;
+    while (rem >= nt - IB) {
+        rem -= nt - IB;
+        ++IB;
     }
-    A[i * lda + j] = negC * acc;
+    const int64_t JB = IB + rem;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t j = JB * 32 + tx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t i = IB * 32 + ty + 8 * k;
+        double acc = 0.0;
+        if (i < n && j < n) {
+            const int64_t lo = min(i, j), hi = max(i, j);
+            for (int a = occ_ptr[lo]; a < occ_ptr[lo + 1]; ++a) {
+                const int64_t Ba = occ_blk[a];
+                const int la = occ_loc[a];
+                for (int b = occ_ptr[hi]; b < occ_ptr[hi + 1]; ++b) {
+                    const int64_t Bb = occ_blk[b];
+                    const int lb = occ_loc[b];
+                    if (Ba < Bb) {
+                        const int64_t t = Ba * nblk - Ba * (Ba - 1) / 2 + (Bb - Ba);
+                        acc += (double)P[toff[t] + (int64_t)la * (L_ptr[Bb + 1] - L_ptr[Bb]) + lb];
+                    } else if (Ba > Bb) {
+                        const int64_t t = Bb * nblk - Bb * (Bb - 1) / 2 + (Ba - Bb);
+                        acc += (double)P[toff[t] + (int64_t)lb * (L_ptr[Ba + 1] - L_ptr[Ba]) + la];
+                    } else {
+                        const int64_t t = Ba * nblk - Ba * (Ba - 1) / 2;
+                        const int64_t nL = L_ptr[Ba + 1] - L_ptr[Ba];
+                        acc += (double)P[toff[t] + (int64_t)la * nL + lb] + (double)P[toff[t] + (int64_t)lb * nL + la];
+                    }
+                }
+            }
+            A[i * lda + j] = negC * acc;
+        }
+        tile[ty + 8 * k][tx] = negC * acc;
+    }
+    if (IB == JB) return;
+    __syncthreads();
+    // transposed tile: rows JB*32 + ..., columns IB*32 + tx
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t r = JB * 32 + ty + 8 * k, c = IB * 32 + tx;
+        if (r < n && c < n) A[r * lda + c] = tile[tx][ty + 8 * k];
     }
 }
 
@@ -1812,12 +1840,13 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
         FL_CUDA_TRY(h, cudaGetLastError());
     }
     {
-        dim3 grid((unsigned)((P.n + 127) / 128), (unsigned)std::min<int64_t>(P.n, 65535));
+        const int64_t nt = (P.n + 31) / 32;
+        const unsigned grid = (unsigned)(nt * (nt + 1) / 2);  // upper-triangle 32 x 32 tiles
         if (f32)
-            compose_far_kernel<float><<<grid, 128, 0, st>>>(P.n, P.nblk, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr, t.toff,
+            compose_far_kernel<float><<<grid, 256, 0, st>>>(P.n, P.nblk, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr, t.toff,
                                                             (const float*)t.P, -C, A, lda);
         else
-            compose_far_kernel<double><<<grid, 128, 0, st>>>(P.n, P.nblk, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr, t.toff,
+            compose_far_kernel<double><<<grid, 256, 0, st>>>(P.n, P.nblk, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr, t.toff,
                                                              (const double*)t.P, -C, A, lda);
         fl::count_launch();
         FL_CUDA_TRY(h, cudaGetLastError());
