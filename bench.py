@@ -98,6 +98,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_rate(total_ms, steps, units_per_step, world, dist=None, device="cpu"):
+    """Whole-job rate over replicas: every rank processed `units_per_step` units in each of
+    `steps` timed steps; the job time is the maximum of the ranks' timed totals (ms).
+    Returns (max time in ms, units of all ranks per second)."""
+    t_max = float(total_ms)
+    if dist is not None and world > 1:
+        import torch
+
+        t = torch.tensor([t_max], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return t_max, world * steps * units_per_step / (t_max / 1000.0)
+
+
 def oracle_sample(seconds_target=15.0):
     """Time the CPU oracle on element-pair rows of the same workload.  Returns
     (ordered element pairs evaluated per second, threads, sample description)."""
@@ -280,12 +294,7 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    t_max = total_ms
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps * n_el * n_el / (t_max / 1000.0)
+    t_max, value = job_rate(total_ms, args.steps, n_el * n_el, world, dist, dev)
 
     # ---- side measurements (untimed for the headline) ----
     def timed(fn, reps=5, flush_between=True):
