@@ -363,13 +363,17 @@ class _Sink:
 
 
 def assemble_matrix(mesh: OracleMesh, s: float, orders: QuadOrders = QuadOrders(),
-                    dof_mode: str = "interior", rows=None, chunk: int = 4096, regional: bool = False):
+                    dof_mode: str = "interior", rows=None, chunk: int = 4096, regional: bool = False,
+                    far_offdiag: bool = True):
     """Dense A^s (or the rows `rows` of it) in the DOF numbering of mesh.dofs().
 
     Returns (A, vertex_of_dof).  Loops over elements K in index order and, for
     each, over partner elements K' and boundary facets e (Section 5).
     regional=True drops the boundary term, which gives the regional fractional
-    Laplacian of Section 2."""
+    Laplacian of Section 2.  far_offdiag=False leaves out the off-diagonal blocks
+    -C ∬ phi_i(x) phi_j(y) k of the separated pairs at vertex-graph distance >= 2
+    (the far field of Section 6) and keeps everything else, their diagonal-block
+    terms included: the sparse near-field part N of A = N + F."""
     if not 0.0 < s < 1.0:
         raise ValueError("s must lie in (0, 1)")
     d = mesh.dim
@@ -404,14 +408,16 @@ def assemble_matrix(mesh: OracleMesh, s: float, orders: QuadOrders = QuadOrders(
                 loc, blk = common_vertex_2d(mesh, s, C, lo, hi, orders.k_vertex)
             sink.add(loc, loc, blk)
         # separated pairs
-        for sel, order in (((shared == 0) & near, orders.k_near), ((shared == 0) & ~near, orders.k_far)):
+        for sel, order, keep_off in (((shared == 0) & near, orders.k_near, True),
+                                     ((shared == 0) & ~near, orders.k_far, far_offdiag)):
             ms = np.nonzero(partner & sel)[0]
             for c0 in range(0, len(ms), chunk):
                 mm = ms[c0:c0 + chunk]
                 off, blk_k, blk_m = separated_blocks(mesh, s, C, k, mm, order)
                 blocks[k] += blk_k
                 blocks[mm] += blk_m
-                sink.add_off(mesh.C[k], mesh.C[mm], off)
+                if keep_off:
+                    sink.add_off(mesh.C[k], mesh.C[mm], off)
         # identical pair
         if has_dof[k]:
             loc, blk = identical_1d(mesh, s, C, k) if d == 1 else identical_2d(mesh, s, C, k, 2 * orders.k_touch)
@@ -436,6 +442,23 @@ def assemble_matrix(mesh: OracleMesh, s: float, orders: QuadOrders = QuadOrders(
         if has_dof[k]:
             sink.add(mesh.C[k], mesh.C[k], blocks[k])
     return sink.A, vod
+
+
+def nearfield_pattern(mesh: OracleMesh, s: float, dof_mode: str = "interior"):
+    """Boolean n x n: (i, j) such that some cell of supp phi_i shares a vertex with, or
+    lies at vertex-graph distance 1 from, some cell of supp phi_j (pure combinatorics)."""
+    vod, dov = mesh.dofs(s, dof_mode)
+    n = len(vod)
+    close = np.zeros((mesh.nc, mesh.nc), dtype=bool)  # cell pairs touching or near
+    for k in range(mesh.nc):
+        shared, near = mesh.classify_cells(k)
+        close[k] = (shared > 0) | near
+    # cells of each DOF's support
+    S = np.zeros((n, mesh.nc), dtype=bool)
+    for i, v in enumerate(vod):
+        S[i, mesh.cells_of_vertex[v]] = True
+    Si = S.astype(np.int64)
+    return (Si @ close.astype(np.int64) @ Si.T) > 0
 
 
 def load_vector(mesh: OracleMesh, s: float, f_nodal=None, dof_mode: str = "interior"):
