@@ -112,10 +112,37 @@ int fl_dof_vertices(fl_handle h, double s, int32_t* vertex_of_dof_host);
  * precision = FL_FP64 or FL_MIXED.  Deterministic: the same call on the same
  * device gives bitwise identical results (no floating-point atomics).
  * The handle owns a scratch workspace sized at the first call for this mesh.
+ * Scheduling: the near, touching and boundary stages run on a second stream owned
+ * by the handle (created at the first call), forked from and joined back into
+ * `stream` by events, concurrently with the far-field stage; to the caller the
+ * call behaves as work enqueued on `stream` alone, and it can be captured into a
+ * CUDA graph once a first call has created that stream.  With profiling on
+ * (fl_set_profiling) every stage runs on `stream`, one after another.
  * Errors: FL_EINVAL (s not in (0,1), lda < n, NULL A), FL_ENOTIMPL (2D with
  * FL_DOF_PAPER and s < 1/2 unless regional), FL_ENOMEM, FL_ECUDA.
  */
 int fl_assemble(fl_handle h, double s, int precision, double* A_dev, int64_t lda, void* stream);
+
+/*
+ * Sparse near-field part N of A^s in CSR form, A = N + F (Sections 5 and 6): F holds
+ * the off-diagonal blocks -C ∬ phi_i(x) phi_j(y) |x-y|^{-d-2s} of the separated
+ * element pairs at vertex-graph distance >= 2 (the far field, where the kernel is
+ * smooth); N holds everything else: touching pairs, separated pairs at distance 1,
+ * identical pairs, the boundary term and the diagonal-block terms of every separated
+ * pair.  Pattern: the (i, j) such that a cell of supp phi_i touches or lies at
+ * distance 1 from a cell of supp phi_j; symmetric, columns ascending in each row.
+ * Same quadrature, precision modes and determinism as fl_assemble (N_ij equals the
+ * value fl_assemble would give for A_ij with F left out).
+ * Two calls: with rowptr_dev == NULL only *nnz (host) is set, no device work; then
+ * rowptr_dev[n + 1] and col_dev[nnz] (int32, device) and val_dev[nnz] (float64,
+ * device), owned by the caller, are filled on `stream`.  The handle's workspace is
+ * the one fl_assemble uses.
+ * Errors: FL_EINVAL (s not in (0,1), NULL nnz, NULL col/val with rowptr_dev set),
+ * FL_ENOTIMPL, FL_ENOMEM, FL_ECUDA as for fl_assemble.
+ */
+int fl_assemble_nearfield_csr(fl_handle h, double s, int precision, int64_t* nnz,
+                              int32_t* rowptr_dev, int32_t* col_dev, double* val_dev,
+                              void* stream);
 
 /*
  * Load vector b = ∫ f phi_i (Section 5, system A u = b) into b_dev[n][ldb]
@@ -146,7 +173,9 @@ typedef struct fl_solve_opts {
                           float32 copy inside float64 iterative refinement */
     const void* A_lo_dev; /* the float32 copy (required when inner_dtype = FL_F32) */
     int64_t ld_lo;
-    double inner_tol;  /* relative tolerance of each inner solve (default 1e-4) */
+    double inner_tol;  /* relative tolerance of each inner solve (default 1e-4); a step
+                          whose residual is already within a factor 1/inner_tol of the
+                          target uses max(inner_tol, tol ||b|| / (2 ||b - A u||)) */
     int inner_maxit;   /* default 2000 */
 } fl_solve_opts;
 
@@ -468,7 +497,8 @@ int fl_get_stats(fl_handle h, double s, fl_stats* st);
 #define FL_NSTAGES       7
 
 /* enable = 1: record a CUDA event pair around every stage of each later fl_assemble
- * on its stream (events only, no synchronisation). */
+ * on its stream (events only, no synchronisation); the stages then run one after
+ * another on that stream, so each pair times one stage alone. */
 int fl_set_profiling(fl_handle h, int enable);
 
 /* Milliseconds of each stage of the last profiled fl_assemble (waits for its events). */

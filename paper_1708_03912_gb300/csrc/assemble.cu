@@ -1105,6 +1105,31 @@ __global__ void gather_csr_kernel(int64_t nnz, const int* csr_row, const int* cs
     val[z] = acc;
 }
 
+// Full symmetric values of the near-field CSR: an upper entry (col >= row) as gathered; a
+// lower entry (i, j), j < i, takes the value of (j, i), found by bisection among row j's
+// ascending columns (the pattern is symmetric, so it is there; NaN marks a broken pattern).
+__global__ void csr_full_values_kernel(int64_t nnz, const int* csr_ptr, const int* csr_row, const int* csr_col,
+                                       const double* val, double* out) {
+    const int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (z >= nnz) return;
+    const int i = csr_row[z], j = csr_col[z];
+    if (j >= i) {
+        out[z] = val[z];
+        return;
+    }
+    int lo = csr_ptr[j], hi = csr_ptr[j + 1] - 1;
+    if (lo > hi) {
+        out[z] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
+    while (lo < hi) {
+        const int mid = lo + (hi - lo) / 2;
+        if (csr_col[mid] < i) lo = mid + 1;
+        else hi = mid;
+    }
+    out[z] = csr_col[lo] == i ? val[lo] : __longlong_as_double(0x7ff8000000000000LL);
+}
+
 // A_ij = -C sum over the block occurrences (Ba, la) of DOF min(i, j) and (Bb, lb) of DOF
 // max(i, j) of the tile partial blocks, in occurrence order (a major, b minor), so A_ij and
 // A_ji are the same sum.  One block per 32 x 32 tile of the upper triangle (tile row
@@ -1661,12 +1686,22 @@ static double frac_constant(int d, double s) {
     return std::pow(2.0, 2 * s) * s * std::tgamma(s + d / 2.0) / (std::pow(pi, d / 2.0) * std::tgamma(1.0 - s));
 }
 
-int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStream_t st) {
+// Output of the near-field CSR route (caller's device arrays).
+struct CsrOut {
+    int32_t* rowptr;
+    int32_t* col;
+    double* val;
+};
+
+static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t lda, const CsrOut* csr,
+                         cudaStream_t st) {
     const int pi = plan_for(h, s);
     if (pi < 0) return FL_EINVAL;
     const Plan& P = h->plan[pi];
-    if (lda < P.n) return set_err(h, FL_EINVAL, "lda < n");
-    if (!A) return set_err(h, FL_EINVAL, "A is NULL");
+    if (!csr) {
+        if (lda < P.n) return set_err(h, FL_EINVAL, "lda < n");
+        if (!A) return set_err(h, FL_EINVAL, "A is NULL");
+    }
     if (precision != FL_FP64 && precision != FL_MIXED) return set_err(h, FL_EINVAL, "unknown precision");
     if (P.dim == 2 && P.paper_all && !h->opt.regional)
         return set_err(h, FL_ENOTIMPL, "2D boundary DOFs (FL_DOF_PAPER with s < 1/2) are not implemented");
@@ -1722,134 +1757,198 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
     }
     FL_CUDA_TRY(h, cudaGetLastError());
     stage_mark(h, st, FL_STAGE_PREP, 1);
-    // far field
+    // Two streams: the near, touching and boundary stages read only the tables and the far rule
+    // offsets and write their own buffers (contribution slots, Dn, Bf), so they run on the
+    // handle's second stream while the far-field stage runs here; their blocks fill the SMs the
+    // far kernel leaves idle (its last wave, spare registers).  The element kernel (which adds
+    // the far row sums) and the sparse gather follow on the second stream once the far stage is
+    // done, while the dense far-field compose runs here; the streams join before the sparse part
+    // is added.  With profiling on every stage runs on the caller's stream, one after another,
+    // so that each event pair brackets one stage alone.
+    cudaStream_t sst = st;
+    if (!h->profiling) {
+        if (!h->side && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) h->side = nullptr;
+        if (h->side && !h->ev_fork) {
+            if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_far, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+                if (h->ev_join) cudaEventDestroy(h->ev_join);
+                h->ev_fork = h->ev_join = h->ev_far = nullptr;
+            }
+        }
+        if (h->side && h->ev_fork && h->ev_join && h->ev_far) {
+            FL_CUDA_TRY(h, cudaEventRecord(h->ev_fork, st));
+            FL_CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+            sst = h->side;
+        }
+    }
+    // far field (launched first: it takes the SMs, the second stream's blocks fill in behind it)
     stage_mark(h, st, FL_STAGE_FAR, 0);
     // float32: keep only the one-MUFU forms (t^2, t^3); lg2 + ex2 beats rsqrt + sqrt here
     const int pw32 = (pw == 4 || pw == 6) ? pw : 0;
     if (f32) FL_TRY(launch_far<float>(h, P, t, rb, ro, expo, pw32, st));
     else FL_TRY(launch_far<double>(h, P, t, rb, ro, expo, pw, st));
     stage_mark(h, st, FL_STAGE_FAR, 1);
-    stage_mark(h, st, FL_STAGE_NEAR, 0);
-    // near separated pairs
-    const int nnear = (int)P.np_a.size();
-    const bool near_fast = (D == 2 && ro.qn == 36) || (D == 1 && ro.qn == 6);
-    if (nnear > 0 && near_fast) {
-        if (D == 2) {
-            if (f32) FL_TRY(launch_near_fast<2, float, 36>(h, P, t, rb, ro, expo, pw32, C, st));
-            else FL_TRY(launch_near_fast<2, double, 36>(h, P, t, rb, ro, expo, pw, C, st));
-        } else {
-            if (f32) FL_TRY(launch_near_fast<1, float, 6>(h, P, t, rb, ro, expo, pw32, C, st));
-            else FL_TRY(launch_near_fast<1, double, 6>(h, P, t, rb, ro, expo, pw, C, st));
-        }
-    } else if (nnear > 0) {
-        const unsigned g = (unsigned)((nnear + 63) / 64);
-#define FL_NEAR(DD, TT, PWV)                                                                                    \
-    near_pair_kernel<DD, TT, PWV><<<g, 64, 0, st>>>(nnear, t.np_a, t.np_b, t.cvx, t.cen, t.jac, t.rule, ro, (TT)expo, \
-                                                    C, t.contrib, P.np_slot0, t.Dn)
-        if (D == 2) {
-            if (f32) { if (pw == 6) FL_NEAR(2, float, 6); else FL_NEAR(2, float, 0); }
-            else { if (pw == 5) FL_NEAR(2, double, 5); else if (pw == 6) FL_NEAR(2, double, 6); else if (pw == 7) FL_NEAR(2, double, 7); else FL_NEAR(2, double, 0); }
-        } else {
-            if (f32) { if (pw == 4) FL_NEAR(1, float, 4); else FL_NEAR(1, float, 0); }
-            else { if (pw == 3) FL_NEAR(1, double, 3); else if (pw == 4) FL_NEAR(1, double, 4); else if (pw == 5) FL_NEAR(1, double, 5); else FL_NEAR(1, double, 0); }
-        }
-#undef FL_NEAR
-        fl::count_launch();
-        FL_CUDA_TRY(h, cudaGetLastError());
-    }
-    stage_mark(h, st, FL_STAGE_NEAR, 1);
-    // touching pairs (float64; float32 in the mixed mode)
-    stage_mark(h, st, FL_STAGE_TOUCH, 0);
-    const int ntp = (int)P.tp_type.size();
-    if (ntp > 0) {
-        const unsigned g = (unsigned)(((int64_t)ntp * 32 + 127) / 128);  // one warp per pair
-#define FL_TOUCH(TT, RULE, PWV) \
-    touch_pair_kernel<TT, PWV><<<g, 128, 0, st>>>(ntp, D, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, RULE, ro, s, C, t.contrib)
-        if (f32) {
-            if (D == 2 && pw == 6) FL_TOUCH(float, t.rule32, 6);
-            else FL_TOUCH(float, t.rule32, 0);
-        } else if (D == 2 && pw == 5) FL_TOUCH(double, t.rule, 5);
-        else if (D == 2 && pw == 6) FL_TOUCH(double, t.rule, 6);
-        else if (D == 2 && pw == 7) FL_TOUCH(double, t.rule, 7);
-        else FL_TOUCH(double, t.rule, 0);
-#undef FL_TOUCH
-        fl::count_launch();
-        FL_CUDA_TRY(h, cudaGetLastError());
-    }
-    stage_mark(h, st, FL_STAGE_TOUCH, 1);
-    // boundary term over far facets (2D)
-    stage_mark(h, st, FL_STAGE_BND, 0);
-    if (D == 2 && !h->opt.regional && P.nf > 0) {
-        if (f32) FL_TRY(launch_bnd<float>(h, P, t, ro, expo, pw32, st));
-        else FL_TRY(launch_bnd<double>(h, P, t, ro, expo, pw, st));
-    }
-    stage_mark(h, st, FL_STAGE_BND, 1);
-    // per element
-    stage_mark(h, st, FL_STAGE_ELEMENT, 0);
-    {
-        ElemArgs E;
-        E.dim = D;
-        E.nc = nc;
-        E.nblk = P.nblk;
-        E.nf = P.nf;
-        E.nnear = nnear;
-        E.cvx = t.cvx;
-        E.cen = t.cen;
-        E.jac = t.jac;
-        E.hasdof = t.hasdof;
-        E.Pd = t.Pd;
-        E.pd_is_float = f32 ? 1 : 0;
-        E.Dn = t.Dn;
-        E.enp_ptr = t.enp_ptr;
-        E.enp_ent = t.enp_ent;
-        E.Bf = t.Bf;
-        E.ef_ptr = t.ef_ptr;
-        E.ef_fac = t.ef_fac;
-        E.ef_cls = t.ef_cls;
-        E.F = t.F;
-        E.FN = t.FN;
-        E.FLEN = t.FLEN;
-        E.V = t.V;
-        E.corner = t.corig;
-        E.rule = t.rule;
-        E.C2s = C / (2.0 * s);
-        E.r2s = 1.0 / (2.0 - 2.0 * s);
-        E.r3s = 1.0 / (3.0 - 2.0 * s);
-        E.r4s = 1.0 / (4.0 - 2.0 * s);
-        E.rule32 = f32 ? t.rule32 : nullptr;
-        E.ro = ro;
-        E.s = s;
-        E.C = C;
-        E.regional = h->opt.regional;
-        E.contrib = t.contrib;
-        E.slot0 = P.el_slot0;
-        const unsigned ge = (unsigned)((nc * 32 + 127) / 128);  // one warp per cell
-        if (D == 2 && pw == 5) { element_kernel<5><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
-        else if (D == 2 && pw == 6) { element_kernel<6><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
-        else if (D == 2 && pw == 7) { element_kernel<7><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
-        else { element_kernel<0><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
-        FL_CUDA_TRY(h, cudaGetLastError());
-    }
-    stage_mark(h, st, FL_STAGE_ELEMENT, 1);
-    // sparse near-field values, then the dense matrix
-    stage_mark(h, st, FL_STAGE_COMPOSE, 0);
+    int side_rc = FL_OK;
     const int64_t nnz = (int64_t)P.csr_col.size();
-    if (nnz > 0) {
-        gather_csr_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, t.csr_row, t.csr_col, t.g_ptr, t.g_slot,
-                                                                         t.contrib, t.csr_val); fl::count_launch();
-        FL_CUDA_TRY(h, cudaGetLastError());
-    }
     {
-        const int64_t nt = (P.n + 31) / 32;
-        const unsigned grid = (unsigned)(nt * (nt + 1) / 2);  // upper-triangle 32 x 32 tiles
-        if (f32)
-            compose_far_kernel<float><<<grid, 256, 0, st>>>(P.n, P.nblk, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr, t.toff,
-                                                            (const float*)t.P, -C, A, lda);
-        else
-            compose_far_kernel<double><<<grid, 256, 0, st>>>(P.n, P.nblk, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr, t.toff,
-                                                             (const double*)t.P, -C, A, lda);
-        fl::count_launch();
-        FL_CUDA_TRY(h, cudaGetLastError());
+        // the stages of the second stream; on an error the join below still runs, so that the
+        // caller's stream never runs ahead of work left on the second stream
+        const cudaStream_t h_st = st;
+        auto run_side = [&]() -> int {
+            const cudaStream_t st = sst;
+            stage_mark(h, st, FL_STAGE_NEAR, 0);
+            // near separated pairs
+            const int nnear = (int)P.np_a.size();
+            const bool near_fast = (D == 2 && ro.qn == 36) || (D == 1 && ro.qn == 6);
+            if (nnear > 0 && near_fast) {
+                if (D == 2) {
+                    if (f32) FL_TRY(launch_near_fast<2, float, 36>(h, P, t, rb, ro, expo, pw32, C, st));
+                    else FL_TRY(launch_near_fast<2, double, 36>(h, P, t, rb, ro, expo, pw, C, st));
+                } else {
+                    if (f32) FL_TRY(launch_near_fast<1, float, 6>(h, P, t, rb, ro, expo, pw32, C, st));
+                    else FL_TRY(launch_near_fast<1, double, 6>(h, P, t, rb, ro, expo, pw, C, st));
+                }
+            } else if (nnear > 0) {
+                const unsigned g = (unsigned)((nnear + 63) / 64);
+#define FL_NEAR(DD, TT, PWV)                                                                                    \
+            near_pair_kernel<DD, TT, PWV><<<g, 64, 0, st>>>(nnear, t.np_a, t.np_b, t.cvx, t.cen, t.jac, t.rule, ro, (TT)expo, \
+                                                            C, t.contrib, P.np_slot0, t.Dn)
+                if (D == 2) {
+                    if (f32) { if (pw == 6) FL_NEAR(2, float, 6); else FL_NEAR(2, float, 0); }
+                    else { if (pw == 5) FL_NEAR(2, double, 5); else if (pw == 6) FL_NEAR(2, double, 6); else if (pw == 7) FL_NEAR(2, double, 7); else FL_NEAR(2, double, 0); }
+                } else {
+                    if (f32) { if (pw == 4) FL_NEAR(1, float, 4); else FL_NEAR(1, float, 0); }
+                    else { if (pw == 3) FL_NEAR(1, double, 3); else if (pw == 4) FL_NEAR(1, double, 4); else if (pw == 5) FL_NEAR(1, double, 5); else FL_NEAR(1, double, 0); }
+                }
+#undef FL_NEAR
+                fl::count_launch();
+                FL_CUDA_TRY(h, cudaGetLastError());
+            }
+            stage_mark(h, st, FL_STAGE_NEAR, 1);
+            // touching pairs (float64; float32 in the mixed mode)
+            stage_mark(h, st, FL_STAGE_TOUCH, 0);
+            const int ntp = (int)P.tp_type.size();
+            if (ntp > 0) {
+                const unsigned g = (unsigned)(((int64_t)ntp * 32 + 127) / 128);  // one warp per pair
+#define FL_TOUCH(TT, RULE, PWV) \
+            touch_pair_kernel<TT, PWV><<<g, 128, 0, st>>>(ntp, D, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, RULE, ro, s, C, t.contrib)
+                if (f32) {
+                    if (D == 2 && pw == 6) FL_TOUCH(float, t.rule32, 6);
+                    else FL_TOUCH(float, t.rule32, 0);
+                } else if (D == 2 && pw == 5) FL_TOUCH(double, t.rule, 5);
+                else if (D == 2 && pw == 6) FL_TOUCH(double, t.rule, 6);
+                else if (D == 2 && pw == 7) FL_TOUCH(double, t.rule, 7);
+                else FL_TOUCH(double, t.rule, 0);
+#undef FL_TOUCH
+                fl::count_launch();
+                FL_CUDA_TRY(h, cudaGetLastError());
+            }
+            stage_mark(h, st, FL_STAGE_TOUCH, 1);
+            // boundary term over far facets (2D)
+            stage_mark(h, st, FL_STAGE_BND, 0);
+            if (D == 2 && !h->opt.regional && P.nf > 0) {
+                if (f32) FL_TRY(launch_bnd<float>(h, P, t, ro, expo, pw32, st));
+                else FL_TRY(launch_bnd<double>(h, P, t, ro, expo, pw, st));
+            }
+            stage_mark(h, st, FL_STAGE_BND, 1);
+            // the element kernel adds the far field's per-point row sums: wait for the far stage
+            if (sst != h_st) {
+                FL_CUDA_TRY(h, cudaEventRecord(h->ev_far, h_st));
+                FL_CUDA_TRY(h, cudaStreamWaitEvent(sst, h->ev_far, 0));
+            }
+            // per element
+            stage_mark(h, st, FL_STAGE_ELEMENT, 0);
+            {
+                ElemArgs E;
+                E.dim = D;
+                E.nc = nc;
+                E.nblk = P.nblk;
+                E.nf = P.nf;
+                E.nnear = nnear;
+                E.cvx = t.cvx;
+                E.cen = t.cen;
+                E.jac = t.jac;
+                E.hasdof = t.hasdof;
+                E.Pd = t.Pd;
+                E.pd_is_float = f32 ? 1 : 0;
+                E.Dn = t.Dn;
+                E.enp_ptr = t.enp_ptr;
+                E.enp_ent = t.enp_ent;
+                E.Bf = t.Bf;
+                E.ef_ptr = t.ef_ptr;
+                E.ef_fac = t.ef_fac;
+                E.ef_cls = t.ef_cls;
+                E.F = t.F;
+                E.FN = t.FN;
+                E.FLEN = t.FLEN;
+                E.V = t.V;
+                E.corner = t.corig;
+                E.rule = t.rule;
+                E.C2s = C / (2.0 * s);
+                E.r2s = 1.0 / (2.0 - 2.0 * s);
+                E.r3s = 1.0 / (3.0 - 2.0 * s);
+                E.r4s = 1.0 / (4.0 - 2.0 * s);
+                E.rule32 = f32 ? t.rule32 : nullptr;
+                E.ro = ro;
+                E.s = s;
+                E.C = C;
+                E.regional = h->opt.regional;
+                E.contrib = t.contrib;
+                E.slot0 = P.el_slot0;
+                const unsigned ge = (unsigned)((nc * 32 + 127) / 128);  // one warp per cell
+                if (D == 2 && pw == 5) { element_kernel<5><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+                else if (D == 2 && pw == 6) { element_kernel<6><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+                else if (D == 2 && pw == 7) { element_kernel<7><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+                else { element_kernel<0><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+                FL_CUDA_TRY(h, cudaGetLastError());
+            }
+            stage_mark(h, st, FL_STAGE_ELEMENT, 1);
+            // sparse near-field values
+            stage_mark(h, st, FL_STAGE_COMPOSE, 0);
+            if (nnz > 0) {
+                gather_csr_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, t.csr_row, t.csr_col, t.g_ptr,
+                                                                                 t.g_slot, t.contrib, t.csr_val);
+                fl::count_launch();
+                FL_CUDA_TRY(h, cudaGetLastError());
+            }
+            return FL_OK;
+        };
+        // the dense far-field part reads only the far stage's partial tiles: it runs here while the
+        // element and gather kernels run on the second stream
+        auto run_compose = [&]() -> int {
+            const int64_t nt = (P.n + 31) / 32;
+            const unsigned grid = (unsigned)(nt * (nt + 1) / 2);  // upper-triangle 32 x 32 tiles
+            if (f32)
+                compose_far_kernel<float><<<grid, 256, 0, st>>>(P.n, P.nblk, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr,
+                                                                t.toff, (const float*)t.P, -C, A, lda);
+            else
+                compose_far_kernel<double><<<grid, 256, 0, st>>>(P.n, P.nblk, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr,
+                                                                 t.toff, (const double*)t.P, -C, A, lda);
+            fl::count_launch();
+            FL_CUDA_TRY(h, cudaGetLastError());
+            return FL_OK;
+        };
+        side_rc = run_side();
+        if (side_rc == FL_OK && !csr) side_rc = run_compose();
+        if (sst != st) {
+            FL_CUDA_TRY(h, cudaEventRecord(h->ev_join, sst));
+            FL_CUDA_TRY(h, cudaStreamWaitEvent(st, h->ev_join, 0));
+        }
+    }
+    if (side_rc != FL_OK) return side_rc;
+    if (csr) {  // the near-field part alone: pattern and full symmetric values
+        if (nnz > 0) {
+            csr_full_values_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, t.csr_ptr, t.csr_row, t.csr_col,
+                                                                                t.csr_val, csr->val); fl::count_launch();
+            FL_CUDA_TRY(h, cudaGetLastError());
+            FL_CUDA_TRY(h, cudaMemcpyAsync(csr->col, t.csr_col, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        }
+        FL_CUDA_TRY(h, cudaMemcpyAsync(csr->rowptr, t.csr_ptr, (P.n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        stage_mark(h, st, FL_STAGE_COMPOSE, 1);
+        return FL_OK;
     }
     if (nnz > 0) {
         add_csr_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, t.csr_row, t.csr_col, t.csr_val, A, lda); fl::count_launch();
@@ -1857,6 +1956,24 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
     }
     stage_mark(h, st, FL_STAGE_COMPOSE, 1);
     return FL_OK;
+}
+
+int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStream_t st) {
+    return assemble_impl(h, s, precision, A, lda, nullptr, st);
+}
+
+int assemble_nearfield_csr(fl_ctx* h, double s, int precision, int64_t* nnz, int32_t* rowptr, int32_t* col,
+                           double* val, cudaStream_t st) {
+    if (!nnz) return set_err(h, FL_EINVAL, "nnz is NULL");
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    const int64_t nz = (int64_t)P.csr_col.size();
+    *nnz = nz;
+    if (!rowptr) return FL_OK;  // size query
+    if (!col || !val) return set_err(h, FL_EINVAL, "col or val is NULL");
+    const CsrOut out{rowptr, col, val};
+    return assemble_impl(h, s, precision, nullptr, 0, &out, st);
 }
 
 // ----------------------------------------------------------- load vector --

@@ -9,6 +9,8 @@
 
 namespace fl {
 int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStream_t st);
+int assemble_nearfield_csr(fl_ctx* h, double s, int precision, int64_t* nnz, int32_t* rowptr, int32_t* col,
+                           double* val, cudaStream_t st);
 int load_vector(fl_ctx* h, double s, const double* f, int nrhs, double* b, int64_t ldb, cudaStream_t st);
 
 int plan_for(fl_ctx* h, double s) {
@@ -123,6 +125,14 @@ void fl_destroy(fl_handle h) {
     }
     for (auto& g : h->cg_graphs) cudaGraphExecDestroy(g.exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->side) {
+        cudaSetDevice(h->device);
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_far) cudaEventDestroy(h->ev_far);
     delete h;
 }
 
@@ -150,6 +160,17 @@ int fl_assemble(fl_handle h, double s, int precision, double* A_dev, int64_t lda
     h->err.clear();
     try {
         return fl::assemble(h, s, precision, A_dev, lda, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        return fl::set_err(h, FL_ENOMEM, "out of host memory");
+    }
+}
+
+int fl_assemble_nearfield_csr(fl_handle h, double s, int precision, int64_t* nnz, int32_t* rowptr_dev,
+                              int32_t* col_dev, double* val_dev, void* stream) {
+    if (!h) return FL_EINVAL;
+    h->err.clear();
+    try {
+        return fl::assemble_nearfield_csr(h, s, precision, nnz, rowptr_dev, col_dev, val_dev, (cudaStream_t)stream);
     } catch (const std::bad_alloc&) {
         return fl::set_err(h, FL_ENOMEM, "out of host memory");
     }

@@ -117,6 +117,10 @@ struct fl_ctx {
     int64_t ws_bytes = 0;
     std::vector<fl::CgGraph> cg_graphs;   // captured CG batches, keyed by their pointers
     cudaStream_t cap_stream = nullptr;    // stream used only for graph capture
+    // second stream of fl_assemble: the near, touching and boundary stages run on it while the
+    // far-field stage runs on the caller's stream (fork/join by the two events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr;
     void* solve_ws = nullptr;     // solver workspace (device), grown on demand
     void* solve_host = nullptr;   // pinned scalars read back by the solver
     size_t solve_ws_bytes = 0;

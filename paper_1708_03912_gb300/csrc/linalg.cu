@@ -1016,7 +1016,11 @@ __global__ void __launch_bounds__(PCG_THREADS, 1)
         rr_prev = rr;
         int it = 0, breakdown = 0;
         float irr = 0.f, irr0 = 0.f;
-        if (!pipe_block_solve<MODE>(c, v, r64, inner_tol, inner_maxit, epoch, it, breakdown, irr, irr0)) return;
+        // the correction is solved no further than the outer test needs: a reduction by
+        // tol ||b|| / ||r|| brings the residual to the target, half of it leaves a margin
+        // for the float32 recurrences (every block has the same rr and bb)
+        const double step_tol = fmax(inner_tol, 0.5 * tol * sqrt(bb / rr));
+        if (!pipe_block_solve<MODE>(c, v, r64, step_tol, inner_maxit, epoch, it, breakdown, irr, irr0)) return;
         inner += it;
         if (breakdown) {
             status = 2;
@@ -1393,7 +1397,9 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
             }
             int its = 0;
             double irel = 0;
-            int ir = pcg(h, w, n, o.inner_dtype, o.A_lo_dev, o.ld_lo, w.dinv_lo, rvec, w.d, o.inner_tol,
+            // the last correction needs only a reduction by tol / rel (half of it as a margin)
+            const double step_tol = std::max(o.inner_tol, 0.5 * o.tol / rel);
+            int ir = pcg(h, w, n, o.inner_dtype, o.A_lo_dev, o.ld_lo, w.dinv_lo, rvec, w.d, step_tol,
                          o.inner_maxit, &its, &irel, st);
             total += its;
             if (ir == FL_ENOTSPD || ir == FL_ECUDA) {

@@ -23,7 +23,7 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
           6: "FL_ETIMEOUT", 7: "FL_ENOTIMPL"}
 
 EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
-           "fl_assemble", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
+           "fl_assemble", "fl_assemble_nearfield_csr", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
            "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
            "fl_matvec_f32_static",
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
@@ -116,6 +116,8 @@ def lib():
     L.fl_dof_vertices.restype = ci
     L.fl_assemble.argtypes = [vp, dbl, ci, vp, i64, vp]
     L.fl_assemble.restype = ci
+    L.fl_assemble_nearfield_csr.argtypes = [vp, dbl, ci, ctypes.POINTER(i64), vp, vp, vp, vp]
+    L.fl_assemble_nearfield_csr.restype = ci
     L.fl_load_vector.argtypes = [vp, dbl, vp, ci, vp, i64, vp]
     L.fl_load_vector.restype = ci
     L.fl_matvec.argtypes = [ci, vp, i64, i64, ci, vp, i64, vp, i64, vp]
@@ -285,6 +287,22 @@ def fl_assemble(h, s, precision, A, stream=None):
     """A: float64 CUDA tensor [n, lda] (row-major, contiguous rows)."""
     assert A.dtype.is_floating_point and A.element_size() == 8 and A.is_cuda and A.stride(1) == 1
     _check(lib().fl_assemble(h, s, precision, _ptr(A), A.stride(0), _stream(stream)), h)
+
+
+def fl_assemble_nearfield_csr(h, s, precision, stream=None):
+    """(rowptr int32 [n+1], col int32 [nnz], val float64 [nnz]) device tensors of the
+    near-field part N of A = N + F."""
+    import torch
+
+    nnz = ctypes.c_int64(0)
+    _check(lib().fl_assemble_nearfield_csr(h, s, precision, ctypes.byref(nnz), None, None, None, _stream(stream)), h)
+    n = fl_num_dofs(h, s)
+    rowptr = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    col = torch.empty(max(1, nnz.value), dtype=torch.int32, device="cuda")
+    val = torch.empty(max(1, nnz.value), dtype=torch.float64, device="cuda")
+    _check(lib().fl_assemble_nearfield_csr(h, s, precision, ctypes.byref(nnz), _ptr(rowptr), _ptr(col), _ptr(val),
+                                           _stream(stream)), h)
+    return rowptr, col[:nnz.value], val[:nnz.value]
 
 
 def fl_load_vector(h, s, f_nodal, b, stream=None):
@@ -682,6 +700,9 @@ class Mesh:
 
     def dof_vertices(self, s):
         return fl_dof_vertices(self.h, s)
+
+    def nearfield_csr(self, s, precision="fp64", stream=None):
+        return fl_assemble_nearfield_csr(self.h, s, FL_MIXED if precision == "mixed" else FL_FP64, stream)
 
     def assemble(self, s, precision="fp64", out=None, stream=None):
         import torch

@@ -121,3 +121,21 @@ def test_pool_stats_without_device_work():
     st = F.fl_pool_stats()
     assert st["cached_device_bytes"] == 0 and st["cached_host_bytes"] == 0
     assert F.fl_pool_trim() == 0
+
+
+def test_nearfield_csr_size_query_matches_oracle_pattern():
+    # the size query of fl_assemble_nearfield_csr is host work only (planner); its nonzero
+    # count equals the oracle's combinatorial near-field pattern
+    _lib_or_skip()
+    import ctypes
+
+    from oracle.assemble import nearfield_pattern
+
+    for (V, T), s in ((synth.disc(4), 0.6), (synth.interval(20), 0.3), (synth.lshape(0.25, 0), 0.5)):
+        h = F.fl_create(V, T)
+        nnz = ctypes.c_int64(-1)
+        assert F.lib().fl_assemble_nearfield_csr(h, s, F.FL_FP64, ctypes.byref(nnz), None, None, None, None) == F.FL_OK
+        assert nnz.value == int(nearfield_pattern(OracleMesh(V, T), s).sum())
+        assert nnz.value == F.fl_get_stats(h, s)["nnz_nearfield"]
+        assert F.lib().fl_assemble_nearfield_csr(h, s, F.FL_FP64, None, None, None, None, None) == F.FL_EINVAL
+        F.fl_destroy(h)

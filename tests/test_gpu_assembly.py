@@ -105,6 +105,69 @@ def test_deterministic_and_symmetric():
     m.close()
 
 
+def test_concurrent_stages_match_serial_schedule():
+    # without profiling the near / touching / boundary stages run on the handle's second stream,
+    # concurrently with the far-field stage; with profiling every stage runs on the caller's
+    # stream in turn.  Both schedules, and a CUDA graph captured from the concurrent one on a
+    # side stream of the caller, give the same bits.
+    V, T = synth.disc(10)
+    m = F.Mesh(V, T)
+    for prec in ("fp64", "mixed"):
+        A_conc = m.assemble(0.75, prec).clone()
+        F.fl_set_profiling(m.h, True)
+        A_ser = m.assemble(0.75, prec).clone()
+        F.fl_set_profiling(m.h, False)
+        assert torch.equal(A_conc, A_ser)
+        A_g = torch.full_like(A_conc, float("nan"))
+        cap = torch.cuda.Stream()
+        cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cap):
+            m.assemble(0.75, prec, out=A_g)  # warm (tables already resident)
+            g = torch.cuda.CUDAGraph()
+            A_g.fill_(float("nan"))
+            with torch.cuda.graph(g, stream=cap):
+                m.assemble(0.75, prec, out=A_g)
+        torch.cuda.current_stream().wait_stream(cap)
+        A_g.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(A_g, A_conc)
+    m.close()
+
+
+@pytest.mark.parametrize("case", ["disc", "interval", "lshape"])
+def test_nearfield_csr_parity(case):
+    # N of A = N + F (far off-diagonal blocks left out) as CSR, against the oracle's N:
+    # same pattern (bit-exact), values within the float64 parity tolerance; the mixed mode
+    # within its stated bound
+    from oracle.assemble import nearfield_pattern
+
+    (V, T), s = {"disc": (synth.disc(10), 0.75), "interval": (synth.graded_interval(70, 2.0), 0.4),
+                 "lshape": (synth.lshape(0.25, 0), 0.5)}[case]
+    om = OracleMesh(V, T)
+    No, _ = assemble_matrix(om, s, far_offdiag=False)
+    pat = nearfield_pattern(om, s)
+    d = np.sqrt(np.outer(np.diag(No), np.diag(No)))
+    m = F.Mesh(V, T)
+    for prec, tol in (("fp64", TOL64), ("mixed", 2e-5)):
+        rowptr, col, val = m.nearfield_csr(s, prec)
+        torch.cuda.synchronize()
+        rp, cl, vl = rowptr.cpu().numpy(), col.cpu().numpy(), val.cpu().numpy()
+        n = len(rp) - 1
+        assert n == No.shape[0] and rp[0] == 0 and rp[-1] == len(cl)
+        G = np.zeros_like(No)
+        Gp = np.zeros(No.shape, dtype=bool)
+        for i in range(n):
+            cols = cl[rp[i]:rp[i + 1]]
+            assert np.all(np.diff(cols) > 0)  # ascending, no duplicates
+            G[i, cols] = vl[rp[i]:rp[i + 1]]
+            Gp[i, cols] = True
+        assert np.array_equal(Gp, pat)
+        assert np.array_equal(G, G.T)  # symmetric values
+        assert float(np.max(np.abs(G - No) / d)) < tol, prec
+    m.close()
+
+
 def test_edge_cases():
     # one DOF in 1D, a single interior vertex in 2D, s close to 0 and 1
     V, T = synth.interval(2)
