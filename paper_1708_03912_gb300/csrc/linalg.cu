@@ -152,6 +152,96 @@ __global__ void gemv_lo_kernel(int64_t n, const TA* __restrict__ A, int64_t lda,
     if (lane == 0) y[row * incy] = t;
 }
 
+// The same products with x staged in shared memory once per block: blocks of 8 warps
+// loop over rows (row = block * 8 + warp, stride grid * 8), so x is read from L2 once per
+// block instead of once per row, and eight 16-byte loads of A per lane are in flight.
+// TX is the type of the staged x (float for float32 / bfloat16 A, double for float64 A).
+template <typename Acc, typename TA>
+__device__ __forceinline__ Acc to_acc(TA v) {
+    if constexpr (std::is_same<TA, __nv_bfloat16>::value) return (Acc)__bfloat162float(v);
+    else return (Acc)v;
+}
+
+constexpr int GEMV_SMEM_WARPS = 8;
+constexpr size_t GEMV_SMEM_MAX = 200 * 1024;  // bytes of staged x
+
+template <typename TA, typename TX>
+__global__ void __launch_bounds__(32 * GEMV_SMEM_WARPS, 4)
+    gemv_smem_kernel(int64_t n, const TA* __restrict__ A, int64_t lda, const double* __restrict__ x, int64_t incx,
+                     const float* __restrict__ xf, double* __restrict__ y, int64_t incy) {
+    constexpr int V = Vec16<TA>::N;
+    constexpr bool F64 = sizeof(TX) == 8;
+    using Acc = typename std::conditional<F64, double, float>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TX* xs = reinterpret_cast<TX*>(smem_raw);
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        if constexpr (F64) xs[i] = x[i * incx];
+        else xs[i] = xf[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t row = (int64_t)blockIdx.x * GEMV_SMEM_WARPS + warp; row < n; row += (int64_t)gridDim.x * GEMV_SMEM_WARPS) {
+        const TA* a = A + row * lda;
+        Acc acc0 = 0, acc1 = 0;
+        // peel to the first 16-byte boundary of the row
+        const int mis = (int)(((uintptr_t)a & 15u) / sizeof(TA));
+        const int64_t p0 = min((int64_t)(mis ? V - mis : 0), n);
+        if (lane < p0) acc0 = fma(to_acc<Acc>(a[lane]), (Acc)xs[lane], acc0);
+        const int64_t m = n - p0;
+        const int64_t nv = (m / (32 * V)) * (32 * V);
+        const uint4* a4 = reinterpret_cast<const uint4*>(a + p0);
+        const TX* xr = xs + p0;
+#pragma unroll 8
+        for (int64_t j = lane; j < nv / V; j += 32) {
+            const uint4 u = __ldcs(a4 + j);
+            if constexpr (F64) {
+                acc0 = fma(__longlong_as_double(((long long)u.y << 32) | u.x), (double)xr[j * 2], acc0);
+                acc1 = fma(__longlong_as_double(((long long)u.w << 32) | u.z), (double)xr[j * 2 + 1], acc1);
+            } else {
+                float av[V];
+                unpack16<TA>(u, av);
+#pragma unroll
+                for (int q = 0; q < V; q += 2) {
+                    acc0 = fmaf(av[q], (float)xr[j * V + q], acc0);
+                    acc1 = fmaf(av[q + 1], (float)xr[j * V + q + 1], acc1);
+                }
+            }
+        }
+        for (int64_t j = p0 + nv + lane; j < n; j += 32) acc0 = fma(to_acc<Acc>(a[j]), (Acc)xs[j], acc0);
+        const double t = warp_sum((double)acc0 + (double)acc1);
+        if (lane == 0) y[row * incy] = t;
+    }
+}
+
+// grid of the shared-memory product: as many blocks as fit on the device at once (or one per
+// 8 rows); 0 when x does not fit
+template <typename TA, typename TX>
+static unsigned gemv_smem_grid(int64_t n) {
+    const size_t smem = (size_t)n * sizeof(TX);
+    if (smem > GEMV_SMEM_MAX) return 0;
+    static int ready = 0, sms = 0, dev_cached = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (!ready || dev != dev_cached) {
+        if (cudaFuncSetAttribute(gemv_smem_kernel<TA, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)GEMV_SMEM_MAX) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        ready = 1;
+        dev_cached = dev;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemv_smem_kernel<TA, TX>, 32 * GEMV_SMEM_WARPS,
+                                                      smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int64_t want = (n + GEMV_SMEM_WARPS - 1) / GEMV_SMEM_WARPS;
+    return (unsigned)std::min<int64_t>(want, (int64_t)sms * per_sm);
+}
+
 __global__ void to_f32_kernel(int64_t n, const double* x, int64_t incx, float* y) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) y[i] = (float)x[i * incx];
@@ -174,10 +264,29 @@ cudaError_t gemv(int dtype, const void* A, int64_t lda, int64_t n, const double*
                  int64_t incy, float* xf, cudaStream_t st, bool xf_ready) {
     const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
     if (dtype == FL_F64) {
+        const unsigned gs = (((uintptr_t)A & 7u) == 0) ? gemv_smem_grid<double, double>(n) : 0u;
+        if (gs) {
+            gemv_smem_kernel<double, double><<<gs, 32 * GEMV_SMEM_WARPS, n * sizeof(double), st>>>(
+                n, (const double*)A, lda, x, incx, nullptr, y, incy);
+            fl::count_launch();
+            return cudaGetLastError();
+        }
         const int vec = (((uintptr_t)A & 7u) == 0) && aligned16(x);
         gemv_f64_kernel<<<blocks, 256, 0, st>>>(n, (const double*)A, lda, x, incx, y, incy, vec); fl::count_launch();
     } else {
         if (!xf_ready) { to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, incx, xf); fl::count_launch(); }
+        const unsigned gs = dtype == FL_F32 ? ((((uintptr_t)A & 3u) == 0) ? gemv_smem_grid<float, float>(n) : 0u)
+                                            : ((((uintptr_t)A & 1u) == 0) ? gemv_smem_grid<__nv_bfloat16, float>(n) : 0u);
+        if (gs) {
+            if (dtype == FL_F32)
+                gemv_smem_kernel<float, float><<<gs, 32 * GEMV_SMEM_WARPS, n * sizeof(float), st>>>(
+                    n, (const float*)A, lda, nullptr, 0, xf, y, incy);
+            else
+                gemv_smem_kernel<__nv_bfloat16, float><<<gs, 32 * GEMV_SMEM_WARPS, n * sizeof(float), st>>>(
+                    n, (const __nv_bfloat16*)A, lda, nullptr, 0, xf, y, incy);
+            fl::count_launch();
+            return cudaGetLastError();
+        }
         if (dtype == FL_F32) {
             const int vec = (((uintptr_t)A & 3u) == 0) && aligned16(xf);
             gemv_lo_kernel<float><<<blocks, 256, 0, st>>>(n, (const float*)A, lda, xf, y, incy, vec); fl::count_launch();

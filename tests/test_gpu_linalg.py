@@ -33,6 +33,28 @@ def test_matvec_dtypes():
             assert np.allclose(Y.cpu().numpy(), ref, rtol=tol, atol=tol * np.sqrt(n))
 
 
+def test_matvec_padded_rows():
+    # leading dimension larger than n: 16-byte aligned rows (lda % 4 == 0) and rows whose
+    # starts drift across the 16-byte boundary (odd lda), every storage type
+    g = torch.Generator(device="cpu").manual_seed(6)
+    n = 777
+    for lda in (780, 781):
+        Af = torch.randn(n, lda, generator=g, dtype=torch.float64).cuda()
+        A = Af[:, :n]
+        X = torch.randn(n, 2, generator=g, dtype=torch.float64).cuda()
+        Y = torch.empty(n, 2, dtype=torch.float64, device="cuda")
+        F.fl_matvec(F.FL_F64, A, X, Y)
+        ref = (A.cpu() @ X.cpu()).numpy()
+        assert np.allclose(Y.cpu().numpy(), ref, rtol=1e-13, atol=1e-12 * np.sqrt(n))
+        for dt, tdt, tol in ((F.FL_F32, torch.float32, 1e-5), (F.FL_BF16, torch.bfloat16, 2e-2)):
+            Alf = torch.zeros(n, lda, dtype=tdt, device="cuda")
+            Al = Alf[:, :n]
+            F.fl_convert(A, dt, Al)
+            F.fl_matvec(dt, Al, X, Y)
+            ref = (Al.double().cpu() @ X.float().double().cpu()).numpy()
+            assert np.allclose(Y.cpu().numpy(), ref, rtol=tol, atol=tol * np.sqrt(n))
+
+
 def test_pcg_matches_cholesky_1d_closed_form():
     s = 0.25
     V, T = synth.interval(128)
