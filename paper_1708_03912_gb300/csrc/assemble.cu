@@ -827,12 +827,14 @@ __device__ __forceinline__ double facet_pow(double r2, double e, bool f32) {
     return kpow<PW>(r2, e);
 }
 
-template <int PW>
+// The block blk (upper triangle, 6 values in 2D) stays in registers: the dimension is a
+// template parameter and every update of it uses a compile-time index.
+template <int PW, int D>
 __global__ void element_kernel(ElemArgs A) {
+    constexpr int NV = D + 1;
     const int lane = threadIdx.x & 31;
     const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (k >= A.nc || !A.hasdof[k]) return;
-    const int D = A.dim, NV = D + 1;
     const RuleOffsets& ro = A.ro;
     const double* rule = A.rule;
     const double s = A.s, C = A.C;
@@ -885,7 +887,9 @@ __global__ void element_kernel(ElemArgs A) {
             if (hb == 0 && a < qf) {
                 const double bf = (D == 2 && !A.regional) ? A.Bf[k * qf + a] : 0.0;
                 const double f = jk * w[a] * (C * Dk + A.C2s * bf);
+#pragma unroll
                 for (int i = 0; i < NV; ++i)
+#pragma unroll
                     for (int j = i; j < NV; ++j) blk[tri_index(i, j, NV)] += f * phi[a * NV + i] * phi[a * NV + j];
             }
         }
@@ -935,7 +939,9 @@ __global__ void element_kernel(ElemArgs A) {
                 }
             }
             const double f = jk * w[a] * (C * Dk + A.C2s * Bn);
+#pragma unroll
             for (int i = 0; i < NV; ++i)
+#pragma unroll
                 for (int j = i; j < NV; ++j) blk[tri_index(i, j, NV)] += f * phi[a * NV + i] * phi[a * NV + j];
         }
     }
@@ -960,7 +966,9 @@ __global__ void element_kernel(ElemArgs A) {
             const float jx = J00 * u0 + J01 * u1, jy = J10 * u0 + J11 * u1;
             const float f = f0 * kpow<PWF>(jx * jx + jy * jy, e2);
             const float g[3] = {-u0 - u1, u0, u1};
+#pragma unroll
             for (int i = 0; i < 3; ++i)
+#pragma unroll
                 for (int j = i; j < 3; ++j) bf[tri_index(i, j, 3)] += f * g[i] * g[j];
         }
         const double beta = 2.0 * A.r2s * A.r3s * A.r4s;
@@ -976,7 +984,9 @@ __global__ void element_kernel(ElemArgs A) {
             const double jx = J00 * u0 + J01 * u1, jy = J10 * u0 + J11 * u1;
             const double f = sc * f0 * kpow<PW>(jx * jx + jy * jy, -(1.0 + s));
             const double g[3] = {-u0 - u1, u0, u1};
+#pragma unroll
             for (int i = 0; i < 3; ++i)
+#pragma unroll
                 for (int j = i; j < 3; ++j) blk[tri_index(i, j, 3)] += f * g[i] * g[j];
         }
     }
@@ -998,9 +1008,8 @@ __global__ void element_kernel(ElemArgs A) {
                     if (lane == 0) {
                         // e is an end of K: exact ∫ phi_i phi_j |x-e|^{-2s}
                         const int me = (cv[0] == e) ? 0 : 1;
-                        double a_[2], b_[2];
-                        a_[me] = 1.0, a_[1 - me] = 0.0;
-                        b_[me] = -1.0, b_[1 - me] = 1.0;
+                        const double a_[2] = {me == 0 ? 1.0 : 0.0, me == 1 ? 1.0 : 0.0};
+                        const double b_[2] = {me == 0 ? -1.0 : 1.0, me == 1 ? -1.0 : 1.0};
                         const double sc = C / (2.0 * s) * pow(jk, 1.0 - 2.0 * s);
                         for (int i = 0; i < 2; ++i)
                             for (int j = i; j < 2; ++j) {
@@ -1039,12 +1048,15 @@ __global__ void element_kernel(ElemArgs A) {
                     const double bx = pR[0] - pE1[0], by = pR[1] - pE1[1];
                     const double* tb = rule + ro.b_own;
                     const double sc = A.C2s * jk * A.FLEN[f] * A.r3s * A.r4s;
+                    double own = 0.0;
                     for (int m = lane; m < ro.n_own; m += 32) {
                         const double o1 = tb[3 * m], o2 = tb[3 * m + 1], wt = tb[3 * m + 2];
                         const double x = ax * o1 + bx * o2, y = ay * o1 + by * o2;
-                        blk[tri_index(r, r, 3)] +=
-                            sc * wt * H * o2 * facet_pow<PW>(x * x + y * y, -(1.0 + s), A.rule32 != nullptr) * o2 * o2;
+                        own += sc * wt * H * o2 * facet_pow<PW>(x * x + y * y, -(1.0 + s), A.rule32 != nullptr) * o2 * o2;
                     }
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        if (q == r) blk[tri_index(q, q, 3)] += own;
                 } else if (cls == 3) {
                     // facet and K share one vertex P
                     const int fa = A.F[2 * f], fb = A.F[2 * f + 1];
@@ -1064,7 +1076,9 @@ __global__ void element_kernel(ElemArgs A) {
                     const double* tb = rule + ro.b_vert;
                     const double sc = A.C2s * jk * A.FLEN[f];
                     const int idx[3] = {ip, iq, ir};
-                    // local order (P, Q, R): a = e_P, bh = (e_Q - e_P) x1 + (e_R - e_Q) x2
+                    // local order (P, Q, R): a = e_P, bh = (e_Q - e_P) x1 + (e_R - e_Q) x2; the
+                    // local block is summed first, then placed by the cell's vertex order
+                    double lb[6] = {};
                     for (int m = lane; m < ro.n_bvert; m += 32) {
                         const double x1 = tb[4 * m], x2 = tb[4 * m + 1], t = tb[4 * m + 2], wt = tb[4 * m + 3];
                         const double xpx = gq[0] * x1 + gr[0] * x2, xpy = gq[1] * x1 + gr[1] * x2;
@@ -1072,24 +1086,38 @@ __global__ void element_kernel(ElemArgs A) {
                         const double dx = xpx - t * ge[0], dy = xpy - t * ge[1];
                         const double g = sc * wt * N * facet_pow<PW>(dx * dx + dy * dy, -(1.0 + s), A.rule32 != nullptr);
                         const double bh[3] = {-x1, x1 - x2, x2};
+#pragma unroll
                         for (int i = 0; i < 3; ++i)
+#pragma unroll
                             for (int j = i; j < 3; ++j) {
                                 const double ai = (i == 0) ? 1.0 : 0.0, aj = (j == 0) ? 1.0 : 0.0;
                                 double val = g * bh[i] * bh[j] * A.r4s + g * (ai * bh[j] + aj * bh[i]) * A.r3s;
-                                if (ai * aj != 0.0) val += g * A.r2s;
-                                int I_ = idx[i], J_ = idx[j];
-                                if (I_ > J_) { const int tmp = I_; I_ = J_; J_ = tmp; }
-                                blk[tri_index(I_, J_, 3)] += val;
+                                if (i == 0 && j == 0) val += g * A.r2s;
+                                lb[tri_index(i, j, 3)] += val;
                             }
                     }
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = i; j < 3; ++j) {
+#pragma unroll
+                            for (int I_ = 0; I_ < 3; ++I_)
+#pragma unroll
+                                for (int J_ = I_; J_ < 3; ++J_)
+                                    if ((idx[i] == I_ && idx[j] == J_) || (idx[i] == J_ && idx[j] == I_))
+                                        blk[tri_index(I_, J_, 3)] += lb[tri_index(i, j, 3)];
+                        }
                 }
             }
         }
     }
-    for (int q = 0; q < 6; ++q) blk[q] = warp_sum(blk[q]);
+#pragma unroll
+    for (int q = 0; q < NV * (NV + 1) / 2; ++q) blk[q] = warp_sum(blk[q]);
     if (lane == 0) {
         double* out = A.contrib + A.slot0 + k * NV * NV;
+#pragma unroll
         for (int i = 0; i < NV; ++i)
+#pragma unroll
             for (int j = i; j < NV; ++j) out[i * NV + j] = out[j * NV + i] = blk[tri_index(i, j, NV)];
     }
 }
@@ -1157,6 +1185,14 @@ __global__ void __launch_bounds__(256) compose_far_kernel(int64_t n, int64_t nbl
         double acc = 0.0;
         if (i < n && j < n) {
             const int64_t lo = min(i, j), hi = max(i, j);
+            // float32 partials: a compensated float32 sum (s, c) holds the total to about
+            // float64 accuracy for these few same-signed terms and keeps the float64 pipe
+            // (1/64 of the float32 rate here) out of the loop; float64 partials: a float64 sum
+            float ks = 0.f, kc = 0.f;
+            auto add = [&](T x) {
+                if constexpr (sizeof(T) == 4) kahan_add(ks, kc, x);
+                else acc += x;
+            };
             for (int a = occ_ptr[lo]; a < occ_ptr[lo + 1]; ++a) {
                 const int64_t Ba = occ_blk[a];
                 const int la = occ_loc[a];
@@ -1165,17 +1201,19 @@ __global__ void __launch_bounds__(256) compose_far_kernel(int64_t n, int64_t nbl
                     const int lb = occ_loc[b];
                     if (Ba < Bb) {
                         const int64_t t = Ba * nblk - Ba * (Ba - 1) / 2 + (Bb - Ba);
-                        acc += (double)P[toff[t] + (int64_t)la * (L_ptr[Bb + 1] - L_ptr[Bb]) + lb];
+                        add(P[toff[t] + (int64_t)la * (L_ptr[Bb + 1] - L_ptr[Bb]) + lb]);
                     } else if (Ba > Bb) {
                         const int64_t t = Bb * nblk - Bb * (Bb - 1) / 2 + (Ba - Bb);
-                        acc += (double)P[toff[t] + (int64_t)lb * (L_ptr[Ba + 1] - L_ptr[Ba]) + la];
+                        add(P[toff[t] + (int64_t)lb * (L_ptr[Ba + 1] - L_ptr[Ba]) + la]);
                     } else {
                         const int64_t t = Ba * nblk - Ba * (Ba - 1) / 2;
                         const int64_t nL = L_ptr[Ba + 1] - L_ptr[Ba];
-                        acc += (double)P[toff[t] + (int64_t)la * nL + lb] + (double)P[toff[t] + (int64_t)lb * nL + la];
+                        add(P[toff[t] + (int64_t)la * nL + lb]);
+                        add(P[toff[t] + (int64_t)lb * nL + la]);
                     }
                 }
             }
+            if constexpr (sizeof(T) == 4) acc = (double)ks - (double)kc;
             A[i * lda + j] = negC * acc;
         }
         tile[ty + 8 * k][tx] = negC * acc;
@@ -1899,10 +1937,11 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
                 E.contrib = t.contrib;
                 E.slot0 = P.el_slot0;
                 const unsigned ge = (unsigned)((nc * 32 + 127) / 128);  // one warp per cell
-                if (D == 2 && pw == 5) { element_kernel<5><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
-                else if (D == 2 && pw == 6) { element_kernel<6><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
-                else if (D == 2 && pw == 7) { element_kernel<7><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
-                else { element_kernel<0><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+                if (D == 2 && pw == 5) { element_kernel<5, 2><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+                else if (D == 2 && pw == 6) { element_kernel<6, 2><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+                else if (D == 2 && pw == 7) { element_kernel<7, 2><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+                else if (D == 2) { element_kernel<0, 2><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+                else { element_kernel<0, 1><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
                 FL_CUDA_TRY(h, cudaGetLastError());
             }
             stage_mark(h, st, FL_STAGE_ELEMENT, 1);
