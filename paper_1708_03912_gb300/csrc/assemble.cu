@@ -11,8 +11,9 @@
 //   near_pairs     separated pairs at distance 1 (order k_near), one thread each
 //   touch_pairs    common-edge / common-vertex pairs, float64, one thread each
 //   bnd_far        element x far boundary facet sums (2D), one warp per 32 cells
-//   element        per cell: diagonal block from the row sums, identical pair,
-//                  boundary term (near/touching facets in float64)
+//   element        per cell, in two parts: the identical pair, near pairs and
+//                  touching/near facets (no far-field input, runs beside far_tile),
+//                  then the diagonal block from the far row sums and far facets
 //   gather_csr     sparse near-field values from the contribution slots
 //   compose        dense A = far partials (fixed order) + near-field values
 #include <cuda_runtime.h>
@@ -21,6 +22,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "context.h"
@@ -799,6 +801,7 @@ struct ElemArgs {
     int regional;
     double* contrib;
     int64_t slot0;
+    double* eblk;  // nc x 6: the far-independent part of each cell's block (PART 1 -> PART 2)
 };
 
 // One warp per cell with DOFs.  Lanes take quadrature points (or partner blocks)
@@ -829,7 +832,11 @@ __device__ __forceinline__ double facet_pow(double r2, double e, bool f32) {
 
 // The block blk (upper triangle, 6 values in 2D) stays in registers: the dimension is a
 // template parameter and every update of it uses a compile-time index.
-template <int PW, int D>
+// PART 1: everything that does not need the far field (near pairs and facets, identical
+// pair, touching facets), summed over the warp into A.eblk[k]; it runs while the far
+// tile kernel runs, on the float64 pipe that kernel leaves idle.  PART 2: the diagonal
+// block from the far row sums and far facets, plus A.eblk[k], into the contribution slots.
+template <int PW, int D, int PART>
 __global__ void element_kernel(ElemArgs A) {
     constexpr int NV = D + 1;
     const int lane = threadIdx.x & 31;
@@ -845,7 +852,7 @@ __global__ void element_kernel(ElemArgs A) {
     // diagonal block from the far row sums and far facets.  Lanes own (point a, half h)
     // and add the partner blocks B = h, h+2, h+4, ... in a fixed order with four
     // independent accumulators; the two halves are then added.
-    {
+    if constexpr (PART == 2) {
         const double* w = rule + ro.far_w;
         const double* phi = rule + ro.far_phi;
         const int npass = (qf + 15) / 16;
@@ -894,6 +901,7 @@ __global__ void element_kernel(ElemArgs A) {
             }
         }
     }
+    if constexpr (PART == 1) {
     // near pairs (both roles) and near boundary facets, order-k_near points
     {
         const double* w = rule + ro.near_w;
@@ -1111,8 +1119,17 @@ __global__ void element_kernel(ElemArgs A) {
             }
         }
     }
+    }  // PART == 1
 #pragma unroll
     for (int q = 0; q < NV * (NV + 1) / 2; ++q) blk[q] = warp_sum(blk[q]);
+    if constexpr (PART == 1) {
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < NV * (NV + 1) / 2; ++q) A.eblk[k * 6 + q] = blk[q];
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < NV * (NV + 1) / 2; ++q) blk[q] += A.eblk[k * 6 + q];
     if (lane == 0) {
         double* out = A.contrib + A.slot0 + k * NV * NV;
 #pragma unroll
@@ -1388,6 +1405,7 @@ int ensure_device(fl_ctx* h, int pi, cudaStream_t st) {
     FL_TRY(alloc(h, &t.pts, (size_t)nc * qf * D * sizeof(double)));
     FL_TRY(alloc(h, (void**)&t.Dn, (size_t)P.np_a.size() * 2 * qn * sizeof(double)));
     FL_TRY(alloc(h, (void**)&t.Bf, (size_t)nc * qf * sizeof(double)));
+    FL_TRY(alloc(h, (void**)&t.eblk, (size_t)nc * 6 * sizeof(double)));
     FL_TRY(alloc(h, (void**)&t.contrib, (size_t)P.nslots * sizeof(double)));
     FL_TRY(alloc(h, (void**)&t.csr_val, P.csr_col.size() * sizeof(double)));
     FL_TRY(alloc(h, &t.facet_rec, (size_t)std::max<int64_t>(P.nf, 1) * sizeof(FacetRec)));
@@ -1892,12 +1910,8 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
                 else FL_TRY(launch_bnd<double>(h, P, t, ro, expo, pw, st));
             }
             stage_mark(h, st, FL_STAGE_BND, 1);
-            // the element kernel adds the far field's per-point row sums: wait for the far stage
-            if (sst != h_st) {
-                FL_CUDA_TRY(h, cudaEventRecord(h->ev_far, h_st));
-                FL_CUDA_TRY(h, cudaStreamWaitEvent(sst, h->ev_far, 0));
-            }
-            // per element
+            // per element: the far-independent part now (beside the far tile kernel), the part
+            // that adds the far field's per-point row sums once the far stage is done
             stage_mark(h, st, FL_STAGE_ELEMENT, 0);
             {
                 ElemArgs E;
@@ -1936,12 +1950,24 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
                 E.regional = h->opt.regional;
                 E.contrib = t.contrib;
                 E.slot0 = P.el_slot0;
+                E.eblk = t.eblk;
                 const unsigned ge = (unsigned)((nc * 32 + 127) / 128);  // one warp per cell
-                if (D == 2 && pw == 5) { element_kernel<5, 2><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
-                else if (D == 2 && pw == 6) { element_kernel<6, 2><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
-                else if (D == 2 && pw == 7) { element_kernel<7, 2><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
-                else if (D == 2) { element_kernel<0, 2><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
-                else { element_kernel<0, 1><<<ge, 128, 0, st>>>(E); fl::count_launch(); }
+                auto launch_elem = [&](auto part) {
+                    constexpr int PT = decltype(part)::value;
+                    if (D == 2 && pw == 5) element_kernel<5, 2, PT><<<ge, 128, 0, st>>>(E);
+                    else if (D == 2 && pw == 6) element_kernel<6, 2, PT><<<ge, 128, 0, st>>>(E);
+                    else if (D == 2 && pw == 7) element_kernel<7, 2, PT><<<ge, 128, 0, st>>>(E);
+                    else if (D == 2) element_kernel<0, 2, PT><<<ge, 128, 0, st>>>(E);
+                    else element_kernel<0, 1, PT><<<ge, 128, 0, st>>>(E);
+                    fl::count_launch();
+                };
+                launch_elem(std::integral_constant<int, 1>{});
+                FL_CUDA_TRY(h, cudaGetLastError());
+                if (sst != h_st) {
+                    FL_CUDA_TRY(h, cudaEventRecord(h->ev_far, h_st));
+                    FL_CUDA_TRY(h, cudaStreamWaitEvent(sst, h->ev_far, 0));
+                }
+                launch_elem(std::integral_constant<int, 2>{});
                 FL_CUDA_TRY(h, cudaGetLastError());
             }
             stage_mark(h, st, FL_STAGE_ELEMENT, 1);

@@ -83,6 +83,7 @@ struct DevTables {
     void* pts = nullptr;    // nc * Qf * dim offsets from centroids
     double* Dn = nullptr;   // nnear * 2 * Qn
     double* Bf = nullptr;   // nc * Qf boundary sums (far facets)
+    double* eblk = nullptr; // nc * 6 far-independent part of each cell's diagonal block
     double* contrib = nullptr;
     double* csr_val = nullptr;
     void* facet_rec = nullptr;  // compact boundary-facet records (2D)

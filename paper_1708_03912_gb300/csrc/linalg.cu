@@ -152,9 +152,10 @@ __global__ void gemv_lo_kernel(int64_t n, const TA* __restrict__ A, int64_t lda,
     if (lane == 0) y[row * incy] = t;
 }
 
-// The same products with x staged in shared memory once per block: blocks of 8 warps
-// loop over rows (row = block * 8 + warp, stride grid * 8), so x is read from L2 once per
-// block instead of once per row, and eight 16-byte loads of A per lane are in flight.
+// The same products with x staged in shared memory once per block: each block takes a
+// contiguous range of rows (as many blocks as fit on the device), its 8 warps share every
+// row and their partial sums are added in a fixed order, so x is read from L2 once per
+// block instead of once per row and eight 16-byte loads of A per thread are in flight.
 // TX is the type of the staged x (float for float32 / bfloat16 A, double for float64 A).
 template <typename Acc, typename TA>
 __device__ __forceinline__ Acc to_acc(TA v) {
@@ -178,21 +179,26 @@ __global__ void __launch_bounds__(32 * GEMV_SMEM_WARPS, 4)
         if constexpr (F64) xs[i] = x[i * incx];
         else xs[i] = xf[i];
     }
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t row = (int64_t)blockIdx.x * GEMV_SMEM_WARPS + warp; row < n; row += (int64_t)gridDim.x * GEMV_SMEM_WARPS) {
+    constexpr int NT = 32 * GEMV_SMEM_WARPS;
+    __shared__ double part[2][GEMV_SMEM_WARPS];
+    // a contiguous, balanced range of rows per block; all 8 warps share each row (thread t
+    // takes the 16-byte chunks t, t + 256, ...), so a block never waits on one long row
+    const int64_t r0 = (int64_t)blockIdx.x * n / gridDim.x, r1 = (int64_t)(blockIdx.x + 1) * n / gridDim.x;
+    __syncthreads();
+    int buf = 0;
+    for (int64_t row = r0; row < r1; ++row, buf ^= 1) {
         const TA* a = A + row * lda;
         Acc acc0 = 0, acc1 = 0;
         // peel to the first 16-byte boundary of the row
         const int mis = (int)(((uintptr_t)a & 15u) / sizeof(TA));
         const int64_t p0 = min((int64_t)(mis ? V - mis : 0), n);
-        if (lane < p0) acc0 = fma(to_acc<Acc>(a[lane]), (Acc)xs[lane], acc0);
-        const int64_t m = n - p0;
-        const int64_t nv = (m / (32 * V)) * (32 * V);
+        if (threadIdx.x < p0) acc0 = fma(to_acc<Acc>(a[threadIdx.x]), (Acc)xs[threadIdx.x], acc0);
+        const int64_t nv = (n - p0) / V;  // whole 16-byte chunks
         const uint4* a4 = reinterpret_cast<const uint4*>(a + p0);
         const TX* xr = xs + p0;
 #pragma unroll 8
-        for (int64_t j = lane; j < nv / V; j += 32) {
+        for (int64_t j = threadIdx.x; j < nv; j += NT) {
             const uint4 u = __ldcs(a4 + j);
             if constexpr (F64) {
                 acc0 = fma(__longlong_as_double(((long long)u.y << 32) | u.x), (double)xr[j * 2], acc0);
@@ -207,21 +213,32 @@ __global__ void __launch_bounds__(32 * GEMV_SMEM_WARPS, 4)
                 }
             }
         }
-        for (int64_t j = p0 + nv + lane; j < n; j += 32) acc0 = fma(to_acc<Acc>(a[j]), (Acc)xs[j], acc0);
+        for (int64_t j = p0 + nv * V + threadIdx.x; j < n; j += NT) acc0 = fma(to_acc<Acc>(a[j]), (Acc)xs[j], acc0);
         const double t = warp_sum((double)acc0 + (double)acc1);
-        if (lane == 0) y[row * incy] = t;
+        if (lane == 0) part[buf][warp] = t;
+        __syncthreads();  // part[buf] complete; part[buf ^ 1] is free again for the next row
+        if (threadIdx.x == 0) {
+            double r = 0.0;
+#pragma unroll
+            for (int w = 0; w < GEMV_SMEM_WARPS; ++w) r += part[buf][w];
+            y[row * incy] = r;
+        }
     }
 }
 
-// grid of the shared-memory product: as many blocks as fit on the device at once (or one per
-// 8 rows); 0 when x does not fit
+// grid of the shared-memory product: as many blocks as fit on the device at once (at most
+// one per row); 0 when x does not fit
 template <typename TA, typename TX>
 static unsigned gemv_smem_grid(int64_t n) {
     const size_t smem = (size_t)n * sizeof(TX);
     if (smem > GEMV_SMEM_MAX) return 0;
-    static int ready = 0, sms = 0, dev_cached = -1;
+    // per host thread (no locking): the attribute is set once per thread and device
+    static thread_local int ready = 0, sms = 0, dev_cached = -1;
+    static thread_local int64_t n_cached = -1;
+    static thread_local unsigned grid_cached = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (ready && dev == dev_cached && n == n_cached) return grid_cached;  // no driver query per product
     if (!ready || dev != dev_cached) {
         if (cudaFuncSetAttribute(gemv_smem_kernel<TA, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)GEMV_SMEM_MAX) != cudaSuccess ||
@@ -238,8 +255,9 @@ static unsigned gemv_smem_grid(int64_t n) {
         cudaGetLastError();
         return 0;
     }
-    const int64_t want = (n + GEMV_SMEM_WARPS - 1) / GEMV_SMEM_WARPS;
-    return (unsigned)std::min<int64_t>(want, (int64_t)sms * per_sm);
+    grid_cached = (unsigned)std::min<int64_t>(n, (int64_t)sms * per_sm);
+    n_cached = n;
+    return grid_cached;
 }
 
 __global__ void to_f32_kernel(int64_t n, const double* x, int64_t incx, float* y) {
