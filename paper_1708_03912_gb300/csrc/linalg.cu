@@ -152,11 +152,14 @@ __global__ void gemv_lo_kernel(int64_t n, const TA* __restrict__ A, int64_t lda,
     if (lane == 0) y[row * incy] = t;
 }
 
-// The same products with x staged in shared memory once per block: each block takes a
-// contiguous range of rows (as many blocks as fit on the device), its 8 warps share every
-// row and their partial sums are added in a fixed order, so x is read from L2 once per
-// block instead of once per row and eight 16-byte loads of A per thread are in flight.
-// TX is the type of the staged x (float for float32 / bfloat16 A, double for float64 A).
+// The same products with x staged in shared memory once per block (8 warps, warp per row,
+// row = block * 8 + warp with stride grid * 8), so x is read from L2 once per block instead
+// of once per row.  A row starting off a 16-byte boundary peels its first elements; the x
+// entries that go with a 16-byte chunk of A are then read as 16-byte words of the staged
+// copy and shifted in registers (a compile-time shift per row alignment), which keeps the
+// shared-memory reads free of bank conflicts.  Each row starts its chunk loop at a
+// row-dependent rotation, so the warps streaming neighbouring rows (a fixed stride apart)
+// do not all address the same memory channels at once.
 template <typename Acc, typename TA>
 __device__ __forceinline__ Acc to_acc(TA v) {
     if constexpr (std::is_same<TA, __nv_bfloat16>::value) return (Acc)__bfloat162float(v);
@@ -164,7 +167,69 @@ __device__ __forceinline__ Acc to_acc(TA v) {
 }
 
 constexpr int GEMV_SMEM_WARPS = 8;
-constexpr size_t GEMV_SMEM_MAX = 200 * 1024;  // bytes of staged x
+constexpr size_t GEMV_SMEM_MAX = 200 * 1024;  // bytes of staged x (padding included)
+constexpr int GEMV_SMEM_PAD = 8;               // zero elements after x: shifted reads stay in bounds
+
+// four floats of x starting at element 4 c + SH (c counted in float4 words)
+template <int SH>
+__device__ __forceinline__ float4 x4_at(const float4* xs4, int64_t c) {
+    const float4 lo = xs4[c];
+    if constexpr (SH == 0) return lo;
+    const float4 hi = xs4[c + 1];
+    if constexpr (SH == 1) return make_float4(lo.y, lo.z, lo.w, hi.x);
+    if constexpr (SH == 2) return make_float4(lo.z, lo.w, hi.x, hi.y);
+    return make_float4(lo.w, hi.x, hi.y, hi.z);
+}
+// two doubles of x starting at element 2 c + SH
+template <int SH>
+__device__ __forceinline__ double2 x2_at(const double2* xs2, int64_t c) {
+    const double2 lo = xs2[c];
+    if constexpr (SH == 0) return lo;
+    const double2 hi = xs2[c + 1];
+    return make_double2(lo.y, hi.x);
+}
+
+// the 16-byte chunks of one row: a4 = first aligned chunk, element p0 of the row; SH = the
+// shift of x within its 16-byte words
+template <typename TA, typename TX, int SH>
+__device__ __forceinline__ void gemv_row_chunks(const uint4* __restrict__ a4, const TX* xs, int64_t p0, int64_t nv,
+                                                int64_t rot, int lane, double& out) {
+    constexpr int V = Vec16<TA>::N;
+    if constexpr (sizeof(TX) == 8) {
+        const double2* xs2 = reinterpret_cast<const double2*>(xs) + (p0 >> 1);
+        double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll 8
+        for (int64_t k = lane; k < nv; k += 32) {
+            int64_t j = k + rot;
+            if (j >= nv) j -= nv;
+            const uint4 u = __ldcs(a4 + j);
+            const double2 xv = x2_at<SH>(xs2, j);
+            acc0 = fma(__longlong_as_double(((long long)u.y << 32) | u.x), xv.x, acc0);
+            acc1 = fma(__longlong_as_double(((long long)u.w << 32) | u.z), xv.y, acc1);
+        }
+        out += acc0 + acc1;
+    } else {
+        const float4* xs4 = reinterpret_cast<const float4*>(xs) + (p0 >> 2);
+        float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll 8
+        for (int64_t k = lane; k < nv; k += 32) {
+            int64_t j = k + rot;
+            if (j >= nv) j -= nv;
+            const uint4 u = __ldcs(a4 + j);
+            float av[V];
+            unpack16<TA>(u, av);
+#pragma unroll
+            for (int h = 0; h < V / 4; ++h) {
+                const float4 xv = x4_at<SH>(xs4, j * (V / 4) + h);
+                acc0 = fmaf(av[4 * h + 0], xv.x, acc0);
+                acc1 = fmaf(av[4 * h + 1], xv.y, acc1);
+                acc0 = fmaf(av[4 * h + 2], xv.z, acc0);
+                acc1 = fmaf(av[4 * h + 3], xv.w, acc1);
+            }
+        }
+        out += (double)acc0 + (double)acc1;
+    }
+}
 
 template <typename TA, typename TX>
 __global__ void __launch_bounds__(32 * GEMV_SMEM_WARPS, 4)
@@ -172,65 +237,55 @@ __global__ void __launch_bounds__(32 * GEMV_SMEM_WARPS, 4)
                      const float* __restrict__ xf, double* __restrict__ y, int64_t incy) {
     constexpr int V = Vec16<TA>::N;
     constexpr bool F64 = sizeof(TX) == 8;
-    using Acc = typename std::conditional<F64, double, float>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TX* xs = reinterpret_cast<TX*>(smem_raw);
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        if constexpr (F64) xs[i] = x[i * incx];
-        else xs[i] = xf[i];
+    // x staged as TX: float64 as is; for float32 / bfloat16 A either the caller's float32 copy
+    // xf or x rounded here (the same rounding as that copy)
+    for (int64_t i = threadIdx.x; i < n + GEMV_SMEM_PAD; i += blockDim.x) {
+        if constexpr (F64) xs[i] = i < n ? x[i * incx] : 0.0;
+        else xs[i] = i < n ? (xf ? xf[i] : (float)x[i * incx]) : 0.f;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NT = 32 * GEMV_SMEM_WARPS;
-    __shared__ double part[2][GEMV_SMEM_WARPS];
-    // a contiguous, balanced range of rows per block; all 8 warps share each row (thread t
-    // takes the 16-byte chunks t, t + 256, ...), so a block never waits on one long row
-    const int64_t r0 = (int64_t)blockIdx.x * n / gridDim.x, r1 = (int64_t)(blockIdx.x + 1) * n / gridDim.x;
     __syncthreads();
-    int buf = 0;
-    for (int64_t row = r0; row < r1; ++row, buf ^= 1) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t row = (int64_t)blockIdx.x * GEMV_SMEM_WARPS + warp; row < n; row += (int64_t)gridDim.x * GEMV_SMEM_WARPS) {
         const TA* a = A + row * lda;
-        Acc acc0 = 0, acc1 = 0;
+        double t = 0.0;
         // peel to the first 16-byte boundary of the row
         const int mis = (int)(((uintptr_t)a & 15u) / sizeof(TA));
         const int64_t p0 = min((int64_t)(mis ? V - mis : 0), n);
-        if (threadIdx.x < p0) acc0 = fma(to_acc<Acc>(a[threadIdx.x]), (Acc)xs[threadIdx.x], acc0);
+        if constexpr (F64) {
+            if (lane < p0) t = a[lane] * xs[lane];
+        } else {
+            if (lane < p0) t = (double)(to_acc<float>(a[lane]) * xs[lane]);
+        }
         const int64_t nv = (n - p0) / V;  // whole 16-byte chunks
+        const int64_t rot = nv > 0 ? (int64_t)(((uint64_t)row * 2654435761ull) % (uint64_t)nv) : 0;
         const uint4* a4 = reinterpret_cast<const uint4*>(a + p0);
-        const TX* xr = xs + p0;
-#pragma unroll 8
-        for (int64_t j = threadIdx.x; j < nv; j += NT) {
-            const uint4 u = __ldcs(a4 + j);
-            if constexpr (F64) {
-                acc0 = fma(__longlong_as_double(((long long)u.y << 32) | u.x), (double)xr[j * 2], acc0);
-                acc1 = fma(__longlong_as_double(((long long)u.w << 32) | u.z), (double)xr[j * 2 + 1], acc1);
-            } else {
-                float av[V];
-                unpack16<TA>(u, av);
-#pragma unroll
-                for (int q = 0; q < V; q += 2) {
-                    acc0 = fmaf(av[q], (float)xr[j * V + q], acc0);
-                    acc1 = fmaf(av[q + 1], (float)xr[j * V + q + 1], acc1);
-                }
+        if constexpr (F64) {
+            if (p0 & 1) gemv_row_chunks<TA, TX, 1>(a4, xs, p0, nv, rot, lane, t);
+            else gemv_row_chunks<TA, TX, 0>(a4, xs, p0, nv, rot, lane, t);
+        } else {
+            switch (p0 & 3) {
+                case 0: gemv_row_chunks<TA, TX, 0>(a4, xs, p0, nv, rot, lane, t); break;
+                case 1: gemv_row_chunks<TA, TX, 1>(a4, xs, p0, nv, rot, lane, t); break;
+                case 2: gemv_row_chunks<TA, TX, 2>(a4, xs, p0, nv, rot, lane, t); break;
+                default: gemv_row_chunks<TA, TX, 3>(a4, xs, p0, nv, rot, lane, t); break;
             }
         }
-        for (int64_t j = p0 + nv * V + threadIdx.x; j < n; j += NT) acc0 = fma(to_acc<Acc>(a[j]), (Acc)xs[j], acc0);
-        const double t = warp_sum((double)acc0 + (double)acc1);
-        if (lane == 0) part[buf][warp] = t;
-        __syncthreads();  // part[buf] complete; part[buf ^ 1] is free again for the next row
-        if (threadIdx.x == 0) {
-            double r = 0.0;
-#pragma unroll
-            for (int w = 0; w < GEMV_SMEM_WARPS; ++w) r += part[buf][w];
-            y[row * incy] = r;
+        for (int64_t j = p0 + nv * V + lane; j < n; j += 32) {
+            if constexpr (F64) t = fma(a[j], xs[j], t);
+            else t += (double)(to_acc<float>(a[j]) * xs[j]);
         }
+        t = warp_sum(t);
+        if (lane == 0) y[row * incy] = t;
     }
 }
 
 // grid of the shared-memory product: as many blocks as fit on the device at once (at most
-// one per row); 0 when x does not fit
+// one per 8 rows); 0 when x does not fit
 template <typename TA, typename TX>
 static unsigned gemv_smem_grid(int64_t n) {
-    const size_t smem = (size_t)n * sizeof(TX);
+    const size_t smem = (size_t)(n + GEMV_SMEM_PAD) * sizeof(TX);
     if (smem > GEMV_SMEM_MAX) return 0;
     // per host thread (no locking): the attribute is set once per thread and device
     static thread_local int ready = 0, sms = 0, dev_cached = -1;
@@ -255,7 +310,7 @@ static unsigned gemv_smem_grid(int64_t n) {
         cudaGetLastError();
         return 0;
     }
-    grid_cached = (unsigned)std::min<int64_t>(n, (int64_t)sms * per_sm);
+    grid_cached = (unsigned)std::min<int64_t>((n + GEMV_SMEM_WARPS - 1) / GEMV_SMEM_WARPS, (int64_t)sms * per_sm);
     n_cached = n;
     return grid_cached;
 }
@@ -276,7 +331,14 @@ __global__ void convert_kernel(int64_t n, const double* A, int64_t lda, TO* B, i
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// grid of the shared-memory product for a float32 / bfloat16 matrix, 0 if it does not apply
+static unsigned gemv_lo_smem_grid(int dtype, const void* A, int64_t n) {
+    if (dtype == FL_F32) return (((uintptr_t)A & 3u) == 0) ? gemv_smem_grid<float, float>(n) : 0u;
+    return (((uintptr_t)A & 1u) == 0) ? gemv_smem_grid<__nv_bfloat16, float>(n) : 0u;
+}
+
 // y = A x for one right-hand side; xf is a float32 scratch copy of x (n) for low-precision A
+// (unused, and may be NULL, when the shared-memory product applies and xf_ready is false)
 // xf_ready: xf already holds x rounded to float32 (the CG keeps such a copy of p)
 cudaError_t gemv(int dtype, const void* A, int64_t lda, int64_t n, const double* x, int64_t incx, double* y,
                  int64_t incy, float* xf, cudaStream_t st, bool xf_ready) {
@@ -284,7 +346,7 @@ cudaError_t gemv(int dtype, const void* A, int64_t lda, int64_t n, const double*
     if (dtype == FL_F64) {
         const unsigned gs = (((uintptr_t)A & 7u) == 0) ? gemv_smem_grid<double, double>(n) : 0u;
         if (gs) {
-            gemv_smem_kernel<double, double><<<gs, 32 * GEMV_SMEM_WARPS, n * sizeof(double), st>>>(
+            gemv_smem_kernel<double, double><<<gs, 32 * GEMV_SMEM_WARPS, (n + GEMV_SMEM_PAD) * sizeof(double), st>>>(
                 n, (const double*)A, lda, x, incx, nullptr, y, incy);
             fl::count_launch();
             return cudaGetLastError();
@@ -292,19 +354,19 @@ cudaError_t gemv(int dtype, const void* A, int64_t lda, int64_t n, const double*
         const int vec = (((uintptr_t)A & 7u) == 0) && aligned16(x);
         gemv_f64_kernel<<<blocks, 256, 0, st>>>(n, (const double*)A, lda, x, incx, y, incy, vec); fl::count_launch();
     } else {
-        if (!xf_ready) { to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, incx, xf); fl::count_launch(); }
-        const unsigned gs = dtype == FL_F32 ? ((((uintptr_t)A & 3u) == 0) ? gemv_smem_grid<float, float>(n) : 0u)
-                                            : ((((uintptr_t)A & 1u) == 0) ? gemv_smem_grid<__nv_bfloat16, float>(n) : 0u);
-        if (gs) {
+        const unsigned gs = gemv_lo_smem_grid(dtype, A, n);
+        if (gs) {  // x rounded while it is staged: no float32 copy in global memory
+            const float* xs = xf_ready ? xf : nullptr;
             if (dtype == FL_F32)
-                gemv_smem_kernel<float, float><<<gs, 32 * GEMV_SMEM_WARPS, n * sizeof(float), st>>>(
-                    n, (const float*)A, lda, nullptr, 0, xf, y, incy);
+                gemv_smem_kernel<float, float><<<gs, 32 * GEMV_SMEM_WARPS, (n + GEMV_SMEM_PAD) * sizeof(float), st>>>(
+                    n, (const float*)A, lda, x, incx, xs, y, incy);
             else
-                gemv_smem_kernel<__nv_bfloat16, float><<<gs, 32 * GEMV_SMEM_WARPS, n * sizeof(float), st>>>(
-                    n, (const __nv_bfloat16*)A, lda, nullptr, 0, xf, y, incy);
+                gemv_smem_kernel<__nv_bfloat16, float><<<gs, 32 * GEMV_SMEM_WARPS, (n + GEMV_SMEM_PAD) * sizeof(float), st>>>(
+                    n, (const __nv_bfloat16*)A, lda, x, incx, xs, y, incy);
             fl::count_launch();
             return cudaGetLastError();
         }
+        if (!xf_ready) { to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, incx, xf); fl::count_launch(); }
         if (dtype == FL_F32) {
             const int vec = (((uintptr_t)A & 3u) == 0) && aligned16(xf);
             gemv_lo_kernel<float><<<blocks, 256, 0, st>>>(n, (const float*)A, lda, xf, y, incy, vec); fl::count_launch();
@@ -1411,8 +1473,8 @@ int fl_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, int nrhs, co
     if (!A_dev || !X_dev || !Y_dev || n < 1 || nrhs < 1 || lda < n || ldx < nrhs || ldy < nrhs) return FL_EINVAL;
     if (dtype != FL_F64 && dtype != FL_F32 && dtype != FL_BF16) return FL_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    float* xf = nullptr;
-    if (dtype != FL_F64) {
+    float* xf = nullptr;  // float32 copy of x, only for a low-precision matrix whose x does not fit the staging
+    if (dtype != FL_F64 && gemv_lo_smem_grid(dtype, A_dev, n) == 0) {
         if (cudaMallocAsync((void**)&xf, n * sizeof(float), st) != cudaSuccess) return FL_ENOMEM;
     }
     for (int r = 0; r < nrhs; ++r) {
