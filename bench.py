@@ -338,6 +338,9 @@ def main():
     xb1 = xb[:, 0].contiguous()
     yb = torch.empty(nb, 1, dtype=torch.float64, device=dev)
     yb1 = torch.empty(nb, dtype=torch.float64, device=dev)
+    # blocks per SM of the staged product from the project's autotuner, for both storage types
+    mv_tuned = {"f64": F.fl_tune_matvec(F.FL_F64, Ab, xb1, yb1, reps=5),
+                "f32": F.fl_tune_matvec(F.FL_F32, Ab32, xb1, yb1, reps=5)}
     mv64 = timed(lambda: F.fl_matvec(F.FL_F64, Ab, xb, yb), reps=10)
     mv32 = timed(lambda: F.fl_matvec(F.FL_F32, Ab32, xb, yb), reps=10)
     mv32s = timed(lambda: F.fl_matvec_f32_static(Ab32, xb1, yb1), reps=10)
@@ -453,6 +456,7 @@ def main():
         "assembly_pairs_per_s": {"mixed": n_el * n_el / (asm_mixed_ms / 1000), "fp64": n_el * n_el / (asm_fp64_ms / 1000)},
         "matvec": {"n": nb, "f64_gbs": nb * nb * 8 / (mv64 / 1000) / 1e9, "f32_gbs": nb * nb * 4 / (mv32 / 1000) / 1e9,
                    "f64_ms": mv64, "f32_ms": mv32, "f32_static_gbs": nb * nb * 4 / (mv32s / 1000) / 1e9,
+                   "tuned_blocks_per_sm": {k: v[0] for k, v in mv_tuned.items()},
                    "hbm_peak_gbs": peaks.get("hbm_gbs"),
                    "note": "bytes of A per product / device time of fl_matvec (x staged in shared memory per block; "
                            "the float32 call includes the rounding of x); L2 flushed; f32_static: the allocation-free "

@@ -457,6 +457,18 @@ int fl_tune_batch(fl_handle h, int nprob, const fl_batch_problem* probs, int rep
                   double* best_ms);
 
 /* Add or replace a table entry for the current device (p0, p1: the kernel's two parameters). */
+/*
+ * Autotuner of the dense matvec (fl_matvec's shared-memory-staged product): times it on
+ * the caller's matrix (dtype FL_F64 or FL_F32, 16-byte loads need A aligned to its
+ * element size) for 1, 2, ... blocks per SM up to what fits, median of reps CUDA-event
+ * timings after a warm-up, on `stream`; records the fastest under ("gemv_smem_f64" |
+ * "gemv_smem_f32", n) for this device, which fl_matvec then uses.  x_dev, y_dev: [n]
+ * float64 (y is overwritten).  *best_per_sm, *best_ms (host, may be NULL) get the choice.
+ * Errors: FL_EINVAL (bad arguments), FL_ENOTIMPL (x too large to stage), FL_ECUDA.
+ */
+int fl_tune_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, const double* x_dev,
+                   double* y_dev, int reps, int* best_per_sm, double* best_ms, void* stream);
+
 int fl_tune_record(const char* kernel, int64_t n, int nrhs, int nslices, int p0, int p1, double ms);
 /* FL_OK and the parameters if the current device has an entry, else FL_ENOTIMPL. */
 int fl_tune_lookup(const char* kernel, int64_t n, int nrhs, int nslices, int* p0, int* p1);

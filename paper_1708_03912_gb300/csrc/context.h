@@ -153,4 +153,5 @@ void tune_record(const std::string& device, const std::string& kernel, int64_t n
                  int p1, double ms);
 bool tune_lookup(const std::string& device, const std::string& kernel, int64_t n, int nrhs, int nslices, int* p0,
                  int* p1);
+unsigned tune_generation();  // changes whenever the table changes
 }  // namespace fl

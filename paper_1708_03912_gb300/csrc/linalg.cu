@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -167,6 +168,21 @@ __device__ __forceinline__ Acc to_acc(TA v) {
 }
 
 constexpr int GEMV_SMEM_WARPS = 8;
+// tuning-table names of the staged products
+template <typename TA>
+struct GemvName;
+template <>
+struct GemvName<double> {
+    static constexpr const char* name = "gemv_smem_f64";
+};
+template <>
+struct GemvName<float> {
+    static constexpr const char* name = "gemv_smem_f32";
+};
+template <>
+struct GemvName<__nv_bfloat16> {
+    static constexpr const char* name = "gemv_smem_bf16";
+};
 constexpr size_t GEMV_SMEM_MAX = 200 * 1024;  // bytes of staged x (padding included)
 constexpr int GEMV_SMEM_PAD = 8;               // zero elements after x: shifted reads stay in bounds
 
@@ -284,16 +300,18 @@ __global__ void __launch_bounds__(32 * GEMV_SMEM_WARPS, 4)
 // grid of the shared-memory product: as many blocks as fit on the device at once (at most
 // one per 8 rows); 0 when x does not fit
 template <typename TA, typename TX>
-static unsigned gemv_smem_grid(int64_t n) {
+static unsigned gemv_smem_grid(int64_t n, int force_per_sm = 0, int* max_per_sm = nullptr) {
     const size_t smem = (size_t)(n + GEMV_SMEM_PAD) * sizeof(TX);
     if (smem > GEMV_SMEM_MAX) return 0;
     // per host thread (no locking): the attribute is set once per thread and device
     static thread_local int ready = 0, sms = 0, dev_cached = -1;
     static thread_local int64_t n_cached = -1;
-    static thread_local unsigned grid_cached = 0;
+    static thread_local unsigned grid_cached = 0, gen_cached = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (ready && dev == dev_cached && n == n_cached) return grid_cached;  // no driver query per product
+    const unsigned gen = tune_generation();
+    if (!force_per_sm && !max_per_sm && ready && dev == dev_cached && n == n_cached && gen == gen_cached)
+        return grid_cached;  // no driver query per product
     if (!ready || dev != dev_cached) {
         if (cudaFuncSetAttribute(gemv_smem_kernel<TA, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)GEMV_SMEM_MAX) != cudaSuccess ||
@@ -310,8 +328,15 @@ static unsigned gemv_smem_grid(int64_t n) {
         cudaGetLastError();
         return 0;
     }
-    grid_cached = (unsigned)std::min<int64_t>((n + GEMV_SMEM_WARPS - 1) / GEMV_SMEM_WARPS, (int64_t)sms * per_sm);
+    if (max_per_sm) *max_per_sm = per_sm;
+    const int64_t want = (n + GEMV_SMEM_WARPS - 1) / GEMV_SMEM_WARPS;
+    if (force_per_sm) return (unsigned)std::min<int64_t>(want, (int64_t)sms * std::min(force_per_sm, per_sm));
+    // blocks per SM from the matvec autotuner (fl_tune_matvec) when it has measured this size
+    int p0 = 0, p1 = 0;
+    if (tune_lookup(device_name(), GemvName<TA>::name, n, 1, 1, &p0, &p1) && p0 >= 1) per_sm = std::min(per_sm, p0);
+    grid_cached = (unsigned)std::min<int64_t>(want, (int64_t)sms * per_sm);
     n_cached = n;
+    gen_cached = gen;
     return grid_cached;
 }
 
@@ -1482,6 +1507,71 @@ int fl_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, int nrhs, co
     }
     if (xf) cudaFreeAsync(xf, st);
     return cudaGetLastError() == cudaSuccess ? FL_OK : FL_ECUDA;
+}
+
+int fl_tune_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, const double* x_dev, double* y_dev, int reps,
+                   int* best_per_sm, double* best_ms, void* stream) {
+    if (!A_dev || !x_dev || !y_dev || n < 1 || lda < n || reps < 1) return FL_EINVAL;
+    if (dtype != FL_F64 && dtype != FL_F32) return FL_EINVAL;
+    if (((uintptr_t)A_dev & (dtype == FL_F64 ? 7u : 3u)) != 0) return FL_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int max_per_sm = 0;
+    const bool f64 = dtype == FL_F64;
+    if ((f64 ? gemv_smem_grid<double, double>(n, 0, &max_per_sm) : gemv_smem_grid<float, float>(n, 0, &max_per_sm)) == 0)
+        return FL_ENOTIMPL;  // x does not fit the shared-memory staging: nothing to tune
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return FL_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return FL_ECUDA;
+    }
+    const size_t smem = (size_t)(n + GEMV_SMEM_PAD) * (f64 ? sizeof(double) : sizeof(float));
+    int best = 0;
+    double best_t = 0.0;
+    int rc = FL_OK;
+    for (int k = 1; k <= max_per_sm && rc == FL_OK; ++k) {
+        const unsigned grid = f64 ? gemv_smem_grid<double, double>(n, k) : gemv_smem_grid<float, float>(n, k);
+        auto launch = [&]() {
+            if (f64)
+                gemv_smem_kernel<double, double><<<grid, 32 * GEMV_SMEM_WARPS, smem, st>>>(n, (const double*)A_dev, lda,
+                                                                                          x_dev, 1, nullptr, y_dev, 1);
+            else
+                gemv_smem_kernel<float, float><<<grid, 32 * GEMV_SMEM_WARPS, smem, st>>>(n, (const float*)A_dev, lda,
+                                                                                        x_dev, 1, nullptr, y_dev, 1);
+            fl::count_launch();
+        };
+        launch();  // warm-up
+        std::vector<float> ts;
+        for (int r = 0; r < reps; ++r) {
+            cudaEventRecord(e0, st);
+            launch();
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = FL_ECUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ts.push_back(ms);
+        }
+        if (rc != FL_OK || cudaGetLastError() != cudaSuccess) {
+            rc = FL_ECUDA;
+            break;
+        }
+        std::sort(ts.begin(), ts.end());
+        const double med = ts[ts.size() / 2];
+        if (!best || med < best_t) {
+            best = k;
+            best_t = med;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != FL_OK) return rc;
+    tune_record(device_name(), f64 ? GemvName<double>::name : GemvName<float>::name, n, 1, 1, best, 0, best_t);
+    if (best_per_sm) *best_per_sm = best;
+    if (best_ms) *best_ms = best_t;
+    return FL_OK;
 }
 
 int fl_convert(const double* A_dev, int64_t lda, int64_t n, int dtype, void* A_lo_dev, int64_t ld_lo, void* stream) {

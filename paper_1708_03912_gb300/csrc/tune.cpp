@@ -7,6 +7,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -24,6 +25,9 @@ struct TuneEntry {
 
 static std::mutex g_tune_mu;
 static std::vector<TuneEntry> g_tune;
+static std::atomic<unsigned> g_tune_gen{0};  // bumped on every change of the table
+
+unsigned tune_generation() { return g_tune_gen.load(std::memory_order_acquire); }
 
 std::string device_name() {
     int dev = 0;
@@ -38,6 +42,7 @@ std::string device_name() {
 void tune_record(const std::string& device, const std::string& kernel, int64_t n, int nrhs, int nslices, int p0,
                  int p1, double ms) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_gen.fetch_add(1, std::memory_order_acq_rel);
     for (TuneEntry& e : g_tune) {
         if (e.device == device && e.kernel == kernel && e.n == n && e.nrhs == nrhs && e.nslices == nslices) {
             e.p0 = p0;
@@ -165,6 +170,7 @@ int fl_tune_lookup(const char* kernel, int64_t n, int nrhs, int nslices, int* p0
 
 void fl_tune_clear(void) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_gen.fetch_add(1, std::memory_order_acq_rel);
     g_tune.clear();
 }
 

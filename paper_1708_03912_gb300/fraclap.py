@@ -27,7 +27,7 @@ EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl
            "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
            "fl_matvec_f32_static",
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
-           "fl_tune_batch", "fl_tune_record", "fl_tune_lookup", "fl_tune_clear", "fl_tune_count", "fl_tune_save",
+           "fl_tune_batch", "fl_tune_matvec", "fl_tune_record", "fl_tune_lookup", "fl_tune_clear", "fl_tune_count", "fl_tune_save",
            "fl_tune_load", "fl_prolongation", "fl_mg_create", "fl_mg_add_level", "fl_mg_setup", "fl_mg_level", "fl_mg_level_copy",
            "fl_mg_omega", "fl_mg_vcycle", "fl_mg_solve", "fl_mg_last_error", "fl_mg_destroy",
            "fl_patches", "fl_lp_create", "fl_lp_num_params", "fl_lp_num_features", "fl_lp_num_samples",
@@ -156,6 +156,8 @@ def lib():
     L.fl_tune_batch.argtypes = [vp, ci, ctypes.POINTER(fl_batch_problem), ci, ctypes.POINTER(fl_batch_opts),
                                 ctypes.POINTER(dbl)]
     L.fl_tune_batch.restype = ci
+    L.fl_tune_matvec.argtypes = [ci, vp, i64, i64, vp, vp, ci, ctypes.POINTER(ci), ctypes.POINTER(dbl), vp]
+    L.fl_tune_matvec.restype = ci
     L.fl_tune_record.argtypes = [ctypes.c_char_p, i64, ci, ci, ci, ci, dbl]
     L.fl_tune_record.restype = ci
     L.fl_tune_lookup.argtypes = [ctypes.c_char_p, i64, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]
@@ -434,6 +436,16 @@ def fl_tune_batch(h, problems, reps=5):
     ms = ctypes.c_double()
     _check(lib().fl_tune_batch(h, len(problems), arr, reps, ctypes.byref(best), ctypes.byref(ms)), h)
     return best, ms.value
+
+
+def fl_tune_matvec(dtype, A, x, y, reps=5, stream=None):
+    """Tune fl_matvec's blocks per SM on A (float64 or float32, n x n, row stride lda);
+    x, y: [n] float64.  Returns (blocks per SM, ms)."""
+    per_sm = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().fl_tune_matvec(dtype, _ptr(A), A.stride(0), A.shape[0], _ptr(x), _ptr(y), reps, ctypes.byref(per_sm),
+                                ctypes.byref(ms), _stream(stream)))
+    return per_sm.value, ms.value
 
 
 def fl_tune_record(kernel, n, nrhs, nslices, p0, p1, ms):

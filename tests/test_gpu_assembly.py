@@ -220,3 +220,21 @@ def test_full_size_disc_sampled_rows():
     assert float(np.max(np.abs(A[rows] - Ar) / d)) < TOL64
     assert float(np.max(np.abs(Am[rows] - Ar) / d)) < 2e-5
     assert np.array_equal(A, A.T)
+
+
+def test_full_size_graded_disc_sampled_rows():
+    # the disc graded toward the boundary (30 rings, mu = 2: 22043 triangles, 8195 DOFs),
+    # 3 seeded rows against the oracle, float64 and mixed modes
+    V, T = synth.disc(30, 2.0)
+    s = 0.5
+    m = F.Mesh(V, T)
+    A = m.assemble(s, "fp64").cpu().numpy()
+    Am = m.assemble(s, "mixed").cpu().numpy()
+    m.close()
+    n = A.shape[0]
+    assert n == 8195
+    rows = synth.random_rows(n, 3)
+    Ar, _ = assemble_matrix(OracleMesh(V, T), s, rows=rows)
+    d = np.sqrt(np.outer(np.diag(A)[rows], np.diag(A)))
+    assert float(np.max(np.abs(A[rows] - Ar) / d)) < TOL64
+    assert float(np.max(np.abs(Am[rows] - Ar) / d)) < 2e-5

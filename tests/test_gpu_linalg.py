@@ -55,6 +55,29 @@ def test_matvec_padded_rows():
             assert np.allclose(Y.cpu().numpy(), ref, rtol=tol, atol=tol * np.sqrt(n))
 
 
+def test_matvec_autotuner_records_and_is_used():
+    # the tuner sweeps blocks per SM of the staged product, records the fastest, and the
+    # product taken with the recorded shape is still the product
+    g = torch.Generator(device="cpu").manual_seed(9)
+    n = 3001
+    A = torch.randn(n, n, generator=g, dtype=torch.float64).cuda()
+    A32 = torch.empty(n, n, dtype=torch.float32, device="cuda")
+    F.fl_convert(A, F.FL_F32, A32)
+    x = torch.randn(n, 1, generator=g, dtype=torch.float64).cuda()
+    x1 = x[:, 0].contiguous()
+    y1 = torch.empty(n, dtype=torch.float64, device="cuda")
+    Y = torch.empty(n, 1, dtype=torch.float64, device="cuda")
+    F.fl_tune_clear()
+    for dt, Ad, name, ref, tol in ((F.FL_F64, A, "gemv_smem_f64", A.cpu() @ x.cpu(), 1e-13),
+                                   (F.FL_F32, A32, "gemv_smem_f32", A32.double().cpu() @ x.float().double().cpu(), 1e-5)):
+        per_sm, ms = F.fl_tune_matvec(dt, Ad, x1, y1, reps=3)
+        assert per_sm >= 1 and ms > 0
+        assert F.fl_tune_lookup(name, n, 1, 1) == (per_sm, 0)
+        F.fl_matvec(dt, Ad, x, Y)
+        assert np.allclose(Y.cpu().numpy(), ref.numpy(), rtol=tol, atol=tol * np.sqrt(n))
+    F.fl_tune_clear()
+
+
 def test_pcg_matches_cholesky_1d_closed_form():
     s = 0.25
     V, T = synth.interval(128)
@@ -137,3 +160,27 @@ def test_small_systems_solve():
         assert info.status == F.FL_OK
         assert np.max(np.abs(u.cpu().numpy() - uo)) <= 1e-8 * np.max(np.abs(uo))
         m.close()
+
+
+@pytest.mark.parametrize("s", [0.25, 0.5, 0.75])
+def test_full_size_graded_disc_refined_solve(s):
+    # the graded disc (8195 DOFs): float64-refined float32 Jacobi-PCG to 1e-8; the residual
+    # ||b - A u|| / ||b|| recomputed on the host in float64 meets the tolerance, and the
+    # plain float64 solve agrees with the refined one to within what the two residuals allow
+    V, T = synth.disc(30, 2.0)
+    m = F.Mesh(V, T)
+    A = m.assemble(s, "mixed")
+    A32 = torch.empty_like(A, dtype=torch.float32)
+    F.fl_convert(A, F.FL_F32, A32)
+    b = m.load_vector(s)
+    u, info = m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3)
+    assert info.status == F.FL_OK
+    Ah, bh, uh = A.cpu().numpy(), b.cpu().numpy(), u.cpu().numpy()
+    rel = np.linalg.norm(bh - Ah @ uh) / np.linalg.norm(bh)
+    assert rel <= 1.05e-8 and abs(rel - info.rel_residual) <= 1e-3 * rel + 1e-15
+    u64, i64 = m.solve(A, b, tol=1e-8)
+    assert i64.status == F.FL_OK
+    d = u64.cpu().numpy() - uh
+    # A d = r_refined - r_f64, so ||d||_A^2 <= (||r1|| + ||r2||) ||d||
+    assert float(d @ (Ah @ d)) <= 2.1e-8 * np.linalg.norm(bh) * np.linalg.norm(d) + 1e-30
+    m.close()
