@@ -16,6 +16,9 @@ are, written out from their definitions:
 * The product the tensor cores form is S_0 (x_hi + x_lo) + S_1 x_hi: every
   slice/vector pair except the smallest, S_1 x_lo.
 
+* Hi + lo float32 storage (the 8-byte matrix the float32 pipe multiplies):
+  hi = fl32(a), lo = fl32(a - hi).
+
 Parity status: pinned in ``tests/test_oracle_lowprec.py`` against the
 float32 -> bfloat16 conversion of PyTorch (a library routine), against tie
 cases constructed from the definition, and against the float64 product within
@@ -83,3 +86,18 @@ def abs_product(S, X):
     if len(S) > 1:
         Y = Y + np.abs(S[1]) @ Xa
     return Y
+
+
+def f32x2_split(A):
+    """Hi + lo float32 storage of a float64 matrix: hi = fl32(a) (round to nearest even),
+    lo = fl32(a - hi) (a - hi is exact in float64).  Returns (hi, lo) as float32 arrays;
+    hi + lo equals a to within 2^-48 |a| (for a in the normal float32 range)."""
+    A = np.asarray(A, dtype=np.float64)
+    hi = A.astype(np.float32)
+    lo = (A - hi.astype(np.float64)).astype(np.float32)
+    return hi, lo
+
+
+def f32x2_product(hi, lo, x):
+    """The product the hi + lo storage represents, (hi + lo) x, in float64."""
+    return (hi.astype(np.float64) + lo.astype(np.float64)) @ np.asarray(x, dtype=np.float64)

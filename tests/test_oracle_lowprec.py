@@ -83,3 +83,23 @@ def test_product_bound_against_float64():
     # with one slice the error is of order 2^-9 (not smaller): the split matters
     _, S = split_bf16(A, 1)
     assert np.max(np.abs(matmul_split(S, X) - At @ X.astype(np.float64)) / scale) > 2.0 ** -14
+
+
+def test_f32x2_split_pins():
+    # hi is the library's float32 rounding, hi + lo reproduces a to 2^-48 |a| (half an ulp of
+    # the float32 remainder), values exact in float32 have lo = 0, signs and scales carry over
+    from oracle.lowprec import f32x2_split, f32x2_product
+
+    rng = np.random.default_rng(20170813)
+    A = rng.standard_normal((40, 40)) * np.exp(rng.uniform(-20, 20, (40, 40)))
+    hi, lo = f32x2_split(A)
+    assert np.array_equal(hi, A.astype(np.float32))
+    err = np.abs(A - (hi.astype(np.float64) + lo.astype(np.float64)))
+    assert np.all(err <= 2.0 ** -48 * np.abs(A))
+    assert np.all(np.abs(lo.astype(np.float64)) <= 2.0 ** -24 * np.abs(A))
+    E = A.astype(np.float32).astype(np.float64)
+    h2, l2 = f32x2_split(E)
+    assert np.array_equal(h2.astype(np.float64), E) and not l2.any()
+    x = rng.standard_normal(40)
+    y = f32x2_product(hi, lo, x)
+    assert np.all(np.abs(y - A @ x) <= 2.0 ** -46 * (np.abs(A) @ np.abs(x)))
