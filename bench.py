@@ -344,6 +344,10 @@ def main():
     mv64 = timed(lambda: F.fl_matvec(F.FL_F64, Ab, xb, yb), reps=10)
     mv32 = timed(lambda: F.fl_matvec(F.FL_F32, Ab32, xb, yb), reps=10)
     mv32s = timed(lambda: F.fl_matvec_f32_static(Ab32, xb1, yb1), reps=10)
+    Ab2 = torch.empty(nb, 2 * nb, dtype=torch.float32, device=dev)  # hi + lo float32 pairs
+    F.fl_convert(Ab, F.FL_F32X2, Ab2)
+    mvx2 = timed(lambda: F.fl_matvec(F.FL_F32X2, Ab2, xb, yb), reps=10)
+    del Ab2
     del Ab, Ab32
     # time to 1e-8: refined float32 solve vs plain float64 Jacobi-PCG on the same matrix
     m.assemble(s, "fp64", out=A)
@@ -456,11 +460,13 @@ def main():
         "assembly_pairs_per_s": {"mixed": n_el * n_el / (asm_mixed_ms / 1000), "fp64": n_el * n_el / (asm_fp64_ms / 1000)},
         "matvec": {"n": nb, "f64_gbs": nb * nb * 8 / (mv64 / 1000) / 1e9, "f32_gbs": nb * nb * 4 / (mv32 / 1000) / 1e9,
                    "f64_ms": mv64, "f32_ms": mv32, "f32_static_gbs": nb * nb * 4 / (mv32s / 1000) / 1e9,
+                   "f32x2_gbs": nb * nb * 8 / (mvx2 / 1000) / 1e9, "f32x2_ms": mvx2,
                    "tuned_blocks_per_sm": {k: v[0] for k, v in mv_tuned.items()},
                    "hbm_peak_gbs": peaks.get("hbm_gbs"),
                    "note": "bytes of A per product / device time of fl_matvec (x staged in shared memory per block; "
                            "the float32 call includes the rounding of x); L2 flushed; f32_static: the allocation-free "
-                           "fl_matvec_f32_static"},
+                           "fl_matvec_f32_static; f32x2: hi + lo float32 pairs (8 bytes per entry) multiplied in double-float "
+                           "arithmetic on the float32 pipe"},
         "solve_ms_to_1e-8": {"f32_refined": sol_mixed, "plain_f64": sol_fp64, "iters_f64": inf64.iterations,
                              "iters_refined": infmx.iterations, "outer": infmx.outer_iterations},
         "batched": batch_line,

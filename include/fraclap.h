@@ -63,6 +63,7 @@ extern "C" {
 #define FL_F64  0
 #define FL_F32  1
 #define FL_BF16 2
+#define FL_F32X2 3  /* float32 hi + lo pair per entry (hi = fl32(a), lo = fl32(a - hi)), 8 bytes */
 
 typedef struct fl_options {
     int k_far;    /* Gauss order per dimension, separated pairs at vertex-graph distance >= 2 (default 4) */
@@ -154,15 +155,22 @@ int fl_load_vector(fl_handle h, double s, const double* f_nodal_dev, int nrhs,
                    double* b_dev, int64_t ldb, void* stream);
 
 /*
- * Y = A X for a dense n x n matrix stored as dtype (FL_F64 / FL_F32 / FL_BF16) with
- * leading dimension lda; X_dev, Y_dev are [n][nrhs] float64 row-major with leading
- * dimensions ldx, ldy (>= nrhs).  Accumulation in float64 (FL_F64) or float32 with
- * float64 per-row totals (FL_F32, FL_BF16).  Streams A once per call.
+ * Y = A X for a dense n x n matrix stored as dtype (FL_F64 / FL_F32 / FL_BF16 /
+ * FL_F32X2) with leading dimension lda (in entries; an FL_F32X2 entry is a float2);
+ * X_dev, Y_dev are [n][nrhs] float64 row-major with leading dimensions ldx, ldy
+ * (>= nrhs).  Accumulation in float64 (FL_F64), float32 with float64 per-row totals
+ * (FL_F32, FL_BF16), or double-float on the float32 pipe (FL_F32X2: x split into
+ * float32 hi + lo, error about 2^-44 of sum_j |a_ij x_j|).  Streams A once per call;
+ * allocates nothing while x fits the shared-memory staging (25k entries for FL_F64 and
+ * FL_F32X2, 51k for FL_F32 and FL_BF16).  FL_EINVAL for an FL_F32X2 matrix that is not
+ * 8-byte aligned.
  */
 int fl_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, int nrhs,
               const double* X_dev, int64_t ldx, double* Y_dev, int64_t ldy, void* stream);
 
-/* A_lo_dev (dtype FL_F32 or FL_BF16, leading dimension ld_lo) = A_dev rounded to nearest. */
+/* A_lo_dev (dtype FL_F32 or FL_BF16, leading dimension ld_lo) = A_dev rounded to nearest;
+ * FL_F32X2: the (hi, lo) float2 pairs hi = fl32(a), lo = fl32(a - hi), A_lo_dev 8-byte
+ * aligned, ld_lo in pairs. */
 int fl_convert(const double* A_dev, int64_t lda, int64_t n, int dtype, void* A_lo_dev,
                int64_t ld_lo, void* stream);
 

@@ -59,6 +59,46 @@ __device__ __forceinline__ float kpow(float r2, float e) {
     }
 }
 
+// ---- double-float arithmetic on the float32 pipe (float64 is ~1/64 of its rate here) ----
+// x = hi + lo + O(2^-47 |x|) with integer operations only (no float64 pipe): hi keeps
+// the leading 24 significand bits (truncated), lo is the float32 value of the 29 bits
+// dropped.  |x| < 2^-126 gives (0, 0); lo is dropped below 2^-74 |x|'s scale.
+__device__ __forceinline__ void df_split(double x, float2& v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((u >> 52) & 0x7ff);
+    if (e <= 1023 - 127) {
+        v = make_float2(0.f, 0.f);
+        return;
+    }
+    const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+    if (e >= 1023 + 128) {  // beyond float32: an infinity that poisons the residual visibly
+        v = make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+        return;
+    }
+    const unsigned long long m = u & ((1ull << 52) - 1);
+    const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(m >> 29));
+    // dropped bits have weight 2^(e - 1023 - 52); as a float32 scale that needs e >= 949
+    float lo = 0.f;
+    if (e >= 1023 - 74) {
+        const float scale = __uint_as_float((unsigned)(e - 1023 - 52 + 127) << 23);
+        lo = __uint2float_rn((unsigned)(m & 0x1FFFFFFFu)) * scale;
+        if (sign) lo = -lo;
+    }
+    v = make_float2(hi, lo);
+}
+
+// (sh, sl) += (ah + al)(uh + ul), dropping al ul
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al, float uh, float ul) {
+    const float p = __fmul_rn(ah, uh);
+    const float e = __fmaf_rn(ah, uh, -p);
+    const float l = __fmaf_rn(ah, ul, __fmaf_rn(al, uh, e));
+    const float t = __fadd_rn(sh, p);
+    const float z = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, l));
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -340,6 +340,127 @@ static unsigned gemv_smem_grid(int64_t n, int force_per_sm = 0, int* max_per_sm 
     return grid_cached;
 }
 
+// Hi + lo float32 storage (FL_F32X2): entry (i, j) is the float2 (hi, lo), hi = fl32(a),
+// lo = fl32(a - hi), 8 bytes like float64 but multiplied on the float32 pipe.  x is split
+// into (hi, lo) by integer operations, and each product is accumulated in double-float
+// arithmetic: y_i = sum_j (hi + lo)_ij (xh + xl)_j to about 2^-44 of sum_j |a_ij x_j|,
+// without the float64 pipe that bounds the FL_F64 product.  x is staged in shared memory
+// (STAGED) or read as float2 from a split copy in global memory.
+template <int SH>
+__device__ __forceinline__ float4 x2pair_at(const float4* xs4, int64_t j) {
+    // the float2 entries 2 j + SH and 2 j + SH + 1 of x as one float4
+    const float4 lo = xs4[j];
+    if constexpr (SH == 0) return lo;
+    const float4 hi = xs4[j + 1];
+    return make_float4(lo.z, lo.w, hi.x, hi.y);
+}
+
+template <int SH>
+__device__ __forceinline__ void gemv_x2_chunks(const uint4* __restrict__ a4, const float4* xs4, int64_t nv, int64_t rot,
+                                               int lane, float (&acc)[4]) {
+#pragma unroll 8
+    for (int64_t k = lane; k < nv; k += 32) {
+        int64_t j = k + rot;
+        if (j >= nv) j -= nv;
+        const uint4 u = __ldcs(a4 + j);
+        const float4 xv = x2pair_at<SH>(xs4, j);
+        df_fma(acc[0], acc[1], __uint_as_float(u.x), __uint_as_float(u.y), xv.x, xv.y);
+        df_fma(acc[2], acc[3], __uint_as_float(u.z), __uint_as_float(u.w), xv.z, xv.w);
+    }
+}
+
+template <bool STAGED>
+__global__ void __launch_bounds__(32 * GEMV_SMEM_WARPS, 4)
+    gemv_x2_kernel(int64_t n, const float2* __restrict__ A, int64_t lda, const double* __restrict__ x, int64_t incx,
+                   const float2* __restrict__ xg, double* __restrict__ y, int64_t incy) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const float2* xs;
+    if constexpr (STAGED) {
+        float2* xw = reinterpret_cast<float2*>(smem_raw);
+        for (int64_t i = threadIdx.x; i < n + GEMV_SMEM_PAD; i += blockDim.x) {
+            float2 v = make_float2(0.f, 0.f);
+            if (i < n) df_split(x[i * incx], v);
+            xw[i] = v;
+        }
+        __syncthreads();
+        xs = xw;
+    } else {
+        xs = xg;  // n + GEMV_SMEM_PAD entries, 16-byte aligned
+    }
+    const float4* xs4 = reinterpret_cast<const float4*>(xs);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t row = (int64_t)blockIdx.x * GEMV_SMEM_WARPS + warp; row < n; row += (int64_t)gridDim.x * GEMV_SMEM_WARPS) {
+        const float2* a = A + row * lda;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const int64_t p0 = (((uintptr_t)a & 15u) != 0) ? 1 : 0;  // rows start 8-byte aligned
+        if (lane < p0) {
+            const float2 av = a[0], xv = xs[0];
+            df_fma(acc[0], acc[1], av.x, av.y, xv.x, xv.y);
+        }
+        const int64_t nv = (n - p0) / 2;  // 16-byte chunks: two entries
+        const int64_t rot = nv > 0 ? (int64_t)(((uint64_t)row * 2654435761ull) % (uint64_t)nv) : 0;
+        const uint4* a4 = reinterpret_cast<const uint4*>(a + p0);
+        if (p0) gemv_x2_chunks<1>(a4, xs4, nv, rot, lane, acc);
+        else gemv_x2_chunks<0>(a4, xs4, nv, rot, lane, acc);
+        for (int64_t j = p0 + 2 * nv + lane; j < n; j += 32) {
+            const float2 av = a[j], xv = xs[j];
+            df_fma(acc[0], acc[1], av.x, av.y, xv.x, xv.y);
+        }
+        const double t = warp_sum(((double)acc[0] + (double)acc[1]) + ((double)acc[2] + (double)acc[3]));
+        if (lane == 0) y[row * incy] = t;
+    }
+}
+
+// x split into (hi, lo) float32 pairs, zero padded (the unstaged product's copy of x)
+__global__ void x2_split_kernel(int64_t n, const double* x, int64_t incx, float2* out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n + GEMV_SMEM_PAD) return;
+    float2 v = make_float2(0.f, 0.f);
+    if (i < n) df_split(x[i * incx], v);
+    out[i] = v;
+}
+
+// grid of the staged hi + lo product (0 when x does not fit), as gemv_smem_grid
+static unsigned gemv_x2_grid(int64_t n) {
+    const size_t smem = (size_t)(n + GEMV_SMEM_PAD) * sizeof(float2);
+    if (smem > GEMV_SMEM_MAX) return 0;
+    static thread_local int ready = 0, sms = 0, dev_cached = -1;
+    static thread_local int64_t n_cached = -1;
+    static thread_local unsigned grid_cached = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (ready && dev == dev_cached && n == n_cached) return grid_cached;
+    if (!ready || dev != dev_cached) {
+        if (cudaFuncSetAttribute(gemv_x2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMV_SMEM_MAX) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        ready = 1;
+        dev_cached = dev;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemv_x2_kernel<true>, 32 * GEMV_SMEM_WARPS, smem) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    grid_cached = (unsigned)std::min<int64_t>((n + GEMV_SMEM_WARPS - 1) / GEMV_SMEM_WARPS, (int64_t)sms * per_sm);
+    n_cached = n;
+    return grid_cached;
+}
+
+__global__ void convert_x2_kernel(int64_t n, const double* A, int64_t lda, float2* B, int64_t ldb) {
+    for (int64_t i = blockIdx.y; i < n; i += gridDim.y)
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+            const double a = A[i * lda + j];
+            const float hi = (float)a;
+            B[i * ldb + j] = make_float2(hi, (float)(a - (double)hi));
+        }
+}
+
 __global__ void to_f32_kernel(int64_t n, const double* x, int64_t incx, float* y) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) y[i] = (float)x[i * incx];
@@ -368,6 +489,21 @@ static unsigned gemv_lo_smem_grid(int dtype, const void* A, int64_t n) {
 cudaError_t gemv(int dtype, const void* A, int64_t lda, int64_t n, const double* x, int64_t incx, double* y,
                  int64_t incy, float* xf, cudaStream_t st, bool xf_ready) {
     const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
+    if (dtype == FL_F32X2) {
+        const unsigned gs = gemv_x2_grid(n);
+        if (gs) {
+            gemv_x2_kernel<true><<<gs, 32 * GEMV_SMEM_WARPS, (n + GEMV_SMEM_PAD) * sizeof(float2), st>>>(
+                n, (const float2*)A, lda, x, incx, nullptr, y, incy);
+        } else {
+            // xf holds 2 (n + GEMV_SMEM_PAD) floats here (fl_matvec sizes it)
+            x2_split_kernel<<<(unsigned)((n + GEMV_SMEM_PAD + 255) / 256), 256, 0, st>>>(n, x, incx, (float2*)xf);
+            fl::count_launch();
+            gemv_x2_kernel<false><<<(unsigned)((n + GEMV_SMEM_WARPS - 1) / GEMV_SMEM_WARPS), 32 * GEMV_SMEM_WARPS, 0,
+                                    st>>>(n, (const float2*)A, lda, x, incx, (const float2*)xf, y, incy);
+        }
+        fl::count_launch();
+        return cudaGetLastError();
+    }
     if (dtype == FL_F64) {
         const unsigned gs = (((uintptr_t)A & 7u) == 0) ? gemv_smem_grid<double, double>(n) : 0u;
         if (gs) {
@@ -1496,10 +1632,15 @@ extern "C" {
 int fl_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, int nrhs, const double* X_dev, int64_t ldx,
               double* Y_dev, int64_t ldy, void* stream) {
     if (!A_dev || !X_dev || !Y_dev || n < 1 || nrhs < 1 || lda < n || ldx < nrhs || ldy < nrhs) return FL_EINVAL;
-    if (dtype != FL_F64 && dtype != FL_F32 && dtype != FL_BF16) return FL_EINVAL;
+    if (dtype != FL_F64 && dtype != FL_F32 && dtype != FL_BF16 && dtype != FL_F32X2) return FL_EINVAL;
+    if (dtype == FL_F32X2 && ((uintptr_t)A_dev & 7u) != 0) return FL_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    float* xf = nullptr;  // float32 copy of x, only for a low-precision matrix whose x does not fit the staging
-    if (dtype != FL_F64 && gemv_lo_smem_grid(dtype, A_dev, n) == 0) {
+    float* xf = nullptr;  // copy of x (float32, or hi + lo pairs), only where x does not fit the staging
+    if (dtype == FL_F32X2) {
+        if (gemv_x2_grid(n) == 0 &&
+            cudaMallocAsync((void**)&xf, (size_t)(n + GEMV_SMEM_PAD) * sizeof(float2), st) != cudaSuccess)
+            return FL_ENOMEM;
+    } else if (dtype != FL_F64 && gemv_lo_smem_grid(dtype, A_dev, n) == 0) {
         if (cudaMallocAsync((void**)&xf, n * sizeof(float), st) != cudaSuccess) return FL_ENOMEM;
     }
     for (int r = 0; r < nrhs; ++r) {
@@ -1578,7 +1719,11 @@ int fl_convert(const double* A_dev, int64_t lda, int64_t n, int dtype, void* A_l
     if (!A_dev || !A_lo_dev || n < 1 || lda < n || ld_lo < n) return FL_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)std::min<int64_t>(n, 65535));
-    if (dtype == FL_F32) { convert_kernel<float><<<grid, 256, 0, st>>>(n, A_dev, lda, (float*)A_lo_dev, ld_lo); fl::count_launch(); }
+    if (dtype == FL_F32X2) {
+        if (((uintptr_t)A_lo_dev & 7u) != 0) return FL_EINVAL;
+        convert_x2_kernel<<<grid, 256, 0, st>>>(n, A_dev, lda, (float2*)A_lo_dev, ld_lo);
+        fl::count_launch();
+    } else if (dtype == FL_F32) { convert_kernel<float><<<grid, 256, 0, st>>>(n, A_dev, lda, (float*)A_lo_dev, ld_lo); fl::count_launch(); }
     else if (dtype == FL_BF16) {
         convert_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(n, A_dev, lda, (__nv_bfloat16*)A_lo_dev, ld_lo);
         fl::count_launch();

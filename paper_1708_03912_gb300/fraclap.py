@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libfraclap.so")
 FL_OK, FL_EINVAL, FL_ENOMEM, FL_ECUDA, FL_ENOTSPD, FL_ENOTCONV, FL_ETIMEOUT, FL_ENOTIMPL = range(8)
 FL_DOF_INTERIOR, FL_DOF_PAPER = 0, 1
 FL_FP64, FL_MIXED = 0, 1
-FL_F64, FL_F32, FL_BF16 = 0, 1, 2
+FL_F64, FL_F32, FL_BF16, FL_F32X2 = 0, 1, 2, 3
 _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOTSPD", 5: "FL_ENOTCONV",
           6: "FL_ETIMEOUT", 7: "FL_ENOTIMPL"}
 
@@ -315,16 +315,22 @@ def fl_load_vector(h, s, f_nodal, b, stream=None):
     _check(lib().fl_load_vector(h, s, fp, nrhs, _ptr(b), ldb, _stream(stream)), h)
 
 
+def _ld(dtype, M):
+    # leading dimension in entries: an FL_F32X2 entry is two float32 values
+    return M.stride(0) // 2 if dtype == FL_F32X2 else M.stride(0)
+
+
 def fl_matvec(dtype, A, X, Y, stream=None):
+    """Y = A X; an FL_F32X2 matrix is a float32 tensor [n, 2 * lda] of (hi, lo) pairs."""
     n = A.shape[0]
     nrhs = X.shape[1] if X.dim() == 2 else 1
     ldx = X.stride(0) if X.dim() == 2 else 1
     ldy = Y.stride(0) if Y.dim() == 2 else 1
-    _check(lib().fl_matvec(dtype, _ptr(A), A.stride(0), n, nrhs, _ptr(X), ldx, _ptr(Y), ldy, _stream(stream)))
+    _check(lib().fl_matvec(dtype, _ptr(A), _ld(dtype, A), n, nrhs, _ptr(X), ldx, _ptr(Y), ldy, _stream(stream)))
 
 
 def fl_convert(A, dtype, out, stream=None):
-    _check(lib().fl_convert(_ptr(A), A.stride(0), A.shape[0], dtype, _ptr(out), out.stride(0), _stream(stream)))
+    _check(lib().fl_convert(_ptr(A), A.stride(0), A.shape[0], dtype, _ptr(out), _ld(dtype, out), _stream(stream)))
 
 
 def fl_default_solve_opts():

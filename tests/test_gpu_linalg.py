@@ -55,6 +55,46 @@ def test_matvec_padded_rows():
             assert np.allclose(Y.cpu().numpy(), ref, rtol=tol, atol=tol * np.sqrt(n))
 
 
+def test_f32x2_storage_and_product():
+    # hi + lo float32 storage: bit-exact against the oracle's split; the double-float product
+    # within 2^-40 of sum_j |a_ij x_j| of the float64 product, for 16-byte aligned rows, rows
+    # drifting across the boundary (odd leading dimension), and an x too long to stage
+    from oracle.lowprec import f32x2_product, f32x2_split
+
+    g = torch.Generator(device="cpu").manual_seed(12)
+    for n, lda in ((1, 1), (1000, 1000), (777, 781)):
+        Af = torch.randn(n, lda, generator=g, dtype=torch.float64)
+        A = Af[:, :n]
+        X = torch.randn(n, 2, generator=g, dtype=torch.float64)
+        A2 = torch.zeros(n, 2 * lda, dtype=torch.float32, device="cuda")  # (hi, lo) pairs, ld = lda
+        Ad = Af.cuda()[:, :n]
+        F.fl_convert(Ad, F.FL_F32X2, A2[:, :2 * n])
+        hi, lo = f32x2_split(A.numpy())
+        got = A2[:, :2 * n].cpu().numpy().reshape(n, n, 2)
+        assert np.array_equal(got[..., 0], hi) and np.array_equal(got[..., 1], lo)
+        Y = torch.empty(n, 2, dtype=torch.float64, device="cuda")
+        F.fl_matvec(F.FL_F32X2, A2[:, :2 * n], X.cuda(), Y)
+        ref = f32x2_product(hi, lo, X.numpy())
+        bound = 2.0 ** -40 * (np.abs(A.numpy()) @ np.abs(X.numpy()))
+        assert np.all(np.abs(Y.cpu().numpy() - ref) <= bound)
+    # x beyond the shared-memory staging (25593 entries): sampled rows
+    n = 25600
+    gc = torch.Generator(device="cuda").manual_seed(13)
+    Ad = torch.randn(n, n, generator=gc, dtype=torch.float64, device="cuda")
+    A2 = torch.empty(n, 2 * n, dtype=torch.float32, device="cuda")
+    F.fl_convert(Ad, F.FL_F32X2, A2)
+    x = torch.randn(n, 1, generator=gc, dtype=torch.float64, device="cuda")
+    y = torch.empty(n, 1, dtype=torch.float64, device="cuda")
+    F.fl_matvec(F.FL_F32X2, A2, x, y)
+    rows = synth.random_rows(n, 16)
+    Ar = Ad[rows].cpu().numpy()
+    hi, lo = f32x2_split(Ar)
+    ref = f32x2_product(hi, lo, x.cpu().numpy())
+    bound = 2.0 ** -40 * (np.abs(Ar) @ np.abs(x.cpu().numpy()))
+    assert np.all(np.abs(y.cpu().numpy()[rows] - ref) <= bound)
+    del Ad, A2
+
+
 def test_matvec_autotuner_records_and_is_used():
     # the tuner sweeps blocks per SM of the staged product, records the fastest, and the
     # product taken with the recorded shape is still the product
