@@ -161,8 +161,9 @@ int fl_load_vector(fl_handle h, double s, const double* f_nodal_dev, int nrhs,
  * (>= nrhs).  Accumulation in float64 (FL_F64), float32 with float64 per-row totals
  * (FL_F32, FL_BF16), or double-float on the float32 pipe (FL_F32X2: x split into
  * float32 hi + lo, error about 2^-44 of sum_j |a_ij x_j|).  Streams A once per call;
- * allocates nothing while x fits the shared-memory staging (25k entries for FL_F64 and
- * FL_F32X2, 51k for FL_F32 and FL_BF16).  FL_EINVAL for an FL_F32X2 matrix that is not
+ * stages x in shared memory (no allocation) while at least two 8-warp blocks per SM
+ * fit with it (x up to about 12k entries for FL_F64 and FL_F32X2, 25k for FL_F32 and
+ * FL_BF16); beyond that float32 / bfloat16 / hi + lo products allocate a copy of x.  FL_EINVAL for an FL_F32X2 matrix that is not
  * 8-byte aligned.
  */
 int fl_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, int nrhs,
@@ -472,7 +473,8 @@ int fl_tune_batch(fl_handle h, int nprob, const fl_batch_problem* probs, int rep
  * timings after a warm-up, on `stream`; records the fastest under ("gemv_smem_f64" |
  * "gemv_smem_f32", n) for this device, which fl_matvec then uses.  x_dev, y_dev: [n]
  * float64 (y is overwritten).  *best_per_sm, *best_ms (host, may be NULL) get the choice.
- * Errors: FL_EINVAL (bad arguments), FL_ENOTIMPL (x too large to stage), FL_ECUDA.
+ * Errors: FL_EINVAL (bad arguments), FL_ENOTIMPL (the staged product is not used at this
+ * size: x too large to stage, or fewer than two blocks per SM fit), FL_ECUDA.
  */
 int fl_tune_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, const double* x_dev,
                    double* y_dev, int reps, int* best_per_sm, double* best_ms, void* stream);

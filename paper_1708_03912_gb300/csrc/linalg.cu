@@ -168,6 +168,30 @@ __device__ __forceinline__ Acc to_acc(TA v) {
 }
 
 constexpr int GEMV_SMEM_WARPS = 8;
+// grids of the staged products for the last few sizes (per host thread and kernel)
+struct GemvGridCache {
+    static constexpr int K = 8;
+    int64_t n[K] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    unsigned gen[K] = {}, grid[K] = {};
+    int next = 0;
+    bool find(int64_t nn, unsigned g, unsigned* out) const {
+        for (int k = 0; k < K; ++k)
+            if (n[k] == nn && gen[k] == g) {
+                *out = grid[k];
+                return true;
+            }
+        return false;
+    }
+    void put(int64_t nn, unsigned g, unsigned gr) {
+        n[next] = nn;
+        gen[next] = g;
+        grid[next] = gr;
+        next = (next + 1) % K;
+    }
+    void clear() {
+        for (int k = 0; k < K; ++k) n[k] = -1;
+    }
+};
 // tuning-table names of the staged products
 template <typename TA>
 struct GemvName;
@@ -303,16 +327,18 @@ template <typename TA, typename TX>
 static unsigned gemv_smem_grid(int64_t n, int force_per_sm = 0, int* max_per_sm = nullptr) {
     const size_t smem = (size_t)(n + GEMV_SMEM_PAD) * sizeof(TX);
     if (smem > GEMV_SMEM_MAX) return 0;
-    // per host thread (no locking): the attribute is set once per thread and device
+    // per host thread (no locking): the attribute is set once per thread and device; the grids
+    // of the last few sizes are kept, so that solvers alternating between levels of different
+    // size (multigrid) make no driver query per product
     static thread_local int ready = 0, sms = 0, dev_cached = -1;
-    static thread_local int64_t n_cached = -1;
-    static thread_local unsigned grid_cached = 0, gen_cached = 0;
+    static thread_local GemvGridCache cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     const unsigned gen = tune_generation();
-    if (!force_per_sm && !max_per_sm && ready && dev == dev_cached && n == n_cached && gen == gen_cached)
-        return grid_cached;  // no driver query per product
+    unsigned hit = 0;
+    if (!force_per_sm && !max_per_sm && ready && dev == dev_cached && cache.find(n, gen, &hit)) return hit;
     if (!ready || dev != dev_cached) {
+        cache.clear();
         if (cudaFuncSetAttribute(gemv_smem_kernel<TA, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)GEMV_SMEM_MAX) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -331,13 +357,18 @@ static unsigned gemv_smem_grid(int64_t n, int force_per_sm = 0, int* max_per_sm 
     if (max_per_sm) *max_per_sm = per_sm;
     const int64_t want = (n + GEMV_SMEM_WARPS - 1) / GEMV_SMEM_WARPS;
     if (force_per_sm) return (unsigned)std::min<int64_t>(want, (int64_t)sms * std::min(force_per_sm, per_sm));
-    // blocks per SM from the matvec autotuner (fl_tune_matvec) when it has measured this size
-    int p0 = 0, p1 = 0;
-    if (tune_lookup(device_name(), GemvName<TA>::name, n, 1, 1, &p0, &p1) && p0 >= 1) per_sm = std::min(per_sm, p0);
-    grid_cached = (unsigned)std::min<int64_t>(want, (int64_t)sms * per_sm);
-    n_cached = n;
-    gen_cached = gen;
-    return grid_cached;
+    unsigned grid = 0;
+    // with one block (8 warps) per SM too few loads are in flight: the warp-per-row kernels,
+    // which keep x in L1/L2, are used instead
+    if (per_sm >= 2) {
+        // blocks per SM from the matvec autotuner (fl_tune_matvec) when it has measured this size
+        int p0 = 0, p1 = 0;
+        if (tune_lookup(device_name(), GemvName<TA>::name, n, 1, 1, &p0, &p1) && p0 >= 1)
+            per_sm = std::min(per_sm, p0);
+        grid = (unsigned)std::min<int64_t>(want, (int64_t)sms * per_sm);
+    }
+    cache.put(n, gen, grid);
+    return grid;
 }
 
 // Hi + lo float32 storage (FL_F32X2): entry (i, j) is the float2 (hi, lo), hi = fl32(a),
@@ -425,12 +456,13 @@ static unsigned gemv_x2_grid(int64_t n) {
     const size_t smem = (size_t)(n + GEMV_SMEM_PAD) * sizeof(float2);
     if (smem > GEMV_SMEM_MAX) return 0;
     static thread_local int ready = 0, sms = 0, dev_cached = -1;
-    static thread_local int64_t n_cached = -1;
-    static thread_local unsigned grid_cached = 0;
+    static thread_local GemvGridCache cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (ready && dev == dev_cached && n == n_cached) return grid_cached;
+    unsigned hit = 0;
+    if (ready && dev == dev_cached && cache.find(n, 0u, &hit)) return hit;
     if (!ready || dev != dev_cached) {
+        cache.clear();
         if (cudaFuncSetAttribute(gemv_x2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMV_SMEM_MAX) !=
                 cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -447,9 +479,11 @@ static unsigned gemv_x2_grid(int64_t n) {
         cudaGetLastError();
         return 0;
     }
-    grid_cached = (unsigned)std::min<int64_t>((n + GEMV_SMEM_WARPS - 1) / GEMV_SMEM_WARPS, (int64_t)sms * per_sm);
-    n_cached = n;
-    return grid_cached;
+    // one block per SM keeps too few loads in flight: the unstaged kernel is used then
+    const unsigned grid =
+        per_sm >= 2 ? (unsigned)std::min<int64_t>((n + GEMV_SMEM_WARPS - 1) / GEMV_SMEM_WARPS, (int64_t)sms * per_sm) : 0u;
+    cache.put(n, 0u, grid);
+    return grid;
 }
 
 __global__ void convert_x2_kernel(int64_t n, const double* A, int64_t lda, float2* B, int64_t ldb) {
@@ -1658,8 +1692,9 @@ int fl_tune_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, const d
     cudaStream_t st = (cudaStream_t)stream;
     int max_per_sm = 0;
     const bool f64 = dtype == FL_F64;
-    if ((f64 ? gemv_smem_grid<double, double>(n, 0, &max_per_sm) : gemv_smem_grid<float, float>(n, 0, &max_per_sm)) == 0)
-        return FL_ENOTIMPL;  // x does not fit the shared-memory staging: nothing to tune
+    if ((f64 ? gemv_smem_grid<double, double>(n, 0, &max_per_sm) : gemv_smem_grid<float, float>(n, 0, &max_per_sm)) == 0 ||
+        max_per_sm < 2)
+        return FL_ENOTIMPL;  // the staged product is not used at this size: nothing to tune
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return FL_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
