@@ -153,14 +153,7 @@ __global__ void gemv_lo_kernel(int64_t n, const TA* __restrict__ A, int64_t lda,
     if (lane == 0) y[row * incy] = t;
 }
 
-// The same products with x staged in shared memory once per block (8 warps, warp per row,
-// row = block * 8 + warp with stride grid * 8), so x is read from L2 once per block instead
-// of once per row.  A row starting off a 16-byte boundary peels its first elements; the x
-// entries that go with a 16-byte chunk of A are then read as 16-byte words of the staged
-// copy and shifted in registers (a compile-time shift per row alignment), which keeps the
-// shared-memory reads free of bank conflicts.  Each row starts its chunk loop at a
-// row-dependent rotation, so the warps streaming neighbouring rows (a fixed stride apart)
-// do not all address the same memory channels at once.
+// a matrix entry in the accumulator's type
 template <typename Acc, typename TA>
 __device__ __forceinline__ Acc to_acc(TA v) {
     if constexpr (std::is_same<TA, __nv_bfloat16>::value) return (Acc)__bfloat162float(v);
@@ -210,6 +203,14 @@ struct GemvName<__nv_bfloat16> {
 constexpr size_t GEMV_SMEM_MAX = 200 * 1024;  // bytes of staged x (padding included)
 constexpr int GEMV_SMEM_PAD = 8;               // zero elements after x: shifted reads stay in bounds
 
+// The same products with x staged in shared memory once per block (8 warps, warp per row,
+// row = block * 8 + warp with stride grid * 8), so x is read from L2 once per block instead
+// of once per row.  A row starting off a 16-byte boundary peels its first elements; the x
+// entries that go with a 16-byte chunk of A are then read as 16-byte words of the staged
+// copy and shifted in registers (a compile-time shift per row alignment), which keeps the
+// shared-memory reads free of bank conflicts.  Each row starts its chunk loop at a
+// row-dependent rotation, so the warps streaming neighbouring rows (a fixed stride apart)
+// do not all address the same memory channels at once.
 // four floats of x starting at element 4 c + SH (c counted in float4 words)
 template <int SH>
 __device__ __forceinline__ float4 x4_at(const float4* xs4, int64_t c) {
