@@ -86,7 +86,9 @@ void fl_default_options(fl_options* opt);
  * The arrays are copied.  Cells are re-oriented (counter-clockwise / left-to-right).
  * Boundary facets are the facets owned by exactly one cell.  The host planner runs
  * here (classification of element pairs, tables); device tables are uploaded lazily
- * by the first device call.  opt may be NULL (defaults).
+ * by the first device call.  opt may be NULL (defaults).  A handle serves one host
+ * thread at a time, and its device calls share the handle's workspace: calls on one
+ * handle enqueued on different streams must not overlap on the GPU.
  * Errors: FL_EINVAL for dim not in {1,2}, indices out of range, degenerate cells,
  * edges shared by more than two triangles, dof_mode unknown, orders outside [1,32].
  */

@@ -1823,7 +1823,10 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
     // so that each event pair brackets one stage alone.
     cudaStream_t sst = st;
     if (!h->profiling) {
-        if (!h->side && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) h->side = nullptr;
+        if (!h->side && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();  // no second stream: the stages run in sequence on the caller's
+            h->side = nullptr;
+        }
         if (h->side && !h->ev_fork) {
             if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
