@@ -234,3 +234,38 @@ def test_load_vector_nodal_one_equals_f1():
     # Σ_i ∫phi_i over all vertices is |Ω|
     bp = load_vector(m, 0.3, dof_mode="paper")
     assert abs(bp.sum() - m.vol.sum()) < 1e-13
+
+
+def test_load_vector_nodal_against_midpoint_rules():
+    # b_i = ∫ f_h phi_i with f_h the P1 interpolant: the integrand is quadratic on each cell,
+    # so the edge-midpoint rule on triangles (|K|/3 times the sum over the three edge
+    # midpoints) and Simpson's rule on intervals integrate it exactly; neither uses the
+    # mass-matrix formula of the oracle
+    rng = np.random.default_rng(20170813)
+    m = OracleMesh(*synth.disc(5))
+    f = rng.standard_normal(m.nv)
+    vod, dov = m.dofs(0.5)
+    b = np.zeros(len(vod))
+    for k in range(m.nc):
+        cell = m.C[k]
+        for a in range(3):
+            for c in range(a + 1, 3):
+                fm = 0.5 * (f[cell[a]] + f[cell[c]])  # f_h at the midpoint of edge (a, c)
+                for v in (cell[a], cell[c]):          # phi_v = 1/2 there, the third hat is 0
+                    if dov[v] >= 0:
+                        b[dov[v]] += m.vol[k] / 3.0 * fm * 0.5
+    assert np.abs(load_vector(m, 0.5, f) - b).max() < 1e-14 * np.abs(b).max()
+    # 1D: Simpson on every cell
+    V, T = synth.graded_interval(20, 1.5)
+    m1 = OracleMesh(V, T)
+    f1 = rng.standard_normal(m1.nv)
+    vod1, dov1 = m1.dofs(0.5)
+    b1 = np.zeros(len(vod1))
+    for k in range(m1.nc):
+        i, j = m1.C[k]
+        h = abs(m1.V[j, 0] - m1.V[i, 0])
+        fm = 0.5 * (f1[i] + f1[j])
+        for v, fv in ((i, f1[i]), (j, f1[j])):   # phi_v: 1 at v, 1/2 at the midpoint, 0 at the other end
+            if dov1[v] >= 0:
+                b1[dov1[v]] += h / 6.0 * (fv * 1.0 + 4.0 * fm * 0.5)
+    assert np.abs(load_vector(m1, 0.5, f1) - b1).max() < 1e-14 * np.abs(b1).max()
