@@ -25,6 +25,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the oracle's numpy runs with the thread count reported as cpu_baseline's cores (one unless the
+# caller sets OMP_NUM_THREADS); set before numpy's BLAS is loaded
+for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, os.environ.get("OMP_NUM_THREADS", "1"))
 
 WORKLOAD = {"workload": "disc-quasi-uniform-25-rings", "domain": "unit disc", "rings": 25, "triangles": 3929,
             "dofs": 1887, "s": 0.75, "f": "1", "dtype_assembly": "f32 separated pairs + f64 near/boundary",
