@@ -139,3 +139,15 @@ def test_nearfield_csr_size_query_matches_oracle_pattern():
         assert nnz.value == F.fl_get_stats(h, s)["nnz_nearfield"]
         assert F.lib().fl_assemble_nearfield_csr(h, s, F.FL_FP64, None, None, None, None, None) == F.FL_EINVAL
         F.fl_destroy(h)
+
+
+def test_header_constants_match_binding():
+    # every #define of include/fraclap.h that the binding mirrors has the same value there
+    text = open(HEADER).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define (FL_[A-Z0-9_]+)\s+(-?\d+)", text, re.M)}
+    mirrored = [k for k in defs if hasattr(F, k)]
+    assert len(mirrored) >= 20
+    for k in mirrored:
+        assert getattr(F, k) == defs[k], k
+    assert F.STAGES == ["prep", "far", "near", "touch", "bnd", "element", "compose"]
+    assert len(F.STAGES) == defs["FL_NSTAGES"]
