@@ -151,3 +151,26 @@ def test_header_constants_match_binding():
         assert getattr(F, k) == defs[k], k
     assert F.STAGES == ["prep", "far", "near", "touch", "bnd", "element", "compose"]
     assert len(F.STAGES) == defs["FL_NSTAGES"]
+
+
+@pytest.mark.parametrize("mesh", ["interval", "disc", "square", "lshape"])
+def test_planner_pair_classes_match_oracle(mesh):
+    # the host planner's counts of unordered element pairs with a DOF on either side, by class
+    # (touching, separated at vertex-graph distance 1, farther), equal the oracle's
+    _lib_or_skip()
+    V, T = {"interval": synth.interval(20), "disc": synth.disc(6), "square": synth.square(5, 0.2),
+            "lshape": synth.lshape(0.25, 0)}[mesh]
+    om = OracleMesh(V, T)
+    for s in (0.3, 0.6):
+        _, dov = om.dofs(s)
+        has = (dov[om.C] >= 0).any(axis=1)
+        counts = np.zeros(3, dtype=np.int64)
+        for k in range(om.nc):
+            shared, near = om.classify_cells(k)
+            m = np.arange(k + 1, om.nc)
+            m = m[has[k] | has[m]]
+            counts += [(shared[m] > 0).sum(), ((shared[m] == 0) & near[m]).sum(), ((shared[m] == 0) & ~near[m]).sum()]
+        h = F.fl_create(V, T)
+        st = F.fl_get_stats(h, s)
+        F.fl_destroy(h)
+        assert (st["n_touch_pairs"], st["n_near_pairs"], st["n_far_pairs"]) == tuple(counts)
