@@ -157,16 +157,19 @@ int fl_load_vector(fl_handle h, double s, const double* f_nodal_dev, int nrhs,
                    double* b_dev, int64_t ldb, void* stream);
 
 /*
- * Y = A X for a dense n x n matrix stored as dtype (FL_F64 / FL_F32 / FL_BF16 /
- * FL_F32X2) with leading dimension lda (in entries; an FL_F32X2 entry is a float2);
+ * The dense matrix-vector product of the iterative solvers (Section 5: n^2 work per
+ * product).  Y = A X for a dense n x n matrix stored as dtype (FL_F64 / FL_F32 / FL_BF16 /
+ * FL_F32X2; the low-precision storages are not in the paper) with leading dimension lda
+ * (in entries; an FL_F32X2 entry is a float2);
  * X_dev, Y_dev are [n][nrhs] float64 row-major with leading dimensions ldx, ldy
  * (>= nrhs).  Accumulation in float64 (FL_F64), float32 with float64 per-row totals
  * (FL_F32, FL_BF16), or double-float on the float32 pipe (FL_F32X2: x split into
  * float32 hi + lo, error about 2^-44 of sum_j |a_ij x_j|).  Streams A once per call;
  * stages x in shared memory (no allocation) while at least two 8-warp blocks per SM
  * fit with it (x up to about 12k entries for FL_F64 and FL_F32X2, 25k for FL_F32 and
- * FL_BF16); beyond that float32 / bfloat16 / hi + lo products allocate a copy of x.  FL_EINVAL for an FL_F32X2 matrix that is not
- * 8-byte aligned.
+ * FL_BF16); beyond that float32 / bfloat16 / hi + lo products allocate a copy of x.
+ * Errors: FL_EINVAL (NULL pointers, n < 1, a leading dimension too small, an unknown
+ * dtype, an FL_F32X2 matrix that is not 8-byte aligned), FL_ENOMEM, FL_ECUDA.
  */
 int fl_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, int nrhs,
               const double* X_dev, int64_t ldx, double* Y_dev, int64_t ldy, void* stream);
