@@ -166,6 +166,63 @@ def run_reference(args):
     return 0
 
 
+def build_problems(F, synth, m, svals, nrhs, nslices, V):
+    """Batched-solve problems on mesh m: for every s the mixed-mode matrix, its bf16 slices and
+    f = 1 plus nrhs - 1 seeded Gaussian nodal loads."""
+    import torch
+
+    f = torch.tensor(synth.gaussian_nodal(len(V), nrhs - 1, seed=synth.SEED + 1), device="cuda") if nrhs > 1 else None
+    probs = []
+    for s in svals:
+        n = m.num_dofs(s)
+        A = m.assemble(s, "mixed")
+        S, d = F.split_bf16(A, nslices)
+        B = torch.empty((n, nrhs), dtype=torch.float64, device="cuda")
+        F.fl_load_vector(m.h, s, None, B[:, :1])
+        if nrhs > 1:
+            F.fl_load_vector(m.h, s, f, B[:, 1:])
+        probs.append({"A": A, "S": S, "nslices": nslices, "dscale": d, "B": B, "U": torch.empty_like(B)})
+    return probs
+
+
+# small named workloads for profilers (`--case`): rings, grading exponent, s
+CASES = {"disc25": (25, 1.0, 0.75), "gdisc30": (30, 2.0, 0.75), "disc10": (10, 1.0, 0.75)}
+
+
+def run_case(args):
+    """One untimed warm-up step and `--steps` profiled steps of assemble -> float32 copy -> load
+    vector -> refined Jacobi-PCG on a small named disc workload; prints the stage times."""
+    import torch
+
+    from paper_1708_03912_gb300 import fraclap as F
+    from paper_1708_03912_gb300 import synth
+
+    M, mu, s = CASES[args.case]
+    V, T = synth.disc(M, mu)
+    m = F.Mesh(V, T)
+    n = m.num_dofs(s)
+    A = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    A32 = torch.empty((n, n), dtype=torch.float32, device="cuda")
+
+    def step():
+        m.assemble(s, args.precision, out=A)
+        if not args.no_solve:
+            F.fl_convert(A, F.FL_F32, A32)
+            b = m.load_vector(s)
+            m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3)
+
+    step()
+    F.fl_set_profiling(m.h, True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    st = F.fl_stage_ms(m.h)
+    print(f"case {args.case}: cells {len(T)} dofs {n} precision {args.precision}; stage ms " +
+          " ".join(f"{k}={v:.3f}" for k, v in st.items()))
+    m.close()
+    return 0
+
+
 def lshape_section(F, synth, timed, dev):
     """L-shape level LSHAPE["level"] (s = 1/2): Jacobi-PCG, multigrid-preconditioned CG on the nested
     levels below it, and flexible CG with the learned stencil trained on a coarser level."""
@@ -235,9 +292,15 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune-file", default=None, help="load/save the autotuner's table (JSON)")
+    ap.add_argument("--case", default=None, choices=sorted(CASES),
+                    help="profiling mode: run a small named workload and print stage times (no JSON line)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="assembly precision of --case")
+    ap.add_argument("--no-solve", action="store_true", help="--case: assembly only")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args)
 
     import numpy as np
     import torch
@@ -370,11 +433,9 @@ def main():
     _, infmx = m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3)
 
     # ---- batched: 4 orders x 64 right-hand sides on the graded disc (n = 8195) ----
-    from paper_1708_03912_gb300.profile_batch import build_problems
-
     Vg, Tg = synth.disc(BATCH["rings"], BATCH["mu"])
     mg = F.Mesh(Vg, Tg)
-    probs = build_problems(mg, BATCH["s"], BATCH["nrhs"], 2, Vg)
+    probs = build_problems(F, synth, mg, BATCH["s"], BATCH["nrhs"], 2, Vg)
     # launch shape of the tensor-core product from the project's autotuner (persisted if asked)
     if args.tune_file and os.path.exists(args.tune_file):
         F.fl_tune_load(args.tune_file)

@@ -191,6 +191,9 @@ typedef struct fl_solve_opts {
                           whose residual is already within a factor 1/inner_tol of the
                           target uses max(inner_tol, tol ||b|| / (2 ||b - A u||)) */
     int inner_maxit;   /* default 2000 */
+    int barrier_timeout_us; /* bound of each grid-barrier wait of the cooperative solvers, in
+                          microseconds (0: the default of 2 s); a wait that runs out makes
+                          the call return FL_ETIMEOUT and leaves the handle usable */
 } fl_solve_opts;
 
 typedef struct fl_solve_info {
@@ -218,7 +221,8 @@ void fl_default_solve_opts(fl_solve_opts* o);
  * message.  info (host) receives counts and the final residual ||b - A u|| /
  * ||b||, computed in float64 with A.  Synchronises `stream`.  Returns FL_OK,
  * FL_ENOTCONV, FL_ENOTSPD, FL_EINVAL, FL_ENOMEM, FL_ECUDA, or FL_ETIMEOUT when a
- * grid barrier of a cooperative launch waited longer than its bound (2 s).
+ * grid barrier of a cooperative launch waited longer than its bound
+ * (o->barrier_timeout_us, default 2 s).
  */
 int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const double* b_dev, double* u_dev,
              const fl_solve_opts* o, fl_solve_info* info, void* stream);
@@ -292,6 +296,11 @@ typedef struct fl_batch_opts {
     int inner_maxit;   /* default 5000 */
     int ctas;          /* CTAs of the persistent kernel (0: one per SM) */
     int stages;        /* TMA pipeline depth (0: as many as shared memory holds) */
+    int barrier_timeout_us; /* bound of each grid-barrier wait of the persistent kernel, in
+                          microseconds (0: 2 s); a wait that runs out makes the call return
+                          FL_ETIMEOUT.  The waits on the copy and tensor-core pipeline keep
+                          their fixed 2 s bound: a CTA drains its own copies in flight with
+                          that bound before it exits */
     int residual;      /* FL_RESID_DF (default): B - A U in double-float arithmetic on the float32
                           pipe (about 2^-47 relative per operand and operation, so each residual
                           entry is exact to about 2^-46 (|A||u|)_i); FL_RESID_F64: float64 FMA,
@@ -564,11 +573,16 @@ void fl_pool_stats(int64_t* cached_device_bytes, int64_t* cached_host_bytes, int
  * y_dev float64 device vectors (contiguous).  Same arithmetic as fl_matvec with
  * FL_F32: x rounded to float32, float32 lane sums, float64 row totals.
  * Returns FL_EINVAL for n < 1 or n > FL_STATIC_MAX_N (nothing is launched), for
- * NULL pointers or lda < n; FL_ECUDA if the device array cannot be located or a
- * launch fails.  Calls no allocator.
+ * NULL pointers or lda < n; FL_ECUDA if the device array cannot be located, if a
+ * CUDA error was already pending on the calling thread when the call began (it is
+ * reported, not cleared, and nothing is launched), or if one of the two launches
+ * fails.  Calls no allocator.
  * The first call on each device looks up that device's copy of the array
- * (cudaGetSymbolAddress) with the device current; make that first call before any
- * stream capture.  All calls on a device share the one array and each call
+ * (cudaGetSymbolAddress) with the device current and keeps the address for the rest
+ * of the process; make that first call before any stream capture.  The kept address
+ * does not survive cudaDeviceReset (or any other destruction of the device's
+ * primary context): do not call this entry point on a device after resetting it.
+ * All calls on a device share the one array and each call
  * rewrites the n entries it reads, so nothing has to be cleared between calls, but
  * calls that overlap on the GPU (different streams, or different host threads)
  * race on it: serialise them.

@@ -78,6 +78,7 @@ struct Params {
     double tol2;
     float* slots;    // [G][rmax][nrmax][128] per-run partial products
     unsigned* gbar;  // grid barrier arrival counter (own cache line, zero at launch)
+    unsigned long long barrier_ns;  // bound of each grid-barrier wait
     int* err;        // bit 0: mbarrier timeout, 1: run-slot overflow, 2: grid barrier timeout
     int* ndone;      // [MAXP] finished columns per problem
     int* active;     // [MAXP] (GEMM-only launches): problem takes part
@@ -651,12 +652,12 @@ __global__ void __launch_bounds__(THREADS, 1) cg_kernel(const __grid_constant__ 
         plan_phase(s, P, G, true);
         if (s.na == 0) break;
         gemm_phase(s, P, blockIdx.x, ro);
-        if (!tc::grid_barrier(P.gbar, epoch, G, P.err) || __ldcg(P.err) != 0) break;
+        if (!tc::grid_barrier(P.gbar, epoch, G, P.err, P.barrier_ns) || __ldcg(P.err) != 0) break;
         const int W = G * (THREADS / 32), gw = blockIdx.x * (THREADS / 32) + (threadIdx.x >> 5);
         vec_phase_x(s, P, gw, W);
-        if (!tc::grid_barrier(P.gbar, epoch, G, P.err) || __ldcg(P.err) != 0) break;
+        if (!tc::grid_barrier(P.gbar, epoch, G, P.err, P.barrier_ns) || __ldcg(P.err) != 0) break;
         vec_phase_y(s, P, gw, W, it);
-        if (!tc::grid_barrier(P.gbar, epoch, G, P.err) || __ldcg(P.err) != 0) break;
+        if (!tc::grid_barrier(P.gbar, epoch, G, P.err, P.barrier_ns) || __ldcg(P.err) != 0) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *P.iters = it;
     __syncthreads();
@@ -1423,6 +1424,7 @@ void fl_default_batch_opts(fl_batch_opts* o) {
     o->inner_maxit = 5000;
     o->ctas = 0;
     o->stages = 0;
+    o->barrier_timeout_us = 0;
     o->residual = FL_RESID_DF;
 }
 
@@ -1434,7 +1436,7 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
     fl_batch_opts o;
     fl_default_batch_opts(&o);
     if (o_in) o = *o_in;
-    if (!(o.tol > 0) || !(o.inner_tol > 0) || o.max_outer < 1 || o.inner_maxit < 1 ||
+    if (!(o.tol > 0) || !(o.inner_tol > 0) || o.max_outer < 1 || o.inner_maxit < 1 || o.barrier_timeout_us < 0 ||
         (o.residual != FL_RESID_F64 && o.residual != FL_RESID_DF))
         return set_err(h, FL_EINVAL, "bad batch options");
     for (int p = 0; p < nprob; ++p) {
@@ -1575,6 +1577,7 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
     P.slots = (float*)(W + off_slots);
     P.err = flags;
     P.gbar = (unsigned*)(W + off_bar);
+    P.barrier_ns = o.barrier_timeout_us > 0 ? 1000ull * (unsigned long long)o.barrier_timeout_us : 2000000000ull;
     P.ndone = flags + 8;
     P.active = flags + 24;
     P.iters = flags + 4;

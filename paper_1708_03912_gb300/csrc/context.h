@@ -111,6 +111,7 @@ struct fl_ctx {
     std::vector<fl::DBuf> bufs;
     int profiling = 0;
     int no_persistent = 0;  // 1: run CG as captured kernel batches instead of one cooperative launch
+    unsigned long long wait_ns = 2000000000ull;  // bound of a grid-barrier wait in the current solve
     cudaEvent_t ev[2 * FL_NSTAGES] = {};
     bool ev_made = false;
     bool ev_recorded = false;

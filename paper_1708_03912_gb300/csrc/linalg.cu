@@ -970,6 +970,7 @@ struct CgBlock {
     T *u, *r, *z, *p, *sv, *dv, *part;
     unsigned* gbar;
     int* err;
+    uint64_t wait_ns;  // bound of each grid-barrier wait
     T* sh;
     int nb, lane, warp;
 };
@@ -1017,7 +1018,7 @@ __device__ __forceinline__ bool cg_block_solve(const CgBlock<T>& c, const double
             c.part[R_ * 1024 + blockIdx.x] = v[1];
         }
     }
-    if (!tc::grid_barrier(c.gbar, epoch, nb, c.err)) return false;
+    if (!tc::grid_barrier(c.gbar, epoch, nb, c.err, c.wait_ns)) return false;
     T gamma, rr0;
     {
         T v[2];
@@ -1072,7 +1073,7 @@ __device__ __forceinline__ bool cg_block_solve(const CgBlock<T>& c, const double
         }
         block_totals<T, 1>(dl, sh);
         if (threadIdx.x == 0) c.part[D_ * 1024 + blockIdx.x] = dl[0];
-        if (!tc::grid_barrier(c.gbar, epoch, nb, c.err)) return false;
+        if (!tc::grid_barrier(c.gbar, epoch, nb, c.err, c.wait_ns)) return false;
         // U
         T delta[1];
         grid_totals<T, 1>(delta, c.part, {D_}, nb, sh);
@@ -1102,7 +1103,7 @@ __device__ __forceinline__ bool cg_block_solve(const CgBlock<T>& c, const double
             c.part[G_ * 1024 + blockIdx.x] = v[0];
             c.part[R_ * 1024 + blockIdx.x] = v[1];
         }
-        if (!tc::grid_barrier(c.gbar, epoch, nb, c.err)) return false;
+        if (!tc::grid_barrier(c.gbar, epoch, nb, c.err, c.wait_ns)) return false;
         gamma_prev = gamma;
         alpha_prev = alpha;
         grid_totals<T, 2>(v, c.part, {G_, R_}, nb, sh);
@@ -1198,7 +1199,7 @@ __device__ __forceinline__ bool pipe_block_solve(const CgBlock<float>& c, const 
         v.s[i] = 0.f;
         v.p[i] = 0.f;
     }
-    if (!tc::grid_barrier(c.gbar, epoch, nb, c.err)) return false;
+    if (!tc::grid_barrier(c.gbar, epoch, nb, c.err, c.wait_ns)) return false;
     // w = A u, m = D^-1 w, partials of r.u, w.u, r.r (set 0)
     rows_product<float, MODE>(c, v.u);
     {
@@ -1215,7 +1216,7 @@ __device__ __forceinline__ bool pipe_block_solve(const CgBlock<float>& c, const 
         if (threadIdx.x == 0)
             for (int k = 0; k < 3; ++k) c.part[k * 1024 + blockIdx.x] = t[k];
     }
-    if (!tc::grid_barrier(c.gbar, epoch, nb, c.err)) return false;
+    if (!tc::grid_barrier(c.gbar, epoch, nb, c.err, c.wait_ns)) return false;
     float gamma_prev = 1.f, alpha_prev = 1.f, rr0 = 0.f, stop = 0.f, rr = 0.f;
     int it = 0, breakdown = 0;
     for (;;) {
@@ -1270,7 +1271,7 @@ __device__ __forceinline__ bool pipe_block_solve(const CgBlock<float>& c, const 
         block_totals<float, 3>(t, sh);
         if (threadIdx.x == 0)
             for (int k = 0; k < 3; ++k) c.part[(3 * (set ^ 1) + k) * 1024 + blockIdx.x] = t[k];
-        if (!tc::grid_barrier(c.gbar, epoch, nb, c.err)) return false;
+        if (!tc::grid_barrier(c.gbar, epoch, nb, c.err, c.wait_ns)) return false;
         gamma_prev = gamma;
         alpha_prev = alpha;
         ++it;
@@ -1285,7 +1286,7 @@ __device__ __forceinline__ bool pipe_block_solve(const CgBlock<float>& c, const 
 template <typename T, int MODE>
 __device__ __forceinline__ CgBlock<T> cg_block(int64_t n, int64_t rpb, int64_t lds, const T* A, int64_t lda, T* u,
                                                T* r, T* z, T* p, T* sv, T* dv, T* part, unsigned* gbar, int* err,
-                                               T* sh, unsigned char* smem_raw) {
+                                               uint64_t wait_ns, T* sh, unsigned char* smem_raw) {
     constexpr int V = 16 / sizeof(T);
     CgBlock<T> c;
     c.n = n;
@@ -1307,6 +1308,7 @@ __device__ __forceinline__ CgBlock<T> cg_block(int64_t n, int64_t rpb, int64_t l
     c.part = part;
     c.gbar = gbar;
     c.err = err;
+    c.wait_ns = wait_ns;
     c.sh = sh;
     c.nb = gridDim.x;
     c.lane = threadIdx.x & 31;
@@ -1319,10 +1321,11 @@ __global__ void __launch_bounds__(PCG_THREADS, 1)
     pcg_persistent_kernel(int64_t n, int64_t rpb, int64_t lds, const T* __restrict__ A, int64_t lda,
                           const double* __restrict__ dinv, const double* __restrict__ rhs, double* d, T* u, T* r,
                           T* z, T* p, T* sv, T* dv, T* part, unsigned* gbar, CgScalars* S, double tol, int maxit,
-                          int* err) {
+                          int* err, unsigned long long wait_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T sh[2 * 33];
-    const CgBlock<T> c = cg_block<T, MODE>(n, rpb, lds, A, lda, u, r, z, p, sv, dv, part, gbar, err, sh, smem_raw);
+    const CgBlock<T> c = cg_block<T, MODE>(n, rpb, lds, A, lda, u, r, z, p, sv, dv, part, gbar, err, wait_ns, sh,
+                                                 smem_raw);
     cg_block_setup<T, MODE>(c);
     if constexpr (sizeof(T) == 4)
         for (int64_t i = c.r0 + threadIdx.x; i < c.r1; i += blockDim.x) dv[i] = (T)dinv[i];
@@ -1359,12 +1362,13 @@ __global__ void __launch_bounds__(PCG_THREADS, 1)
                              const float* __restrict__ A32, int64_t ld32, const double* __restrict__ dinv32,
                              const double* __restrict__ b, double* u, double* r64, const PipeVecs v,
                              float* partf, double* partd, unsigned* gbar, RefineOut* out, double tol,
-                             double inner_tol, int max_outer, int inner_maxit, int* err) {
+                             double inner_tol, int max_outer, int inner_maxit, int* err,
+                             unsigned long long wait_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float sh[3 * 33];
     __shared__ double shd[33];
     const CgBlock<float> c = cg_block<float, MODE>(n, rpb, lds, A32, ld32, v.x, v.r, v.z, v.p, v.s, v.dv, partf,
-                                                   gbar, err, sh, smem_raw);
+                                                   gbar, err, wait_ns, sh, smem_raw);
     cg_block_setup<float, MODE>(c);
     for (int64_t i = c.r0 + threadIdx.x; i < c.r1; i += blockDim.x) {
         v.dv[i] = (float)dinv32[i];
@@ -1386,7 +1390,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1)
         }
         block_totals<double, 1>(rv, shd);
         if (threadIdx.x == 0) partd[blockIdx.x] = rv[0];
-        if (!tc::grid_barrier(gbar, epoch, c.nb, err)) return;
+        if (!tc::grid_barrier(gbar, epoch, c.nb, err, c.wait_ns)) return;
         grid_totals<double, 1>(rv, partd, {0}, c.nb, shd);
         rr = rv[0];
         if (outer == 0) bb = rr;
@@ -1413,7 +1417,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1)
         }
         for (int64_t i = c.r0 + threadIdx.x; i < c.r1; i += blockDim.x) u[i] += (double)v.x[i];
         ++outer;
-        if (!tc::grid_barrier(gbar, epoch, c.nb, err)) return;
+        if (!tc::grid_barrier(gbar, epoch, c.nb, err, c.wait_ns)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         out->rr = rr;
@@ -1496,7 +1500,7 @@ static bool pcg_persistent(fl_ctx* h, SolveWork& w, int64_t n, int dtype, const 
     void* args[] = {(void*)&n,   (void*)&rpb,  (void*)&lds,  (void*)&Mv.p,  (void*)&ldm,   (void*)&dinv,
                     (void*)&rhs, (void*)&d,    (void*)&u,    (void*)&w.r,   (void*)&w.z,   (void*)&w.p,
                     (void*)&w.sv, (void*)&dv,  (void*)&part, (void*)&w.gbar, (void*)&w.s,  (void*)&tol,
-                    (void*)&maxit, (void*)&err};
+                    (void*)&maxit, (void*)&err, (void*)&h->wait_ns};
     const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(PCG_THREADS), args, smem, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1563,7 +1567,7 @@ static bool refine_persistent(fl_ctx* h, SolveWork& w, int64_t n, const double* 
                     (void*)&A32,  (void*)&ld32,   (void*)&dinv32, (void*)&b,       (void*)&u,
                     (void*)&r64,  (void*)&v,      (void*)&partf, (void*)&partd,    (void*)&w.gbar,
                     (void*)&out,  (void*)&tol,    (void*)&inner_tol, (void*)&max_outer, (void*)&inner_maxit,
-                    (void*)&err};
+                    (void*)&err,  (void*)&h->wait_ns};
     const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(PCG_THREADS), args, smem, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1778,6 +1782,7 @@ void fl_default_solve_opts(fl_solve_opts* o) {
     o->ld_lo = 0;
     o->inner_tol = 1e-4;
     o->inner_maxit = 2000;
+    o->barrier_timeout_us = 0;
 }
 
 int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const double* b_dev, double* u_dev,
@@ -1792,6 +1797,8 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
         return set_err(h, FL_EINVAL, "inner_dtype");
     if (o.inner_dtype != FL_F64 && (!o.A_lo_dev || o.ld_lo < n))
         return set_err(h, FL_EINVAL, "low-precision copy missing");
+    if (o.barrier_timeout_us < 0) return set_err(h, FL_EINVAL, "barrier_timeout_us");
+    h->wait_ns = o.barrier_timeout_us > 0 ? 1000ull * (unsigned long long)o.barrier_timeout_us : 2000000000ull;
     cudaStream_t st = (cudaStream_t)stream;
     FL_CU(h, cudaSetDevice(h->device));
     SolveWork w;
@@ -1862,7 +1869,7 @@ int fl_solve(fl_handle h, int64_t n, const double* A_dev, int64_t lda, const dou
             int ir = pcg(h, w, n, o.inner_dtype, o.A_lo_dev, o.ld_lo, w.dinv_lo, rvec, w.d, step_tol,
                          o.inner_maxit, &its, &irel, st);
             total += its;
-            if (ir == FL_ENOTSPD || ir == FL_ECUDA) {
+            if (ir == FL_ENOTSPD || ir == FL_ECUDA || ir == FL_ETIMEOUT) {
                 status = ir;
                 break;
             }

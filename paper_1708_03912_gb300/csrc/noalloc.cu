@@ -26,7 +26,8 @@ static __device__ __align__(256) float g_xf_static[FL_STATIC_MAX_N];
 
 constexpr int kMaxDevices = 128;
 std::mutex g_mu;
-float* g_xf_ptr[kMaxDevices] = {};  // device address of g_xf_static per device, set once
+float* g_xf_ptr[kMaxDevices] = {};  // device address of g_xf_static per device, set once (not valid
+                                    // after a reset of that device's primary context)
 
 // In host code g_xf_static names a host-side stand-in, not device memory, so the
 // device address is looked up once per device with that device current.
@@ -85,6 +86,9 @@ extern "C" int fl_matvec_f32_static(const float* A_dev, int64_t lda, int64_t n, 
                                     void* stream) {
     if (n < 1 || n > FL_STATIC_MAX_N) return FL_EINVAL;
     if (!A_dev || !x_dev || !y_dev || lda < n) return FL_EINVAL;
+    // an error left pending by earlier work is reported, not cleared (and not blamed on a
+    // launch of this call): the caller still sees it where it came from
+    if (cudaPeekAtLastError() != cudaSuccess) return FL_ECUDA;
     float* xf = nullptr;
     const int r = static_scratch(&xf);
     if (r != FL_OK) return r;
@@ -92,6 +96,7 @@ extern "C" int fl_matvec_f32_static(const float* A_dev, int64_t lda, int64_t n, 
     // the n staged entries are rewritten before they are read, so nothing needs clearing
     xf_from_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x_dev, xf);
     fl::count_launch(1);
+    if (cudaGetLastError() != cudaSuccess) return FL_ECUDA;
     const int vec = (((uintptr_t)A_dev & 15u) == 0) && (lda % 4 == 0);
     gemv_f32_static<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(n, A_dev, lda, xf, y_dev, vec);
     fl::count_launch(1);

@@ -158,9 +158,10 @@ __device__ __forceinline__ void tmem_wait_ld() {
 // Barrier over all blocks of a co-resident (cooperative) grid on a monotone arrival
 // counter (zero at launch, on a cache line of its own): barrier number `epoch` is
 // passed when the counter reaches epoch * nblocks.  Arrival is a fire-and-forget
-// release add; the wait polls with acquire loads.  Bounded: on timeout sets bit 2 of
-// *err and returns false (the caller then winds down).
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& epoch, unsigned nblocks, int* err) {
+// release add; the wait polls with acquire loads.  Bounded by limit_ns of %globaltimer:
+// on timeout sets bit 2 of *err and returns false (the caller then winds down).
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& epoch, unsigned nblocks, int* err,
+                                             uint64_t limit_ns = WAIT_LIMIT_NS) {
     __syncthreads();
     __shared__ int ok_s;
     ++epoch;
@@ -175,7 +176,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& epoch, u
             const uint64_t t0 = globaltimer();
             do {
                 asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
-                if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                if (globaltimer() - t0 > limit_ns) {
                     atomicOr(err, 4);
                     ok = 0;
                     break;

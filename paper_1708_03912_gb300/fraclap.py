@@ -53,7 +53,7 @@ class fl_options(ctypes.Structure):
 class fl_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("inner_dtype", ctypes.c_int),
                 ("A_lo_dev", ctypes.c_void_p), ("ld_lo", ctypes.c_int64), ("inner_tol", ctypes.c_double),
-                ("inner_maxit", ctypes.c_int)]
+                ("inner_maxit", ctypes.c_int), ("barrier_timeout_us", ctypes.c_int)]
 
 
 class fl_stats(ctypes.Structure):
@@ -82,7 +82,7 @@ class fl_batch_problem(ctypes.Structure):
 class fl_batch_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("inner_maxit", ctypes.c_int), ("ctas", ctypes.c_int), ("stages", ctypes.c_int),
-                ("residual", ctypes.c_int)]
+                ("barrier_timeout_us", ctypes.c_int), ("residual", ctypes.c_int)]
 
 
 class fl_batch_info(ctypes.Structure):
@@ -384,8 +384,20 @@ def fl_pool_stats():
 
 def fl_matvec_f32_static(A32, x, y, stream=None):
     """y = A32 x without any device allocation (for callers that cannot allocate);
-    n <= FL_STATIC_MAX_N.  Returns the status code (0 = FL_OK) instead of raising."""
-    return lib().fl_matvec_f32_static(_ptr(A32), A32.stride(0), A32.shape[0], _ptr(x), _ptr(y), _stream(stream))
+    n <= FL_STATIC_MAX_N.  A32: float32 CUDA [n, lda] with unit column stride; x, y:
+    contiguous float64 CUDA vectors of length n.  Returns the status code (0 = FL_OK)
+    instead of raising."""
+    import torch
+
+    n = A32.shape[0]
+    if A32.dtype != torch.float32 or A32.dim() != 2 or A32.shape[1] != n or A32.stride(1) != 1:
+        raise ValueError("A32 must be an n x n float32 matrix with unit column stride")
+    for name, v in (("x", x), ("y", y)):
+        if v.dtype != torch.float64 or v.dim() != 1 or v.shape[0] != n or not v.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 vector of length {n}")
+    if not (A32.is_cuda and x.is_cuda and y.is_cuda):
+        raise ValueError("A32, x and y must be CUDA tensors")
+    return lib().fl_matvec_f32_static(_ptr(A32), A32.stride(0), n, _ptr(x), _ptr(y), _stream(stream))
 
 
 def fl_split_bf16_bytes(n, nslices):

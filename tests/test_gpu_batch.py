@@ -224,3 +224,23 @@ def test_autotuner_feeds_the_solver(disc10):
     assert r == F.FL_OK and (info.stages, info.ctas) == (best.stages, best.ctas)
     F.fl_tune_clear()
     F.fl_destroy(h)
+
+
+def test_batched_barrier_timeout_is_reported(disc10):
+    # a 1 us grid-barrier bound in the persistent batched kernel: FL_ETIMEOUT, then the same
+    # handle solves the same problem with the default bound
+    V, T, A = disc10
+    om = OracleMesh(V, T)
+    B = np.concatenate([load_vector(om, 0.75)[:, None], load_vector(om, 0.75, synth.gaussian_nodal(om.nv, 15))], 1)
+    q = _problem(A, B, 2)
+    h = F.fl_create(V, T)
+    o = F.fl_default_batch_opts()
+    assert o.barrier_timeout_us == 0
+    o.barrier_timeout_us = 1
+    with pytest.raises(F.FlError) as e:
+        F.fl_batch_solve(h, [q], o)
+    assert e.value.code == F.FL_ETIMEOUT
+    o.barrier_timeout_us = 0
+    r, info, rel, st = F.fl_batch_solve(h, [q], o)
+    F.fl_destroy(h)
+    assert r == F.FL_OK and np.all(rel <= 1e-8)

@@ -224,3 +224,39 @@ def test_full_size_graded_disc_refined_solve(s):
     # A d = r_refined - r_f64, so ||d||_A^2 <= (||r1|| + ||r2||) ||d||
     assert float(d @ (Ah @ d)) <= 2.1e-8 * np.linalg.norm(bh) * np.linalg.norm(d) + 1e-30
     m.close()
+
+
+def test_barrier_timeout_is_reported_and_the_handle_stays_usable():
+    # a grid-barrier bound of 1 us cannot be met by 152 blocks doing real work between
+    # barriers: the cooperative solve gives up, reports FL_ETIMEOUT, and the next call on the
+    # same handle (default bound) converges.  Every wait gives up and returns; nothing hangs.
+    V, T = synth.disc(25)
+    s = 0.75
+    m = F.Mesh(V, T)
+    A = m.assemble(s, "fp64")
+    A32 = torch.empty(A.shape, dtype=torch.float32, device="cuda")
+    F.fl_convert(A, F.FL_F32, A32)
+    b = m.load_vector(s)
+    u = torch.empty_like(b)
+    for refined in (False, True):
+        o = F.fl_default_solve_opts()
+        assert o.barrier_timeout_us == 0
+        o.tol = 1e-10
+        if refined:
+            o.inner_dtype = F.FL_F32
+            o.A_lo_dev = A32.data_ptr()
+            o.ld_lo = A32.stride(0)
+        o.barrier_timeout_us = 1
+        with pytest.raises(F.FlError) as e:
+            F.fl_solve(m.h, A, b, u, o)
+        assert e.value.code == F.FL_ETIMEOUT
+        assert "grid barrier" in str(e.value)
+        o.barrier_timeout_us = 0
+        info = F.fl_solve(m.h, A, b, u, o)
+        assert info.status == F.FL_OK and info.rel_residual <= 1e-10
+    o = F.fl_default_solve_opts()
+    o.barrier_timeout_us = -1
+    with pytest.raises(F.FlError) as e:
+        F.fl_solve(m.h, A, b, u, o)
+    assert e.value.code == F.FL_EINVAL
+    m.close()

@@ -69,3 +69,22 @@ def test_pattern_and_agreement_with_full_matrix():
     assert np.max(np.abs(N - A)[nofar] / d[nofar]) < 1e-14
     # and where far pairs exist, N differs from A (the far field was left out)
     assert np.max(np.abs(N - A)[~nofar] / d[~nofar]) > 1e-6
+
+
+def test_disjoint_support_entries_are_negative_and_inside_the_far_part():
+    # Section 6: for DOFs whose supports share no vertex, a(phi_i, phi_j) = -C ∬ phi_i phi_j k < 0;
+    # the entry-wise float64 parity check measures those entries relative to themselves.  Every
+    # touching pair is in the near-field pattern (touching cells are near-field pairs).
+    import sys
+    import os
+
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from parity import touching_mask
+
+    for (V, T), s in ((synth.disc(5), 0.3), (synth.graded_interval(30, 2.0), 0.7), (synth.lshape(0.25, 0), 0.5)):
+        om = OracleMesh(V, T)
+        A, _ = assemble_matrix(om, s)
+        M = touching_mask(om, s)
+        assert np.all(A[~M] < 0)
+        assert np.all(nearfield_pattern(om, s)[M])
+        assert np.all(np.diag(M))
