@@ -73,6 +73,10 @@ typedef struct fl_options {
     int k_bnd;    /* element/boundary-facet pairs that touch (default 8) */
     int regional; /* 1: drop the boundary term (regional fractional Laplacian, Section 2) */
     int k_vertex; /* common-vertex pairs, 3D regular variables (default 6) */
+    int far_f64_pipe; /* FL_FP64 mode, 2D, k_far = 4, s in {1/4, 1/2, 3/4}: the separated pairs at
+                         distance >= 2 are evaluated in double-word arithmetic on the float32 pipe
+                         (about 2^-47 relative per operation; default 0); 1 evaluates them in
+                         float64 on the float64 pipe instead.  Other cases always use float64. */
 } fl_options;
 
 typedef struct fl_ctx* fl_handle;
@@ -125,6 +129,26 @@ int fl_dof_vertices(fl_handle h, double s, int32_t* vertex_of_dof_host);
  * FL_DOF_PAPER and s < 1/2 unless regional), FL_ENOMEM, FL_ECUDA.
  */
 int fl_assemble(fl_handle h, double s, int precision, double* A_dev, int64_t lda, void* stream);
+
+/*
+ * Autotuner of the element-pair tile kernel (no counterpart in the paper).  In the FL_FP64
+ * mode on 2D meshes with k_far = 4 and s in {1/4, 1/2, 3/4} the separated pairs at
+ * distance >= 2 (Section 5's N_el^2 part) run in double-word arithmetic, one 4-warp block
+ * per 32 x 32 tile of cells, in launch variants 2, 3, 4 (the minimum number of resident
+ * blocks per SM the kernel is compiled for, which caps its registers per thread).
+ * fl_tune_assemble assembles A (A_dev, lda as for fl_assemble) once per variant plus
+ * `reps` timed times with the stages in sequence, takes the median CUDA-event time of the
+ * far stage, and records the fastest in the tuning table under ("far_tile_dw<PW>", number
+ * of cells); later assemblies of any handle on a mesh with that cell count use it.
+ * best_variant / best_ms (host, optional) receive the winner.  Synchronises `stream`.
+ * Errors: FL_ENOTIMPL (the double-word kernel does not apply), FL_EINVAL, FL_ENOMEM,
+ * FL_ECUDA.
+ * fl_set_far_variant fixes the variant of h's later assemblies (2, 3 or 4; 0: the tuning
+ * table, else 3).  Errors: FL_EINVAL.
+ */
+int fl_tune_assemble(fl_handle h, double s, double* A_dev, int64_t lda, int reps, int* best_variant, double* best_ms,
+                     void* stream);
+int fl_set_far_variant(fl_handle h, int variant);
 
 /*
  * Sparse near-field part N of A^s in CSR form, A = N + F (Sections 5 and 6): F holds

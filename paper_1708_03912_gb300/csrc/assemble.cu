@@ -1403,6 +1403,7 @@ int ensure_device(fl_ctx* h, int pi, cudaStream_t st) {
     FL_TRY(alloc(h, &t.P, (size_t)P.toff.back() * sizeof(double)));
     FL_TRY(alloc(h, &t.Pd, (size_t)P.nblk * nc * qf * sizeof(double)));
     FL_TRY(alloc(h, &t.pts, (size_t)nc * qf * D * sizeof(double)));
+    if (D == 2 && qf == 16) FL_TRY(alloc(h, &t.pts_dw, (size_t)nc * 16 * sizeof(float4)));
     FL_TRY(alloc(h, (void**)&t.Dn, (size_t)P.np_a.size() * 2 * qn * sizeof(double)));
     FL_TRY(alloc(h, (void**)&t.Bf, (size_t)nc * qf * sizeof(double)));
     FL_TRY(alloc(h, (void**)&t.eblk, (size_t)nc * 6 * sizeof(double)));
@@ -1807,6 +1808,7 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
     if (D == 2) {
         if (f32) { prep_points<float, 2><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (float*)t.pts); fl::count_launch(); }
         else { prep_points<double, 2><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts); fl::count_launch(); }
+        if (!f32 && far_dw_applies(h, P, pw)) FL_TRY(prep_far_dw(h, P, t, ro, st));
     } else {
         if (f32) { prep_points<float, 1><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (float*)t.pts); fl::count_launch(); }
         else { prep_points<double, 1><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts); fl::count_launch(); }
@@ -1848,6 +1850,7 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
     // float32: keep only the one-MUFU forms (t^2, t^3); lg2 + ex2 beats rsqrt + sqrt here
     const int pw32 = (pw == 4 || pw == 6) ? pw : 0;
     if (f32) FL_TRY(launch_far<float>(h, P, t, rb, ro, expo, pw32, st));
+    else if (far_dw_applies(h, P, pw)) FL_TRY(launch_far_dw(h, P, t, rb, ro, pw, st));
     else FL_TRY(launch_far<double>(h, P, t, rb, ro, expo, pw, st));
     stage_mark(h, st, FL_STAGE_FAR, 1);
     int side_rc = FL_OK;
@@ -2028,6 +2031,55 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
 
 int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStream_t st) {
     return assemble_impl(h, s, precision, A, lda, nullptr, st);
+}
+
+// Sweep the launch variants of the float64-mode double-word far kernel on this handle's
+// mesh at order s: for each, one warm-up assembly and `reps` profiled ones (stages in
+// sequence, the far stage timed alone by CUDA events); the median decides.  The winner is
+// recorded in the tuning table under (kernel, cell count), which later assemblies consult.
+int tune_assemble(fl_ctx* h, double s, double* A, int64_t lda, int reps, int* best_variant, double* best_ms,
+                  cudaStream_t st) {
+    if (reps < 1) return set_err(h, FL_EINVAL, "reps < 1");
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    const int pw = pw_mode(P.dim, s);
+    if (!far_dw_applies(h, P, pw))
+        return set_err(h, FL_ENOTIMPL, "no launch variants to tune (float64 mode, 2D, k_far = 4, s in {1/4, 1/2, 3/4})");
+    const int prof0 = h->profiling, var0 = h->far_variant;
+    int best = 0, rc = FL_OK;
+    double best_t = 0.0;
+    h->profiling = 1;
+    for (int v = 2; v <= 4 && rc == FL_OK; ++v) {
+        h->far_variant = v;
+        rc = assemble_impl(h, s, FL_FP64, A, lda, nullptr, st);
+        std::vector<float> ts;
+        for (int r = 0; r < reps && rc == FL_OK; ++r) {
+            rc = assemble_impl(h, s, FL_FP64, A, lda, nullptr, st);
+            if (rc != FL_OK) break;
+            if (cudaEventSynchronize(h->ev[2 * FL_STAGE_FAR + 1]) != cudaSuccess) {
+                rc = set_err(h, FL_ECUDA, "cudaEventSynchronize");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, h->ev[2 * FL_STAGE_FAR], h->ev[2 * FL_STAGE_FAR + 1]);
+            ts.push_back(ms);
+        }
+        if (rc != FL_OK) break;
+        std::sort(ts.begin(), ts.end());
+        const double med = ts[ts.size() / 2];
+        if (!best || med < best_t) {
+            best = v;
+            best_t = med;
+        }
+    }
+    h->profiling = prof0;
+    h->far_variant = var0;
+    if (rc != FL_OK) return rc;
+    far_dw_record(P, pw, best, best_t);
+    if (best_variant) *best_variant = best;
+    if (best_ms) *best_ms = best_t;
+    return FL_OK;
 }
 
 int assemble_nearfield_csr(fl_ctx* h, double s, int precision, int64_t* nnz, int32_t* rowptr, int32_t* col,

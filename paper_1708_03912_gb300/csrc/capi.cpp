@@ -9,6 +9,8 @@
 
 namespace fl {
 int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStream_t st);
+int tune_assemble(fl_ctx* h, double s, double* A, int64_t lda, int reps, int* best_variant, double* best_ms,
+                  cudaStream_t st);
 int assemble_nearfield_csr(fl_ctx* h, double s, int precision, int64_t* nnz, int32_t* rowptr, int32_t* col,
                            double* val, cudaStream_t st);
 int load_vector(fl_ctx* h, double s, const double* f, int nrhs, double* b, int64_t ldb, cudaStream_t st);
@@ -53,6 +55,7 @@ void fl_default_options(fl_options* o) {
     o->k_bnd = 8;
     o->regional = 0;
     o->k_vertex = 6;
+    o->far_f64_pipe = 0;
 }
 
 int fl_create(fl_handle* out, int dim, int64_t n_vertices, const double* vertices_host, int64_t n_cells,
@@ -83,6 +86,7 @@ int fl_create(fl_handle* out, int dim, int64_t n_vertices, const double* vertice
     h->dim = dim;
     h->dof_mode = dof_mode;
     h->opt = o;
+    h->far_f64_pipe = o.far_f64_pipe ? 1 : 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         dev = 0;
@@ -163,6 +167,24 @@ int fl_assemble(fl_handle h, double s, int precision, double* A_dev, int64_t lda
     } catch (const std::bad_alloc&) {
         return fl::set_err(h, FL_ENOMEM, "out of host memory");
     }
+}
+
+int fl_tune_assemble(fl_handle h, double s, double* A_dev, int64_t lda, int reps, int* best_variant, double* best_ms,
+                     void* stream) {
+    if (!h) return FL_EINVAL;
+    h->err.clear();
+    try {
+        return fl::tune_assemble(h, s, A_dev, lda, reps, best_variant, best_ms, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        return fl::set_err(h, FL_ENOMEM, "out of host memory");
+    }
+}
+
+int fl_set_far_variant(fl_handle h, int variant) {
+    if (!h) return FL_EINVAL;
+    if (variant != 0 && (variant < 2 || variant > 4)) return fl::set_err(h, FL_EINVAL, "variant must be 0 or 2..4");
+    h->far_variant = variant;
+    return FL_OK;
 }
 
 int fl_assemble_nearfield_csr(fl_handle h, double s, int precision, int64_t* nnz, int32_t* rowptr_dev,

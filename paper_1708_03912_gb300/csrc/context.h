@@ -81,6 +81,7 @@ struct DevTables {
     void* P = nullptr;      // partial far-field tiles
     void* Pd = nullptr;     // nblk * nc * Qf partial row sums
     void* pts = nullptr;    // nc * Qf * dim offsets from centroids
+    void* pts_dw = nullptr; // nc * 16 double-word offsets (2D, float64 mode, k_far = 4)
     double* Dn = nullptr;   // nnear * 2 * Qn
     double* Bf = nullptr;   // nc * Qf boundary sums (far facets)
     double* eblk = nullptr; // nc * 6 far-independent part of each cell's diagonal block
@@ -112,6 +113,8 @@ struct fl_ctx {
     int profiling = 0;
     int no_persistent = 0;  // 1: run CG as captured kernel batches instead of one cooperative launch
     unsigned long long wait_ns = 2000000000ull;  // bound of a grid-barrier wait in the current solve
+    int far_f64_pipe = 0;   // 1: float64-mode separated pairs on the float64 pipe (double-word otherwise)
+    int far_variant = 0;    // launch variant of the double-word far kernel (0: tuning table, else 3)
     cudaEvent_t ev[2 * FL_NSTAGES] = {};
     bool ev_made = false;
     bool ev_recorded = false;
@@ -155,4 +158,13 @@ void tune_record(const std::string& device, const std::string& kernel, int64_t n
 bool tune_lookup(const std::string& device, const std::string& kernel, int64_t n, int nrhs, int nslices, int* p0,
                  int* p1);
 unsigned tune_generation();  // changes whenever the table changes
+// float64-mode separated pairs in double-word arithmetic (far_dw.cu): whether they apply
+// (2D, k_far = 4, s in {1/4, 1/2, 3/4}), the double-word point offsets, the tile kernel,
+// the launch variant it takes and the autotuner's record of one
+bool far_dw_applies(const fl_ctx* h, const Plan& P, int pw);
+int prep_far_dw(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, cudaStream_t st);
+int launch_far_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro, int pw,
+                  cudaStream_t st);
+int far_dw_variant(const fl_ctx* h, const Plan& P, int pw);
+void far_dw_record(const Plan& P, int pw, int variant, double ms);
 }  // namespace fl

@@ -99,6 +99,103 @@ __device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al,
     sl = __fadd_rn(sl, __fadd_rn(err, l));
 }
 
+// ---- double-word numbers: an unevaluated sum h + l of two floats ----
+// Built from the error-free transformations of Knuth (TwoSum) and Dekker (Fast2Sum, the
+// exact product by FMA) and the double-word algorithms analysed by Joldes, Muller and
+// Popescu (ACM TOMS 44, 2017): each operation below is exact to a few units of 2^-48
+// relative, on the float32 pipe.
+struct dw {
+    float h, l;
+};
+
+// a + b = s + e exactly (any magnitudes)
+__device__ __forceinline__ dw two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// a + b = s + e exactly when |a| >= |b| (or a = 0)
+__device__ __forceinline__ dw fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// a b = p + e exactly
+__device__ __forceinline__ dw two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ dw dw_from(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double dw_to(dw x) { return (double)x.h + (double)x.l; }
+// x + y, renormalised
+__device__ __forceinline__ dw dw_add(dw x, dw y) {
+    dw s = two_sum(x.h, y.h);
+    s.l = __fadd_rn(s.l, __fadd_rn(x.l, y.l));
+    return fast_two_sum(s.h, s.l);
+}
+// x - y (not renormalised: |l| stays within a few ulp of h)
+__device__ __forceinline__ dw dw_sub(dw x, dw y) {
+    dw s = two_sum(x.h, -y.h);
+    s.l = __fadd_rn(s.l, __fsub_rn(x.l, y.l));
+    return s;
+}
+// x y and x^2 (the l x l term, below 2^-48 relative, is dropped; not renormalised)
+__device__ __forceinline__ dw dw_mul(dw x, dw y) {
+    dw p = two_prod(x.h, y.h);
+    p.l = __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, p.l));
+    return p;
+}
+__device__ __forceinline__ dw dw_sqr(dw x) {
+    dw p = two_prod(x.h, x.h);
+    p.l = __fmaf_rn(x.h, x.l, __fmaf_rn(x.h, x.l, p.l));
+    return p;
+}
+// s += c k for non-negative terms; the low part gathers the product and sum errors and is
+// left unnormalised (callers renormalise after a bounded number of terms)
+__device__ __forceinline__ void dw_mac(dw& s, dw c, dw k) {
+    const float p = __fmul_rn(c.h, k.h);
+    float e = __fmaf_rn(c.h, k.h, -p);
+    e = __fmaf_rn(c.h, k.l, e);
+    e = __fmaf_rn(c.l, k.h, e);
+    const dw t = two_sum(s.h, p);
+    s.h = t.h;
+    s.l = __fadd_rn(s.l, __fadd_rn(t.l, e));
+}
+__device__ __forceinline__ dw dw_renorm(dw x) { return fast_two_sum(x.h, x.l); }
+
+// x^{-1/2}: the float32 estimate t0 (about 2^-22) corrected by one Newton step written in
+// double-word terms, t = t0 (1 - rho)^{-1/2} ~ t0 (1 + rho/2 + 3 rho^2/8), rho = 1 - x t0^2
+// computed from the exact square of t0 (1 - g.h is exact for g.h in [1/2, 2]).
+__device__ __forceinline__ dw dw_rsqrt(dw x) {
+    const float t0 = rsqrt_approx(x.h);
+    const dw g = dw_mul(x, two_prod(t0, t0));
+    const float rho = __fsub_rn(__fsub_rn(1.f, g.h), g.l);
+    return {t0, __fmul_rn(__fmul_rn(t0, rho), __fmaf_rn(0.375f, rho, 0.5f))};
+}
+// x^{-1/4}: v = v0 (1 - rho)^{-1/4} ~ v0 (1 + rho/4 + 5 rho^2/32), rho = 1 - x v0^4
+__device__ __forceinline__ dw dw_rqrt(dw x) {
+    const float v0 = rsqrt_approx(sqrt_approx(x.h));
+    const dw g = dw_mul(x, dw_sqr(two_prod(v0, v0)));
+    const float rho = __fsub_rn(__fsub_rn(1.f, g.h), g.l);
+    return {v0, __fmul_rn(__fmul_rn(v0, rho), __fmaf_rn(0.15625f, rho, 0.25f))};
+}
+// r2^e, e = -PW/4, for PW in {5, 6, 7} (2D kernels of order s = 1/4, 1/2, 3/4)
+template <int PW>
+__device__ __forceinline__ dw dw_kpow(dw r2) {
+    static_assert(PW == 5 || PW == 6 || PW == 7, "double-word powers: PW 5, 6, 7");
+    if constexpr (PW == 6) {
+        const dw t = dw_rsqrt(r2);
+        return dw_mul(dw_sqr(t), t);
+    } else {
+        const dw v = dw_rqrt(r2);
+        const dw v2 = dw_sqr(v), v4 = dw_sqr(v2);
+        if constexpr (PW == 5) return dw_mul(v4, v);
+        else return dw_mul(dw_mul(v4, v2), v);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

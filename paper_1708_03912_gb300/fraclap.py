@@ -23,7 +23,7 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
           6: "FL_ETIMEOUT", 7: "FL_ENOTIMPL"}
 
 EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
-           "fl_assemble", "fl_assemble_nearfield_csr", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
+           "fl_assemble", "fl_tune_assemble", "fl_set_far_variant", "fl_assemble_nearfield_csr", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
            "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
            "fl_matvec_f32_static",
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
@@ -47,7 +47,8 @@ class FlError(RuntimeError):
 
 class fl_options(ctypes.Structure):
     _fields_ = [("k_far", ctypes.c_int), ("k_near", ctypes.c_int), ("k_touch", ctypes.c_int),
-                ("k_bnd", ctypes.c_int), ("regional", ctypes.c_int), ("k_vertex", ctypes.c_int)]
+                ("k_bnd", ctypes.c_int), ("regional", ctypes.c_int), ("k_vertex", ctypes.c_int),
+                ("far_f64_pipe", ctypes.c_int)]
 
 
 class fl_solve_opts(ctypes.Structure):
@@ -116,6 +117,10 @@ def lib():
     L.fl_dof_vertices.restype = ci
     L.fl_assemble.argtypes = [vp, dbl, ci, vp, i64, vp]
     L.fl_assemble.restype = ci
+    L.fl_tune_assemble.argtypes = [vp, dbl, vp, i64, ci, ctypes.POINTER(ci), ctypes.POINTER(dbl), vp]
+    L.fl_tune_assemble.restype = ci
+    L.fl_set_far_variant.argtypes = [vp, ci]
+    L.fl_set_far_variant.restype = ci
     L.fl_assemble_nearfield_csr.argtypes = [vp, dbl, ci, ctypes.POINTER(i64), vp, vp, vp, vp]
     L.fl_assemble_nearfield_csr.restype = ci
     L.fl_load_vector.argtypes = [vp, dbl, vp, ci, vp, i64, vp]
@@ -289,6 +294,20 @@ def fl_assemble(h, s, precision, A, stream=None):
     """A: float64 CUDA tensor [n, lda] (row-major, contiguous rows)."""
     assert A.dtype.is_floating_point and A.element_size() == 8 and A.is_cuda and A.stride(1) == 1
     _check(lib().fl_assemble(h, s, precision, _ptr(A), A.stride(0), _stream(stream)), h)
+
+
+def fl_tune_assemble(h, s, A, reps=5, stream=None):
+    """Sweep the float64-mode far-kernel launch variants on A's mesh (A as for fl_assemble);
+    returns (best variant, its median far-stage ms) and records it in the tuning table."""
+    v = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().fl_tune_assemble(h, s, _ptr(A), A.stride(0), reps, ctypes.byref(v), ctypes.byref(ms),
+                                  _stream(stream)), h)
+    return v.value, ms.value
+
+
+def fl_set_far_variant(h, variant):
+    _check(lib().fl_set_far_variant(h, variant), h)
 
 
 def fl_assemble_nearfield_csr(h, s, precision, stream=None):
@@ -707,10 +726,11 @@ class Mesh:
     """Owns one fl_handle.  Orders and the DOF rule are fixed at creation."""
 
     def __init__(self, vertices, cells, dof_mode="interior", k_far=4, k_near=6, k_touch=8, k_bnd=8, regional=False,
-                 k_vertex=6):
+                 k_vertex=6, far_f64_pipe=False):
         o = fl_default_options()
         o.k_far, o.k_near, o.k_touch, o.k_bnd, o.regional = k_far, k_near, k_touch, k_bnd, int(regional)
         o.k_vertex = k_vertex
+        o.far_f64_pipe = int(far_f64_pipe)
         self.h = fl_create(vertices, cells, FL_DOF_PAPER if dof_mode == "paper" else FL_DOF_INTERIOR, o)
         self.dim = 1 if np.asarray(vertices).ndim == 1 else np.asarray(vertices).shape[1]
 

@@ -248,3 +248,45 @@ def test_full_size_graded_disc_sampled_rows():
     check_f64(A, Ar, om, s, TOL64, rows=rows, diag=np.diag(A))
     d = np.sqrt(np.outer(np.diag(A)[rows], np.diag(A)))
     assert float(np.max(np.abs(Am[rows] - Ar) / d)) < 2e-5
+
+
+@pytest.mark.parametrize("s", [0.25, 0.5, 0.75])
+def test_double_word_far_field_matches_float64_pipe(s):
+    # the float64 mode evaluates the separated pairs at distance >= 2 in double-word arithmetic
+    # (2D, k_far = 4, s in {1/4, 1/2, 3/4}); the same pairs on the float64 pipe give the same
+    # matrix to well inside the 1e-12 entry tolerance, and both pass it against the oracle
+    V, T = synth.disc(7, 2.0)  # graded toward the boundary: far pairs of very different sizes
+    om = OracleMesh(V, T)
+    Ao, _ = assemble_matrix(om, s)
+    A_dw = gpu_matrix(V, T, s)
+    A_64 = gpu_matrix(V, T, s, far_f64_pipe=True)
+    check_f64(A_dw, Ao, om, s, TOL64)
+    check_f64(A_64, Ao, om, s, TOL64)
+    far, near = check_f64(A_dw, A_64, om, s, 1e-13)
+    print(f"s {s}: double-word vs float64 pipe: {far:.1e} (disjoint supports), {near:.1e} (touching)")
+
+
+def test_far_variants_and_autotuner():
+    # every launch variant of the double-word far kernel gives the same bits; the autotuner
+    # records its winner under (kernel, cell count) and later assemblies of a new handle on the
+    # same mesh use it (same bits again)
+    V, T = synth.disc(10)
+    s = 0.75
+    m = F.Mesh(V, T)
+    ref = m.assemble(s, "fp64").clone()
+    for v in (2, 3, 4):
+        F.fl_set_far_variant(m.h, v)
+        assert torch.equal(m.assemble(s, "fp64"), ref), v
+    F.fl_set_far_variant(m.h, 0)
+    F.fl_tune_clear()
+    best, ms = F.fl_tune_assemble(m.h, s, ref.clone(), reps=3)
+    assert best in (2, 3, 4) and ms > 0
+    assert F.fl_tune_lookup("far_tile_dw<7>", len(T), 1, 1) == (best, 0)
+    m2 = F.Mesh(V, T)
+    assert torch.equal(m2.assemble(s, "fp64"), ref)
+    with pytest.raises(F.FlError) as e:
+        F.fl_tune_assemble(m2.h, 0.6, ref.clone(), reps=1)  # generic s: no double-word kernel
+    assert e.value.code == F.FL_ENOTIMPL
+    m2.close()
+    m.close()
+    F.fl_tune_clear()
