@@ -134,8 +134,9 @@ int fl_assemble(fl_handle h, double s, int precision, double* A_dev, int64_t lda
  * Autotuner of the element-pair tile kernel (no counterpart in the paper).  In the FL_FP64
  * mode on 2D meshes with k_far = 4 and s in {1/4, 1/2, 3/4} the separated pairs at
  * distance >= 2 (Section 5's N_el^2 part) run in double-word arithmetic, one 4-warp block
- * per 32 x 32 tile of cells, in launch variants 2, 3, 4 (the minimum number of resident
- * blocks per SM the kernel is compiled for, which caps its registers per thread).
+ * per 32 x 32 tile of cells, in launch variants 1-4: the unroll of the loop over the column
+ * cell's quadrature points and the minimum number of resident blocks per SM the kernel is
+ * compiled for (which caps its registers per thread) are (4, 1), (1, 2), (2, 2), (1, 3).
  * fl_tune_assemble assembles A (A_dev, lda as for fl_assemble) once per variant plus
  * `reps` timed times with the stages in sequence, takes the median CUDA-event time of the
  * far stage, and records the fastest in the tuning table under ("far_tile_dw<PW>", number
@@ -143,8 +144,8 @@ int fl_assemble(fl_handle h, double s, int precision, double* A_dev, int64_t lda
  * best_variant / best_ms (host, optional) receive the winner.  Synchronises `stream`.
  * Errors: FL_ENOTIMPL (the double-word kernel does not apply), FL_EINVAL, FL_ENOMEM,
  * FL_ECUDA.
- * fl_set_far_variant fixes the variant of h's later assemblies (2, 3 or 4; 0: the tuning
- * table, else 3).  Errors: FL_EINVAL.
+ * fl_set_far_variant fixes the variant of h's later assemblies (1-4; 0: the tuning table,
+ * else 3).  Errors: FL_EINVAL.
  */
 int fl_tune_assemble(fl_handle h, double s, double* A_dev, int64_t lda, int reps, int* best_variant, double* best_ms,
                      void* stream);

@@ -673,12 +673,6 @@ __global__ void touch_pair_kernel(int ntp, int dim, const int* tp_type, const in
 // compact per-facet record (start point, edge, normal and length, float64).
 constexpr int BND_WARPS = 4;
 
-struct FacetRec {
-    double e0x, e0y;   // start point
-    double ex, ey;     // edge vector E1 - E0
-    double nx, ny;     // inward unit normal
-    double len, pad;
-};
 
 __global__ void facet_records_kernel(int64_t nf, const int* F, const double* FN, const double* FLEN, const double* V,
                                      FacetRec* out) {
@@ -1403,7 +1397,11 @@ int ensure_device(fl_ctx* h, int pi, cudaStream_t st) {
     FL_TRY(alloc(h, &t.P, (size_t)P.toff.back() * sizeof(double)));
     FL_TRY(alloc(h, &t.Pd, (size_t)P.nblk * nc * qf * sizeof(double)));
     FL_TRY(alloc(h, &t.pts, (size_t)nc * qf * D * sizeof(double)));
-    if (D == 2 && qf == 16) FL_TRY(alloc(h, &t.pts_dw, (size_t)nc * 16 * sizeof(float4)));
+    if (D == 2 && qf == 16) {
+        FL_TRY(alloc(h, &t.pts_dw, (size_t)nc * 16 * sizeof(float4)));
+        const int nch = bnd_dw_chunks(nc);
+        if (nch > 1) FL_TRY(alloc(h, (void**)&t.Bfp, (size_t)nch * nc * 16 * sizeof(double)));
+    }
     FL_TRY(alloc(h, (void**)&t.Dn, (size_t)P.np_a.size() * 2 * qn * sizeof(double)));
     FL_TRY(alloc(h, (void**)&t.Bf, (size_t)nc * qf * sizeof(double)));
     FL_TRY(alloc(h, (void**)&t.eblk, (size_t)nc * 6 * sizeof(double)));
@@ -1913,6 +1911,7 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
             stage_mark(h, st, FL_STAGE_BND, 0);
             if (D == 2 && !h->opt.regional && P.nf > 0) {
                 if (f32) FL_TRY(launch_bnd<float>(h, P, t, ro, expo, pw32, st));
+                else if (far_dw_applies(h, P, pw)) FL_TRY(launch_bnd_dw(h, P, t, rb, ro, pw, st));
                 else FL_TRY(launch_bnd<double>(h, P, t, ro, expo, pw, st));
             }
             stage_mark(h, st, FL_STAGE_BND, 1);
@@ -2050,7 +2049,7 @@ int tune_assemble(fl_ctx* h, double s, double* A, int64_t lda, int reps, int* be
     int best = 0, rc = FL_OK;
     double best_t = 0.0;
     h->profiling = 1;
-    for (int v = 2; v <= 4 && rc == FL_OK; ++v) {
+    for (int v = 1; v <= 4 && rc == FL_OK; ++v) {
         h->far_variant = v;
         rc = assemble_impl(h, s, FL_FP64, A, lda, nullptr, st);
         std::vector<float> ts;

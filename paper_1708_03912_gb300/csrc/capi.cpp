@@ -182,7 +182,7 @@ int fl_tune_assemble(fl_handle h, double s, double* A_dev, int64_t lda, int reps
 
 int fl_set_far_variant(fl_handle h, int variant) {
     if (!h) return FL_EINVAL;
-    if (variant != 0 && (variant < 2 || variant > 4)) return fl::set_err(h, FL_EINVAL, "variant must be 0 or 2..4");
+    if (variant < 0 || variant > 4) return fl::set_err(h, FL_EINVAL, "variant must lie in 0..4");
     h->far_variant = variant;
     return FL_OK;
 }

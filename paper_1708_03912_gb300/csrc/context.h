@@ -39,6 +39,15 @@ struct RuleOffsets {
     int n_edge, n_vert, n_1d, n_ident, n_own, n_bvert;
 };
 
+// Compact record of a boundary facet (2D): the edge from e0 to e0 + (ex, ey) with its
+// inward unit normal and length.
+struct FacetRec {
+    double e0x, e0y;   // start point
+    double ex, ey;     // edge vector E1 - E0
+    double nx, ny;     // inward unit normal
+    double len, pad;
+};
+
 // One device allocation owned by a handle.
 struct DBuf {
     void* p = nullptr;
@@ -84,6 +93,7 @@ struct DevTables {
     void* pts_dw = nullptr; // nc * 16 double-word offsets (2D, float64 mode, k_far = 4)
     double* Dn = nullptr;   // nnear * 2 * Qn
     double* Bf = nullptr;   // nc * Qf boundary sums (far facets)
+    double* Bfp = nullptr;  // facet-chunk partials of Bf (double-word boundary kernel)
     double* eblk = nullptr; // nc * 6 far-independent part of each cell's diagonal block
     double* contrib = nullptr;
     double* csr_val = nullptr;
@@ -166,5 +176,8 @@ int prep_far_dw(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, c
 int launch_far_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro, int pw,
                   cudaStream_t st);
 int far_dw_variant(const fl_ctx* h, const Plan& P, int pw);
+int bnd_dw_chunks(int64_t nc);
+int launch_bnd_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro, int pw,
+                  cudaStream_t st);
 void far_dw_record(const Plan& P, int pw, int variant, double ms);
 }  // namespace fl

@@ -165,34 +165,58 @@ __device__ __forceinline__ void dw_mac(dw& s, dw c, dw k) {
 }
 __device__ __forceinline__ dw dw_renorm(dw x) { return fast_two_sum(x.h, x.l); }
 
-// x^{-1/2}: the float32 estimate t0 (about 2^-22) corrected by one Newton step written in
-// double-word terms, t = t0 (1 - rho)^{-1/2} ~ t0 (1 + rho/2 + 3 rho^2/8), rho = 1 - x t0^2
-// computed from the exact square of t0 (1 - g.h is exact for g.h in [1/2, 2]).
-__device__ __forceinline__ dw dw_rsqrt(dw x) {
-    const float t0 = rsqrt_approx(x.h);
-    const dw g = dw_mul(x, two_prod(t0, t0));
-    const float rho = __fsub_rn(__fsub_rn(1.f, g.h), g.l);
-    return {t0, __fmul_rn(__fmul_rn(t0, rho), __fmaf_rn(0.375f, rho, 0.5f))};
+// s += c k for non-negative c k and s: as dw_mac, with the running sum by Fast2Sum on the
+// ordered pair (max, min) of the two high parts
+__device__ __forceinline__ void dw_mac_pos(dw& s, dw c, dw k) {
+    const float p = __fmul_rn(c.h, k.h);
+    float e = __fmaf_rn(c.h, k.h, -p);
+    e = __fmaf_rn(c.h, k.l, e);
+    e = __fmaf_rn(c.l, k.h, e);
+    const dw t = fast_two_sum(fmaxf(s.h, p), fminf(s.h, p));
+    s.h = t.h;
+    s.l = __fadd_rn(s.l, __fadd_rn(t.l, e));
 }
-// x^{-1/4}: v = v0 (1 - rho)^{-1/4} ~ v0 (1 + rho/4 + 5 rho^2/32), rho = 1 - x v0^4
-__device__ __forceinline__ dw dw_rqrt(dw x) {
-    const float v0 = rsqrt_approx(sqrt_approx(x.h));
-    const dw g = dw_mul(x, dw_sqr(two_prod(v0, v0)));
-    const float rho = __fsub_rn(__fsub_rn(1.f, g.h), g.l);
-    return {v0, __fmul_rn(__fmul_rn(v0, rho), __fmaf_rn(0.15625f, rho, 0.25f))};
-}
-// r2^e, e = -PW/4, for PW in {5, 6, 7} (2D kernels of order s = 1/4, 1/2, 3/4)
+
+// r2^e, e = -PW/4, for PW in {5, 6, 7} (2D kernels of order s = 1/4, 1/2, 3/4).  From the
+// float32 estimate y0 of r2^{-1/2} (PW 6) or r2^{-1/4} (PW 5, 7), about 2^-21 relative:
+// k0 = y0^m in double-word terms (m = 3, 5, 7; built from the exact square of y0), then
+// rho = 1 - r2 y0^2 (or 1 - r2 y0^4) from the same products, and
+// k = k0 (1 - rho)^{-m/2 or -m/4} by the expansion to second order in rho (third-order
+// terms are below 2^-56).  The float32 correction term is rounded once: about 2^-42 relative
+// in the worst case, typically well below.
 template <int PW>
-__device__ __forceinline__ dw dw_kpow(dw r2) {
+__device__ __forceinline__ dw dw_kpow(dw x) {
     static_assert(PW == 5 || PW == 6 || PW == 7, "double-word powers: PW 5, 6, 7");
     if constexpr (PW == 6) {
-        const dw t = dw_rsqrt(r2);
-        return dw_mul(dw_sqr(t), t);
+        const float t0 = rsqrt_approx(x.h);
+        const dw t2 = two_prod(t0, t0);
+        const dw g = dw_mul(x, t2);  // x t0^2 ~ 1
+        const float rho = __fsub_rn(__fsub_rn(1.f, g.h), g.l);
+        dw k = two_prod(t2.h, t0);  // t0^3
+        k.l = __fmaf_rn(t2.l, t0, k.l);
+        const float c = __fmul_rn(rho, __fmaf_rn(1.875f, rho, 1.5f));  // (1-rho)^{-3/2} - 1
+        k.l = __fmaf_rn(k.h, c, k.l);
+        return k;
     } else {
-        const dw v = dw_rqrt(r2);
-        const dw v2 = dw_sqr(v), v4 = dw_sqr(v2);
-        if constexpr (PW == 5) return dw_mul(v4, v);
-        else return dw_mul(dw_mul(v4, v2), v);
+        const float v0 = rsqrt_approx(sqrt_approx(x.h));
+        const dw v2 = two_prod(v0, v0);
+        const dw v4 = dw_sqr(v2);
+        const dw g = dw_mul(x, v4);  // x v0^4 ~ 1
+        const float rho = __fsub_rn(__fsub_rn(1.f, g.h), g.l);
+        dw k;
+        float c;
+        if constexpr (PW == 5) {
+            k = two_prod(v4.h, v0);  // v0^5
+            k.l = __fmaf_rn(v4.l, v0, k.l);
+            c = __fmul_rn(rho, __fmaf_rn(1.40625f, rho, 1.25f));  // (1-rho)^{-5/4} - 1
+        } else {
+            const dw v6 = dw_mul(v4, v2);
+            k = two_prod(v6.h, v0);  // v0^7
+            k.l = __fmaf_rn(v6.l, v0, k.l);
+            c = __fmul_rn(rho, __fmaf_rn(2.40625f, rho, 1.75f));  // (1-rho)^{-7/4} - 1
+        }
+        k.l = __fmaf_rn(k.h, c, k.l);
+        return k;
     }
 }
 

@@ -17,8 +17,9 @@
 // row sums are combined in a fixed order, the column sums once per tile, so the result is
 // bitwise reproducible.  Outputs are those of the float64 far kernel: the per-tile partial
 // blocks over the local DOF lists and the per-point row sums for the diagonal blocks.
-// Variants (the launch's minimum resident blocks per SM, which bounds the registers a
-// thread may use) are swept by fl_tune_assemble and recorded in the tuning table.
+// Launch variants (the unroll of the inner point loop, and the minimum resident blocks per
+// SM, which bounds the registers a thread may use) are swept by fl_tune_assemble and
+// recorded in the tuning table.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -97,7 +98,7 @@ __device__ __forceinline__ dw reduce_scatter4_dw(const dw (&v)[4], int lane) {
     return w;
 }
 
-template <int PW, int MINB>
+template <int PW, int UB, int MINB>
 __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
     far_tile_dw_kernel(const DwTileArgs A, const __grid_constant__ FarRuleDW R, int maxL) {
     constexpr int Q = DW_Q, NA = Q / DW_WARPS;
@@ -112,8 +113,10 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
     const int nI = (int)min((int64_t)32, nc - K0);
 
     float4* sQ = reinterpret_cast<float4*>(smem_raw);                  // [Q][32] column points
-    dw* sOff = reinterpret_cast<dw*>(sQ + Q * 32);                      // [DW_WARPS][9][32] partial blocks
-    double* sD = reinterpret_cast<double*>(sOff + DW_WARPS * 9 * 32);  // [32][Q] diagonal tile row sums
+    dw* sS = reinterpret_cast<dw*>(sQ + Q * 32);                        // [DW_WARPS][Q][32] column sums
+    dw* sOff = sS + DW_WARPS * Q * 32;                                  // [DW_WARPS][9][32] partial blocks
+    dw* sW = sOff + DW_WARPS * 9 * 32;                                  // [Q * NV] weight x shape value
+    double* sD = reinterpret_cast<double*>(sW + Q * NV);                // [32][Q] diagonal tile row sums
     double* sCen = sD + 32 * Q;                                         // [32][2]
     double* sJac = sCen + 64;                                           // [32]
     double* priv = sJac + 32;                                           // [NV][maxL][32]
@@ -124,6 +127,8 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
     const bool valid = Kt < nc;
     for (int b = warp; b < Q; b += DW_WARPS)
         sQ[b * 32 + lane] = valid ? A.pts[Kt * Q + b] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < DW_WARPS * Q * 32; i += blockDim.x) sS[i] = {0.f, 0.f};
+    for (int i = threadIdx.x; i < Q * NV; i += blockDim.x) sW[i] = R.wphi[i];
     for (int i = threadIdx.x; i < nI * 2; i += blockDim.x) sCen[i] = A.cen[K0 * 2 + i];
     for (int i = threadIdx.x; i < nI * NV; i += blockDim.x) sLoc[i] = A.loc[K0 * NV + i];
     for (int i = threadIdx.x; i < nI; i += blockDim.x) {
@@ -147,9 +152,7 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
         ee = A.ex_ptr[Kt + 1];
     }
     const dw wjd = dw_from(wj);
-    dw S[Q];  // column sums of this lane's cell over this warp's row points
-#pragma unroll
-    for (int b = 0; b < Q; ++b) S[b] = {0.f, 0.f};
+    dw* mS = sS + warp * Q * 32 + lane;  // this thread's column sums, stride 32
     // an inactive lane's row cell is moved far away (every value stays finite) and its
     // kernel values are multiplied by zero
     const double far_away = 1e15;
@@ -172,6 +175,43 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
         const dw Dy = dw_from(act ? sCen[kk * 2 + 1] - cj[1] : far_away);
         const double wK = sJac[kk];
         const dw wKd = dw_from(wK);
+        // this warp's row points a = warp + DW_WARPS m: offsets from c_K', weights; the weights
+        // of an inactive lane are zero, so its (finite) kernel values add nothing
+        dw X[NA], Y[NA], waK[NA], t[NA][NV];
+#pragma unroll
+        for (int m = 0; m < NA; ++m) {
+            const int a = warp + DW_WARPS * m;
+            const float4 pa = __ldg(A.pts + K * Q + a);
+            X[m] = dw_add(Dx, dw{pa.x, pa.y});
+            Y[m] = dw_add(Dy, dw{pa.z, pa.w});
+            waK[m] = dw_mul(R.w[a], wKd);
+            waK[m].h = __fmul_rn(waK[m].h, mask);
+            waK[m].l = __fmul_rn(waK[m].l, mask);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) t[m][v] = {0.f, 0.f};
+        }
+#pragma unroll UB
+        for (int b = 0; b < Q; ++b) {
+            const float4 q = sQ[b * 32 + lane];
+            const dw c0 = sW[b * NV], c1 = sW[b * NV + 1], c2 = sW[b * NV + 2];
+            dw sb = mS[b * 32];
+#pragma unroll
+            for (int m = 0; m < NA; ++m) {
+                const dw dx = dw_sub(X[m], dw{q.x, q.y});
+                const dw dy = dw_sub(Y[m], dw{q.z, q.w});
+                // |x - y|^2 = dx^2 + dy^2: exact squares of the high parts, both non-negative
+                const dw px = two_prod(dx.h, dx.h), py = two_prod(dy.h, dy.h);
+                dw r2 = fast_two_sum(fmaxf(px.h, py.h), fminf(px.h, py.h));
+                const float cr = __fmaf_rn(dx.h, dx.l, __fmul_rn(dy.h, dy.l));
+                r2.l = __fadd_rn(r2.l, __fmaf_rn(2.f, cr, __fadd_rn(px.l, py.l)));
+                const dw kv = dw_kpow<PW>(r2);
+                dw_mac_pos(t[m][0], c0, kv);
+                dw_mac_pos(t[m][1], c1, kv);
+                dw_mac_pos(t[m][2], c2, kv);
+                dw_mac_pos(sb, waK[m], kv);
+            }
+            mS[b * 32] = sb;
+        }
         dw off[NV][NV];
 #pragma unroll
         for (int i = 0; i < NV; ++i)
@@ -181,40 +221,19 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
 #pragma unroll
         for (int m = 0; m < NA; ++m) {
             const int a = warp + DW_WARPS * m;
-            const float4 pa = __ldg(A.pts + K * Q + a);
-            const dw X = dw_add(Dx, dw{pa.x, pa.y});
-            const dw Y = dw_add(Dy, dw{pa.z, pa.w});
-            const dw waK = dw_mul(R.w[a], wKd);
-            dw t[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) t[v] = {0.f, 0.f};
+            for (int v = 0; v < NV; ++v) t[m][v] = dw_renorm(t[m][v]);
+            ru[m] = dw_mul(dw_add(dw_add(t[m][0], t[m][1]), t[m][2]), wjd);
+            ru[m].h = __fmul_rn(ru[m].h, mask);
+            ru[m].l = __fmul_rn(ru[m].l, mask);
 #pragma unroll
-            for (int b = 0; b < Q; ++b) {
-                const float4 q = sQ[b * 32 + lane];
-                const dw dx = dw_sub(X, dw{q.x, q.y});
-                const dw dy = dw_sub(Y, dw{q.z, q.w});
-                // |x - y|^2 = dx^2 + dy^2: exact squares of the high parts, both non-negative
-                const dw px = two_prod(dx.h, dx.h), py = two_prod(dy.h, dy.h);
-                dw r2 = fast_two_sum(fmaxf(px.h, py.h), fminf(px.h, py.h));
-                const float cr = __fmaf_rn(dx.h, dx.l, __fmul_rn(dy.h, dy.l));
-                r2.l = __fadd_rn(r2.l, __fmaf_rn(2.f, cr, __fadd_rn(px.l, py.l)));
-                dw kv = dw_kpow<PW>(r2);
-                kv.h = __fmul_rn(kv.h, mask);
-                kv.l = __fmul_rn(kv.l, mask);
+            for (int i = 0; i < NV; ++i) {
+                const dw c = R.wphi[a * NV + i];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) dw_mac(t[v], R.wphi[b * NV + v], kv);
-                dw_mac(S[b], waK, kv);
+                for (int j = 0; j < NV; ++j) dw_mac_pos(off[i][j], c, t[m][j]);
             }
-#pragma unroll
-            for (int v = 0; v < NV; ++v) t[v] = dw_renorm(t[v]);
-            ru[m] = dw_mul(dw_add(dw_add(t[0], t[1]), t[2]), wjd);
-#pragma unroll
-            for (int i = 0; i < NV; ++i)
-#pragma unroll
-                for (int j = 0; j < NV; ++j) dw_mac(off[i][j], R.wphi[a * NV + i], t[j]);
         }
-#pragma unroll
-        for (int b = 0; b < Q; ++b) S[b] = dw_renorm(S[b]);
+        for (int b = 0; b < Q; ++b) mS[b * 32] = dw_renorm(mS[b * 32]);
         // row sums of cell K over this tile's columns: lane l ends with the total of row point
         // warp + DW_WARPS (2 ((l >> 4) & 1) + ((l >> 3) & 1))
         {
@@ -248,18 +267,12 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
         }
         __syncthreads();
     }
-    // column sums: the warps' parts added in warp order (sOff reused as [Q][32])
-    dw* sS = sOff;
-    for (int w = 0; w < DW_WARPS; ++w) {
-        if (warp == w) {
-#pragma unroll
-            for (int b = 0; b < Q; ++b) sS[b * 32 + lane] = (w == 0) ? S[b] : dw_add(sS[b * 32 + lane], S[b]);
-        }
-        __syncthreads();
-    }
+    // column sums of this tile's cells: the warps' parts added in warp order
     if (valid) {
         for (int b = warp; b < Q; b += DW_WARPS) {
-            double v = dw_to(sS[b * 32 + lane]);
+            dw acc = sS[b * 32 + lane];
+            for (int w = 1; w < DW_WARPS; ++w) acc = dw_add(acc, sS[(w * Q + b) * 32 + lane]);
+            double v = dw_to(acc);
             if (I == J) v += sD[lane * Q + b];
             A.Pd[((int64_t)Kt * A.nblk + I) * Q + b] = v;
         }
@@ -279,12 +292,129 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
     }
 }
 
+// Element x far boundary facet sums of the boundary term (Section 2: the Omega x Omega^c part
+// of the form reduced to the boundary), float64 mode, double-word arithmetic.  For cell k
+// and its far rule point x_a: Bf[k][a] = sum over far facets e of sum_b w_b |e|
+// n_e.(x_a - y_b) |x_a - y_b|^{-2-2s}, y_b the k_far-point Gauss rule on e.  n_e.(x - y)
+// is taken as n.(c_k - e0) + n.(x_a - c_k) - t_b n.E (the last term is zero up to the
+// rounding of the stored normal and is kept as a float32 correction).  One lane per cell,
+// BW_WARPS warps stride over the facets, their partial sums are added in warp order.
+constexpr int BW_WARPS = 4;
+constexpr int BW_K = 4;  // Gauss points per facet (k_far = 4)
+
+struct BndRuleDW {
+    dw t[BW_K];
+    dw w[BW_K];
+};
+
+template <int PW>
+__global__ void __launch_bounds__(32 * BW_WARPS)
+    bnd_far_dw_kernel(int64_t nc, int64_t nf, const double* __restrict__ cen, const float4* __restrict__ pts,
+                      const char* __restrict__ hasdof, const int* __restrict__ ef_ptr, const int* __restrict__ ef_fac,
+                      const FacetRec* __restrict__ FR, const __grid_constant__ BndRuleDW G, double* __restrict__ Bf) {
+    constexpr int Q = DW_Q;
+    // facet chunk blockIdx.y of gridDim.y: its partial sums go to Bf + blockIdx.y nc Q
+    const int64_t f_lo = nf * blockIdx.y / gridDim.y, f_hi = nf * (blockIdx.y + 1) / gridDim.y;
+    Bf += (int64_t)blockIdx.y * nc * Q;
+    __shared__ float4 sX[Q][32];
+    __shared__ dw part[BW_WARPS][Q][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t k = (int64_t)blockIdx.x * 32 + lane;
+    const bool valid = k < nc && hasdof[k];
+    for (int a = wid; a < Q; a += BW_WARPS) sX[a][lane] = valid ? pts[k * Q + a] : make_float4(0.f, 0.f, 0.f, 0.f);
+    double c[2] = {0.0, 0.0};
+    int ep = 0, ee = 0;
+    if (valid) {
+        c[0] = cen[2 * k];
+        c[1] = cen[2 * k + 1];
+        ep = ef_ptr[k];
+        ee = ef_ptr[k + 1];
+        while (ep < ee && ef_fac[ep] < f_lo) ++ep;
+    }
+    __syncthreads();
+    dw B[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) B[a] = {0.f, 0.f};
+    const bool any = __any_sync(0xffffffffu, valid);
+    const double far_away = 1e15;
+    for (int64_t f = f_lo + wid; any && f < f_hi; f += BW_WARPS) {
+        bool act = valid;
+        if (act) {
+            while (ep < ee && ef_fac[ep] < f) ++ep;
+            if (ep < ee && ef_fac[ep] == f) act = false;
+        }
+        const FacetRec r = FR[f];
+        const float mask = act ? 1.f : 0.f;
+        const dw Dx = dw_from(act ? c[0] - r.e0x : far_away), Dy = dw_from(act ? c[1] - r.e0y : far_away);
+        const dw Ex = dw_from(r.ex), Ey = dw_from(r.ey), nx = dw_from(r.nx), ny = dw_from(r.ny);
+        const dw Ld = dw_from(r.len);
+        const float nE = (float)(r.nx * r.ex + r.ny * r.ey);
+        dw Ux[BW_K], Uy[BW_K], LW[BW_K];
+        float c2[BW_K];
+#pragma unroll
+        for (int b = 0; b < BW_K; ++b) {
+            Ux[b] = dw_sub(Dx, dw_mul(G.t[b], Ex));
+            Uy[b] = dw_sub(Dy, dw_mul(G.t[b], Ey));
+            LW[b] = dw_mul(G.w[b], Ld);
+            c2[b] = __fmul_rn(__fmul_rn(G.t[b].h, nE), LW[b].h);
+        }
+        const dw d0 = dw_add(dw_mul(nx, Dx), dw_mul(ny, Dy));  // n.(c_k - e0)
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const float4 q = sX[a][lane];
+            const dw X = {q.x, q.y}, Y = {q.z, q.w};
+            const dw da = dw_add(d0, dw_add(dw_mul(nx, X), dw_mul(ny, Y)));  // n.(x_a - e0)
+            dw T = {0.f, 0.f};
+            float corr = 0.f;
+#pragma unroll
+            for (int b = 0; b < BW_K; ++b) {
+                dw dx = two_sum(Ux[b].h, X.h);
+                dx.l = __fadd_rn(dx.l, __fadd_rn(Ux[b].l, X.l));
+                dw dy = two_sum(Uy[b].h, Y.h);
+                dy.l = __fadd_rn(dy.l, __fadd_rn(Uy[b].l, Y.l));
+                const dw px = two_prod(dx.h, dx.h), py = two_prod(dy.h, dy.h);
+                dw r2 = fast_two_sum(fmaxf(px.h, py.h), fminf(px.h, py.h));
+                const float cr = __fmaf_rn(dx.h, dx.l, __fmul_rn(dy.h, dy.l));
+                r2.l = __fadd_rn(r2.l, __fmaf_rn(2.f, cr, __fadd_rn(px.l, py.l)));
+                dw kv = dw_kpow<PW>(r2);
+                kv.h = __fmul_rn(kv.h, mask);
+                kv.l = __fmul_rn(kv.l, mask);
+                dw_mac(T, LW[b], kv);
+                corr = __fmaf_rn(c2[b], kv.h, corr);
+            }
+            dw_mac(B[a], da, dw_renorm(T));
+            B[a].l = __fsub_rn(B[a].l, corr);
+        }
+#pragma unroll
+        for (int a = 0; a < Q; ++a) B[a] = dw_renorm(B[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) part[wid][a][lane] = B[a];
+    __syncthreads();
+    if (valid)
+        for (int a = wid; a < Q; a += BW_WARPS) {
+            dw acc = part[0][a][lane];
+            for (int w = 1; w < BW_WARPS; ++w) acc = dw_add(acc, part[w][a][lane]);
+            Bf[k * Q + a] = dw_to(acc);
+        }
+}
+
+// partial boundary sums of the facet chunks -> Bf, chunks added in order
+__global__ void bnd_chunks_sum(int64_t m, int nch, const double* __restrict__ part, double* __restrict__ Bf) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double acc = part[i];
+    for (int c = 1; c < nch; ++c) acc += part[(int64_t)c * m + i];
+    Bf[i] = acc;
+}
+
 size_t dw_smem_bytes(int maxL) {
-    return (size_t)DW_Q * 32 * sizeof(float4) + (size_t)DW_WARPS * 9 * 32 * sizeof(dw) + 32 * DW_Q * sizeof(double) +
+    return (size_t)DW_Q * 32 * sizeof(float4) + (size_t)DW_WARPS * DW_Q * 32 * sizeof(dw) +
+           (size_t)DW_WARPS * 9 * 32 * sizeof(dw) + DW_Q * NV * sizeof(dw) + 32 * DW_Q * sizeof(double) +
            96 * sizeof(double) + (size_t)NV * maxL * 32 * sizeof(double) + 32 * NV * sizeof(int) + 32 * sizeof(int);
 }
 
-template <int PW, int MINB>
+template <int PW, int UB, int MINB>
 int launch_t(fl_ctx* h, const Plan& P, DevTables& t, const FarRuleDW& R, cudaStream_t st) {
     DwTileArgs A;
     A.cen = t.cen;
@@ -306,7 +436,7 @@ int launch_t(fl_ctx* h, const Plan& P, DevTables& t, const FarRuleDW& R, cudaStr
     const int maxL = std::max(1, P.maxL);
     const size_t smem = dw_smem_bytes(maxL);
     const int64_t ntiles = (int64_t)P.tiles.size() / 2;
-    auto kern = far_tile_dw_kernel<PW, MINB>;
+    auto kern = far_tile_dw_kernel<PW, UB, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_err(h, FL_ECUDA, std::string("far_tile_dw smem: ") + cudaGetErrorString(e));
     if (ntiles > 0) {
@@ -318,18 +448,34 @@ int launch_t(fl_ctx* h, const Plan& P, DevTables& t, const FarRuleDW& R, cudaStr
     return FL_OK;
 }
 
+// launch variants: (unroll of the loop over the column cell's points, minimum resident
+// blocks per SM)   1: (4, 1)   2: (1, 2)   3: (2, 2)   4: (1, 3)
+constexpr int DW_VARIANTS = 4;
+
 template <int PW>
 int launch_pw(fl_ctx* h, const Plan& P, DevTables& t, const FarRuleDW& R, int variant, cudaStream_t st) {
     switch (variant) {
-        case 2: return launch_t<PW, 2>(h, P, t, R, st);
-        case 4: return launch_t<PW, 4>(h, P, t, R, st);
-        default: return launch_t<PW, 3>(h, P, t, R, st);
+        case 1: return launch_t<PW, 4, 1>(h, P, t, R, st);
+        case 2: return launch_t<PW, 1, 2>(h, P, t, R, st);
+        case 4: return launch_t<PW, 1, 3>(h, P, t, R, st);
+        default: return launch_t<PW, 2, 2>(h, P, t, R, st);
     }
 }
 
 std::string kernel_name(int pw) { return "far_tile_dw<" + std::to_string(pw) + ">"; }
 
 }  // namespace
+
+// facet chunks of the double-word boundary kernel: about four waves of 3 blocks per SM
+int bnd_dw_chunks(int64_t nc) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    const int64_t nb = std::max<int64_t>(1, (nc + 31) / 32);
+    return (int)std::min<int64_t>(8, std::max<int64_t>(1, (12 * (int64_t)sms + nb - 1) / nb));
+}
 
 bool far_dw_applies(const fl_ctx* h, const Plan& P, int pw) {
     return P.dim == 2 && h->opt.k_far == 4 && (pw == 5 || pw == 6 || pw == 7) && !h->far_f64_pipe;
@@ -345,12 +491,12 @@ int prep_far_dw(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, c
     return e == cudaSuccess ? FL_OK : set_err(h, FL_ECUDA, std::string("prep_points_dw: ") + cudaGetErrorString(e));
 }
 
-// Variant (minimum resident blocks per SM) of the launch: the caller's choice if > 0, else
-// the tuning table's entry for this kernel and cell count, else 3.
+// Variant of the launch: the caller's choice if > 0, else the tuning table's entry for this
+// kernel and cell count, else 3 (the fastest on the disc workloads measured).
 int far_dw_variant(const fl_ctx* h, const Plan& P, int pw) {
     if (h->far_variant > 0) return h->far_variant;
     int p0 = 0, p1 = 0;
-    if (tune_lookup(device_name(), kernel_name(pw), P.nc, 1, 1, &p0, &p1) && p0 >= 2 && p0 <= 4) return p0;
+    if (tune_lookup(device_name(), kernel_name(pw), P.nc, 1, 1, &p0, &p1) && p0 >= 1 && p0 <= DW_VARIANTS) return p0;
     return 3;
 }
 
@@ -373,6 +519,40 @@ int launch_far_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<doub
         case 6: return launch_pw<6>(h, P, t, R, variant, st);
         default: return launch_pw<7>(h, P, t, R, variant, st);
     }
+}
+
+int launch_bnd_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro, int pw,
+                  cudaStream_t st) {
+    BndRuleDW G;
+    for (int b = 0; b < BW_K; ++b) {
+        const double tb = rb[ro.glf_t + b], wb = rb[ro.glf_w + b];
+        G.t[b].h = (float)tb;
+        G.t[b].l = (float)(tb - (double)G.t[b].h);
+        G.w[b].h = (float)wb;
+        G.w[b].l = (float)(wb - (double)G.w[b].h);
+    }
+    const unsigned nb = (unsigned)((P.nc + 31) / 32);
+    const FacetRec* FR = (const FacetRec*)t.facet_rec;
+    // facets split into chunks (one grid row each) so that small meshes still fill the GPU
+    const int nch = bnd_dw_chunks(P.nc);
+    double* out = nch > 1 ? t.Bfp : t.Bf;
+    if (nb > 0) {
+#define FL_BNDW(PWV)                                                                                             \
+    bnd_far_dw_kernel<PWV><<<dim3(nb, nch), 32 * BW_WARPS, 0, st>>>(P.nc, P.nf, t.cen, (const float4*)t.pts_dw, \
+                                                                   t.hasdof, t.ef_ptr, t.ef_fac, FR, G, out)
+        if (pw == 5) FL_BNDW(5);
+        else if (pw == 6) FL_BNDW(6);
+        else FL_BNDW(7);
+#undef FL_BNDW
+        count_launch(1);
+        if (nch > 1) {
+            const int64_t m = P.nc * DW_Q;
+            bnd_chunks_sum<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, nch, t.Bfp, t.Bf);
+            count_launch(1);
+        }
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FL_OK : set_err(h, FL_ECUDA, std::string("bnd_far_dw: ") + cudaGetErrorString(e));
 }
 
 void far_dw_record(const Plan& P, int pw, int variant, double ms) {
