@@ -1,18 +1,24 @@
 """Benchmark of the dense fractional-Laplacian hot path on GB300.
 
-One step = one pass of the hot path on the quasi-uniform unit-disc workload
-(25 rings, 3929 triangles, 1887 interior DOFs, s = 0.75, f = 1):
-  assemble A^s (float32 separated pairs, float64 touching pairs / boundary /
-  reductions) -> float32 copy -> load vector -> float64-refined Jacobi-PCG on the
-  float32 copy to ||b - A u|| <= 1e-8 ||b||.
-value = element pairs per second over the whole step: N_el^2 ordered pairs (K, K')
-of the double sum of Section 5 per step, times steps, divided by the timed device
-time (max over ranks).  Side figures: assembly-only pair rate in both precisions,
-the float64 / float32 dense matvec bandwidth on the assembled matrix, and the time
-to 1e-8 of the refined solve against plain float64 Jacobi-PCG.
+One step = one pass of the hot path on the L-shape workload of Section 7.3: the domain
+[0,2]^2 minus [1,2]^2, refined toward the re-entrant corner and the boundary by
+newest-vertex bisection (level 5: 73,432 triangles, 35,693 interior DOFs), s = 1/2, f = 1:
+  assemble A^s in the float64 mode -> float32 copy -> load vector -> float64-refined
+  Jacobi-PCG (float32 inner iterations on the float32 copy) to ||b - A u|| <= 1e-8 ||b||.
+In the float64 mode the separated pairs at vertex-graph distance >= 2 and the element x far
+facet sums run in double-word arithmetic on the float32 pipe (about 2^-47 relative per
+operation); every other stage and every reduction is float64.  The matrix meets the float64
+parity bar (1e-12 per entry) against the oracle.
+value = N_el^2 ordered element pairs (the terms of the double sum of Section 5) per step,
+times steps, divided by the timed device time (max over ranks).  Inputs are resident in HBM
+(the dense matrices, 15 GB, are far larger than L2).  Side figures: the other
+configurations (1D interval, quasi-uniform disc, graded disc at three orders, the batched
+solves), the mixed mode and its error, the float64-pipe assembly, dense matvec bandwidth,
+the L-shape preconditioners, stage times and the end-to-end rate through the public API.
 
---impl reference times the CPU oracle (oracle/) on a bounded sample of the same
-workload (element-pair rows), on this machine's host cores.
+--impl reference times the CPU oracle (oracle/) on a bounded sample of the same workload
+(one seeded DOF row per step: every element pair of its support), on this machine's host
+cores.  --case NAME runs a small named workload for profilers.
 """
 import argparse
 import json
@@ -30,18 +36,30 @@ sys.path.insert(0, ROOT)
 for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_var, os.environ.get("OMP_NUM_THREADS", "1"))
 
-WORKLOAD = {"workload": "disc-quasi-uniform-25-rings", "domain": "unit disc", "rings": 25, "triangles": 3929,
-            "dofs": 1887, "s": 0.75, "f": "1", "dtype_assembly": "f32 separated pairs + f64 near/boundary",
-            "solve": "f64-refined Jacobi-PCG on f32 copy to 1e-8", "l2": "flushed between timed steps (512 MiB write)"}
+LSHAPE_LEVEL, LSHAPE_S = 5, 0.5
+WORKLOAD = {"workload": "lshape-level5-s0.5", "domain": "L-shape [0,2]^2 minus [1,2]^2 (Section 7.3)",
+            "mesh": "uniform 96 triangles + 5 levels of newest-vertex bisection toward (1,1) and the boundary",
+            "triangles": 73432, "dofs": 35693, "s": LSHAPE_S, "f": "1",
+            "assembly": "float64 mode: separated pairs (distance >= 2) and far boundary facets in double-word "
+                        "arithmetic on the float32 pipe, all other stages and reductions float64; 1e-12 per entry",
+            "solve": "float64-refined Jacobi-PCG, float32 inner iterations on the float32 copy, to 1e-8",
+            "l2": "inputs larger than L2 (A: 10.2 GB float64, 5.1 GB float32)"}
 METRIC = "element pairs/s assembled; matvec HBM GB/s; solve time to 1e-8 vs plain FP64"
-# the L-shape workload: nested levels 1..4 of the corner- and boundary-refined L-shape
-LSHAPE = {"level": 4, "s": 0.5}
-# the batched workload: 4 orders x 64 loads on the disc graded toward the boundary
-BATCH = {"rings": 30, "mu": 2.0, "s": [0.25, 0.5, 0.75, 0.9], "nrhs": 64}
-# DRAM bytes (read 1.434 MB + write 2.044 MB) per launch of far_tile_kernel<2,float,16,0> on this
-# workload, from one ncu capture of the current kernel; reset to None whenever that kernel changes.
-FAR_KERNEL_DRAM_BYTES = 3.478e6
 UNIT = "element pairs/s"
+# configurations measured beside the headline
+DISC = {"rings": 25, "s": 0.75}                       # quasi-uniform disc, 3929 triangles
+GDISC = {"rings": 30, "mu": 2.0, "s": [0.25, 0.5, 0.75]}  # graded disc, 22043 triangles, n = 8195
+BATCH = {"rings": 30, "mu": 2.0, "s": [0.25, 0.5, 0.75, 0.9], "nrhs": 64}
+INTERVAL = {"cells": 128, "s": 0.25}
+# FP32-pipe operations of one double-word kernel evaluation (difference, |x-y|^2, power,
+# three shape-weighted sums and the column sum), per order: the algorithmic work unit of the
+# roofline below (per-point and per-tile work is not counted)
+DW_OPS_PER_EVAL = {5: 92, 6: 88, 7: 96}
+# DRAM bytes per far pair of far_tile_dw_kernel (partial tiles and per-point row sums written,
+# cell data read): 51.9 MB read + 2810.2 MB written over 242,559,275 far pairs in one ncu
+# capture of far_tile_dw_kernel<6,2,2> on the graded disc (22043 triangles, s = 1/2); the
+# kernel's traffic grows with the far pairs (tiles and row-sum blocks both scale with N_el^2)
+FAR_DW_DRAM_BYTES_PER_PAIR = (51888384 + 2810236928) / 242559275
 
 
 def load_peaks():
@@ -116,42 +134,50 @@ def job_rate(total_ms, steps, units_per_step, world, dist=None, device="cpu"):
     return t_max, world * steps * units_per_step / (t_max / 1000.0)
 
 
-def oracle_sample(seconds_target=15.0):
-    """Time the CPU oracle on element-pair rows of the same workload.  Returns
-    (ordered element pairs evaluated per second, threads, sample description)."""
-    import numpy as np
+_ORACLE = {}
 
+
+def oracle_sample(nrows):
+    """Time the CPU oracle on `nrows` seeded DOF rows of the headline workload (every element
+    pair with a cell in those rows' supports).  Returns (ordered element pairs per second,
+    seconds, threads, sample description)."""
     from oracle import OracleMesh, assemble_matrix
     from paper_1708_03912_gb300 import synth
 
-    V, T = synth.disc(WORKLOAD["rings"])
-    om = OracleMesh(V, T)
-    s = WORKLOAD["s"]
-    n = len(om.dofs(s)[0])
-    rows = synth.random_rows(n, 4)
-    # ordered pairs covered: each active cell against every cell (both orders of each unordered pair)
+    if "om" not in _ORACLE:
+        V, T = synth.lshape(0.25, LSHAPE_LEVEL)
+        _ORACLE["om"] = OracleMesh(V, T)
+        _ORACLE["k"] = 0
+    om = _ORACLE["om"]
+    vod = om.dofs(LSHAPE_S)[0]
+    # successive calls take successive rows of one seeded permutation
+    import numpy as np
+
+    perm = np.random.default_rng(synth.SEED).permutation(len(vod))
+    rows = np.sort(perm[_ORACLE["k"]:_ORACLE["k"] + nrows])
+    _ORACLE["k"] += nrows
     active = set()
-    vod = om.dofs(s)[0]
     for r in rows:
         active.update(om.cells_of_vertex[vod[r]])
     t0 = time.perf_counter()
-    assemble_matrix(om, s, rows=rows)
+    assemble_matrix(om, LSHAPE_S, rows=rows)
     dt = time.perf_counter() - t0
     pairs = 2 * len(active) * om.nc - len(active) ** 2  # unordered pairs touching the active set, x2 ordered
     threads = int(os.environ.get("OMP_NUM_THREADS", "1"))
-    return pairs / dt, dt, threads, f"{len(rows)} seeded rows = {len(active)} cells x {om.nc} partner cells"
+    return pairs / dt, dt, threads, (f"{len(rows)} seeded DOF row(s) = {len(active)} cells x {om.nc} partner cells "
+                                     f"of the L-shape level {LSHAPE_LEVEL}, numpy float64")
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    vals = []
     for _ in range(args.warmup):
-        oracle_sample()
+        oracle_sample(1)
+    vals = []
     t_all = 0.0
     for _ in range(args.steps):
-        v, dt, threads, desc = oracle_sample()
+        v, dt, threads, desc = oracle_sample(1)
         vals.append(v)
         t_all += dt
     value = statistics.mean(vals)
@@ -160,7 +186,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(WORKLOAD),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": desc + ", numpy float64, host cores of the GPU box"},
+                             "sample": desc + ", host cores of the GPU box"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -186,7 +212,7 @@ def build_problems(F, synth, m, svals, nrhs, nslices, V):
 
 
 # small named workloads for profilers (`--case`): rings, grading exponent, s
-CASES = {"disc25": (25, 1.0, 0.75), "gdisc30": (30, 2.0, 0.75), "disc10": (10, 1.0, 0.75)}
+CASES = {"disc25": (25, 1.0, 0.75), "gdisc30": (30, 2.0, 0.75), "gdisc30s5": (30, 2.0, 0.5), "disc10": (10, 1.0, 0.75)}
 
 
 def run_case(args):
@@ -223,25 +249,224 @@ def run_case(args):
     return 0
 
 
-def lshape_section(F, synth, timed, dev):
-    """L-shape level LSHAPE["level"] (s = 1/2): Jacobi-PCG, multigrid-preconditioned CG on the nested
-    levels below it, and flexible CG with the learned stencil trained on a coarser level."""
+def scaled_error(A, E, chunk=2048):
+    """max |A_ij - E_ij| / sqrt(E_ii E_jj) over two device matrices (float64), row chunks."""
     import torch
 
-    s = LSHAPE["s"]
-    lev = LSHAPE["level"]
-    meshes = [synth.lshape(0.25, l) for l in range(lev, 0, -1)]  # fine to coarse
-    hs = [F.fl_create(V, T) for V, T in meshes]
-    mf = F.Mesh(*meshes[0])
-    A = mf.assemble(s, "mixed")
+    d = torch.sqrt(torch.diagonal(E))
+    worst = 0.0
+    for r0 in range(0, A.shape[0], chunk):
+        r1 = min(A.shape[0], r0 + chunk)
+        e = (A[r0:r1] - E[r0:r1]).abs_() / (d[r0:r1, None] * d[None, :])
+        worst = max(worst, float(e.max()))
+    return worst
+
+
+def _opts(F, tol):
+    o = F.fl_default_solve_opts()
+    o.tol = tol
+    return o
+
+
+def interval_section(F, synth, timed):
+    """1D interval (-1, 1), 128 uniform cells, s = 1/4, f = 1: float64 assembly and CG to 1e-12;
+    the energy b.u against the closed form of Section 7 (the Galerkin gap is positive)."""
+    import math
+
+    s = INTERVAL["s"]
+    V, T = synth.interval(INTERVAL["cells"])
+    m = F.Mesh(V, T)
+    A = m.assemble(s, "fp64")
+    b = m.load_vector(s)
+    u, info = m.solve(A, b, tol=1e-12)
+    energy = float((b * u).sum())
+    exact = 2.0 ** (-2 * s) * math.pi / (math.gamma(s + 0.5) * math.gamma(s + 1.5))
+    out = {"workload": f"interval (-1,1), {INTERVAL['cells']} cells, s = {s}, f = 1", "n": A.shape[0],
+           "assembly_ms": timed(lambda: m.assemble(s, "fp64", out=A), reps=5),
+           "solve_ms_to_1e-12": timed(lambda: m.solve(A, b, tol=1e-12), reps=5), "iterations": info.iterations,
+           "energy": energy, "energy_exact": exact, "energy_gap": exact - energy}
+    m.close()
+    return out
+
+
+def disc_section(F, synth, timed):
+    """Quasi-uniform disc (3929 triangles, 1887 DOFs), s = 3/4: float64 vs mixed assembly, the
+    mixed mode's error against the float64 matrix, the float64-pipe far kernel for reference."""
+    import torch
+
+    s = DISC["s"]
+    V, T = synth.disc(DISC["rings"])
+    m = F.Mesh(V, T)
+    A = m.assemble(s, "fp64")
+    Am = m.assemble(s, "mixed")
+    n_el = len(T)
+    t64 = timed(lambda: m.assemble(s, "fp64", out=A), reps=5)
+    tmx = timed(lambda: m.assemble(s, "mixed", out=Am), reps=5)
+    m64 = F.Mesh(V, T, far_f64_pipe=True)
+    A64p = m64.assemble(s, "fp64")
+    tpipe = timed(lambda: m64.assemble(s, "fp64", out=A64p), reps=2)
+    out = {"workload": f"quasi-uniform unit disc, {DISC['rings']} rings, {n_el} triangles, n = {A.shape[0]}, s = {s}",
+           "fp64_assembly_ms": t64, "mixed_assembly_ms": tmx, "fp64_pipe_assembly_ms": tpipe,
+           "pairs_per_s": {"fp64": n_el * n_el / (t64 / 1000), "mixed": n_el * n_el / (tmx / 1000),
+                           "fp64_pipe": n_el * n_el / (tpipe / 1000)},
+           "mixed_error_scaled": scaled_error(Am, A), "dw_vs_fp64_pipe_scaled": scaled_error(A, A64p)}
+    m64.close()
+    m.close()
+    del A, Am, A64p
+    torch.cuda.empty_cache()
+    return out
+
+
+def gdisc_section(F, synth, timed):
+    """Graded disc (22043 triangles, n = 8195) at s = 1/4, 1/2, 3/4: float64 assembly, the float32
+    copy (256 MB) with float64-refined CG to 1e-8 against plain float64 Jacobi-PCG."""
+    import torch
+
+    V, T = synth.disc(GDISC["rings"], GDISC["mu"])
+    m = F.Mesh(V, T)
+    n_el = len(T)
+    out = {"workload": f"unit disc graded toward the boundary, {GDISC['rings']} rings, mu {GDISC['mu']}, "
+                       f"{n_el} triangles", "per_s": {}}
+    for s in GDISC["s"]:
+        A = m.assemble(s, "fp64")
+        n = A.shape[0]
+        A32 = torch.empty((n, n), dtype=torch.float32, device=A.device)
+        F.fl_convert(A, F.FL_F32, A32)
+        b = m.load_vector(s)
+        _, i64 = m.solve(A, b, tol=1e-8)
+        _, imx = m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3)
+        out["per_s"][str(s)] = {
+            "n": n, "fp64_assembly_ms": timed(lambda: m.assemble(s, "fp64", out=A), reps=2),
+            "solve_ms_to_1e-8": {"f32_refined": timed(lambda: m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3), reps=3),
+                                 "plain_f64": timed(lambda: m.solve(A, b, tol=1e-8), reps=3)},
+            "iterations": {"plain_f64": i64.iterations, "f32_refined_inner": imx.iterations,
+                           "f32_refined_outer": imx.outer_iterations},
+            "rel_residual_f64": {"plain_f64": i64.rel_residual, "f32_refined": imx.rel_residual}}
+        del A, A32
+    out["pairs_per_s_fp64"] = {s: n_el * n_el / (v["fp64_assembly_ms"] / 1000) for s, v in out["per_s"].items()}
+    m.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_section(F, synth, timed, peaks, tune_file):
+    """4 orders x 64 right-hand sides on the graded disc: the batched tensor-core solve against
+    plain float64 Jacobi-PCG column by column (all 256 columns timed)."""
+    import torch
+
+    Vg, Tg = synth.disc(BATCH["rings"], BATCH["mu"])
+    mg = F.Mesh(Vg, Tg)
+    probs = build_problems(F, synth, mg, BATCH["s"], BATCH["nrhs"], 2, Vg)
+    if tune_file and os.path.exists(tune_file):
+        F.fl_tune_load(tune_file)
+    tuned, tuned_ms = F.fl_tune_batch(mg.h, probs, reps=5)
+    if tune_file:
+        F.fl_tune_save(tune_file)
+    ob = F.fl_default_batch_opts()
+    ob.inner_tol = 1e-4
+    binfo = {}
+
+    def batched():
+        r_, inf_, rel_, st_ = F.fl_batch_solve(mg.h, probs, ob)
+        binfo.update(status=int(r_), outer=inf_.outer_iterations, inner=inf_.inner_iterations,
+                     max_rel=float(rel_.max()), ctas=inf_.ctas, stages=inf_.stages)
+
+    batched()
+    batch_ms = timed(batched, reps=3)
+    # plain float64 Jacobi-PCG on every column of every problem, one solve each, timed as a whole
+    cols = []
+    for q in probs:
+        for j in range(BATCH["nrhs"]):
+            cols.append((q["A"], q["B"][:, j].contiguous()))
+    mg.solve(cols[0][0], cols[0][1])
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for Aq, bq in cols:
+        mg.solve(Aq, bq)
+    e1.record()
+    e1.synchronize()
+    plain_total = e0.elapsed_time(e1)
+    gemm_bytes = sum(F.fl_split_bf16_bytes(q["A"].shape[0], 2) for q in probs)
+    gemm_flops = sum(2 * 3 * q["A"].shape[0] ** 2 * BATCH["nrhs"] for q in probs)
+    out = {
+        "workload": f"graded disc {BATCH['rings']} rings mu {BATCH['mu']}, n = {probs[0]['A'].shape[0]}, "
+                    f"s = {BATCH['s']}, {BATCH['nrhs']} right-hand sides (f = 1 and seeded Gaussian nodal loads)",
+        "ms_to_1e-8": batch_ms, "systems": BATCH["nrhs"] * len(BATCH["s"]),
+        "plain_f64_ms": plain_total, "plain_f64_note": "every one of the 256 columns solved by float64 Jacobi-PCG",
+        "speedup_vs_plain_f64": plain_total / batch_ms, **binfo,
+        "autotune": {"stages": tuned.stages, "ctas": tuned.ctas, "gemm_ms": tuned_ms},
+        "tc_gemm": {"ms": tuned_ms, "bytes": gemm_bytes, "gbs": gemm_bytes / (tuned_ms / 1000) / 1e9,
+                    "frac_of_measured_hbm": gemm_bytes / (tuned_ms / 1000) / 1e9 / peaks.get("hbm_gbs", 6660.3),
+                    "tflops": gemm_flops / (tuned_ms / 1000) / 1e12,
+                    "note": "tcgen05 GEMM kernel alone (autotuner timing), 4 matrices x 2 bf16 slices x 64 columns"}}
+    del probs, cols
+    mg.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def matvec_section(F, timed, peaks, A, A32):
+    """Dense matvec bandwidth: n = 8195 (random matrix, L2 flushed between products) and the
+    headline matrix (n = 35693: 10.2 GB float64, 5.1 GB float32)."""
+    import torch
+
+    out = {}
+    nb = 8195
+    Ab = torch.randn(nb, nb, dtype=torch.float64, device=A.device)
+    Ab32 = Ab.float()
+    xb = torch.randn(nb, 1, dtype=torch.float64, device=A.device)
+    yb = torch.empty(nb, 1, dtype=torch.float64, device=A.device)
+    xb1 = xb[:, 0].contiguous()
+    yb1 = torch.empty(nb, dtype=torch.float64, device=A.device)
+
+    def tune_mv(dt, M):
+        try:
+            return F.fl_tune_matvec(dt, M, xb1, yb1, reps=5)
+        except F.FlError as e:  # FL_ENOTIMPL: the staged product is not used at this size
+            if e.code != F.FL_ENOTIMPL:
+                raise
+            return (None, None)
+
+    tuned = {"f64": tune_mv(F.FL_F64, Ab), "f32": tune_mv(F.FL_F32, Ab32)}
+    mv64 = timed(lambda: F.fl_matvec(F.FL_F64, Ab, xb, yb), reps=10)
+    mv32 = timed(lambda: F.fl_matvec(F.FL_F32, Ab32, xb, yb), reps=10)
+    mv32s = timed(lambda: F.fl_matvec_f32_static(Ab32, xb1, yb1), reps=10)
+    Ab2 = torch.empty(nb, 2 * nb, dtype=torch.float32, device=A.device)
+    F.fl_convert(Ab, F.FL_F32X2, Ab2)
+    mvx2 = timed(lambda: F.fl_matvec(F.FL_F32X2, Ab2, xb, yb), reps=10)
+    del Ab2, Ab, Ab32
+    out["n8195"] = {"f64_gbs": nb * nb * 8 / (mv64 / 1000) / 1e9, "f32_gbs": nb * nb * 4 / (mv32 / 1000) / 1e9,
+                    "f32_static_gbs": nb * nb * 4 / (mv32s / 1000) / 1e9, "f32x2_gbs": nb * nb * 8 / (mvx2 / 1000) / 1e9,
+                    "tuned_blocks_per_sm": {k: v[0] for k, v in tuned.items()}}
     n = A.shape[0]
-    b = mf.load_vector(s)
+    x = torch.randn(n, 1, dtype=torch.float64, device=A.device)
+    y = torch.empty(n, 1, dtype=torch.float64, device=A.device)
+    big64 = timed(lambda: F.fl_matvec(F.FL_F64, A, x, y), reps=5, flush_between=False)
+    big32 = timed(lambda: F.fl_matvec(F.FL_F32, A32, x, y), reps=5, flush_between=False)
+    out[f"n{n}"] = {"f64_gbs": n * n * 8 / (big64 / 1000) / 1e9, "f32_gbs": n * n * 4 / (big32 / 1000) / 1e9,
+                    "f64_ms": big64, "f32_ms": big32}
+    out["hbm_peak_gbs"] = peaks.get("hbm_gbs")
+    out["note"] = ("bytes of A per product / device time of fl_matvec; n = 8195 with L2 flushed between products; the "
+                   "headline matrix is 10.2 GB (float64) / 5.1 GB (float32), far beyond L2")
+    return out
+
+
+def lshape_precond_section(F, synth, timed, A, b, h5):
+    """Preconditioners on the headline system (L-shape level 5, s = 1/2, f = 1, tol 1e-8):
+    Jacobi-PCG, multigrid-preconditioned CG on the nested levels 5..2, flexible CG with the
+    learned stencil (trained on level 2, weights transferred), all with setup/training times."""
+    import torch
+
+    s = LSHAPE_S
     u = torch.empty_like(b)
-    out = {"workload": f"L-shape [0,2]^2 minus [1,2]^2, level {lev} (refined towards (1,1) and the boundary), "
-                       f"n = {n}, s = {s}, f = 1, tol 1e-8, float64 matvec", "n": n}
-    _, ij = mf.solve(A, b, tol=1e-8)
-    out["jacobi_pcg"] = {"ms": timed(lambda: mf.solve(A, b, tol=1e-8), reps=2), "iterations": ij.iterations}
-    # multigrid on the nested levels
+    meshes = [synth.lshape(0.25, lev) for lev in range(LSHAPE_LEVEL - 1, 1, -1)]  # levels 4..2
+    hs = [h5] + [F.fl_create(V, T) for V, T in meshes]
+    out = {"n": A.shape[0]}
+    info = F.fl_solve(h5, A, b, u, _opts(F, 1e-8))
+    out["jacobi_pcg"] = {"ms": timed(lambda: F.fl_solve(h5, A, b, u, _opts(F, 1e-8)), reps=2, flush_between=False),
+                         "iterations": info.iterations}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     mg = F.Multigrid(A)
@@ -252,10 +477,9 @@ def lshape_section(F, synth, timed, dev):
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1000
     im = mg.solve(b, u, tol=1e-8, maxit=500)
-    out["mg_pcg"] = {"ms": timed(lambda: mg.solve(b, u, tol=1e-8, maxit=500), reps=2), "iterations": im.iterations,
-                     "setup_ms": setup_ms, "levels": [F.fl_num_dofs(h, s) for h in hs]}
-    # learned stencil: trained on level 2 from noise-started CG pairs, transferred to this level
-    V2, T2 = synth.lshape(0.25, 2)
+    out["mg_pcg"] = {"ms": timed(lambda: mg.solve(b, u, tol=1e-8, maxit=500), reps=2, flush_between=False),
+                     "iterations": im.iterations, "setup_ms": setup_ms, "levels": [F.fl_num_dofs(h, s) for h in hs]}
+    V2, T2 = meshes[-1]
     m2 = F.Mesh(V2, T2)
     A2 = m2.assemble(s, "mixed")
     torch.cuda.synchronize()
@@ -265,21 +489,20 @@ def lshape_section(F, synth, timed, dev):
     loss = lp2.train(2000, batch=8192, lr=1e-3)
     torch.cuda.synchronize()
     train_ms = (time.perf_counter() - t0) * 1000
-    lp = F.LearnedPreconditioner(mf.h, s, seed=1)
+    lp = F.LearnedPreconditioner(h5, s, seed=1)
     lp.set_params(lp2.params())
-    il = F.fl_fcg_solve(mf.h, A, b, u, lp=lp, mg=mg, tol=1e-8)
-    out["learned_fcg"] = {"ms": timed(lambda: F.fl_fcg_solve(mf.h, A, b, u, lp=lp, mg=mg, tol=1e-8), reps=2),
+    il = F.fl_fcg_solve(h5, A, b, u, lp=lp, mg=mg, tol=1e-8)
+    out["learned_fcg"] = {"ms": timed(lambda: F.fl_fcg_solve(h5, A, b, u, lp=lp, mg=mg, tol=1e-8), reps=2,
+                                      flush_between=False),
                           "iterations": il.iterations, "fallback_at": il.fallback_at,
                           "rel_residual_f64": il.rel_residual, "train_ms": train_ms, "train_loss": loss,
                           "note": "stencil network trained on level 2 (2000 Adam steps, batch 8192), weights "
                                   "transferred; multigrid as fallback"}
-    ij2 = F.fl_fcg_solve(mf.h, A, b, u, mg=mg, tol=1e-8)
-    out["mg_fcg_iterations"] = ij2.iterations
+    out["mg_fcg_iterations"] = F.fl_fcg_solve(h5, A, b, u, mg=mg, tol=1e-8).iterations
     for obj in (lp, lp2, mg):
         obj.close()
     m2.close()
-    mf.close()
-    for h in hs:
+    for h in hs[1:]:
         F.fl_destroy(h)
     return out
 
@@ -291,6 +514,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side", action="store_true", help="headline step only (no side sections)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the far-kernel autotuner (default launch shape)")
     ap.add_argument("--tune-file", default=None, help="load/save the autotuner's table (JSON)")
     ap.add_argument("--case", default=None, choices=sorted(CASES),
                     help="profiling mode: run a small named workload and print stage times (no JSON line)")
@@ -302,7 +527,6 @@ def main():
     if args.case:
         return run_case(args)
 
-    import numpy as np
     import torch
 
     from paper_1708_03912_gb300 import fraclap as F
@@ -319,8 +543,9 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    s = WORKLOAD["s"]
-    V, T = synth.disc(WORKLOAD["rings"])
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    s = LSHAPE_S
+    V, T = synth.lshape(0.25, LSHAPE_LEVEL)
     n_el = len(T)
     m = F.Mesh(V, T)
     n = m.num_dofs(s)
@@ -328,9 +553,10 @@ def main():
     A = torch.empty((n, n), dtype=torch.float64, device=dev)
     A32 = torch.empty((n, n), dtype=torch.float32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    infos = []
 
     def step():
-        m.assemble(s, "mixed", out=A)
+        m.assemble(s, "fp64", out=A)
         F.fl_convert(A, F.FL_F32, A32)
         b = m.load_vector(s)
         u, info = m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3)
@@ -339,6 +565,16 @@ def main():
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
+    # launch shape of the far kernel from the project's autotuner (recorded in its table, which
+    # the timed assemblies consult)
+    tune = None
+    if not args.no_tune:
+        tv, tms = F.fl_tune_assemble(m.h, s, A, reps=1)
+        tune = {"variant": tv, "far_ms": tms, "note": "fl_tune_assemble: one timed far stage per launch variant"}
+        step()
+        torch.cuda.synchronize()
+    # the far stage is timed by the library's CUDA events on this stream, the schedule unchanged
+    F.fl_set_profiling(m.h, 2)
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
@@ -346,9 +582,8 @@ def main():
     torch.cuda.synchronize()
     launches0 = F.fl_launch_count()
     total_ms = 0.0
-    infos = []
+    far_ms = []
     for _ in range(args.steps):
-        flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -356,14 +591,16 @@ def main():
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
+        far_ms.append(F.fl_stage_ms(m.h)["far"])
     torch.cuda.synchronize()
     launches = F.fl_launch_count() - launches0
     if dist:
         dist.barrier()
     clk = clocks.stop()
+    F.fl_set_profiling(m.h, 0)
     t_max, value = job_rate(total_ms, args.steps, n_el * n_el, world, dist, dev)
+    last = infos[-1]
 
-    # ---- side measurements (untimed for the headline) ----
     def timed(fn, reps=5, flush_between=True):
         ts = []
         for _ in range(reps):
@@ -379,119 +616,71 @@ def main():
         return statistics.median(ts)
 
     peaks = load_peaks()
-    asm_mixed_ms = timed(lambda: m.assemble(s, "mixed", out=A))
-    asm_fp64_ms = timed(lambda: m.assemble(s, "fp64", out=A), reps=3)
-    # dominant kernel: the far-field tile kernel, timed by the library's events on this stream
-    F.fl_set_profiling(m.h, True)
-    far_ms = []
-    stage_tot = {k: 0.0 for k in F.STAGES}
-    for _ in range(5):
-        flush.zero_()
-        m.assemble(s, "mixed", out=A)
-        st = F.fl_stage_ms(m.h)
-        far_ms.append(st["far"])
-        for k in st:
-            stage_tot[k] += st[k] / 5
-    F.fl_set_profiling(m.h, False)
+    # ---- roofline of the dominant kernel: far_tile_dw_kernel (FP32 pipe) ----
+    pw = {0.25: 5, 0.5: 6, 0.75: 7}[s]
     far_avg = statistics.mean(far_ms)
-    q = 16  # collapsed rule of order 4
-    evals = stats["n_far_pairs"] * q * q
-    # dense matvec bandwidth on an HBM-resident matrix of the graded-disc size (n = 8195:
-    # 537 MB float64, 269 MB float32, both larger than L2), L2 flushed between products
-    nb = 8195
-    Ab = torch.randn(nb, nb, dtype=torch.float64, device=dev)
-    Ab32 = Ab.float()
-    xb = torch.randn(nb, 1, dtype=torch.float64, device=dev)
-    xb1 = xb[:, 0].contiguous()
-    yb = torch.empty(nb, 1, dtype=torch.float64, device=dev)
-    yb1 = torch.empty(nb, dtype=torch.float64, device=dev)
-    # blocks per SM of the staged product from the project's autotuner, for both storage types
-    def tune_mv(dt, M):
-        try:
-            return F.fl_tune_matvec(dt, M, xb1, yb1, reps=5)
-        except F.FlError as e:  # FL_ENOTIMPL: the staged product is not used at this size
-            if e.code != F.FL_ENOTIMPL:
-                raise
-            return (None, None)
-
-    mv_tuned = {"f64": tune_mv(F.FL_F64, Ab), "f32": tune_mv(F.FL_F32, Ab32)}
-    mv64 = timed(lambda: F.fl_matvec(F.FL_F64, Ab, xb, yb), reps=10)
-    mv32 = timed(lambda: F.fl_matvec(F.FL_F32, Ab32, xb, yb), reps=10)
-    mv32s = timed(lambda: F.fl_matvec_f32_static(Ab32, xb1, yb1), reps=10)
-    Ab2 = torch.empty(nb, 2 * nb, dtype=torch.float32, device=dev)  # hi + lo float32 pairs
-    F.fl_convert(Ab, F.FL_F32X2, Ab2)
-    mvx2 = timed(lambda: F.fl_matvec(F.FL_F32X2, Ab2, xb, yb), reps=10)
-    del Ab2
-    del Ab, Ab32
-    # time to 1e-8: refined float32 solve vs plain float64 Jacobi-PCG on the same matrix
-    m.assemble(s, "fp64", out=A)
-    F.fl_convert(A, F.FL_F32, A32)
-    b = m.load_vector(s)
-    sol_mixed = timed(lambda: m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3), reps=3)
-    sol_fp64 = timed(lambda: m.solve(A, b, tol=1e-8), reps=3)
-    _, inf64 = m.solve(A, b, tol=1e-8)
-    _, infmx = m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3)
-
-    # ---- batched: 4 orders x 64 right-hand sides on the graded disc (n = 8195) ----
-    Vg, Tg = synth.disc(BATCH["rings"], BATCH["mu"])
-    mg = F.Mesh(Vg, Tg)
-    probs = build_problems(F, synth, mg, BATCH["s"], BATCH["nrhs"], 2, Vg)
-    # launch shape of the tensor-core product from the project's autotuner (persisted if asked)
-    if args.tune_file and os.path.exists(args.tune_file):
-        F.fl_tune_load(args.tune_file)
-    tuned, tuned_ms = F.fl_tune_batch(mg.h, probs, reps=5)
-    if args.tune_file:
-        F.fl_tune_save(args.tune_file)
-    ob = F.fl_default_batch_opts()
-    ob.inner_tol = 1e-4
-    binfo = {}
-
-    def batched():
-        r_, inf_, rel_, st_ = F.fl_batch_solve(mg.h, probs, ob)
-        binfo.update(status=int(r_), outer=inf_.outer_iterations, inner=inf_.inner_iterations,
-                     max_rel=float(rel_.max()), ctas=inf_.ctas, stages=inf_.stages)
-
-    batched()
-    batch_ms = timed(batched, reps=3)
-    # plain float64 Jacobi-PCG on the same systems: f = 1 and the first Gaussian load for every s,
-    # the per-column mean extrapolated to all columns
-    plain_cols = []
-    for q in probs:
-        for j in (0, 1):
-            bj = q["B"][:, j].contiguous()
-            mg.solve(q["A"], bj)
-            plain_cols.append(timed(lambda: mg.solve(q["A"], bj), reps=1, flush_between=True))
-    plain_total = statistics.mean(plain_cols) * BATCH["nrhs"] * len(BATCH["s"])
-    # the tensor-core product alone, from the autotuner's CUDA-event timing of the GEMM kernel over all
-    # four matrices (two bf16 slices each, 64 columns): bytes = slice tiles streamed once
-    nbg = probs[2]["A"].shape[0]
-    gemm_bytes = sum(F.fl_split_bf16_bytes(q["A"].shape[0], 2) for q in probs)
-    gemm_flops = sum(2 * 3 * q["A"].shape[0] ** 2 * BATCH["nrhs"] for q in probs)
-    batch_line = {
-        "workload": f"graded disc {BATCH['rings']} rings mu {BATCH['mu']}, n = {nbg}, s = {BATCH['s']}, "
-                    f"{BATCH['nrhs']} right-hand sides (f = 1 and seeded Gaussian nodal loads)",
-        "ms_to_1e-8": batch_ms, "systems": BATCH["nrhs"] * len(BATCH["s"]),
-        "plain_f64_ms_extrapolated": plain_total,
-        "plain_f64_note": "mean of 2 timed single-column float64 Jacobi-PCG solves per s, times 64 columns",
-        "speedup_vs_plain_f64": plain_total / batch_ms, **binfo,
-        "autotune": {"stages": tuned.stages, "ctas": tuned.ctas, "gemm_ms": tuned_ms,
-                     "note": "fl_tune_batch sweep of pipeline depth x CTA count on these slices"},
-        "tc_gemm": {"ms": tuned_ms, "bytes": gemm_bytes, "gbs": gemm_bytes / (tuned_ms / 1000) / 1e9,
-                    "frac_of_measured_hbm": gemm_bytes / (tuned_ms / 1000) / 1e9 / peaks.get("hbm_gbs", 6660.3),
-                    "tflops": gemm_flops / (tuned_ms / 1000) / 1e12,
-                    "note": "tcgen05 GEMM kernel alone (autotuner timing), 4 matrices x 2 bf16 slices x 64 columns "
-                            "(3 bf16 products), HBM-bound: 48 flop/byte"},
-    }
-    del probs
-    mg.close()
-
-    # ---- L-shape refined towards the corner and the boundary: preconditioners, time to 1e-8 ----
-    lsh = lshape_section(F, synth, timed, dev)
+    evals = stats["n_far_pairs"] * 256
+    ops = evals * DW_OPS_PER_EVAL[pw]
+    clock_hz = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    peak_ops = sms * 128 * clock_hz
+    achieved = ops / (far_avg / 1000.0)
+    traffic = FAR_DW_DRAM_BYTES_PER_PAIR * stats["n_far_pairs"] if FAR_DW_DRAM_BYTES_PER_PAIR else None
+    # the same evaluations on the float64 pipe: 24.7 float64 operations each (ncu, float64
+    # far kernel, quasi-uniform disc), at 2 per clock and SM
+    dp_roof_evals = sms * 2 * clock_hz / 24.7
+    shapes = {1: "4,1", 2: "1,2", 3: "2,2", 4: "1,3"}
+    variant = tune["variant"] if tune else 3
+    roofline = {"bound": "alu", "kernel": f"far_tile_dw_kernel<{pw},{shapes[variant]}>", "achieved": achieved / 1e12,
+                "peak": peak_ops / 1e12, "unit": "T FP32-ops/s", "frac": achieved / peak_ops, "traffic": traffic,
+                "evals_per_s": evals / (far_avg / 1000.0), "far_ms": far_avg, "evals_per_launch": evals,
+                "traffic_note": "ncu DRAM bytes per far pair on the graded disc x far pairs of this workload",
+                "note": f"algorithmic FP32-pipe operations = far pairs x 256 evaluations x {DW_OPS_PER_EVAL[pw]} "
+                        f"(double-word evaluation: difference, |x-y|^2, power, three weighted sums, column sum); "
+                        f"peak = {sms} SMs x 128 FP32 lanes x max SM clock (of unit counts); far stage timed by CUDA "
+                        f"events on the caller's stream in every timed step; the float64 pipe's roof for the same "
+                        f"evaluations is {dp_roof_evals:.3e}/s (24.7 float64 ops each at 2/clk/SM): this kernel runs at "
+                        f"{evals / (far_avg / 1000.0) / dp_roof_evals:.2f}x that roof"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, triangles=n_el, dofs=n, parallelism=f"replicas x{world}"),
+        "roofline": roofline,
+        "solve": {"iterations_inner": last.iterations, "outer": last.outer_iterations,
+                  "rel_residual_f64": last.rel_residual},
+        "gpu_launches": int(launches), "clocks": clk, "far_autotune": tune}
+    if not args.no_side:
+        F.fl_set_profiling(m.h, 1)
+        m.assemble(s, "fp64", out=A)
+        line["stage_ms"] = F.fl_stage_ms(m.h)
+        F.fl_set_profiling(m.h, 0)
+        asm_ms = timed(lambda: m.assemble(s, "fp64", out=A), reps=2, flush_between=False)
+        b = m.load_vector(s)
+        line["lshape"] = {"assembly_fp64_ms": asm_ms, "assembly_pairs_per_s": n_el * n_el / (asm_ms / 1000),
+                          "solve_ms_to_1e-8": {
+                              "f32_refined": timed(lambda: m.solve(A, b, tol=1e-8, A_lo=A32, inner_tol=1e-3), reps=3,
+                                                   flush_between=False),
+                              "plain_f64": timed(lambda: m.solve(A, b, tol=1e-8), reps=2, flush_between=False)}}
+        Am = m.assemble(s, "mixed")
+        mx_ms = timed(lambda: m.assemble(s, "mixed", out=Am), reps=2, flush_between=False)
+        line["lshape"]["mixed"] = {"assembly_ms": mx_ms, "pairs_per_s": n_el * n_el / (mx_ms / 1000),
+                                   "error_scaled_vs_fp64": scaled_error(Am, A)}
+        del Am
+        torch.cuda.empty_cache()
+        line["lshape"]["preconditioners"] = lshape_precond_section(F, synth, timed, A, b, m.h)
+        line["matvec"] = matvec_section(F, timed, peaks, A, A32)
+        line["interval"] = interval_section(F, synth, timed)
+        line["disc"] = disc_section(F, synth, timed)
+        line["gdisc"] = gdisc_section(F, synth, timed)
+        line["batched"] = batch_section(F, synth, timed, peaks, args.tune_file)
 
     # ---- end to end through the public API with host buffers ----
+    del A, A32
+    torch.cuda.empty_cache()
+
     def e2e_step():
         mm = F.Mesh(V, T)
-        AA = mm.assemble(s, "mixed")
+        AA = mm.assemble(s, "fp64")
         AL = torch.empty((n, n), dtype=torch.float32, device=dev)
         F.fl_convert(AA, F.FL_F32, AL)
         bb = mm.load_vector(s)
@@ -504,52 +693,16 @@ def main():
     e2e_step()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 2))
     for _ in range(e2e_steps):
         _, st_e = e2e_step()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     h2d = int(st_e["h2d_bytes"] + V.nbytes + T.nbytes)
-    d2h = n * 8
-
-    sm_clock = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    # far kernel (float32, s = 3/4): one MUFU.LG2 (16 results/clk/SM) and one MUFU.EX2 (32/clk/SM on GB300,
-    # measured) per kernel evaluation -> 1 / (1/16 + 1/32) = 10.67 evaluations/clk/SM
-    evals_per_clk_sm = 1.0 / (1.0 / 16 + 1.0 / 32)
-    peak_evals = 152 * evals_per_clk_sm * (peaks.get("sm_max_mhz", 2070.0) * 1e6)
-    achieved = evals / (far_avg / 1000.0)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
-        "config": dict(WORKLOAD, cells=n_el, parallelism=f"replicas x{world}"),
-        "roofline": {"bound": "alu", "kernel": "far_tile_kernel<2,float,16,0>", "achieved": achieved / 1e9,
-                     "peak": peak_evals / 1e9, "unit": "Geval/s", "frac": achieved / peak_evals,
-                     "traffic": FAR_KERNEL_DRAM_BYTES,
-                     "note": "kernel evaluations |x-y|^{-2-2s}; peak = 152 SMs x 10.67 evals/clk (MUFU lg2 16/clk + "
-                             "ex2 32/clk per SM) x max SM clock; evals = far pairs x 16 x 16"},
-        "stage_ms": stage_tot,
-        "assembly_pairs_per_s": {"mixed": n_el * n_el / (asm_mixed_ms / 1000), "fp64": n_el * n_el / (asm_fp64_ms / 1000)},
-        "matvec": {"n": nb, "f64_gbs": nb * nb * 8 / (mv64 / 1000) / 1e9, "f32_gbs": nb * nb * 4 / (mv32 / 1000) / 1e9,
-                   "f64_ms": mv64, "f32_ms": mv32, "f32_static_gbs": nb * nb * 4 / (mv32s / 1000) / 1e9,
-                   "f32x2_gbs": nb * nb * 8 / (mvx2 / 1000) / 1e9, "f32x2_ms": mvx2,
-                   "tuned_blocks_per_sm": {k: v[0] for k, v in mv_tuned.items()},
-                   "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                   "note": "bytes of A per product / device time of fl_matvec (x staged in shared memory per block; "
-                           "the float32 call includes the rounding of x); L2 flushed; f32_static: the allocation-free "
-                           "fl_matvec_f32_static; f32x2: hi + lo float32 pairs (8 bytes per entry) multiplied in double-float "
-                           "arithmetic on the float32 pipe"},
-        "solve_ms_to_1e-8": {"f32_refined": sol_mixed, "plain_f64": sol_fp64, "iters_f64": inf64.iterations,
-                             "iters_refined": infmx.iterations, "outer": infmx.outer_iterations},
-        "batched": batch_line,
-        "lshape": lsh,
-        "gpu_launches": int(launches),
-        "clocks": clk,
-        "e2e": {"value": n_el * n_el / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "note": "Mesh(host arrays) -> planner -> table upload -> assemble -> solve -> u to host"},
-    }
+    line["e2e"] = {"value": n_el * n_el / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n * 8,
+                   "note": "Mesh(host arrays) -> planner -> table upload -> assemble -> f32 copy -> solve -> u to host"}
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        v, dt, threads, desc = oracle_sample()
+        v, dt, threads, desc = oracle_sample(2)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
     m.close()
     if rank == 0:

@@ -559,7 +559,10 @@ int fl_get_stats(fl_handle h, double s, fl_stats* st);
 
 /* enable = 1: record a CUDA event pair around every stage of each later fl_assemble
  * on its stream (events only, no synchronisation); the stages then run one after
- * another on that stream, so each pair times one stage alone. */
+ * another on that stream, so each pair times one stage alone.  enable = 2: only the far
+ * stage (FL_STAGE_FAR) is bracketed, on the caller's stream, and the schedule is left as
+ * without profiling (the other stages run beside it on the handle's second stream);
+ * fl_stage_ms then reports the far stage and zeros.  enable = 0: off.  Errors: FL_EINVAL. */
 int fl_set_profiling(fl_handle h, int enable);
 
 /* Milliseconds of each stage of the last profiled fl_assemble (waits for its events). */

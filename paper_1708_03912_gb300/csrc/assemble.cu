@@ -1305,6 +1305,7 @@ int alloc(fl_ctx* h, void** dst, size_t bytes) {
 // CUDA event pair around stage i when profiling is on
 void stage_mark(fl_ctx* h, cudaStream_t st, int i, int end) {
     if (!h->profiling) return;
+    if (h->profiling == 2 && i != FL_STAGE_FAR) return;  // the far stage alone, schedule unchanged
     if (!h->ev_made) {
         for (int k = 0; k < 2 * FL_NSTAGES; ++k) cudaEventCreate(&h->ev[k]);
         h->ev_made = true;
@@ -1822,7 +1823,7 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
     // is added.  With profiling on every stage runs on the caller's stream, one after another,
     // so that each event pair brackets one stage alone.
     cudaStream_t sst = st;
-    if (!h->profiling) {
+    if (h->profiling != 1) {
         if (!h->side && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();  // no second stream: the stages run in sequence on the caller's
             h->side = nullptr;

@@ -233,17 +233,24 @@ int fl_get_stats(fl_handle h, double s, fl_stats* st) {
 
 int fl_set_profiling(fl_handle h, int enable) {
     if (!h) return FL_EINVAL;
-    h->profiling = enable ? 1 : 0;
+    if (enable < 0 || enable > 2) return fl::set_err(h, FL_EINVAL, "enable must be 0, 1 or 2");
+    h->profiling = enable;
+    h->ev_recorded = false;
     return FL_OK;
 }
 
 int fl_stage_ms(fl_handle h, double* ms) {
     if (!h || !ms) return FL_EINVAL;
     if (!h->ev_recorded) return fl::set_err(h, FL_EINVAL, "no profiled fl_assemble yet");
-    if (cudaEventSynchronize(h->ev[2 * FL_NSTAGES - 1]) != cudaSuccess)
+    const int last = h->profiling == 2 ? FL_STAGE_FAR : FL_NSTAGES - 1;
+    if (cudaEventSynchronize(h->ev[2 * last + 1]) != cudaSuccess)
         return fl::set_err(h, FL_ECUDA, "cudaEventSynchronize");
     for (int i = 0; i < FL_NSTAGES; ++i) {
         float t = 0.f;
+        if (h->profiling == 2 && i != FL_STAGE_FAR) {
+            ms[i] = 0.0;
+            continue;
+        }
         if (cudaEventElapsedTime(&t, h->ev[2 * i], h->ev[2 * i + 1]) != cudaSuccess) {
             cudaGetLastError();
             t = 0.f;

@@ -376,6 +376,7 @@ def fl_get_stats(h, s):
 
 
 def fl_set_profiling(h, enable=True):
+    """enable: False/0 off, True/1 every stage in sequence, 2 the far stage alone (schedule kept)."""
     _check(lib().fl_set_profiling(h, int(enable)), h)
 
 
