@@ -182,6 +182,23 @@ int fl_load_vector(fl_handle h, double s, const double* f_nodal_dev, int nrhs,
                    double* b_dev, int64_t ldb, void* stream);
 
 /*
+ * Fractional heat equation d_t u + (-Delta)^s u = f (Section 2).  Implicit time steps give
+ * systems (M + dt A^s) u = b with the P1 mass matrix M (Section 5); with implicit Euler,
+ * (M + dt A^s) u^{k+1} = M u^k + dt F.  Both calls work on h's DOF set for order s.
+ * fl_heat_matrix: H_dev = M + dt A_dev for the dense float64 A^s (n x n, row pitch lda) of
+ * h's mesh at order s; H_dev (pitch ldh) may be A_dev itself (then ldh = lda) but must not
+ * overlap it otherwise.  dt >= 0.  Deterministic (fixed summation order).
+ * fl_mass_apply: Y = alpha M X + beta B for nrhs columns; X, B, Y float64 row-major
+ * [n][ld*] (column r at +r); B may be NULL when beta = 0; Y must not be X.  With f the P1
+ * interpolant of nodal values, the load vector F of fl_load_vector is M_full f.
+ * Errors: FL_EINVAL (bad pointers, pitches, dt < 0, overlap), FL_ENOMEM, FL_ECUDA.
+ */
+int fl_heat_matrix(fl_handle h, double s, double dt, const double* A_dev, int64_t lda, double* H_dev, int64_t ldh,
+                   void* stream);
+int fl_mass_apply(fl_handle h, double s, int nrhs, double alpha, const double* X_dev, int64_t ldx, double beta,
+                  const double* B_dev, int64_t ldb, double* Y_dev, int64_t ldy, void* stream);
+
+/*
  * The dense matrix-vector product of the iterative solvers (Section 5: n^2 work per
  * product).  Y = A X for a dense n x n matrix stored as dtype (FL_F64 / FL_F32 / FL_BF16 /
  * FL_F32X2; the low-precision storages are not in the paper) with leading dimension lda

@@ -16,11 +16,13 @@ assemble  element-pair assembly (Section 5, eqs. elementPair / elementPairBounda
 exact     closed forms used as pins: C(d,s), ball solutions (Section 7),
           exact 1D matrix and exact 2D matrix through edge pairs
 solve     Cholesky and Jacobi-preconditioned CG (Section 5)
+heat      P1 mass matrix and implicit Euler steps of the fractional heat equation
+          (Sections 2 and 5: systems (M + dt A^s) u = b)
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against a
 closed form, a library routine on a special case, or brute force; none is
 "parity unpinned".
 """
-from . import mesh, rules, assemble, exact, solve  # noqa: F401
+from . import mesh, rules, assemble, exact, solve, heat  # noqa: F401
 from .mesh import OracleMesh  # noqa: F401
 from .assemble import assemble_matrix, load_vector, QuadOrders  # noqa: F401

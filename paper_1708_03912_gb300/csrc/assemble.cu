@@ -1388,6 +1388,7 @@ int ensure_device(fl_ctx* h, int pi, cudaStream_t st) {
     U.add(t.g_ptr, P.g_ptr);
     U.add(t.g_slot, P.g_slot);
     U.add(t.vod, P.vod);
+    U.add(t.dov, P.dov);
     U.add(t.corig, corner);
     U.add(t.cells, P.C);
     std::vector<int64_t> v2cp(P.v2c_ptr.begin(), P.v2c_ptr.end());
@@ -2124,6 +2125,112 @@ __global__ void load_vector_kernel(int64_t n, int dim, const int* vod, const int
         }
     }
     b[i * ldb + r] = acc;
+}
+
+// ---------------------------------------------------- fractional heat equation --
+// Implicit time steps of the fractional heat equation (Section 2) give systems
+// (M + dt A^s) u = b with the P1 mass matrix M (Section 5).  M is applied cell by cell from
+// the element mass matrix |K| (1 + delta_ab) / ((d + 1)(d + 2)); one thread per DOF row sums
+// over the cells around its vertex in a fixed order.
+
+// Y = alpha M X + beta B for column r
+__global__ void mass_apply_kernel(int64_t n, int dim, const int* vod, const int* dov, const int64_t* v2c_ptr,
+                                  const int* v2c, const int* cells, const double* jac_orig, double alpha,
+                                  const double* X, int64_t ldx, double beta, const double* B, int64_t ldb, double* Y,
+                                  int64_t ldy, int r) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int NV = dim + 1;
+    const int vtx = vod[i];
+    const double scale = (dim == 2) ? 0.5 : 1.0;  // |K| = jac/2 (2D), jac (1D)
+    const double den = 1.0 / ((dim + 1.0) * (dim + 2.0));
+    double acc = 0.0;
+    for (int64_t q = v2c_ptr[vtx]; q < v2c_ptr[vtx + 1]; ++q) {
+        const int K = v2c[q];
+        double sacc = 0.0;
+        for (int a = 0; a < NV; ++a) {
+            const int u = cells[(int64_t)K * NV + a];
+            const int j = dov[u];
+            if (j >= 0) sacc += ((u == vtx) ? 2.0 : 1.0) * X[(int64_t)j * ldx + r];
+        }
+        acc += scale * jac_orig[K] * den * sacc;
+    }
+    double y = alpha * acc;
+    if (beta != 0.0) y += beta * B[i * ldb + r];
+    Y[i * ldy + r] = y;
+}
+
+// H = dt A, entry by entry (H may be A)
+__global__ void scale_matrix_kernel(int64_t n, double dt, const double* A, int64_t lda, double* H, int64_t ldh) {
+    for (int64_t row = blockIdx.y; row < n; row += gridDim.y)
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+            H[row * ldh + j] = dt * A[row * lda + j];
+}
+
+// H += M, one thread per row
+__global__ void add_mass_kernel(int64_t n, int dim, const int* vod, const int* dov, const int64_t* v2c_ptr,
+                                const int* v2c, const int* cells, const double* jac_orig, double* H, int64_t ldh) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int NV = dim + 1;
+    const int vtx = vod[i];
+    const double scale = (dim == 2) ? 0.5 : 1.0;
+    const double den = 1.0 / ((dim + 1.0) * (dim + 2.0));
+    double* row = H + i * ldh;
+    for (int64_t q = v2c_ptr[vtx]; q < v2c_ptr[vtx + 1]; ++q) {
+        const int K = v2c[q];
+        const double m = scale * jac_orig[K] * den;
+        for (int a = 0; a < NV; ++a) {
+            const int u = cells[(int64_t)K * NV + a];
+            const int j = dov[u];
+            if (j >= 0) row[j] += ((u == vtx) ? 2.0 : 1.0) * m;
+        }
+    }
+}
+
+int heat_matrix(fl_ctx* h, double s, double dt, const double* A, int64_t lda, double* H, int64_t ldh,
+                cudaStream_t st) {
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    if (!A || !H || lda < P.n || ldh < P.n || !(dt >= 0.0)) return set_err(h, FL_EINVAL, "bad A / H / lda / ldh / dt");
+    if (H != A && (H < A + P.n * lda && A < H + P.n * ldh)) return set_err(h, FL_EINVAL, "H overlaps A without being A");
+    if (H == A && ldh != lda) return set_err(h, FL_EINVAL, "in place needs ldh = lda");
+    FL_CUDA_TRY(h, cudaSetDevice(h->device));
+    FL_TRY(ensure_device(h, pi, st));
+    DevTables& t = h->dev[pi];
+    const unsigned gx = (unsigned)std::min<int64_t>((P.n + 255) / 256, 64);
+    const unsigned gy = (unsigned)std::min<int64_t>(P.n, 65535);
+    if (P.n > 0) {
+        scale_matrix_kernel<<<dim3(gx, gy), 256, 0, st>>>(P.n, dt, A, lda, H, ldh);
+        fl::count_launch();
+        add_mass_kernel<<<(unsigned)((P.n + 127) / 128), 128, 0, st>>>(P.n, P.dim, t.vod, t.dov, t.v2c_ptr, t.v2c,
+                                                                        t.cells, t.jac_orig, H, ldh);
+        fl::count_launch();
+    }
+    FL_CUDA_TRY(h, cudaGetLastError());
+    return FL_OK;
+}
+
+int mass_apply(fl_ctx* h, double s, int nrhs, double alpha, const double* X, int64_t ldx, double beta, const double* B,
+               int64_t ldb, double* Y, int64_t ldy, cudaStream_t st) {
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    if (!X || !Y || nrhs < 1 || ldx < nrhs || ldy < nrhs || (beta != 0.0 && (!B || ldb < nrhs)))
+        return set_err(h, FL_EINVAL, "bad X / B / Y / leading dimensions");
+    if (X == Y) return set_err(h, FL_EINVAL, "Y must not be X");
+    FL_CUDA_TRY(h, cudaSetDevice(h->device));
+    FL_TRY(ensure_device(h, pi, st));
+    DevTables& t = h->dev[pi];
+    const unsigned g = (unsigned)((P.n + 127) / 128);
+    for (int r = 0; r < nrhs && P.n > 0; ++r) {
+        mass_apply_kernel<<<g, 128, 0, st>>>(P.n, P.dim, t.vod, t.dov, t.v2c_ptr, t.v2c, t.cells, t.jac_orig, alpha, X,
+                                             ldx, beta, B, ldb, Y, ldy, r);
+        fl::count_launch();
+    }
+    FL_CUDA_TRY(h, cudaGetLastError());
+    return FL_OK;
 }
 
 int load_vector(fl_ctx* h, double s, const double* f, int nrhs, double* b, int64_t ldb, cudaStream_t st) {

@@ -14,6 +14,9 @@ int tune_assemble(fl_ctx* h, double s, double* A, int64_t lda, int reps, int* be
 int assemble_nearfield_csr(fl_ctx* h, double s, int precision, int64_t* nnz, int32_t* rowptr, int32_t* col,
                            double* val, cudaStream_t st);
 int load_vector(fl_ctx* h, double s, const double* f, int nrhs, double* b, int64_t ldb, cudaStream_t st);
+int heat_matrix(fl_ctx* h, double s, double dt, const double* A, int64_t lda, double* H, int64_t ldh, cudaStream_t st);
+int mass_apply(fl_ctx* h, double s, int nrhs, double alpha, const double* X, int64_t ldx, double beta, const double* B,
+               int64_t ldb, double* Y, int64_t ldy, cudaStream_t st);
 
 int plan_for(fl_ctx* h, double s) {
     if (!(s > 0.0 && s < 1.0)) {
@@ -193,6 +196,28 @@ int fl_assemble_nearfield_csr(fl_handle h, double s, int precision, int64_t* nnz
     h->err.clear();
     try {
         return fl::assemble_nearfield_csr(h, s, precision, nnz, rowptr_dev, col_dev, val_dev, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        return fl::set_err(h, FL_ENOMEM, "out of host memory");
+    }
+}
+
+int fl_heat_matrix(fl_handle h, double s, double dt, const double* A_dev, int64_t lda, double* H_dev, int64_t ldh,
+                   void* stream) {
+    if (!h) return FL_EINVAL;
+    h->err.clear();
+    try {
+        return fl::heat_matrix(h, s, dt, A_dev, lda, H_dev, ldh, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        return fl::set_err(h, FL_ENOMEM, "out of host memory");
+    }
+}
+
+int fl_mass_apply(fl_handle h, double s, int nrhs, double alpha, const double* X_dev, int64_t ldx, double beta,
+                  const double* B_dev, int64_t ldb, double* Y_dev, int64_t ldy, void* stream) {
+    if (!h) return FL_EINVAL;
+    h->err.clear();
+    try {
+        return fl::mass_apply(h, s, nrhs, alpha, X_dev, ldx, beta, B_dev, ldb, Y_dev, ldy, (cudaStream_t)stream);
     } catch (const std::bad_alloc&) {
         return fl::set_err(h, FL_ENOMEM, "out of host memory");
     }

@@ -84,6 +84,7 @@ struct DevTables {
     int64_t *v2c_ptr = nullptr;
     int* v2c = nullptr;
     int* vod = nullptr;
+    int* dov = nullptr;     // nv: vertex -> dof or -1
     int* corig = nullptr;   // nc*nvpc vertex ids of the internal-order cells
     int* cells = nullptr;   // nc*nvpc oriented cells in original order
     // workspace (sized for float64)

@@ -24,7 +24,7 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
 
 EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
            "fl_assemble", "fl_tune_assemble", "fl_set_far_variant", "fl_assemble_nearfield_csr", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
-           "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
+           "fl_heat_matrix", "fl_mass_apply", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
            "fl_matvec_f32_static",
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
            "fl_tune_batch", "fl_tune_matvec", "fl_tune_record", "fl_tune_lookup", "fl_tune_clear", "fl_tune_count", "fl_tune_save",
@@ -129,6 +129,10 @@ def lib():
     L.fl_matvec.restype = ci
     L.fl_convert.argtypes = [vp, i64, i64, ci, vp, i64, vp]
     L.fl_convert.restype = ci
+    L.fl_heat_matrix.argtypes = [vp, dbl, dbl, vp, i64, vp, i64, vp]
+    L.fl_heat_matrix.restype = ci
+    L.fl_mass_apply.argtypes = [vp, dbl, ci, dbl, vp, i64, dbl, vp, i64, vp, i64, vp]
+    L.fl_mass_apply.restype = ci
     L.fl_default_solve_opts.argtypes = [ctypes.POINTER(fl_solve_opts)]
     L.fl_default_solve_opts.restype = None
     L.fl_solve.argtypes = [vp, i64, vp, i64, vp, vp, ctypes.POINTER(fl_solve_opts), ctypes.POINTER(fl_solve_info), vp]
@@ -350,6 +354,19 @@ def fl_matvec(dtype, A, X, Y, stream=None):
 
 def fl_convert(A, dtype, out, stream=None):
     _check(lib().fl_convert(_ptr(A), A.stride(0), A.shape[0], dtype, _ptr(out), _ld(dtype, out), _stream(stream)))
+
+
+def fl_heat_matrix(h, s, dt, A, H, stream=None):
+    """H = M + dt A (H may be A)."""
+    _check(lib().fl_heat_matrix(h, s, dt, _ptr(A), A.stride(0), _ptr(H), H.stride(0), _stream(stream)), h)
+
+
+def fl_mass_apply(h, s, alpha, X, beta, B, Y, stream=None):
+    """Y = alpha M X + beta B (X, B, Y float64 [n] or [n, nrhs]; B may be None when beta = 0)."""
+    nrhs = X.shape[1] if X.dim() == 2 else 1
+    ld = lambda T: (T.stride(0) if T.dim() == 2 else 1) if T is not None else 1  # noqa: E731
+    _check(lib().fl_mass_apply(h, s, nrhs, alpha, _ptr(X), ld(X), beta, _ptr(B) if B is not None else None, ld(B),
+                               _ptr(Y), ld(Y), _stream(stream)), h)
 
 
 def fl_default_solve_opts():
@@ -786,3 +803,20 @@ class Mesh:
         u = torch.empty_like(b)
         info = fl_solve(self.h, A, b, u, o, stream)
         return u, info
+
+    def heat_steps(self, A, s, dt, u0, F, steps, tol=1e-10, stream=None):
+        """Implicit Euler for the fractional heat equation (Sections 2 and 5): from u0, `steps`
+        solves of (M + dt A) u^{k+1} = M u^k + dt F by Jacobi-PCG.  Returns (u, [fl_solve_info])."""
+        import torch
+
+        H = torch.empty_like(A)
+        fl_heat_matrix(self.h, s, dt, A, H, stream)
+        u = u0.clone()
+        rhs = torch.empty_like(u0)
+        o = fl_default_solve_opts()
+        o.tol = tol
+        infos = []
+        for _ in range(steps):
+            fl_mass_apply(self.h, s, 1.0, u, dt, F, rhs, stream)
+            infos.append(fl_solve(self.h, H, rhs, u, o, stream))
+        return u, infos
