@@ -453,6 +453,59 @@ def matvec_section(F, timed, peaks, A, A32):
     return out
 
 
+def hmatrix_section(F, timed, A, h5):
+    """Cluster method (Section 6) on the headline matrix: H-matrix products for Chebyshev orders
+    4 and 6 (leaves of 32 DOFs, eta = 1) against the dense float64 product: time, error, size."""
+    import torch
+
+    s = LSHAPE_S
+    n = A.shape[0]
+    x = torch.randn(n, dtype=torch.float64, device=A.device, generator=torch.Generator(device=A.device).manual_seed(5))
+    ref = torch.empty(n, 1, dtype=torch.float64, device=A.device)
+    dense_ms = timed(lambda: F.fl_matvec(F.FL_F64, A, x[:, None], ref), reps=5, flush_between=False)
+    out = {"dense_f64_matvec_ms": dense_ms, "n": n, "leaf": 32, "eta": 1.0}
+    for m in (4, 6):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H = F.HMatrix(h5, s, m=m, eta=1.0, leaf=32)
+        H.set_near(A)
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t0) * 1000
+        y = torch.empty(n, dtype=torch.float64, device=A.device)
+        H.matvec(x, y)
+        ms = timed(lambda: H.matvec(x, y), reps=10)
+        err = float(torch.linalg.norm(y - ref[:, 0]) / torch.linalg.norm(ref[:, 0]))
+        out[f"m{m}"] = {"matvec_ms": ms, "speedup_vs_dense": dense_ms / ms, "rel_error_vs_dense": err,
+                        "setup_ms_from_dense": setup_ms, **H.info()}
+        H.close()
+    return out
+
+
+def heat_section(F, synth, timed):
+    """Fractional heat equation (Sections 2 and 5) on the graded disc, s = 1/2: implicit Euler
+    with the float64 matrix M + dt A^s, Jacobi-PCG to 1e-10 per step, dt = 1e-3."""
+    import torch
+
+    s, dt, steps = 0.5, 1e-3, 10
+    V, T = synth.disc(GDISC["rings"], GDISC["mu"])
+    m = F.Mesh(V, T)
+    A = m.assemble(s, "fp64")
+    b = m.load_vector(s)
+    u0 = torch.zeros_like(b)
+    m.heat_steps(A, s, dt, u0, b, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    u, infos = m.heat_steps(A, s, dt, u0, b, steps)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) * 1000
+    _, i_a = m.solve(A, b, tol=1e-10)
+    out = {"workload": f"graded disc, n = {A.shape[0]}, s = {s}, dt = {dt}, f = 1, u0 = 0, {steps} implicit Euler steps",
+           "ms_per_step": wall / steps, "iterations_per_step": [i.iterations for i in infos],
+           "iterations_steady_system": i_a.iterations}
+    m.close()
+    return out
+
+
 def lshape_precond_section(F, synth, timed, A, b, h5):
     """Preconditioners on the headline system (L-shape level 5, s = 1/2, f = 1, tol 1e-8):
     Jacobi-PCG, multigrid-preconditioned CG on the nested levels 5..2, flexible CG with the
@@ -668,6 +721,8 @@ def main():
         del Am
         torch.cuda.empty_cache()
         line["lshape"]["preconditioners"] = lshape_precond_section(F, synth, timed, A, b, m.h)
+        line["lshape"]["hmatrix"] = hmatrix_section(F, timed, A, m.h)
+        line["heat"] = heat_section(F, synth, timed)
         line["matvec"] = matvec_section(F, timed, peaks, A, A32)
         line["interval"] = interval_section(F, synth, timed)
         line["disc"] = disc_section(F, synth, timed)

@@ -376,6 +376,53 @@ int fl_batch_solve(fl_handle h, int nprob, const fl_batch_problem* probs, const 
                    fl_batch_info* info, double* rel_residual_host, int* status_host, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Cluster method (Section 6): the stiffness matrix as an H-matrix.  The DOFs are
+ * organised in a binary cluster tree (a cluster with more than `leaf` DOFs is split at the
+ * middle of the longest side of its DOF vertices' bounding box); the cluster box is the
+ * smallest cube containing the supports of its basis functions.  A pair of clusters is
+ * admissible when eta dist >= max(diam, diam) (distance and diameters of the cubes); the
+ * partition comes from the recursion over pairs from (root, root).  On admissible pairs
+ * the kernel |x-y|^{-d-2s} is replaced by its tensor Chebyshev interpolant of order m, so
+ * those blocks become -C U_sigma K_{sigma tau} U_tau^T with the basis far-field
+ * coefficients (int phi_i L_alpha, Gauss order m + 1 per cell) moved through the tree by
+ * the shift coefficients; inadmissible pairs of leaves keep their exact entries (near
+ * field, CSR).  The product costs O(n log^{2d} n) instead of the dense n^2.
+ * ------------------------------------------------------------------------ */
+typedef struct fl_hm* fl_hmatrix;
+
+/*
+ * Host only (no device work): the cluster tree and partition of h's DOF set for order s.
+ * sizes[0..2] receive the numbers of nodes, admissible pairs and near-field leaf pairs;
+ * with non-NULL arrays also: perm [n] (DOFs in tree order), node [nodes][4] (range lo, hi
+ * of the node in perm, first and second son or -1), far [2 * pairs] and near
+ * [2 * pairs] (node ids sigma, tau in the order of the recursion).  Nodes are numbered
+ * depth first, first son first.  Call once with NULL arrays to size them.
+ * Errors: FL_EINVAL (leaf < 1, eta < 0, s not in (0, 1)).
+ */
+int fl_cluster_plan(fl_handle h, double s, double eta, int leaf, int64_t* sizes, int32_t* perm, int32_t* node,
+                    int32_t* far, int32_t* near);
+
+/*
+ * Builds the H-matrix of A^s on h's mesh: the plan above, then on the device the leaf
+ * coefficients, the shift coefficients and the kernel matrices of the admissible pairs
+ * (float64, m^{2d} per pair).  m in [1, 12].  The handle h must outlive the H-matrix.
+ * Errors: FL_EINVAL, FL_ENOMEM, FL_ECUDA (message in h).
+ */
+int fl_hmatrix_create(fl_handle h, double s, int m, double eta, int leaf, fl_hmatrix* out, void* stream);
+/* Near-field entries A_ij (i, j in inadmissible leaf pairs) gathered from the dense float64
+ * A (row pitch lda) of the same mesh and order.  Errors: FL_EINVAL, FL_ECUDA. */
+int fl_hmatrix_set_near(fl_hmatrix H, const double* A_dev, int64_t lda, void* stream);
+/* y_dev = H x_dev (float64 [n], y must not be x): near-field CSR product, upward pass,
+ * couplings, downward pass; fixed summation orders.  Errors: FL_EINVAL (no near field
+ * yet), FL_ECUDA. */
+int fl_hmatrix_matvec(fl_hmatrix H, const double* x_dev, double* y_dev, void* stream);
+/* info[0..5]: nodes, admissible pairs, near-field leaf pairs, near-field entries, device
+ * bytes held, tree depth. */
+int fl_hmatrix_info(fl_hmatrix H, int64_t* info);
+const char* fl_hmatrix_last_error(fl_hmatrix H);
+void fl_hmatrix_destroy(fl_hmatrix H);
+
+/* ------------------------------------------------------------------------
  * Multigrid (Section 5 proposes multigrid for these dense systems; no algorithm is
  * given, this is the Galerkin V-cycle on nested meshes).
  * ------------------------------------------------------------------------ */

@@ -2030,6 +2030,8 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
     return FL_OK;
 }
 
+int ensure_device_tables(fl_ctx* h, int pi, cudaStream_t st) { return ensure_device(h, pi, st); }
+
 int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStream_t st) {
     return assemble_impl(h, s, precision, A, lda, nullptr, st);
 }

@@ -150,6 +150,8 @@ namespace fl {
 void count_launch(int n = 1);
 // returns plan index for order s (building it on demand); -1 on error (h->err set)
 int plan_for(fl_ctx* h, double s);
+// device copies of plan pi's tables (uploaded once per handle and plan)
+int ensure_device_tables(fl_ctx* h, int pi, cudaStream_t st);
 // caching allocator (pool.cpp): device and pinned host blocks reused across handles
 cudaError_t pool_dev_alloc(void** out, size_t bytes);
 void pool_dev_free(void* p);

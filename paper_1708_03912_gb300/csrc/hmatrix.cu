@@ -1,0 +1,528 @@
+// Cluster-method (H-matrix) approximation of the stiffness matrix and its product
+// (Section 6 of arXiv:1708.03912).
+//
+// On an admissible pair of clusters (sigma, tau) the supports are disjoint and
+// a(phi_i, phi_j) = -C(d,s) int int k(x,y) phi_i(x) phi_j(y); the kernel
+// k = |x-y|^{-d-2s} is replaced by its tensor Chebyshev interpolant of order m on the two
+// cluster cubes, sum_{alpha,beta} k(xi_alpha^sigma, xi_beta^tau) L_alpha^sigma(x) L_beta^tau(y).
+// The product y = A x then splits into
+//   near field   y_i += sum_j A_ij x_j over the inadmissible leaf pairs (exact entries, CSR);
+//   upward pass  xh_c = sum_{i in c} (int phi_i L_alpha^c) x_i on the leaves (the basis
+//                far-field coefficients, Gauss order m+1 per cell), and
+//                xh_f = sum_sons S_son^T xh_son with the shift coefficients
+//                S_son[beta][alpha] = L_alpha^f(xi_beta^son);
+//   couplings    yh_sigma = sum over its admissible partners tau of K_{sigma tau} xh_tau;
+//   downward     yh_son += S_son yh_f, and y_i += -C sum_alpha (int phi_i L_alpha) yh_leaf.
+// Cluster tree and partition: cluster.cpp (host).  Every sum runs in a fixed order, so the
+// product is bitwise reproducible; all arithmetic is float64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "cluster.h"
+#include "context.h"
+#include "device.h"
+
+struct fl_hm {
+    fl_ctx* mesh = nullptr;
+    int device = 0, pi = 0, d = 0, m = 0, md = 0;
+    double s = 0.0, C = 0.0;
+    fl::ClusterPlan plan;
+    std::vector<int> nz_ptr_h;  // near CSR row pointer (host copy, for sizes)
+    int64_t nnz = 0, bytes = 0;
+    std::vector<void*> bufs;
+    // device arrays
+    int *perm = nullptr, *leaf_of = nullptr, *parent = nullptr;
+    int *lo_d = nullptr, *hi_d = nullptr, *son_d = nullptr;
+    double *center = nullptr, *side = nullptr;
+    double *coef = nullptr, *shift = nullptr, *kmat = nullptr;
+    int *far_ptr = nullptr, *far_tau = nullptr;
+    int *up_nodes = nullptr, *down_nodes = nullptr, *leaves = nullptr;
+    std::vector<int> up_off, down_off;  // per level offsets (host)
+    int nleaves = 0, nsig = 0;
+    int* sig_nodes = nullptr;  // nodes with admissible partners, in node order
+    int *nz_ptr = nullptr, *nz_row = nullptr, *nz_col = nullptr;
+    double* nz_val = nullptr;
+    bool near_ready = false;
+    double *xh = nullptr, *yh = nullptr;
+    std::string err;
+};
+
+namespace fl {
+namespace {
+
+int hm_fail(fl_hm* H, int code, const std::string& msg) {
+    if (H) H->err = msg;
+    return code;
+}
+
+template <typename T>
+int hm_upload(fl_hm* H, T** dst, const std::vector<T>& src, cudaStream_t st) {
+    void* p = nullptr;
+    const size_t bytes = std::max<size_t>(src.size() * sizeof(T), 16);
+    if (pool_dev_alloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return hm_fail(H, FL_ENOMEM, "cluster tables");
+    }
+    H->bufs.push_back(p);
+    H->bytes += (int64_t)bytes;
+    *dst = (T*)p;
+    if (!src.empty() && cudaMemcpyAsync(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return hm_fail(H, FL_ECUDA, "cluster table upload");
+    return FL_OK;
+}
+
+int hm_alloc(fl_hm* H, double** dst, size_t count) {
+    void* p = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(double), 16);
+    if (pool_dev_alloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return hm_fail(H, FL_ENOMEM, "cluster workspace");
+    }
+    H->bufs.push_back(p);
+    H->bytes += (int64_t)bytes;
+    *dst = (double*)p;
+    return FL_OK;
+}
+
+// 1D Lagrange basis value l_k(t) of the m Chebyshev points of [c - L/2, c + L/2]
+__device__ double cheb_node(double c, double L, int m, int k) {
+    return c + 0.5 * L * cos((2.0 * (k + 1) - 1.0) * M_PI / (2.0 * m));
+}
+__device__ double lagrange1(double c, double L, int m, int k, double t) {
+    const double xk = cheb_node(c, L, m, k);
+    double v = 1.0;
+    for (int l = 0; l < m; ++l)
+        if (l != k) v *= (t - cheb_node(c, L, m, l)) / (xk - cheb_node(c, L, m, l));
+    return v;
+}
+// tensor Lagrange polynomial alpha of cluster (c, L) at x
+__device__ double lagrange_d(const double* c, double L, int m, int d, int alpha, const double* x) {
+    if (d == 1) return lagrange1(c[0], L, m, alpha, x[0]);
+    return lagrange1(c[0], L, m, alpha / m, x[0]) * lagrange1(c[1], L, m, alpha % m, x[1]);
+}
+__device__ void cheb_point_d(const double* c, double L, int m, int d, int alpha, double* x) {
+    if (d == 1) {
+        x[0] = cheb_node(c[0], L, m, alpha);
+    } else {
+        x[0] = cheb_node(c[0], L, m, alpha / m);
+        x[1] = cheb_node(c[1], L, m, alpha % m);
+    }
+}
+
+// leaf coefficients int phi_i L_alpha^leaf, one thread per (tree position, alpha); the rule
+// (lam [q][d], w [q], on the reference cell) integrates the degree 2m-1 integrand exactly
+__global__ void leaf_coef_kernel(int64_t n, int d, int m, int md, const int* perm, const int* leaf_of,
+                                 const double* center, const double* side, const int* vod, const int64_t* v2c_ptr,
+                                 const int* v2c, const int* cells, const double* V, const double* jac, int q,
+                                 const double* lam, const double* w, double* coef) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * md) return;
+    const int64_t p = t / md;
+    const int alpha = (int)(t - p * md);
+    const int c = leaf_of[p];
+    const int v = vod[perm[p]];
+    const int nv = d + 1;
+    double acc = 0.0;
+    for (int64_t e = v2c_ptr[v]; e < v2c_ptr[v + 1]; ++e) {
+        const int K = v2c[e];
+        const int* cell = cells + (int64_t)K * nv;
+        int a = 0;
+        while (cell[a] != v) ++a;
+        for (int r = 0; r < q; ++r) {
+            double x[2];
+            double phi;
+            if (d == 1) {
+                const double tt = lam[r];
+                x[0] = V[cell[0]] + tt * (V[cell[1]] - V[cell[0]]);
+                phi = a == 0 ? 1.0 - tt : tt;
+            } else {
+                const double l1 = lam[2 * r], l2 = lam[2 * r + 1];
+                for (int k = 0; k < 2; ++k)
+                    x[k] = V[2 * cell[0] + k] + l1 * (V[2 * cell[1] + k] - V[2 * cell[0] + k]) +
+                           l2 * (V[2 * cell[2] + k] - V[2 * cell[0] + k]);
+                phi = a == 0 ? 1.0 - l1 - l2 : (a == 1 ? l1 : l2);
+            }
+            acc += w[r] * jac[K] * phi * lagrange_d(center + (int64_t)c * d, side[c], m, d, alpha, x);
+        }
+    }
+    coef[p * md + alpha] = acc;
+}
+
+// shift coefficients S_son[beta][alpha] = L_alpha^father(xi_beta^son), one thread per entry
+__global__ void shift_kernel(int nodes, int d, int m, int md, const int* parent, const double* center,
+                             const double* side, double* S) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nodes * md * md) return;
+    const int c = (int)(t / ((int64_t)md * md));
+    const int r = (int)(t - (int64_t)c * md * md);
+    const int beta = r / md, alpha = r - beta * md;
+    const int f = parent[c];
+    if (f < 0) {
+        S[t] = 0.0;
+        return;
+    }
+    double x[2];
+    cheb_point_d(center + (int64_t)c * d, side[c], m, d, beta, x);
+    S[t] = lagrange_d(center + (int64_t)f * d, side[f], m, d, alpha, x);
+}
+
+// kernel matrices of the admissible pairs, in sigma-major order: K[b][alpha][beta]
+__global__ void kmat_kernel(int nfar, int d, int m, int md, const int* far_sig, const int* far_tau,
+                            const double* center, const double* side, double expo, double* K) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nfar * md * md) return;
+    const int b = (int)(t / ((int64_t)md * md));
+    const int r = (int)(t - (int64_t)b * md * md);
+    const int alpha = r / md, beta = r - alpha * md;
+    const int a = far_sig[b], c = far_tau[b];
+    double xa[2], xb[2];
+    cheb_point_d(center + (int64_t)a * d, side[a], m, d, alpha, xa);
+    cheb_point_d(center + (int64_t)c * d, side[c], m, d, beta, xb);
+    double r2 = 0.0;
+    for (int k = 0; k < d; ++k) r2 += (xa[k] - xb[k]) * (xa[k] - xb[k]);
+    K[t] = pow(r2, expo);
+}
+
+__global__ void near_gather_kernel(int64_t nnz, const int* row, const int* col, const double* A, int64_t lda,
+                                   double* val) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < nnz) val[e] = A[(int64_t)row[e] * lda + col[e]];
+}
+
+// y = N x, one warp per row (columns ascending)
+__global__ void near_spmv_kernel(int64_t n, const int* ptr, const int* col, const double* val, const double* x,
+                                 double* y) {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double acc = 0.0;
+    for (int e = ptr[row] + lane; e < ptr[row + 1]; e += 32) acc = fma(val[e], x[col[e]], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) y[row] = acc;
+}
+
+// upward pass on the leaves: xh[c][alpha] = sum_{p in c} coef[p][alpha] x[perm[p]]
+__global__ void up_leaf_kernel(int nleaves, int md, const int* leaves, const int* lo, const int* hi, const int* perm,
+                               const double* coef, const double* x, double* xh) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nleaves * md) return;
+    const int c = leaves[t / md];
+    const int alpha = (int)(t % md);
+    double acc = 0.0;
+    for (int p = lo[c]; p < hi[c]; ++p) acc = fma(coef[(int64_t)p * md + alpha], x[perm[p]], acc);
+    xh[(int64_t)c * md + alpha] = acc;
+}
+
+// upward pass on one level of fathers: xh[f][alpha] = sum_sons sum_beta S_son[beta][alpha] xh[son][beta]
+__global__ void up_level_kernel(int count, int md, const int* nodes, const int* son, const double* S, double* xh) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)count * md) return;
+    const int f = nodes[t / md];
+    const int alpha = (int)(t % md);
+    double acc = 0.0;
+    for (int q = 0; q < 2; ++q) {
+        const int c = son[2 * f + q];
+        const double* Sc = S + (int64_t)c * md * md;
+        for (int beta = 0; beta < md; ++beta) acc = fma(Sc[(int64_t)beta * md + alpha], xh[(int64_t)c * md + beta], acc);
+    }
+    xh[(int64_t)f * md + alpha] = acc;
+}
+
+// couplings: yh[sigma][alpha] = sum over sigma's admissible partners of K xh[tau]
+__global__ void couple_kernel(int nsig, int md, const int* sig_nodes, const int* far_ptr, const int* far_tau,
+                              const double* K, const double* xh, double* yh) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nsig * md) return;
+    const int sgm = sig_nodes[t / md];
+    const int alpha = (int)(t % md);
+    double acc = 0.0;
+    for (int b = far_ptr[sgm]; b < far_ptr[sgm + 1]; ++b) {
+        const double* Kb = K + (int64_t)b * md * md + (int64_t)alpha * md;
+        const double* xt = xh + (int64_t)far_tau[b] * md;
+        for (int beta = 0; beta < md; ++beta) acc = fma(Kb[beta], xt[beta], acc);
+    }
+    yh[(int64_t)sgm * md + alpha] = acc;
+}
+
+// downward pass on one level: yh[c][beta] += sum_alpha S_c[beta][alpha] yh[father][alpha]
+__global__ void down_level_kernel(int count, int md, const int* nodes, const int* parent, const double* S, double* yh) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)count * md) return;
+    const int c = nodes[t / md];
+    const int beta = (int)(t % md);
+    const int f = parent[c];
+    const double* Sc = S + (int64_t)c * md * md + (int64_t)beta * md;
+    double acc = yh[(int64_t)c * md + beta];
+    for (int alpha = 0; alpha < md; ++alpha) acc = fma(Sc[alpha], yh[(int64_t)f * md + alpha], acc);
+    yh[(int64_t)c * md + beta] = acc;
+}
+
+// leaves to DOFs: y[perm[p]] += mC sum_alpha coef[p][alpha] yh[leaf][alpha]
+__global__ void down_leaf_kernel(int64_t n, int md, const int* perm, const int* leaf_of, const double* coef,
+                                 const double* yh, double mC, double* y) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double* cp = coef + p * md;
+    const double* yl = yh + (int64_t)leaf_of[p] * md;
+    double acc = 0.0;
+    for (int alpha = 0; alpha < md; ++alpha) acc = fma(cp[alpha], yl[alpha], acc);
+    y[perm[p]] += mC * acc;
+}
+
+unsigned blocks_for(int64_t work, int threads) { return (unsigned)std::max<int64_t>(1, (work + threads - 1) / threads); }
+
+}  // namespace
+}  // namespace fl
+
+using namespace fl;
+
+static double frac_constant_h(int d, double s) {
+    return std::pow(2.0, 2 * s) * s * std::tgamma(s + d / 2.0) / (std::pow(M_PI, d / 2.0) * std::tgamma(1.0 - s));
+}
+
+extern "C" {
+
+int fl_cluster_plan(fl_handle h, double s, double eta, int leaf, int64_t* sizes, int32_t* perm, int32_t* node,
+                    int32_t* far, int32_t* near) {
+    if (!h || !sizes) return FL_EINVAL;
+    h->err.clear();
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    ClusterPlan C;
+    if (build_cluster_plan(h->plan[pi], eta, leaf, C) != FL_OK) return set_err(h, FL_EINVAL, "leaf < 1 or eta < 0");
+    sizes[0] = C.nodes;
+    sizes[1] = (int64_t)C.far.size() / 2;
+    sizes[2] = (int64_t)C.near.size() / 2;
+    if (perm) std::copy(C.perm.begin(), C.perm.end(), perm);
+    if (node)
+        for (int c = 0; c < C.nodes; ++c) {
+            node[4 * c] = C.lo[c];
+            node[4 * c + 1] = C.hi[c];
+            node[4 * c + 2] = C.son[2 * c];
+            node[4 * c + 3] = C.son[2 * c + 1];
+        }
+    if (far) std::copy(C.far.begin(), C.far.end(), far);
+    if (near) std::copy(C.near.begin(), C.near.end(), near);
+    return FL_OK;
+}
+
+void fl_hmatrix_destroy(fl_hmatrix H) {
+    if (!H) return;
+    if (!H->bufs.empty()) {
+        cudaSetDevice(H->device);
+        cudaDeviceSynchronize();
+        for (void* p : H->bufs) pool_dev_free(p);
+    }
+    delete H;
+}
+
+int fl_hmatrix_create(fl_handle h, double s, int m, double eta, int leaf, fl_hmatrix* out, void* stream) {
+    if (!h || !out) return FL_EINVAL;
+    h->err.clear();
+    *out = nullptr;
+    if (m < 1 || m > 12) return set_err(h, FL_EINVAL, "Chebyshev order m must lie in [1, 12]");
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    fl_hm* H = new (std::nothrow) fl_hm;
+    if (!H) return set_err(h, FL_ENOMEM, "out of host memory");
+    H->mesh = h;
+    H->device = h->device;
+    H->pi = pi;
+    H->d = P.dim;
+    H->m = m;
+    H->md = P.dim == 1 ? m : m * m;
+    H->s = s;
+    H->C = frac_constant_h(P.dim, s);
+    cudaStream_t st = (cudaStream_t)stream;
+    auto fail = [&](int code, const std::string& msg) {
+        set_err(h, code, msg + (H->err.empty() ? "" : ": " + H->err));
+        fl_hmatrix_destroy(H);
+        return code;
+    };
+    try {
+        if (build_cluster_plan(P, eta, leaf, H->plan) != FL_OK) return fail(FL_EINVAL, "leaf < 1 or eta < 0");
+        if (cudaSetDevice(h->device) != cudaSuccess) return fail(FL_ECUDA, "cudaSetDevice");
+        // the mesh tables (vertices, cells, vertex -> cells) come from the handle
+        if (ensure_device_tables(h, pi, st) != FL_OK) return fail(FL_ECUDA, "mesh tables");
+        const ClusterPlan& C = H->plan;
+        const int nn = C.nodes, md = H->md, d = H->d;
+        const int64_t n = C.n;
+        std::vector<int> parent(nn, -1), leaf_of(n, -1), leaves;
+        for (int c = 0; c < nn; ++c) {
+            for (int q = 0; q < 2; ++q)
+                if (C.son[2 * c + q] >= 0) parent[C.son[2 * c + q]] = c;
+            if (C.son[2 * c] < 0) {
+                leaves.push_back(c);
+                for (int p = C.lo[c]; p < C.hi[c]; ++p) leaf_of[p] = c;
+            }
+        }
+        // level lists: fathers for the upward pass (deepest first), non-root nodes for the
+        // downward pass (shallowest first)
+        std::vector<int> up, down;
+        H->up_off.assign(1, 0);
+        for (int L = C.depth - 1; L >= 0; --L) {
+            for (int c = 0; c < nn; ++c)
+                if (C.level[c] == L && C.son[2 * c] >= 0) up.push_back(c);
+            H->up_off.push_back((int)up.size());
+        }
+        H->down_off.assign(1, 0);
+        for (int L = 1; L <= C.depth; ++L) {
+            for (int c = 0; c < nn; ++c)
+                if (C.level[c] == L) down.push_back(c);
+            H->down_off.push_back((int)down.size());
+        }
+        // admissible pairs grouped by sigma (in node order; within sigma in partition order)
+        const int nfar = (int)C.far.size() / 2;
+        std::vector<int> far_ptr(nn + 1, 0), far_sig(nfar), far_tau(nfar), sig_nodes;
+        for (int b = 0; b < nfar; ++b) ++far_ptr[C.far[2 * b] + 1];
+        for (int c = 0; c < nn; ++c) far_ptr[c + 1] += far_ptr[c];
+        {
+            std::vector<int> fill(far_ptr.begin(), far_ptr.end() - 1);
+            for (int b = 0; b < nfar; ++b) {
+                const int k = fill[C.far[2 * b]]++;
+                far_sig[k] = C.far[2 * b];
+                far_tau[k] = C.far[2 * b + 1];
+            }
+        }
+        for (int c = 0; c < nn; ++c)
+            if (far_ptr[c + 1] > far_ptr[c]) sig_nodes.push_back(c);
+        // near field CSR over the original DOF numbering, columns ascending
+        std::vector<std::vector<int>> cols(n);
+        for (size_t b = 0; b + 1 < C.near.size(); b += 2) {
+            const int a = C.near[b], c = C.near[b + 1];
+            for (int p = C.lo[a]; p < C.hi[a]; ++p)
+                for (int q = C.lo[c]; q < C.hi[c]; ++q) cols[C.perm[p]].push_back(C.perm[q]);
+        }
+        std::vector<int> nz_ptr(n + 1, 0), nz_row, nz_col;
+        for (int64_t i = 0; i < n; ++i) {
+            std::sort(cols[i].begin(), cols[i].end());
+            nz_ptr[i + 1] = nz_ptr[i] + (int)cols[i].size();
+            for (int j : cols[i]) {
+                nz_row.push_back((int)i);
+                nz_col.push_back(j);
+            }
+        }
+        H->nnz = nz_ptr[n];
+        H->nleaves = (int)leaves.size();
+        H->nsig = (int)sig_nodes.size();
+        // quadrature of the leaf coefficients: Gauss order m + 1 (collapsed on triangles)
+        const Rule R = make_rule(d, m + 1);
+        std::vector<int> lo(C.lo), hi(C.hi), son(C.son);
+        int *d_lo = nullptr, *d_hi = nullptr, *d_son = nullptr, *d_far_sig = nullptr;
+        double *d_lam = nullptr, *d_w = nullptr;
+        int rc = FL_OK;
+        if ((rc = hm_upload(H, &H->perm, C.perm, st)) || (rc = hm_upload(H, &H->leaf_of, leaf_of, st)) ||
+            (rc = hm_upload(H, &H->parent, parent, st)) || (rc = hm_upload(H, &H->center, C.center, st)) ||
+            (rc = hm_upload(H, &H->side, C.side, st)) || (rc = hm_upload(H, &d_lo, lo, st)) ||
+            (rc = hm_upload(H, &d_hi, hi, st)) || (rc = hm_upload(H, &d_son, son, st)) ||
+            (rc = hm_upload(H, &H->far_ptr, far_ptr, st)) || (rc = hm_upload(H, &H->far_tau, far_tau, st)) ||
+            (rc = hm_upload(H, &d_far_sig, far_sig, st)) || (rc = hm_upload(H, &H->sig_nodes, sig_nodes, st)) ||
+            (rc = hm_upload(H, &H->up_nodes, up, st)) || (rc = hm_upload(H, &H->down_nodes, down, st)) ||
+            (rc = hm_upload(H, &H->leaves, leaves, st)) || (rc = hm_upload(H, &H->nz_ptr, nz_ptr, st)) ||
+            (rc = hm_upload(H, &H->nz_row, nz_row, st)) || (rc = hm_upload(H, &H->nz_col, nz_col, st)) ||
+            (rc = hm_upload(H, &d_lam, R.lam, st)) || (rc = hm_upload(H, &d_w, R.w, st)))
+            return fail(rc, "cluster tables");
+        H->lo_d = d_lo;
+        H->hi_d = d_hi;
+        H->son_d = d_son;
+        if ((rc = hm_alloc(H, &H->coef, (size_t)n * md)) || (rc = hm_alloc(H, &H->shift, (size_t)nn * md * md)) ||
+            (rc = hm_alloc(H, &H->kmat, (size_t)nfar * md * md)) || (rc = hm_alloc(H, &H->xh, (size_t)nn * md)) ||
+            (rc = hm_alloc(H, &H->yh, (size_t)nn * md)) || (rc = hm_alloc(H, &H->nz_val, (size_t)H->nnz)))
+            return fail(rc, "cluster workspace");
+        const DevTables& t = h->dev[pi];
+        leaf_coef_kernel<<<blocks_for(n * md, 128), 128, 0, st>>>(n, d, H->m, md, H->perm, H->leaf_of, H->center,
+                                                                  H->side, t.vod, t.v2c_ptr, t.v2c, t.cells, t.V,
+                                                                  t.jac_orig, R.q, d_lam, d_w, H->coef);
+        shift_kernel<<<blocks_for((int64_t)nn * md * md, 128), 128, 0, st>>>(nn, d, H->m, md, H->parent, H->center,
+                                                                            H->side, H->shift);
+        if (nfar > 0)
+            kmat_kernel<<<blocks_for((int64_t)nfar * md * md, 128), 128, 0, st>>>(
+                nfar, d, H->m, md, d_far_sig, H->far_tau, H->center, H->side, -(d + 2.0 * s) / 2.0, H->kmat);
+        count_launch(nfar > 0 ? 3 : 2);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(FL_ECUDA, std::string("cluster set-up: ") + cudaGetErrorString(e));
+    } catch (const std::bad_alloc&) {
+        return fail(FL_ENOMEM, "out of host memory");
+    }
+    *out = H;
+    return FL_OK;
+}
+
+int fl_hmatrix_set_near(fl_hmatrix H, const double* A_dev, int64_t lda, void* stream) {
+    if (!H) return FL_EINVAL;
+    H->err.clear();
+    if (!A_dev || lda < H->plan.n) return hm_fail(H, FL_EINVAL, "bad A / lda");
+    if (cudaSetDevice(H->device) != cudaSuccess) return hm_fail(H, FL_ECUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (H->nnz > 0) {
+        near_gather_kernel<<<blocks_for(H->nnz, 256), 256, 0, st>>>(H->nnz, H->nz_row, H->nz_col, A_dev, lda, H->nz_val);
+        count_launch(1);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return hm_fail(H, FL_ECUDA, std::string("near gather: ") + cudaGetErrorString(e));
+    H->near_ready = true;
+    return FL_OK;
+}
+
+int fl_hmatrix_matvec(fl_hmatrix H, const double* x_dev, double* y_dev, void* stream) {
+    if (!H) return FL_EINVAL;
+    H->err.clear();
+    if (!x_dev || !y_dev || x_dev == y_dev) return hm_fail(H, FL_EINVAL, "bad x / y (y must not be x)");
+    if (!H->near_ready) return hm_fail(H, FL_EINVAL, "near field not set (fl_hmatrix_set_near)");
+    if (cudaSetDevice(H->device) != cudaSuccess) return hm_fail(H, FL_ECUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    const ClusterPlan& C = H->plan;
+    const int64_t n = C.n;
+    const int md = H->md, nn = C.nodes;
+    int launches = 0;
+    near_spmv_kernel<<<blocks_for(n * 32, 256), 256, 0, st>>>(n, H->nz_ptr, H->nz_col, H->nz_val, x_dev, y_dev);
+    up_leaf_kernel<<<blocks_for((int64_t)H->nleaves * md, 128), 128, 0, st>>>(H->nleaves, md, H->leaves, H->lo_d,
+                                                                             H->hi_d, H->perm, H->coef, x_dev, H->xh);
+    launches += 2;
+    for (size_t L = 0; L + 1 < H->up_off.size(); ++L) {
+        const int cnt = H->up_off[L + 1] - H->up_off[L];
+        if (cnt == 0) continue;
+        up_level_kernel<<<blocks_for((int64_t)cnt * md, 128), 128, 0, st>>>(cnt, md, H->up_nodes + H->up_off[L],
+                                                                           H->son_d, H->shift, H->xh);
+        ++launches;
+    }
+    if (cudaMemsetAsync(H->yh, 0, (size_t)nn * md * sizeof(double), st) != cudaSuccess)
+        return hm_fail(H, FL_ECUDA, "memset");
+    if (H->nsig > 0) {
+        couple_kernel<<<blocks_for((int64_t)H->nsig * md, 128), 128, 0, st>>>(H->nsig, md, H->sig_nodes, H->far_ptr,
+                                                                             H->far_tau, H->kmat, H->xh, H->yh);
+        ++launches;
+    }
+    for (size_t L = 0; L + 1 < H->down_off.size(); ++L) {
+        const int cnt = H->down_off[L + 1] - H->down_off[L];
+        if (cnt == 0) continue;
+        down_level_kernel<<<blocks_for((int64_t)cnt * md, 128), 128, 0, st>>>(cnt, md, H->down_nodes + H->down_off[L],
+                                                                             H->parent, H->shift, H->yh);
+        ++launches;
+    }
+    down_leaf_kernel<<<blocks_for(n, 128), 128, 0, st>>>(n, md, H->perm, H->leaf_of, H->coef, H->yh, -H->C, y_dev);
+    ++launches;
+    count_launch(launches);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FL_OK : hm_fail(H, FL_ECUDA, std::string("H-matrix product: ") + cudaGetErrorString(e));
+}
+
+int fl_hmatrix_info(fl_hmatrix H, int64_t* info) {
+    if (!H || !info) return FL_EINVAL;
+    info[0] = H->plan.nodes;
+    info[1] = (int64_t)H->plan.far.size() / 2;
+    info[2] = (int64_t)H->plan.near.size() / 2;
+    info[3] = H->nnz;
+    info[4] = H->bytes;
+    info[5] = H->plan.depth;
+    return FL_OK;
+}
+
+const char* fl_hmatrix_last_error(fl_hmatrix H) { return H ? H->err.c_str() : "null H-matrix handle"; }
+
+}  // extern "C"

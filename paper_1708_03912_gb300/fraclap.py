@@ -24,7 +24,8 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
 
 EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
            "fl_assemble", "fl_tune_assemble", "fl_set_far_variant", "fl_assemble_nearfield_csr", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
-           "fl_heat_matrix", "fl_mass_apply", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
+           "fl_heat_matrix", "fl_mass_apply", "fl_cluster_plan", "fl_hmatrix_create", "fl_hmatrix_set_near",
+           "fl_hmatrix_matvec", "fl_hmatrix_info", "fl_hmatrix_last_error", "fl_hmatrix_destroy", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
            "fl_matvec_f32_static",
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
            "fl_tune_batch", "fl_tune_matvec", "fl_tune_record", "fl_tune_lookup", "fl_tune_clear", "fl_tune_count", "fl_tune_save",
@@ -133,6 +134,20 @@ def lib():
     L.fl_heat_matrix.restype = ci
     L.fl_mass_apply.argtypes = [vp, dbl, ci, dbl, vp, i64, dbl, vp, i64, vp, i64, vp]
     L.fl_mass_apply.restype = ci
+    L.fl_cluster_plan.argtypes = [vp, dbl, dbl, ci, ctypes.POINTER(i64), vp, vp, vp, vp]
+    L.fl_cluster_plan.restype = ci
+    L.fl_hmatrix_create.argtypes = [vp, dbl, ci, dbl, ci, ctypes.POINTER(vp), vp]
+    L.fl_hmatrix_create.restype = ci
+    L.fl_hmatrix_set_near.argtypes = [vp, vp, i64, vp]
+    L.fl_hmatrix_set_near.restype = ci
+    L.fl_hmatrix_matvec.argtypes = [vp, vp, vp, vp]
+    L.fl_hmatrix_matvec.restype = ci
+    L.fl_hmatrix_info.argtypes = [vp, ctypes.POINTER(i64)]
+    L.fl_hmatrix_info.restype = ci
+    L.fl_hmatrix_last_error.argtypes = [vp]
+    L.fl_hmatrix_last_error.restype = ctypes.c_char_p
+    L.fl_hmatrix_destroy.argtypes = [vp]
+    L.fl_hmatrix_destroy.restype = None
     L.fl_default_solve_opts.argtypes = [ctypes.POINTER(fl_solve_opts)]
     L.fl_default_solve_opts.restype = None
     L.fl_solve.argtypes = [vp, i64, vp, i64, vp, vp, ctypes.POINTER(fl_solve_opts), ctypes.POINTER(fl_solve_info), vp]
@@ -367,6 +382,56 @@ def fl_mass_apply(h, s, alpha, X, beta, B, Y, stream=None):
     ld = lambda T: (T.stride(0) if T.dim() == 2 else 1) if T is not None else 1  # noqa: E731
     _check(lib().fl_mass_apply(h, s, nrhs, alpha, _ptr(X), ld(X), beta, _ptr(B) if B is not None else None, ld(B),
                                _ptr(Y), ld(Y), _stream(stream)), h)
+
+
+def fl_cluster_plan(h, s, eta=1.0, leaf=32):
+    """Host-only cluster tree and partition: dict with perm [n], node [nodes, 4] (lo, hi, son0,
+    son1), far [pairs, 2], near [pairs, 2] (int32 numpy arrays)."""
+    sizes = (ctypes.c_int64 * 3)()
+    _check(lib().fl_cluster_plan(h, s, eta, leaf, sizes, None, None, None, None), h)
+    nn, nf, nr = sizes[0], sizes[1], sizes[2]
+    n = fl_num_dofs(h, s)
+    perm = np.zeros(n, dtype=np.int32)
+    node = np.zeros((nn, 4), dtype=np.int32)
+    far = np.zeros((nf, 2), dtype=np.int32)
+    near = np.zeros((nr, 2), dtype=np.int32)
+    _check(lib().fl_cluster_plan(h, s, eta, leaf, sizes, perm.ctypes.data, node.ctypes.data, far.ctypes.data,
+                                 near.ctypes.data), h)
+    return {"perm": perm, "node": node, "far": far, "near": near}
+
+
+class HMatrix:
+    """Cluster-method approximation of A^s on a mesh handle (Section 6); owns an fl_hmatrix."""
+
+    def __init__(self, h, s, m=4, eta=1.0, leaf=32, stream=None):
+        self.hm = ctypes.c_void_p()
+        _check(lib().fl_hmatrix_create(h, s, m, eta, leaf, ctypes.byref(self.hm), _stream(stream)), h)
+
+    def _check(self, r):
+        if r != FL_OK:
+            raise FlError(r, lib().fl_hmatrix_last_error(self.hm).decode(errors="replace"))
+
+    def set_near(self, A, stream=None):
+        self._check(lib().fl_hmatrix_set_near(self.hm, _ptr(A), A.stride(0), _stream(stream)))
+
+    def matvec(self, x, y, stream=None):
+        self._check(lib().fl_hmatrix_matvec(self.hm, _ptr(x), _ptr(y), _stream(stream)))
+
+    def info(self):
+        v = (ctypes.c_int64 * 6)()
+        self._check(lib().fl_hmatrix_info(self.hm, v))
+        return dict(zip(["nodes", "far_pairs", "near_pairs", "near_entries", "device_bytes", "depth"], list(v)))
+
+    def close(self):
+        if self.hm:
+            lib().fl_hmatrix_destroy(self.hm)
+            self.hm = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fl_default_solve_opts():
