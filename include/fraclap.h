@@ -102,7 +102,8 @@ int fl_create(fl_handle* h, int dim, int64_t n_vertices, const double* vertices_
 /* Release the handle and every device buffer it owns (synchronises the device). */
 void fl_destroy(fl_handle h);
 
-/* Last error message of the handle ("" if none); valid until the next call on h. */
+/* Last error message of the handle ("" if none); valid until the next call on h.  With
+ * h = NULL: the message of the calling thread's last failed fl_create or fl_refine. */
 const char* fl_last_error(fl_handle h);
 
 /* Number n of degrees of freedom for order s (depends on s only under FL_DOF_PAPER). */
@@ -197,6 +198,68 @@ int fl_heat_matrix(fl_handle h, double s, double dt, const double* A_dev, int64_
                    void* stream);
 int fl_mass_apply(fl_handle h, double s, int nrhs, double alpha, const double* X_dev, int64_t ldx, double beta,
                   const double* B_dev, int64_t ldb, double* Y_dev, int64_t ldy, void* stream);
+
+/*
+ * Adaptive refinement (Section 4 with Appendix A; the loop of Section 7: solve, estimate,
+ * mark with the maximum strategy, refine without hanging nodes).
+ *
+ * Cell rule of order k_cell (the points where the strong form is evaluated): 1D Gauss-Legendre
+ * on [x0, x1], q = k_cell points at x0 + t_a (x1 - x0); 2D the collapsed product rule,
+ * q = k_cell^2 points at v0 + l1 (v1 - v0) + l2 (v2 - v0), l1 = t_a, l2 = t_b (1 - t_a), point
+ * (a, b) at index a k_cell + b, weight w_a w_b (1 - t_a) 2|K|; (v0, v1, v2) the cell's vertices
+ * in the given order, swapped to (v0, v2, v1) for a clockwise cell, as fl_create orients them.
+ *
+ * fl_strong_form: S_dev[K q + a] = (-Delta)^s u_h at point a of cell K (original cell order),
+ *   u_h = sum_i u_i phi_i with u_dev the n float64 DOF values of h's DOF set at s (device).
+ *   Lemma 4.1 turns the hypersingular integral into regular integrals over cell boundaries
+ *   (eq. (8); eq. (9) for s = 1 - d/2, i.e. 1D with s = 1/2).  The three edges of the point's
+ *   own cell are integrated by Gauss-Legendre of order k_near (the integrand is nearly
+ *   singular there), every other edge by order k_edge (1D: the facets are points and neither
+ *   order matters).  1 <= k_cell <= 16, 1 <= k_edge <= 32, 1 <= k_near <= 64.  Cost
+ *   O(n_cells q n_edges k_edge): every point meets every edge.  Float64 accuracy; 2D with
+ *   s in {1/4, 1/2, 3/4} runs in double-word arithmetic on the float32 pipe (unless the
+ *   handle's options set far_f64_pipe), the rest on the float64 pipe.  Deterministic.  Uses
+ *   a device workspace owned by h, grown on demand (the call may synchronise to grow it).
+ * fl_br_indicators: eta_dev[n] = the Babuska-Rheinboldt indicators (eq. (BRindicators)),
+ *   eta_i^2 = sum over the cells K around DOF i's vertex of h_K^{2s} ||f - (-Delta)^s u_h||^2
+ *   on K, h_K the longest edge (1D: the length), the L2 norm by the cell rule above.
+ *   f_nodal_dev NULL: f = 1; else n_vertices float64 nodal values, f their P1 interpolant.
+ *   S_dev: NULL, or [n_cells q] float64 that receives the strong form.  Synchronises `stream`.
+ * fl_mark_max: maximum marking with threshold theta, 0 < theta <= 1 (Section 7 uses 0.8):
+ *   DOF i is marked when eta_i >= theta max_j eta_j (float64).  dof_marks_dev[n] (uint8,
+ *   may be NULL) = 1 for marked DOFs, else 0; cell_marks_dev[n_cells] (uint8, may be NULL) = 1
+ *   for the cells around a marked DOF's vertex (the patches S_i), else 0.  Not both NULL.
+ * Errors: FL_EINVAL (s not in (0,1), NULL pointers, orders out of range, theta), FL_ENOMEM,
+ *   FL_ECUDA.
+ */
+int fl_strong_form(fl_handle h, double s, const double* u_dev, int k_cell, int k_edge, int k_near, double* S_dev,
+                   void* stream);
+int fl_br_indicators(fl_handle h, double s, const double* u_dev, const double* f_nodal_dev, int k_cell, int k_edge,
+                     int k_near, double* eta_dev, double* S_dev, void* stream);
+int fl_mark_max(fl_handle h, double s, const double* eta_dev, double theta, uint8_t* dof_marks_dev,
+                uint8_t* cell_marks_dev, void* stream);
+
+/*
+ * Conforming refinement of the cells with cell_marks[k] != 0 (host arrays; no handle, no
+ * device work).  Input as fl_create: vertices [n_vertices][dim], cells [n_cells][dim+1].
+ * 1D: a marked interval (a, b) becomes (a, m), (m, b).  2D: newest-vertex bisection; a cell
+ * (v0, v1, v2) has newest vertex v0 and refinement edge {v1, v2}, and bisects into
+ * (m, v0, v1), (m, v2, v0) with m the edge's midpoint.  Every marked cell is bisected, and
+ * neighbours are bisected as far as needed to leave no hanging node: the set of halved edges
+ * is the smallest that holds the marked cells' refinement edges and, with any edge of a cell,
+ * that cell's refinement edge.  A cell thus becomes 1 to 4 cells; the result does not depend
+ * on the order of the cells.  Numbering: old vertices keep their ids, midpoints follow in
+ * order of creation (cells in input order; per cell the refinement edge's midpoint, then
+ * those of its first and second child); each cell is replaced in place by its children.
+ * Outputs (caller-owned host arrays): vertices_out [cap_vertices][dim], cells_out
+ * [cap_cells][dim+1], and their counts.  n_vertices + 3 n_cells vertices and 4 n_cells cells
+ * always suffice.  Errors: FL_EINVAL for bad arguments, an index out of range, an edge shared
+ * by more than two cells, or a capacity below the result (the needed counts are still
+ * stored); FL_ENOMEM.  fl_last_error(NULL) gives the message.
+ */
+int fl_refine(int dim, int64_t n_vertices, const double* vertices, int64_t n_cells, const int32_t* cells,
+              const uint8_t* cell_marks, int64_t cap_vertices, int64_t cap_cells, double* vertices_out,
+              int32_t* cells_out, int64_t* n_vertices_out, int64_t* n_cells_out);
 
 /*
  * The dense matrix-vector product of the iterative solvers (Section 5: n^2 work per

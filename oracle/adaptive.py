@@ -61,33 +61,45 @@ def _gradient(mesh: OracleMesh, k, u):
     return np.linalg.solve(J, np.array([u[cell[1]] - u[cell[0]], u[cell[2]] - u[cell[0]]]))
 
 
-def _boundary(mesh: OracleMesh, k, k_edge):
-    """Quadrature on the boundary of cell k, one entry per facet: (vertex set, points [m, d],
-    weights [m], outward normals [m, d], nodal interpolation weights [m, d+1])."""
-    cell = mesh.C[k]
-    if mesh.dim == 1:
-        return [(frozenset([cell[0]]), mesh.V[cell[0]][None, :], np.ones(1), np.array([[-1.0]]), np.array([[1.0, 0.0]])),
-                (frozenset([cell[1]]), mesh.V[cell[1]][None, :], np.ones(1), np.array([[1.0]]), np.array([[0.0, 1.0]]))]
+def _boundary_arrays(mesh: OracleMesh, k_edge):
+    """Quadrature on the boundaries of all cells, one row per (cell, facet): vertex keys
+    [nc, F, 2] (sorted ids; 1D: the vertex twice), points [nc, F, g, d], weights [nc, F, g],
+    outward normals [nc, F, d], nodal interpolation weights [nc, F, g, d+1]."""
+    nc, d = mesh.nc, mesh.dim
+    if d == 1:
+        keys = np.stack([np.stack([mesh.C[:, 0], mesh.C[:, 0]], 1), np.stack([mesh.C[:, 1], mesh.C[:, 1]], 1)], 1)
+        Y = mesh.V[mesh.C][:, :, None, :]                    # [nc, 2, 1, 1]
+        W = np.ones((nc, 2, 1))
+        N = np.tile(np.array([[-1.0], [1.0]]), (nc, 1, 1))
+        B = np.zeros((nc, 2, 1, 2))
+        B[:, 0, 0, 0] = 1.0
+        B[:, 1, 0, 1] = 1.0
+        return keys, Y, W, N, B
     t, w = rules.gauss01(k_edge)
-    P = mesh.V[cell]
-    out = []
-    centroid = P.mean(axis=0)
+    P = mesh.V[mesh.C]                                        # [nc, 3, 2]
+    centroid = P.mean(axis=1)
+    keys, Y, W, N, B = [], [], [], [], []
     for a, b in ((0, 1), (1, 2), (2, 0)):
-        e = P[b] - P[a]
-        L = math.hypot(e[0], e[1])
-        n = np.array([e[1], -e[0]]) / L
-        if np.dot(n, P[a] - centroid) < 0:
-            n = -n
-        bary = np.zeros((len(t), 3))
-        bary[:, a] = 1.0 - t
-        bary[:, b] = t
-        out.append((frozenset([cell[a], cell[b]]), P[a] + t[:, None] * e, w * L, np.tile(n, (len(t), 1)), bary))
-    return out
+        e = P[:, b] - P[:, a]
+        L = np.hypot(e[:, 0], e[:, 1])
+        n = np.stack([e[:, 1], -e[:, 0]], 1) / L[:, None]
+        flip = np.sum(n * (P[:, a] - centroid), axis=1) < 0
+        n[flip] = -n[flip]
+        keys.append(np.sort(np.stack([mesh.C[:, a], mesh.C[:, b]], 1), axis=1))
+        Y.append(P[:, a, None, :] + t[None, :, None] * e[:, None, :])
+        W.append(w[None, :] * L[:, None])
+        N.append(n)
+        bary = np.zeros((nc, len(t), 3))
+        bary[:, :, a] = 1.0 - t[None, :]
+        bary[:, :, b] = t[None, :]
+        B.append(bary)
+    return np.stack(keys, 1), np.stack(Y, 1), np.stack(W, 1), np.stack(N, 1), np.stack(B, 1)
 
 
 def strong_form(mesh: OracleMesh, s: float, u_dof, k_cell: int = 3, k_edge: int = 4, k_near: int = 16,
-                dof_mode: str = "interior"):
-    """(-Delta)^s u_h at the cell-rule points of every cell: [nc, q] (Lemma 4.1)."""
+                dof_mode: str = "interior", cells=None):
+    """(-Delta)^s u_h at the cell-rule points of every cell: [nc, q] (Lemma 4.1); with `cells`,
+    only at the points of those cells: [len(cells), q]."""
     d = mesh.dim
     C = frac_constant(d, s)
     u = _nodal(mesh, s, u_dof, dof_mode)
@@ -95,41 +107,50 @@ def strong_form(mesh: OracleMesh, s: float, u_dof, k_cell: int = 3, k_edge: int 
     q = X.shape[1]
     log_case = abs(s - (1.0 - d / 2.0)) < 1e-14
     m = d + 2.0 * s - 2.0
-    grads = [_gradient(mesh, k, u) for k in range(mesh.nc)]
-    bnd = [_boundary(mesh, k, k_edge) for k in range(mesh.nc)]
-    bnd_near = [_boundary(mesh, k, k_near) for k in range(mesh.nc)]
-    out = np.zeros((mesh.nc, q))
-    for k0 in range(mesh.nc):
+    grads = np.array([_gradient(mesh, k, u) for k in range(mesh.nc)])      # [nc, d]
+    far = _boundary_arrays(mesh, k_edge)
+    near = _boundary_arrays(mesh, k_near)
+    keys = far[0]
+    all_cells = np.arange(mesh.nc)
+    cells = all_cells if cells is None else np.asarray(cells)
+    out = np.zeros((len(cells), q))
+
+    def terms(x, arrays, sel, k0, idx):
+        """The integrals over the facets sel ([nc, F] mask) of the boundaries of the cells idx,
+        with the weights of eq. (8)/(9): 1/m (log case: 1) and -u(x)/(2s) on K0's own boundary,
+        1/(2s m) (log case: 1/(2s)) and -u(y)/(2s) on every other cell's boundary."""
+        Y, W, N, B = (a[idx] for a in arrays[1:])
+        sel = sel[idx]
+        diff = x - Y                                          # [cells, F, g, d]
+        r = np.sqrt(np.sum(diff * diff, axis=-1))
+        gn = np.sum(N * grads[idx][:, None, :], axis=-1)      # [cells, F]
+        nd = np.sum(N[:, :, None, :] * diff, axis=-1)         # [cells, F, g]
+        kern = np.log(1.0 / r) if log_case else r ** (-m)
+        g_int = np.sum(W * kern, axis=-1) * gn                # [cells, F]
+        uy = np.einsum("kfgv,kv->kfg", B, u[mesh.C[idx]])
+        own = idx == k0
+        g_w = np.where(own, 1.0 if log_case else 1.0 / m, 1.0 / (2.0 * s) if log_case else 1.0 / (2.0 * s * m))
+        val = np.sum(np.where(sel, g_int * g_w[:, None], 0.0))
+        u_int = np.sum(W * nd / r ** (d + 2.0 * s) * uy, axis=-1)       # other cells: u(y)
+        o_int = np.sum(W * nd / r ** (d + 2.0 * s), axis=-1)            # own cell: times u(x)
+        return val, np.where(sel & ~own[:, None], u_int, 0.0), np.where(sel & own[:, None], o_int, 0.0)
+
+    for row, k0 in enumerate(cells):
+        # facets of K0, whichever cell's boundary they are part of
+        sel_near = np.any(np.all(keys[:, :, None, :] == keys[k0][None, None, :, :], axis=-1), axis=-1)  # [nc, F]
+        near_cells = np.nonzero(sel_near.any(axis=1))[0]
         for a in range(q):
             x = X[k0, a]
-            # u(x) from the cell's nodal values at the reference point
             if d == 1:
                 lam = np.array([1.0 - ref[a, 0], ref[a, 0]])
             else:
                 lam = np.array([1.0 - ref[a, 0] - ref[a, 1], ref[a, 0], ref[a, 1]])
             ux = lam @ u[mesh.C[k0]]
-            own = {f[0] for f in bnd_near[k0]}
             val = 0.0
-            for k in range(mesh.nc):
-                for fi, (key, y, w, n, bary) in enumerate(bnd[k]):
-                    if key in own:
-                        key, y, w, n, bary = bnd_near[k][fi]
-                    diff = x[None, :] - y
-                    r = np.sqrt(np.sum(diff * diff, axis=1))
-                    gn = n @ grads[k]
-                    nd = np.sum(n * diff, axis=1)
-                    if log_case:
-                        g_term = np.sum(w * gn * np.log(1.0 / r))
-                    else:
-                        g_term = np.sum(w * gn / r ** m)
-                    if k == k0:
-                        val += g_term if log_case else g_term / m
-                        val -= ux / (2.0 * s) * np.sum(w * nd / r ** (d + 2.0 * s))
-                    else:
-                        uy = bary @ u[mesh.C[k]]
-                        val += (g_term / (2.0 * s)) if log_case else g_term / (2.0 * s * m)
-                        val -= np.sum(w * uy * nd / r ** (d + 2.0 * s)) / (2.0 * s)
-            out[k0, a] = C * val
+            for arrays, sel, idx in ((far, ~sel_near, all_cells), (near, sel_near, near_cells)):
+                v, u_other, own_int = terms(x, arrays, sel, k0, idx)
+                val += v - np.sum(u_other) / (2.0 * s) - ux / (2.0 * s) * np.sum(own_int)
+            out[row, a] = C * val
     return out
 
 

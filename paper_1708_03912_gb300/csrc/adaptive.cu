@@ -1,0 +1,804 @@
+// Adaptive refinement on the device (Section 4 and Appendix A of arXiv:1708.03912): the
+// strong form (-Delta)^s u_h at the points of a cell rule, the Babuska-Rheinboldt indicators
+// and maximum marking.  The refinement of the marked cells is host code (refine.cpp).
+//
+// Lemma 4.1 writes (-Delta)^s u_h(x), x inside the cell K0, as regular integrals over cell
+// boundaries (eq. (8); eq. (9), with a logarithmic kernel, when s = 1 - d/2).  With
+// m = d + 2s - 2, n_K the outward normal of K and C = C(d, s):
+//   (-Delta)^s u_h(x) / C = (1/m) int_{dK0} n.grad u_K0 |x-y|^{-m} - u(x)/(2s) int_{dK0} n.(x-y) |x-y|^{-d-2s}
+//       + sum_{K != K0} [ 1/(2sm) int_{dK} n.grad u_K |x-y|^{-m} - 1/(2s) int_{dK} u(y) n.(x-y) |x-y|^{-d-2s} ].
+// Here the sum is gathered by facet instead of by cell.  Both sides of a facet see the same
+// quadrature points, so the discrete sums agree up to rounding:
+//   * a facet e not on dK0 between K+ and K- (n_e outward of K+) contributes
+//     1/(2sm) int_e n_e.(grad u_K+ - grad u_K-) |x-y|^{-m}, the jump of the normal derivative:
+//     the u(y) terms of its two sides cancel, u_h being continuous;
+//   * a boundary facet not on dK0 contributes 1/(2sm) int_e n.grad u_K |x-y|^{-m}
+//     - 1/(2s) int_e u(y) n.(x-y) |x-y|^{-d-2s}; the second part vanishes unless boundary
+//     vertices carry degrees of freedom;
+//   * a facet e of K0 with neighbour K' (n0 outward of K0) contributes
+//     int_e [(1/m) n0.grad u_K0 - 1/(2sm) n0.grad u_K'] |x-y|^{-m}
+//     - 1/(2s) int_e (u(x) - u(y)) n0.(x-y) |x-y|^{-d-2s}, with u(x) - u(y) = grad u_K0.(x-y)
+//     (u_h is linear on K0); on the boundary, without K', the first bracket keeps its first
+//     term and u(x) - u(y) becomes u(x).
+// In the log case |x-y|^{-m} / m becomes log(1/|x-y|) (and 1/(2sm) becomes 1/(2s)).  The
+// facets of K0 are integrated by Gauss-Legendre of order k_near, all others by order k_edge
+// (1D: the facets are points).
+//
+// Kernels: sf_prep (cell gradients and the points, in the planner's spatial cell order),
+// sf_facet (per facet and Gauss point: the point and its coefficient), sf_far_dw (2D with s in
+// {1/4, 1/2, 3/4}: the sum over the facets not on dK0 in double-word arithmetic on the float32
+// pipe, coordinates taken relative to an origin per block so that the difference of nearby
+// points keeps its relative accuracy), sf_far_f64 (other s, and 1D: float64), sf_near (the
+// facets of K0 in float64, and the sum of the parts).  Every sum runs in a fixed order: the
+// result is bitwise reproducible.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "context.h"
+#include "device.h"
+
+namespace fl {
+namespace {
+
+#define SF_TRY(...)                 \
+    do {                            \
+        int r_ = (__VA_ARGS__);     \
+        if (r_ != FL_OK) return r_; \
+    } while (0)
+#define SF_CUDA(h, x)                                                                                     \
+    do {                                                                                                  \
+        cudaError_t e_ = (x);                                                                             \
+        if (e_ != cudaSuccess) return set_err(h, FL_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int SF_THREADS = 128;
+constexpr int SF_TREC = 512;   // facet points per shared-memory tile
+constexpr int SF_MAXK_CELL = 16, SF_MAXK_EDGE = 32, SF_MAXK_NEAR = 64;
+
+double frac_const(int d, double s) {
+    // C(d, s) = 2^{2s} s Gamma((d + 2s)/2) / (pi^{d/2} Gamma(1 - s))
+    return std::pow(2.0, 2.0 * s) * s * std::tgamma((d + 2.0 * s) / 2.0) /
+           (std::pow(M_PI, d / 2.0) * std::tgamma(1.0 - s));
+}
+
+// ------------------------------------------------------------------ kernels --
+
+// gradients of u_h on every cell (original order) and the cell-rule points (internal order)
+__global__ void sf_prep_kernel(int64_t nc, int d, int q, const int* __restrict__ perm, const int* __restrict__ cells,
+                               const double* __restrict__ V, const int* __restrict__ dov, const double* __restrict__ u,
+                               const double* __restrict__ lam, double* __restrict__ grad, double* __restrict__ X) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nc) return;
+    const int K = perm[k];
+    const int* c = cells + (int64_t)K * (d + 1);
+    double uv[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j <= d; ++j) {
+        const int i = dov[c[j]];
+        uv[j] = i >= 0 ? u[i] : 0.0;
+    }
+    if (d == 1) {
+        const double x0 = V[c[0]], x1 = V[c[1]];
+        grad[K] = (uv[1] - uv[0]) / (x1 - x0);
+        for (int a = 0; a < q; ++a) X[k * q + a] = x0 + lam[a] * (x1 - x0);
+    } else {
+        const double p0x = V[2 * c[0]], p0y = V[2 * c[0] + 1];
+        const double e1x = V[2 * c[1]] - p0x, e1y = V[2 * c[1] + 1] - p0y;
+        const double e2x = V[2 * c[2]] - p0x, e2y = V[2 * c[2] + 1] - p0y;
+        const double du1 = uv[1] - uv[0], du2 = uv[2] - uv[0];
+        const double det = e1x * e2y - e1y * e2x;
+        grad[2 * K] = (du1 * e2y - du2 * e1y) / det;
+        grad[2 * K + 1] = (e1x * du2 - e2x * du1) / det;
+        for (int a = 0; a < q; ++a) {
+            const double l1 = lam[2 * a], l2 = lam[2 * a + 1];
+            X[2 * (k * q + a)] = p0x + l1 * e1x + l2 * e2x;
+            X[2 * (k * q + a) + 1] = p0y + l1 * e1y + l2 * e2y;
+        }
+    }
+}
+
+// per facet e and Gauss point g: the point y, cA = w |e| J_e cA_scale (J_e the jump of the
+// normal derivative, the one-sided value on the boundary) and, on boundary facets,
+// cB = w |e| u(y) cB_scale
+__global__ void sf_facet_kernel(int64_t nfac, int64_t nint, int d, int ke, const int* __restrict__ fac,
+                                const double* __restrict__ fn, const double* __restrict__ V, const int* __restrict__ dov,
+                                const double* __restrict__ u, const double* __restrict__ grad,
+                                const double* __restrict__ te, const double* __restrict__ we, double cA_scale,
+                                double cB_scale, int termB, double* __restrict__ yrec, double* __restrict__ crec,
+                                double* __restrict__ brec) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nfac * ke) return;
+    const int64_t e = i / ke;
+    const int g = (int)(i - e * ke);
+    const int a = fac[4 * e], b = fac[4 * e + 1], kp = fac[4 * e + 2], km = fac[4 * e + 3];
+    const double* n = fn + e * (d + 1);
+    const double L = n[d];
+    double J = 0.0;
+    for (int c = 0; c < d; ++c) J += n[c] * (grad[(int64_t)kp * d + c] - (km >= 0 ? grad[(int64_t)km * d + c] : 0.0));
+    double w, t = 0.0;
+    if (d == 1) {
+        yrec[i] = V[a];
+        w = 1.0;
+    } else {
+        t = te[g];
+        const double ax = V[2 * a], ay = V[2 * a + 1];
+        yrec[2 * i] = ax + t * (V[2 * b] - ax);
+        yrec[2 * i + 1] = ay + t * (V[2 * b + 1] - ay);
+        w = we[g] * L;
+    }
+    crec[i] = w * J * cA_scale;
+    if (termB && e >= nint) {
+        const int ia = dov[a], ib = dov[b];
+        const double ua = ia >= 0 ? u[ia] : 0.0, ub = ib >= 0 ? u[ib] : 0.0;
+        const double uy = d == 1 ? ua : (1.0 - t) * ua + t * ub;
+        brec[(e - nint) * ke + g] = w * uy * cB_scale;
+    }
+}
+
+// Sum over the facet points of facets [f_begin, f_end) not on the boundary of the point's own
+// cell, 2D, double-word.  BND = false: c |x-y|^{-2s} with PWK = 4s; BND = true (boundary facets,
+// term with u(y)): c n.(x-y) |x-y|^{-2-2s} with PWK = 4 + 4s.  Each thread takes R points of
+// the block's range (stride SF_THREADS); blockIdx.y picks the facet chunk.
+template <int PWK, bool BND, int R>
+__global__ void __launch_bounds__(SF_THREADS) sf_far_dw_kernel(
+    int64_t npts, int q, const double* __restrict__ X, const int* __restrict__ perm, const int* __restrict__ c2f,
+    int ke, int64_t f_begin, int64_t f_end, int64_t fac_per_chunk, const double* __restrict__ yrec,
+    const double* __restrict__ crec, const double* __restrict__ fn, double* __restrict__ part) {
+    __shared__ float4 sy[SF_TREC];
+    __shared__ float2 sc[SF_TREC];
+    __shared__ float4 sn[BND ? SF_TREC : 1];
+    const int64_t pb = (int64_t)blockIdx.x * SF_THREADS * R;
+    // origin of the block: its first point
+    const double ox = X[2 * pb], oy = X[2 * pb + 1];
+    dw xr[R], yr[R], acc[R];
+    int f0[R], f1[R], f2[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t p = pb + r * SF_THREADS + threadIdx.x;
+        acc[r] = {0.f, 0.f};
+        if (p < npts) {
+            xr[r] = dw_from(X[2 * p] - ox);
+            yr[r] = dw_from(X[2 * p + 1] - oy);
+            const int K = perm[p / q];
+            f0[r] = c2f[3 * K];
+            f1[r] = c2f[3 * K + 1];
+            f2[r] = c2f[3 * K + 2];
+        } else {
+            xr[r] = {0.f, 0.f};
+            yr[r] = {0.f, 0.f};
+            f0[r] = f1[r] = f2[r] = -1;
+        }
+    }
+    const int64_t fb = f_begin + (int64_t)blockIdx.y * fac_per_chunk;
+    const int64_t fe = min(f_end, fb + fac_per_chunk);
+    const int fpt = SF_TREC / ke;
+    for (int64_t f = fb; f < fe; f += fpt) {
+        const int nf = (int)min((int64_t)fpt, fe - f);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nf * ke; i += SF_THREADS) {
+            const int64_t gi = f * ke + i;
+            const dw yx = dw_from(yrec[2 * gi] - ox), yy = dw_from(yrec[2 * gi + 1] - oy);
+            sy[i] = make_float4(yx.h, yx.l, yy.h, yy.l);
+            const dw c = dw_from(BND ? crec[gi - f_begin * ke] : crec[gi]);
+            sc[i] = make_float2(c.h, c.l);
+            if constexpr (BND) {
+                const int64_t e = f + i / ke;
+                const dw nx = dw_from(fn[3 * e]), ny = dw_from(fn[3 * e + 1]);
+                sn[i] = make_float4(nx.h, nx.l, ny.h, ny.l);
+            }
+        }
+        __syncthreads();
+        for (int j = 0; j < nf; ++j) {
+            const int e = (int)(f + j);
+            bool use[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) use[r] = e != f0[r] && e != f1[r] && e != f2[r];
+            for (int g = 0; g < ke; ++g) {
+                const float4 y = sy[j * ke + g];
+                const float2 c2 = sc[j * ke + g];
+                const dw c = {c2.x, c2.y};
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (!use[r]) continue;
+                    // x - y: the low parts' difference can be as large as the high parts'
+                    // when the points are close, so the pair is renormalised (TwoSum) before
+                    // it is squared
+                    dw dx = two_sum(xr[r].h, -y.x);
+                    dx = two_sum(dx.h, __fadd_rn(dx.l, __fsub_rn(xr[r].l, y.y)));
+                    dw dy = two_sum(yr[r].h, -y.z);
+                    dy = two_sum(dy.h, __fadd_rn(dy.l, __fsub_rn(yr[r].l, y.w)));
+                    const dw r2 = dw_add(dw_sqr(dx), dw_sqr(dy));
+                    dw k = dw_kpow<PWK>(r2);
+                    if constexpr (BND) {
+                        const float4 nn = sn[j * ke + g];
+                        const dw nd = dw_add(dw_mul(dw{nn.x, nn.y}, dx), dw_mul(dw{nn.z, nn.w}, dy));
+                        k = dw_mul(k, nd);
+                    }
+                    dw_mac(acc[r], c, k);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = dw_renorm(acc[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t p = pb + r * SF_THREADS + threadIdx.x;
+        if (p < npts) part[(int64_t)blockIdx.y * npts + p] = dw_to(acc[r]);
+    }
+}
+
+// The same sum in float64 for any s and for 1D: c |x-y|^{-m} (log case: c log(1/|x-y|)) on every
+// facet, plus cB n.(x-y) |x-y|^{-d-2s} on boundary facets when termB.
+__global__ void __launch_bounds__(SF_THREADS) sf_far_f64_kernel(
+    int64_t npts, int q, int d, const double* __restrict__ X, const int* __restrict__ perm, const int* __restrict__ c2f,
+    int ke, int64_t nfac, int64_t nint, int64_t fac_per_chunk, const double* __restrict__ yrec,
+    const double* __restrict__ crec, const double* __restrict__ brec, const double* __restrict__ fn, int termB, double m,
+    double pB, int logc, double* __restrict__ part) {
+    const int64_t p = (int64_t)blockIdx.x * SF_THREADS + threadIdx.x;
+    if (p >= npts) return;
+    const int nfc = d + 1;
+    const int K = perm[p / q];
+    int own[3] = {-1, -1, -1};
+    for (int j = 0; j < nfc; ++j) own[j] = c2f[(int64_t)K * nfc + j];
+    const double x0 = X[p * d], x1 = d == 2 ? X[p * d + 1] : 0.0;
+    const int64_t fb = (int64_t)blockIdx.y * fac_per_chunk;
+    const int64_t fe = min(nfac, fb + fac_per_chunk);
+    double acc = 0.0;
+    for (int64_t e = fb; e < fe; ++e) {
+        if (e == own[0] || e == own[1] || e == own[2]) continue;
+        for (int g = 0; g < ke; ++g) {
+            const int64_t i = e * ke + g;
+            const double dx = x0 - yrec[i * d], dy = d == 2 ? x1 - yrec[i * d + 1] : 0.0;
+            const double r2 = dx * dx + dy * dy;
+            acc += crec[i] * (logc ? -0.5 * log(r2) : pow(r2, -0.5 * m));
+            if (termB && e >= nint) {
+                const double* n = fn + e * (d + 1);
+                const double nd = n[0] * dx + (d == 2 ? n[1] * dy : 0.0);
+                acc += brec[(e - nint) * ke + g] * nd * pow(r2, -0.5 * pB);
+            }
+        }
+    }
+    part[(int64_t)blockIdx.y * npts + p] = acc;
+}
+
+// the facets of the point's own cell (float64, order k_near) and the sum of all parts:
+// S[K q + a] = C (near + sum over chunks of part)
+__global__ void sf_near_kernel(int64_t npts, int q, int d, const double* __restrict__ X, const double* __restrict__ lam,
+                               const int* __restrict__ perm, const int* __restrict__ cells, const double* __restrict__ V,
+                               const int* __restrict__ dov, const double* __restrict__ u,
+                               const double* __restrict__ grad, const int* __restrict__ c2f,
+                               const int* __restrict__ fac, const double* __restrict__ fn, int kn,
+                               const double* __restrict__ tn, const double* __restrict__ wn, double s, double m,
+                               double pB, int logc, int nparts, const double* __restrict__ part, double C,
+                               double* __restrict__ S) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npts) return;
+    const int64_t kint = p / q;
+    const int a = (int)(p - kint * q);
+    const int K0 = perm[kint];
+    const int nfc = d + 1;
+    const double x0 = X[p * d], x1 = d == 2 ? X[p * d + 1] : 0.0;
+    // u(x) from the cell's nodal values
+    const int* c = cells + (int64_t)K0 * nfc;
+    double ux = 0.0;
+    {
+        double l[3];
+        if (d == 1) {
+            l[0] = 1.0 - lam[a];
+            l[1] = lam[a];
+        } else {
+            l[1] = lam[2 * a];
+            l[2] = lam[2 * a + 1];
+            l[0] = 1.0 - l[1] - l[2];
+        }
+        for (int j = 0; j < nfc; ++j) {
+            const int i = dov[c[j]];
+            ux += l[j] * (i >= 0 ? u[i] : 0.0);
+        }
+    }
+    const double g0x = grad[(int64_t)K0 * d], g0y = d == 2 ? grad[(int64_t)K0 * d + 1] : 0.0;
+    const double cown = logc ? 1.0 : 1.0 / m;
+    const double cnbr = logc ? 1.0 / (2.0 * s) : 1.0 / (2.0 * s * m);
+    double near = 0.0;
+    for (int j = 0; j < nfc; ++j) {
+        const int e = c2f[(int64_t)K0 * nfc + j];
+        const int va = fac[4 * e], vb = fac[4 * e + 1], kp = fac[4 * e + 2], km = fac[4 * e + 3];
+        const double* n = fn + (int64_t)e * (d + 1);
+        const double sg = kp == K0 ? 1.0 : -1.0;
+        const int Kn = kp == K0 ? km : kp;
+        const double n0x = sg * n[0], n0y = d == 2 ? sg * n[1] : 0.0;
+        double cg = cown * (n0x * g0x + n0y * g0y);
+        if (Kn >= 0)
+            cg -= cnbr * (n0x * grad[(int64_t)Kn * d] + (d == 2 ? n0y * grad[(int64_t)Kn * d + 1] : 0.0));
+        const int ng = d == 1 ? 1 : kn;
+        for (int g = 0; g < ng; ++g) {
+            double yx, yy = 0.0, w;
+            if (d == 1) {
+                yx = V[va];
+                w = 1.0;
+            } else {
+                const double t = tn[g];
+                const double ax = V[2 * va], ay = V[2 * va + 1];
+                yx = ax + t * (V[2 * vb] - ax);
+                yy = ay + t * (V[2 * vb + 1] - ay);
+                w = wn[g] * n[d];
+            }
+            const double dx = x0 - yx, dy = x1 - yy;
+            const double r2 = dx * dx + dy * dy;
+            const double k0 = logc ? -0.5 * log(r2) : pow(r2, -0.5 * m);
+            const double k1 = pow(r2, -0.5 * pB);
+            const double nd = n0x * dx + n0y * dy;
+            const double du = Kn >= 0 ? g0x * dx + g0y * dy : ux;
+            near += w * (cg * k0 - du * nd * k1 / (2.0 * s));
+        }
+    }
+    double acc = 0.0;
+    for (int r = 0; r < nparts; ++r) acc += part[(int64_t)r * npts + p];
+    S[(int64_t)K0 * q + a] = C * (acc + near);
+}
+
+// per cell: h_K^{2s} sum_a W_a (f(x_a) - S_a)^2
+__global__ void br_cell_kernel(int64_t nc, int d, int q, const int* __restrict__ cells, const double* __restrict__ V,
+                               const double* __restrict__ jac, const double* __restrict__ lam,
+                               const double* __restrict__ w, const double* __restrict__ f, const double* __restrict__ S,
+                               double two_s, double* __restrict__ err) {
+    const int64_t K = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (K >= nc) return;
+    const int* c = cells + K * (d + 1);
+    double h;
+    if (d == 1) {
+        h = V[c[1]] - V[c[0]];
+    } else {
+        h = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            const int a = c[j], b = c[(j + 1) % 3];
+            h = fmax(h, hypot(V[2 * b] - V[2 * a], V[2 * b + 1] - V[2 * a + 1]));
+        }
+    }
+    double sum = 0.0;
+    for (int a = 0; a < q; ++a) {
+        double fx = 1.0;
+        if (f) {
+            if (d == 1) {
+                fx = (1.0 - lam[a]) * f[c[0]] + lam[a] * f[c[1]];
+            } else {
+                const double l1 = lam[2 * a], l2 = lam[2 * a + 1];
+                fx = (1.0 - l1 - l2) * f[c[0]] + l1 * f[c[1]] + l2 * f[c[2]];
+            }
+        }
+        const double r = fx - S[K * q + a];
+        sum += w[a] * jac[K] * r * r;
+    }
+    err[K] = pow(h, two_s) * sum;
+}
+
+// per DOF: eta_i = sqrt(sum over the cells around its vertex)
+__global__ void br_dof_kernel(int64_t n, const int* __restrict__ vod, const int64_t* __restrict__ v2c_ptr,
+                              const int* __restrict__ v2c, const double* __restrict__ err, double* __restrict__ eta) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int v = vod[i];
+    double acc = 0.0;
+    for (int64_t k = v2c_ptr[v]; k < v2c_ptr[v + 1]; ++k) acc += err[v2c[k]];
+    eta[i] = sqrt(acc);
+}
+
+// one block: *thr = theta max_i eta_i
+__global__ void mark_max_kernel(int64_t n, const double* __restrict__ eta, double theta, double* __restrict__ thr) {
+    __shared__ double red[32];
+    double mx = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, eta[i]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (threadIdx.x == 0) *thr = theta * mx;
+    }
+}
+
+__global__ void mark_dof_kernel(int64_t n, const double* __restrict__ eta, const double* __restrict__ thr,
+                                uint8_t* __restrict__ marks) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) marks[i] = eta[i] >= *thr ? 1 : 0;
+}
+
+__global__ void mark_cell_kernel(int64_t nc, int nvpc, const int* __restrict__ cells, const int* __restrict__ dov,
+                                 const double* __restrict__ eta, const double* __restrict__ thr,
+                                 uint8_t* __restrict__ marks) {
+    const int64_t K = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (K >= nc) return;
+    uint8_t m = 0;
+    for (int j = 0; j < nvpc; ++j) {
+        const int i = dov[cells[K * nvpc + j]];
+        if (i >= 0 && eta[i] >= *thr) m = 1;
+    }
+    marks[K] = m;
+}
+
+// ------------------------------------------------------------------ host --
+
+int dev_alloc(fl_ctx* h, void** dst, size_t bytes) {
+    *dst = nullptr;
+    cudaError_t e = pool_dev_alloc(dst, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("adaptive tables: ") + cudaGetErrorString(e));
+    h->bufs.push_back({*dst, bytes});
+    h->ws_bytes += (int64_t)bytes;
+    return FL_OK;
+}
+
+template <typename X>
+int upload(fl_ctx* h, X** dst, const std::vector<X>& src, cudaStream_t st) {
+    SF_TRY(dev_alloc(h, (void**)dst, src.size() * sizeof(X)));
+    if (!src.empty()) {
+        SF_CUDA(h, cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(X), cudaMemcpyHostToDevice, st));
+        SF_CUDA(h, cudaStreamSynchronize(st));
+    }
+    h->h2d_bytes += (int64_t)(src.size() * sizeof(X));
+    return FL_OK;
+}
+
+// Facets of the mesh for the strong form: interior facets first (the lower cell id is K+),
+// then boundary facets; cell -> facets in the cell's own order (2D edges v0v1, v1v2, v2v0;
+// 1D left, right end).
+int ensure_sf_topology(fl_ctx* h, int pi, cudaStream_t st) {
+    DevTables& t = h->dev[pi];
+    if (t.sf_ready) return FL_OK;
+    const Plan& P = h->plan[pi];
+    const int d = P.dim, nvpc = P.nvpc;
+    const int64_t nc = P.nc;
+    struct Fac {
+        int a, b, kp, km;
+        double n[2], len;
+    };
+    std::vector<Fac> F;
+    std::vector<int> c2f_local(nc * nvpc, -1);
+    if (d == 1) {
+        // facet per vertex; K+ = the cell whose right end it is (normal +1)
+        std::vector<int> right(P.nv, -1), left(P.nv, -1);
+        for (int64_t K = 0; K < nc; ++K) {
+            left[P.C[K * 2]] = (int)K;
+            right[P.C[K * 2 + 1]] = (int)K;
+        }
+        std::vector<int> fid(P.nv, -1);
+        for (int pass = 0; pass < 2; ++pass)
+            for (int64_t v = 0; v < P.nv; ++v) {
+                const bool interior = left[v] >= 0 && right[v] >= 0;
+                if (interior != (pass == 0) || (left[v] < 0 && right[v] < 0)) continue;
+                Fac f{};
+                f.a = f.b = (int)v;
+                if (right[v] >= 0) {
+                    f.kp = right[v];
+                    f.km = left[v];
+                    f.n[0] = 1.0;
+                } else {
+                    f.kp = left[v];
+                    f.km = -1;
+                    f.n[0] = -1.0;
+                }
+                f.len = 1.0;
+                fid[v] = (int)F.size();
+                F.push_back(f);
+            }
+        for (int64_t K = 0; K < nc; ++K) {
+            c2f_local[K * 2] = fid[P.C[K * 2]];
+            c2f_local[K * 2 + 1] = fid[P.C[K * 2 + 1]];
+        }
+    } else {
+        std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> edges;  // sorted key -> (cell, local edge)
+        for (int64_t K = 0; K < nc; ++K)
+            for (int j = 0; j < 3; ++j) {
+                const int a = P.C[K * 3 + j], b = P.C[K * 3 + (j + 1) % 3];
+                edges[{std::min(a, b), std::max(a, b)}].push_back({(int)K, j});
+            }
+        std::vector<std::pair<int, int>> order_int, order_bnd;  // (first cell, local edge) by cell order
+        for (auto& kv : edges) {
+            auto& L = kv.second;
+            std::sort(L.begin(), L.end());
+            if (L.size() > 2) return set_err(h, FL_EINVAL, "non-conforming mesh: an edge in more than two cells");
+        }
+        // deterministic numbering: interior facets by (K+, local edge), then boundary facets
+        for (int pass = 0; pass < 2; ++pass) {
+            std::vector<std::pair<std::pair<int, int>, std::pair<int, int>>> lst;
+            for (auto& kv : edges)
+                if ((kv.second.size() == 2) == (pass == 0)) lst.push_back({kv.second[0], kv.first});
+            std::sort(lst.begin(), lst.end());
+            for (auto& it : lst) {
+                const auto& L = edges[it.second];
+                const int K = L[0].first, j = L[0].second;
+                Fac f{};
+                f.a = P.C[(int64_t)K * 3 + j];
+                f.b = P.C[(int64_t)K * 3 + (j + 1) % 3];
+                f.kp = K;
+                f.km = L.size() == 2 ? L[1].first : -1;
+                const double ex = P.V[2 * f.b] - P.V[2 * f.a], ey = P.V[2 * f.b + 1] - P.V[2 * f.a + 1];
+                f.len = std::hypot(ex, ey);
+                // counter-clockwise cells: the outward normal is the edge vector turned clockwise
+                f.n[0] = ey / f.len;
+                f.n[1] = -ex / f.len;
+                const int id = (int)F.size();
+                F.push_back(f);
+                for (const auto& cj : L) c2f_local[(int64_t)cj.first * 3 + cj.second] = id;
+            }
+        }
+    }
+    int64_t nint = 0;
+    for (const auto& f : F) nint += f.km >= 0;
+    std::vector<int> fac(F.size() * 4);
+    std::vector<double> fn(F.size() * (d + 1));
+    for (size_t e = 0; e < F.size(); ++e) {
+        fac[4 * e] = F[e].a;
+        fac[4 * e + 1] = F[e].b;
+        fac[4 * e + 2] = F[e].kp;
+        fac[4 * e + 3] = F[e].km;
+        for (int c = 0; c < d; ++c) fn[e * (d + 1) + c] = F[e].n[c];
+        fn[e * (d + 1) + d] = F[e].len;
+    }
+    SF_CUDA(h, cudaSetDevice(h->device));
+    SF_TRY(upload(h, &t.sf_fac, fac, st));
+    SF_TRY(upload(h, &t.sf_fn, fn, st));
+    SF_TRY(upload(h, &t.sf_c2f, c2f_local, st));
+    SF_TRY(upload(h, &t.sf_perm, P.perm, st));
+    t.sf_nfac = (int64_t)F.size();
+    t.sf_nint = nint;
+    t.sf_ready = true;
+    return FL_OK;
+}
+
+// rule tables: cell rule (lam q*d, w q), edge rule (t, w: k_edge), near rule (t, w: k_near)
+int ensure_sf_rules(fl_ctx* h, int pi, int kc, int ke, int kn, cudaStream_t st) {
+    DevTables& t = h->dev[pi];
+    if (t.sf_rule && t.sf_rule_key[0] == kc && t.sf_rule_key[1] == ke && t.sf_rule_key[2] == kn) return FL_OK;
+    const Plan& P = h->plan[pi];
+    const Rule R = make_rule(P.dim, kc);
+    std::vector<double> tab(R.lam);
+    tab.insert(tab.end(), R.w.begin(), R.w.end());
+    std::vector<double> x, w;
+    gauss01(ke, x, w);
+    tab.insert(tab.end(), x.begin(), x.end());
+    tab.insert(tab.end(), w.begin(), w.end());
+    gauss01(kn, x, w);
+    tab.insert(tab.end(), x.begin(), x.end());
+    tab.insert(tab.end(), w.begin(), w.end());
+    if (tab.size() > t.sf_rule_cap) {
+        SF_TRY(dev_alloc(h, (void**)&t.sf_rule, tab.size() * sizeof(double)));
+        t.sf_rule_cap = tab.size();
+    }
+    SF_CUDA(h, cudaMemcpyAsync(t.sf_rule, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    SF_CUDA(h, cudaStreamSynchronize(st));
+    t.sf_rule_key[0] = kc;
+    t.sf_rule_key[1] = ke;
+    t.sf_rule_key[2] = kn;
+    return FL_OK;
+}
+
+int ensure_ws(fl_ctx* h, size_t bytes) {
+    if (bytes <= h->sf_ws_bytes) return FL_OK;
+    if (h->sf_ws) {
+        SF_CUDA(h, cudaDeviceSynchronize());
+        pool_dev_free(h->sf_ws);
+        h->sf_ws = nullptr;
+        h->sf_ws_bytes = 0;
+    }
+    cudaError_t e = pool_dev_alloc(&h->sf_ws, bytes);
+    if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("adaptive workspace: ") + cudaGetErrorString(e));
+    h->sf_ws_bytes = bytes;
+    return FL_OK;
+}
+
+// s in {1/4, 1/2, 3/4} as 4s, else 0
+int quarter(double s) {
+    for (int k = 1; k <= 3; ++k)
+        if (s == k / 4.0) return k;
+    return 0;
+}
+
+template <int PW0>
+void launch_far_dw(int R, dim3 grid, int64_t npts, int q, const double* X, const int* perm, const int* c2f, int ke,
+                   int64_t fb, int64_t fe, int64_t fpc, const double* yrec, const double* crec, const double* fn,
+                   double* part, cudaStream_t st) {
+    if (R == 2)
+        sf_far_dw_kernel<PW0, false, 2><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec,
+                                                                      crec, fn, part);
+    else
+        sf_far_dw_kernel<PW0, false, 1><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec,
+                                                                      crec, fn, part);
+}
+
+template <int PW>
+void launch_bnd_dw(dim3 grid, int64_t npts, int q, const double* X, const int* perm, const int* c2f, int ke,
+                   int64_t fb, int64_t fe, int64_t fpc, const double* yrec, const double* brec, const double* fn,
+                   double* part, cudaStream_t st) {
+    sf_far_dw_kernel<PW, true, 1><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec, brec, fn,
+                                                                part);
+}
+
+}  // namespace
+
+int strong_form(fl_ctx* h, double s, const double* u, int kc, int ke, int kn, double* S, cudaStream_t st) {
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    if (!u || !S) return set_err(h, FL_EINVAL, "NULL u or S");
+    if (kc < 1 || kc > SF_MAXK_CELL || ke < 1 || ke > SF_MAXK_EDGE || kn < 1 || kn > SF_MAXK_NEAR)
+        return set_err(h, FL_EINVAL, "k_cell in [1,16], k_edge in [1,32], k_near in [1,64]");
+    SF_CUDA(h, cudaSetDevice(h->device));
+    SF_TRY(ensure_device_tables(h, pi, st));
+    SF_TRY(ensure_sf_topology(h, pi, st));
+    SF_TRY(ensure_sf_rules(h, pi, kc, ke, kn, st));
+    DevTables& t = h->dev[pi];
+    const int d = P.dim;
+    const int64_t nc = P.nc, nfac = t.sf_nfac, nint = t.sf_nint, nb = nfac - nint;
+    const int q = d == 1 ? kc : kc * kc;
+    const int64_t npts = nc * q;
+    const int ke_eff = d == 1 ? 1 : ke;
+    const double m = d + 2.0 * s - 2.0, pB = d + 2.0 * s;
+    const int logc = std::fabs(m) < 1e-14;
+    const double cA_scale = logc ? 1.0 / (2.0 * s) : 1.0 / (2.0 * s * m);
+    const double cB_scale = -1.0 / (2.0 * s);
+    // boundary values of u_h are zero unless boundary vertices are degrees of freedom
+    bool termB = false;
+    for (int64_t v = 0; v < P.nv && !termB; ++v) termB = P.onb[v] && P.dov[v] >= 0;
+    const int pw0 = d == 2 ? quarter(s) : 0;
+    const bool use_dw = pw0 > 0 && !h->far_f64_pipe;
+    // chunks of facets so that the grid fills the device
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const int R = use_dw && npts >= (int64_t)sms * SF_THREADS * 8 ? 2 : 1;
+    const int64_t bx = (npts + (int64_t)SF_THREADS * R - 1) / ((int64_t)SF_THREADS * R);
+    const int64_t want = (int64_t)sms * 8;
+    int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(64, (want + bx - 1) / bx));
+    chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, nfac / 16));
+    const int64_t fpc = (nfac + chunks - 1) / chunks;
+    int64_t bchunks = 0, bfpc = 1;
+    if (use_dw && termB && nb > 0) {
+        bchunks = std::max<int64_t>(1, std::min<int64_t>(16, std::min<int64_t>((want + bx - 1) / bx, nb)));
+        bfpc = (nb + bchunks - 1) / bchunks;
+    }
+    const int64_t nparts = chunks + bchunks;
+    // workspace: grad, X, yrec, crec, brec, part
+    const size_t n_grad = nc * d, n_X = npts * d, n_y = nfac * ke_eff * d, n_c = nfac * ke_eff,
+                 n_b = std::max<int64_t>(nb, 1) * ke_eff, n_part = nparts * npts;
+    const size_t total = (n_grad + n_X + n_y + n_c + n_b + n_part + 8 * 6) * sizeof(double);
+    SF_TRY(ensure_ws(h, total));
+    double* base = (double*)h->sf_ws;
+    auto take = [&](size_t n) {
+        double* p = base;
+        base += (n + 7) / 8 * 8;
+        return p;
+    };
+    double* grad = take(n_grad);
+    double* X = take(n_X);
+    double* yrec = take(n_y);
+    double* crec = take(n_c);
+    double* brec = take(n_b);
+    double* part = take(n_part);
+    const double* lam = t.sf_rule;
+    const Rule Rc = make_rule(d, kc);  // sizes only
+    const double* wc = t.sf_rule + Rc.lam.size();
+    const double* te = wc + Rc.w.size();
+    const double* we = te + ke;
+    const double* tn = we + ke;
+    const double* wn = tn + kn;
+    (void)wc;
+    if (nc > 0) {
+        sf_prep_kernel<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(nc, d, q, t.sf_perm, t.cells, t.V, t.dov, u, lam,
+                                                                     grad, X);
+        count_launch();
+        const int64_t nrec = nfac * ke_eff;
+        sf_facet_kernel<<<(unsigned)((nrec + 127) / 128), 128, 0, st>>>(nfac, nint, d, ke_eff, t.sf_fac, t.sf_fn, t.V,
+                                                                        t.dov, u, grad, te, we, cA_scale, cB_scale,
+                                                                        termB ? 1 : 0, yrec, crec, brec);
+        count_launch();
+        if (use_dw) {
+            const dim3 grid((unsigned)bx, (unsigned)chunks);
+            switch (pw0) {
+                case 1: launch_far_dw<1>(R, grid, npts, q, X, t.sf_perm, t.sf_c2f, ke, 0, nfac, fpc, yrec, crec, t.sf_fn, part, st); break;
+                case 2: launch_far_dw<2>(R, grid, npts, q, X, t.sf_perm, t.sf_c2f, ke, 0, nfac, fpc, yrec, crec, t.sf_fn, part, st); break;
+                default: launch_far_dw<3>(R, grid, npts, q, X, t.sf_perm, t.sf_c2f, ke, 0, nfac, fpc, yrec, crec, t.sf_fn, part, st); break;
+            }
+            count_launch();
+            if (bchunks > 0) {
+                const int64_t bx1 = (npts + SF_THREADS - 1) / SF_THREADS;
+                const dim3 g2((unsigned)bx1, (unsigned)bchunks);
+                double* bpart = part + chunks * npts;
+                switch (pw0) {
+                    case 1: launch_bnd_dw<5>(g2, npts, q, X, t.sf_perm, t.sf_c2f, ke, nint, nfac, bfpc, yrec, brec, t.sf_fn, bpart, st); break;
+                    case 2: launch_bnd_dw<6>(g2, npts, q, X, t.sf_perm, t.sf_c2f, ke, nint, nfac, bfpc, yrec, brec, t.sf_fn, bpart, st); break;
+                    default: launch_bnd_dw<7>(g2, npts, q, X, t.sf_perm, t.sf_c2f, ke, nint, nfac, bfpc, yrec, brec, t.sf_fn, bpart, st); break;
+                }
+                count_launch();
+            }
+        } else {
+            const dim3 grid((unsigned)((npts + SF_THREADS - 1) / SF_THREADS), (unsigned)chunks);
+            sf_far_f64_kernel<<<grid, SF_THREADS, 0, st>>>(npts, q, d, X, t.sf_perm, t.sf_c2f, ke_eff, nfac, nint, fpc,
+                                                           yrec, crec, brec, t.sf_fn, termB ? 1 : 0, m, pB, logc, part);
+            count_launch();
+        }
+        sf_near_kernel<<<(unsigned)((npts + 127) / 128), 128, 0, st>>>(
+            npts, q, d, X, lam, t.sf_perm, t.cells, t.V, t.dov, u, grad, t.sf_c2f, t.sf_fac, t.sf_fn, kn, tn, wn, s, m,
+            pB, logc, (int)nparts, part, frac_const(d, s), S);
+        count_launch();
+    }
+    SF_CUDA(h, cudaGetLastError());
+    return FL_OK;
+}
+
+int br_indicators(fl_ctx* h, double s, const double* u, const double* f, int kc, int ke, int kn, double* eta,
+                  double* S_out, cudaStream_t st) {
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    if (!eta) return set_err(h, FL_EINVAL, "NULL eta");
+    if (kc < 1 || kc > SF_MAXK_CELL) return set_err(h, FL_EINVAL, "k_cell in [1,16]");
+    const int d = P.dim;
+    const int q = d == 1 ? kc : kc * kc;
+    const int64_t nc = P.nc;
+    // S (caller's or scratch) and the per-cell errors live after the strong-form workspace
+    double* S = S_out;
+    double* err = nullptr;
+    void* scratch = nullptr;
+    const size_t extra = ((S_out ? 0 : nc * q) + nc) * sizeof(double);
+    cudaError_t e = pool_dev_alloc(&scratch, std::max<size_t>(extra, 16));
+    if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("indicator scratch: ") + cudaGetErrorString(e));
+    if (!S) S = (double*)scratch;
+    err = (double*)scratch + (S_out ? 0 : nc * q);
+    int r = strong_form(h, s, u, kc, ke, kn, S, st);
+    if (r == FL_OK) {
+        DevTables& t = h->dev[pi];
+        const Rule Rc = make_rule(d, kc);
+        const double* lam = t.sf_rule;
+        const double* wc = t.sf_rule + Rc.lam.size();
+        br_cell_kernel<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(nc, d, q, t.cells, t.V, t.jac_orig, lam, wc, f, S,
+                                                                     2.0 * s, err);
+        count_launch();
+        if (P.n > 0) {
+            br_dof_kernel<<<(unsigned)((P.n + 127) / 128), 128, 0, st>>>(P.n, t.vod, t.v2c_ptr, t.v2c, err, eta);
+            count_launch();
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) r = set_err(h, FL_ECUDA, std::string("indicator kernels: ") + cudaGetErrorString(e));
+    }
+    // the scratch block goes back to the pool once the stream has used it
+    cudaError_t es = cudaStreamSynchronize(st);
+    pool_dev_free(scratch);
+    if (r == FL_OK && es != cudaSuccess) r = set_err(h, FL_ECUDA, std::string("indicators: ") + cudaGetErrorString(es));
+    return r;
+}
+
+int mark_max(fl_ctx* h, double s, const double* eta, double theta, uint8_t* dof_marks, uint8_t* cell_marks,
+             cudaStream_t st) {
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    if (!eta || (!dof_marks && !cell_marks)) return set_err(h, FL_EINVAL, "NULL eta, or no output");
+    if (!(theta > 0.0 && theta <= 1.0)) return set_err(h, FL_EINVAL, "theta must lie in (0, 1]");
+    SF_CUDA(h, cudaSetDevice(h->device));
+    SF_TRY(ensure_device_tables(h, pi, st));
+    SF_TRY(ensure_ws(h, std::max<size_t>(h->sf_ws_bytes, 64)));
+    DevTables& t = h->dev[pi];
+    double* thr = (double*)h->sf_ws;
+    mark_max_kernel<<<1, 1024, 0, st>>>(P.n, eta, theta, thr);
+    count_launch();
+    if (dof_marks && P.n > 0) {
+        mark_dof_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, st>>>(P.n, eta, thr, dof_marks);
+        count_launch();
+    }
+    if (cell_marks) {
+        mark_cell_kernel<<<(unsigned)((P.nc + 255) / 256), 256, 0, st>>>(P.nc, P.nvpc, t.cells, t.dov, eta, thr,
+                                                                        cell_marks);
+        count_launch();
+    }
+    SF_CUDA(h, cudaGetLastError());
+    return FL_OK;
+}
+
+}  // namespace fl

@@ -119,7 +119,7 @@ int fl_create(fl_handle* out, int dim, int64_t n_vertices, const double* vertice
 
 void fl_destroy(fl_handle h) {
     if (!h) return;
-    if (!h->bufs.empty() || h->solve_ws || h->batch_ws || h->batch_host) {
+    if (!h->bufs.empty() || h->solve_ws || h->batch_ws || h->batch_host || h->sf_ws) {
         cudaSetDevice(h->device);
         cudaDeviceSynchronize();
         for (auto& b : h->bufs) fl::pool_dev_free(b.p);  // back to the cache (the device is idle)
@@ -129,6 +129,7 @@ void fl_destroy(fl_handle h) {
         if (h->solve_host) fl::pool_host_free(h->solve_host);
         if (h->batch_ws) fl::pool_dev_free(h->batch_ws);
         if (h->batch_host) fl::pool_host_free(h->batch_host);
+        if (h->sf_ws) fl::pool_dev_free(h->sf_ws);
     }
     for (auto& g : h->cg_graphs) cudaGraphExecDestroy(g.exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -221,6 +222,52 @@ int fl_mass_apply(fl_handle h, double s, int nrhs, double alpha, const double* X
     } catch (const std::bad_alloc&) {
         return fl::set_err(h, FL_ENOMEM, "out of host memory");
     }
+}
+
+int fl_strong_form(fl_handle h, double s, const double* u_dev, int k_cell, int k_edge, int k_near, double* S_dev,
+                   void* stream) {
+    if (!h) return FL_EINVAL;
+    h->err.clear();
+    try {
+        return fl::strong_form(h, s, u_dev, k_cell, k_edge, k_near, S_dev, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        return fl::set_err(h, FL_ENOMEM, "out of host memory");
+    }
+}
+
+int fl_br_indicators(fl_handle h, double s, const double* u_dev, const double* f_nodal_dev, int k_cell, int k_edge,
+                     int k_near, double* eta_dev, double* S_dev, void* stream) {
+    if (!h) return FL_EINVAL;
+    h->err.clear();
+    try {
+        return fl::br_indicators(h, s, u_dev, f_nodal_dev, k_cell, k_edge, k_near, eta_dev, S_dev,
+                                 (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        return fl::set_err(h, FL_ENOMEM, "out of host memory");
+    }
+}
+
+int fl_mark_max(fl_handle h, double s, const double* eta_dev, double theta, uint8_t* dof_marks_dev,
+                uint8_t* cell_marks_dev, void* stream) {
+    if (!h) return FL_EINVAL;
+    h->err.clear();
+    return fl::mark_max(h, s, eta_dev, theta, dof_marks_dev, cell_marks_dev, (cudaStream_t)stream);
+}
+
+int fl_refine(int dim, int64_t n_vertices, const double* vertices, int64_t n_cells, const int32_t* cells,
+              const uint8_t* cell_marks, int64_t cap_vertices, int64_t cap_cells, double* vertices_out,
+              int32_t* cells_out, int64_t* n_vertices_out, int64_t* n_cells_out) {
+    std::string err;
+    int r;
+    try {
+        r = fl::refine_mesh(dim, n_vertices, vertices, n_cells, cells, cell_marks, cap_vertices, cap_cells,
+                            vertices_out, cells_out, n_vertices_out, n_cells_out, err);
+    } catch (const std::bad_alloc&) {
+        r = FL_ENOMEM;
+        err = "out of host memory in fl_refine";
+    }
+    if (r != FL_OK) g_create_err = err;
+    return r;
 }
 
 int fl_load_vector(fl_handle h, double s, const double* f_nodal_dev, int nrhs, double* b_dev, int64_t ldb,

@@ -107,6 +107,16 @@ struct DevTables {
     bool rule32_ready = false;   // the float32 copy matches them
     std::vector<double> rule_host;
     RuleOffsets rule_ro{};
+    // strong form of the adaptive loop (adaptive.cu), built on first use
+    bool sf_ready = false;
+    int64_t sf_nfac = 0, sf_nint = 0;  // facets; the first sf_nint are interior
+    int* sf_fac = nullptr;     // nfac*4: vertices a, b (1D: a twice), cell K+, cell K- (-1 on the boundary)
+    double* sf_fn = nullptr;   // nfac*(dim+1): unit normal outward of K+, length (1D: 1)
+    int* sf_c2f = nullptr;     // nc*nvpc: facets of every cell (original order)
+    int* sf_perm = nullptr;    // nc: internal -> original cell
+    double* sf_rule = nullptr; // cell rule, edge rule, near-edge rule of the last call
+    size_t sf_rule_cap = 0;
+    int sf_rule_key[3] = {0, 0, 0};
 };
 
 }  // namespace fl
@@ -143,6 +153,8 @@ struct fl_ctx {
     void* batch_ws = nullptr;     // batched-solver workspace (device), grown on demand
     size_t batch_ws_bytes = 0;
     void* batch_host = nullptr;   // pinned scalars of the batched solver
+    void* sf_ws = nullptr;        // strong-form workspace (device), grown on demand
+    size_t sf_ws_bytes = 0;
 };
 
 namespace fl {
@@ -183,4 +195,13 @@ int bnd_dw_chunks(int64_t nc);
 int launch_bnd_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro, int pw,
                   cudaStream_t st);
 void far_dw_record(const Plan& P, int pw, int variant, double ms);
+// adaptive loop (adaptive.cu, refine.cpp)
+int strong_form(fl_ctx* h, double s, const double* u, int k_cell, int k_edge, int k_near, double* S, cudaStream_t st);
+int br_indicators(fl_ctx* h, double s, const double* u, const double* f, int k_cell, int k_edge, int k_near,
+                  double* eta, double* S, cudaStream_t st);
+int mark_max(fl_ctx* h, double s, const double* eta, double theta, uint8_t* dof_marks, uint8_t* cell_marks,
+             cudaStream_t st);
+int refine_mesh(int dim, int64_t nv, const double* V, int64_t nc, const int32_t* C, const uint8_t* marks,
+                int64_t cap_v, int64_t cap_c, double* V_out, int32_t* C_out, int64_t* nv_out, int64_t* nc_out,
+                std::string& err);
 }  // namespace fl

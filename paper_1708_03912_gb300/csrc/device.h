@@ -177,24 +177,33 @@ __device__ __forceinline__ void dw_mac_pos(dw& s, dw c, dw k) {
     s.l = __fadd_rn(s.l, __fadd_rn(t.l, e));
 }
 
-// r2^e, e = -PW/4, for PW in {5, 6, 7} (2D kernels of order s = 1/4, 1/2, 3/4).  From the
-// float32 estimate y0 of r2^{-1/2} (PW 6) or r2^{-1/4} (PW 5, 7), about 2^-21 relative:
-// k0 = y0^m in double-word terms (m = 3, 5, 7; built from the exact square of y0), then
-// rho = 1 - r2 y0^2 (or 1 - r2 y0^4) from the same products, and
+// r2^e, e = -PW/4, for PW in {5, 6, 7} (2D kernels |x-y|^{-2-2s} of order s = 1/4, 1/2, 3/4)
+// and PW in {1, 2, 3} (|x-y|^{-2s}, the strong form's single-layer kernel).  From the
+// float32 estimate y0 of r2^{-1/2} (PW 2, 6) or r2^{-1/4} (PW 1, 3, 5, 7), about 2^-21
+// relative: k0 = y0^m in double-word terms (m = 1, 3, 5, 7; built from the exact square of
+// y0), then rho = 1 - r2 y0^2 (or 1 - r2 y0^4) from the same products, and
 // k = k0 (1 - rho)^{-m/2 or -m/4} by the expansion to second order in rho (third-order
 // terms are below 2^-56).  The float32 correction term is rounded once: about 2^-42 relative
 // in the worst case, typically well below.
 template <int PW>
 __device__ __forceinline__ dw dw_kpow(dw x) {
-    static_assert(PW == 5 || PW == 6 || PW == 7, "double-word powers: PW 5, 6, 7");
-    if constexpr (PW == 6) {
+    static_assert(PW == 1 || PW == 2 || PW == 3 || PW == 5 || PW == 6 || PW == 7,
+                  "double-word powers: PW 1, 2, 3, 5, 6, 7");
+    if constexpr (PW == 2 || PW == 6) {
         const float t0 = rsqrt_approx(x.h);
         const dw t2 = two_prod(t0, t0);
         const dw g = dw_mul(x, t2);  // x t0^2 ~ 1
         const float rho = __fsub_rn(__fsub_rn(1.f, g.h), g.l);
-        dw k = two_prod(t2.h, t0);  // t0^3
-        k.l = __fmaf_rn(t2.l, t0, k.l);
-        const float c = __fmul_rn(rho, __fmaf_rn(1.875f, rho, 1.5f));  // (1-rho)^{-3/2} - 1
+        dw k;
+        float c;
+        if constexpr (PW == 2) {
+            k = {t0, 0.f};
+            c = __fmul_rn(rho, __fmaf_rn(0.375f, rho, 0.5f));  // (1-rho)^{-1/2} - 1
+        } else {
+            k = two_prod(t2.h, t0);  // t0^3
+            k.l = __fmaf_rn(t2.l, t0, k.l);
+            c = __fmul_rn(rho, __fmaf_rn(1.875f, rho, 1.5f));  // (1-rho)^{-3/2} - 1
+        }
         k.l = __fmaf_rn(k.h, c, k.l);
         return k;
     } else {
@@ -205,7 +214,14 @@ __device__ __forceinline__ dw dw_kpow(dw x) {
         const float rho = __fsub_rn(__fsub_rn(1.f, g.h), g.l);
         dw k;
         float c;
-        if constexpr (PW == 5) {
+        if constexpr (PW == 1) {
+            k = {v0, 0.f};
+            c = __fmul_rn(rho, __fmaf_rn(0.15625f, rho, 0.25f));  // (1-rho)^{-1/4} - 1
+        } else if constexpr (PW == 3) {
+            k = two_prod(v2.h, v0);  // v0^3
+            k.l = __fmaf_rn(v2.l, v0, k.l);
+            c = __fmul_rn(rho, __fmaf_rn(0.65625f, rho, 0.75f));  // (1-rho)^{-3/4} - 1
+        } else if constexpr (PW == 5) {
             k = two_prod(v4.h, v0);  // v0^5
             k.l = __fmaf_rn(v4.l, v0, k.l);
             c = __fmul_rn(rho, __fmaf_rn(1.40625f, rho, 1.25f));  // (1-rho)^{-5/4} - 1

@@ -24,7 +24,8 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
 
 EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
            "fl_assemble", "fl_tune_assemble", "fl_set_far_variant", "fl_assemble_nearfield_csr", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
-           "fl_heat_matrix", "fl_mass_apply", "fl_cluster_plan", "fl_hmatrix_create", "fl_hmatrix_set_near",
+           "fl_heat_matrix", "fl_mass_apply", "fl_strong_form", "fl_br_indicators", "fl_mark_max", "fl_refine",
+           "fl_cluster_plan", "fl_hmatrix_create", "fl_hmatrix_set_near",
            "fl_hmatrix_matvec", "fl_hmatrix_info", "fl_hmatrix_last_error", "fl_hmatrix_destroy", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
            "fl_matvec_f32_static",
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
@@ -134,6 +135,15 @@ def lib():
     L.fl_heat_matrix.restype = ci
     L.fl_mass_apply.argtypes = [vp, dbl, ci, dbl, vp, i64, dbl, vp, i64, vp, i64, vp]
     L.fl_mass_apply.restype = ci
+    L.fl_strong_form.argtypes = [vp, dbl, vp, ci, ci, ci, vp, vp]
+    L.fl_strong_form.restype = ci
+    L.fl_br_indicators.argtypes = [vp, dbl, vp, vp, ci, ci, ci, vp, vp, vp]
+    L.fl_br_indicators.restype = ci
+    L.fl_mark_max.argtypes = [vp, dbl, vp, dbl, vp, vp, vp]
+    L.fl_mark_max.restype = ci
+    L.fl_refine.argtypes = [ci, i64, vp, i64, vp, vp, i64, i64, vp, vp, ctypes.POINTER(ctypes.c_int64),
+                            ctypes.POINTER(ctypes.c_int64)]
+    L.fl_refine.restype = ci
     L.fl_cluster_plan.argtypes = [vp, dbl, dbl, ci, ctypes.POINTER(i64), vp, vp, vp, vp]
     L.fl_cluster_plan.restype = ci
     L.fl_hmatrix_create.argtypes = [vp, dbl, ci, dbl, ci, ctypes.POINTER(vp), vp]
@@ -382,6 +392,47 @@ def fl_mass_apply(h, s, alpha, X, beta, B, Y, stream=None):
     ld = lambda T: (T.stride(0) if T.dim() == 2 else 1) if T is not None else 1  # noqa: E731
     _check(lib().fl_mass_apply(h, s, nrhs, alpha, _ptr(X), ld(X), beta, _ptr(B) if B is not None else None, ld(B),
                                _ptr(Y), ld(Y), _stream(stream)), h)
+
+
+def _rule_points(k_cell, dim):
+    return k_cell if dim == 1 else k_cell * k_cell
+
+
+def fl_strong_form(h, s, u, k_cell, k_edge, k_near, S, stream=None):
+    """S [n_cells, q] = (-Delta)^s u_h at the cell-rule points (u: n float64 DOF values)."""
+    _check(lib().fl_strong_form(h, s, _ptr(u), k_cell, k_edge, k_near, _ptr(S), _stream(stream)), h)
+
+
+def fl_br_indicators(h, s, u, f_nodal, k_cell, k_edge, k_near, eta, S=None, stream=None):
+    """eta [n] = BR indicators; f_nodal None (f = 1) or [n_vertices]; S optional [n_cells, q]."""
+    _check(lib().fl_br_indicators(h, s, _ptr(u), _ptr(f_nodal) if f_nodal is not None else None, k_cell, k_edge,
+                                  k_near, _ptr(eta), _ptr(S) if S is not None else None, _stream(stream)), h)
+
+
+def fl_mark_max(h, s, eta, theta, dof_marks=None, cell_marks=None, stream=None):
+    """Maximum marking into uint8 tensors dof_marks [n] and/or cell_marks [n_cells]."""
+    _check(lib().fl_mark_max(h, s, _ptr(eta), theta, _ptr(dof_marks) if dof_marks is not None else None,
+                             _ptr(cell_marks) if cell_marks is not None else None, _stream(stream)), h)
+
+
+def fl_refine(vertices, cells, cell_marks):
+    """Conforming refinement of the marked cells (host arrays): returns (vertices, cells)."""
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    C = np.ascontiguousarray(cells, dtype=np.int32)
+    M = np.ascontiguousarray(cell_marks, dtype=np.uint8)
+    if M.shape != (C.shape[0],):
+        raise ValueError("one mark per cell")
+    dim = V.shape[1]
+    cap_v, cap_c = V.shape[0] + 3 * C.shape[0], 4 * C.shape[0]
+    Vo = np.empty((cap_v, dim), dtype=np.float64)
+    Co = np.empty((cap_c, dim + 1), dtype=np.int32)
+    nv, nc = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().fl_refine(dim, V.shape[0], V.ctypes.data, C.shape[0], C.ctypes.data, M.ctypes.data, cap_v, cap_c,
+                           Vo.ctypes.data, Co.ctypes.data, ctypes.byref(nv), ctypes.byref(nc)), None)
+    Vo = Vo[:nv.value].copy()
+    return (Vo[:, 0] if np.asarray(vertices).ndim == 1 else Vo), Co[:nc.value].copy()
 
 
 def fl_cluster_plan(h, s, eta=1.0, leaf=32):
@@ -869,6 +920,37 @@ class Mesh:
         info = fl_solve(self.h, A, b, u, o, stream)
         return u, info
 
+    def strong_form(self, s, u, k_cell=3, k_edge=4, k_near=16, stream=None):
+        """(-Delta)^s u_h at the cell-rule points: float64 tensor [n_cells, q] (Lemma 4.1)."""
+        import torch
+
+        nc = fl_get_stats(self.h, s)["n_cells"]
+        S = torch.empty((nc, _rule_points(k_cell, self.dim)), dtype=torch.float64, device=u.device)
+        fl_strong_form(self.h, s, u, k_cell, k_edge, k_near, S, stream)
+        return S
+
+    def br_indicators(self, s, u, f_nodal=None, k_cell=3, k_edge=4, k_near=16, return_S=False, stream=None):
+        """Babuska-Rheinboldt indicators eta [n] (and the strong form with return_S)."""
+        import torch
+
+        eta = torch.empty(self.num_dofs(s), dtype=torch.float64, device=u.device)
+        S = None
+        if return_S:
+            nc = fl_get_stats(self.h, s)["n_cells"]
+            S = torch.empty((nc, _rule_points(k_cell, self.dim)), dtype=torch.float64, device=u.device)
+        fl_br_indicators(self.h, s, u, f_nodal, k_cell, k_edge, k_near, eta, S, stream)
+        return (eta, S) if return_S else eta
+
+    def mark_max(self, s, eta, theta=0.8, stream=None):
+        """Maximum marking: (dof_marks [n], cell_marks [n_cells]) as uint8 tensors."""
+        import torch
+
+        nc = fl_get_stats(self.h, s)["n_cells"]
+        dm = torch.empty(eta.shape[0], dtype=torch.uint8, device=eta.device)
+        cm = torch.empty(nc, dtype=torch.uint8, device=eta.device)
+        fl_mark_max(self.h, s, eta, theta, dm, cm, stream)
+        return dm, cm
+
     def heat_steps(self, A, s, dt, u0, F, steps, tol=1e-10, stream=None):
         """Implicit Euler for the fractional heat equation (Sections 2 and 5): from u0, `steps`
         solves of (M + dt A) u^{k+1} = M u^k + dt F by Jacobi-PCG.  Returns (u, [fl_solve_info])."""
@@ -885,3 +967,53 @@ class Mesh:
             fl_mass_apply(self.h, s, 1.0, u, dt, F, rhs, stream)
             infos.append(fl_solve(self.h, H, rhs, u, o, stream))
         return u, infos
+
+
+def adaptive_loop(vertices, cells, s, steps, theta=0.8, f_nodal=None, tol=1e-10, k_cell=3, k_edge=4, k_near=16,
+                  max_dofs=None, dof_mode="interior", timings=False):
+    """The adaptive loop of Section 7.  Per step: assemble A^s (float64) and b, solve A u = b
+    (Jacobi-PCG), compute the BR indicators, mark with the maximum strategy (threshold theta) and
+    refine the marked patches (newest-vertex bisection with closure).  f_nodal: None (f = 1) or
+    a function of the vertex coordinates [nv, d] returning nodal values.  Stops after `steps`
+    solves or once n exceeds max_dofs.  Returns one dict per step (host arrays: vertices,
+    cells, u, eta, dof_marks, cell_marks; n, iterations; with timings, the milliseconds of
+    assembly, solve and indicators by CUDA events)."""
+    import torch
+
+    V = np.asarray(vertices, dtype=np.float64)
+    C = np.asarray(cells, dtype=np.int32)
+    out = []
+    for _ in range(steps):
+        mesh = Mesh(V, C, dof_mode=dof_mode)
+        try:
+            n = mesh.num_dofs(s)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if timings else None
+            fv = None
+            if f_nodal is not None:
+                fv = torch.as_tensor(np.ascontiguousarray(f_nodal(V), dtype=np.float64), device="cuda")
+            if ev:
+                ev[0].record()
+            A = mesh.assemble(s)
+            b = mesh.load_vector(s, fv)
+            if ev:
+                ev[1].record()
+            u, info = mesh.solve(A, b, tol=tol)
+            if ev:
+                ev[2].record()
+            eta = mesh.br_indicators(s, u, fv, k_cell, k_edge, k_near)
+            if ev:
+                ev[3].record()
+            dm, cm = mesh.mark_max(s, eta, theta)
+            torch.cuda.synchronize()
+            rec = {"vertices": V, "cells": C, "n": n, "u": u.cpu().numpy(), "eta": eta.cpu().numpy(),
+                   "dof_marks": dm.cpu().numpy(), "cell_marks": cm.cpu().numpy(), "iterations": info.iterations}
+            if ev:
+                rec["ms"] = {"assemble": ev[0].elapsed_time(ev[1]), "solve": ev[1].elapsed_time(ev[2]),
+                             "indicators": ev[2].elapsed_time(ev[3])}
+            out.append(rec)
+        finally:
+            mesh.close()
+        if max_dofs is not None and n >= max_dofs:
+            break
+        V, C = fl_refine(V, C, rec["cell_marks"])
+    return out
