@@ -506,6 +506,58 @@ def heat_section(F, synth, timed):
     return out
 
 
+# float32-pipe operations of one evaluation in the strong form's double-word facet sum
+# (sf_far_dw_kernel, by s = PW0/4): two renormalised differences (11 each), two squares (4
+# each), their sum (11), the power (11 / 15 / 18 for PW0 2 / 1 / 3, plus one or two MUFU
+# operations not counted) and the multiply-accumulate (12)
+SF_DW_OPS_PER_EVAL = {1: 68, 2: 64, 3: 71}
+
+
+def adaptive_section(F, synth, timed, peaks, sms, m, A, b, n_el):
+    """Adaptive loop (Sections 4 and 7): the strong form and BR indicators on the headline
+    L-shape (73432 cells, s = 1/2, orders k_cell = 3, k_edge = 4, k_near = 16), with the
+    rate and the FP32-pipe roofline of the facet sum; then the whole loop (assemble, solve,
+    estimate, mark with theta = 0.8, refine) from the 96-cell L-shape up to about 4000 DOFs."""
+    import numpy as np
+    import torch
+
+    s, kc, ke, kn = LSHAPE_S, 3, 4, 16
+    u, _ = m.solve(A, b, tol=1e-8)
+    nc = n_el
+    S = torch.empty((nc, kc * kc), dtype=torch.float64, device="cuda")
+    eta = torch.empty(u.shape[0], dtype=torch.float64, device="cuda")
+    F.fl_strong_form(m.h, s, u, kc, ke, kn, S)
+    sf_ms = timed(lambda: F.fl_strong_form(m.h, s, u, kc, ke, kn, S), reps=3, flush_between=False)
+    ind_ms = timed(lambda: F.fl_br_indicators(m.h, s, u, None, kc, ke, kn, eta), reps=2, flush_between=False)
+    stats = F.fl_get_stats(m.h, s)
+    n_edges = stats["n_vertices"] + stats["n_cells"] - 1  # Euler: V - E + F = 1 on a simply connected domain
+    evals = nc * kc * kc * (n_edges - 3) * ke
+    ops = evals * SF_DW_OPS_PER_EVAL[int(round(4 * s))]
+    clock_hz = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    peak_ops = sms * 128 * clock_hz
+    out = {"workload": f"L-shape level {LSHAPE_LEVEL}, {nc} cells, {n_edges} edges, s = {s}, u = the solution, "
+                       f"k_cell = {kc} ({kc * kc} points per cell), k_edge = {ke}, k_near = {kn}",
+           "strong_form_ms": sf_ms, "indicators_ms": ind_ms, "point_edge_evaluations": evals,
+           "evaluations_per_s": evals / (sf_ms / 1000),
+           "roofline_whole_call": {"bound": "alu", "kernel": f"sf_far_dw_kernel<{int(round(4 * s))},false,2,4> and the "
+                                   "small prep/facet/near kernels of the call", "achieved": ops / (sf_ms / 1000) / 1e12,
+                                   "peak": peak_ops / 1e12, "unit": "T FP32-ops/s",
+                                   "frac": ops / (sf_ms / 1000) / peak_ops,
+                                   "peak_from": "SMs x 128 FP32 lanes x max SM clock (measured clock)"}}
+    # the loop
+    V0, T0 = synth.lshape(0.25, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = F.adaptive_loop(V0, T0, s, steps=30, theta=0.8, max_dofs=4000, timings=True)
+    wall = (time.perf_counter() - t0) * 1000
+    out["loop"] = {"workload": "L-shape from 96 cells, f = 1, s = 1/2, theta = 0.8, solve to 1e-10",
+                   "steps": len(steps), "n": [st["n"] for st in steps],
+                   "estimator": [float(np.sqrt(np.sum(st["eta"] ** 2))) for st in steps],
+                   "wall_ms": wall, "last_step_ms": steps[-1]["ms"],
+                   "gpu_ms_total": {k: sum(st["ms"][k] for st in steps) for k in ("assemble", "solve", "indicators")}}
+    return out
+
+
 def lshape_precond_section(F, synth, timed, A, b, h5):
     """Preconditioners on the headline system (L-shape level 5, s = 1/2, f = 1, tol 1e-8):
     Jacobi-PCG, multigrid-preconditioned CG on the nested levels 5..2, flexible CG with the
@@ -722,6 +774,7 @@ def main():
         torch.cuda.empty_cache()
         line["lshape"]["preconditioners"] = lshape_precond_section(F, synth, timed, A, b, m.h)
         line["lshape"]["hmatrix"] = hmatrix_section(F, timed, A, m.h)
+        line["lshape"]["adaptive"] = adaptive_section(F, synth, timed, peaks, sms, m, A, b, n_el)
         line["heat"] = heat_section(F, synth, timed)
         line["matvec"] = matvec_section(F, timed, peaks, A, A32)
         line["interval"] = interval_section(F, synth, timed)

@@ -141,11 +141,36 @@ __global__ void sf_facet_kernel(int64_t nfac, int64_t nint, int d, int ke, const
     }
 }
 
+// One term of the double-word facet sum: acc += c |x-y|^{-PWK/2} (BND: c n.(x-y) |x-y|^{-PWK/2}),
+// x = (xh + xl, yh + yl) and the facet point y relative to the same origin.
+template <int PWK, bool BND>
+__device__ __forceinline__ void sf_term(dw& acc, dw xr, dw yr, float4 y, dw c, float4 nn) {
+    // x - y.  TwoSum of the high parts, then the low parts' difference added and the pair
+    // renormalised by Fast2Sum: the low parts can make up as much as the high parts' difference
+    // when the points are close, and dropping that would cost the square its accuracy.  Fast2Sum
+    // is exact here: either the high parts are within a factor 2 (their difference is exact, a
+    // nonzero multiple of the smaller one's ulp, which the low parts' difference does not
+    // exceed in exponent), or the difference dwarfs the low parts, or it is zero.
+    dw dx = two_sum(xr.h, -y.x);
+    dx = fast_two_sum(dx.h, __fadd_rn(dx.l, __fsub_rn(xr.l, y.y)));
+    dw dy = two_sum(yr.h, -y.z);
+    dy = fast_two_sum(dy.h, __fadd_rn(dy.l, __fsub_rn(yr.l, y.w)));
+    const dw r2 = dw_add(dw_sqr(dx), dw_sqr(dy));
+    dw k = dw_kpow<PWK>(r2);
+    if constexpr (BND) {
+        const dw nd = dw_add(dw_mul(dw{nn.x, nn.y}, dx), dw_mul(dw{nn.z, nn.w}, dy));
+        k = dw_mul(k, nd);
+    }
+    dw_mac(acc, c, k);
+}
+
 // Sum over the facet points of facets [f_begin, f_end) not on the boundary of the point's own
 // cell, 2D, double-word.  BND = false: c |x-y|^{-2s} with PWK = 4s; BND = true (boundary facets,
 // term with u(y)): c n.(x-y) |x-y|^{-2-2s} with PWK = 4 + 4s.  Each thread takes R points of
-// the block's range (stride SF_THREADS); blockIdx.y picks the facet chunk.
-template <int PWK, bool BND, int R>
+// the block's range (stride SF_THREADS); blockIdx.y picks the facet chunk.  KE > 0 fixes the
+// Gauss order on the facets at compile time (ke must equal it), 0 takes ke.  A facet that no
+// lane of the warp owns (nearly all of them) runs without per-point tests.
+template <int PWK, bool BND, int R, int KE>
 __global__ void __launch_bounds__(SF_THREADS) sf_far_dw_kernel(
     int64_t npts, int q, const double* __restrict__ X, const int* __restrict__ perm, const int* __restrict__ c2f,
     int ke, int64_t f_begin, int64_t f_end, int64_t fac_per_chunk, const double* __restrict__ yrec,
@@ -153,6 +178,7 @@ __global__ void __launch_bounds__(SF_THREADS) sf_far_dw_kernel(
     __shared__ float4 sy[SF_TREC];
     __shared__ float2 sc[SF_TREC];
     __shared__ float4 sn[BND ? SF_TREC : 1];
+    const int kq = KE > 0 ? KE : ke;
     const int64_t pb = (int64_t)blockIdx.x * SF_THREADS * R;
     // origin of the block: its first point
     const double ox = X[2 * pb], oy = X[2 * pb + 1];
@@ -177,18 +203,19 @@ __global__ void __launch_bounds__(SF_THREADS) sf_far_dw_kernel(
     }
     const int64_t fb = f_begin + (int64_t)blockIdx.y * fac_per_chunk;
     const int64_t fe = min(f_end, fb + fac_per_chunk);
-    const int fpt = SF_TREC / ke;
+    const int fpt = SF_TREC / kq;
+    const float4 nn0 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t f = fb; f < fe; f += fpt) {
         const int nf = (int)min((int64_t)fpt, fe - f);
         __syncthreads();
-        for (int i = threadIdx.x; i < nf * ke; i += SF_THREADS) {
-            const int64_t gi = f * ke + i;
+        for (int i = threadIdx.x; i < nf * kq; i += SF_THREADS) {
+            const int64_t gi = f * kq + i;
             const dw yx = dw_from(yrec[2 * gi] - ox), yy = dw_from(yrec[2 * gi + 1] - oy);
             sy[i] = make_float4(yx.h, yx.l, yy.h, yy.l);
-            const dw c = dw_from(BND ? crec[gi - f_begin * ke] : crec[gi]);
+            const dw c = dw_from(BND ? crec[gi - f_begin * kq] : crec[gi]);
             sc[i] = make_float2(c.h, c.l);
             if constexpr (BND) {
-                const int64_t e = f + i / ke;
+                const int64_t e = f + i / kq;
                 const dw nx = dw_from(fn[3 * e]), ny = dw_from(fn[3 * e + 1]);
                 sn[i] = make_float4(nx.h, nx.l, ny.h, ny.l);
             }
@@ -196,31 +223,29 @@ __global__ void __launch_bounds__(SF_THREADS) sf_far_dw_kernel(
         __syncthreads();
         for (int j = 0; j < nf; ++j) {
             const int e = (int)(f + j);
-            bool use[R];
+            bool use[R], all = true;
 #pragma unroll
-            for (int r = 0; r < R; ++r) use[r] = e != f0[r] && e != f1[r] && e != f2[r];
-            for (int g = 0; g < ke; ++g) {
-                const float4 y = sy[j * ke + g];
-                const float2 c2 = sc[j * ke + g];
-                const dw c = {c2.x, c2.y};
+            for (int r = 0; r < R; ++r) {
+                use[r] = e != f0[r] && e != f1[r] && e != f2[r];
+                all = all && use[r];
+            }
+            if (__all_sync(0xffffffffu, all)) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (!use[r]) continue;
-                    // x - y: the low parts' difference can be as large as the high parts'
-                    // when the points are close, so the pair is renormalised (TwoSum) before
-                    // it is squared
-                    dw dx = two_sum(xr[r].h, -y.x);
-                    dx = two_sum(dx.h, __fadd_rn(dx.l, __fsub_rn(xr[r].l, y.y)));
-                    dw dy = two_sum(yr[r].h, -y.z);
-                    dy = two_sum(dy.h, __fadd_rn(dy.l, __fsub_rn(yr[r].l, y.w)));
-                    const dw r2 = dw_add(dw_sqr(dx), dw_sqr(dy));
-                    dw k = dw_kpow<PWK>(r2);
-                    if constexpr (BND) {
-                        const float4 nn = sn[j * ke + g];
-                        const dw nd = dw_add(dw_mul(dw{nn.x, nn.y}, dx), dw_mul(dw{nn.z, nn.w}, dy));
-                        k = dw_mul(k, nd);
-                    }
-                    dw_mac(acc[r], c, k);
+                for (int g = 0; g < kq; ++g) {
+                    const float4 y = sy[j * kq + g];
+                    const float2 c2 = sc[j * kq + g];
+                    const float4 nn = BND ? sn[j * kq + g] : nn0;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) sf_term<PWK, BND>(acc[r], xr[r], yr[r], y, dw{c2.x, c2.y}, nn);
+                }
+            } else {
+                for (int g = 0; g < kq; ++g) {
+                    const float4 y = sy[j * kq + g];
+                    const float2 c2 = sc[j * kq + g];
+                    const float4 nn = BND ? sn[j * kq + g] : nn0;
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (use[r]) sf_term<PWK, BND>(acc[r], xr[r], yr[r], y, dw{c2.x, c2.y}, nn);
                 }
             }
 #pragma unroll
@@ -601,24 +626,34 @@ int quarter(double s) {
     return 0;
 }
 
+template <int PW0, int R>
+void launch_far_dw_r(dim3 grid, int64_t npts, int q, const double* X, const int* perm, const int* c2f, int ke,
+                     int64_t fb, int64_t fe, int64_t fpc, const double* yrec, const double* crec, const double* fn,
+                     double* part, cudaStream_t st) {
+    if (ke == 4)
+        sf_far_dw_kernel<PW0, false, R, 4><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec,
+                                                                         crec, fn, part);
+    else
+        sf_far_dw_kernel<PW0, false, R, 0><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec,
+                                                                         crec, fn, part);
+}
+
 template <int PW0>
 void launch_far_dw(int R, dim3 grid, int64_t npts, int q, const double* X, const int* perm, const int* c2f, int ke,
                    int64_t fb, int64_t fe, int64_t fpc, const double* yrec, const double* crec, const double* fn,
                    double* part, cudaStream_t st) {
     if (R == 2)
-        sf_far_dw_kernel<PW0, false, 2><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec,
-                                                                      crec, fn, part);
+        launch_far_dw_r<PW0, 2>(grid, npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec, crec, fn, part, st);
     else
-        sf_far_dw_kernel<PW0, false, 1><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec,
-                                                                      crec, fn, part);
+        launch_far_dw_r<PW0, 1>(grid, npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec, crec, fn, part, st);
 }
 
 template <int PW>
 void launch_bnd_dw(dim3 grid, int64_t npts, int q, const double* X, const int* perm, const int* c2f, int ke,
                    int64_t fb, int64_t fe, int64_t fpc, const double* yrec, const double* brec, const double* fn,
                    double* part, cudaStream_t st) {
-    sf_far_dw_kernel<PW, true, 1><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec, brec, fn,
-                                                                part);
+    sf_far_dw_kernel<PW, true, 1, 0><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec, brec,
+                                                                   fn, part);
 }
 
 }  // namespace
@@ -652,6 +687,7 @@ int strong_form(fl_ctx* h, double s, const double* u, int kc, int ke, int kn, do
     // chunks of facets so that the grid fills the device
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    // two points per thread once the grid fills the device (four measured slower: 80 registers)
     const int R = use_dw && npts >= (int64_t)sms * SF_THREADS * 8 ? 2 : 1;
     const int64_t bx = (npts + (int64_t)SF_THREADS * R - 1) / ((int64_t)SF_THREADS * R);
     const int64_t want = (int64_t)sms * 8;
