@@ -213,6 +213,37 @@ def build_problems(F, synth, m, svals, nrhs, nslices, V):
 
 # small named workloads for profilers (`--case`): rings, grading exponent, s
 CASES = {"disc25": (25, 1.0, 0.75), "gdisc30": (30, 2.0, 0.75), "gdisc30s5": (30, 2.0, 0.5), "disc10": (10, 1.0, 0.75)}
+# strong-form profiling cases: L-shape level, s
+SF_CASES = {"sf_lshape3": (3, 0.5), "sf_lshape5": (5, 0.5)}
+
+
+def run_sf_case(args):
+    """The strong form (k_cell 3, k_edge 4, k_near 16) of the solution on an L-shape level:
+    one untimed call, then `--steps` calls timed by CUDA events; prints the times."""
+    import torch
+
+    from paper_1708_03912_gb300 import fraclap as F
+    from paper_1708_03912_gb300 import synth
+
+    level, s = SF_CASES[args.case]
+    V, T = synth.lshape(0.25, level)
+    m = F.Mesh(V, T)
+    A = m.assemble(s, "fp64")
+    u, _ = m.solve(A, m.load_vector(s), tol=1e-8)
+    del A
+    S = torch.empty((len(T), 9), dtype=torch.float64, device="cuda")
+    F.fl_strong_form(m.h, s, u, 3, 4, 16, S)
+    ts = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        F.fl_strong_form(m.h, s, u, 3, 4, 16, S)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    print(f"case {args.case}: cells {len(T)} dofs {u.shape[0]} strong form ms " + " ".join(f"{t:.3f}" for t in ts))
+    m.close()
+    return 0
 
 
 def run_case(args):
@@ -622,13 +653,15 @@ def main():
     ap.add_argument("--no-side", action="store_true", help="headline step only (no side sections)")
     ap.add_argument("--no-tune", action="store_true", help="skip the far-kernel autotuner (default launch shape)")
     ap.add_argument("--tune-file", default=None, help="load/save the autotuner's table (JSON)")
-    ap.add_argument("--case", default=None, choices=sorted(CASES),
+    ap.add_argument("--case", default=None, choices=sorted(CASES) + sorted(SF_CASES),
                     help="profiling mode: run a small named workload and print stage times (no JSON line)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="assembly precision of --case")
     ap.add_argument("--no-solve", action="store_true", help="--case: assembly only")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case in SF_CASES:
+        return run_sf_case(args)
     if args.case:
         return run_case(args)
 

@@ -97,9 +97,11 @@ def _boundary_arrays(mesh: OracleMesh, k_edge):
 
 
 def strong_form(mesh: OracleMesh, s: float, u_dof, k_cell: int = 3, k_edge: int = 4, k_near: int = 16,
-                dof_mode: str = "interior", cells=None):
+                dof_mode: str = "interior", cells=None, with_abs: bool = False):
     """(-Delta)^s u_h at the cell-rule points of every cell: [nc, q] (Lemma 4.1); with `cells`,
-    only at the points of those cells: [len(cells), q]."""
+    only at the points of those cells: [len(cells), q].  with_abs: also C times the sum of the
+    absolute values of all terms at each point (the size of what the sum cancels, which sets the
+    rounding error of any evaluation of it, this one included)."""
     d = mesh.dim
     C = frac_constant(d, s)
     u = _nodal(mesh, s, u_dof, dof_mode)
@@ -114,8 +116,9 @@ def strong_form(mesh: OracleMesh, s: float, u_dof, k_cell: int = 3, k_edge: int 
     all_cells = np.arange(mesh.nc)
     cells = all_cells if cells is None else np.asarray(cells)
     out = np.zeros((len(cells), q))
+    out_abs = np.zeros((len(cells), q))
 
-    def terms(x, arrays, sel, k0, idx):
+    def terms(x, ux, arrays, sel, k0, idx):
         """The integrals over the facets sel ([nc, F] mask) of the boundaries of the cells idx,
         with the weights of eq. (8)/(9): 1/m (log case: 1) and -u(x)/(2s) on K0's own boundary,
         1/(2s m) (log case: 1/(2s)) and -u(y)/(2s) on every other cell's boundary."""
@@ -131,9 +134,12 @@ def strong_form(mesh: OracleMesh, s: float, u_dof, k_cell: int = 3, k_edge: int 
         own = idx == k0
         g_w = np.where(own, 1.0 if log_case else 1.0 / m, 1.0 / (2.0 * s) if log_case else 1.0 / (2.0 * s * m))
         val = np.sum(np.where(sel, g_int * g_w[:, None], 0.0))
+        g_abs = np.sum(np.where(sel, np.abs(np.sum(W * kern, axis=-1) * gn * g_w[:, None]), 0.0))
         u_int = np.sum(W * nd / r ** (d + 2.0 * s) * uy, axis=-1)       # other cells: u(y)
         o_int = np.sum(W * nd / r ** (d + 2.0 * s), axis=-1)            # own cell: times u(x)
-        return val, np.where(sel & ~own[:, None], u_int, 0.0), np.where(sel & own[:, None], o_int, 0.0)
+        u_abs = np.sum(np.abs(W * nd / r ** (d + 2.0 * s)) * np.where(own[:, None, None], abs(ux), np.abs(uy)), axis=-1)
+        g_abs += np.sum(np.where(sel, u_abs, 0.0)) / (2.0 * s)
+        return val, np.where(sel & ~own[:, None], u_int, 0.0), np.where(sel & own[:, None], o_int, 0.0), g_abs
 
     for row, k0 in enumerate(cells):
         # facets of K0, whichever cell's boundary they are part of
@@ -147,11 +153,14 @@ def strong_form(mesh: OracleMesh, s: float, u_dof, k_cell: int = 3, k_edge: int 
                 lam = np.array([1.0 - ref[a, 0] - ref[a, 1], ref[a, 0], ref[a, 1]])
             ux = lam @ u[mesh.C[k0]]
             val = 0.0
+            size = 0.0
             for arrays, sel, idx in ((far, ~sel_near, all_cells), (near, sel_near, near_cells)):
-                v, u_other, own_int = terms(x, arrays, sel, k0, idx)
+                v, u_other, own_int, g_abs = terms(x, ux, arrays, sel, k0, idx)
                 val += v - np.sum(u_other) / (2.0 * s) - ux / (2.0 * s) * np.sum(own_int)
+                size += g_abs
             out[row, a] = C * val
-    return out
+            out_abs[row, a] = abs(C) * size
+    return (out, out_abs) if with_abs else out
 
 
 def cell_diameters(mesh: OracleMesh):

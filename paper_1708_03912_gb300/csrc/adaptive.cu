@@ -26,11 +26,12 @@
 //
 // Kernels: sf_prep (cell gradients and the points, in the planner's spatial cell order),
 // sf_facet (per facet and Gauss point: the point and its coefficient), sf_far_dw (2D with s in
-// {1/4, 1/2, 3/4}: the sum over the facets not on dK0 in double-word arithmetic on the float32
-// pipe, coordinates taken relative to an origin per block so that the difference of nearby
-// points keeps its relative accuracy), sf_far_f64 (other s, and 1D: float64), sf_near (the
-// facets of K0 in float64, and the sum of the parts).  Every sum runs in a fixed order: the
-// result is bitwise reproducible.
+// {1/4, 1/2, 3/4}: the sum over the facets that share no vertex with K0, in double-word
+// arithmetic on the float32 pipe, coordinates relative to an origin per block), sf_far_f64
+// (other s, and 1D: the same facets in float64), sf_near (float64: the facets of K0, the other
+// facets through a vertex of K0 -- the ones close to x, where double-word coordinates, good to
+// 2^-48 of their size, would lose the relative accuracy of x - y -- and the sum of the parts).
+// Every sum runs in a fixed order: the result is bitwise reproducible.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -164,26 +165,28 @@ __device__ __forceinline__ void sf_term(dw& acc, dw xr, dw yr, float4 y, dw c, f
     dw_mac(acc, c, k);
 }
 
-// Sum over the facet points of facets [f_begin, f_end) not on the boundary of the point's own
-// cell, 2D, double-word.  BND = false: c |x-y|^{-2s} with PWK = 4s; BND = true (boundary facets,
+// Sum over the facet points of facets [f_begin, f_end) that share no vertex with the point's own
+// cell (those are summed in float64 by sf_near_kernel), 2D, double-word.  BND = false: c |x-y|^{-2s} with PWK = 4s; BND = true (boundary facets,
 // term with u(y)): c n.(x-y) |x-y|^{-2-2s} with PWK = 4 + 4s.  Each thread takes R points of
 // the block's range (stride SF_THREADS); blockIdx.y picks the facet chunk.  KE > 0 fixes the
 // Gauss order on the facets at compile time (ke must equal it), 0 takes ke.  A facet that no
 // lane of the warp owns (nearly all of them) runs without per-point tests.
 template <int PWK, bool BND, int R, int KE>
 __global__ void __launch_bounds__(SF_THREADS) sf_far_dw_kernel(
-    int64_t npts, int q, const double* __restrict__ X, const int* __restrict__ perm, const int* __restrict__ c2f,
-    int ke, int64_t f_begin, int64_t f_end, int64_t fac_per_chunk, const double* __restrict__ yrec,
-    const double* __restrict__ crec, const double* __restrict__ fn, double* __restrict__ part) {
+    int64_t npts, int q, const double* __restrict__ X, const int* __restrict__ perm, const int* __restrict__ cells,
+    const int* __restrict__ fac, int ke, int64_t f_begin, int64_t f_end, int64_t fac_per_chunk,
+    const double* __restrict__ yrec, const double* __restrict__ crec, const double* __restrict__ fn,
+    double* __restrict__ part) {
     __shared__ float4 sy[SF_TREC];
     __shared__ float2 sc[SF_TREC];
     __shared__ float4 sn[BND ? SF_TREC : 1];
+    __shared__ int2 sab[SF_TREC];  // facet end points
     const int kq = KE > 0 ? KE : ke;
     const int64_t pb = (int64_t)blockIdx.x * SF_THREADS * R;
     // origin of the block: its first point
     const double ox = X[2 * pb], oy = X[2 * pb + 1];
     dw xr[R], yr[R], acc[R];
-    int f0[R], f1[R], f2[R];
+    int v0[R], v1[R], v2[R];  // the vertices of the point's cell
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int64_t p = pb + r * SF_THREADS + threadIdx.x;
@@ -192,13 +195,13 @@ __global__ void __launch_bounds__(SF_THREADS) sf_far_dw_kernel(
             xr[r] = dw_from(X[2 * p] - ox);
             yr[r] = dw_from(X[2 * p + 1] - oy);
             const int K = perm[p / q];
-            f0[r] = c2f[3 * K];
-            f1[r] = c2f[3 * K + 1];
-            f2[r] = c2f[3 * K + 2];
+            v0[r] = cells[3 * K];
+            v1[r] = cells[3 * K + 1];
+            v2[r] = cells[3 * K + 2];
         } else {
             xr[r] = {0.f, 0.f};
             yr[r] = {0.f, 0.f};
-            f0[r] = f1[r] = f2[r] = -1;
+            v0[r] = v1[r] = v2[r] = -1;
         }
     }
     const int64_t fb = f_begin + (int64_t)blockIdx.y * fac_per_chunk;
@@ -220,13 +223,15 @@ __global__ void __launch_bounds__(SF_THREADS) sf_far_dw_kernel(
                 sn[i] = make_float4(nx.h, nx.l, ny.h, ny.l);
             }
         }
+        for (int i = threadIdx.x; i < nf; i += SF_THREADS) sab[i] = make_int2(fac[4 * (f + i)], fac[4 * (f + i) + 1]);
         __syncthreads();
         for (int j = 0; j < nf; ++j) {
-            const int e = (int)(f + j);
+            const int2 ab = sab[j];
             bool use[R], all = true;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                use[r] = e != f0[r] && e != f1[r] && e != f2[r];
+                use[r] = ab.x != v0[r] && ab.x != v1[r] && ab.x != v2[r] && ab.y != v0[r] && ab.y != v1[r] &&
+                         ab.y != v2[r];
                 all = all && use[r];
             }
             if (__all_sync(0xffffffffu, all)) {
@@ -260,9 +265,11 @@ __global__ void __launch_bounds__(SF_THREADS) sf_far_dw_kernel(
 }
 
 // The same sum in float64 for any s and for 1D: c |x-y|^{-m} (log case: c log(1/|x-y|)) on every
-// facet, plus cB n.(x-y) |x-y|^{-d-2s} on boundary facets when termB.
+// facet that shares no vertex with the point's cell, plus cB n.(x-y) |x-y|^{-d-2s} on boundary
+// facets when termB.
 __global__ void __launch_bounds__(SF_THREADS) sf_far_f64_kernel(
-    int64_t npts, int q, int d, const double* __restrict__ X, const int* __restrict__ perm, const int* __restrict__ c2f,
+    int64_t npts, int q, int d, const double* __restrict__ X, const int* __restrict__ perm, const int* __restrict__ cells,
+    const int* __restrict__ fac,
     int ke, int64_t nfac, int64_t nint, int64_t fac_per_chunk, const double* __restrict__ yrec,
     const double* __restrict__ crec, const double* __restrict__ brec, const double* __restrict__ fn, int termB, double m,
     double pB, int logc, double* __restrict__ part) {
@@ -270,14 +277,15 @@ __global__ void __launch_bounds__(SF_THREADS) sf_far_f64_kernel(
     if (p >= npts) return;
     const int nfc = d + 1;
     const int K = perm[p / q];
-    int own[3] = {-1, -1, -1};
-    for (int j = 0; j < nfc; ++j) own[j] = c2f[(int64_t)K * nfc + j];
+    int vk[3] = {-1, -1, -1};
+    for (int j = 0; j < nfc; ++j) vk[j] = cells[(int64_t)K * nfc + j];
     const double x0 = X[p * d], x1 = d == 2 ? X[p * d + 1] : 0.0;
     const int64_t fb = (int64_t)blockIdx.y * fac_per_chunk;
     const int64_t fe = min(nfac, fb + fac_per_chunk);
     double acc = 0.0;
     for (int64_t e = fb; e < fe; ++e) {
-        if (e == own[0] || e == own[1] || e == own[2]) continue;
+        const int a = fac[4 * e], b = fac[4 * e + 1];
+        if (a == vk[0] || a == vk[1] || a == vk[2] || b == vk[0] || b == vk[1] || b == vk[2]) continue;
         for (int g = 0; g < ke; ++g) {
             const int64_t i = e * ke + g;
             const double dx = x0 - yrec[i * d], dy = d == 2 ? x1 - yrec[i * d + 1] : 0.0;
@@ -293,16 +301,20 @@ __global__ void __launch_bounds__(SF_THREADS) sf_far_f64_kernel(
     part[(int64_t)blockIdx.y * npts + p] = acc;
 }
 
-// the facets of the point's own cell (float64, order k_near) and the sum of all parts:
+// the facets of the point's own cell (float64, order k_near), the other facets that share a
+// vertex with it (float64, order k_edge: the close ones, whose difference x - y double-word
+// coordinates would resolve only to 2^-48 of the coordinates), and the sum of all parts:
 // S[K q + a] = C (near + sum over chunks of part)
 __global__ void sf_near_kernel(int64_t npts, int q, int d, const double* __restrict__ X, const double* __restrict__ lam,
                                const int* __restrict__ perm, const int* __restrict__ cells, const double* __restrict__ V,
                                const int* __restrict__ dov, const double* __restrict__ u,
                                const double* __restrict__ grad, const int* __restrict__ c2f,
                                const int* __restrict__ fac, const double* __restrict__ fn, int kn,
-                               const double* __restrict__ tn, const double* __restrict__ wn, double s, double m,
-                               double pB, int logc, int nparts, const double* __restrict__ part, double C,
-                               double* __restrict__ S) {
+                               const double* __restrict__ tn, const double* __restrict__ wn,
+                               const int* __restrict__ v2e_ptr, const int* __restrict__ v2e, int ke, int64_t nint,
+                               int termB, const double* __restrict__ yrec, const double* __restrict__ crec,
+                               const double* __restrict__ brec, double s, double m, double pB, int logc, int nparts,
+                               const double* __restrict__ part, double C, double* __restrict__ S) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npts) return;
     const int64_t kint = p / q;
@@ -362,6 +374,21 @@ __global__ void sf_near_kernel(int64_t npts, int q, int d, const double* __restr
             const double nd = n0x * dx + n0y * dy;
             const double du = Kn >= 0 ? g0x * dx + g0y * dy : ux;
             near += w * (cg * k0 - du * nd * k1 / (2.0 * s));
+        }
+    }
+    // the vertex star: facets through one vertex of K0 that are not its own (in 1D there are none)
+    for (int j = 0; j < nfc && d == 2; ++j) {
+        for (int qq = v2e_ptr[c[j]]; qq < v2e_ptr[c[j] + 1]; ++qq) {
+            const int e = v2e[qq];
+            if (e == c2f[(int64_t)K0 * 3] || e == c2f[(int64_t)K0 * 3 + 1] || e == c2f[(int64_t)K0 * 3 + 2]) continue;
+            const double* n = fn + (int64_t)e * 3;
+            for (int g = 0; g < ke; ++g) {
+                const int64_t i = (int64_t)e * ke + g;
+                const double dx = x0 - yrec[2 * i], dy = x1 - yrec[2 * i + 1];
+                const double r2 = dx * dx + dy * dy;
+                near += crec[i] * pow(r2, -0.5 * m);
+                if (termB && e >= nint) near += brec[(e - nint) * ke + g] * (n[0] * dx + n[1] * dy) * pow(r2, -0.5 * pB);
+            }
         }
     }
     double acc = 0.0;
@@ -571,6 +598,20 @@ int ensure_sf_topology(fl_ctx* h, int pi, cudaStream_t st) {
     SF_TRY(upload(h, &t.sf_fac, fac, st));
     SF_TRY(upload(h, &t.sf_fn, fn, st));
     SF_TRY(upload(h, &t.sf_c2f, c2f_local, st));
+    // vertex -> facets through it (2D)
+    std::vector<int> v2e_ptr(P.nv + 1, 0), v2e;
+    if (d == 2) {
+        for (const auto& f : F) ++v2e_ptr[f.a + 1], ++v2e_ptr[f.b + 1];
+        for (int64_t v = 0; v < P.nv; ++v) v2e_ptr[v + 1] += v2e_ptr[v];
+        v2e.resize(v2e_ptr[P.nv]);
+        std::vector<int> fill(v2e_ptr.begin(), v2e_ptr.end() - 1);
+        for (size_t e = 0; e < F.size(); ++e) {
+            v2e[fill[F[e].a]++] = (int)e;
+            v2e[fill[F[e].b]++] = (int)e;
+        }
+    }
+    SF_TRY(upload(h, &t.sf_v2e_ptr, v2e_ptr, st));
+    SF_TRY(upload(h, &t.sf_v2e, v2e, st));
     SF_TRY(upload(h, &t.sf_perm, P.perm, st));
     t.sf_nfac = (int64_t)F.size();
     t.sf_nint = nint;
@@ -627,33 +668,33 @@ int quarter(double s) {
 }
 
 template <int PW0, int R>
-void launch_far_dw_r(dim3 grid, int64_t npts, int q, const double* X, const int* perm, const int* c2f, int ke,
-                     int64_t fb, int64_t fe, int64_t fpc, const double* yrec, const double* crec, const double* fn,
-                     double* part, cudaStream_t st) {
+void launch_far_dw_r(dim3 grid, int64_t npts, int q, const double* X, const int* perm, const int* cells,
+                     const int* fac, int ke, int64_t fb, int64_t fe, int64_t fpc, const double* yrec,
+                     const double* crec, const double* fn, double* part, cudaStream_t st) {
     if (ke == 4)
-        sf_far_dw_kernel<PW0, false, R, 4><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec,
-                                                                         crec, fn, part);
+        sf_far_dw_kernel<PW0, false, R, 4><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, cells, fac, ke, fb, fe, fpc,
+                                                                         yrec, crec, fn, part);
     else
-        sf_far_dw_kernel<PW0, false, R, 0><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec,
-                                                                         crec, fn, part);
+        sf_far_dw_kernel<PW0, false, R, 0><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, cells, fac, ke, fb, fe, fpc,
+                                                                         yrec, crec, fn, part);
 }
 
 template <int PW0>
-void launch_far_dw(int R, dim3 grid, int64_t npts, int q, const double* X, const int* perm, const int* c2f, int ke,
-                   int64_t fb, int64_t fe, int64_t fpc, const double* yrec, const double* crec, const double* fn,
-                   double* part, cudaStream_t st) {
+void launch_far_dw(int R, dim3 grid, int64_t npts, int q, const double* X, const int* perm, const int* cells,
+                   const int* fac, int ke, int64_t fb, int64_t fe, int64_t fpc, const double* yrec,
+                   const double* crec, const double* fn, double* part, cudaStream_t st) {
     if (R == 2)
-        launch_far_dw_r<PW0, 2>(grid, npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec, crec, fn, part, st);
+        launch_far_dw_r<PW0, 2>(grid, npts, q, X, perm, cells, fac, ke, fb, fe, fpc, yrec, crec, fn, part, st);
     else
-        launch_far_dw_r<PW0, 1>(grid, npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec, crec, fn, part, st);
+        launch_far_dw_r<PW0, 1>(grid, npts, q, X, perm, cells, fac, ke, fb, fe, fpc, yrec, crec, fn, part, st);
 }
 
 template <int PW>
-void launch_bnd_dw(dim3 grid, int64_t npts, int q, const double* X, const int* perm, const int* c2f, int ke,
-                   int64_t fb, int64_t fe, int64_t fpc, const double* yrec, const double* brec, const double* fn,
-                   double* part, cudaStream_t st) {
-    sf_far_dw_kernel<PW, true, 1, 0><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, c2f, ke, fb, fe, fpc, yrec, brec,
-                                                                   fn, part);
+void launch_bnd_dw(dim3 grid, int64_t npts, int q, const double* X, const int* perm, const int* cells,
+                   const int* fac, int ke, int64_t fb, int64_t fe, int64_t fpc, const double* yrec,
+                   const double* brec, const double* fn, double* part, cudaStream_t st) {
+    sf_far_dw_kernel<PW, true, 1, 0><<<grid, SF_THREADS, 0, st>>>(npts, q, X, perm, cells, fac, ke, fb, fe, fpc, yrec,
+                                                                   brec, fn, part);
 }
 
 }  // namespace
@@ -737,9 +778,9 @@ int strong_form(fl_ctx* h, double s, const double* u, int kc, int ke, int kn, do
         if (use_dw) {
             const dim3 grid((unsigned)bx, (unsigned)chunks);
             switch (pw0) {
-                case 1: launch_far_dw<1>(R, grid, npts, q, X, t.sf_perm, t.sf_c2f, ke, 0, nfac, fpc, yrec, crec, t.sf_fn, part, st); break;
-                case 2: launch_far_dw<2>(R, grid, npts, q, X, t.sf_perm, t.sf_c2f, ke, 0, nfac, fpc, yrec, crec, t.sf_fn, part, st); break;
-                default: launch_far_dw<3>(R, grid, npts, q, X, t.sf_perm, t.sf_c2f, ke, 0, nfac, fpc, yrec, crec, t.sf_fn, part, st); break;
+                case 1: launch_far_dw<1>(R, grid, npts, q, X, t.sf_perm, t.cells, t.sf_fac, ke, 0, nfac, fpc, yrec, crec, t.sf_fn, part, st); break;
+                case 2: launch_far_dw<2>(R, grid, npts, q, X, t.sf_perm, t.cells, t.sf_fac, ke, 0, nfac, fpc, yrec, crec, t.sf_fn, part, st); break;
+                default: launch_far_dw<3>(R, grid, npts, q, X, t.sf_perm, t.cells, t.sf_fac, ke, 0, nfac, fpc, yrec, crec, t.sf_fn, part, st); break;
             }
             count_launch();
             if (bchunks > 0) {
@@ -747,21 +788,22 @@ int strong_form(fl_ctx* h, double s, const double* u, int kc, int ke, int kn, do
                 const dim3 g2((unsigned)bx1, (unsigned)bchunks);
                 double* bpart = part + chunks * npts;
                 switch (pw0) {
-                    case 1: launch_bnd_dw<5>(g2, npts, q, X, t.sf_perm, t.sf_c2f, ke, nint, nfac, bfpc, yrec, brec, t.sf_fn, bpart, st); break;
-                    case 2: launch_bnd_dw<6>(g2, npts, q, X, t.sf_perm, t.sf_c2f, ke, nint, nfac, bfpc, yrec, brec, t.sf_fn, bpart, st); break;
-                    default: launch_bnd_dw<7>(g2, npts, q, X, t.sf_perm, t.sf_c2f, ke, nint, nfac, bfpc, yrec, brec, t.sf_fn, bpart, st); break;
+                    case 1: launch_bnd_dw<5>(g2, npts, q, X, t.sf_perm, t.cells, t.sf_fac, ke, nint, nfac, bfpc, yrec, brec, t.sf_fn, bpart, st); break;
+                    case 2: launch_bnd_dw<6>(g2, npts, q, X, t.sf_perm, t.cells, t.sf_fac, ke, nint, nfac, bfpc, yrec, brec, t.sf_fn, bpart, st); break;
+                    default: launch_bnd_dw<7>(g2, npts, q, X, t.sf_perm, t.cells, t.sf_fac, ke, nint, nfac, bfpc, yrec, brec, t.sf_fn, bpart, st); break;
                 }
                 count_launch();
             }
         } else {
             const dim3 grid((unsigned)((npts + SF_THREADS - 1) / SF_THREADS), (unsigned)chunks);
-            sf_far_f64_kernel<<<grid, SF_THREADS, 0, st>>>(npts, q, d, X, t.sf_perm, t.sf_c2f, ke_eff, nfac, nint, fpc,
+            sf_far_f64_kernel<<<grid, SF_THREADS, 0, st>>>(npts, q, d, X, t.sf_perm, t.cells, t.sf_fac, ke_eff, nfac, nint, fpc,
                                                            yrec, crec, brec, t.sf_fn, termB ? 1 : 0, m, pB, logc, part);
             count_launch();
         }
         sf_near_kernel<<<(unsigned)((npts + 127) / 128), 128, 0, st>>>(
-            npts, q, d, X, lam, t.sf_perm, t.cells, t.V, t.dov, u, grad, t.sf_c2f, t.sf_fac, t.sf_fn, kn, tn, wn, s, m,
-            pB, logc, (int)nparts, part, frac_const(d, s), S);
+            npts, q, d, X, lam, t.sf_perm, t.cells, t.V, t.dov, u, grad, t.sf_c2f, t.sf_fac, t.sf_fn, kn, tn, wn,
+            t.sf_v2e_ptr, t.sf_v2e, ke_eff, nint, termB ? 1 : 0, yrec, crec, brec, s, m, pB, logc, (int)nparts, part,
+            frac_const(d, s), S);
         count_launch();
     }
     SF_CUDA(h, cudaGetLastError());

@@ -114,6 +114,7 @@ struct DevTables {
     double* sf_fn = nullptr;   // nfac*(dim+1): unit normal outward of K+, length (1D: 1)
     int* sf_c2f = nullptr;     // nc*nvpc: facets of every cell (original order)
     int* sf_perm = nullptr;    // nc: internal -> original cell
+    int *sf_v2e_ptr = nullptr, *sf_v2e = nullptr;  // vertex -> facets through it (2D)
     double* sf_rule = nullptr; // cell rule, edge rule, near-edge rule of the last call
     size_t sf_rule_cap = 0;
     int sf_rule_key[3] = {0, 0, 0};
