@@ -10,7 +10,7 @@ Mesh shapes follow the paper's numerical examples (Section 7): the interval
 radii r_i = 1 - (1 - i/M)^mu as in Section 3), and the L-shaped domain
 [0,2]^2 minus [1,2]^2 refined towards the re-entrant corner and the boundary.
 The paper's adaptively refined meshes are not available, so these stand in
-for them.
+for them.  The sector mesh serves the symmetry-reduced problem (Section 7).
 """
 from __future__ import annotations
 
@@ -91,6 +91,54 @@ def disc(M: int, mu: float = 1.0):
         tris.append((0, idx0[k], idx0[(k + 1) % len(idx0)]))
     for (ia, aa), (ib, ab) in zip(rings[:-1], rings[1:]):
         tris.extend(_zipper(ia, aa, ib, ab, pts))
+    return np.array(pts, dtype=np.float64), np.array(tris, dtype=np.int32)
+
+
+def _zipper_open(inner, outer, pts):
+    """Triangulate the strip between two open polylines (first and last points on the two
+    cut rays), closing each step with the shorter diagonal."""
+    na, nb = len(inner) - 1, len(outer) - 1
+    tris = []
+    i = j = 0
+
+    def d2(p, q):
+        return (pts[p][0] - pts[q][0]) ** 2 + (pts[p][1] - pts[q][1]) ** 2
+
+    while i < na or j < nb:
+        if j == nb:
+            adv_inner = True
+        elif i == na:
+            adv_inner = False
+        else:
+            adv_inner = d2(inner[i + 1], outer[j]) < d2(inner[i], outer[j + 1])
+        if adv_inner:
+            tris.append((inner[i], outer[j], inner[i + 1]))
+            i += 1
+        else:
+            tris.append((inner[i], outer[j], outer[j + 1]))
+            j += 1
+    return tris
+
+
+def sector(K: int, M: int):
+    """Uniform mesh of the circular sector {r <= 1, 0 <= phi <= 2 pi / K} (Section 7's
+    periodic example with K = 8): M rings at radii j/M, ring j carrying
+    max(1, round(2 pi j / K)) + 1 equally spaced points from phi = 0 to phi = 2 pi / K, so the
+    vertices on the two cut rays sit at the same radii (the rotation by 2 pi / K maps one ray's
+    vertices onto the other's).  Rings are joined by the shorter-diagonal walk, the first by a
+    fan around the centre."""
+    pts = [(0.0, 0.0)]
+    rings = [[0]]
+    for j in range(1, M + 1):
+        r = j / M
+        n = max(1, int(round(2 * math.pi * j / K)))
+        idx = list(range(len(pts), len(pts) + n + 1))
+        pts.extend((r * math.cos(2 * math.pi * t / (K * n)), r * math.sin(2 * math.pi * t / (K * n)))
+                   for t in range(n + 1))
+        rings.append(idx)
+    tris = [(0, rings[1][t], rings[1][t + 1]) for t in range(len(rings[1]) - 1)]
+    for a, b in zip(rings[1:-1], rings[2:]):
+        tris.extend(_zipper_open(a, b, pts))
     return np.array(pts, dtype=np.float64), np.array(tris, dtype=np.int32)
 
 
