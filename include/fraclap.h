@@ -99,6 +99,31 @@ void fl_default_options(fl_options* opt);
 int fl_create(fl_handle* h, int dim, int64_t n_vertices, const double* vertices_host,
               int64_t n_cells, const int32_t* cells_host, int dof_mode, const fl_options* opt);
 
+/*
+ * Symmetry reduction (Section 7, "Exploiting Symmetry"): Omega, f and hence u invariant under
+ * the rotation B by 2 pi / K about the origin.  The caller meshes the sector
+ * {0 <= phi <= 2 pi / K} (vertices_host [n_vertices][2], cells_host [n_cells][3], host arrays,
+ * copied) so that the rotation maps the vertices on the ray phi = 0 onto those on the ray
+ * phi = 2 pi / K; the handle holds the whole mesh, the K copies rotated by 2 pi l / K with
+ * vertices closer than 1e-10 merged.  Its problem is the reduced one: one unknown per orbit
+ * {B^l v} of interior vertices (numbered by the lowest sector vertex of the orbit, ascending;
+ * fl_dof_vertices gives those sector vertices, fl_num_dofs their count n_red), the Galerkin
+ * problem on the periodic subspace.  fl_assemble writes the n_red x n_red matrix: the
+ * symmetric part of (|O_r| / K) sum_{j in O_c} A[rep_r, j], i.e. P^T A P / K with A the whole
+ * mesh's matrix (the paper's bilinear form with the effective kernel
+ * k_eff(x, y) = sum_l |x - B^l y|^{-d-2s}, over K); only the element pairs with a cell in a
+ * representative's support are evaluated, about 2/K of the whole mesh's.  fl_load_vector
+ * takes f_nodal_dev as [n_vertices (of the sector)][nrhs] and writes P^T b / K (n_red rows).
+ * fl_solve / fl_matvec work on the reduced matrix as on any other (n = n_red).  Always interior
+ * DOFs (dof_mode FL_DOF_INTERIOR).  Not available on such a handle (FL_ENOTIMPL): the
+ * near-field CSR, heat-equation, adaptive, cluster-method, multigrid-prolongation and learned
+ * preconditioner calls.
+ * Errors: FL_EINVAL (NULL arrays, K outside [2, 64], index out of range, a copy that does not
+ * close up into orbits), the errors of fl_create.
+ */
+int fl_create_sector(fl_handle* h, int64_t n_vertices, const double* vertices_host, int64_t n_cells,
+                     const int32_t* cells_host, int K, const fl_options* opt);
+
 /* Release the handle and every device buffer it owns (synchronises the device). */
 void fl_destroy(fl_handle h);
 

@@ -1250,6 +1250,110 @@ __global__ void add_csr_kernel(int64_t nnz, const int* csr_row, const int* csr_c
     if (j != i) A[j * lda + i] += v;
 }
 
+// ------------------------------------------------- symmetry reduction --
+// Rows of the orbit representatives (Section 7, "Exploiting Symmetry"): R[r][j] is the far-field
+// part of the whole matrix's entry (rep_r, j), summed from the tile partials exactly as
+// compose_far_kernel sums them (occurrences of min(i, j) major), so R[r][j] equals that entry.
+// Every tile read holds a representative's cell and is in the list; a missing one (a broken
+// plan) shows as NaN.  Grid: x over columns, y over representatives (strided).
+template <typename T>
+__global__ void compose_rows_kernel(int64_t n, int64_t nred, int64_t nblk, const int* red_rep, const int* occ_ptr,
+                                    const int* occ_blk, const int* occ_loc, const int* L_ptr, const int64_t* tri_list,
+                                    const int64_t* toff, const T* P, double negC, double* R, int64_t ldr) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    for (int64_t r = blockIdx.y; r < nred; r += gridDim.y) {
+        const int64_t i = red_rep[r];
+        const int64_t lo = min(i, j), hi = max(i, j);
+        double acc = 0.0;
+        float ks = 0.f, kc = 0.f;
+        bool missing = false;
+        auto add = [&](T x) {
+            if constexpr (sizeof(T) == 4) kahan_add(ks, kc, x);
+            else acc += x;
+        };
+        for (int a = occ_ptr[lo]; a < occ_ptr[lo + 1]; ++a) {
+            const int64_t Ba = occ_blk[a];
+            const int la = occ_loc[a];
+            for (int b = occ_ptr[hi]; b < occ_ptr[hi + 1]; ++b) {
+                const int64_t Bb = occ_blk[b];
+                const int lb = occ_loc[b];
+                const int64_t B0 = min(Ba, Bb), B1 = max(Ba, Bb);
+                const int64_t pos = tri_list[B0 * nblk - B0 * (B0 - 1) / 2 + (B1 - B0)];
+                if (pos < 0) {
+                    missing = true;
+                    continue;
+                }
+                if (Ba < Bb) {
+                    add(P[toff[pos] + (int64_t)la * (L_ptr[Bb + 1] - L_ptr[Bb]) + lb]);
+                } else if (Ba > Bb) {
+                    add(P[toff[pos] + (int64_t)lb * (L_ptr[Ba + 1] - L_ptr[Ba]) + la]);
+                } else {
+                    const int64_t nL = L_ptr[Ba + 1] - L_ptr[Ba];
+                    add(P[toff[pos] + (int64_t)la * nL + lb]);
+                    add(P[toff[pos] + (int64_t)lb * nL + la]);
+                }
+            }
+        }
+        if constexpr (sizeof(T) == 4) acc = (double)ks - (double)kc;
+        R[r * ldr + j] = missing ? __longlong_as_double(0x7ff8000000000000LL) : negC * acc;
+    }
+}
+
+// the sparse near-field part added to the representatives' rows (upper entries serve both)
+__global__ void add_csr_rows_kernel(int64_t nnz, const int* csr_row, const int* csr_col, const double* val,
+                                    const int* red_row, double* R, int64_t ldr) {
+    const int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (z >= nnz) return;
+    const int64_t i = csr_row[z], j = csr_col[z];
+    if (j < i) return;
+    const double v = val[z];
+    const int ri = red_row[i];
+    if (ri >= 0) R[ri * ldr + j] += v;
+    if (j != i) {
+        const int rj = red_row[j];
+        if (rj >= 0) R[rj * ldr + i] += v;
+    }
+}
+
+// A[r][c] = ((|O_r| / K) sum_{j in O_c} R[r][j] + (|O_c| / K) sum_{i in O_r} R[c][i]) / 2: the
+// symmetric part of the row formula for P^T A P / K (bitwise symmetric: both entries add the
+// same two terms)
+__global__ void fold_sym_kernel(int64_t nred, int K, const int* red_ptr, const int* red_mem, const double* R,
+                                int64_t ldr, double* A, int64_t lda) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nred) return;
+    for (int64_t r = blockIdx.y; r < nred; r += gridDim.y) {
+        double x = 0.0, y = 0.0;
+        for (int q = red_ptr[c]; q < red_ptr[c + 1]; ++q) x += R[r * ldr + red_mem[q]];
+        for (int q = red_ptr[r]; q < red_ptr[r + 1]; ++q) y += R[c * ldr + red_mem[q]];
+        const double sr = (double)(red_ptr[r + 1] - red_ptr[r]) / K, sc = (double)(red_ptr[c + 1] - red_ptr[c]) / K;
+        // unfused products and sum, so that (r, c) and (c, r) round alike
+        A[r * lda + c] = 0.5 * __dadd_rn(__dmul_rn(sr, x), __dmul_rn(sc, y));
+    }
+}
+
+// nodal values of a periodic f on the whole mesh from those on the sector
+__global__ void expand_nodal_kernel(int64_t nv, int nrhs, const int* sector_of, const double* f, double* fw) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nv * nrhs) return;
+    const int64_t w = i / nrhs;
+    const int c = (int)(i - w * nrhs);
+    fw[i] = f[(int64_t)sector_of[w] * nrhs + c];
+}
+
+// b[r][c] = (1/K) sum_{i in O_r} bw[i][c]
+__global__ void fold_vec_kernel(int64_t nred, int K, int nrhs, const int* red_ptr, const int* red_mem,
+                                const double* bw, double* b, int64_t ldb) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nred * nrhs) return;
+    const int64_t r = i / nrhs;
+    const int c = (int)(i - r * nrhs);
+    double acc = 0.0;
+    for (int q = red_ptr[r]; q < red_ptr[r + 1]; ++q) acc += bw[(int64_t)red_mem[q] * nrhs + c];
+    b[r * ldb + c] = acc / K;
+}
+
 // ---------------------------------------------------------------- host side --
 namespace {
 
@@ -1394,6 +1498,18 @@ int ensure_device(fl_ctx* h, int pi, cudaStream_t st) {
     std::vector<int64_t> v2cp(P.v2c_ptr.begin(), P.v2c_ptr.end());
     U.add(t.v2c_ptr, v2cp);
     U.add(t.v2c, P.v2c);
+    std::vector<int> sector_of;
+    if (P.sym_K) {
+        U.add(t.red_rep, P.red_rep);
+        U.add(t.red_ptr, P.red_ptr);
+        U.add(t.red_mem, P.red_mem);
+        U.add(t.red_row, P.red_row);
+        U.add(t.tri_list, P.tri_list);
+        sector_of.assign(P.nv, 0);
+        for (int l = 0; l < h->sym_K; ++l)
+            for (int64_t v = 0; v < h->sym_nvs; ++v) sector_of[h->sym_vmap[(size_t)l * h->sym_nvs + v]] = (int)v;
+        U.add(t.sector_of, sector_of);
+    }
     FL_TRY(upload_all(h, U, st));
     const int qf = qf_of(h), qn = qn_of(h);
     FL_TRY(alloc(h, &t.P, (size_t)P.toff.back() * sizeof(double)));
@@ -1755,8 +1871,9 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
     const int pi = plan_for(h, s);
     if (pi < 0) return FL_EINVAL;
     const Plan& P = h->plan[pi];
+    const bool sym = P.sym_K > 0;
     if (!csr) {
-        if (lda < P.n) return set_err(h, FL_EINVAL, "lda < n");
+        if (lda < (sym ? P.n_red : P.n)) return set_err(h, FL_EINVAL, "lda < n");
         if (!A) return set_err(h, FL_EINVAL, "A is NULL");
     }
     if (precision != FL_FP64 && precision != FL_MIXED) return set_err(h, FL_EINVAL, "unknown precision");
@@ -1803,6 +1920,28 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
     const int pw = pw_mode(D, s);
     const int64_t nc = P.nc;
     const unsigned gb = (unsigned)((nc + 127) / 128);
+    // symmetry reduction: the representatives' rows R (n_red x n) in the handle's workspace; the
+    // row sums of tiles left out stay zero (they belong to cells of no representative)
+    double* R = nullptr;
+    const int64_t ldr = (P.n + 3) / 4 * 4;
+    if (sym) {
+        const size_t need = (size_t)std::max<int64_t>(P.n_red, 1) * ldr * sizeof(double);
+        if (need > h->sym_ws_bytes) {
+            if (h->sym_ws) {
+                FL_CUDA_TRY(h, cudaStreamSynchronize(st));
+                pool_dev_free(h->sym_ws);
+                h->sym_ws = nullptr;
+                h->sym_ws_bytes = 0;
+            }
+            if (pool_dev_alloc(&h->sym_ws, need) != cudaSuccess) {
+                cudaGetLastError();
+                return set_err(h, FL_ENOMEM, "reduced-assembly workspace");
+            }
+            h->sym_ws_bytes = need;
+        }
+        R = (double*)h->sym_ws;
+        FL_CUDA_TRY(h, cudaMemsetAsync(t.Pd, 0, (size_t)P.nblk * nc * qf_of(h) * sizeof(double), st));
+    }
     // far rule offsets
     stage_mark(h, st, FL_STAGE_PREP, 0);
     if (D == 2) {
@@ -1991,6 +2130,20 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
         // the dense far-field part reads only the far stage's partial tiles: it runs here while the
         // element and gather kernels run on the second stream
         auto run_compose = [&]() -> int {
+            if (sym) {
+                const dim3 grid((unsigned)((P.n + 255) / 256), (unsigned)std::min<int64_t>(std::max<int64_t>(P.n_red, 1), 65535));
+                if (f32)
+                    compose_rows_kernel<float><<<grid, 256, 0, st>>>(P.n, P.n_red, P.nblk, t.red_rep, t.occ_ptr,
+                                                                     t.occ_blk, t.occ_loc, t.L_ptr, t.tri_list, t.toff,
+                                                                     (const float*)t.P, -C, R, ldr);
+                else
+                    compose_rows_kernel<double><<<grid, 256, 0, st>>>(P.n, P.n_red, P.nblk, t.red_rep, t.occ_ptr,
+                                                                      t.occ_blk, t.occ_loc, t.L_ptr, t.tri_list, t.toff,
+                                                                      (const double*)t.P, -C, R, ldr);
+                fl::count_launch();
+                FL_CUDA_TRY(h, cudaGetLastError());
+                return FL_OK;
+            }
             const int64_t nt = (P.n + 31) / 32;
             const unsigned grid = (unsigned)(nt * (nt + 1) / 2);  // upper-triangle 32 x 32 tiles
             if (f32)
@@ -2019,6 +2172,21 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
             FL_CUDA_TRY(h, cudaMemcpyAsync(csr->col, t.csr_col, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
         }
         FL_CUDA_TRY(h, cudaMemcpyAsync(csr->rowptr, t.csr_ptr, (P.n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        stage_mark(h, st, FL_STAGE_COMPOSE, 1);
+        return FL_OK;
+    }
+    if (sym) {
+        if (nnz > 0) {
+            add_csr_rows_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, t.csr_row, t.csr_col, t.csr_val,
+                                                                               t.red_row, R, ldr);
+            fl::count_launch();
+        }
+        if (P.n_red > 0) {
+            const dim3 grid((unsigned)((P.n_red + 127) / 128), (unsigned)std::min<int64_t>(P.n_red, 65535));
+            fold_sym_kernel<<<grid, 128, 0, st>>>(P.n_red, P.sym_K, t.red_ptr, t.red_mem, R, ldr, A, lda);
+            fl::count_launch();
+        }
+        FL_CUDA_TRY(h, cudaGetLastError());
         stage_mark(h, st, FL_STAGE_COMPOSE, 1);
         return FL_OK;
     }
@@ -2244,6 +2412,38 @@ int load_vector(fl_ctx* h, double s, const double* f, int nrhs, double* b, int64
     FL_CUDA_TRY(h, cudaSetDevice(h->device));
     FL_TRY(ensure_device(h, pi, st));
     DevTables& t = h->dev[pi];
+    if (P.sym_K) {
+        // whole-mesh load vector of the periodic f (nodal values on the sector's vertices), folded
+        void* ws = nullptr;
+        const size_t need = ((size_t)P.n + (f ? (size_t)P.nv : 0)) * nrhs * sizeof(double);
+        if (pool_dev_alloc(&ws, std::max<size_t>(need, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(h, FL_ENOMEM, "reduced load-vector workspace");
+        }
+        double* bw = (double*)ws;
+        double* fw = f ? bw + (size_t)P.n * nrhs : nullptr;
+        if (f) {
+            expand_nodal_kernel<<<(unsigned)((P.nv * nrhs + 127) / 128), 128, 0, st>>>(P.nv, nrhs, t.sector_of, f, fw);
+            fl::count_launch();
+        }
+        const unsigned g = (unsigned)((P.n + 127) / 128);
+        for (int r = 0; r < nrhs && P.n > 0; ++r) {
+            load_vector_kernel<<<g, 128, 0, st>>>(P.n, P.dim, t.vod, t.v2c_ptr, t.v2c, t.cells, t.jac_orig, fw, nrhs, r,
+                                                  bw, nrhs);
+            fl::count_launch();
+        }
+        if (P.n_red > 0) {
+            fold_vec_kernel<<<(unsigned)((P.n_red * nrhs + 127) / 128), 128, 0, st>>>(P.n_red, P.sym_K, nrhs, t.red_ptr,
+                                                                                      t.red_mem, bw, b, ldb);
+            fl::count_launch();
+        }
+        cudaError_t e = cudaGetLastError();
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        pool_dev_free(ws);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return set_err(h, FL_ECUDA, std::string("reduced load vector: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return FL_OK;
+    }
     const unsigned g = (unsigned)((P.n + 127) / 128);
     for (int r = 0; r < nrhs; ++r) {
         load_vector_kernel<<<g, 128, 0, st>>>(P.n, P.dim, t.vod, t.v2c_ptr, t.v2c, t.cells, t.jac_orig, f, nrhs, r, b, ldb); fl::count_launch();

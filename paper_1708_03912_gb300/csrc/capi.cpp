@@ -29,6 +29,7 @@ int plan_for(fl_ctx* h, double s) {
         h->plan[idx] = h->plan[0];
         std::string err;
         int r = plan_dofs(h->plan[idx], idx, err);
+        if (r == FL_OK && h->sym_K) r = plan_symmetry(h->plan[idx], h->sym_K, h->sym_nvs, h->sym_vmap, err);
         if (r != FL_OK) {
             set_err(h, r, err);
             return -1;
@@ -36,6 +37,10 @@ int plan_for(fl_ctx* h, double s) {
         h->planned[idx] = true;
     }
     return idx;
+}
+
+int sym_unsupported(fl_ctx* h, const char* what) {
+    return set_err(h, FL_ENOTIMPL, std::string(what) + " is not available on a symmetry-reduced (sector) handle");
 }
 }  // namespace fl
 
@@ -61,8 +66,15 @@ void fl_default_options(fl_options* o) {
     o->far_f64_pipe = 0;
 }
 
-int fl_create(fl_handle* out, int dim, int64_t n_vertices, const double* vertices_host, int64_t n_cells,
-              const int32_t* cells_host, int dof_mode, const fl_options* opt) {
+// sector: the symmetry reduction's K and copy map (vertices and cells are then the whole mesh)
+struct SectorArgs {
+    int K;
+    int64_t nvs;
+    std::vector<int> vmap;
+};
+
+static int create_impl(fl_handle* out, int dim, int64_t n_vertices, const double* vertices_host, int64_t n_cells,
+                       const int32_t* cells_host, int dof_mode, const fl_options* opt, SectorArgs* sec) {
     g_create_err.clear();
     if (!out) {
         g_create_err = "handle pointer is NULL";
@@ -99,9 +111,25 @@ int fl_create(fl_handle* out, int dim, int64_t n_vertices, const double* vertice
     std::string err;
     int r;
     try {
-        r = fl::plan_mesh(h->plan[0], dim, n_vertices, vertices_host, n_cells, cells_host, err);
+        // symmetry reduction: the cells at a copy-0 vertex (every representative's support lies
+        // among them) first, so that they fill few blocks of the tile scheme
+        std::vector<char> first;
+        if (sec) {
+            std::vector<char> c0(n_vertices, 0);
+            for (int64_t v = 0; v < sec->nvs; ++v) c0[sec->vmap[v]] = 1;
+            first.assign(n_cells, 0);
+            for (int64_t k = 0; k < n_cells; ++k)
+                for (int a = 0; a < 3; ++a) first[k] |= c0[cells_host[3 * k + a]];
+        }
+        r = fl::plan_mesh(h->plan[0], dim, n_vertices, vertices_host, n_cells, cells_host, err, sec ? &first : nullptr);
         if (r == FL_OK) {
             r = fl::plan_dofs(h->plan[0], 0, err);
+            if (r == FL_OK && sec) {
+                h->sym_K = sec->K;
+                h->sym_nvs = sec->nvs;
+                h->sym_vmap = sec->vmap;
+                r = fl::plan_symmetry(h->plan[0], sec->K, sec->nvs, h->sym_vmap, err);
+            }
             if (r == FL_OK) h->planned[0] = true;
         }
     } catch (const std::bad_alloc&) {
@@ -117,9 +145,73 @@ int fl_create(fl_handle* out, int dim, int64_t n_vertices, const double* vertice
     return FL_OK;
 }
 
+int fl_create(fl_handle* out, int dim, int64_t n_vertices, const double* vertices_host, int64_t n_cells,
+              const int32_t* cells_host, int dof_mode, const fl_options* opt) {
+    return create_impl(out, dim, n_vertices, vertices_host, n_cells, cells_host, dof_mode, opt, nullptr);
+}
+
+int fl_create_sector(fl_handle* out, int64_t n_vertices, const double* vertices_host, int64_t n_cells,
+                     const int32_t* cells_host, int K, const fl_options* opt) {
+    g_create_err.clear();
+    if (!out || !vertices_host || !cells_host || n_vertices < 3 || n_cells < 1) {
+        g_create_err = "NULL pointer or empty sector mesh";
+        return FL_EINVAL;
+    }
+    if (K < 2 || K > 64) {
+        g_create_err = "K must lie in [2, 64]";
+        return FL_EINVAL;
+    }
+    for (int64_t i = 0; i < 3 * n_cells; ++i)
+        if (cells_host[i] < 0 || cells_host[i] >= n_vertices) {
+            g_create_err = "cell vertex index out of range";
+            return FL_EINVAL;
+        }
+    SectorArgs sec;
+    sec.K = K;
+    sec.nvs = n_vertices;
+    std::vector<double> W;
+    std::vector<int32_t> CW;
+    try {
+        fl::replicate_sector(n_vertices, vertices_host, n_cells, cells_host, K, W, CW, sec.vmap);
+    } catch (const std::bad_alloc&) {
+        g_create_err = "out of host memory";
+        return FL_ENOMEM;
+    }
+    // the sector must be the wedge 0 <= phi <= 2 pi / K, and each vertex on its second ray must
+    // meet the rotated image of one on its first ray
+    {
+        const double wedge = 2.0 * M_PI / K;
+        std::vector<char> hit(W.size() / 2, 0);
+        for (int64_t u = 0; u < n_vertices; ++u) hit[sec.vmap[(size_t)n_vertices + u]] = 1;  // copy 1
+        int64_t n_first = 0, n_second = 0;
+        for (int64_t v = 0; v < n_vertices; ++v) {
+            const double x = vertices_host[2 * v], y = vertices_host[2 * v + 1];
+            const double r = std::hypot(x, y);
+            if (r < 1e-12) continue;
+            n_first += std::fabs(std::atan2(y, x)) < 1e-9;
+            n_second += std::fabs(std::atan2(y, x) - wedge) < 1e-9;
+            const double phi = std::atan2(y, x);
+            if (phi < -1e-9 || phi > wedge + 1e-9) {
+                g_create_err = "a vertex outside the wedge 0 <= phi <= 2 pi / K";
+                return FL_EINVAL;
+            }
+            if (std::fabs(phi - wedge) < 1e-9 && !hit[sec.vmap[v]]) {
+                g_create_err = "a vertex on the ray phi = 2 pi / K without the rotated image of one on phi = 0";
+                return FL_EINVAL;
+            }
+        }
+        if (n_first == 0 || n_first != n_second) {
+            g_create_err = "the sector's two rays carry different numbers of vertices (not a wedge of angle 2 pi / K?)";
+            return FL_EINVAL;
+        }
+    }
+    return create_impl(out, 2, (int64_t)W.size() / 2, W.data(), (int64_t)CW.size() / 3, CW.data(), FL_DOF_INTERIOR,
+                       opt, &sec);
+}
+
 void fl_destroy(fl_handle h) {
     if (!h) return;
-    if (!h->bufs.empty() || h->solve_ws || h->batch_ws || h->batch_host || h->sf_ws) {
+    if (!h->bufs.empty() || h->solve_ws || h->batch_ws || h->batch_host || h->sf_ws || h->sym_ws) {
         cudaSetDevice(h->device);
         cudaDeviceSynchronize();
         for (auto& b : h->bufs) fl::pool_dev_free(b.p);  // back to the cache (the device is idle)
@@ -130,6 +222,7 @@ void fl_destroy(fl_handle h) {
         if (h->batch_ws) fl::pool_dev_free(h->batch_ws);
         if (h->batch_host) fl::pool_host_free(h->batch_host);
         if (h->sf_ws) fl::pool_dev_free(h->sf_ws);
+        if (h->sym_ws) fl::pool_dev_free(h->sym_ws);
     }
     for (auto& g : h->cg_graphs) cudaGraphExecDestroy(g.exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -150,7 +243,7 @@ int fl_num_dofs(fl_handle h, double s, int64_t* n) {
     if (!h || !n) return FL_EINVAL;
     int pi = fl::plan_for(h, s);
     if (pi < 0) return FL_EINVAL;
-    *n = h->plan[pi].n;
+    *n = h->plan[pi].sym_K ? h->plan[pi].n_red : h->plan[pi].n;
     return FL_OK;
 }
 
@@ -159,6 +252,10 @@ int fl_dof_vertices(fl_handle h, double s, int32_t* vod) {
     int pi = fl::plan_for(h, s);
     if (pi < 0) return FL_EINVAL;
     const auto& P = h->plan[pi];
+    if (P.sym_K) {
+        for (int64_t r = 0; r < P.n_red; ++r) vod[r] = P.red_vertex[r];
+        return FL_OK;
+    }
     for (int64_t i = 0; i < P.n; ++i) vod[i] = P.vod[i];
     return FL_OK;
 }
@@ -194,6 +291,7 @@ int fl_set_far_variant(fl_handle h, int variant) {
 int fl_assemble_nearfield_csr(fl_handle h, double s, int precision, int64_t* nnz, int32_t* rowptr_dev,
                               int32_t* col_dev, double* val_dev, void* stream) {
     if (!h) return FL_EINVAL;
+    if (h->sym_K) return fl::sym_unsupported(h, "fl_assemble_nearfield_csr");
     h->err.clear();
     try {
         return fl::assemble_nearfield_csr(h, s, precision, nnz, rowptr_dev, col_dev, val_dev, (cudaStream_t)stream);
@@ -205,6 +303,7 @@ int fl_assemble_nearfield_csr(fl_handle h, double s, int precision, int64_t* nnz
 int fl_heat_matrix(fl_handle h, double s, double dt, const double* A_dev, int64_t lda, double* H_dev, int64_t ldh,
                    void* stream) {
     if (!h) return FL_EINVAL;
+    if (h->sym_K) return fl::sym_unsupported(h, "fl_heat_matrix");
     h->err.clear();
     try {
         return fl::heat_matrix(h, s, dt, A_dev, lda, H_dev, ldh, (cudaStream_t)stream);
@@ -216,6 +315,7 @@ int fl_heat_matrix(fl_handle h, double s, double dt, const double* A_dev, int64_
 int fl_mass_apply(fl_handle h, double s, int nrhs, double alpha, const double* X_dev, int64_t ldx, double beta,
                   const double* B_dev, int64_t ldb, double* Y_dev, int64_t ldy, void* stream) {
     if (!h) return FL_EINVAL;
+    if (h->sym_K) return fl::sym_unsupported(h, "fl_mass_apply");
     h->err.clear();
     try {
         return fl::mass_apply(h, s, nrhs, alpha, X_dev, ldx, beta, B_dev, ldb, Y_dev, ldy, (cudaStream_t)stream);
@@ -227,6 +327,7 @@ int fl_mass_apply(fl_handle h, double s, int nrhs, double alpha, const double* X
 int fl_strong_form(fl_handle h, double s, const double* u_dev, int k_cell, int k_edge, int k_near, double* S_dev,
                    void* stream) {
     if (!h) return FL_EINVAL;
+    if (h->sym_K) return fl::sym_unsupported(h, "fl_strong_form");
     h->err.clear();
     try {
         return fl::strong_form(h, s, u_dev, k_cell, k_edge, k_near, S_dev, (cudaStream_t)stream);
@@ -238,6 +339,7 @@ int fl_strong_form(fl_handle h, double s, const double* u_dev, int k_cell, int k
 int fl_br_indicators(fl_handle h, double s, const double* u_dev, const double* f_nodal_dev, int k_cell, int k_edge,
                      int k_near, double* eta_dev, double* S_dev, void* stream) {
     if (!h) return FL_EINVAL;
+    if (h->sym_K) return fl::sym_unsupported(h, "fl_br_indicators");
     h->err.clear();
     try {
         return fl::br_indicators(h, s, u_dev, f_nodal_dev, k_cell, k_edge, k_near, eta_dev, S_dev,
@@ -250,6 +352,7 @@ int fl_br_indicators(fl_handle h, double s, const double* u_dev, const double* f
 int fl_mark_max(fl_handle h, double s, const double* eta_dev, double theta, uint8_t* dof_marks_dev,
                 uint8_t* cell_marks_dev, void* stream) {
     if (!h) return FL_EINVAL;
+    if (h->sym_K) return fl::sym_unsupported(h, "fl_mark_max");
     h->err.clear();
     return fl::mark_max(h, s, eta_dev, theta, dof_marks_dev, cell_marks_dev, (cudaStream_t)stream);
 }
@@ -286,7 +389,7 @@ int fl_get_stats(fl_handle h, double s, fl_stats* st) {
     o.n_cells = P.nc;
     o.n_vertices = P.nv;
     o.n_facets = P.nf;
-    o.n_dofs = P.n;
+    o.n_dofs = P.sym_K ? P.n_red : P.n;
     o.n_tiles = (int64_t)P.tiles.size() / 2;
     o.n_touch_pairs = (int64_t)P.tp_type.size();
     o.n_near_pairs = (int64_t)P.np_a.size();

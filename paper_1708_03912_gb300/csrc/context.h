@@ -107,6 +107,10 @@ struct DevTables {
     bool rule32_ready = false;   // the float32 copy matches them
     std::vector<double> rule_host;
     RuleOffsets rule_ro{};
+    // symmetry reduction (Plan::sym_K > 0)
+    int *red_rep = nullptr, *red_ptr = nullptr, *red_mem = nullptr, *red_row = nullptr;
+    int64_t* tri_list = nullptr;
+    int* sector_of = nullptr;  // whole vertex -> the sector vertex it copies
     // strong form of the adaptive loop (adaptive.cu), built on first use
     bool sf_ready = false;
     int64_t sf_nfac = 0, sf_nint = 0;  // facets; the first sf_nint are interior
@@ -156,6 +160,13 @@ struct fl_ctx {
     void* batch_host = nullptr;   // pinned scalars of the batched solver
     void* sf_ws = nullptr;        // strong-form workspace (device), grown on demand
     size_t sf_ws_bytes = 0;
+    // symmetry reduction (fl_create_sector): the mesh is sym_K rotated copies of a sector
+    int sym_K = 0;
+    int64_t sym_nvs = 0;            // sector vertices
+    std::vector<int> sym_vmap;      // sym_K * sym_nvs: whole vertex of copy l of sector vertex v
+    int* sym_sector_of = nullptr;   // device, whole vertex -> a sector vertex it copies
+    void* sym_ws = nullptr;         // reduced-assembly workspace (representatives' rows), grown on demand
+    size_t sym_ws_bytes = 0;
 };
 
 namespace fl {
@@ -163,6 +174,8 @@ namespace fl {
 void count_launch(int n = 1);
 // returns plan index for order s (building it on demand); -1 on error (h->err set)
 int plan_for(fl_ctx* h, double s);
+// FL_ENOTIMPL with a message for calls that do not take a symmetry-reduced handle
+int sym_unsupported(fl_ctx* h, const char* what);
 // device copies of plan pi's tables (uploaded once per handle and plan)
 int ensure_device_tables(fl_ctx* h, int pi, cudaStream_t st);
 // caching allocator (pool.cpp): device and pinned host blocks reused across handles

@@ -290,6 +290,7 @@ int fl_cluster_plan(fl_handle h, double s, double eta, int leaf, int64_t* sizes,
                     int32_t* far, int32_t* near) {
     if (!h || !sizes) return FL_EINVAL;
     h->err.clear();
+    if (h->sym_K) return sym_unsupported(h, "fl_cluster_plan");
     const int pi = plan_for(h, s);
     if (pi < 0) return FL_EINVAL;
     ClusterPlan C;
@@ -324,6 +325,7 @@ int fl_hmatrix_create(fl_handle h, double s, int m, double eta, int leaf, fl_hma
     if (!h || !out) return FL_EINVAL;
     h->err.clear();
     *out = nullptr;
+    if (h->sym_K) return sym_unsupported(h, "fl_hmatrix_create");
     if (m < 1 || m > 12) return set_err(h, FL_EINVAL, "Chebyshev order m must lie in [1, 12]");
     const int pi = plan_for(h, s);
     if (pi < 0) return FL_EINVAL;

@@ -77,11 +77,29 @@ struct Plan {
     std::vector<int> csr_col;
     std::vector<int64_t> g_ptr;      // nnz + 1
     std::vector<int64_t> g_slot;
+    // ----- symmetry reduction (fl_create_sector; symmetry.cpp) -----
+    int sym_K = 0;                   // > 0: the mesh is K rotated copies of a sector
+    int64_t n_red = 0;               // orbits of the DOFs (the reduced problem's size)
+    std::vector<int> red_rep;        // n_red: the whole DOF whose row represents orbit r
+    std::vector<int> red_ptr, red_mem;  // orbit -> its whole DOFs, ascending
+    std::vector<int> red_row;        // whole DOF -> r if it represents orbit r, else -1
+    std::vector<int> red_vertex;     // n_red: the sector vertex of orbit r
+    std::vector<int64_t> tri_list;   // upper-triangle tile index -> position in tiles, or -1
 };
 
-// Builds the mesh part (orientation, facets, adjacency, spatial order).
-int plan_mesh(Plan& P, int dim, int64_t nv, const double* V, int64_t nc, const int32_t* C, std::string& err);
+// Builds the mesh part (orientation, facets, adjacency, spatial order: Morton order of the cell
+// centroids, with the cells flagged in `first`, if given, ahead of the rest).
+int plan_mesh(Plan& P, int dim, int64_t nv, const double* V, int64_t nc, const int32_t* C, std::string& err,
+              const std::vector<char>* first = nullptr);
 // Builds the DOF-dependent part.
 int plan_dofs(Plan& P, int paper_all, std::string& err);
+// Symmetry reduction (symmetry.cpp).  replicate_sector: the K copies of a sector mesh rotated by
+// 2 pi l / K about the origin, vertices closer than 1e-10 in both coordinates merged (the
+// earliest one kept), cells copy by copy; vmap[l * nv + v] = whole vertex of copy l of v.
+void replicate_sector(int64_t nv, const double* V, int64_t nc, const int32_t* C, int K, std::vector<double>& W,
+                      std::vector<int32_t>& CW, std::vector<int>& vmap);
+// The orbits of P's DOFs (needs plan_dofs first) and the tiles restricted to the blocks
+// holding a cell of a representative's support; vmap as from replicate_sector.
+int plan_symmetry(Plan& P, int K, int64_t nvs, const std::vector<int>& vmap, std::string& err);
 
 }  // namespace fl

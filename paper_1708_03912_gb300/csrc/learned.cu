@@ -429,6 +429,7 @@ extern "C" {
 
 int fl_patches(fl_handle h, double s, int K, int32_t* nbr_host, double* hlen_host, int32_t* hop_host) {
     if (!h || K < 1 || K > 20) return FL_EINVAL;
+    if (h->sym_K) return sym_unsupported(h, "fl_patches");
     const int pi = plan_for(h, s);
     if (pi < 0) return FL_EINVAL;
     const Plan& P = h->plan[pi];
@@ -489,6 +490,7 @@ int fl_patches(fl_handle h, double s, int K, int32_t* nbr_host, double* hlen_hos
 
 int fl_lp_create(fl_lp_handle* out, fl_handle mesh, double s, int K, int hidden, uint64_t seed) {
     if (!out || !mesh) return FL_EINVAL;
+    if (mesh->sym_K) return sym_unsupported(mesh, "fl_lp_create");
     if (K != KK || hidden != HH) return FL_ENOTIMPL;  // the kernels are compiled for K = 12, width 64
     fl_lp* m = new (std::nothrow) fl_lp;
     if (!m) return FL_ENOMEM;

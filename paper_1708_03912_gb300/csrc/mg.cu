@@ -421,6 +421,7 @@ extern "C" {
 int fl_prolongation(fl_handle fine, fl_handle coarse, double s, int64_t* nnz, int32_t* rowptr, int32_t* col,
                     double* val) {
     if (!fine || !coarse || !nnz) return FL_EINVAL;
+    if (fine->sym_K || coarse->sym_K) return sym_unsupported(fine->sym_K ? fine : coarse, "fl_prolongation");
     if (fine->dim != coarse->dim) return set_err(fine, FL_EINVAL, "meshes of different dimension");
     const int pf = plan_for(fine, s), pc = plan_for(coarse, s);
     if (pf < 0) return FL_EINVAL;

@@ -100,7 +100,8 @@ static uint32_t spread16(uint32_t x) {
     return x;
 }
 
-int plan_mesh(Plan& P, int dim, int64_t nv, const double* V, int64_t nc, const int32_t* C, std::string& err) {
+int plan_mesh(Plan& P, int dim, int64_t nv, const double* V, int64_t nc, const int32_t* C, std::string& err,
+              const std::vector<char>* first) {
     if (dim != 1 && dim != 2) { err = "dim must be 1 or 2"; return FL_EINVAL; }
     if (nv < dim + 1 || nc < 1 || !V || !C) { err = "empty mesh or NULL arrays"; return FL_EINVAL; }
     if (nv > (1LL << 30) || nc > (1LL << 29)) { err = "mesh too large"; return FL_EINVAL; }
@@ -236,6 +237,8 @@ int plan_mesh(Plan& P, int dim, int64_t nv, const double* V, int64_t nc, const i
         key[k] = ((uint64_t)z << 32) | (uint64_t)k;
     }
     std::sort(key.begin(), key.end());
+    // cells flagged `first` ahead of the others, each part in Morton order
+    if (first) std::stable_partition(key.begin(), key.end(), [&](uint64_t x) { return (*first)[x & 0xffffffffu] != 0; });
     P.perm.resize(nc);
     P.iperm.resize(nc);
     for (int64_t i = 0; i < nc; ++i) {

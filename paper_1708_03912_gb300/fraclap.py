@@ -22,7 +22,7 @@ FL_F64, FL_F32, FL_BF16, FL_F32X2 = 0, 1, 2, 3
 _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOTSPD", 5: "FL_ENOTCONV",
           6: "FL_ETIMEOUT", 7: "FL_ENOTIMPL"}
 
-EXPORTS = ["fl_default_options", "fl_create", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
+EXPORTS = ["fl_default_options", "fl_create", "fl_create_sector", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
            "fl_assemble", "fl_tune_assemble", "fl_set_far_variant", "fl_assemble_nearfield_csr", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
            "fl_heat_matrix", "fl_mass_apply", "fl_strong_form", "fl_br_indicators", "fl_mark_max", "fl_refine",
            "fl_cluster_plan", "fl_hmatrix_create", "fl_hmatrix_set_near",
@@ -135,6 +135,8 @@ def lib():
     L.fl_heat_matrix.restype = ci
     L.fl_mass_apply.argtypes = [vp, dbl, ci, dbl, vp, i64, dbl, vp, i64, vp, i64, vp]
     L.fl_mass_apply.restype = ci
+    L.fl_create_sector.argtypes = [ctypes.POINTER(ctypes.c_void_p), i64, vp, i64, vp, ci, vp]
+    L.fl_create_sector.restype = ci
     L.fl_strong_form.argtypes = [vp, dbl, vp, ci, ci, ci, vp, vp]
     L.fl_strong_form.restype = ci
     L.fl_br_indicators.argtypes = [vp, dbl, vp, vp, ci, ci, ci, vp, vp, vp]
@@ -300,6 +302,17 @@ def fl_create(vertices, cells, dof_mode=FL_DOF_INTERIOR, options=None):
     r = lib().fl_create(ctypes.byref(h), V.shape[1], V.shape[0], V.ctypes.data, C.shape[0], C.ctypes.data, dof_mode,
                         ctypes.byref(opt))
     _check(r, None)
+    return h
+
+
+def fl_create_sector(vertices, cells, K, options=None):
+    """Handle of the symmetry-reduced problem on the K rotated copies of a sector mesh."""
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    C = np.ascontiguousarray(cells, dtype=np.int32)
+    h = ctypes.c_void_p()
+    opt = options if options is not None else fl_default_options()
+    _check(lib().fl_create_sector(ctypes.byref(h), V.shape[0], V.ctypes.data, C.shape[0], C.ctypes.data, K,
+                                  ctypes.byref(opt)), None)
     return h
 
 
@@ -867,6 +880,19 @@ class Mesh:
         o.far_f64_pipe = int(far_f64_pipe)
         self.h = fl_create(vertices, cells, FL_DOF_PAPER if dof_mode == "paper" else FL_DOF_INTERIOR, o)
         self.dim = 1 if np.asarray(vertices).ndim == 1 else np.asarray(vertices).shape[1]
+
+    @classmethod
+    def sector(cls, vertices, cells, K, k_far=4, k_near=6, k_touch=8, k_bnd=8, k_vertex=6, far_f64_pipe=False):
+        """The symmetry-reduced problem (Section 7): the sector mesh's K rotated copies, one
+        unknown per orbit; assemble / load_vector / solve then work on the reduced system
+        (load_vector takes f on the sector's vertices)."""
+        m = cls.__new__(cls)
+        o = fl_default_options()
+        o.k_far, o.k_near, o.k_touch, o.k_bnd, o.k_vertex = k_far, k_near, k_touch, k_bnd, k_vertex
+        o.far_f64_pipe = int(far_f64_pipe)
+        m.h = fl_create_sector(vertices, cells, K, o)
+        m.dim = 2
+        return m
 
     def close(self):
         if self.h:
