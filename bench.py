@@ -589,6 +589,53 @@ def adaptive_section(F, synth, timed, peaks, sms, m, A, b, n_el):
     return out
 
 
+def symmetry_section(F, synth, timed):
+    """Section 7's periodic example: f = f_{2,8} on the unit disc, reduced to the sector
+    0 <= phi <= pi/4 (K = 8) and solved there; against the same disc meshed whole.  The
+    energy error is ||u - u_h||^2 = <f, u> - <f, u_h> with <f, u> in closed form (Gauss-Jacobi)."""
+    import numpy as np
+    import torch
+    from scipy import special
+
+    K, M, s = 8, 64, 0.5
+    V, T = synth.sector(K, M)
+    lam = 2 ** (2 * s) * special.gamma(3 + s) * special.gamma(11 + s) / (special.gamma(3) * special.gamma(11))
+
+    def f28(P):
+        r2 = np.sum(P ** 2, axis=1)
+        return lam * r2 ** 4 * np.cos(8 * np.arctan2(P[:, 1], P[:, 0])) * special.eval_jacobi(2, s, 8, 2 * r2 - 1)
+
+    x, w = special.roots_jacobi(10, s, 0.0)
+    fu = lam * np.pi / 2 * 2 ** (-s - 1) * np.sum(w * ((1 + x) / 2) ** 8 * special.eval_jacobi(2, s, 8, x) ** 2)
+    out = {"workload": f"sector 0 <= phi <= pi/4 of the unit disc, {len(T)} cells (whole disc {K * len(T)}), "
+                       f"s = {s}, f = f_2,8 (nodal), k_eff over K = {K} copies"}
+    ms = F.Mesh.sector(V, T, K)
+    Ar = ms.assemble(s)
+    out["reduced"] = {"n": Ar.shape[0], "tiles": F.fl_get_stats(ms.h, s)["n_tiles"],
+                      "assembly_ms": timed(lambda: ms.assemble(s, out=Ar), reps=2, flush_between=False)}
+    br = ms.load_vector(s, torch.tensor(f28(V), device="cuda"))
+    ur, info = ms.solve(Ar, br, tol=1e-10)
+    out["reduced"]["solve_ms"] = timed(lambda: ms.solve(Ar, br, tol=1e-10), reps=2, flush_between=False)
+    out["reduced"]["cg_iterations"] = info.iterations
+    out["reduced"]["energy_error"] = float(np.sqrt(max(fu - K * float(br @ ur), 0.0)))
+    del Ar
+    W, C = synth.rotated_copies(V, T, K)
+    mw = F.Mesh(W, C)
+    Aw = mw.assemble(s)
+    out["whole"] = {"n": Aw.shape[0], "tiles": F.fl_get_stats(mw.h, s)["n_tiles"],
+                    "assembly_ms": timed(lambda: mw.assemble(s, out=Aw), reps=2, flush_between=False)}
+    bw = mw.load_vector(s, torch.tensor(f28(W), device="cuda"))
+    uw, iw = mw.solve(Aw, bw, tol=1e-10)
+    out["whole"]["solve_ms"] = timed(lambda: mw.solve(Aw, bw, tol=1e-10), reps=2, flush_between=False)
+    out["whole"]["cg_iterations"] = iw.iterations
+    out["whole"]["energy_error"] = float(np.sqrt(max(fu - float(bw @ uw), 0.0)))
+    out["assembly_speedup"] = out["whole"]["assembly_ms"] / out["reduced"]["assembly_ms"]
+    out["solve_speedup"] = out["whole"]["solve_ms"] / out["reduced"]["solve_ms"]
+    ms.close()
+    mw.close()
+    return out
+
+
 def lshape_precond_section(F, synth, timed, A, b, h5):
     """Preconditioners on the headline system (L-shape level 5, s = 1/2, f = 1, tol 1e-8):
     Jacobi-PCG, multigrid-preconditioned CG on the nested levels 5..2, flexible CG with the
@@ -809,6 +856,7 @@ def main():
         line["lshape"]["hmatrix"] = hmatrix_section(F, timed, A, m.h)
         line["lshape"]["adaptive"] = adaptive_section(F, synth, timed, peaks, sms, m, A, b, n_el)
         line["heat"] = heat_section(F, synth, timed)
+        line["symmetry"] = symmetry_section(F, synth, timed)
         line["matvec"] = matvec_section(F, timed, peaks, A, A32)
         line["interval"] = interval_section(F, synth, timed)
         line["disc"] = disc_section(F, synth, timed)

@@ -142,6 +142,26 @@ def sector(K: int, M: int):
     return np.array(pts, dtype=np.float64), np.array(tris, dtype=np.int32)
 
 
+def rotated_copies(V, T, K: int):
+    """The K copies of a sector mesh rotated by 2 pi l / K about the origin, coincident
+    vertices (the cut rays, the centre) merged: the whole mesh the sector stands for."""
+    V = np.asarray(V, dtype=np.float64)
+    pts, idx = [], {}
+    cells = []
+    for l in range(K):
+        c, s_ = math.cos(2 * math.pi * l / K), math.sin(2 * math.pi * l / K)
+        vid = []
+        for x, y in V:
+            p = (c * x - s_ * y, s_ * x + c * y)
+            key = (round(p[0], 9), round(p[1], 9))
+            if key not in idx:
+                idx[key] = len(pts)
+                pts.append(p)
+            vid.append(idx[key])
+        cells.extend([vid[a], vid[b], vid[d]] for a, b, d in np.asarray(T))
+    return np.array(pts, dtype=np.float64), np.array(cells, dtype=np.int32)
+
+
 def square(m: int, jitter: float = 0.0, seed: int = SEED, lo: float = -1.0, hi: float = 1.0):
     """Structured triangulation of [lo,hi]^2 with m x m cells, interior vertices jittered.
 
