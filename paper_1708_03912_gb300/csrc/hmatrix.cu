@@ -15,6 +15,11 @@
 //   downward     yh_son += S_son yh_f, and y_i += -C sum_alpha (int phi_i L_alpha) yh_leaf.
 // Cluster tree and partition: cluster.cpp (host).  Every sum runs in a fixed order, so the
 // product is bitwise reproducible; all arithmetic is float64.
+// Schedule: the near-field product runs on a second stream beside the far-field chain; the
+// passes take one launch per direction below a split level (one block per subtree walks all
+// of its levels) and one above it (one block walks the top levels); the couplings are pair
+// products followed by per-node sums; the whole product is captured once per (x, y) as a
+// CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,16 +43,33 @@ struct fl_hm {
     int *perm = nullptr, *leaf_of = nullptr, *parent = nullptr;
     int *lo_d = nullptr, *hi_d = nullptr, *son_d = nullptr;
     double *center = nullptr, *side = nullptr;
-    double *coef = nullptr, *shift = nullptr, *kmat = nullptr;
+    double *coef = nullptr, *shift = nullptr, *shiftT = nullptr, *kmat = nullptr;
     int *far_ptr = nullptr, *far_tau = nullptr;
-    int *up_nodes = nullptr, *down_nodes = nullptr, *leaves = nullptr;
-    std::vector<int> up_off, down_off;  // per level offsets (host)
+    int* leaves = nullptr;
+    // the passes in four launches: the tree splits at level `split`; below it one block per
+    // subtree walks all its levels, above it one block walks the top levels
+    int split = 0, nsub = 0, sub_levels = 0, ntop_up = 0, ntop_down = 0;
+    int *sub_off = nullptr, *sub_nodes = nullptr;           // per subtree and level: its nodes
+    int *top_up_off = nullptr, *top_up = nullptr;           // internal nodes above the split, deepest level first
+    int *top_down_off = nullptr, *top_down = nullptr;       // nodes of levels 1..split
     int nleaves = 0, nsig = 0;
     int* sig_nodes = nullptr;  // nodes with admissible partners, in node order
     int *nz_ptr = nullptr, *nz_row = nullptr, *nz_col = nullptr;
     double* nz_val = nullptr;
     bool near_ready = false;
     double *xh = nullptr, *yh = nullptr;
+    double* Pb = nullptr;  // per admissible pair: K_b xh[tau]
+    // products captured as CUDA graphs, keyed by (x, y): the near-field product runs on a second
+    // stream beside the chain of small far-field launches, and the graph launches them at once
+    struct Graph {
+        const double* x;
+        double* y;
+        cudaGraphExec_t exec;
+        int launches;  // kernels the graph holds
+    };
+    std::vector<Graph> graphs;
+    cudaStream_t cap = nullptr, side_st = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
 };
 
@@ -152,22 +174,24 @@ __global__ void leaf_coef_kernel(int64_t n, int d, int m, int md, const int* per
     coef[p * md + alpha] = acc;
 }
 
-// shift coefficients S_son[beta][alpha] = L_alpha^father(xi_beta^son), one thread per entry
+// shift coefficients S_son[beta][alpha] = L_alpha^father(xi_beta^son), one thread per entry, and
+// their transpose ST_son[alpha][beta] (the downward pass reads them along beta)
 __global__ void shift_kernel(int nodes, int d, int m, int md, const int* parent, const double* center,
-                             const double* side, double* S) {
+                             const double* side, double* S, double* ST) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)nodes * md * md) return;
     const int c = (int)(t / ((int64_t)md * md));
     const int r = (int)(t - (int64_t)c * md * md);
     const int beta = r / md, alpha = r - beta * md;
     const int f = parent[c];
-    if (f < 0) {
-        S[t] = 0.0;
-        return;
+    double v = 0.0;
+    if (f >= 0) {
+        double x[2];
+        cheb_point_d(center + (int64_t)c * d, side[c], m, d, beta, x);
+        v = lagrange_d(center + (int64_t)f * d, side[f], m, d, alpha, x);
     }
-    double x[2];
-    cheb_point_d(center + (int64_t)c * d, side[c], m, d, beta, x);
-    S[t] = lagrange_d(center + (int64_t)f * d, side[f], m, d, alpha, x);
+    S[t] = v;
+    ST[(int64_t)c * md * md + (int64_t)alpha * md + beta] = v;
 }
 
 // kernel matrices of the admissible pairs, in sigma-major order: K[b][alpha][beta]
@@ -199,9 +223,20 @@ __global__ void near_spmv_kernel(int64_t n, const int* ptr, const int* col, cons
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
-    double acc = 0.0;
-    for (int e = ptr[row] + lane; e < ptr[row + 1]; e += 32) acc = fma(val[e], x[col[e]], acc);
-    acc = warp_sum(acc);
+    // four entries per lane in flight, four accumulators
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    const int e1 = ptr[row + 1];
+    int e = ptr[row] + lane;
+    for (; e + 96 < e1; e += 128) {
+        const double v0 = __ldcs(val + e), v1 = __ldcs(val + e + 32), v2 = __ldcs(val + e + 64), v3 = __ldcs(val + e + 96);
+        const int c0 = __ldcs(col + e), c1 = __ldcs(col + e + 32), c2 = __ldcs(col + e + 64), c3 = __ldcs(col + e + 96);
+        a0 = fma(v0, x[c0], a0);
+        a1 = fma(v1, x[c1], a1);
+        a2 = fma(v2, x[c2], a2);
+        a3 = fma(v3, x[c3], a3);
+    }
+    for (; e < e1; e += 32) a0 = fma(val[e], x[col[e]], a0);
+    const double acc = warp_sum((a0 + a1) + (a2 + a3));
     if (lane == 0) y[row] = acc;
 }
 
@@ -217,48 +252,117 @@ __global__ void up_leaf_kernel(int nleaves, int md, const int* leaves, const int
     xh[(int64_t)c * md + alpha] = acc;
 }
 
-// upward pass on one level of fathers: xh[f][alpha] = sum_sons sum_beta S_son[beta][alpha] xh[son][beta]
-__global__ void up_level_kernel(int count, int md, const int* nodes, const int* son, const double* S, double* xh) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)count * md) return;
-    const int f = nodes[t / md];
-    const int alpha = (int)(t % md);
-    double acc = 0.0;
-    for (int q = 0; q < 2; ++q) {
-        const int c = son[2 * f + q];
-        const double* Sc = S + (int64_t)c * md * md;
-        for (int beta = 0; beta < md; ++beta) acc = fma(Sc[(int64_t)beta * md + alpha], xh[(int64_t)c * md + beta], acc);
+// Products with the md x md matrices of the passes: MD > 0 fixes md at compile time (the loops
+// unroll, four accumulators keep loads in flight), MD = 0 takes md.  Threads of one node are
+// consecutive in alpha (beta), and every matrix is laid out so that they read consecutive
+// addresses.
+template <int MD>
+__device__ __forceinline__ double dot_strided(const double* __restrict__ Mx, int64_t stride, const double* __restrict__ v,
+                                              int md) {
+    const int n = MD ? MD : md;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int k = 0;
+#pragma unroll
+    for (; k + 4 <= n; k += 4) {
+        a0 = fma(Mx[(int64_t)k * stride], v[k], a0);
+        a1 = fma(Mx[(int64_t)(k + 1) * stride], v[k + 1], a1);
+        a2 = fma(Mx[(int64_t)(k + 2) * stride], v[k + 2], a2);
+        a3 = fma(Mx[(int64_t)(k + 3) * stride], v[k + 3], a3);
     }
-    xh[(int64_t)f * md + alpha] = acc;
+    for (; k < n; ++k) a0 = fma(Mx[(int64_t)k * stride], v[k], a0);
+    return (a0 + a1) + (a2 + a3);
 }
 
-// couplings: yh[sigma][alpha] = sum over sigma's admissible partners of K xh[tau]
-__global__ void couple_kernel(int nsig, int md, const int* sig_nodes, const int* far_ptr, const int* far_tau,
-                              const double* K, const double* xh, double* yh) {
+// couplings, in two fully parallel steps: per admissible pair b = (sigma, tau) and alpha,
+// Pb[b][alpha] = sum_beta K_b[alpha][beta] xh[tau][beta]; then per (sigma, alpha)
+// yh[sigma][alpha] = sum over sigma's pairs, in pair order, of Pb[b][alpha]
+template <int MD>
+__global__ void pair_product_kernel(int nfar, int md_rt, const int* far_tau, const double* K, const double* xh,
+                                    double* Pb) {
+    const int md = MD ? MD : md_rt;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nfar * md) return;
+    const int64_t b = t / md;
+    const int alpha = (int)(t - b * md);
+    Pb[t] = dot_strided<MD>(K + b * md * md + (int64_t)alpha * md, 1, xh + (int64_t)far_tau[b] * md, md);
+}
+
+__global__ void couple_sum_kernel(int nsig, int md, const int* sig_nodes, const int* far_ptr, const double* Pb,
+                                  double* yh) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)nsig * md) return;
     const int sgm = sig_nodes[t / md];
     const int alpha = (int)(t % md);
     double acc = 0.0;
-    for (int b = far_ptr[sgm]; b < far_ptr[sgm + 1]; ++b) {
-        const double* Kb = K + (int64_t)b * md * md + (int64_t)alpha * md;
-        const double* xt = xh + (int64_t)far_tau[b] * md;
-        for (int beta = 0; beta < md; ++beta) acc = fma(Kb[beta], xt[beta], acc);
-    }
+    for (int b = far_ptr[sgm]; b < far_ptr[sgm + 1]; ++b) acc += Pb[(int64_t)b * md + alpha];
     yh[(int64_t)sgm * md + alpha] = acc;
 }
 
-// downward pass on one level: yh[c][beta] += sum_alpha S_c[beta][alpha] yh[father][alpha]
-__global__ void down_level_kernel(int count, int md, const int* nodes, const int* parent, const double* S, double* yh) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)count * md) return;
-    const int c = nodes[t / md];
-    const int beta = (int)(t % md);
-    const int f = parent[c];
-    const double* Sc = S + (int64_t)c * md * md + (int64_t)beta * md;
-    double acc = yh[(int64_t)c * md + beta];
-    for (int alpha = 0; alpha < md; ++alpha) acc = fma(Sc[alpha], yh[(int64_t)f * md + alpha], acc);
-    yh[(int64_t)c * md + beta] = acc;
+// the upward pass of a list of levels (in order) in one block: xh[f] for the internal nodes
+template <int MD>
+__device__ __forceinline__ void up_levels(int nlev, const int* off, const int* nodes, int md, const int* son,
+                                          const double* S, double* xh) {
+    for (int j = 0; j < nlev; ++j) {
+        const int lo = off[j], cnt = off[j + 1] - lo;
+        for (int t = threadIdx.x; t < cnt * md; t += blockDim.x) {
+            const int f = nodes[lo + t / md];
+            if (son[2 * f] < 0) continue;
+            const int alpha = t % md;
+            double acc = 0.0;
+            for (int q = 0; q < 2; ++q) {
+                const int c = son[2 * f + q];
+                acc += dot_strided<MD>(S + (int64_t)c * md * md + alpha, md, xh + (int64_t)c * md, md);
+            }
+            xh[(int64_t)f * md + alpha] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// the downward pass of a list of levels (in order) in one block: yh[c] += ST_c yh[parent]
+template <int MD>
+__device__ __forceinline__ void down_levels(int nlev, const int* off, const int* nodes, int md, const int* parent,
+                                            const double* ST, double* yh) {
+    for (int j = 0; j < nlev; ++j) {
+        const int lo = off[j], cnt = off[j + 1] - lo;
+        for (int t = threadIdx.x; t < cnt * md; t += blockDim.x) {
+            const int c = nodes[lo + t / md];
+            const int beta = t % md;
+            yh[(int64_t)c * md + beta] +=
+                dot_strided<MD>(ST + (int64_t)c * md * md + beta, md, yh + (int64_t)parent[c] * md, md);
+        }
+        __syncthreads();
+    }
+}
+
+// subtree k (one block): its levels from the deepest up to its root
+template <int MD>
+__global__ void up_sub_kernel(int nlev, int md_rt, const int* sub_off, const int* sub_nodes, const int* son,
+                              const double* S, double* xh) {
+    const int md = MD ? MD : md_rt;
+    const int* off = sub_off + (int64_t)blockIdx.x * (nlev + 1);
+    // levels stored root first: walk them backwards through a reversed offset view
+    for (int j = nlev - 1; j >= 0; --j) up_levels<MD>(1, off + j, sub_nodes, md, son, S, xh);
+}
+
+template <int MD>
+__global__ void up_top_kernel(int nlev, int md_rt, const int* off, const int* nodes, const int* son, const double* S,
+                              double* xh) {
+    up_levels<MD>(nlev, off, nodes, MD ? MD : md_rt, son, S, xh);
+}
+
+template <int MD>
+__global__ void down_top_kernel(int nlev, int md_rt, const int* off, const int* nodes, const int* parent,
+                                const double* ST, double* yh) {
+    down_levels<MD>(nlev, off, nodes, MD ? MD : md_rt, parent, ST, yh);
+}
+
+// subtree k (one block): its levels below its root, top down
+template <int MD>
+__global__ void down_sub_kernel(int nlev, int md_rt, const int* sub_off, const int* sub_nodes, const int* parent,
+                                const double* ST, double* yh) {
+    const int* off = sub_off + (int64_t)blockIdx.x * (nlev + 1);
+    down_levels<MD>(nlev - 1, off + 1, sub_nodes, MD ? MD : md_rt, parent, ST, yh);
 }
 
 // leaves to DOFs: y[perm[p]] += mC sum_alpha coef[p][alpha] yh[leaf][alpha]
@@ -313,11 +417,16 @@ int fl_cluster_plan(fl_handle h, double s, double eta, int leaf, int64_t* sizes,
 
 void fl_hmatrix_destroy(fl_hmatrix H) {
     if (!H) return;
-    if (!H->bufs.empty()) {
+    if (!H->bufs.empty() || !H->graphs.empty()) {
         cudaSetDevice(H->device);
         cudaDeviceSynchronize();
         for (void* p : H->bufs) pool_dev_free(p);
     }
+    for (auto& g : H->graphs) cudaGraphExecDestroy(g.exec);
+    if (H->cap) cudaStreamDestroy(H->cap);
+    if (H->side_st) cudaStreamDestroy(H->side_st);
+    if (H->ev_fork) cudaEventDestroy(H->ev_fork);
+    if (H->ev_join) cudaEventDestroy(H->ev_join);
     delete H;
 }
 
@@ -365,19 +474,50 @@ int fl_hmatrix_create(fl_handle h, double s, int m, double eta, int leaf, fl_hma
         }
         // level lists: fathers for the upward pass (deepest first), non-root nodes for the
         // downward pass (shallowest first)
-        std::vector<int> up, down;
-        H->up_off.assign(1, 0);
-        for (int L = C.depth - 1; L >= 0; --L) {
+        // split level: the first holding at least 64 nodes (the deepest if none does)
+        std::vector<int> per_level(C.depth + 1, 0);
+        for (int c = 0; c < nn; ++c) ++per_level[C.level[c]];
+        int Ls = C.depth;
+        for (int L = 0; L <= C.depth; ++L)
+            if (per_level[L] >= 64) {
+                Ls = L;
+                break;
+            }
+        H->split = Ls;
+        std::vector<int> top_up, top_up_off(1, 0), top_down, top_down_off(1, 0);
+        for (int L = Ls - 1; L >= 0; --L) {
             for (int c = 0; c < nn; ++c)
-                if (C.level[c] == L && C.son[2 * c] >= 0) up.push_back(c);
-            H->up_off.push_back((int)up.size());
+                if (C.level[c] == L && C.son[2 * c] >= 0) top_up.push_back(c);
+            top_up_off.push_back((int)top_up.size());
         }
-        H->down_off.assign(1, 0);
-        for (int L = 1; L <= C.depth; ++L) {
+        for (int L = 1; L <= Ls; ++L) {
             for (int c = 0; c < nn; ++c)
-                if (C.level[c] == L) down.push_back(c);
-            H->down_off.push_back((int)down.size());
+                if (C.level[c] == L) top_down.push_back(c);
+            top_down_off.push_back((int)top_down.size());
         }
+        H->ntop_up = Ls;
+        H->ntop_down = Ls;
+        // subtrees rooted at the split level, their nodes level by level (root first)
+        const int NL = C.depth - Ls + 1;
+        std::vector<int> sub_nodes, sub_off;
+        for (int r = 0; r < nn; ++r) {
+            if (C.level[r] != Ls) continue;
+            std::vector<int> cur(1, r), nxt;
+            for (int j = 0; j < NL; ++j) {
+                sub_off.push_back((int)sub_nodes.size());
+                sub_nodes.insert(sub_nodes.end(), cur.begin(), cur.end());
+                nxt.clear();
+                for (int c : cur)
+                    if (C.son[2 * c] >= 0) {
+                        nxt.push_back(C.son[2 * c]);
+                        nxt.push_back(C.son[2 * c + 1]);
+                    }
+                cur.swap(nxt);
+            }
+            sub_off.push_back((int)sub_nodes.size());
+            ++H->nsub;
+        }
+        H->sub_levels = NL;
         // admissible pairs grouped by sigma (in node order; within sigma in partition order)
         const int nfar = (int)C.far.size() / 2;
         std::vector<int> far_ptr(nn + 1, 0), far_sig(nfar), far_tau(nfar), sig_nodes;
@@ -424,7 +564,10 @@ int fl_hmatrix_create(fl_handle h, double s, int m, double eta, int leaf, fl_hma
             (rc = hm_upload(H, &d_hi, hi, st)) || (rc = hm_upload(H, &d_son, son, st)) ||
             (rc = hm_upload(H, &H->far_ptr, far_ptr, st)) || (rc = hm_upload(H, &H->far_tau, far_tau, st)) ||
             (rc = hm_upload(H, &d_far_sig, far_sig, st)) || (rc = hm_upload(H, &H->sig_nodes, sig_nodes, st)) ||
-            (rc = hm_upload(H, &H->up_nodes, up, st)) || (rc = hm_upload(H, &H->down_nodes, down, st)) ||
+            (rc = hm_upload(H, &H->sub_off, sub_off, st)) || (rc = hm_upload(H, &H->sub_nodes, sub_nodes, st)) ||
+            (rc = hm_upload(H, &H->top_up_off, top_up_off, st)) || (rc = hm_upload(H, &H->top_up, top_up, st)) ||
+            (rc = hm_upload(H, &H->top_down_off, top_down_off, st)) ||
+            (rc = hm_upload(H, &H->top_down, top_down, st)) ||
             (rc = hm_upload(H, &H->leaves, leaves, st)) || (rc = hm_upload(H, &H->nz_ptr, nz_ptr, st)) ||
             (rc = hm_upload(H, &H->nz_row, nz_row, st)) || (rc = hm_upload(H, &H->nz_col, nz_col, st)) ||
             (rc = hm_upload(H, &d_lam, R.lam, st)) || (rc = hm_upload(H, &d_w, R.w, st)))
@@ -433,15 +576,17 @@ int fl_hmatrix_create(fl_handle h, double s, int m, double eta, int leaf, fl_hma
         H->hi_d = d_hi;
         H->son_d = d_son;
         if ((rc = hm_alloc(H, &H->coef, (size_t)n * md)) || (rc = hm_alloc(H, &H->shift, (size_t)nn * md * md)) ||
+            (rc = hm_alloc(H, &H->shiftT, (size_t)nn * md * md)) ||
             (rc = hm_alloc(H, &H->kmat, (size_t)nfar * md * md)) || (rc = hm_alloc(H, &H->xh, (size_t)nn * md)) ||
-            (rc = hm_alloc(H, &H->yh, (size_t)nn * md)) || (rc = hm_alloc(H, &H->nz_val, (size_t)H->nnz)))
+            (rc = hm_alloc(H, &H->yh, (size_t)nn * md)) ||
+            (rc = hm_alloc(H, &H->Pb, (size_t)std::max(nfar, 1) * md)) || (rc = hm_alloc(H, &H->nz_val, (size_t)H->nnz)))
             return fail(rc, "cluster workspace");
         const DevTables& t = h->dev[pi];
         leaf_coef_kernel<<<blocks_for(n * md, 128), 128, 0, st>>>(n, d, H->m, md, H->perm, H->leaf_of, H->center,
                                                                   H->side, t.vod, t.v2c_ptr, t.v2c, t.cells, t.V,
                                                                   t.jac_orig, R.q, d_lam, d_w, H->coef);
         shift_kernel<<<blocks_for((int64_t)nn * md * md, 128), 128, 0, st>>>(nn, d, H->m, md, H->parent, H->center,
-                                                                            H->side, H->shift);
+                                                                            H->side, H->shift, H->shiftT);
         if (nfar > 0)
             kmat_kernel<<<blocks_for((int64_t)nfar * md * md, 128), 128, 0, st>>>(
                 nfar, d, H->m, md, d_far_sig, H->far_tau, H->center, H->side, -(d + 2.0 * s) / 2.0, H->kmat);
@@ -471,6 +616,76 @@ int fl_hmatrix_set_near(fl_hmatrix H, const double* A_dev, int64_t lda, void* st
     return FL_OK;
 }
 
+}  // extern "C"
+
+namespace fl {
+namespace {
+// The launches of one product: the near-field CSR product on `side` (forked from and joined
+// back to `st`; on `st` itself when side is null), the upward pass, couplings and downward
+// pass on `st`, then the leaf expansion, which adds the far field into y after the join.
+// Returns the launch count, or -1.
+int hm_enqueue(fl_hm* H, const double* x_dev, double* y_dev, cudaStream_t st, cudaStream_t side) {
+    const ClusterPlan& C = H->plan;
+    const int64_t n = C.n;
+    const int md = H->md, nn = C.nodes;
+    int launches = 0;
+    if (side) {
+        if (cudaEventRecord(H->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(side, H->ev_fork, 0) != cudaSuccess)
+            return -1;
+    }
+    cudaStream_t ns = side ? side : st;
+    near_spmv_kernel<<<blocks_for(n * 32, 256), 256, 0, ns>>>(n, H->nz_ptr, H->nz_col, H->nz_val, x_dev, y_dev);
+    if (side && cudaEventRecord(H->ev_join, side) != cudaSuccess) return -1;
+    up_leaf_kernel<<<blocks_for((int64_t)H->nleaves * md, 128), 128, 0, st>>>(H->nleaves, md, H->leaves, H->lo_d,
+                                                                             H->hi_d, H->perm, H->coef, x_dev, H->xh);
+    launches += 2;
+    // upward pass: the subtrees below the split level, one block each, then the top in one block
+    if (H->nsub > 0) {
+        if (md == 16) up_sub_kernel<16><<<H->nsub, 256, 0, st>>>(H->sub_levels, md, H->sub_off, H->sub_nodes, H->son_d, H->shift, H->xh);
+        else if (md == 36) up_sub_kernel<36><<<H->nsub, 256, 0, st>>>(H->sub_levels, md, H->sub_off, H->sub_nodes, H->son_d, H->shift, H->xh);
+        else up_sub_kernel<0><<<H->nsub, 256, 0, st>>>(H->sub_levels, md, H->sub_off, H->sub_nodes, H->son_d, H->shift, H->xh);
+        ++launches;
+    }
+    if (H->ntop_up > 0) {
+        if (md == 16) up_top_kernel<16><<<1, 1024, 0, st>>>(H->ntop_up, md, H->top_up_off, H->top_up, H->son_d, H->shift, H->xh);
+        else if (md == 36) up_top_kernel<36><<<1, 1024, 0, st>>>(H->ntop_up, md, H->top_up_off, H->top_up, H->son_d, H->shift, H->xh);
+        else up_top_kernel<0><<<1, 1024, 0, st>>>(H->ntop_up, md, H->top_up_off, H->top_up, H->son_d, H->shift, H->xh);
+        ++launches;
+    }
+    if (cudaMemsetAsync(H->yh, 0, (size_t)nn * md * sizeof(double), st) != cudaSuccess) return -1;
+    if (H->nsig > 0) {
+        const int nfar = (int)(H->plan.far.size() / 2);
+        const dim3 g = blocks_for((int64_t)nfar * md, 128);
+        if (md == 16) pair_product_kernel<16><<<g, 128, 0, st>>>(nfar, md, H->far_tau, H->kmat, H->xh, H->Pb);
+        else if (md == 36) pair_product_kernel<36><<<g, 128, 0, st>>>(nfar, md, H->far_tau, H->kmat, H->xh, H->Pb);
+        else pair_product_kernel<0><<<g, 128, 0, st>>>(nfar, md, H->far_tau, H->kmat, H->xh, H->Pb);
+        couple_sum_kernel<<<blocks_for((int64_t)H->nsig * md, 128), 128, 0, st>>>(H->nsig, md, H->sig_nodes, H->far_ptr,
+                                                                                 H->Pb, H->yh);
+        launches += 2;
+    }
+    // downward pass: the top levels in one block, then the subtrees, one block each
+    if (H->ntop_down > 0) {
+        if (md == 16) down_top_kernel<16><<<1, 1024, 0, st>>>(H->ntop_down, md, H->top_down_off, H->top_down, H->parent, H->shiftT, H->yh);
+        else if (md == 36) down_top_kernel<36><<<1, 1024, 0, st>>>(H->ntop_down, md, H->top_down_off, H->top_down, H->parent, H->shiftT, H->yh);
+        else down_top_kernel<0><<<1, 1024, 0, st>>>(H->ntop_down, md, H->top_down_off, H->top_down, H->parent, H->shiftT, H->yh);
+        ++launches;
+    }
+    if (H->nsub > 0 && H->sub_levels > 1) {
+        if (md == 16) down_sub_kernel<16><<<H->nsub, 256, 0, st>>>(H->sub_levels, md, H->sub_off, H->sub_nodes, H->parent, H->shiftT, H->yh);
+        else if (md == 36) down_sub_kernel<36><<<H->nsub, 256, 0, st>>>(H->sub_levels, md, H->sub_off, H->sub_nodes, H->parent, H->shiftT, H->yh);
+        else down_sub_kernel<0><<<H->nsub, 256, 0, st>>>(H->sub_levels, md, H->sub_off, H->sub_nodes, H->parent, H->shiftT, H->yh);
+        ++launches;
+    }
+    if (side && cudaStreamWaitEvent(st, H->ev_join, 0) != cudaSuccess) return -1;
+    down_leaf_kernel<<<blocks_for(n, 128), 128, 0, st>>>(n, md, H->perm, H->leaf_of, H->coef, H->yh, -H->C, y_dev);
+    ++launches;
+    return cudaGetLastError() == cudaSuccess ? launches : -1;
+}
+}  // namespace
+}  // namespace fl
+
+extern "C" {
+
 int fl_hmatrix_matvec(fl_hmatrix H, const double* x_dev, double* y_dev, void* stream) {
     if (!H) return FL_EINVAL;
     H->err.clear();
@@ -478,40 +693,57 @@ int fl_hmatrix_matvec(fl_hmatrix H, const double* x_dev, double* y_dev, void* st
     if (!H->near_ready) return hm_fail(H, FL_EINVAL, "near field not set (fl_hmatrix_set_near)");
     if (cudaSetDevice(H->device) != cudaSuccess) return hm_fail(H, FL_ECUDA, "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
-    const ClusterPlan& C = H->plan;
-    const int64_t n = C.n;
-    const int md = H->md, nn = C.nodes;
-    int launches = 0;
-    near_spmv_kernel<<<blocks_for(n * 32, 256), 256, 0, st>>>(n, H->nz_ptr, H->nz_col, H->nz_val, x_dev, y_dev);
-    up_leaf_kernel<<<blocks_for((int64_t)H->nleaves * md, 128), 128, 0, st>>>(H->nleaves, md, H->leaves, H->lo_d,
-                                                                             H->hi_d, H->perm, H->coef, x_dev, H->xh);
-    launches += 2;
-    for (size_t L = 0; L + 1 < H->up_off.size(); ++L) {
-        const int cnt = H->up_off[L + 1] - H->up_off[L];
-        if (cnt == 0) continue;
-        up_level_kernel<<<blocks_for((int64_t)cnt * md, 128), 128, 0, st>>>(cnt, md, H->up_nodes + H->up_off[L],
-                                                                           H->son_d, H->shift, H->xh);
-        ++launches;
+    // a product is launched as the graph captured for this (x, y), captured on first use
+    cudaGraphExec_t exec = nullptr;
+    int launches = -1;
+    for (const auto& g : H->graphs)
+        if (g.x == x_dev && g.y == y_dev) {
+            exec = g.exec;
+            launches = g.launches;
+        }
+    if (!exec) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const bool capturing = st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+        cudaGetLastError();
+        if (!H->cap && !capturing) {
+            if (cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&H->side_st, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&H->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&H->ev_join, cudaEventDisableTiming) != cudaSuccess)
+                return hm_fail(H, FL_ECUDA, "product streams");
+        }
+        if (!capturing && H->graphs.size() < 8) {
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return hm_fail(H, FL_ECUDA, "graph capture");
+            launches = fl::hm_enqueue(H, x_dev, y_dev, H->cap, H->side_st);
+            const cudaError_t ec = cudaStreamEndCapture(H->cap, &graph);
+            if (launches < 0 || ec != cudaSuccess || !graph) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return hm_fail(H, FL_ECUDA, "H-matrix product capture");
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) {
+                cudaGetLastError();
+                return hm_fail(H, FL_ECUDA, "H-matrix product graph");
+            }
+            H->graphs.push_back({x_dev, y_dev, exec, launches});
+        }
     }
-    if (cudaMemsetAsync(H->yh, 0, (size_t)nn * md * sizeof(double), st) != cudaSuccess)
-        return hm_fail(H, FL_ECUDA, "memset");
-    if (H->nsig > 0) {
-        couple_kernel<<<blocks_for((int64_t)H->nsig * md, 128), 128, 0, st>>>(H->nsig, md, H->sig_nodes, H->far_ptr,
-                                                                             H->far_tau, H->kmat, H->xh, H->yh);
-        ++launches;
+    if (exec) {
+        if (cudaGraphLaunch(exec, st) != cudaSuccess) {
+            cudaGetLastError();
+            return hm_fail(H, FL_ECUDA, "H-matrix product graph launch");
+        }
+    } else {
+        // inside a caller's capture, or more (x, y) pairs than kept graphs: launches on `st`
+        launches = fl::hm_enqueue(H, x_dev, y_dev, st, nullptr);
+        if (launches < 0) return hm_fail(H, FL_ECUDA, "H-matrix product launch");
     }
-    for (size_t L = 0; L + 1 < H->down_off.size(); ++L) {
-        const int cnt = H->down_off[L + 1] - H->down_off[L];
-        if (cnt == 0) continue;
-        down_level_kernel<<<blocks_for((int64_t)cnt * md, 128), 128, 0, st>>>(cnt, md, H->down_nodes + H->down_off[L],
-                                                                             H->parent, H->shift, H->yh);
-        ++launches;
-    }
-    down_leaf_kernel<<<blocks_for(n, 128), 128, 0, st>>>(n, md, H->perm, H->leaf_of, H->coef, H->yh, -H->C, y_dev);
-    ++launches;
     count_launch(launches);
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? FL_OK : hm_fail(H, FL_ECUDA, std::string("H-matrix product: ") + cudaGetErrorString(e));
+    return FL_OK;
 }
 
 int fl_hmatrix_info(fl_hmatrix H, int64_t* info) {
