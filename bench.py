@@ -59,7 +59,7 @@ DW_OPS_PER_EVAL = {5: 92, 6: 88, 7: 96}
 # cell data read): 51.9 MB read + 2810.2 MB written over 242,559,275 far pairs in one ncu
 # capture of far_tile_dw_kernel<6,2,2> on the graded disc (22043 triangles, s = 1/2); the
 # kernel's traffic grows with the far pairs (tiles and row-sum blocks both scale with N_el^2)
-FAR_DW_DRAM_BYTES_PER_PAIR = (51888384 + 2810236928) / 242559275
+FAR_DW_DRAM_BYTES_PER_PAIR = (46037248 + 2808832512) / 242559275
 
 
 def load_peaks():

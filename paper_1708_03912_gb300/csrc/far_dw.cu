@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
     double* sD = reinterpret_cast<double*>(sW + Q * NV);                // [32][Q] diagonal tile row sums
     double* sCen = sD + 32 * Q;                                         // [32][2]
     double* sJac = sCen + 64;                                           // [32]
-    double* priv = sJac + 32;                                           // [NV][maxL][32]
+    dw* priv = reinterpret_cast<dw*>(sJac + 32);                        // [NV][maxL][32] double-word
     int* sLoc = reinterpret_cast<int*>(priv + NV * maxL * 32);          // [32][NV]
     int* sHas = sLoc + 32 * NV;                                         // [32]
 
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
         sJac[i] = A.jac[K0 + i];
         sHas[i] = A.hasdof[K0 + i];
     }
-    for (int i = threadIdx.x; i < NV * nLI * 32; i += blockDim.x) priv[i] = 0.0;
+    for (int i = threadIdx.x; i < NV * nLI * 32; i += blockDim.x) priv[i] = {0.f, 0.f};
     for (int i = threadIdx.x; i < 32 * Q; i += blockDim.x) sD[i] = 0.0;
     __syncthreads();
 
@@ -253,7 +253,8 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
         // lane-private partial block
         if (warp < NV && act) {
             const int j = warp;
-            const double sc = wK * wj;
+            // |K| |K'| as a double-word number: the accumulation stays on the float32 pipe
+            const dw sc = dw_mul(wKd, wjd);
 #pragma unroll
             for (int i = 0; i < NV; ++i) {
                 const int li = sLoc[kk * NV + i];
@@ -261,7 +262,8 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
                     dw o = sOff[(i * NV + j) * 32 + lane];
 #pragma unroll
                     for (int w = 1; w < DW_WARPS; ++w) o = dw_add(o, sOff[(w * 9 + i * NV + j) * 32 + lane]);
-                    priv[(j * nLI + li) * 32 + lane] += dw_to(o) * sc;
+                    dw& pv = priv[(j * nLI + li) * 32 + lane];
+                    pv = dw_add(pv, dw_mul(o, sc));
                 }
             }
         }
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
         for (int q = A.inc_ptr[pJ + lj]; q < A.inc_ptr[pJ + lj + 1]; ++q) {
             const int e = A.inc_ent[q];
             const int l = e / NV, j = e - l * NV;
-            acc += priv[(j * nLI + li) * 32 + l];
+            acc += dw_to(priv[(j * nLI + li) * 32 + l]);
         }
         Pt[idx] = acc;
     }
