@@ -215,6 +215,65 @@ def build_problems(F, synth, m, svals, nrhs, nslices, V):
 CASES = {"disc25": (25, 1.0, 0.75), "gdisc30": (30, 2.0, 0.75), "gdisc30s5": (30, 2.0, 0.5), "disc10": (10, 1.0, 0.75)}
 # strong-form profiling cases: L-shape level, s
 SF_CASES = {"sf_lshape3": (3, 0.5), "sf_lshape5": (5, 0.5)}
+# dense-product and H-matrix-product profiling cases
+MV_CASES = {"mv_f32_20000": (20000, "f32"), "mv_f64_20000": (20000, "f64"), "mv_f32_35693": (35693, "f32")}
+HM_CASES = {"hm_lshape4": (4, 4)}
+
+
+def run_mv_case(args):
+    """`--steps` products y = A x (fl_matvec) with a seeded Gaussian A of the named size and
+    type, after one untimed product; prints the CUDA-event times."""
+    import torch
+
+    from paper_1708_03912_gb300 import fraclap as F
+
+    n, t = MV_CASES[args.case]
+    g = torch.Generator(device="cuda").manual_seed(7)
+    A = torch.randn(n, n, dtype=torch.float32 if t == "f32" else torch.float64, device="cuda", generator=g)
+    x = torch.randn(n, 1, dtype=torch.float64, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    dt = F.FL_F32 if t == "f32" else F.FL_F64
+    F.fl_matvec(dt, A, x, y)
+    ts = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        F.fl_matvec(dt, A, x, y)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    print(f"case {args.case}: n {n} {t} product ms " + " ".join(f"{v:.4f}" for v in ts))
+    return 0
+
+
+def run_hm_case(args):
+    """The H-matrix product (m = 4, leaves of 32, eta = 1) on an L-shape level: set-up from the
+    float64 matrix, one untimed product, then `--steps` products timed by CUDA events."""
+    import torch
+
+    from paper_1708_03912_gb300 import fraclap as F
+    from paper_1708_03912_gb300 import synth
+
+    level, m = HM_CASES[args.case]
+    V, T = synth.lshape(0.25, level)
+    mesh = F.Mesh(V, T)
+    A = mesh.assemble(0.5)
+    H = F.HMatrix(mesh.h, 0.5, m=m, eta=1.0, leaf=32)
+    H.set_near(A)
+    x = torch.randn(A.shape[0], dtype=torch.float64, device="cuda", generator=torch.Generator(device="cuda").manual_seed(5))
+    y = torch.empty_like(x)
+    H.matvec(x, y)
+    ts = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        H.matvec(x, y)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    print(f"case {args.case}: n {A.shape[0]} m {m} product ms " + " ".join(f"{v:.4f}" for v in ts))
+    H.close()
+    return 0
 
 
 def run_sf_case(args):
@@ -700,7 +759,7 @@ def main():
     ap.add_argument("--no-side", action="store_true", help="headline step only (no side sections)")
     ap.add_argument("--no-tune", action="store_true", help="skip the far-kernel autotuner (default launch shape)")
     ap.add_argument("--tune-file", default=None, help="load/save the autotuner's table (JSON)")
-    ap.add_argument("--case", default=None, choices=sorted(CASES) + sorted(SF_CASES),
+    ap.add_argument("--case", default=None, choices=sorted(CASES) + sorted(SF_CASES) + sorted(MV_CASES) + sorted(HM_CASES),
                     help="profiling mode: run a small named workload and print stage times (no JSON line)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="assembly precision of --case")
     ap.add_argument("--no-solve", action="store_true", help="--case: assembly only")
@@ -709,6 +768,10 @@ def main():
         return run_reference(args)
     if args.case in SF_CASES:
         return run_sf_case(args)
+    if args.case in MV_CASES:
+        return run_mv_case(args)
+    if args.case in HM_CASES:
+        return run_hm_case(args)
     if args.case:
         return run_case(args)
 
