@@ -658,14 +658,15 @@ int fl_tune_batch(fl_handle h, int nprob, const fl_batch_problem* probs, int rep
 
 /* Add or replace a table entry for the current device (p0, p1: the kernel's two parameters). */
 /*
- * Autotuner of the dense matvec (fl_matvec's shared-memory-staged product): times it on
- * the caller's matrix (dtype FL_F64 or FL_F32, 16-byte loads need A aligned to its
- * element size) for 1, 2, ... blocks per SM up to what fits, median of reps CUDA-event
- * timings after a warm-up, on `stream`; records the fastest under ("gemv_smem_f64" |
- * "gemv_smem_f32", n) for this device, which fl_matvec then uses.  x_dev, y_dev: [n]
- * float64 (y is overwritten).  *best_per_sm, *best_ms (host, may be NULL) get the choice.
- * Errors: FL_EINVAL (bad arguments), FL_ENOTIMPL (the staged product is not used at this
- * size: x too large to stage, or fewer than two blocks per SM fit), FL_ECUDA.
+ * Autotuner of the dense matvec (fl_matvec's shared-memory-staged products): times the one
+ * fl_matvec uses on the caller's matrix (dtype FL_F64: the 8-warp staged product; FL_F32: the
+ * 16-warp row-dot product; A aligned to its element size) for 1, 2, ... blocks per SM up to
+ * what fits (at most 4 for FL_F32), median of reps CUDA-event timings after a warm-up, on
+ * `stream`; records the fastest under ("gemv_smem_f64" | "gemv_rows_f32", n) for this device,
+ * which fl_matvec then uses.  x_dev, y_dev: [n] float64 (y is overwritten).  *best_per_sm,
+ * *best_ms (host, may be NULL) get the choice.  Errors: FL_EINVAL (bad arguments),
+ * FL_ENOTIMPL (the staged product is not used at this size: x too large to stage, or for
+ * FL_F64 fewer than two blocks per SM fit), FL_ECUDA.
  */
 int fl_tune_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, const double* x_dev,
                    double* y_dev, int reps, int* best_per_sm, double* best_ms, void* stream);

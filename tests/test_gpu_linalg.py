@@ -96,8 +96,8 @@ def test_f32x2_storage_and_product():
 
 
 def test_matvec_autotuner_records_and_is_used():
-    # the tuner sweeps blocks per SM of the staged product, records the fastest, and the
-    # product taken with the recorded shape is still the product
+    # the tuner sweeps blocks per SM of the staged product (float32: the row-dot product),
+    # records the fastest, and the product taken with the recorded shape is still the product
     g = torch.Generator(device="cpu").manual_seed(9)
     n = 3001
     A = torch.randn(n, n, generator=g, dtype=torch.float64).cuda()
@@ -109,7 +109,7 @@ def test_matvec_autotuner_records_and_is_used():
     Y = torch.empty(n, 1, dtype=torch.float64, device="cuda")
     F.fl_tune_clear()
     for dt, Ad, name, ref, tol in ((F.FL_F64, A, "gemv_smem_f64", A.cpu() @ x.cpu(), 1e-13),
-                                   (F.FL_F32, A32, "gemv_smem_f32", A32.double().cpu() @ x.float().double().cpu(), 1e-5)):
+                                   (F.FL_F32, A32, "gemv_rows_f32", A32.double().cpu() @ x.float().double().cpu(), 1e-5)):
         per_sm, ms = F.fl_tune_matvec(dt, Ad, x1, y1, reps=3)
         assert per_sm >= 1 and ms > 0
         assert F.fl_tune_lookup(name, n, 1, 1) == (per_sm, 0)
