@@ -543,7 +543,7 @@ def matvec_section(F, timed, peaks, A, A32):
     return out
 
 
-def hmatrix_section(F, timed, A, h5):
+def hmatrix_section(F, timed, A, h5, b=None):
     """Cluster method (Section 6) on the headline matrix: H-matrix products for Chebyshev orders
     4 and 6 (leaves of 32 DOFs, eta = 1) against the dense float64 product: time, error, size."""
     import torch
@@ -554,6 +554,10 @@ def hmatrix_section(F, timed, A, h5):
     ref = torch.empty(n, 1, dtype=torch.float64, device=A.device)
     dense_ms = timed(lambda: F.fl_matvec(F.FL_F64, A, x[:, None], ref), reps=5, flush_between=False)
     out = {"dense_f64_matvec_ms": dense_ms, "n": n, "leaf": 32, "eta": 1.0}
+    u_dense = None
+    if b is not None:
+        u_dense = torch.empty_like(b)
+        F.fl_solve(h5, A, b, u_dense, _opts(F, 1e-10))
     for m in (4, 6):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -567,7 +571,17 @@ def hmatrix_section(F, timed, A, h5):
         err = float(torch.linalg.norm(y - ref[:, 0]) / torch.linalg.norm(ref[:, 0]))
         out[f"m{m}"] = {"matvec_ms": ms, "speedup_vs_dense": dense_ms / ms, "rel_error_vs_dense": err,
                         "setup_ms_from_dense": setup_ms, **H.info()}
+        # Jacobi-PCG with the H-matrix product to 1e-8 (f = 1), against the dense solve
+        if b is not None:
+            uh, ih = H.solve(b, tol=1e-8)
+            solve_ms = timed(lambda: H.solve(b, tol=1e-8), reps=2, flush_between=False)
+            out[f"m{m}"]["jacobi_pcg"] = {"ms": solve_ms, "iterations": ih.iterations,
+                                          "max_error_vs_dense_solution": float((uh - u_dense).abs().max() /
+                                                                               u_dense.abs().max())}
         H.close()
+    if b is not None:
+        out["dense_jacobi_pcg_ms"] = timed(lambda: F.fl_solve(h5, A, b, torch.empty_like(b), _opts(F, 1e-8)), reps=2,
+                                           flush_between=False)
     return out
 
 
@@ -916,7 +930,7 @@ def main():
         del Am
         torch.cuda.empty_cache()
         line["lshape"]["preconditioners"] = lshape_precond_section(F, synth, timed, A, b, m.h)
-        line["lshape"]["hmatrix"] = hmatrix_section(F, timed, A, m.h)
+        line["lshape"]["hmatrix"] = hmatrix_section(F, timed, A, m.h, b)
         line["lshape"]["adaptive"] = adaptive_section(F, synth, timed, peaks, sms, m, A, b, n_el)
         line["heat"] = heat_section(F, synth, timed)
         line["symmetry"] = symmetry_section(F, synth, timed)

@@ -506,6 +506,18 @@ int fl_hmatrix_set_near(fl_hmatrix H, const double* A_dev, int64_t lda, void* st
 int fl_hmatrix_matvec(fl_hmatrix H, const double* x_dev, double* y_dev, void* stream);
 /* info[0..5]: nodes, admissible pairs, near-field leaf pairs, near-field entries, device
  * bytes held, tree depth. */
+/*
+ * Solve A u = b with the cluster method's product in place of the dense one: Jacobi-PCG
+ * (Section 5) on the H-matrix, the diagonal taken from the near field (exact entries), from
+ * u = 0 until ||b - H u||_2 <= o->tol ||b||_2 (the H-matrix's own residual) or o->maxit steps
+ * (the other fl_solve_opts fields are ignored; NULL: the defaults).  b_dev, u_dev: [n] float64,
+ * DOF order (u overwritten, must not be b).  The scalars of each step are read back to the host
+ * (the call synchronises `stream` every step).  The solution differs from the dense solve by the
+ * interpolation error of the far field.  Returns FL_OK, FL_ENOTCONV, FL_ENOTSPD, or FL_EINVAL /
+ * FL_ENOMEM / FL_ECUDA; *info (may be NULL) gets iterations and the final relative residual.
+ */
+int fl_hmatrix_solve(fl_hmatrix H, const double* b_dev, double* u_dev, const fl_solve_opts* o, fl_solve_info* info,
+                     void* stream);
 int fl_hmatrix_info(fl_hmatrix H, int64_t* info);
 const char* fl_hmatrix_last_error(fl_hmatrix H);
 void fl_hmatrix_destroy(fl_hmatrix H);

@@ -59,6 +59,9 @@ struct fl_hm {
     bool near_ready = false;
     double *xh = nullptr, *yh = nullptr;
     double* Pb = nullptr;  // per admissible pair: K_b xh[tau]
+    // Jacobi-PCG with the product (fl_hmatrix_solve), allocated on first use
+    double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_dinv = nullptr;
+    double *cg_part = nullptr, *cg_scal = nullptr, *cg_host = nullptr;
     // products captured as CUDA graphs, keyed by (x, y): the near-field product runs on a second
     // stream beside the chain of small far-field launches, and the graph launches them at once
     struct Graph {
@@ -377,6 +380,84 @@ __global__ void down_leaf_kernel(int64_t n, int md, const int* perm, const int* 
     y[perm[p]] += mC * acc;
 }
 
+// ------------------------------------------------------------ Jacobi-PCG --
+constexpr int HCG_BLOCKS = 256, HCG_THREADS = 256;
+
+// dinv[i] = 1 / A_ii from the near field (the diagonal lies in every leaf's own block)
+__global__ void hcg_diag_kernel(int64_t n, const int* ptr, const int* col, const double* val, double* dinv) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d = 0.0;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e)
+        if (col[e] == i) d = val[e];
+    dinv[i] = d > 0.0 ? 1.0 / d : 0.0;
+}
+
+// per block: the partial sums of a.b and c.d (fixed grid, fixed order)
+__global__ void hcg_dots_kernel(int64_t n, const double* a, const double* b, const double* c, const double* d,
+                                double* part) {
+    __shared__ double sh[2][HCG_THREADS / 32];
+    double s0 = 0.0, s1 = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        s0 = fma(a[i], b[i], s0);
+        if (c) s1 = fma(c[i], d[i], s1);
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = s0;
+        sh[1][threadIdx.x >> 5] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int w = 0; w < HCG_THREADS / 32; ++w) {
+            t0 += sh[0][w];
+            t1 += sh[1][w];
+        }
+        part[2 * blockIdx.x] = t0;
+        part[2 * blockIdx.x + 1] = t1;
+    }
+}
+
+// out[k] = sum over blocks of part[2 b + k], k = 0, 1 (one thread each, block order)
+__global__ void hcg_sum_kernel(const double* part, double* out) {
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int b = 0; b < HCG_BLOCKS; ++b) t += part[2 * b + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+}
+
+// u += alpha p, r -= alpha q, z = D^-1 r (alpha = scal[0] / scal[2])
+__global__ void hcg_update_kernel(int64_t n, const double* scal, const double* p, const double* q,
+                                  const double* dinv, double* u, double* r, double* z) {
+    const double alpha = scal[0] / scal[2];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        u[i] = fma(alpha, p[i], u[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        z[i] = dinv[i] * ri;
+    }
+}
+
+// p = z + beta p (beta = scal[1] / scal[0], the new and old r.z); the new r.z becomes the old
+__global__ void hcg_direction_kernel(int64_t n, double* scal, const double* z, double* p) {
+    const double beta = scal[1] / scal[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void hcg_start_kernel(int64_t n, const double* b, const double* dinv, double* u, double* r, double* z,
+                                 double* p) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        u[i] = 0.0;
+        r[i] = b[i];
+        z[i] = dinv[i] * b[i];
+        p[i] = z[i];
+    }
+}
+
 unsigned blocks_for(int64_t work, int threads) { return (unsigned)std::max<int64_t>(1, (work + threads - 1) / threads); }
 
 }  // namespace
@@ -423,6 +504,7 @@ void fl_hmatrix_destroy(fl_hmatrix H) {
         for (void* p : H->bufs) pool_dev_free(p);
     }
     for (auto& g : H->graphs) cudaGraphExecDestroy(g.exec);
+    if (H->cg_host) pool_host_free(H->cg_host);
     if (H->cap) cudaStreamDestroy(H->cap);
     if (H->side_st) cudaStreamDestroy(H->side_st);
     if (H->ev_fork) cudaEventDestroy(H->ev_fork);
@@ -758,5 +840,78 @@ int fl_hmatrix_info(fl_hmatrix H, int64_t* info) {
 }
 
 const char* fl_hmatrix_last_error(fl_hmatrix H) { return H ? H->err.c_str() : "null H-matrix handle"; }
+
+int fl_hmatrix_solve(fl_hmatrix H, const double* b_dev, double* u_dev, const fl_solve_opts* o, fl_solve_info* info,
+                     void* stream) {
+    if (!H) return FL_EINVAL;
+    H->err.clear();
+    if (!b_dev || !u_dev || b_dev == u_dev) return hm_fail(H, FL_EINVAL, "bad b / u");
+    if (!H->near_ready) return hm_fail(H, FL_EINVAL, "near field not set (fl_hmatrix_set_near)");
+    fl_solve_opts d{};
+    fl_default_solve_opts(&d);
+    const fl_solve_opts& op = o ? *o : d;
+    if (!(op.tol > 0.0) || op.maxit < 1) return hm_fail(H, FL_EINVAL, "tol must be > 0, maxit >= 1");
+    if (cudaSetDevice(H->device) != cudaSuccess) return hm_fail(H, FL_ECUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = H->plan.n;
+    int rc;
+    if (!H->cg_r) {
+        if ((rc = hm_alloc(H, &H->cg_r, n)) || (rc = hm_alloc(H, &H->cg_z, n)) || (rc = hm_alloc(H, &H->cg_p, n)) ||
+            (rc = hm_alloc(H, &H->cg_q, n)) || (rc = hm_alloc(H, &H->cg_dinv, n)) ||
+            (rc = hm_alloc(H, &H->cg_part, 2 * HCG_BLOCKS)) || (rc = hm_alloc(H, &H->cg_scal, 4)))
+            return rc;
+        void* hp = nullptr;
+        if (pool_host_alloc(&hp, 4 * sizeof(double)) != cudaSuccess) return hm_fail(H, FL_ENOMEM, "pinned scalars");
+        H->cg_host = (double*)hp;
+        hcg_diag_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, H->nz_ptr, H->nz_col, H->nz_val, H->cg_dinv);
+        count_launch();
+    }
+    double* r = H->cg_r;
+    double* z = H->cg_z;
+    double* p = H->cg_p;
+    double* q = H->cg_q;
+    double* sc = H->cg_scal;  // [0] r.z (old), [1] r.z (new) / r.r, [2] p.q, [3] b.b
+    double* hs = H->cg_host;
+    auto dots = [&](const double* a, const double* b2, const double* c, const double* d2, double* out) {
+        hcg_dots_kernel<<<HCG_BLOCKS, HCG_THREADS, 0, st>>>(n, a, b2, c, d2, H->cg_part);
+        hcg_sum_kernel<<<1, 32, 0, st>>>(H->cg_part, out);
+        count_launch(2);
+    };
+    hcg_start_kernel<<<HCG_BLOCKS, HCG_THREADS, 0, st>>>(n, b_dev, H->cg_dinv, u_dev, r, z, p);
+    count_launch();
+    dots(r, z, b_dev, b_dev, sc);  // sc[0] = r.z, sc[1] = b.b
+    if (cudaMemcpyAsync(hs, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return hm_fail(H, FL_ECUDA, "solver scalars");
+    const double bb = hs[1];
+    fl_solve_info out{};
+    out.outer_iterations = 1;
+    out.status = FL_ENOTCONV;
+    double rel = bb > 0.0 ? 1.0 : 0.0;
+    if (bb == 0.0) out.status = FL_OK;
+    int it = 0;
+    while (out.status == FL_ENOTCONV && it < op.maxit) {
+        if ((rc = fl_hmatrix_matvec(H, p, q, stream)) != FL_OK) return rc;
+        dots(p, q, nullptr, nullptr, sc + 2);  // sc[2] = p.q
+        hcg_update_kernel<<<HCG_BLOCKS, HCG_THREADS, 0, st>>>(n, sc, p, q, H->cg_dinv, u_dev, r, z);
+        dots(r, z, r, r, sc + 1);  // sc[1] = r.z (new), sc[2] = r.r
+        hcg_direction_kernel<<<HCG_BLOCKS, HCG_THREADS, 0, st>>>(n, sc, z, p);
+        count_launch(2);
+        ++it;
+        if (cudaMemcpyAsync(hs, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return hm_fail(H, FL_ECUDA, "solver scalars");
+        rel = std::sqrt(std::max(hs[2], 0.0) / bb);
+        if (!(hs[1] > 0.0) && rel > op.tol) out.status = FL_ENOTSPD;
+        else if (rel <= op.tol) out.status = FL_OK;
+        // the direction kernel has moved beta's numerator: r.z (new) is the next old value
+        if (cudaMemcpyAsync(sc, sc + 1, sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return hm_fail(H, FL_ECUDA, "solver scalars");
+    }
+    out.iterations = it;
+    out.rel_residual = rel;
+    if (info) *info = out;
+    return out.status;
+}
 
 }  // extern "C"

@@ -26,7 +26,7 @@ EXPORTS = ["fl_default_options", "fl_create", "fl_create_sector", "fl_destroy", 
            "fl_assemble", "fl_tune_assemble", "fl_set_far_variant", "fl_assemble_nearfield_csr", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
            "fl_heat_matrix", "fl_mass_apply", "fl_strong_form", "fl_br_indicators", "fl_mark_max", "fl_refine",
            "fl_cluster_plan", "fl_hmatrix_create", "fl_hmatrix_set_near",
-           "fl_hmatrix_matvec", "fl_hmatrix_info", "fl_hmatrix_last_error", "fl_hmatrix_destroy", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
+           "fl_hmatrix_matvec", "fl_hmatrix_solve", "fl_hmatrix_info", "fl_hmatrix_last_error", "fl_hmatrix_destroy", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
            "fl_matvec_f32_static",
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
            "fl_tune_batch", "fl_tune_matvec", "fl_tune_record", "fl_tune_lookup", "fl_tune_clear", "fl_tune_count", "fl_tune_save",
@@ -154,6 +154,8 @@ def lib():
     L.fl_hmatrix_set_near.restype = ci
     L.fl_hmatrix_matvec.argtypes = [vp, vp, vp, vp]
     L.fl_hmatrix_matvec.restype = ci
+    L.fl_hmatrix_solve.argtypes = [vp, vp, vp, ctypes.POINTER(fl_solve_opts), ctypes.POINTER(fl_solve_info), vp]
+    L.fl_hmatrix_solve.restype = ci
     L.fl_hmatrix_info.argtypes = [vp, ctypes.POINTER(i64)]
     L.fl_hmatrix_info.restype = ci
     L.fl_hmatrix_last_error.argtypes = [vp]
@@ -480,6 +482,20 @@ class HMatrix:
 
     def matvec(self, x, y, stream=None):
         self._check(lib().fl_hmatrix_matvec(self.hm, _ptr(x), _ptr(y), _stream(stream)))
+
+    def solve(self, b, tol=1e-8, maxit=10000, stream=None):
+        """Jacobi-PCG with the H-matrix product: (u, fl_solve_info); ENOTCONV / ENOTSPD are
+        reported in info.status rather than raised."""
+        import torch
+
+        o = fl_default_solve_opts()
+        o.tol, o.maxit = tol, maxit
+        info = fl_solve_info()
+        u = torch.empty_like(b)
+        r = lib().fl_hmatrix_solve(self.hm, _ptr(b), _ptr(u), ctypes.byref(o), ctypes.byref(info), _stream(stream))
+        if r not in (FL_OK, FL_ENOTCONV, FL_ENOTSPD):
+            self._check(r)
+        return u, info
 
     def info(self):
         v = (ctypes.c_int64 * 6)()

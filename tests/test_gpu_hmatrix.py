@@ -81,3 +81,38 @@ def test_hmatrix_errors():
         F.HMatrix(mesh.h, 0.5, m=0)
     H.close()
     mesh.close()
+
+
+def test_hmatrix_solve():
+    # Jacobi-PCG with the H-matrix product (Section 5's solver, Section 6's operator): the
+    # returned u satisfies the stated residual with the oracle's H-matrix product, and it is
+    # the dense solution up to the far field's interpolation error
+    from oracle import load_vector, solve
+
+    V, T = synth.disc(7, 2.0)
+    s, m, leaf = 0.5, 6, 4
+    om = OracleMesh(V, T)
+    Ao, _ = assemble_matrix(om, s)
+    bo = load_vector(om, s)
+    mesh = F.Mesh(V, T)
+    A = mesh.assemble(s, "fp64")
+    H = F.HMatrix(mesh.h, s, m=m, eta=1.0, leaf=leaf)
+    H.set_near(A)
+    b = torch.tensor(bo, device="cuda")
+    u, info = H.solve(b, tol=1e-10)
+    assert info.status == F.FL_OK and info.rel_residual <= 1e-10
+    ug = u.cpu().numpy()
+    res = np.linalg.norm(bo - hmatvec(Ao, om, s, ug, m=m, eta=1.0, leaf=leaf)) / np.linalg.norm(bo)
+    assert res <= 2e-10, res
+    uo = solve.cholesky_solve(Ao, bo)
+    err = np.max(np.abs(ug - uo)) / np.max(np.abs(uo))
+    _, idense = mesh.solve(A, b, tol=1e-10)
+    print(f"H-matrix solve: {info.iterations} steps (dense {idense.iterations}), residual {res:.1e}, "
+          f"error vs dense {err:.1e}")
+    assert err < 1e-6
+    assert abs(info.iterations - idense.iterations) <= 3
+    # a limit of one step reports that it did not converge
+    _, i1 = H.solve(b, tol=1e-12, maxit=1)
+    assert i1.status == F.FL_ENOTCONV and i1.iterations == 1
+    H.close()
+    mesh.close()
