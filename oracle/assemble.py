@@ -298,29 +298,91 @@ def boundary_vertex_2d(mesh, s, C, k, f, kb):
     return [P, Q, R], val
 
 
-def boundary_separated(mesh, s, C, k, fs, order):
-    """Σ over non-touching facets fs of a^{K×e} with the order-`order` Gauss rule."""
+def facet_sum(mesh, s, C, k, Y0, Y1, n, flen, order):
+    """C/(2s) ∫_K phi_i phi_j(x) Σ_e ∫_e n_e·(x-y) |x-y|^{-d-2s} dy dx over the facets e from Y0
+    to Y1 (1D: the points Y0, flen unused) with unit normals n and lengths flen, by the
+    order-`order` rules on K and on every e.  With the inward normals of the boundary facets of
+    Omega this is the boundary term; by the divergence theorem, with the normals pointing into a
+    region N, the inner integral is (2s) ∫_{R^d minus N} |x-y|^{-d-2s} dy for x in N."""
     d = mesh.dim
     xa, wa, pha = cell_points(mesh, k, order)
     xa, wa = xa[0], wa[0]
-    n = mesh.normals[fs]
     if d == 1:
-        y = mesh.V[mesh.facets[fs, 0]]
-        diff = xa[None, :, :] - y[:, None, :]
+        diff = xa[None, :, :] - Y0[:, None, :]
         nd = np.sum(n[:, None, :] * diff, axis=-1)
         r2 = np.sum(diff * diff, axis=-1)
         B = np.sum(nd * r2 ** (-(1.0 + 2.0 * s) / 2.0), axis=0)
     else:
         t, wt = rules.gauss01(order)
-        E0 = mesh.V[mesh.facets[fs, 0]]
-        E1 = mesh.V[mesh.facets[fs, 1]]
-        y = E0[:, None, :] + t[None, :, None] * (E1 - E0)[:, None, :]
-        wy = wt[None, :] * mesh.facet_len[fs][:, None]
+        y = Y0[:, None, :] + t[None, :, None] * (Y1 - Y0)[:, None, :]
+        wy = wt[None, :] * flen[:, None]
         diff = xa[None, :, None, :] - y[:, None, :, :]
         nd = np.einsum("fd,fqbd->fqb", n, diff)
         r2 = np.sum(diff * diff, axis=-1)
         B = np.sum(nd * r2 ** (-(2.0 + 2.0 * s) / 2.0) * wy[:, None, :], axis=(0, 2))
     return C / (2.0 * s) * np.einsum("ai,aj,a->ij", pha, pha, wa * B)
+
+
+def boundary_separated(mesh, s, C, k, fs, order):
+    """Σ over non-touching facets fs of a^{K×e} with the order-`order` Gauss rule."""
+    Y0 = mesh.V[mesh.facets[fs, 0]]
+    Y1 = mesh.V[mesh.facets[fs, -1]]
+    return facet_sum(mesh, s, C, k, Y0, Y1, mesh.normals[fs], mesh.facet_len[fs], order)
+
+
+def near_region_facets(mesh, k):
+    """The boundary of N(K), the union of cell k and the cells touching it or at vertex-graph
+    distance 1 from it (the cells whose pairs with k are integrated locally).  Returns
+    (Y0, Y1, n, flen, verts, bidx): per facet its end points (1D: Y1 = Y0), the unit normal
+    pointing into N(K), its length (1 in 1D), its vertex ids and the index of the boundary facet
+    of Omega it is, or -1 for a facet between a cell of N(K) and one outside it."""
+    shared, near = mesh.classify_cells(k)
+    inN = (shared > 0) | near
+    Y0, Y1, nrm, flen, verts, bidx = [], [], [], [], [], []
+    if mesh.dim == 1:
+        for m in np.nonzero(inN)[0]:
+            for side, v in enumerate(mesh.C[m]):
+                others = [c for c in mesh.cells_of_vertex[v] if c != m]
+                if others and inN[others[0]]:
+                    continue
+                f = -1
+                if not others:
+                    f = int(np.nonzero(mesh.facets[:, 0] == v)[0][0])
+                Y0.append(mesh.V[v])
+                Y1.append(mesh.V[v])
+                nrm.append([1.0 if side == 0 else -1.0])  # into the interval m
+                flen.append(1.0)
+                verts.append([v])
+                bidx.append(f)
+    else:
+        for m in np.nonzero(inN)[0]:
+            a, b, c = mesh.C[m]
+            for p, q, r in ((a, b, c), (b, c, a), (c, a, b)):
+                key = (min(p, q), max(p, q))
+                other = [o for o, _ in mesh.edge_owners[key] if o != m]
+                if other and inN[other[0]]:
+                    continue
+                P0, P1 = mesh.V[key[0]], mesh.V[key[1]]
+                if other:
+                    f = -1
+                    t = P1 - P0
+                    n = np.array([-t[1], t[0]]) / np.hypot(t[0], t[1])
+                    if np.dot(n, mesh.V[r] - P0) < 0:
+                        n = -n
+                    ln = float(np.hypot(t[0], t[1]))
+                else:
+                    f = mesh.facet_of_edge[(int(key[0]), int(key[1]))]
+                    n = mesh.normals[f]
+                    ln = mesh.facet_len[f]
+                Y0.append(P0)
+                Y1.append(P1)
+                nrm.append(n)
+                flen.append(ln)
+                verts.append([key[0], key[1]])
+                bidx.append(f)
+    return (np.array(Y0).reshape(-1, mesh.dim), np.array(Y1).reshape(-1, mesh.dim),
+            np.array(nrm).reshape(-1, mesh.dim), np.array(flen), np.array(verts, dtype=np.int64).reshape(-1, mesh.dim),
+            np.array(bidx, dtype=np.int64))
 
 
 # ------------------------------------------------------------- assembly ----
@@ -364,7 +426,7 @@ class _Sink:
 
 def assemble_matrix(mesh: OracleMesh, s: float, orders: QuadOrders = QuadOrders(),
                     dof_mode: str = "interior", rows=None, chunk: int = 4096, regional: bool = False,
-                    far_offdiag: bool = True):
+                    far_offdiag: bool = True, self_term: str = "pairs"):
     """Dense A^s (or the rows `rows` of it) in the DOF numbering of mesh.dofs().
 
     Returns (A, vertex_of_dof).  Loops over elements K in index order and, for
@@ -373,9 +435,26 @@ def assemble_matrix(mesh: OracleMesh, s: float, orders: QuadOrders = QuadOrders(
     Laplacian of Section 2.  far_offdiag=False leaves out the off-diagonal blocks
     -C ∬ phi_i(x) phi_j(y) k of the separated pairs at vertex-graph distance >= 2
     (the far field of Section 6) and keeps everything else, their diagonal-block
-    terms included: the sparse near-field part N of A = N + F."""
+    terms included: the sparse near-field part N of A = N + F.
+
+    self_term="near_region" computes the diagonal blocks from local data only, as the
+    near-field assembly of the cluster method needs (Section 6: the near field is assembled
+    by local computations).  For x in K, the far pairs' diagonal-block terms and the
+    boundary term add up to C ∫_{R^d minus N(K)} |x-y|^{-d-2s} dy, N(K) the union of K and
+    the cells touching it or at vertex-graph distance 1 (these pairs stay as they are); by
+    the divergence theorem that is C/(2s) times the integral over the boundary of N(K) of
+    n·(x-y)|x-y|^{-d-2s}, n pointing into N(K).  Its facets that share a vertex with K are
+    boundary facets of Omega and keep the singular rules of the boundary term; the others
+    take Gauss order k_near (vertex-graph distance 1 from K) or k_far.  Only the diagonal
+    blocks change: the entries of two DOFs whose supports share no cell are those of
+    "pairs"."""
     if not 0.0 < s < 1.0:
         raise ValueError("s must lie in (0, 1)")
+    if self_term not in ("pairs", "near_region"):
+        raise ValueError(self_term)
+    near_region = self_term == "near_region"
+    if near_region and regional:
+        raise ValueError("the near-region form includes the boundary term; regional=True is not supported")
     d = mesh.dim
     if d == 2 and dof_mode == "paper" and s < 0.5 and not regional:
         raise NotImplementedError("2D boundary DOFs (paper mode, s < 1/2) are not supported")
@@ -407,22 +486,43 @@ def assemble_matrix(mesh: OracleMesh, s: float, orders: QuadOrders = QuadOrders(
             else:
                 loc, blk = common_vertex_2d(mesh, s, C, lo, hi, orders.k_vertex)
             sink.add(loc, loc, blk)
-        # separated pairs
-        for sel, order, keep_off in (((shared == 0) & near, orders.k_near, True),
-                                     ((shared == 0) & ~near, orders.k_far, far_offdiag)):
+        # separated pairs (with near_region, the far pairs' diagonal-block terms are left to
+        # the boundary of N(K) below)
+        for sel, order, keep_off, keep_diag in (((shared == 0) & near, orders.k_near, True, True),
+                                                ((shared == 0) & ~near, orders.k_far, far_offdiag, not near_region)):
             ms = np.nonzero(partner & sel)[0]
             for c0 in range(0, len(ms), chunk):
                 mm = ms[c0:c0 + chunk]
                 off, blk_k, blk_m = separated_blocks(mesh, s, C, k, mm, order)
-                blocks[k] += blk_k
-                blocks[mm] += blk_m
+                if keep_diag:
+                    blocks[k] += blk_k
+                    blocks[mm] += blk_m
                 if keep_off:
                     sink.add_off(mesh.C[k], mesh.C[mm], off)
         # identical pair
         if has_dof[k]:
             loc, blk = identical_1d(mesh, s, C, k) if d == 1 else identical_2d(mesh, s, C, k, 2 * orders.k_touch)
             sink.add(loc, loc, blk)
-        if has_dof[k] and not regional:
+        if has_dof[k] and near_region:
+            Y0, Y1, nrm, flen, verts, bidx = near_region_facets(mesh, k)
+            m0, m1 = mesh.rings(k)
+            fsh = m0[verts].sum(axis=1)
+            fnear = (fsh == 0) & m1[verts].any(axis=1)
+            for q in np.nonzero(fsh > 0)[0]:
+                f = int(bidx[q])
+                if f < 0:
+                    raise AssertionError("a facet between two cells of N(K) cannot touch K")
+                if d == 1:
+                    loc, blk = boundary_touch_1d(mesh, s, C, k, f, dov[mesh.facets[f, 0]] >= 0)
+                elif fsh[q] == 2:
+                    loc, blk = boundary_own_edge_2d(mesh, s, C, k, f, orders.k_bnd)
+                else:
+                    loc, blk = boundary_vertex_2d(mesh, s, C, k, f, orders.k_bnd)
+                sink.add(loc, loc, blk)
+            for sel, order in ((fnear, orders.k_near), (~fnear & (fsh == 0), orders.k_far)):
+                if sel.any():
+                    blocks[k] += facet_sum(mesh, s, C, k, Y0[sel], Y1[sel], nrm[sel], flen[sel], order)
+        elif has_dof[k] and not regional:
             # boundary facets
             fsh, fnear = mesh.classify_facets(k)
             for f in np.nonzero(fsh > 0)[0]:

@@ -94,6 +94,9 @@ class OracleMesh:
             self.facets = np.array(fac, dtype=np.int64).reshape(-1, 2)
             self.normals = np.array(nrm, dtype=np.float64).reshape(-1, 2)
             self.facet_cell = np.array(fcell, dtype=np.int64)
+            # edge (sorted vertex pair) -> [(cell, opposite vertex)], and boundary edge -> facet index
+            self.edge_owners = edges
+            self.facet_of_edge = {(int(p), int(q)): f for f, (p, q) in enumerate(self.facets)}
         self.on_boundary = np.zeros(self.nv, dtype=bool)
         self.on_boundary[self.facets.ravel()] = True
         self.facet_len = (np.ones(len(self.facets)) if self.dim == 1 else
