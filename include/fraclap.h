@@ -489,6 +489,19 @@ typedef struct fl_hm* fl_hmatrix;
  */
 int fl_cluster_plan(fl_handle h, double s, double eta, int leaf, int64_t* sizes, int32_t* perm, int32_t* node,
                     int32_t* far, int32_t* near);
+/*
+ * Host only: the plan of fl_hmatrix_assemble_near for the same partition.  sizes[0..3] receive
+ * the tiles, the facet-list entries, the facet-table size and the number of cells; with
+ * non-NULL arrays also cell_perm [cells] (internal cell order -> cell index of the input),
+ * ef_ptr [cells + 1], ef_fac and ef_cls [entries] (per internal cell with DOFs: the facets of the
+ * boundary of N(K), ascending ids, and their classes: 2 / 3 = shares two / one vertex with K,
+ * 1 = a vertex is a mesh neighbour of one of K, 0 = the rest), fac_vert [table * dim] (vertex
+ * ids; ids below the number of boundary facets of Omega are those facets) and fac_normal
+ * [table * dim] (unit normals pointing into N(K)).  Call once with NULL arrays to size them.
+ * Errors: FL_EINVAL, FL_ENOMEM.
+ */
+int fl_near_region_plan(fl_handle h, double s, double eta, int leaf, int64_t* sizes, int32_t* cell_perm,
+                        int32_t* ef_ptr, int32_t* ef_fac, int32_t* ef_cls, int32_t* fac_vert, double* fac_normal);
 
 /*
  * Builds the H-matrix of A^s on h's mesh: the plan above, then on the device the leaf
@@ -500,6 +513,37 @@ int fl_hmatrix_create(fl_handle h, double s, int m, double eta, int leaf, fl_hma
 /* Near-field entries A_ij (i, j in inadmissible leaf pairs) gathered from the dense float64
  * A (row pitch lda) of the same mesh and order.  Errors: FL_EINVAL, FL_ECUDA. */
 int fl_hmatrix_set_near(fl_hmatrix H, const double* A_dev, int64_t lda, void* stream);
+/*
+ * Near-field entries computed directly, by local computations only (Section 6: the near field
+ * is assembled into a sparse matrix; its cost is that of the near field, O(n log^{2d} n), with
+ * no dense matrix).  An entry a(phi_i, phi_j) gets
+ *   - the separated pairs at vertex-graph distance >= 2 of a cell of supp phi_i and a cell of
+ *     supp phi_j: only the 32 x 32 tiles of element blocks that near-field entries touch are
+ *     computed (float64 rules of the dense assembly, double-word arithmetic where its float64
+ *     mode uses it);
+ *   - the touching, near (distance 1) and identical pairs as in the dense assembly;
+ *   - the diagonal blocks, where the part that sums over the far cells and the boundary term
+ *     is, for x in K, C/(2s) times the integral over the boundary of N(K) (K, its touching
+ *     cells and the cells at distance 1) of n.(x - y)|x - y|^{-d-2s}, n pointing into N(K):
+ *     by the divergence theorem the same quantity, integrated over fewer facets (its facets
+ *     at distance 1 with the k_near rules, the others with k_far, the boundary facets of
+ *     Omega that touch K with the singular rules of the boundary term).
+ * Entries whose DOFs share no cell equal the dense float64 matrix's bit for bit; the others
+ * differ from it by the quadrature error of the far part of the diagonal blocks.  The first
+ * call plans (host) and allocates the tiles' workspace; later calls recompute the values.
+ * Not for regional operators, symmetry-reduced handles or 2D boundary DOFs (FL_ENOTIMPL).
+ * Errors: FL_EINVAL, FL_ENOMEM, FL_ENOTIMPL, FL_ECUDA.
+ */
+int fl_hmatrix_assemble_near(fl_hmatrix H, void* stream);
+/* The near field as CSR over the DOFs (rows ascending, columns ascending in a row): *nnz
+ * receives the entry count; non-NULL device arrays rowptr_dev [n + 1], col_dev [nnz] and
+ * val_dev [nnz] (float64) receive the pattern and the values (the values need a near field,
+ * else FL_EINVAL).  Copies on `stream`.  Errors: FL_EINVAL, FL_ECUDA. */
+int fl_hmatrix_get_near(fl_hmatrix H, int64_t* nnz, int32_t* rowptr_dev, int32_t* col_dev, double* val_dev,
+                        void* stream);
+/* info[0..2] after fl_hmatrix_assemble_near: tiles computed, their partial-block entries,
+ * device bytes of its plan and workspace (zeros before the first call). */
+int fl_hmatrix_near_info(fl_hmatrix H, int64_t* info);
 /* y_dev = H x_dev (float64 [n], y must not be x): near-field CSR product, upward pass,
  * couplings, downward pass; fixed summation orders.  Errors: FL_EINVAL (no near field
  * yet), FL_ECUDA. */

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfraclap.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["planner.cpp", "cluster.cpp", "capi.cpp", "tune.cpp", "pool.cpp", "assemble.cu", "far_dw.cu", "hmatrix.cu", "adaptive.cu", "refine.cpp", "symmetry.cpp", "linalg.cu", "noalloc.cu", "batch.cu", "mg.cu", "learned.cu"]
+SOURCES = ["planner.cpp", "cluster.cpp", "capi.cpp", "tune.cpp", "pool.cpp", "assemble.cu", "far_dw.cu", "hmatrix.cu", "adaptive.cu", "refine.cpp", "symmetry.cpp", "hnear.cpp", "linalg.cu", "noalloc.cu", "batch.cu", "mg.cu", "learned.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

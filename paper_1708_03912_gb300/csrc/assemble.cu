@@ -25,6 +25,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "cluster.h"
 #include "context.h"
 #include "device.h"
 
@@ -66,7 +67,7 @@ struct FarArgs {
     const int* inc_ptr;
     const int* inc_ent;
     T* P;
-    T* Pd;      // [cell][block][point] row sums
+    T* Pd;      // [cell][block][point] row sums; null: not wanted (the cluster method's near field)
     int64_t nc;
     int64_t nblk;
     T expo;
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
             if ((lane & 1) == 0) {
                 const int a = point_of_lane16(lane);
                 if (I == J) sD[kk * Q + a] += myDa;
-                else A.Pd[((int64_t)K * A.nblk + J) * Q + a] = myDa;
+                else if (A.Pd) A.Pd[((int64_t)K * A.nblk + J) * Q + a] = myDa;
             }
             __syncwarp();  // sU is rewritten by the next row cell
             continue;
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
             const int a = w * 32 + lane;
             if (a < Q) {
                 if (I == J) sD[kk * Q + a] += myD[w];
-                else A.Pd[((int64_t)K * A.nblk + J) * Q + a] = myD[w];
+                else if (A.Pd) A.Pd[((int64_t)K * A.nblk + J) * Q + a] = myD[w];
             }
         }
     }
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(32) far_tile_kernel(const FarArgs<T> A, const 
             S[2 * c + 1] = (T)S2[c].y;
         }
     }
-    if (valid) {
+    if (valid && A.Pd) {
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
             T v = S[b];
@@ -796,6 +797,13 @@ struct ElemArgs {
     double* contrib;
     int64_t slot0;
     double* eblk;  // nc x 6: the far-independent part of each cell's block (PART 1 -> PART 2)
+    // 1: the cluster method's near field.  The ef lists then hold, per cell K, the facets of the
+    // boundary of N(K) (K, its touching cells and those at vertex-graph distance 1), classes 0-3
+    // (0 = far), with normals pointing into N(K), in place of the boundary facets of Omega; there
+    // are no far row sums (nblk = 0) and no Bf: the far pairs' diagonal-block terms and the
+    // boundary term are the integral over that boundary (divergence theorem), its class-0
+    // facets at the far rule's points in PART 2 (2D) or in the facet loop (1D).
+    int cluster;
 };
 
 // One warp per cell with DOFs.  Lanes take quadrature points (or partner blocks)
@@ -886,7 +894,31 @@ __global__ void element_kernel(ElemArgs A) {
             const double other = __shfl_xor_sync(0xffffffffu, Dk, 16);
             Dk = (hb == 0) ? Dk + other : other + Dk;
             if (hb == 0 && a < qf) {
-                const double bf = (D == 2 && !A.regional) ? A.Bf[k * qf + a] : 0.0;
+                double bf = 0.0;
+                if (D == 2 && !A.regional && !A.cluster) bf = A.Bf[k * qf + a];
+                if (D == 2 && A.cluster) {
+                    // class-0 facets of the boundary of N(K) at far-rule point a, k_far-point Gauss rule
+                    const double* lam = rule + ro.far_lam;
+                    const double* gt = rule + ro.glf_t;
+                    const double* gw = rule + ro.glf_w;
+                    double xa[2];
+                    for (int d = 0; d < 2; ++d)
+                        xa[d] = v[d] + lam[a * 2] * (v[2 + d] - v[d]) + lam[a * 2 + 1] * (v[4 + d] - v[d]);
+                    for (int q = A.ef_ptr[k]; q < A.ef_ptr[k + 1]; ++q) {
+                        if (A.ef_cls[q] != 0) continue;
+                        const int f = A.ef_fac[q];
+                        const double* E0 = A.V + 2 * A.F[2 * f];
+                        const double* E1 = A.V + 2 * A.F[2 * f + 1];
+                        double acc = 0.0;
+                        for (int b = 0; b < ro.kf; ++b) {
+                            const double dx = xa[0] - (E0[0] + gt[b] * (E1[0] - E0[0]));
+                            const double dy = xa[1] - (E0[1] + gt[b] * (E1[1] - E0[1]));
+                            acc += gw[b] * A.FLEN[f] * (A.FN[2 * f] * dx + A.FN[2 * f + 1] * dy) *
+                                   facet_pow<PW>(dx * dx + dy * dy, -(1.0 + s), false);
+                        }
+                        bf += acc;
+                    }
+                }
                 const double f = jk * w[a] * (C * Dk + A.C2s * bf);
 #pragma unroll
                 for (int i = 0; i < NV; ++i)
@@ -1000,10 +1032,18 @@ __global__ void element_kernel(ElemArgs A) {
             const double* w = rule + ro.far_w;
             const double* lam = rule + ro.far_lam;
             const double* phi = rule + ro.far_phi;
-            for (int64_t f = 0; f < A.nf; ++f) {
+            // dense: every boundary facet of Omega, classes from the list; cluster: the list itself
+            const int64_t nloop = A.cluster ? (int64_t)(ee - ep) : A.nf;
+            for (int64_t it = 0; it < nloop; ++it) {
+                int64_t f = it;
                 int cls = 0;
-                while (ep < ee && A.ef_fac[ep] < f) ++ep;
-                if (ep < ee && A.ef_fac[ep] == f) cls = A.ef_cls[ep];
+                if (A.cluster) {
+                    f = A.ef_fac[ep + it];
+                    cls = A.ef_cls[ep + it];
+                } else {
+                    while (ep < ee && A.ef_fac[ep] < f) ++ep;
+                    if (ep < ee && A.ef_fac[ep] == f) cls = A.ef_cls[ep];
+                }
                 if (cls == 1) continue;  // near: done above
                 const int e = A.F[f];
                 if (cls == 2) {
@@ -1250,6 +1290,73 @@ __global__ void add_csr_kernel(int64_t nnz, const int* csr_row, const int* csr_c
     if (j != i) A[j * lda + i] += v;
 }
 
+// Near-field entries of the cluster method (Section 6).  Entry z = (i, j): the contribution slots
+// of the mesh plan's sparse entry (min, max), if that entry exists, summed in its gather order,
+// plus -C times the tile partials over the block occurrences of min(i, j) (major) and max(i, j),
+// summed as compose_far_kernel sums them; the product and the sum are not fused, so an entry
+// whose slots hold no diagonal block is bitwise the dense matrix's.  Tiles are found by
+// bisection in their row of the tile list; a tile missing from it (a broken plan) gives NaN.
+__global__ void hnear_compose_kernel(int64_t nnz, const int* __restrict__ nz_row, const int* __restrict__ nz_col,
+                                     const int* __restrict__ csr_ptr, const int* __restrict__ csr_col,
+                                     const int64_t* __restrict__ g_ptr, const int64_t* __restrict__ g_slot,
+                                     const double* __restrict__ contrib, const int* __restrict__ occ_ptr,
+                                     const int* __restrict__ occ_blk, const int* __restrict__ occ_loc,
+                                     const int* __restrict__ L_ptr, const int* __restrict__ trow_ptr,
+                                     const int* __restrict__ tiles, const int64_t* __restrict__ toff,
+                                     const double* __restrict__ Pt, double negC, double* __restrict__ val) {
+    const int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (z >= nnz) return;
+    const int i = nz_row[z], j = nz_col[z];
+    const int lo = min(i, j), hi = max(i, j);
+    double acc = 0.0;
+    {
+        int a = csr_ptr[lo], b = csr_ptr[lo + 1] - 1;
+        if (a <= b) {
+            while (a < b) {
+                const int mid = a + (b - a) / 2;
+                if (csr_col[mid] < hi) a = mid + 1;
+                else b = mid;
+            }
+            if (csr_col[a] == hi)
+                for (int64_t q = g_ptr[a]; q < g_ptr[a + 1]; ++q) acc += contrib[g_slot[q]];
+        }
+    }
+    double far = 0.0;
+    bool missing = false;
+    for (int oa = occ_ptr[lo]; oa < occ_ptr[lo + 1]; ++oa) {
+        const int Ba = occ_blk[oa], la = occ_loc[oa];
+        for (int ob = occ_ptr[hi]; ob < occ_ptr[hi + 1]; ++ob) {
+            const int Bb = occ_blk[ob], lb = occ_loc[ob];
+            const int B0 = min(Ba, Bb), B1 = max(Ba, Bb);
+            int a = trow_ptr[B0], b = trow_ptr[B0 + 1] - 1;
+            if (a > b) {
+                missing = true;
+                continue;
+            }
+            while (a < b) {
+                const int mid = a + (b - a) / 2;
+                if (tiles[2 * mid + 1] < B1) a = mid + 1;
+                else b = mid;
+            }
+            if (tiles[2 * a + 1] != B1) {
+                missing = true;
+                continue;
+            }
+            const int64_t base = toff[a];
+            if (Ba < Bb) {
+                far += Pt[base + (int64_t)la * (L_ptr[Bb + 1] - L_ptr[Bb]) + lb];
+            } else if (Ba > Bb) {
+                far += Pt[base + (int64_t)lb * (L_ptr[Ba + 1] - L_ptr[Ba]) + la];
+            } else {
+                const int64_t nL = L_ptr[Ba + 1] - L_ptr[Ba];
+                far += Pt[base + (int64_t)la * nL + lb];
+                far += Pt[base + (int64_t)lb * nL + la];
+            }
+        }
+    }
+    val[z] = missing ? __longlong_as_double(0x7ff8000000000000LL) : __dadd_rn(__dmul_rn(negC, far), acc);
+}
+
 // ------------------------------------------------- symmetry reduction --
 // Rows of the orbit representatives (Section 7, "Exploiting Symmetry"): R[r][j] is the far-field
 // part of the whole matrix's entry (rep_r, j), summed from the tile partials exactly as
@@ -1468,8 +1575,6 @@ int ensure_device(fl_ctx* h, int pi, cudaStream_t st) {
     U.add(t.L_ptr, P.L_ptr);
     U.add(t.inc_ptr, P.inc_ptr);
     U.add(t.inc_ent, P.inc_ent);
-    U.add(t.tiles, P.tiles);
-    U.add(t.toff, P.toff);
     U.add(t.occ_ptr, P.occ_ptr);
     U.add(t.occ_blk, P.occ_blk);
     U.add(t.occ_loc, P.occ_loc);
@@ -1504,7 +1609,6 @@ int ensure_device(fl_ctx* h, int pi, cudaStream_t st) {
         U.add(t.red_ptr, P.red_ptr);
         U.add(t.red_mem, P.red_mem);
         U.add(t.red_row, P.red_row);
-        U.add(t.tri_list, P.tri_list);
         sector_of.assign(P.nv, 0);
         for (int l = 0; l < h->sym_K; ++l)
             for (int64_t v = 0; v < h->sym_nvs; ++v) sector_of[h->sym_vmap[(size_t)l * h->sym_nvs + v]] = (int)v;
@@ -1512,8 +1616,6 @@ int ensure_device(fl_ctx* h, int pi, cudaStream_t st) {
     }
     FL_TRY(upload_all(h, U, st));
     const int qf = qf_of(h), qn = qn_of(h);
-    FL_TRY(alloc(h, &t.P, (size_t)P.toff.back() * sizeof(double)));
-    FL_TRY(alloc(h, &t.Pd, (size_t)P.nblk * nc * qf * sizeof(double)));
     FL_TRY(alloc(h, &t.pts, (size_t)nc * qf * D * sizeof(double)));
     if (D == 2 && qf == 16) {
         FL_TRY(alloc(h, &t.pts_dw, (size_t)nc * 16 * sizeof(float4)));
@@ -1533,6 +1635,26 @@ int ensure_device(fl_ctx* h, int pi, cudaStream_t st) {
         FL_CUDA_TRY(h, cudaGetLastError());
     }
     t.ready = true;
+    return FL_OK;
+}
+
+// The dense assembly's tile tables and far-field workspace (every upper-triangle tile of the
+// block pairs, its partial blocks and the per-point row sums: O(n^2) memory), separate from
+// ensure_device so that the calls that need none of it (the cluster method, the strong form,
+// the mass matrix) never allocate it.
+int ensure_dense(fl_ctx* h, int pi, cudaStream_t st) {
+    DevTables& t = h->dev[pi];
+    FL_TRY(ensure_device(h, pi, st));
+    if (t.dense_ready) return FL_OK;
+    const Plan& P = h->plan[pi];
+    Uploads U;
+    U.add(t.tiles, P.tiles);
+    U.add(t.toff, P.toff);
+    if (P.sym_K) U.add(t.tri_list, P.tri_list);
+    FL_TRY(upload_all(h, U, st));
+    FL_TRY(alloc(h, &t.P, (size_t)P.toff.back() * sizeof(double)));
+    FL_TRY(alloc(h, &t.Pd, (size_t)P.nblk * P.nc * qf_of(h) * sizeof(double)));
+    t.dense_ready = true;
     return FL_OK;
 }
 
@@ -1699,7 +1821,7 @@ int pw_mode(int dim, double s) {
 
 template <int D, typename T, int Q, int PW>
 int launch_far_t(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro,
-                 double expo, cudaStream_t st) {
+                 double expo, int64_t ntiles, cudaStream_t st) {
     constexpr int NV = D + 1;
     FarRule<T, Q, NV> R;
     for (int a = 0; a < Q; ++a) {
@@ -1729,56 +1851,59 @@ int launch_far_t(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<doubl
     const int maxL = std::max(1, P.maxL);
     size_t smem = 32 * D * sizeof(double) + 32 * sizeof(double) + 32 * Q * (Q == 16 ? 1 : D) * sizeof(T) + 32 * Q * sizeof(T) +
                   (size_t)NV * maxL * 32 * sizeof(T) + 32 * NV * sizeof(int) + 32 * sizeof(int);
-    const int64_t ntiles = (int64_t)P.tiles.size() / 2;
     auto kern = far_tile_kernel<D, T, Q, PW>;
     FL_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)ntiles, 32, smem, st>>>(A, R, maxL); fl::count_launch();
+    if (ntiles > 0) {
+        kern<<<(unsigned)ntiles, 32, smem, st>>>(A, R, maxL);
+        fl::count_launch();
+    }
     FL_CUDA_TRY(h, cudaGetLastError());
     return FL_OK;
 }
 
 template <int D, typename T, int Q>
 int launch_far_q(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro,
-                 double expo, int pw, cudaStream_t st) {
+                 double expo, int pw, int64_t nt, cudaStream_t st) {
     // specialised square-root forms only for the default orders (k_far = 4)
     if constexpr (D == 2 && Q == 16) {
         switch (pw) {
-            case 5: return launch_far_t<D, T, Q, 5>(h, P, t, rb, ro, expo, st);
-            case 6: return launch_far_t<D, T, Q, 6>(h, P, t, rb, ro, expo, st);
-            case 7: return launch_far_t<D, T, Q, 7>(h, P, t, rb, ro, expo, st);
+            case 5: return launch_far_t<D, T, Q, 5>(h, P, t, rb, ro, expo, nt, st);
+            case 6: return launch_far_t<D, T, Q, 6>(h, P, t, rb, ro, expo, nt, st);
+            case 7: return launch_far_t<D, T, Q, 7>(h, P, t, rb, ro, expo, nt, st);
             default: break;
         }
     } else if constexpr (D == 1 && Q == 4) {
         switch (pw) {
-            case 3: return launch_far_t<D, T, Q, 3>(h, P, t, rb, ro, expo, st);
-            case 4: return launch_far_t<D, T, Q, 4>(h, P, t, rb, ro, expo, st);
-            case 5: return launch_far_t<D, T, Q, 5>(h, P, t, rb, ro, expo, st);
+            case 3: return launch_far_t<D, T, Q, 3>(h, P, t, rb, ro, expo, nt, st);
+            case 4: return launch_far_t<D, T, Q, 4>(h, P, t, rb, ro, expo, nt, st);
+            case 5: return launch_far_t<D, T, Q, 5>(h, P, t, rb, ro, expo, nt, st);
             default: break;
         }
     }
-    return launch_far_t<D, T, Q, 0>(h, P, t, rb, ro, expo, st);
+    return launch_far_t<D, T, Q, 0>(h, P, t, rb, ro, expo, nt, st);
 }
 
 template <typename T>
 int launch_far(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro,
-               double expo, int pw, cudaStream_t st) {
+               double expo, int pw, cudaStream_t st, int64_t ntiles = -1) {
     const int k = h->opt.k_far;
+    const int64_t nt = ntiles >= 0 ? ntiles : (int64_t)P.tiles.size() / 2;
     if (P.dim == 2) {
         switch (k) {
-            case 3: return launch_far_q<2, T, 9>(h, P, t, rb, ro, expo, pw, st);
-            case 4: return launch_far_q<2, T, 16>(h, P, t, rb, ro, expo, pw, st);
-            case 5: return launch_far_q<2, T, 25>(h, P, t, rb, ro, expo, pw, st);
-            case 6: return launch_far_q<2, T, 36>(h, P, t, rb, ro, expo, pw, st);
+            case 3: return launch_far_q<2, T, 9>(h, P, t, rb, ro, expo, pw, nt, st);
+            case 4: return launch_far_q<2, T, 16>(h, P, t, rb, ro, expo, pw, nt, st);
+            case 5: return launch_far_q<2, T, 25>(h, P, t, rb, ro, expo, pw, nt, st);
+            case 6: return launch_far_q<2, T, 36>(h, P, t, rb, ro, expo, pw, nt, st);
             default: break;
         }
     } else {
         switch (k) {
-            case 2: return launch_far_q<1, T, 2>(h, P, t, rb, ro, expo, pw, st);
-            case 3: return launch_far_q<1, T, 3>(h, P, t, rb, ro, expo, pw, st);
-            case 4: return launch_far_q<1, T, 4>(h, P, t, rb, ro, expo, pw, st);
-            case 5: return launch_far_q<1, T, 5>(h, P, t, rb, ro, expo, pw, st);
-            case 6: return launch_far_q<1, T, 6>(h, P, t, rb, ro, expo, pw, st);
-            case 8: return launch_far_q<1, T, 8>(h, P, t, rb, ro, expo, pw, st);
+            case 2: return launch_far_q<1, T, 2>(h, P, t, rb, ro, expo, pw, nt, st);
+            case 3: return launch_far_q<1, T, 3>(h, P, t, rb, ro, expo, pw, nt, st);
+            case 4: return launch_far_q<1, T, 4>(h, P, t, rb, ro, expo, pw, nt, st);
+            case 5: return launch_far_q<1, T, 5>(h, P, t, rb, ro, expo, pw, nt, st);
+            case 6: return launch_far_q<1, T, 6>(h, P, t, rb, ro, expo, pw, nt, st);
+            case 8: return launch_far_q<1, T, 8>(h, P, t, rb, ro, expo, pw, nt, st);
             default: break;
         }
     }
@@ -1866,26 +1991,130 @@ struct CsrOut {
     double* val;
 };
 
-static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t lda, const CsrOut* csr,
-                         cudaStream_t st) {
-    const int pi = plan_for(h, s);
-    if (pi < 0) return FL_EINVAL;
-    const Plan& P = h->plan[pi];
-    const bool sym = P.sym_K > 0;
-    if (!csr) {
-        if (lda < (sym ? P.n_red : P.n)) return set_err(h, FL_EINVAL, "lda < n");
-        if (!A) return set_err(h, FL_EINVAL, "A is NULL");
-    }
-    if (precision != FL_FP64 && precision != FL_MIXED) return set_err(h, FL_EINVAL, "unknown precision");
-    if (P.dim == 2 && P.paper_all && !h->opt.regional)
-        return set_err(h, FL_ENOTIMPL, "2D boundary DOFs (FL_DOF_PAPER with s < 1/2) are not implemented");
-    FL_CUDA_TRY(h, cudaSetDevice(h->device));
-    FL_TRY(ensure_device(h, pi, st));
-    DevTables& t = h->dev[pi];
+// Near separated pairs (vertex-graph distance 1): off-diagonal blocks (times -C) into the
+// contribution slots, per-point row sums of both cells into Dn.
+static int launch_near_pairs(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb,
+                             const RuleOffsets& ro, double expo, int pw, bool f32, double C, cudaStream_t st) {
     const int D = P.dim;
-    // per-s rule tables, built and uploaded once per (handle, s): repeated assemblies at the
-    // same s do no host work here and no host-synchronising copy
-    const bool f32 = precision == FL_MIXED;
+    const int pw32 = (pw == 4 || pw == 6) ? pw : 0;
+    const int nnear = (int)P.np_a.size();
+    const bool near_fast = (D == 2 && ro.qn == 36) || (D == 1 && ro.qn == 6);
+    if (nnear > 0 && near_fast) {
+        if (D == 2) {
+            if (f32) FL_TRY(launch_near_fast<2, float, 36>(h, P, t, rb, ro, expo, pw32, C, st));
+            else FL_TRY(launch_near_fast<2, double, 36>(h, P, t, rb, ro, expo, pw, C, st));
+        } else {
+            if (f32) FL_TRY(launch_near_fast<1, float, 6>(h, P, t, rb, ro, expo, pw32, C, st));
+            else FL_TRY(launch_near_fast<1, double, 6>(h, P, t, rb, ro, expo, pw, C, st));
+        }
+    } else if (nnear > 0) {
+        const unsigned g = (unsigned)((nnear + 63) / 64);
+#define FL_NEAR(DD, TT, PWV)                                                                                    \
+    near_pair_kernel<DD, TT, PWV><<<g, 64, 0, st>>>(nnear, t.np_a, t.np_b, t.cvx, t.cen, t.jac, t.rule, ro, (TT)expo, \
+                                                    C, t.contrib, P.np_slot0, t.Dn)
+        if (D == 2) {
+            if (f32) { if (pw == 6) FL_NEAR(2, float, 6); else FL_NEAR(2, float, 0); }
+            else { if (pw == 5) FL_NEAR(2, double, 5); else if (pw == 6) FL_NEAR(2, double, 6); else if (pw == 7) FL_NEAR(2, double, 7); else FL_NEAR(2, double, 0); }
+        } else {
+            if (f32) { if (pw == 4) FL_NEAR(1, float, 4); else FL_NEAR(1, float, 0); }
+            else { if (pw == 3) FL_NEAR(1, double, 3); else if (pw == 4) FL_NEAR(1, double, 4); else if (pw == 5) FL_NEAR(1, double, 5); else FL_NEAR(1, double, 0); }
+        }
+#undef FL_NEAR
+        fl::count_launch();
+        FL_CUDA_TRY(h, cudaGetLastError());
+    }
+    return FL_OK;
+}
+
+// Touching pairs (common edge / common vertex), one warp each, full blocks into their slots.
+static int launch_touch_pairs(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, double s, double C,
+                              int pw, bool f32, cudaStream_t st) {
+    const int D = P.dim;
+    const int ntp = (int)P.tp_type.size();
+    if (ntp == 0) return FL_OK;
+    const unsigned g = (unsigned)(((int64_t)ntp * 32 + 127) / 128);  // one warp per pair
+#define FL_TOUCH(TT, RULE, PWV) \
+    touch_pair_kernel<TT, PWV><<<g, 128, 0, st>>>(ntp, D, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, RULE, ro, s, C, t.contrib)
+    if (f32) {
+        if (D == 2 && pw == 6) FL_TOUCH(float, t.rule32, 6);
+        else FL_TOUCH(float, t.rule32, 0);
+    } else if (D == 2 && pw == 5) FL_TOUCH(double, t.rule, 5);
+    else if (D == 2 && pw == 6) FL_TOUCH(double, t.rule, 6);
+    else if (D == 2 && pw == 7) FL_TOUCH(double, t.rule, 7);
+    else FL_TOUCH(double, t.rule, 0);
+#undef FL_TOUCH
+    fl::count_launch();
+    FL_CUDA_TRY(h, cudaGetLastError());
+    return FL_OK;
+}
+
+static ElemArgs elem_args(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, double s, double C, bool f32) {
+    ElemArgs E;
+    E.dim = P.dim;
+    E.nc = P.nc;
+    E.nblk = P.nblk;
+    E.nf = P.nf;
+    E.nnear = (int64_t)P.np_a.size();
+    E.cvx = t.cvx;
+    E.cen = t.cen;
+    E.jac = t.jac;
+    E.hasdof = t.hasdof;
+    E.Pd = t.Pd;
+    E.pd_is_float = f32 ? 1 : 0;
+    E.Dn = t.Dn;
+    E.enp_ptr = t.enp_ptr;
+    E.enp_ent = t.enp_ent;
+    E.Bf = t.Bf;
+    E.ef_ptr = t.ef_ptr;
+    E.ef_fac = t.ef_fac;
+    E.ef_cls = t.ef_cls;
+    E.F = t.F;
+    E.FN = t.FN;
+    E.FLEN = t.FLEN;
+    E.V = t.V;
+    E.corner = t.corig;
+    E.rule = t.rule;
+    E.C2s = C / (2.0 * s);
+    E.r2s = 1.0 / (2.0 - 2.0 * s);
+    E.r3s = 1.0 / (3.0 - 2.0 * s);
+    E.r4s = 1.0 / (4.0 - 2.0 * s);
+    E.rule32 = f32 ? t.rule32 : nullptr;
+    E.ro = ro;
+    E.s = s;
+    E.C = C;
+    E.regional = h->opt.regional;
+    E.contrib = t.contrib;
+    E.slot0 = P.el_slot0;
+    E.eblk = t.eblk;
+    E.cluster = 0;
+    return E;
+}
+
+// One warp per cell; part 1 (far-independent) or part 2 (the diagonal block into its slots).
+static int launch_element(fl_ctx* h, const ElemArgs& E, int pw, int part, cudaStream_t st) {
+    const int D = E.dim;
+    const unsigned ge = (unsigned)((E.nc * 32 + 127) / 128);
+    auto go = [&](auto pt) {
+        constexpr int PT = decltype(pt)::value;
+        if (D == 2 && pw == 5) element_kernel<5, 2, PT><<<ge, 128, 0, st>>>(E);
+        else if (D == 2 && pw == 6) element_kernel<6, 2, PT><<<ge, 128, 0, st>>>(E);
+        else if (D == 2 && pw == 7) element_kernel<7, 2, PT><<<ge, 128, 0, st>>>(E);
+        else if (D == 2) element_kernel<0, 2, PT><<<ge, 128, 0, st>>>(E);
+        else element_kernel<0, 1, PT><<<ge, 128, 0, st>>>(E);
+    };
+    if (E.nc > 0) {
+        if (part == 1) go(std::integral_constant<int, 1>{});
+        else go(std::integral_constant<int, 2>{});
+        fl::count_launch();
+    }
+    FL_CUDA_TRY(h, cudaGetLastError());
+    return FL_OK;
+}
+
+// Per-s rule tables on the device, built and uploaded once per (handle, plan, s): repeated
+// calls at the same s do no host work and no host-synchronising copy.  f32: also the float32
+// copy (mixed-mode touching pairs and identical pair).
+static int ensure_rules(fl_ctx* h, DevTables& t, double s, bool f32, cudaStream_t st) {
     if (!(t.rule_s == s)) {
         t.rule_s = std::nan("");
         t.rule32_ready = false;
@@ -1901,7 +2130,7 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
         FL_CUDA_TRY(h, cudaMemcpyAsync(t.rule, rb.data(), rb.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         t.rule_s = s;
     }
-    if (f32 && !t.rule32_ready) {  // float32 copy of the tables (mixed-mode touching pairs, identical pair)
+    if (f32 && !t.rule32_ready) {
         const std::vector<double>& rb = t.rule_host;
         if (t.rule32_len < rb.size()) {
             void* p = nullptr;
@@ -1913,6 +2142,28 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
         FL_CUDA_TRY(h, cudaMemcpyAsync(t.rule32, rb32.data(), rb32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
         t.rule32_ready = true;
     }
+    return FL_OK;
+}
+
+static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t lda, const CsrOut* csr,
+                         cudaStream_t st) {
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    const bool sym = P.sym_K > 0;
+    if (!csr) {
+        if (lda < (sym ? P.n_red : P.n)) return set_err(h, FL_EINVAL, "lda < n");
+        if (!A) return set_err(h, FL_EINVAL, "A is NULL");
+    }
+    if (precision != FL_FP64 && precision != FL_MIXED) return set_err(h, FL_EINVAL, "unknown precision");
+    if (P.dim == 2 && P.paper_all && !h->opt.regional)
+        return set_err(h, FL_ENOTIMPL, "2D boundary DOFs (FL_DOF_PAPER with s < 1/2) are not implemented");
+    FL_CUDA_TRY(h, cudaSetDevice(h->device));
+    FL_TRY(ensure_dense(h, pi, st));
+    DevTables& t = h->dev[pi];
+    const int D = P.dim;
+    const bool f32 = precision == FL_MIXED;
+    FL_TRY(ensure_rules(h, t, s, f32, st));
     const std::vector<double>& rb = t.rule_host;
     const RuleOffsets& ro = t.rule_ro;
     const double C = frac_constant(D, s);
@@ -2001,52 +2252,11 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
         auto run_side = [&]() -> int {
             const cudaStream_t st = sst;
             stage_mark(h, st, FL_STAGE_NEAR, 0);
-            // near separated pairs
-            const int nnear = (int)P.np_a.size();
-            const bool near_fast = (D == 2 && ro.qn == 36) || (D == 1 && ro.qn == 6);
-            if (nnear > 0 && near_fast) {
-                if (D == 2) {
-                    if (f32) FL_TRY(launch_near_fast<2, float, 36>(h, P, t, rb, ro, expo, pw32, C, st));
-                    else FL_TRY(launch_near_fast<2, double, 36>(h, P, t, rb, ro, expo, pw, C, st));
-                } else {
-                    if (f32) FL_TRY(launch_near_fast<1, float, 6>(h, P, t, rb, ro, expo, pw32, C, st));
-                    else FL_TRY(launch_near_fast<1, double, 6>(h, P, t, rb, ro, expo, pw, C, st));
-                }
-            } else if (nnear > 0) {
-                const unsigned g = (unsigned)((nnear + 63) / 64);
-#define FL_NEAR(DD, TT, PWV)                                                                                    \
-            near_pair_kernel<DD, TT, PWV><<<g, 64, 0, st>>>(nnear, t.np_a, t.np_b, t.cvx, t.cen, t.jac, t.rule, ro, (TT)expo, \
-                                                            C, t.contrib, P.np_slot0, t.Dn)
-                if (D == 2) {
-                    if (f32) { if (pw == 6) FL_NEAR(2, float, 6); else FL_NEAR(2, float, 0); }
-                    else { if (pw == 5) FL_NEAR(2, double, 5); else if (pw == 6) FL_NEAR(2, double, 6); else if (pw == 7) FL_NEAR(2, double, 7); else FL_NEAR(2, double, 0); }
-                } else {
-                    if (f32) { if (pw == 4) FL_NEAR(1, float, 4); else FL_NEAR(1, float, 0); }
-                    else { if (pw == 3) FL_NEAR(1, double, 3); else if (pw == 4) FL_NEAR(1, double, 4); else if (pw == 5) FL_NEAR(1, double, 5); else FL_NEAR(1, double, 0); }
-                }
-#undef FL_NEAR
-                fl::count_launch();
-                FL_CUDA_TRY(h, cudaGetLastError());
-            }
+            FL_TRY(launch_near_pairs(h, P, t, rb, ro, expo, pw, f32, C, st));
             stage_mark(h, st, FL_STAGE_NEAR, 1);
             // touching pairs (float64; float32 in the mixed mode)
             stage_mark(h, st, FL_STAGE_TOUCH, 0);
-            const int ntp = (int)P.tp_type.size();
-            if (ntp > 0) {
-                const unsigned g = (unsigned)(((int64_t)ntp * 32 + 127) / 128);  // one warp per pair
-#define FL_TOUCH(TT, RULE, PWV) \
-            touch_pair_kernel<TT, PWV><<<g, 128, 0, st>>>(ntp, D, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, RULE, ro, s, C, t.contrib)
-                if (f32) {
-                    if (D == 2 && pw == 6) FL_TOUCH(float, t.rule32, 6);
-                    else FL_TOUCH(float, t.rule32, 0);
-                } else if (D == 2 && pw == 5) FL_TOUCH(double, t.rule, 5);
-                else if (D == 2 && pw == 6) FL_TOUCH(double, t.rule, 6);
-                else if (D == 2 && pw == 7) FL_TOUCH(double, t.rule, 7);
-                else FL_TOUCH(double, t.rule, 0);
-#undef FL_TOUCH
-                fl::count_launch();
-                FL_CUDA_TRY(h, cudaGetLastError());
-            }
+            FL_TRY(launch_touch_pairs(h, P, t, ro, s, C, pw, f32, st));
             stage_mark(h, st, FL_STAGE_TOUCH, 1);
             // boundary term over far facets (2D)
             stage_mark(h, st, FL_STAGE_BND, 0);
@@ -2060,61 +2270,13 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
             // that adds the far field's per-point row sums once the far stage is done
             stage_mark(h, st, FL_STAGE_ELEMENT, 0);
             {
-                ElemArgs E;
-                E.dim = D;
-                E.nc = nc;
-                E.nblk = P.nblk;
-                E.nf = P.nf;
-                E.nnear = nnear;
-                E.cvx = t.cvx;
-                E.cen = t.cen;
-                E.jac = t.jac;
-                E.hasdof = t.hasdof;
-                E.Pd = t.Pd;
-                E.pd_is_float = f32 ? 1 : 0;
-                E.Dn = t.Dn;
-                E.enp_ptr = t.enp_ptr;
-                E.enp_ent = t.enp_ent;
-                E.Bf = t.Bf;
-                E.ef_ptr = t.ef_ptr;
-                E.ef_fac = t.ef_fac;
-                E.ef_cls = t.ef_cls;
-                E.F = t.F;
-                E.FN = t.FN;
-                E.FLEN = t.FLEN;
-                E.V = t.V;
-                E.corner = t.corig;
-                E.rule = t.rule;
-                E.C2s = C / (2.0 * s);
-                E.r2s = 1.0 / (2.0 - 2.0 * s);
-                E.r3s = 1.0 / (3.0 - 2.0 * s);
-                E.r4s = 1.0 / (4.0 - 2.0 * s);
-                E.rule32 = f32 ? t.rule32 : nullptr;
-                E.ro = ro;
-                E.s = s;
-                E.C = C;
-                E.regional = h->opt.regional;
-                E.contrib = t.contrib;
-                E.slot0 = P.el_slot0;
-                E.eblk = t.eblk;
-                const unsigned ge = (unsigned)((nc * 32 + 127) / 128);  // one warp per cell
-                auto launch_elem = [&](auto part) {
-                    constexpr int PT = decltype(part)::value;
-                    if (D == 2 && pw == 5) element_kernel<5, 2, PT><<<ge, 128, 0, st>>>(E);
-                    else if (D == 2 && pw == 6) element_kernel<6, 2, PT><<<ge, 128, 0, st>>>(E);
-                    else if (D == 2 && pw == 7) element_kernel<7, 2, PT><<<ge, 128, 0, st>>>(E);
-                    else if (D == 2) element_kernel<0, 2, PT><<<ge, 128, 0, st>>>(E);
-                    else element_kernel<0, 1, PT><<<ge, 128, 0, st>>>(E);
-                    fl::count_launch();
-                };
-                launch_elem(std::integral_constant<int, 1>{});
-                FL_CUDA_TRY(h, cudaGetLastError());
+                const ElemArgs E = elem_args(h, P, t, ro, s, C, f32);
+                FL_TRY(launch_element(h, E, pw, 1, st));
                 if (sst != h_st) {
                     FL_CUDA_TRY(h, cudaEventRecord(h->ev_far, h_st));
                     FL_CUDA_TRY(h, cudaStreamWaitEvent(sst, h->ev_far, 0));
                 }
-                launch_elem(std::integral_constant<int, 2>{});
-                FL_CUDA_TRY(h, cudaGetLastError());
+                FL_TRY(launch_element(h, E, pw, 2, st));
             }
             stage_mark(h, st, FL_STAGE_ELEMENT, 1);
             // sparse near-field values
@@ -2208,6 +2370,71 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
 // mesh at order s: for each, one warm-up assembly and `reps` profiled ones (stages in
 // sequence, the far stage timed alone by CUDA events); the median decides.  The winner is
 // recorded in the tuning table under (kernel, cell count), which later assemblies consult.
+// The near field of the cluster method from local computations (Section 6): the tiles the
+// near-field entries touch (separated pairs at distance >= 2, the off-diagonal blocks only),
+// near and touching pairs as in the dense assembly, the diagonal blocks with the integral over
+// the boundary of N(K) in place of the far pairs' and the boundary facets' part (element
+// kernel, cluster mode), and the entries composed from these.  Float64 (double-word far pairs
+// where the dense float64 mode takes them).  No O(n^2) table or workspace is touched.
+int assemble_hnear(fl_ctx* h, int pi, double s, const HNearDev& q, int64_t nnz, const int* nz_row,
+                   const int* nz_col, double* nz_val, cudaStream_t st) {
+    const Plan& P = h->plan[pi];
+    if (P.sym_K) return sym_unsupported(h, "the cluster method's near-field assembly");
+    if (h->opt.regional) return set_err(h, FL_ENOTIMPL, "the near-field assembly needs the boundary term (not regional)");
+    if (P.dim == 2 && P.paper_all) return set_err(h, FL_ENOTIMPL, "2D boundary DOFs are not implemented");
+    FL_CUDA_TRY(h, cudaSetDevice(h->device));
+    FL_TRY(ensure_device(h, pi, st));
+    FL_TRY(ensure_rules(h, h->dev[pi], s, false, st));
+    DevTables t = h->dev[pi];  // the mesh tables, with this assembly's tiles, facets and workspace
+    t.tiles = q.tiles;
+    t.toff = q.toff;
+    t.P = q.P;
+    t.Pd = nullptr;
+    t.ef_ptr = q.ef_ptr;
+    t.ef_fac = q.ef_fac;
+    t.ef_cls = q.ef_cls;
+    t.F = q.F;
+    t.FN = q.FN;
+    t.FLEN = q.FLEN;
+    const std::vector<double>& rb = t.rule_host;
+    const RuleOffsets& ro = t.rule_ro;
+    const int D = P.dim;
+    const double C = frac_constant(D, s);
+    const double expo = -(D + 2.0 * s) / 2.0;
+    const int pw = pw_mode(D, s);
+    const int64_t nc = P.nc;
+    const unsigned gb = (unsigned)((nc + 127) / 128);
+    if (nc > 0) {
+        if (D == 2) prep_points<double, 2><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts);
+        else prep_points<double, 1><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts);
+        fl::count_launch();
+    }
+    FL_CUDA_TRY(h, cudaGetLastError());
+    const bool dw = D == 2 && far_dw_applies(h, P, pw);
+    if (dw) FL_TRY(prep_far_dw(h, P, t, ro, st));
+    if (q.ntiles > 0) {
+        if (dw) FL_TRY(launch_far_dw(h, P, t, rb, ro, pw, st, q.ntiles));
+        else FL_TRY(launch_far<double>(h, P, t, rb, ro, expo, pw, st, q.ntiles));
+    }
+    FL_TRY(launch_near_pairs(h, P, t, rb, ro, expo, pw, false, C, st));
+    FL_TRY(launch_touch_pairs(h, P, t, ro, s, C, pw, false, st));
+    ElemArgs E = elem_args(h, P, t, ro, s, C, false);
+    E.cluster = 1;
+    E.nblk = 0;
+    E.Pd = nullptr;
+    E.Bf = nullptr;
+    FL_TRY(launch_element(h, E, pw, 1, st));
+    FL_TRY(launch_element(h, E, pw, 2, st));
+    if (nnz > 0) {
+        hnear_compose_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(
+            nnz, nz_row, nz_col, t.csr_ptr, t.csr_col, t.g_ptr, t.g_slot, t.contrib, t.occ_ptr, t.occ_blk, t.occ_loc,
+            t.L_ptr, q.trow_ptr, q.tiles, q.toff, q.P, -C, nz_val);
+        fl::count_launch();
+    }
+    FL_CUDA_TRY(h, cudaGetLastError());
+    return FL_OK;
+}
+
 int tune_assemble(fl_ctx* h, double s, double* A, int64_t lda, int reps, int* best_variant, double* best_ms,
                   cudaStream_t st) {
     if (reps < 1) return set_err(h, FL_EINVAL, "reps < 1");

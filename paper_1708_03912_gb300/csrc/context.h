@@ -57,6 +57,7 @@ struct DBuf {
 // Device copies of one Plan (one DOF set).
 struct DevTables {
     bool ready = false;
+    bool dense_ready = false;  // the dense assembly's tiles and far-field workspace (ensure_dense)
     // mesh
     double* V = nullptr;        // nv*dim
     double* jac_orig = nullptr; // nc (original order)
@@ -202,13 +203,19 @@ unsigned tune_generation();  // changes whenever the table changes
 // the launch variant it takes and the autotuner's record of one
 bool far_dw_applies(const fl_ctx* h, const Plan& P, int pw);
 int prep_far_dw(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, cudaStream_t st);
+// (ntiles < 0: all of P.tiles; else the first ntiles of the tile list in t)
 int launch_far_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro, int pw,
-                  cudaStream_t st);
+                  cudaStream_t st, int64_t ntiles = -1);
 int far_dw_variant(const fl_ctx* h, const Plan& P, int pw);
 int bnd_dw_chunks(int64_t nc);
 int launch_bnd_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro, int pw,
                   cudaStream_t st);
 void far_dw_record(const Plan& P, int pw, int variant, double ms);
+// the cluster method's near field from local computations (assemble.cu): nnz entries (row, col
+// DOF ids) into nz_val; uses the handle's contribution slots and row-sum buffers
+struct HNearDev;
+int assemble_hnear(fl_ctx* h, int pi, double s, const HNearDev& q, int64_t nnz, const int* nz_row,
+                   const int* nz_col, double* nz_val, cudaStream_t st);
 // adaptive loop (adaptive.cu, refine.cpp)
 int strong_form(fl_ctx* h, double s, const double* u, int k_cell, int k_edge, int k_near, double* S, cudaStream_t st);
 int br_indicators(fl_ctx* h, double s, const double* u, const double* f, int k_cell, int k_edge, int k_near,

@@ -55,7 +55,7 @@ struct DwTileArgs {
     const int* inc_ent;
     const float4* pts;  // [cell][16] (x.h, x.l, y.h, y.l)
     double* P;
-    double* Pd;  // [cell][block][point] row sums
+    double* Pd;  // [cell][block][point] row sums; null: not wanted (the cluster method's near field)
     int64_t nc;
     int64_t nblk;
 };
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
         }
         act = act && (hj || sHas[kk] != 0);
         if (!__any_sync(0xffffffffu, act)) {  // the same in every warp of the block
-            if (I != J)
+            if (I != J && A.Pd)
                 for (int a = threadIdx.x; a < Q; a += blockDim.x) A.Pd[((int64_t)K * A.nblk + J) * Q + a] = 0.0;
             continue;
         }
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
             if ((lane & 7) == 0) {
                 const int a = warp + DW_WARPS * ((((lane >> 4) & 1) << 1) | ((lane >> 3) & 1));
                 if (I == J) sD[kk * Q + a] += dw_to(tot);
-                else A.Pd[((int64_t)K * A.nblk + J) * Q + a] = dw_to(tot);
+                else if (A.Pd) A.Pd[((int64_t)K * A.nblk + J) * Q + a] = dw_to(tot);
             }
         }
 #pragma unroll
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
         __syncthreads();
     }
     // column sums of this tile's cells: the warps' parts added in warp order
-    if (valid) {
+    if (valid && A.Pd) {
         for (int b = warp; b < Q; b += DW_WARPS) {
             dw acc = sS[b * 32 + lane];
             for (int w = 1; w < DW_WARPS; ++w) acc = dw_add(acc, sS[(w * Q + b) * 32 + lane]);
@@ -417,7 +417,7 @@ size_t dw_smem_bytes(int maxL) {
 }
 
 template <int PW, int UB, int MINB>
-int launch_t(fl_ctx* h, const Plan& P, DevTables& t, const FarRuleDW& R, cudaStream_t st) {
+int launch_t(fl_ctx* h, const Plan& P, DevTables& t, const FarRuleDW& R, int64_t ntiles, cudaStream_t st) {
     DwTileArgs A;
     A.cen = t.cen;
     A.jac = t.jac;
@@ -437,7 +437,6 @@ int launch_t(fl_ctx* h, const Plan& P, DevTables& t, const FarRuleDW& R, cudaStr
     A.nblk = P.nblk;
     const int maxL = std::max(1, P.maxL);
     const size_t smem = dw_smem_bytes(maxL);
-    const int64_t ntiles = (int64_t)P.tiles.size() / 2;
     auto kern = far_tile_dw_kernel<PW, UB, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_err(h, FL_ECUDA, std::string("far_tile_dw smem: ") + cudaGetErrorString(e));
@@ -455,12 +454,12 @@ int launch_t(fl_ctx* h, const Plan& P, DevTables& t, const FarRuleDW& R, cudaStr
 constexpr int DW_VARIANTS = 4;
 
 template <int PW>
-int launch_pw(fl_ctx* h, const Plan& P, DevTables& t, const FarRuleDW& R, int variant, cudaStream_t st) {
+int launch_pw(fl_ctx* h, const Plan& P, DevTables& t, const FarRuleDW& R, int variant, int64_t nt, cudaStream_t st) {
     switch (variant) {
-        case 1: return launch_t<PW, 4, 1>(h, P, t, R, st);
-        case 2: return launch_t<PW, 1, 2>(h, P, t, R, st);
-        case 4: return launch_t<PW, 1, 3>(h, P, t, R, st);
-        default: return launch_t<PW, 2, 2>(h, P, t, R, st);
+        case 1: return launch_t<PW, 4, 1>(h, P, t, R, nt, st);
+        case 2: return launch_t<PW, 1, 2>(h, P, t, R, nt, st);
+        case 4: return launch_t<PW, 1, 3>(h, P, t, R, nt, st);
+        default: return launch_t<PW, 2, 2>(h, P, t, R, nt, st);
     }
 }
 
@@ -503,7 +502,8 @@ int far_dw_variant(const fl_ctx* h, const Plan& P, int pw) {
 }
 
 int launch_far_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro, int pw,
-                  cudaStream_t st) {
+                  cudaStream_t st, int64_t ntiles) {
+    const int64_t nt = ntiles >= 0 ? ntiles : (int64_t)P.tiles.size() / 2;
     FarRuleDW R;
     for (int a = 0; a < DW_Q; ++a) {
         const double w = rb[ro.far_w + a];
@@ -517,9 +517,9 @@ int launch_far_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<doub
     }
     const int variant = far_dw_variant(h, P, pw);
     switch (pw) {
-        case 5: return launch_pw<5>(h, P, t, R, variant, st);
-        case 6: return launch_pw<6>(h, P, t, R, variant, st);
-        default: return launch_pw<7>(h, P, t, R, variant, st);
+        case 5: return launch_pw<5>(h, P, t, R, variant, nt, st);
+        case 6: return launch_pw<6>(h, P, t, R, variant, nt, st);
+        default: return launch_pw<7>(h, P, t, R, variant, nt, st);
     }
 }
 

@@ -57,6 +57,10 @@ struct fl_hm {
     int *nz_ptr = nullptr, *nz_row = nullptr, *nz_col = nullptr;
     double* nz_val = nullptr;
     bool near_ready = false;
+    // the near field from local computations (fl_hmatrix_assemble_near), planned on first use
+    bool hn_planned = false;
+    fl::HNearDev hn;
+    int64_t hn_entries = 0, hn_bytes = 0;  // tile partial entries; bytes of the plan and workspace
     double *xh = nullptr, *yh = nullptr;
     double* Pb = nullptr;  // per admissible pair: K_b xh[tau]
     // Jacobi-PCG with the product (fl_hmatrix_solve), allocated on first use
@@ -496,6 +500,37 @@ int fl_cluster_plan(fl_handle h, double s, double eta, int leaf, int64_t* sizes,
     return FL_OK;
 }
 
+int fl_near_region_plan(fl_handle h, double s, double eta, int leaf, int64_t* sizes, int32_t* cell_perm,
+                        int32_t* ef_ptr, int32_t* ef_fac, int32_t* ef_cls, int32_t* fac_vert, double* fac_normal) {
+    if (!h || !sizes) return FL_EINVAL;
+    h->err.clear();
+    if (h->sym_K) return sym_unsupported(h, "fl_near_region_plan");
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    try {
+        ClusterPlan C;
+        if (build_cluster_plan(P, eta, leaf, C) != FL_OK) return set_err(h, FL_EINVAL, "leaf < 1 or eta < 0");
+        HNearPlan Q;
+        std::string err;
+        const int rc = plan_hnear(P, C, Q, err);
+        if (rc != FL_OK) return set_err(h, rc, err);
+        sizes[0] = (int64_t)Q.tiles.size() / 2;
+        sizes[1] = (int64_t)Q.ef_fac.size();
+        sizes[2] = (int64_t)Q.FLEN.size();
+        sizes[3] = P.nc;
+        if (cell_perm) std::copy(P.perm.begin(), P.perm.end(), cell_perm);
+        if (ef_ptr) std::copy(Q.ef_ptr.begin(), Q.ef_ptr.end(), ef_ptr);
+        if (ef_fac) std::copy(Q.ef_fac.begin(), Q.ef_fac.end(), ef_fac);
+        if (ef_cls) std::copy(Q.ef_cls.begin(), Q.ef_cls.end(), ef_cls);
+        if (fac_vert) std::copy(Q.F.begin(), Q.F.end(), fac_vert);
+        if (fac_normal) std::copy(Q.FN.begin(), Q.FN.end(), fac_normal);
+    } catch (const std::bad_alloc&) {
+        return set_err(h, FL_ENOMEM, "out of host memory");
+    }
+    return FL_OK;
+}
+
 void fl_hmatrix_destroy(fl_hmatrix H) {
     if (!H) return;
     if (!H->bufs.empty() || !H->graphs.empty()) {
@@ -695,6 +730,70 @@ int fl_hmatrix_set_near(fl_hmatrix H, const double* A_dev, int64_t lda, void* st
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return hm_fail(H, FL_ECUDA, std::string("near gather: ") + cudaGetErrorString(e));
     H->near_ready = true;
+    return FL_OK;
+}
+
+int fl_hmatrix_assemble_near(fl_hmatrix H, void* stream) {
+    if (!H) return FL_EINVAL;
+    H->err.clear();
+    if (cudaSetDevice(H->device) != cudaSuccess) return hm_fail(H, FL_ECUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    fl_ctx* h = H->mesh;
+    int rc = FL_OK;
+    if (!H->hn_planned) {
+        const int64_t b0 = H->bytes;
+        try {
+            fl::HNearPlan Q;
+            std::string err;
+            rc = fl::plan_hnear(h->plan[H->pi], H->plan, Q, err);
+            if (rc != FL_OK) return hm_fail(H, rc, err);
+            fl::HNearDev& q = H->hn;
+            if ((rc = hm_upload(H, &q.tiles, Q.tiles, st)) || (rc = hm_upload(H, &q.toff, Q.toff, st)) ||
+                (rc = hm_upload(H, &q.trow_ptr, Q.trow_ptr, st)) || (rc = hm_upload(H, &q.F, Q.F, st)) ||
+                (rc = hm_upload(H, &q.FN, Q.FN, st)) || (rc = hm_upload(H, &q.FLEN, Q.FLEN, st)) ||
+                (rc = hm_upload(H, &q.ef_ptr, Q.ef_ptr, st)) || (rc = hm_upload(H, &q.ef_fac, Q.ef_fac, st)) ||
+                (rc = hm_upload(H, &q.ef_cls, Q.ef_cls, st)))
+                return rc;
+            if ((rc = hm_alloc(H, &q.P, (size_t)Q.toff.back()))) return rc;
+            q.ntiles = (int64_t)Q.tiles.size() / 2;
+            H->hn_entries = Q.toff.back();
+        } catch (const std::bad_alloc&) {
+            return hm_fail(H, FL_ENOMEM, "out of host memory");
+        }
+        H->hn_bytes = H->bytes - b0;
+        H->hn_planned = true;
+    }
+    rc = fl::assemble_hnear(h, H->pi, H->s, H->hn, H->nnz, H->nz_row, H->nz_col, H->nz_val, st);
+    if (rc != FL_OK) return hm_fail(H, rc, h->err);
+    H->near_ready = true;
+    return FL_OK;
+}
+
+int fl_hmatrix_get_near(fl_hmatrix H, int64_t* nnz, int32_t* rowptr_dev, int32_t* col_dev, double* val_dev,
+                        void* stream) {
+    if (!H || !nnz) return FL_EINVAL;
+    H->err.clear();
+    *nnz = H->nnz;
+    if (!rowptr_dev && !col_dev && !val_dev) return FL_OK;
+    if (val_dev && !H->near_ready) return hm_fail(H, FL_EINVAL, "near field not set");
+    if (cudaSetDevice(H->device) != cudaSuccess) return hm_fail(H, FL_ECUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (rowptr_dev)
+        e = cudaMemcpyAsync(rowptr_dev, H->nz_ptr, (H->plan.n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && col_dev && H->nnz > 0)
+        e = cudaMemcpyAsync(col_dev, H->nz_col, H->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && val_dev && H->nnz > 0)
+        e = cudaMemcpyAsync(val_dev, H->nz_val, H->nnz * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return hm_fail(H, FL_ECUDA, std::string("near-field copy: ") + cudaGetErrorString(e));
+    return FL_OK;
+}
+
+int fl_hmatrix_near_info(fl_hmatrix H, int64_t* info) {
+    if (!H || !info) return FL_EINVAL;
+    info[0] = H->hn.ntiles;
+    info[1] = H->hn_entries;
+    info[2] = H->hn_bytes;
     return FL_OK;
 }
 

@@ -25,8 +25,8 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
 EXPORTS = ["fl_default_options", "fl_create", "fl_create_sector", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
            "fl_assemble", "fl_tune_assemble", "fl_set_far_variant", "fl_assemble_nearfield_csr", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
            "fl_heat_matrix", "fl_mass_apply", "fl_strong_form", "fl_br_indicators", "fl_mark_max", "fl_refine",
-           "fl_cluster_plan", "fl_hmatrix_create", "fl_hmatrix_set_near",
-           "fl_hmatrix_matvec", "fl_hmatrix_solve", "fl_hmatrix_info", "fl_hmatrix_last_error", "fl_hmatrix_destroy", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
+           "fl_cluster_plan", "fl_near_region_plan", "fl_hmatrix_create", "fl_hmatrix_set_near",
+           "fl_hmatrix_matvec", "fl_hmatrix_solve", "fl_hmatrix_info", "fl_hmatrix_assemble_near", "fl_hmatrix_near_info", "fl_hmatrix_get_near", "fl_hmatrix_last_error", "fl_hmatrix_destroy", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
            "fl_matvec_f32_static",
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
            "fl_tune_batch", "fl_tune_matvec", "fl_tune_record", "fl_tune_lookup", "fl_tune_clear", "fl_tune_count", "fl_tune_save",
@@ -148,6 +148,8 @@ def lib():
     L.fl_refine.restype = ci
     L.fl_cluster_plan.argtypes = [vp, dbl, dbl, ci, ctypes.POINTER(i64), vp, vp, vp, vp]
     L.fl_cluster_plan.restype = ci
+    L.fl_near_region_plan.argtypes = [vp, dbl, dbl, ci, ctypes.POINTER(i64), vp, vp, vp, vp, vp, vp]
+    L.fl_near_region_plan.restype = ci
     L.fl_hmatrix_create.argtypes = [vp, dbl, ci, dbl, ci, ctypes.POINTER(vp), vp]
     L.fl_hmatrix_create.restype = ci
     L.fl_hmatrix_set_near.argtypes = [vp, vp, i64, vp]
@@ -158,6 +160,12 @@ def lib():
     L.fl_hmatrix_solve.restype = ci
     L.fl_hmatrix_info.argtypes = [vp, ctypes.POINTER(i64)]
     L.fl_hmatrix_info.restype = ci
+    L.fl_hmatrix_assemble_near.argtypes = [vp, vp]
+    L.fl_hmatrix_assemble_near.restype = ci
+    L.fl_hmatrix_near_info.argtypes = [vp, ctypes.POINTER(i64)]
+    L.fl_hmatrix_near_info.restype = ci
+    L.fl_hmatrix_get_near.argtypes = [vp, ctypes.POINTER(i64), vp, vp, vp, vp]
+    L.fl_hmatrix_get_near.restype = ci
     L.fl_hmatrix_last_error.argtypes = [vp]
     L.fl_hmatrix_last_error.restype = ctypes.c_char_p
     L.fl_hmatrix_destroy.argtypes = [vp]
@@ -466,12 +474,29 @@ def fl_cluster_plan(h, s, eta=1.0, leaf=32):
     return {"perm": perm, "node": node, "far": far, "near": near}
 
 
+def fl_near_region_plan(h, s, dim, eta=1.0, leaf=32):
+    """Host-only plan of the direct near-field assembly for a dim-dimensional mesh: dict with
+    tiles (count), cell_perm [cells], ef_ptr [cells + 1], ef_fac, ef_cls [entries], fac_vert
+    [table, dim], fac_normal [table, dim] (numpy arrays)."""
+    sizes = (ctypes.c_int64 * 4)()
+    _check(lib().fl_near_region_plan(h, s, eta, leaf, sizes, None, None, None, None, None, None), h)
+    nt, ne, nfac, nc = sizes[0], sizes[1], sizes[2], sizes[3]
+    out = {"tiles": nt, "cell_perm": np.zeros(nc, dtype=np.int32), "ef_ptr": np.zeros(nc + 1, dtype=np.int32),
+           "ef_fac": np.zeros(ne, dtype=np.int32), "ef_cls": np.zeros(ne, dtype=np.int32),
+           "fac_vert": np.zeros((nfac, dim), dtype=np.int32), "fac_normal": np.zeros((nfac, dim))}
+    _check(lib().fl_near_region_plan(h, s, eta, leaf, sizes, out["cell_perm"].ctypes.data, out["ef_ptr"].ctypes.data,
+                                     out["ef_fac"].ctypes.data, out["ef_cls"].ctypes.data,
+                                     out["fac_vert"].ctypes.data, out["fac_normal"].ctypes.data), h)
+    return out
+
+
 class HMatrix:
     """Cluster-method approximation of A^s on a mesh handle (Section 6); owns an fl_hmatrix."""
 
     def __init__(self, h, s, m=4, eta=1.0, leaf=32, stream=None):
         self.hm = ctypes.c_void_p()
         _check(lib().fl_hmatrix_create(h, s, m, eta, leaf, ctypes.byref(self.hm), _stream(stream)), h)
+        self.n = fl_num_dofs(h, s)
 
     def _check(self, r):
         if r != FL_OK:
@@ -479,6 +504,29 @@ class HMatrix:
 
     def set_near(self, A, stream=None):
         self._check(lib().fl_hmatrix_set_near(self.hm, _ptr(A), A.stride(0), _stream(stream)))
+
+    def assemble_near(self, stream=None):
+        """Near-field entries by local computations (no dense matrix)."""
+        self._check(lib().fl_hmatrix_assemble_near(self.hm, _stream(stream)))
+
+    def get_near(self, stream=None):
+        """The near field as (rowptr, col, val) CUDA tensors (int32, int32, float64)."""
+        import torch
+
+        nnz = ctypes.c_int64(0)
+        self._check(lib().fl_hmatrix_get_near(self.hm, ctypes.byref(nnz), None, None, None, None))
+        n = self.n
+        rowptr = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+        col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device="cuda")
+        val = torch.empty(max(nnz.value, 1), dtype=torch.float64, device="cuda")
+        self._check(lib().fl_hmatrix_get_near(self.hm, ctypes.byref(nnz), _ptr(rowptr), _ptr(col), _ptr(val),
+                                              _stream(stream)))
+        return rowptr, col[: nnz.value], val[: nnz.value]
+
+    def near_info(self):
+        v = (ctypes.c_int64 * 3)()
+        self._check(lib().fl_hmatrix_near_info(self.hm, v))
+        return dict(zip(["tiles", "tile_entries", "device_bytes"], list(v)))
 
     def matvec(self, x, y, stream=None):
         self._check(lib().fl_hmatrix_matvec(self.hm, _ptr(x), _ptr(y), _stream(stream)))
