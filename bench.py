@@ -218,6 +218,8 @@ SF_CASES = {"sf_lshape3": (3, 0.5), "sf_lshape5": (5, 0.5)}
 # dense-product and H-matrix-product profiling cases
 MV_CASES = {"mv_f32_20000": (20000, "f32"), "mv_f64_20000": (20000, "f64"), "mv_f32_35693": (35693, "f32")}
 HM_CASES = {"hm_lshape4": (4, 4)}
+# near field of the cluster method assembled directly: L-shape level (m = 4, leaves of 32, eta = 1)
+HN_CASES = {"hn_lshape5": 5, "hn_lshape3": 3}
 
 
 def run_mv_case(args):
@@ -273,6 +275,33 @@ def run_hm_case(args):
         ts.append(a.elapsed_time(b))
     print(f"case {args.case}: n {A.shape[0]} m {m} product ms " + " ".join(f"{v:.4f}" for v in ts))
     H.close()
+    return 0
+
+
+def run_hn_case(args):
+    """The cluster method's near field by local computations (fl_hmatrix_assemble_near) on an
+    L-shape level: the first call (plans), then `--steps` calls timed by CUDA events."""
+    import torch
+
+    from paper_1708_03912_gb300 import fraclap as F
+    from paper_1708_03912_gb300 import synth
+
+    V, T = synth.lshape(0.25, HN_CASES[args.case])
+    mesh = F.Mesh(V, T)
+    H = F.HMatrix(mesh.h, 0.5, m=4, eta=1.0, leaf=32)
+    H.assemble_near()
+    ts = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        H.assemble_near()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    print(f"case {args.case}: n {H.n} near field {H.info()['near_entries']} entries, {H.near_info()['tiles']} tiles, "
+          f"assembly ms " + " ".join(f"{v:.3f}" for v in ts))
+    H.close()
+    mesh.close()
     return 0
 
 
@@ -578,10 +607,72 @@ def hmatrix_section(F, timed, A, h5, b=None):
             out[f"m{m}"]["jacobi_pcg"] = {"ms": solve_ms, "iterations": ih.iterations,
                                           "max_error_vs_dense_solution": float((uh - u_dense).abs().max() /
                                                                                u_dense.abs().max())}
+        # the near field by local computations instead of from the dense matrix
+        Hn = F.HMatrix(h5, s, m=m, eta=1.0, leaf=32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Hn.assemble_near()
+        torch.cuda.synchronize()
+        first_ms = (time.perf_counter() - t0) * 1000
+        near_ms = timed(lambda: Hn.assemble_near(), reps=3, flush_between=False)
+        _, _, vd = H.get_near()
+        _, _, va = Hn.get_near()
+        yn = torch.empty(n, dtype=torch.float64, device=A.device)
+        Hn.matvec(x, yn)
+        rec = {"assembly_ms": near_ms, "first_call_ms_with_plan": first_ms,
+               "entries_bitwise_equal_to_dense": float((va == vd).double().mean()),
+               "product_rel_error_vs_dense": float(torch.linalg.norm(yn - ref[:, 0]) / torch.linalg.norm(ref[:, 0])),
+               **Hn.near_info(), "dense_tiles": F.fl_get_stats(h5, s)["n_tiles"]}
+        if b is not None:
+            un, i_n = Hn.solve(b, tol=1e-8)
+            rec["jacobi_pcg"] = {"ms": timed(lambda: Hn.solve(b, tol=1e-8), reps=2, flush_between=False),
+                                 "iterations": i_n.iterations,
+                                 "max_error_vs_dense_solution": float((un - u_dense).abs().max() / u_dense.abs().max())}
+        out[f"m{m}"]["near_assembled"] = rec
+        Hn.close()
         H.close()
     if b is not None:
         out["dense_jacobi_pcg_ms"] = timed(lambda: F.fl_solve(h5, A, b, torch.empty_like(b), _opts(F, 1e-8)), reps=2,
                                            flush_between=False)
+    return out
+
+
+def hmatrix_large_section(F, synth, timed, level=7):
+    """The cluster method where the dense path does not fit: L-shape at `level` (level 7: 287102
+    cells, n = 141504, s = 1/2), the whole chain through the public API -- mesh handle, H-matrix
+    (m = 4, eta = 1, leaves of 32), near field by local computations, Jacobi-PCG to 1e-8 (f = 1).
+    Host wall times for the planning calls, CUDA events for the device work."""
+    import torch
+
+    s = LSHAPE_S
+    V, T = synth.lshape(0.25, level)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mesh = F.Mesh(V, T)
+    H = F.HMatrix(mesh.h, s, m=4, eta=1.0, leaf=32)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    H.assemble_near()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    near_ms = timed(lambda: H.assemble_near(), reps=2, flush_between=False)
+    b = mesh.load_vector(s)
+    u, info = H.solve(b, tol=1e-8)
+    solve_ms = timed(lambda: H.solve(b, tol=1e-8), reps=2, flush_between=False)
+    st = F.fl_get_stats(mesh.h, s)
+    n = H.n
+    nblk = (len(T) + 31) // 32
+    out = {"workload": f"L-shape level {level}, {len(T)} cells, n = {n}, s = {s}, m = 4, eta = 1, leaf = 32, f = 1",
+           "create_s": t1 - t0, "first_near_s_with_plan": t2 - t1, "near_assembly_ms": near_ms,
+           "jacobi_pcg": {"ms": solve_ms, "iterations": info.iterations, "status": info.status,
+                          "rel_residual": info.rel_residual},
+           "h_info": H.info(), "near_info": H.near_info(), "handle_workspace_bytes": st["workspace_bytes"],
+           "dense_would_need": {"tiles": st["n_tiles"], "matrix_f64_bytes": 8 * n * n,
+                                "row_sum_bytes": nblk * len(T) * 16 * 8},
+           "note": "no dense matrix is formed; the dense float64 assembly of this mesh would hold the matrix plus "
+                   "per-point row sums of every cell against every element block (row_sum_bytes), beyond one GPU"}
+    H.close()
+    mesh.close()
     return out
 
 
@@ -773,7 +864,7 @@ def main():
     ap.add_argument("--no-side", action="store_true", help="headline step only (no side sections)")
     ap.add_argument("--no-tune", action="store_true", help="skip the far-kernel autotuner (default launch shape)")
     ap.add_argument("--tune-file", default=None, help="load/save the autotuner's table (JSON)")
-    ap.add_argument("--case", default=None, choices=sorted(CASES) + sorted(SF_CASES) + sorted(MV_CASES) + sorted(HM_CASES),
+    ap.add_argument("--case", default=None, choices=sorted(CASES) + sorted(SF_CASES) + sorted(MV_CASES) + sorted(HM_CASES) + sorted(HN_CASES),
                     help="profiling mode: run a small named workload and print stage times (no JSON line)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="assembly precision of --case")
     ap.add_argument("--no-solve", action="store_true", help="--case: assembly only")
@@ -786,6 +877,8 @@ def main():
         return run_mv_case(args)
     if args.case in HM_CASES:
         return run_hm_case(args)
+    if args.case in HN_CASES:
+        return run_hn_case(args)
     if args.case:
         return run_case(args)
 
@@ -931,6 +1024,7 @@ def main():
         torch.cuda.empty_cache()
         line["lshape"]["preconditioners"] = lshape_precond_section(F, synth, timed, A, b, m.h)
         line["lshape"]["hmatrix"] = hmatrix_section(F, timed, A, m.h, b)
+        line["hmatrix_large"] = hmatrix_large_section(F, synth, timed)
         line["lshape"]["adaptive"] = adaptive_section(F, synth, timed, peaks, sms, m, A, b, n_el)
         line["heat"] = heat_section(F, synth, timed)
         line["symmetry"] = symmetry_section(F, synth, timed)

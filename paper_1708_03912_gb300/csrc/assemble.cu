@@ -2111,6 +2111,26 @@ static int launch_element(fl_ctx* h, const ElemArgs& E, int pw, int part, cudaSt
     return FL_OK;
 }
 
+// The handle's second stream and its fork / join / far events, created on first use; false
+// when they cannot be had (the stages then run in sequence on the caller's stream).
+static bool side_stream(fl_ctx* h) {
+    if (!h->side && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        h->side = nullptr;
+    }
+    if (h->side && !h->ev_fork) {
+        if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_far, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+            if (h->ev_join) cudaEventDestroy(h->ev_join);
+            h->ev_fork = h->ev_join = h->ev_far = nullptr;
+        }
+    }
+    return h->side && h->ev_fork && h->ev_join && h->ev_far;
+}
+
 // Per-s rule tables on the device, built and uploaded once per (handle, plan, s): repeated
 // calls at the same s do no host work and no host-synchronising copy.  f32: also the float32
 // copy (mixed-mode touching pairs and identical pair).
@@ -2214,26 +2234,10 @@ static int assemble_impl(fl_ctx* h, double s, int precision, double* A, int64_t 
     // is added.  With profiling on every stage runs on the caller's stream, one after another,
     // so that each event pair brackets one stage alone.
     cudaStream_t sst = st;
-    if (h->profiling != 1) {
-        if (!h->side && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();  // no second stream: the stages run in sequence on the caller's
-            h->side = nullptr;
-        }
-        if (h->side && !h->ev_fork) {
-            if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&h->ev_far, cudaEventDisableTiming) != cudaSuccess) {
-                cudaGetLastError();
-                if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-                if (h->ev_join) cudaEventDestroy(h->ev_join);
-                h->ev_fork = h->ev_join = h->ev_far = nullptr;
-            }
-        }
-        if (h->side && h->ev_fork && h->ev_join && h->ev_far) {
-            FL_CUDA_TRY(h, cudaEventRecord(h->ev_fork, st));
-            FL_CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-            sst = h->side;
-        }
+    if (h->profiling != 1 && side_stream(h)) {
+        FL_CUDA_TRY(h, cudaEventRecord(h->ev_fork, st));
+        FL_CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        sst = h->side;
     }
     // far field (launched first: it takes the SMs, the second stream's blocks fill in behind it)
     stage_mark(h, st, FL_STAGE_FAR, 0);
@@ -2412,19 +2416,34 @@ int assemble_hnear(fl_ctx* h, int pi, double s, const HNearDev& q, int64_t nnz, 
     FL_CUDA_TRY(h, cudaGetLastError());
     const bool dw = D == 2 && far_dw_applies(h, P, pw);
     if (dw) FL_TRY(prep_far_dw(h, P, t, ro, st));
-    if (q.ntiles > 0) {
-        if (dw) FL_TRY(launch_far_dw(h, P, t, rb, ro, pw, st, q.ntiles));
-        else FL_TRY(launch_far<double>(h, P, t, rb, ro, expo, pw, st, q.ntiles));
+    // the local pairs and the cell blocks on the second stream, beside the tiles (they share no
+    // buffer with them); the streams join before the entries are composed
+    cudaStream_t sst = st;
+    if (h->profiling != 1 && side_stream(h)) {
+        FL_CUDA_TRY(h, cudaEventRecord(h->ev_fork, st));
+        FL_CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        sst = h->side;
     }
-    FL_TRY(launch_near_pairs(h, P, t, rb, ro, expo, pw, false, C, st));
-    FL_TRY(launch_touch_pairs(h, P, t, ro, s, C, pw, false, st));
+    int rc = FL_OK;
+    if (q.ntiles > 0) {
+        if (dw) rc = launch_far_dw(h, P, t, rb, ro, pw, st, q.ntiles);
+        else rc = launch_far<double>(h, P, t, rb, ro, expo, pw, st, q.ntiles);
+    }
     ElemArgs E = elem_args(h, P, t, ro, s, C, false);
     E.cluster = 1;
     E.nblk = 0;
     E.Pd = nullptr;
     E.Bf = nullptr;
-    FL_TRY(launch_element(h, E, pw, 1, st));
-    FL_TRY(launch_element(h, E, pw, 2, st));
+    int side_rc = launch_near_pairs(h, P, t, rb, ro, expo, pw, false, C, sst);
+    if (side_rc == FL_OK) side_rc = launch_touch_pairs(h, P, t, ro, s, C, pw, false, sst);
+    if (side_rc == FL_OK) side_rc = launch_element(h, E, pw, 1, sst);
+    if (side_rc == FL_OK) side_rc = launch_element(h, E, pw, 2, sst);
+    if (sst != st) {  // joined even after an error, so that the caller's stream never runs ahead
+        FL_CUDA_TRY(h, cudaEventRecord(h->ev_join, sst));
+        FL_CUDA_TRY(h, cudaStreamWaitEvent(st, h->ev_join, 0));
+    }
+    FL_TRY(rc);
+    FL_TRY(side_rc);
     if (nnz > 0) {
         hnear_compose_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(
             nnz, nz_row, nz_col, t.csr_ptr, t.csr_col, t.g_ptr, t.g_slot, t.contrib, t.occ_ptr, t.occ_blk, t.occ_loc,

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -142,6 +143,15 @@ __device__ void cheb_point_d(const double* c, double L, int m, int d, int alpha,
     }
 }
 
+// the same 1D Lagrange value from the cluster's nodes computed once (x[l] = cheb_node(.., l)):
+// the same operations in the same order as lagrange1
+__device__ double lagrange1_nodes(const double* x, int m, int k, double t) {
+    double v = 1.0;
+    for (int l = 0; l < m; ++l)
+        if (l != k) v *= (t - x[l]) / (x[k] - x[l]);
+    return v;
+}
+
 // leaf coefficients int phi_i L_alpha^leaf, one thread per (tree position, alpha); the rule
 // (lam [q][d], w [q], on the reference cell) integrates the degree 2m-1 integrand exactly
 __global__ void leaf_coef_kernel(int64_t n, int d, int m, int md, const int* perm, const int* leaf_of,
@@ -155,6 +165,11 @@ __global__ void leaf_coef_kernel(int64_t n, int d, int m, int md, const int* per
     const int c = leaf_of[p];
     const int v = vod[perm[p]];
     const int nv = d + 1;
+    // the leaf's Chebyshev nodes per axis (m <= 12), computed once per thread
+    double xn[2][12];
+    for (int k = 0; k < d; ++k)
+        for (int l = 0; l < m; ++l) xn[k][l] = cheb_node(center[(int64_t)c * d + k], side[c], m, l);
+    const int a0 = d == 1 ? alpha : alpha / m, a1 = d == 1 ? 0 : alpha % m;
     double acc = 0.0;
     for (int64_t e = v2c_ptr[v]; e < v2c_ptr[v + 1]; ++e) {
         const int K = v2c[e];
@@ -175,7 +190,9 @@ __global__ void leaf_coef_kernel(int64_t n, int d, int m, int md, const int* per
                            l2 * (V[2 * cell[2] + k] - V[2 * cell[0] + k]);
                 phi = a == 0 ? 1.0 - l1 - l2 : (a == 1 ? l1 : l2);
             }
-            acc += w[r] * jac[K] * phi * lagrange_d(center + (int64_t)c * d, side[c], m, d, alpha, x);
+            const double Lv = d == 1 ? lagrange1_nodes(xn[0], m, a0, x[0])
+                                     : lagrange1_nodes(xn[0], m, a0, x[0]) * lagrange1_nodes(xn[1], m, a1, x[1]);
+            acc += w[r] * jac[K] * phi * Lv;
         }
     }
     coef[p * md + alpha] = acc;
@@ -650,21 +667,29 @@ int fl_hmatrix_create(fl_handle h, double s, int m, double eta, int leaf, fl_hma
         }
         for (int c = 0; c < nn; ++c)
             if (far_ptr[c + 1] > far_ptr[c]) sig_nodes.push_back(c);
-        // near field CSR over the original DOF numbering, columns ascending
-        std::vector<std::vector<int>> cols(n);
+        // near field CSR over the original DOF numbering, columns ascending.  Every row of a leaf
+        // has the same columns (the DOFs of the leaf's near partners), so each leaf's column list
+        // is sorted once and copied into its rows.
+        std::vector<std::vector<int>> lcols(nn);
         for (size_t b = 0; b + 1 < C.near.size(); b += 2) {
             const int a = C.near[b], c = C.near[b + 1];
-            for (int p = C.lo[a]; p < C.hi[a]; ++p)
-                for (int q = C.lo[c]; q < C.hi[c]; ++q) cols[C.perm[p]].push_back(C.perm[q]);
+            for (int q = C.lo[c]; q < C.hi[c]; ++q) lcols[a].push_back(C.perm[q]);
         }
-        std::vector<int> nz_ptr(n + 1, 0), nz_row, nz_col;
+        for (int c : leaves) std::sort(lcols[c].begin(), lcols[c].end());
+        std::vector<int> rowleaf(n, -1);
+        for (int c : leaves)
+            for (int p = C.lo[c]; p < C.hi[c]; ++p) rowleaf[C.perm[p]] = c;
+        std::vector<int> nz_ptr(n + 1, 0);
         for (int64_t i = 0; i < n; ++i) {
-            std::sort(cols[i].begin(), cols[i].end());
-            nz_ptr[i + 1] = nz_ptr[i] + (int)cols[i].size();
-            for (int j : cols[i]) {
-                nz_row.push_back((int)i);
-                nz_col.push_back(j);
-            }
+            const int64_t next = (int64_t)nz_ptr[i] + (int64_t)lcols[rowleaf[i]].size();
+            if (next > INT32_MAX) return fail(FL_ENOMEM, "near field larger than 2^31 entries");
+            nz_ptr[i + 1] = (int)next;
+        }
+        std::vector<int> nz_row(nz_ptr[n]), nz_col(nz_ptr[n]);
+        for (int64_t i = 0; i < n; ++i) {
+            const std::vector<int>& L = lcols[rowleaf[i]];
+            std::copy(L.begin(), L.end(), nz_col.begin() + nz_ptr[i]);
+            std::fill(nz_row.begin() + nz_ptr[i], nz_row.begin() + nz_ptr[i + 1], (int)i);
         }
         H->nnz = nz_ptr[n];
         H->nleaves = (int)leaves.size();
