@@ -1617,6 +1617,7 @@ int ensure_device(fl_ctx* h, int pi, cudaStream_t st) {
     FL_TRY(upload_all(h, U, st));
     const int qf = qf_of(h), qn = qn_of(h);
     FL_TRY(alloc(h, &t.pts, (size_t)nc * qf * D * sizeof(double)));
+    if (D == 2 && qn == 36) FL_TRY(alloc(h, &t.pts_near_dw, (size_t)nc * 36 * sizeof(float4)));
     if (D == 2 && qf == 16) {
         FL_TRY(alloc(h, &t.pts_dw, (size_t)nc * 16 * sizeof(float4)));
         const int nch = bnd_dw_chunks(nc);
@@ -1999,7 +2000,9 @@ static int launch_near_pairs(fl_ctx* h, const Plan& P, DevTables& t, const std::
     const int pw32 = (pw == 4 || pw == 6) ? pw : 0;
     const int nnear = (int)P.np_a.size();
     const bool near_fast = (D == 2 && ro.qn == 36) || (D == 1 && ro.qn == 6);
-    if (nnear > 0 && near_fast) {
+    if (nnear > 0 && !f32 && near_dw_applies(h, P, pw)) {
+        FL_TRY(launch_near_dw(h, P, t, rb, ro, pw, C, st));
+    } else if (nnear > 0 && near_fast) {
         if (D == 2) {
             if (f32) FL_TRY(launch_near_fast<2, float, 36>(h, P, t, rb, ro, expo, pw32, C, st));
             else FL_TRY(launch_near_fast<2, double, 36>(h, P, t, rb, ro, expo, pw, C, st));

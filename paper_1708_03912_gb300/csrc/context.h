@@ -93,6 +93,7 @@ struct DevTables {
     void* Pd = nullptr;     // nblk * nc * Qf partial row sums
     void* pts = nullptr;    // nc * Qf * dim offsets from centroids
     void* pts_dw = nullptr; // nc * 16 double-word offsets (2D, float64 mode, k_far = 4)
+    void* pts_near_dw = nullptr;  // nc * 36 double-word offsets of the near rule (2D, k_near = 6)
     double* Dn = nullptr;   // nnear * 2 * Qn
     double* Bf = nullptr;   // nc * Qf boundary sums (far facets)
     double* Bfp = nullptr;  // facet-chunk partials of Bf (double-word boundary kernel)
@@ -211,6 +212,11 @@ int bnd_dw_chunks(int64_t nc);
 int launch_bnd_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro, int pw,
                   cudaStream_t st);
 void far_dw_record(const Plan& P, int pw, int variant, double ms);
+// float64-mode near pairs (vertex-graph distance 1) in double-word arithmetic (far_dw.cu):
+// 2D, k_near = 6, s in {1/4, 1/2, 3/4}, unless the float64 pipe is requested
+bool near_dw_applies(const fl_ctx* h, const Plan& P, int pw);
+int launch_near_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro, int pw,
+                   double C, cudaStream_t st);
 // the cluster method's near field from local computations (assemble.cu): nnz entries (row, col
 // DOF ids) into nz_val; uses the handle's contribution slots and row-sum buffers
 struct HNearDev;

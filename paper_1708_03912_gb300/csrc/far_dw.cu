@@ -401,6 +401,104 @@ __global__ void __launch_bounds__(32 * BW_WARPS)
         }
 }
 
+// Near separated pairs (vertex-graph distance 1) of the float64 mode in double-word arithmetic:
+// the order-6 collapsed Gauss rule (36 points) on both cells, one thread per unordered pair,
+// the same outputs as the float64 near-pair kernel (off-diagonal block times -C into the
+// contribution slots, the per-point row sums of both cells into Dn).  Point offsets from the
+// cell centroids come from a per-cell double-word table (prep_near_dw); every sum is a
+// double-word accumulator, renormalised after each row point.
+constexpr int NQ = 36;  // collapsed Gauss rule of order 6
+
+struct NearRuleDW {
+    dw w[NQ];
+    dw wphi[NQ * NV];
+};
+
+__global__ void prep_near_dw(const double* cvx, const double* cen, const double* lam, int64_t nc, float4* pts) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nc * NQ) return;
+    const int64_t k = t / NQ;
+    const int a = (int)(t - k * NQ);
+    const double* v = cvx + k * 6;
+    dw o[2];
+    for (int d = 0; d < 2; ++d) {
+        const double x = v[d] + lam[2 * a] * (v[2 + d] - v[d]) + lam[2 * a + 1] * (v[4 + d] - v[d]);
+        o[d] = dw_from(x - cen[k * 2 + d]);
+    }
+    pts[t] = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
+}
+
+template <int PW>
+__global__ void __launch_bounds__(128) near_pair_dw_kernel(int nnear, const int* __restrict__ np_a,
+                                                           const int* __restrict__ np_b, const double* __restrict__ cen,
+                                                           const double* __restrict__ jac,
+                                                           const float4* __restrict__ pts,
+                                                           const __grid_constant__ NearRuleDW R, double C,
+                                                           double* __restrict__ contrib, int64_t slot0,
+                                                           double* __restrict__ Dn) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnear) return;
+    const int ka = np_a[p], kb = np_b[p];
+    const dw Dx = dw_from(cen[2 * (int64_t)ka] - cen[2 * (int64_t)kb]);
+    const dw Dy = dw_from(cen[2 * (int64_t)ka + 1] - cen[2 * (int64_t)kb + 1]);
+    const float4* pa = pts + (int64_t)ka * NQ;
+    const float4* pb = pts + (int64_t)kb * NQ;
+    const double ja = jac[ka], jb = jac[kb];
+    double* Da = Dn + ((int64_t)p * 2 + 0) * NQ;
+    double* Db = Dn + ((int64_t)p * 2 + 1) * NQ;
+    dw S[NQ];
+#pragma unroll
+    for (int b = 0; b < NQ; ++b) S[b] = {0.f, 0.f};
+    dw off[NV][NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) off[i][j] = {0.f, 0.f};
+#pragma unroll 1
+    for (int a = 0; a < NQ; ++a) {
+        const float4 qa = __ldg(pa + a);
+        const dw X = dw_add(Dx, dw{qa.x, qa.y});
+        const dw Y = dw_add(Dy, dw{qa.z, qa.w});
+        const dw wa = R.w[a];
+        dw t[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) t[v] = {0.f, 0.f};
+#pragma unroll
+        for (int b = 0; b < NQ; ++b) {
+            const float4 qb = __ldg(pb + b);
+            const dw dx = dw_sub(X, dw{qb.x, qb.y});
+            const dw dy = dw_sub(Y, dw{qb.z, qb.w});
+            // |x - y|^2 = dx^2 + dy^2: exact squares of the high parts, both non-negative
+            const dw px = two_prod(dx.h, dx.h), py = two_prod(dy.h, dy.h);
+            dw r2 = fast_two_sum(fmaxf(px.h, py.h), fminf(px.h, py.h));
+            const float cr = __fmaf_rn(dx.h, dx.l, __fmul_rn(dy.h, dy.l));
+            r2.l = __fadd_rn(r2.l, __fmaf_rn(2.f, cr, __fadd_rn(px.l, py.l)));
+            const dw kv = dw_kpow<PW>(r2);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) dw_mac_pos(t[v], R.wphi[b * NV + v], kv);
+            dw_mac_pos(S[b], wa, kv);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) t[v] = dw_renorm(t[v]);
+#pragma unroll
+        for (int b = 0; b < NQ; ++b) S[b] = dw_renorm(S[b]);
+        Da[a] = jb * dw_to(dw_add(dw_add(t[0], t[1]), t[2]));
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const dw c = R.wphi[a * NV + i];
+#pragma unroll
+            for (int j = 0; j < NV; ++j) dw_mac_pos(off[i][j], c, t[j]);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < NQ; ++b) Db[b] = ja * dw_to(S[b]);
+    double* out = contrib + slot0 + (int64_t)p * NV * NV;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) out[i * NV + j] = -C * ja * jb * dw_to(dw_renorm(off[i][j]));
+}
+
 // partial boundary sums of the facet chunks -> Bf, chunks added in order
 __global__ void bnd_chunks_sum(int64_t m, int nch, const double* __restrict__ part, double* __restrict__ Bf) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -555,6 +653,39 @@ int launch_bnd_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<doub
     }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FL_OK : set_err(h, FL_ECUDA, std::string("bnd_far_dw: ") + cudaGetErrorString(e));
+}
+
+bool near_dw_applies(const fl_ctx* h, const Plan& P, int pw) {
+    return P.dim == 2 && h->opt.k_near == 6 && (pw == 5 || pw == 6 || pw == 7) && !h->far_f64_pipe;
+}
+
+int launch_near_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro, int pw,
+                   double C, cudaStream_t st) {
+    const int nnear = (int)P.np_a.size();
+    if (nnear == 0) return FL_OK;
+    if (ro.qn != NQ || !t.pts_near_dw) return set_err(h, FL_EINVAL, "near_pair_dw: order-6 rule and its point table needed");
+    NearRuleDW R;
+    for (int a = 0; a < NQ; ++a) {
+        const double w = rb[ro.near_w + a];
+        R.w[a].h = (float)w;
+        R.w[a].l = (float)(w - (double)R.w[a].h);
+        for (int v = 0; v < NV; ++v) {
+            const double c = w * rb[ro.near_phi + a * NV + v];
+            R.wphi[a * NV + v].h = (float)c;
+            R.wphi[a * NV + v].l = (float)(c - (double)R.wphi[a * NV + v].h);
+        }
+    }
+    const int64_t np = P.nc * NQ;
+    prep_near_dw<<<(unsigned)((np + 127) / 128), 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.near_lam, P.nc,
+                                                               (float4*)t.pts_near_dw);
+    const unsigned g = (unsigned)((nnear + 127) / 128);
+    const float4* pts = (const float4*)t.pts_near_dw;
+    if (pw == 5) near_pair_dw_kernel<5><<<g, 128, 0, st>>>(nnear, t.np_a, t.np_b, t.cen, t.jac, pts, R, C, t.contrib, P.np_slot0, t.Dn);
+    else if (pw == 6) near_pair_dw_kernel<6><<<g, 128, 0, st>>>(nnear, t.np_a, t.np_b, t.cen, t.jac, pts, R, C, t.contrib, P.np_slot0, t.Dn);
+    else near_pair_dw_kernel<7><<<g, 128, 0, st>>>(nnear, t.np_a, t.np_b, t.cen, t.jac, pts, R, C, t.contrib, P.np_slot0, t.Dn);
+    count_launch(2);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FL_OK : set_err(h, FL_ECUDA, std::string("near_pair_dw: ") + cudaGetErrorString(e));
 }
 
 void far_dw_record(const Plan& P, int pw, int variant, double ms) {
