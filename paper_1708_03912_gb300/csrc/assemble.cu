@@ -2395,6 +2395,7 @@ int assemble_hnear(fl_ctx* h, int pi, double s, const HNearDev& q, int64_t nnz, 
     DevTables t = h->dev[pi];  // the mesh tables, with this assembly's tiles, facets and workspace
     t.tiles = q.tiles;
     t.toff = q.toff;
+    t.tile_rowmask = q.rowmask;
     t.P = q.P;
     t.Pd = nullptr;
     t.ef_ptr = q.ef_ptr;

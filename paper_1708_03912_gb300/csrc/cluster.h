@@ -32,6 +32,8 @@ struct HNearPlan {
     std::vector<int> tiles;        // 2 per tile (I <= J), ordered by (I, J)
     std::vector<int64_t> toff;     // tiles + 1: offsets of the tiles' partial blocks
     std::vector<int> trow_ptr;     // nblk + 1: the tiles of block row I are trow_ptr[I] .. trow_ptr[I + 1] - 1
+    std::vector<uint32_t> rowmask; // per tile: bit kk set when row cell 32 I + kk pairs with a cell of block J
+                                   // in some near-field entry (the far kernel skips the other rows)
     std::vector<int> F;            // facet table, dim vertex ids per facet: the boundary facets of
     std::vector<double> FN, FLEN;  // Omega (ids < nf) then (nf + nvpc M + e): facet e of internal
                                    // cell M, normal pointing into M
@@ -48,6 +50,7 @@ struct HNearDev {
     int* tiles = nullptr;
     int64_t* toff = nullptr;
     int* trow_ptr = nullptr;
+    uint32_t* rowmask = nullptr;
     int* F = nullptr;
     double *FN = nullptr, *FLEN = nullptr;
     int *ef_ptr = nullptr, *ef_fac = nullptr, *ef_cls = nullptr;

@@ -74,6 +74,7 @@ struct DevTables {
     int *L_ptr = nullptr, *inc_ptr = nullptr, *inc_ent = nullptr;
     int* tiles = nullptr;
     int64_t* toff = nullptr;
+    const uint32_t* tile_rowmask = nullptr;  // per tile, the row cells to compute (null: all; the double-word far kernel)
     int *occ_ptr = nullptr, *occ_blk = nullptr, *occ_loc = nullptr;
     int *ex_ptr = nullptr, *ex_idx = nullptr;
     int *np_a = nullptr, *np_b = nullptr, *enp_ptr = nullptr, *enp_ent = nullptr;

@@ -50,6 +50,7 @@ struct DwTileArgs {
     const int* ex_idx;
     const int* tiles;
     const int64_t* toff;
+    const uint32_t* rowmask;  // per tile: the row cells to compute (null: all)
     const int* L_ptr;
     const int* inc_ptr;
     const int* inc_ent;
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
     const int64_t nc = A.nc;
     const int64_t K0 = (int64_t)I * 32, Kt0 = (int64_t)J * 32;
     const int nI = (int)min((int64_t)32, nc - K0);
+    const uint32_t rmask = A.rowmask ? A.rowmask[tix] : 0xffffffffu;
 
     float4* sQ = reinterpret_cast<float4*>(smem_raw);                  // [Q][32] column points
     dw* sS = reinterpret_cast<dw*>(sQ + Q * 32);                        // [DW_WARPS][Q][32] column sums
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(32 * DW_WARPS, MINB)
 
     for (int kk = 0; kk < nI; ++kk) {
         const int64_t K = K0 + kk;
-        bool act = valid && (I != J || kk < lane);
+        bool act = valid && (I != J || kk < lane) && ((rmask >> kk) & 1u);
         if (act) {
             while (ep < ee && A.ex_idx[ep] < K) ++ep;
             if (ep < ee && A.ex_idx[ep] == K) act = false;
@@ -525,6 +527,7 @@ int launch_t(fl_ctx* h, const Plan& P, DevTables& t, const FarRuleDW& R, int64_t
     A.ex_idx = t.ex_idx;
     A.tiles = t.tiles;
     A.toff = t.toff;
+    A.rowmask = t.tile_rowmask;
     A.L_ptr = t.L_ptr;
     A.inc_ptr = t.inc_ptr;
     A.inc_ent = t.inc_ent;

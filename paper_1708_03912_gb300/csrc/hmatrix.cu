@@ -774,7 +774,8 @@ int fl_hmatrix_assemble_near(fl_hmatrix H, void* stream) {
             if (rc != FL_OK) return hm_fail(H, rc, err);
             fl::HNearDev& q = H->hn;
             if ((rc = hm_upload(H, &q.tiles, Q.tiles, st)) || (rc = hm_upload(H, &q.toff, Q.toff, st)) ||
-                (rc = hm_upload(H, &q.trow_ptr, Q.trow_ptr, st)) || (rc = hm_upload(H, &q.F, Q.F, st)) ||
+                (rc = hm_upload(H, &q.trow_ptr, Q.trow_ptr, st)) || (rc = hm_upload(H, &q.rowmask, Q.rowmask, st)) ||
+                (rc = hm_upload(H, &q.F, Q.F, st)) ||
                 (rc = hm_upload(H, &q.FN, Q.FN, st)) || (rc = hm_upload(H, &q.FLEN, Q.FLEN, st)) ||
                 (rc = hm_upload(H, &q.ef_ptr, Q.ef_ptr, st)) || (rc = hm_upload(H, &q.ef_fac, Q.ef_fac, st)) ||
                 (rc = hm_upload(H, &q.ef_cls, Q.ef_cls, st)))

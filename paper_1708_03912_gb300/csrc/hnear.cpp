@@ -70,6 +70,66 @@ int plan_hnear(const Plan& P, const ClusterPlan& C, HNearPlan& Q, std::string& e
         Q.trow_ptr[I + 1] = (int)(Q.tiles.size() / 2);
         std::vector<int>().swap(r);
     }
+    // ---- per tile, the row cells of block I that pair with some cell of block J in a near-field
+    // entry (a DOF of one in a leaf, a DOF of the other in a leaf near-paired with it); the far
+    // kernel skips the other rows, whose contributions no near-field entry reads
+    {
+        std::vector<int> lidx(C.nodes, -1);
+        int nl = 0;
+        for (int a = 0; a < C.nodes; ++a)
+            if (C.son[2 * a] < 0) lidx[a] = nl++;
+        const int64_t words = (nl + 63) / 64;
+        std::vector<uint64_t> adj((size_t)nl * words, 0);
+        for (size_t b = 0; b + 1 < C.near.size(); b += 2) {
+            const int a = lidx[C.near[b]], c = lidx[C.near[b + 1]];
+            adj[(size_t)a * words + c / 64] |= 1ull << (c % 64);
+        }
+        std::vector<int> dof_leaf(P.n, -1);
+        for (int a = 0; a < C.nodes; ++a)
+            if (lidx[a] >= 0)
+                for (int p = C.lo[a]; p < C.hi[a]; ++p) dof_leaf[C.perm[p]] = lidx[a];
+        // leaves of each internal cell's DOFs (up to nvpc, -1 padded)
+        std::vector<int> cl((size_t)nc * m, -1);
+        for (int64_t k = 0; k < nc; ++k)
+            for (int a = 0; a < m; ++a) {
+                const int i = P.cdof[k * m + a];
+                cl[k * m + a] = i >= 0 ? dof_leaf[i] : -1;
+            }
+        const int64_t nt = (int64_t)Q.tiles.size() / 2;
+        Q.rowmask.assign(nt, 0u);
+        std::vector<int> U;
+        int lastJ = -1;
+        for (int64_t t = 0; t < nt; ++t) {
+            const int I = Q.tiles[2 * t], J = Q.tiles[2 * t + 1];
+            if (J != lastJ) {  // leaves of block J's cells
+                U.clear();
+                for (int64_t k = (int64_t)J * TILE; k < std::min(nc, (int64_t)(J + 1) * TILE); ++k)
+                    for (int a = 0; a < m; ++a)
+                        if (cl[k * m + a] >= 0) U.push_back(cl[k * m + a]);
+                std::sort(U.begin(), U.end());
+                U.erase(std::unique(U.begin(), U.end()), U.end());
+                lastJ = J;
+            }
+            uint32_t mask = 0;
+            for (int kk = 0; kk < TILE; ++kk) {
+                const int64_t k = (int64_t)I * TILE + kk;
+                if (k >= nc) break;
+                bool need = false;
+                for (int a = 0; a < m && !need; ++a) {
+                    const int la = cl[k * m + a];
+                    if (la < 0) continue;
+                    const uint64_t* row = &adj[(size_t)la * words];
+                    for (int lb : U)
+                        if ((row[lb / 64] >> (lb % 64)) & 1ull) {
+                            need = true;
+                            break;
+                        }
+                }
+                if (need) mask |= 1u << kk;
+            }
+            Q.rowmask[t] = mask;
+        }
+    }
     // ---- facet table: the boundary facets of Omega (ids 0 .. nf-1, as in the mesh plan), then
     // one oriented copy per (internal cell M, facet e of M) with the normal pointing into M
     const int64_t ntab = nf + (int64_t)m * nc;
