@@ -2035,6 +2035,7 @@ static int launch_touch_pairs(fl_ctx* h, const Plan& P, DevTables& t, const Rule
     const int D = P.dim;
     const int ntp = (int)P.tp_type.size();
     if (ntp == 0) return FL_OK;
+    if (!f32 && touch_dw_applies(h, P, pw)) return launch_touch_dw(h, P, t, ro, s, C, pw, st);
     const unsigned g = (unsigned)(((int64_t)ntp * 32 + 127) / 128);  // one warp per pair
 #define FL_TOUCH(TT, RULE, PWV) \
     touch_pair_kernel<TT, PWV><<<g, 128, 0, st>>>(ntp, D, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, RULE, ro, s, C, t.contrib)
@@ -2151,6 +2152,20 @@ static int ensure_rules(fl_ctx* h, DevTables& t, double s, bool f32, cudaStream_
             t.rule_len = rb.size();
         }
         FL_CUDA_TRY(h, cudaMemcpyAsync(t.rule, rb.data(), rb.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        // double-word copy (high float, float of the remainder)
+        if (t.rule_dw_len < rb.size()) {
+            void* p = nullptr;
+            FL_TRY(alloc(h, &p, rb.size() * sizeof(float2)));
+            t.rule_dw = p;
+            t.rule_dw_len = rb.size();
+        }
+        std::vector<float2> rdw(rb.size());
+        for (size_t i = 0; i < rb.size(); ++i) {
+            const float hi = (float)rb[i];
+            rdw[i] = make_float2(hi, (float)(rb[i] - (double)hi));
+        }
+        FL_CUDA_TRY(h, cudaMemcpyAsync(t.rule_dw, rdw.data(), rdw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+        FL_CUDA_TRY(h, cudaStreamSynchronize(st));  // the staging vector is freed on return
         t.rule_s = s;
     }
     if (f32 && !t.rule32_ready) {

@@ -106,6 +106,8 @@ struct DevTables {
     size_t rule_len = 0;
     float* rule32 = nullptr;  // their float32 copy (mixed-mode touching pairs)
     size_t rule32_len = 0;
+    void* rule_dw = nullptr;  // their double-word copy (float pairs; float64-mode touching pairs)
+    size_t rule_dw_len = 0;
     double rule_s = -1.0;        // the s the device tables hold (NaN while being rebuilt)
     bool rule32_ready = false;   // the float32 copy matches them
     std::vector<double> rule_host;
@@ -216,6 +218,10 @@ void far_dw_record(const Plan& P, int pw, int variant, double ms);
 // float64-mode near pairs (vertex-graph distance 1) in double-word arithmetic (far_dw.cu):
 // 2D, k_near = 6, s in {1/4, 1/2, 3/4}, unless the float64 pipe is requested
 bool near_dw_applies(const fl_ctx* h, const Plan& P, int pw);
+// float64-mode touching pairs (2D) in double-word arithmetic, s in {1/4, 1/2, 3/4}
+bool touch_dw_applies(const fl_ctx* h, const Plan& P, int pw);
+int launch_touch_dw(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, double s, double C, int pw,
+                    cudaStream_t st);
 int launch_near_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<double>& rb, const RuleOffsets& ro, int pw,
                    double C, cudaStream_t st);
 // the cluster method's near field from local computations (assemble.cu): nnz entries (row, col

@@ -501,6 +501,105 @@ __global__ void __launch_bounds__(128) near_pair_dw_kernel(int nnear, const int*
         for (int j = 0; j < NV; ++j) out[i * NV + j] = -C * ja * jb * dw_to(dw_renorm(off[i][j]));
 }
 
+// Touching pairs of the float64 mode (2D: common edge, common vertex) in double-word arithmetic:
+// the singular rules' tables (angular / Duffy points with the exact radial factor in their
+// weights) as double-word numbers, one warp per pair, lanes over the points in a strided order,
+// then a butterfly sum; the outputs of the float64 touching kernel.  The terms are signed
+// (products of shape-function differences), so the sums use the signed accumulation.
+__device__ __forceinline__ dw ldw(const float2* t, int i) {
+    const float2 v = t[i];
+    return {v.x, v.y};
+}
+
+template <int NL>
+__device__ __forceinline__ void touch_accumulate(dw (&acc)[NL * (NL + 1) / 2], dw f, const float2* r) {
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < NL; ++i) {
+        const dw fi = dw_mul(f, ldw(r, i));
+#pragma unroll
+        for (int j = i; j < NL; ++j) dw_mac(acc[q++], fi, ldw(r, j));
+    }
+}
+
+template <int PW>
+__global__ void __launch_bounds__(128) touch_pair_dw_kernel(int ntp, const int* __restrict__ tp_type,
+                                                            const int* __restrict__ tp_vert,
+                                                            const int* __restrict__ tp_cell,
+                                                            const int64_t* __restrict__ tp_slot,
+                                                            const double* __restrict__ V,
+                                                            const double* __restrict__ jac_orig,
+                                                            const float2* __restrict__ rdw, RuleOffsets ro, double s,
+                                                            double C, double* __restrict__ contrib) {
+    const int lane = threadIdx.x & 31;
+    const int p = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (p >= ntp) return;
+    const int type = tp_type[p];
+    const int* tv = tp_vert + 5 * p;
+    double* out = contrib + tp_slot[p];
+    const double jK = jac_orig[tp_cell[2 * p]], jM = jac_orig[tp_cell[2 * p + 1]];
+    if (type == 0) {  // common edge [P,Q], thirds R (K) and Rt (M)
+        const double *P_ = V + 2 * tv[0], *Q_ = V + 2 * tv[1], *R_ = V + 2 * tv[2], *Rt = V + 2 * tv[3];
+        const dw a0 = dw_from(Q_[0] - P_[0]), a1 = dw_from(Q_[1] - P_[1]);
+        const dw b0 = dw_from(R_[0] - Q_[0]), b1 = dw_from(R_[1] - Q_[1]);
+        const dw c0 = dw_from(-(Rt[0] - Q_[0])), c1 = dw_from(-(Rt[1] - Q_[1]));
+        const float2* tb = rdw + ro.t_edge;
+        dw acc[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) acc[q] = {0.f, 0.f};
+        for (int m = lane; m < ro.n_edge; m += 32) {
+            const float2* r = tb + 8 * m;  // dphi[4], w1, w2, w3, weight
+            const dw w1 = ldw(r, 4), w2 = ldw(r, 5), w3 = ldw(r, 6);
+            const dw x = dw_add(dw_add(dw_mul(a0, w1), dw_mul(b0, w2)), dw_mul(c0, w3));
+            const dw y = dw_add(dw_add(dw_mul(a1, w1), dw_mul(b1, w2)), dw_mul(c1, w3));
+            const dw kv = dw_kpow<PW>(dw_add(dw_sqr(x), dw_sqr(y)));
+            touch_accumulate<4>(acc, dw_mul(ldw(r, 7), kv), r);
+#pragma unroll
+            for (int q = 0; q < 10; ++q) acc[q] = dw_renorm(acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 10; ++q)
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) acc[q] = dw_add(acc[q], dw_shfl_xor(acc[q], o));
+        if (lane == 0) {
+            const double sc = C * jK * jM / ((3.0 - 2.0 * s) * (4.0 - 2.0 * s));
+            int q = 0;
+            for (int i = 0; i < 4; ++i)
+                for (int j = i; j < 4; ++j, ++q) out[i * 4 + j] = out[j * 4 + i] = sc * dw_to(acc[q]);
+        }
+    } else {  // common vertex P: K = (P,Q,R), M = (P,Qt,Rt)
+        const double *P_ = V + 2 * tv[0], *Q_ = V + 2 * tv[1], *R_ = V + 2 * tv[2], *Qt = V + 2 * tv[3], *Rt = V + 2 * tv[4];
+        const dw g10 = dw_from(Q_[0] - P_[0]), g11 = dw_from(Q_[1] - P_[1]);
+        const dw g20 = dw_from(R_[0] - Q_[0]), g21 = dw_from(R_[1] - Q_[1]);
+        const dw g30 = dw_from(-(Qt[0] - P_[0])), g31 = dw_from(-(Qt[1] - P_[1]));
+        const dw g40 = dw_from(-(Rt[0] - Qt[0])), g41 = dw_from(-(Rt[1] - Qt[1]));
+        const float2* tb = rdw + ro.t_vert;
+        dw acc[15];
+#pragma unroll
+        for (int q = 0; q < 15; ++q) acc[q] = {0.f, 0.f};
+        for (int m = lane; m < ro.n_vert; m += 32) {
+            const float2* r = tb + 10 * m;  // dphi[5], x1, x2, y1, y2, weight
+            const dw u1 = ldw(r, 5), u2 = ldw(r, 6), u3 = ldw(r, 7), u4 = ldw(r, 8);
+            const dw x = dw_add(dw_add(dw_mul(g10, u1), dw_mul(g20, u2)), dw_add(dw_mul(g30, u3), dw_mul(g40, u4)));
+            const dw y = dw_add(dw_add(dw_mul(g11, u1), dw_mul(g21, u2)), dw_add(dw_mul(g31, u3), dw_mul(g41, u4)));
+            const dw kv = dw_kpow<PW>(dw_add(dw_sqr(x), dw_sqr(y)));
+            touch_accumulate<5>(acc, dw_mul(ldw(r, 9), kv), r);
+#pragma unroll
+            for (int q = 0; q < 15; ++q) acc[q] = dw_renorm(acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 15; ++q)
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) acc[q] = dw_add(acc[q], dw_shfl_xor(acc[q], o));
+        if (lane == 0) {
+            const double sc = C * jK * jM / (4.0 - 2.0 * s);
+            int q = 0;
+            for (int i = 0; i < 5; ++i)
+                for (int j = i; j < 5; ++j, ++q) out[i * 5 + j] = out[j * 5 + i] = sc * dw_to(acc[q]);
+        }
+    }
+}
+
 // partial boundary sums of the facet chunks -> Bf, chunks added in order
 __global__ void bnd_chunks_sum(int64_t m, int nch, const double* __restrict__ part, double* __restrict__ Bf) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -689,6 +788,24 @@ int launch_near_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<dou
     count_launch(2);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FL_OK : set_err(h, FL_ECUDA, std::string("near_pair_dw: ") + cudaGetErrorString(e));
+}
+
+bool touch_dw_applies(const fl_ctx* h, const Plan& P, int pw) {
+    return P.dim == 2 && (pw == 5 || pw == 6 || pw == 7) && !h->far_f64_pipe;
+}
+
+int launch_touch_dw(fl_ctx* h, const Plan& P, DevTables& t, const RuleOffsets& ro, double s, double C, int pw,
+                    cudaStream_t st) {
+    const int ntp = (int)P.tp_type.size();
+    if (ntp == 0) return FL_OK;
+    if (!t.rule_dw) return set_err(h, FL_EINVAL, "touch_pair_dw: double-word rule tables missing");
+    const unsigned g = (unsigned)(((int64_t)ntp * 32 + 127) / 128);
+    if (pw == 5) touch_pair_dw_kernel<5><<<g, 128, 0, st>>>(ntp, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, (const float2*)t.rule_dw, ro, s, C, t.contrib);
+    else if (pw == 6) touch_pair_dw_kernel<6><<<g, 128, 0, st>>>(ntp, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, (const float2*)t.rule_dw, ro, s, C, t.contrib);
+    else touch_pair_dw_kernel<7><<<g, 128, 0, st>>>(ntp, t.tp_type, t.tp_vert, t.tp_cell, t.tp_slot, t.V, t.jac_orig, (const float2*)t.rule_dw, ro, s, C, t.contrib);
+    count_launch(1);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FL_OK : set_err(h, FL_ECUDA, std::string("touch_pair_dw: ") + cudaGetErrorString(e));
 }
 
 void far_dw_record(const Plan& P, int pw, int variant, double ms) {
