@@ -221,3 +221,78 @@ def hmatvec(A, mesh: OracleMesh, s: float, x, m: int = 4, eta: float = 1.0, leaf
         if not tree.sons[c]:
             y[tree.dofs[c]] += -frac_constant(tree.d, s) * (coef[c] @ yh[c])
     return y
+
+
+def _far_field_coefficients(tree: ClusterTree, far, s: float, x, m: int):
+    """yh[c]: for every node c, sum over the admissible pairs (rho, tau) with rho c or an ancestor
+    of c of the kernel couplings of tau's far-field coefficients of x, expanded in c's Chebyshev
+    basis (upward pass, couplings, downward pass of the product)."""
+    nc = len(tree.dofs)
+    md = m ** tree.d
+    coef = {c: leaf_coefficients(tree, c, m) for c in range(nc) if not tree.sons[c]}
+    xh = np.zeros((nc, md))
+    for c in reversed(range(nc)):
+        if tree.sons[c]:
+            for sn in tree.sons[c]:
+                xh[c] += shift_matrix(tree, c, sn, m).T @ xh[sn]
+        else:
+            xh[c] = coef[c].T @ x[tree.dofs[c]]
+    yh = np.zeros((nc, md))
+    for a, b in far:
+        yh[a] += kernel_matrix(tree, a, b, m, s) @ xh[b]
+    for c in range(nc):
+        for sn in tree.sons[c]:
+            yh[sn] += shift_matrix(tree, c, sn, m) @ yh[c]
+    return yh
+
+
+def strong_form_cluster(mesh: OracleMesh, s: float, u_dof, m: int = 4, eta: float = 1.0, leaf: int = 32,
+                        k_cell: int = 3, k_edge: int = 4, k_near: int = 16, dof_mode: str = "interior"):
+    """(-Delta)^s u_h at the cell-rule points of every cell [nc, q] by the cluster method
+    (Section 6): for a point x0 of cell K0, i0 the DOF of K0 closest to x0 and sigma its leaf,
+    u = u_N + u_F with u_N the part on the DOFs of sigma's inadmissible partners; the strong form
+    of u_N is Lemma 4.1's (strong_form with u_N), and that of u_F, whose support lies in
+    admissible partners' boxes away from x0, is -C int k(x0, y) u_F(y) dy, approximated by
+    Chebyshev interpolation: -C sum_alpha L_alpha^sigma(x0) yh_sigma[alpha], yh from the
+    product's upward pass, couplings and downward pass applied to u.
+
+    Readings: ties in "closest" go to the lower DOF index; a cell without a DOF vertex (all its
+    vertices on the boundary) belongs to no support, so its points take the strong form of u
+    itself (no far part)."""
+    from .adaptive import cell_rule_points, strong_form
+
+    tree = ClusterTree(mesh, s, leaf, dof_mode)
+    far, near = block_partition(tree, eta)
+    u_dof = np.asarray(u_dof, dtype=np.float64)
+    yh = _far_field_coefficients(tree, far, s, u_dof, m)
+    C = frac_constant(tree.d, s)
+    leaf_of = np.empty(tree.n, dtype=np.int64)
+    for c in range(len(tree.dofs)):
+        if not tree.sons[c]:
+            leaf_of[tree.dofs[c]] = c
+    partners = {}
+    for a, b in near:
+        partners.setdefault(a, []).append(b)
+    _, dov = mesh.dofs(s, dof_mode)
+    X, _, _ = cell_rule_points(mesh, k_cell)
+    q = X.shape[1]
+    out = np.zeros((mesh.nc, q))
+    opts = dict(k_cell=k_cell, k_edge=k_edge, k_near=k_near, dof_mode=dof_mode)
+    for k0 in range(mesh.nc):
+        dofs = [int(dov[v]) for v in mesh.C[k0] if dov[v] >= 0]
+        if not dofs:
+            out[k0] = strong_form(mesh, s, u_dof, cells=[k0], **opts)[0]
+            continue
+        cache = {}
+        for a in range(q):
+            x0 = X[k0, a]
+            dist = [float(np.sum((mesh.V[tree.vod[i]] - x0) ** 2)) for i in dofs]
+            i0 = min(zip(dist, dofs))[1]
+            sigma = int(leaf_of[i0])
+            if sigma not in cache:
+                uN = np.zeros_like(u_dof)
+                for tau in partners.get(sigma, []):
+                    uN[tree.dofs[tau]] = u_dof[tree.dofs[tau]]
+                cache[sigma] = strong_form(mesh, s, uN, cells=[k0], **opts)[0]
+            out[k0, a] = cache[sigma][a] - C * float(lagrange(tree, sigma, m, x0[None, :])[0] @ yh[sigma])
+    return out
