@@ -541,6 +541,25 @@ int fl_hmatrix_assemble_near(fl_hmatrix H, void* stream);
  * else FL_EINVAL).  Copies on `stream`.  Errors: FL_EINVAL, FL_ECUDA. */
 int fl_hmatrix_get_near(fl_hmatrix H, int64_t* nnz, int32_t* rowptr_dev, int32_t* col_dev, double* val_dev,
                         void* stream);
+/*
+ * The strong form (-Delta)^s u_h by the cluster method (Section 6), at the points of the cell rule
+ * of order k_cell (S_dev [cells][k_cell^2], cells in input order, as fl_strong_form).  For a point
+ * x0 of cell K0, with sigma the leaf of K0's DOF closest to x0 (ties: the lower DOF), u splits
+ * into u_N, its part on the DOFs of sigma's inadmissible partners, and u_F, the rest: the strong
+ * form of u_N is Lemma 4.1's (the facets of the cells touching a near DOF: those of K0 and through
+ * its vertices in float64 with orders k_near / k_edge, the others in double-word arithmetic), that
+ * of u_F is -C sum_alpha L_alpha^sigma(x0) yh_sigma[alpha] with yh the far-field coefficients of
+ * u from the H-matrix product's upward pass, couplings and downward pass.  Points of cells without
+ * a DOF vertex take the strong form of u itself.  Needs no near field.  2D, s in {1/4, 1/2, 3/4},
+ * interior DOFs (else FL_ENOTIMPL).  The first call for a k_cell plans (host).  Errors: FL_EINVAL,
+ * FL_ENOMEM, FL_ENOTIMPL, FL_ECUDA.
+ */
+int fl_hmatrix_strong_form(fl_hmatrix H, const double* u_dev, int k_cell, int k_edge, int k_near, double* S_dev,
+                           void* stream);
+/* The Babuska-Rheinboldt indicators (as fl_br_indicators, f_dev nodal or NULL for f = 1) from the
+ * cluster method's strong form; S_dev [cells][k_cell^2] receives the strong form. */
+int fl_hmatrix_br_indicators(fl_hmatrix H, const double* u_dev, const double* f_dev, int k_cell, int k_edge,
+                             int k_near, double* eta_dev, double* S_dev, void* stream);
 /* info[0..2] after fl_hmatrix_assemble_near: tiles computed, their partial-block entries,
  * device bytes of its plan and workspace (zeros before the first call). */
 int fl_hmatrix_near_info(fl_hmatrix H, int64_t* info);

@@ -42,6 +42,7 @@
 #include <utility>
 #include <vector>
 
+#include "cluster.h"
 #include "context.h"
 #include "device.h"
 
@@ -396,6 +397,253 @@ __global__ void sf_near_kernel(int64_t npts, int q, int d, const double* __restr
     S[(int64_t)K0 * q + a] = C * (acc + near);
 }
 
+// ------------------------------------------------ strong form by the cluster method --
+// (Section 6: for a point x0 of cell K0 and sigma the leaf of K0's DOF closest to x0,
+// u = u_N + u_F with u_N on the DOFs of sigma's inadmissible partners; the strong form of u_N
+// is Lemma 4.1's, that of u_F is -C int k(x0, y) u_F(y) dy = -C sum_alpha L_alpha^sigma(x0)
+// yh_sigma[alpha] with the far-field coefficients of the H-matrix product of u.)
+
+constexpr int HSF_FCH = 2048;  // facets per chunk of the far kernel
+
+__device__ __forceinline__ bool hsf_near(const uint32_t* bits, int leaf) {
+    return (bits[leaf >> 5] >> (leaf & 31)) & 1u;
+}
+
+// nodal value of the near part of u at vertex v (0 off the near DOFs)
+__device__ __forceinline__ double hsf_u(int v, const int* dov, const double* u, const int* dof_leaf,
+                                        const uint32_t* bits) {
+    const int i = dov[v];
+    return (i >= 0 && hsf_near(bits, dof_leaf[i])) ? u[i] : 0.0;
+}
+
+// gradient of the near part on the (original) cell K, 2D; the expressions of sf_prep_kernel
+__device__ void hsf_grad(int K, const int* cells, const double* V, const int* dov, const double* u,
+                         const int* dof_leaf, const uint32_t* bits, double& gx, double& gy) {
+    const int* c = cells + (int64_t)K * 3;
+    const double u0 = hsf_u(c[0], dov, u, dof_leaf, bits), u1 = hsf_u(c[1], dov, u, dof_leaf, bits),
+                 u2 = hsf_u(c[2], dov, u, dof_leaf, bits);
+    const double p0x = V[2 * c[0]], p0y = V[2 * c[0] + 1];
+    const double e1x = V[2 * c[1]] - p0x, e1y = V[2 * c[1] + 1] - p0y;
+    const double e2x = V[2 * c[2]] - p0x, e2y = V[2 * c[2] + 1] - p0y;
+    const double du1 = u1 - u0, du2 = u2 - u0;
+    const double det = e1x * e2y - e1y * e2x;
+    gx = (du1 * e2y - du2 * e1y) / det;
+    gy = (e1x * du2 - e2x * du1) / det;
+}
+
+// per group and facet of its list: the jump of the near part's normal derivative times 1/(2sm)
+__global__ void hsf_jump_kernel(const int64_t* __restrict__ gf_ptr, const int* __restrict__ gf_fac,
+                                const uint32_t* __restrict__ gbits, int words, const int* __restrict__ fac,
+                                const double* __restrict__ fn, const int* __restrict__ cells,
+                                const double* __restrict__ V, const int* __restrict__ dov,
+                                const double* __restrict__ u, const int* __restrict__ dof_leaf, double cA_scale,
+                                double* __restrict__ cj) {
+    const int g = blockIdx.y;
+    const int64_t idx = gf_ptr[g] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= gf_ptr[g + 1]) return;
+    const uint32_t* bits = gbits + (int64_t)g * words;
+    const int e = gf_fac[idx];
+    const int kp = fac[4 * e + 2], km = fac[4 * e + 3];
+    double gx, gy;
+    hsf_grad(kp, cells, V, dov, u, dof_leaf, bits, gx, gy);
+    double J = fn[3 * e] * gx + fn[3 * e + 1] * gy;
+    if (km >= 0) {
+        hsf_grad(km, cells, V, dov, u, dof_leaf, bits, gx, gy);
+        J -= fn[3 * e] * gx + fn[3 * e + 1] * gy;
+    }
+    cj[idx] = J * cA_scale;
+}
+
+// The far facets of each point's group (those sharing no vertex with the point's cell),
+// double-word as in sf_far_dw_kernel: block = (group, 128 of its points, a chunk of its facets).
+template <int PWK>
+__global__ void __launch_bounds__(SF_THREADS) hsf_far_dw_kernel(
+    const int* __restrict__ blk_g, const int* __restrict__ blk_p0, const int* __restrict__ blk_ch,
+    const int* __restrict__ gp_ptr, const int* __restrict__ gp_idx, const int64_t* __restrict__ gf_ptr,
+    const int* __restrict__ gf_fac, const int64_t* __restrict__ gpo, int q, const double* __restrict__ X,
+    const int* __restrict__ perm, const int* __restrict__ cells, const int* __restrict__ fac,
+    const double* __restrict__ fn, int ke, const double* __restrict__ yrec, const double* __restrict__ we,
+    const double* __restrict__ cj, double* __restrict__ part) {
+    __shared__ float4 sy[SF_TREC];
+    __shared__ float2 sc[SF_TREC];
+    __shared__ int2 sab[SF_TREC];
+    const int b = blockIdx.x;
+    const int g = blk_g[b], ch = blk_ch[b];
+    const int ng = gp_ptr[g + 1] - gp_ptr[g];
+    const int i = blk_p0[b] + threadIdx.x;
+    const bool valid = i < ng;
+    const int p0 = gp_idx[gp_ptr[g] + blk_p0[b]];
+    const double ox = X[2 * (int64_t)p0], oy = X[2 * (int64_t)p0 + 1];
+    dw xr = {0.f, 0.f}, yr = {0.f, 0.f}, acc = {0.f, 0.f};
+    int v0 = -1, v1 = -1, v2 = -1;
+    if (valid) {
+        const int p = gp_idx[gp_ptr[g] + i];
+        xr = dw_from(X[2 * (int64_t)p] - ox);
+        yr = dw_from(X[2 * (int64_t)p + 1] - oy);
+        const int K = perm[p / q];
+        v0 = cells[3 * K];
+        v1 = cells[3 * K + 1];
+        v2 = cells[3 * K + 2];
+    }
+    const int64_t fb = gf_ptr[g] + (int64_t)ch * HSF_FCH;
+    const int64_t fe = min(gf_ptr[g + 1], fb + HSF_FCH);
+    const int fpt = SF_TREC / ke;
+    const float4 nn0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t f = fb; f < fe; f += fpt) {
+        const int nf = (int)min((int64_t)fpt, fe - f);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nf * ke; t += SF_THREADS) {
+            const int64_t idx = f + t / ke;
+            const int gq = t - (t / ke) * ke;
+            const int e = gf_fac[idx];
+            const int64_t gi = (int64_t)e * ke + gq;
+            const dw yx = dw_from(yrec[2 * gi] - ox), yy = dw_from(yrec[2 * gi + 1] - oy);
+            sy[t] = make_float4(yx.h, yx.l, yy.h, yy.l);
+            const dw c = dw_from(we[gq] * fn[3 * e + 2] * cj[idx]);
+            sc[t] = make_float2(c.h, c.l);
+        }
+        for (int t = threadIdx.x; t < nf; t += SF_THREADS) {
+            const int e = gf_fac[f + t];
+            sab[t] = make_int2(fac[4 * e], fac[4 * e + 1]);
+        }
+        __syncthreads();
+        for (int j = 0; j < nf; ++j) {
+            const int2 ab = sab[j];
+            const bool use = ab.x != v0 && ab.x != v1 && ab.x != v2 && ab.y != v0 && ab.y != v1 && ab.y != v2;
+            if (__all_sync(0xffffffffu, use)) {
+                for (int gq = 0; gq < ke; ++gq) {
+                    const float2 c2 = sc[j * ke + gq];
+                    sf_term<PWK, false>(acc, xr, yr, sy[j * ke + gq], dw{c2.x, c2.y}, nn0);
+                }
+            } else if (use) {
+                for (int gq = 0; gq < ke; ++gq) {
+                    const float2 c2 = sc[j * ke + gq];
+                    sf_term<PWK, false>(acc, xr, yr, sy[j * ke + gq], dw{c2.x, c2.y}, nn0);
+                }
+            }
+            acc = dw_renorm(acc);
+        }
+    }
+    if (valid) part[gpo[g] + (int64_t)ch * ng + i] = dw_to(acc);
+}
+
+__device__ __forceinline__ double hsf_cheb_node(double c, double L, int m, int k) {
+    return c + 0.5 * L * cos((2.0 * (k + 1) - 1.0) * M_PI / (2.0 * m));
+}
+
+// per point: the facets of its cell and the other facets through its vertices for the near part
+// (float64, as sf_near_kernel with the near part's values), the far-kernel chunks of its group in
+// order, and the far field -sum_alpha L_alpha^sigma(x0) yh_sigma[alpha]; S[K0 q + a] = C (...)
+__global__ void hsf_near_kernel(int64_t npts, int q, const double* __restrict__ X, const double* __restrict__ lam,
+                                const int* __restrict__ perm, const int* __restrict__ cells,
+                                const double* __restrict__ V, const int* __restrict__ dov, const double* __restrict__ u,
+                                const int* __restrict__ c2f, const int* __restrict__ fac, const double* __restrict__ fn,
+                                int kn, const double* __restrict__ tn, const double* __restrict__ wn,
+                                const int* __restrict__ v2e_ptr, const int* __restrict__ v2e, int ke,
+                                const double* __restrict__ yrec, const double* __restrict__ we,
+                                const int* __restrict__ pgroup, const int* __restrict__ plocal,
+                                const uint32_t* __restrict__ gbits, int words, const int* __restrict__ dof_leaf,
+                                const int* __restrict__ gnode, const int* __restrict__ gp_ptr,
+                                const int* __restrict__ gch, const int64_t* __restrict__ gpo,
+                                const double* __restrict__ part, int m, int md, const double* __restrict__ yh,
+                                const double* __restrict__ center, const double* __restrict__ side, double s,
+                                double mexp, double C, double* __restrict__ S) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npts) return;
+    const int64_t kint = p / q;
+    const int a = (int)(p - kint * q);
+    const int K0 = perm[kint];
+    const int g = pgroup[p];
+    const uint32_t* bits = gbits + (int64_t)g * words;
+    const double x0 = X[2 * p], x1 = X[2 * p + 1];
+    const int* c = cells + (int64_t)K0 * 3;
+    double ux;
+    {
+        const double l1 = lam[2 * a], l2 = lam[2 * a + 1], l0 = 1.0 - l1 - l2;
+        ux = l0 * hsf_u(c[0], dov, u, dof_leaf, bits) + l1 * hsf_u(c[1], dov, u, dof_leaf, bits) +
+             l2 * hsf_u(c[2], dov, u, dof_leaf, bits);
+    }
+    double g0x, g0y;
+    hsf_grad(K0, cells, V, dov, u, dof_leaf, bits, g0x, g0y);
+    const double cown = 1.0 / mexp, cnbr = 1.0 / (2.0 * s * mexp), cA = 1.0 / (2.0 * s * mexp);
+    double near = 0.0;
+    for (int j = 0; j < 3; ++j) {
+        const int e = c2f[(int64_t)K0 * 3 + j];
+        const int va = fac[4 * e], vb = fac[4 * e + 1], kp = fac[4 * e + 2], km = fac[4 * e + 3];
+        const double* n = fn + (int64_t)e * 3;
+        const double sg = kp == K0 ? 1.0 : -1.0;
+        const int Kn = kp == K0 ? km : kp;
+        const double n0x = sg * n[0], n0y = sg * n[1];
+        double cg = cown * (n0x * g0x + n0y * g0y);
+        if (Kn >= 0) {
+            double gx, gy;
+            hsf_grad(Kn, cells, V, dov, u, dof_leaf, bits, gx, gy);
+            cg -= cnbr * (n0x * gx + n0y * gy);
+        }
+        for (int gq = 0; gq < kn; ++gq) {
+            const double t = tn[gq];
+            const double ax = V[2 * va], ay = V[2 * va + 1];
+            const double yx = ax + t * (V[2 * vb] - ax), yy = ay + t * (V[2 * vb + 1] - ay);
+            const double w = wn[gq] * n[2];
+            const double dx = x0 - yx, dy = x1 - yy;
+            const double r2 = dx * dx + dy * dy;
+            const double k0 = pow(r2, -0.5 * mexp);
+            const double k1 = pow(r2, -0.5 * (2.0 + 2.0 * s));
+            const double nd = n0x * dx + n0y * dy;
+            const double du = Kn >= 0 ? g0x * dx + g0y * dy : ux;
+            near += w * (cg * k0 - du * nd * k1 / (2.0 * s));
+        }
+    }
+    for (int j = 0; j < 3; ++j) {
+        for (int qq = v2e_ptr[c[j]]; qq < v2e_ptr[c[j] + 1]; ++qq) {
+            const int e = v2e[qq];
+            if (e == c2f[(int64_t)K0 * 3] || e == c2f[(int64_t)K0 * 3 + 1] || e == c2f[(int64_t)K0 * 3 + 2]) continue;
+            const int kp = fac[4 * e + 2], km = fac[4 * e + 3];
+            double gx, gy;
+            hsf_grad(kp, cells, V, dov, u, dof_leaf, bits, gx, gy);
+            double J = fn[3 * e] * gx + fn[3 * e + 1] * gy;
+            if (km >= 0) {
+                hsf_grad(km, cells, V, dov, u, dof_leaf, bits, gx, gy);
+                J -= fn[3 * e] * gx + fn[3 * e + 1] * gy;
+            }
+            const double cjv = J * cA;
+            for (int gq = 0; gq < ke; ++gq) {
+                const int64_t i = (int64_t)e * ke + gq;
+                const double dx = x0 - yrec[2 * i], dy = x1 - yrec[2 * i + 1];
+                near += we[gq] * fn[3 * e + 2] * cjv * pow(dx * dx + dy * dy, -0.5 * mexp);
+            }
+        }
+    }
+    double acc = 0.0;
+    const int ng = gp_ptr[g + 1] - gp_ptr[g];
+    const int il = plocal[p];
+    for (int ch = 0; ch < gch[g]; ++ch) acc += part[gpo[g] + (int64_t)ch * ng + il];
+    double farf = 0.0;
+    const int cn = gnode[g];
+    if (cn >= 0) {
+        double lx[12], ly[12];
+        const double cx = center[2 * (int64_t)cn], cy = center[2 * (int64_t)cn + 1], L = side[cn];
+        for (int k = 0; k < m; ++k) {
+            const double xk = hsf_cheb_node(cx, L, m, k), yk = hsf_cheb_node(cy, L, m, k);
+            double vx = 1.0, vy = 1.0;
+            for (int l = 0; l < m; ++l)
+                if (l != k) {
+                    vx *= (x0 - hsf_cheb_node(cx, L, m, l)) / (xk - hsf_cheb_node(cx, L, m, l));
+                    vy *= (x1 - hsf_cheb_node(cy, L, m, l)) / (yk - hsf_cheb_node(cy, L, m, l));
+                }
+            lx[k] = vx;
+            ly[k] = vy;
+        }
+        const double* y = yh + (int64_t)cn * md;
+        for (int k0 = 0; k0 < m; ++k0) {
+            double r = 0.0;
+            for (int k1 = 0; k1 < m; ++k1) r += ly[k1] * y[k0 * m + k1];
+            farf += lx[k0] * r;
+        }
+    }
+    S[(int64_t)K0 * q + a] = C * (acc + near - farf);
+}
+
 // per cell: h_K^{2s} sum_a W_a (f(x_a) - S_a)^2
 __global__ void br_cell_kernel(int64_t nc, int d, int q, const int* __restrict__ cells, const double* __restrict__ V,
                                const double* __restrict__ jac, const double* __restrict__ lam,
@@ -598,6 +846,7 @@ int ensure_sf_topology(fl_ctx* h, int pi, cudaStream_t st) {
     SF_TRY(upload(h, &t.sf_fac, fac, st));
     SF_TRY(upload(h, &t.sf_fn, fn, st));
     SF_TRY(upload(h, &t.sf_c2f, c2f_local, st));
+    t.sf_c2f_host = c2f_local;
     // vertex -> facets through it (2D)
     std::vector<int> v2e_ptr(P.nv + 1, 0), v2e;
     if (d == 2) {
@@ -808,6 +1057,273 @@ int strong_form(fl_ctx* h, double s, const double* u, int kc, int ke, int kn, do
     }
     SF_CUDA(h, cudaGetLastError());
     return FL_OK;
+}
+
+int sf_topology(fl_ctx* h, int pi, cudaStream_t st, const std::vector<int>** c2f, int64_t* nfac) {
+    SF_CUDA(h, cudaSetDevice(h->device));
+    SF_TRY(ensure_device_tables(h, pi, st));
+    SF_TRY(ensure_sf_topology(h, pi, st));
+    *c2f = &h->dev[pi].sf_c2f_host;
+    *nfac = h->dev[pi].sf_nfac;
+    return FL_OK;
+}
+
+int plan_hsf(const Plan& P, const ClusterPlan& C, const std::vector<int>& c2f, int64_t nfac, int kc, HsfPlan& Q,
+             std::string& err) {
+    Q = HsfPlan();
+    if (P.dim != 2) {
+        err = "the cluster strong form is 2D";
+        return FL_ENOTIMPL;
+    }
+    const int64_t nc = P.nc, n = P.n;
+    const Rule R = make_rule(2, kc);
+    const int q = R.q;
+    Q.kc = kc;
+    Q.npts = nc * q;
+    // leaves in node order; the leaf of every DOF
+    std::vector<int> lidx(C.nodes, -1), leaves;
+    for (int a = 0; a < C.nodes; ++a)
+        if (C.son[2 * a] < 0) {
+            lidx[a] = (int)leaves.size();
+            leaves.push_back(a);
+        }
+    const int nl = (int)leaves.size();
+    Q.words = (nl + 31) / 32;
+    Q.dof_leaf.assign(n, -1);
+    std::vector<int> dof_node(n, -1);
+    for (int a : leaves)
+        for (int p = C.lo[a]; p < C.hi[a]; ++p) {
+            Q.dof_leaf[C.perm[p]] = lidx[a];
+            dof_node[C.perm[p]] = a;
+        }
+    // each point's group: the leaf of its cell's DOF closest to it (ties: lower DOF), or the group
+    // of cells without DOFs
+    std::vector<int> gof_node(C.nodes, -1);
+    std::vector<int> pnode(Q.npts, -1);
+    bool any_free = false;
+    for (int64_t k = 0; k < nc; ++k) {
+        const int K = P.perm[k];
+        const int* c = &P.C[(int64_t)K * 3];
+        const double p0x = P.V[2 * c[0]], p0y = P.V[2 * c[0] + 1];
+        const double e1x = P.V[2 * c[1]] - p0x, e1y = P.V[2 * c[1] + 1] - p0y;
+        const double e2x = P.V[2 * c[2]] - p0x, e2y = P.V[2 * c[2] + 1] - p0y;
+        for (int a = 0; a < q; ++a) {
+            const double l1 = R.lam[2 * a], l2 = R.lam[2 * a + 1];
+            const double x = p0x + l1 * e1x + l2 * e2x, y = p0y + l1 * e1y + l2 * e2y;
+            int best = -1;
+            double bd = 0.0;
+            for (int j = 0; j < 3; ++j) {
+                const int i = P.dov[c[j]];
+                if (i < 0) continue;
+                const double dx = P.V[2 * c[j]] - x, dy = P.V[2 * c[j] + 1] - y;
+                const double dd = dx * dx + dy * dy;
+                if (best < 0 || dd < bd || (dd == bd && i < best)) {
+                    best = i;
+                    bd = dd;
+                }
+            }
+            pnode[k * q + a] = best >= 0 ? dof_node[best] : -1;
+            any_free = any_free || best < 0;
+        }
+    }
+    for (int64_t p = 0; p < Q.npts; ++p)
+        if (pnode[p] >= 0) gof_node[pnode[p]] = 1;
+    for (int a : leaves)
+        if (gof_node[a] > 0) {
+            gof_node[a] = Q.groups++;
+            Q.gnode.push_back(a);
+        }
+    const int free_group = any_free ? Q.groups++ : -1;
+    if (any_free) Q.gnode.push_back(-1);
+    if (Q.groups > 65535) {
+        err = "more than 65535 point groups";
+        return FL_ENOTIMPL;
+    }
+    const int G = Q.groups;
+    Q.pgroup.resize(Q.npts);
+    Q.plocal.resize(Q.npts);
+    Q.gp_ptr.assign(G + 1, 0);
+    for (int64_t p = 0; p < Q.npts; ++p) {
+        Q.pgroup[p] = pnode[p] >= 0 ? gof_node[pnode[p]] : free_group;
+        ++Q.gp_ptr[Q.pgroup[p] + 1];
+    }
+    for (int g = 0; g < G; ++g) Q.gp_ptr[g + 1] += Q.gp_ptr[g];
+    Q.gp_idx.resize(Q.npts);
+    {
+        std::vector<int> fill(Q.gp_ptr.begin(), Q.gp_ptr.end() - 1);
+        for (int64_t p = 0; p < Q.npts; ++p) {
+            const int g = Q.pgroup[p];
+            Q.plocal[p] = fill[g] - Q.gp_ptr[g];
+            Q.gp_idx[fill[g]++] = (int)p;
+        }
+    }
+    // per group: near leaves and the facets of the cells touching a near DOF
+    std::vector<std::vector<int>> partners(C.nodes);
+    for (size_t b = 0; b + 1 < C.near.size(); b += 2) partners[C.near[b]].push_back(C.near[b + 1]);
+    Q.gbits.assign((size_t)G * Q.words, 0u);
+    Q.gf_ptr.assign(G + 1, 0);
+    std::vector<int64_t> cmark(nc, -1), fmark(nfac, -1);
+    std::vector<int> fl;
+    for (int g = 0; g < G; ++g) {
+        uint32_t* bits = &Q.gbits[(size_t)g * Q.words];
+        fl.clear();
+        if (Q.gnode[g] < 0) {
+            for (int l = 0; l < nl; ++l) bits[l >> 5] |= 1u << (l & 31);
+            for (int64_t e = 0; e < nfac; ++e) fl.push_back((int)e);
+        } else {
+            for (int tau : partners[Q.gnode[g]]) {
+                const int l = lidx[tau];
+                bits[l >> 5] |= 1u << (l & 31);
+                for (int pp = C.lo[tau]; pp < C.hi[tau]; ++pp) {
+                    const int v = P.vod[C.perm[pp]];
+                    for (int r = P.v2c_ptr[v]; r < P.v2c_ptr[v + 1]; ++r) {
+                        const int K = P.v2c[r];
+                        if (cmark[K] == g) continue;
+                        cmark[K] = g;
+                        for (int j = 0; j < 3; ++j) {
+                            const int e = c2f[(int64_t)K * 3 + j];
+                            if (fmark[e] == g) continue;
+                            fmark[e] = g;
+                            fl.push_back(e);
+                        }
+                    }
+                }
+            }
+            std::sort(fl.begin(), fl.end());
+        }
+        Q.gf_fac.insert(Q.gf_fac.end(), fl.begin(), fl.end());
+        Q.gf_ptr[g + 1] = (int64_t)Q.gf_fac.size();
+        Q.maxf = std::max<int64_t>(Q.maxf, (int64_t)fl.size());
+    }
+    // far-kernel blocks: (group, 128 points, facet chunk); partial sums per group: points x chunks
+    Q.gch.resize(G);
+    Q.gpo.resize(G);
+    int64_t off = 0;
+    for (int g = 0; g < G; ++g) {
+        const int64_t nf = Q.gf_ptr[g + 1] - Q.gf_ptr[g];
+        const int ng = Q.gp_ptr[g + 1] - Q.gp_ptr[g];
+        Q.gch[g] = (int)std::max<int64_t>(1, (nf + HSF_FCH - 1) / HSF_FCH);
+        Q.gpo[g] = off;
+        off += (int64_t)ng * Q.gch[g];
+        for (int p0 = 0; p0 < ng; p0 += SF_THREADS)
+            for (int ch = 0; ch < Q.gch[g]; ++ch) {
+                Q.blk_g.push_back(g);
+                Q.blk_p0.push_back(p0);
+                Q.blk_ch.push_back(ch);
+            }
+    }
+    Q.nparts = off;
+    return FL_OK;
+}
+
+int strong_form_cluster(fl_ctx* h, double s, const double* u, int kc, int ke, int kn, const HsfDev& g, double* S,
+                        cudaStream_t st) {
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    if (!u || !S) return set_err(h, FL_EINVAL, "NULL u or S");
+    if (P.dim != 2) return set_err(h, FL_ENOTIMPL, "the cluster strong form is 2D");
+    if (kc < 1 || kc > SF_MAXK_CELL || ke < 1 || ke > SF_MAXK_EDGE || kn < 1 || kn > SF_MAXK_NEAR)
+        return set_err(h, FL_EINVAL, "k_cell in [1,16], k_edge in [1,32], k_near in [1,64]");
+    const int pw0 = quarter(s);
+    if (pw0 == 0) return set_err(h, FL_ENOTIMPL, "the cluster strong form takes s in {1/4, 1/2, 3/4}");
+    for (int64_t v = 0; v < P.nv; ++v)
+        if (P.onb[v] && P.dov[v] >= 0) return set_err(h, FL_ENOTIMPL, "the cluster strong form takes interior DOFs");
+    SF_CUDA(h, cudaSetDevice(h->device));
+    SF_TRY(ensure_device_tables(h, pi, st));
+    SF_TRY(ensure_sf_topology(h, pi, st));
+    SF_TRY(ensure_sf_rules(h, pi, kc, ke, kn, st));
+    DevTables& t = h->dev[pi];
+    const int64_t nc = P.nc, nfac = t.sf_nfac, nint = t.sf_nint;
+    const int q = kc * kc;
+    const int64_t npts = nc * q;
+    const double mexp = 2.0 * s;
+    const double cA_scale = 1.0 / (2.0 * s * mexp);
+    // workspace: grad (unused values), X, yrec, crec, brec (geometry of the facet points)
+    const size_t n_grad = nc * 2, n_X = npts * 2, n_y = nfac * ke * 2, n_c = nfac * ke, n_b = ke;
+    SF_TRY(ensure_ws(h, (n_grad + n_X + n_y + n_c + n_b + 8 * 5) * sizeof(double)));
+    double* base = (double*)h->sf_ws;
+    auto take = [&](size_t n) {
+        double* p = base;
+        base += (n + 7) / 8 * 8;
+        return p;
+    };
+    double* grad = take(n_grad);
+    double* X = take(n_X);
+    double* yrec = take(n_y);
+    double* crec = take(n_c);
+    double* brec = take(n_b);
+    const double* lam = t.sf_rule;
+    const Rule Rc = make_rule(2, kc);
+    const double* wc = t.sf_rule + Rc.lam.size();
+    const double* te = wc + Rc.w.size();
+    const double* we = te + ke;
+    const double* tn = we + ke;
+    const double* wn = tn + kn;
+    if (nc == 0) return FL_OK;
+    sf_prep_kernel<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(nc, 2, q, t.sf_perm, t.cells, t.V, t.dov, u, lam, grad, X);
+    const int64_t nrec = nfac * ke;
+    sf_facet_kernel<<<(unsigned)((nrec + 127) / 128), 128, 0, st>>>(nfac, nint, 2, ke, t.sf_fac, t.sf_fn, t.V, t.dov, u,
+                                                                    grad, te, we, 1.0, 0.0, 0, yrec, crec, brec);
+    count_launch(2);
+    // near parts' jumps per group and facet
+    if (g.groups > 0 && g.maxf > 0) {
+        const dim3 grid((unsigned)((g.maxf + 127) / 128), (unsigned)g.groups);
+        hsf_jump_kernel<<<grid, 128, 0, st>>>(g.gf_ptr, g.gf_fac, g.gbits, g.words, t.sf_fac, t.sf_fn, t.cells, t.V,
+                                              t.dov, u, g.dof_leaf, cA_scale, g.cj);
+        count_launch();
+    }
+    if (g.nblocks > 0) {
+        const unsigned nb = (unsigned)g.nblocks;
+#define HSF_FAR(PW)                                                                                                   \
+    hsf_far_dw_kernel<PW><<<nb, SF_THREADS, 0, st>>>(g.blk_g, g.blk_p0, g.blk_ch, g.gp_ptr, g.gp_idx, g.gf_ptr,      \
+                                                     g.gf_fac, g.gpo, q, X, t.sf_perm, t.cells, t.sf_fac, t.sf_fn, ke, \
+                                                     yrec, we, g.cj, g.part)
+        if (pw0 == 1) HSF_FAR(1);
+        else if (pw0 == 2) HSF_FAR(2);
+        else HSF_FAR(3);
+#undef HSF_FAR
+        count_launch();
+    }
+    hsf_near_kernel<<<(unsigned)((npts + 127) / 128), 128, 0, st>>>(
+        npts, q, X, lam, t.sf_perm, t.cells, t.V, t.dov, u, t.sf_c2f, t.sf_fac, t.sf_fn, kn, tn, wn, t.sf_v2e_ptr,
+        t.sf_v2e, ke, yrec, we, g.pgroup, g.plocal, g.gbits, g.words, g.dof_leaf, g.gnode, g.gp_ptr, g.gch, g.gpo,
+        g.part, g.m, g.md, g.yh, g.center, g.side, s, mexp, frac_const(2, s), S);
+    count_launch();
+    SF_CUDA(h, cudaGetLastError());
+    return FL_OK;
+}
+
+int br_from_strong_form(fl_ctx* h, double s, const double* f, int kc, const double* S, double* eta, cudaStream_t st) {
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    if (!eta || !S) return set_err(h, FL_EINVAL, "NULL eta or S");
+    const int d = P.dim;
+    const int q = d == 1 ? kc : kc * kc;
+    const int64_t nc = P.nc;
+    DevTables& t = h->dev[pi];
+    void* scratch = nullptr;
+    cudaError_t e = pool_dev_alloc(&scratch, std::max<size_t>(nc * sizeof(double), 16));
+    if (e != cudaSuccess) return set_err(h, FL_ENOMEM, std::string("indicator scratch: ") + cudaGetErrorString(e));
+    double* err = (double*)scratch;
+    const Rule Rc = make_rule(d, kc);
+    const double* lam = t.sf_rule;
+    const double* wc = t.sf_rule + Rc.lam.size();
+    br_cell_kernel<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(nc, d, q, t.cells, t.V, t.jac_orig, lam, wc, f, S,
+                                                                 2.0 * s, err);
+    count_launch();
+    if (P.n > 0) {
+        br_dof_kernel<<<(unsigned)((P.n + 127) / 128), 128, 0, st>>>(P.n, t.vod, t.v2c_ptr, t.v2c, err, eta);
+        count_launch();
+    }
+    int r = FL_OK;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) r = set_err(h, FL_ECUDA, std::string("indicator kernels: ") + cudaGetErrorString(e));
+    const cudaError_t es = cudaStreamSynchronize(st);
+    pool_dev_free(scratch);
+    if (r == FL_OK && es != cudaSuccess) r = set_err(h, FL_ECUDA, std::string("indicators: ") + cudaGetErrorString(es));
+    return r;
 }
 
 int br_indicators(fl_ctx* h, double s, const double* u, const double* f, int kc, int ke, int kn, double* eta,

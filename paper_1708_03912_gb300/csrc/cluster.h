@@ -57,4 +57,41 @@ struct HNearDev {
     double* P = nullptr;  // partial blocks of the tiles
 };
 
+// The strong form by the cluster method (adaptive.cu): the cell-rule points grouped by the leaf
+// of the DOF of their cell closest to them (ties: the lower DOF; cells without a DOF vertex form
+// one group of their own, with every DOF near and no far part), per group the near leaves as a
+// bitset and the facets where the near part's normal derivative can jump (the facets of the cells
+// touching a near DOF), and the far kernel's blocks.
+struct HsfPlan {
+    int kc = 0;
+    int64_t npts = 0;
+    int groups = 0, words = 0;            // groups; 32-bit words per near-leaf bitset
+    std::vector<int> gnode;               // per group: its leaf node, or -1 (the cells without DOFs)
+    std::vector<int> gp_ptr, gp_idx;      // per group: its points (internal cell k, point a: k q + a)
+    std::vector<int> pgroup, plocal;      // per point: its group and its position in the group's list
+    std::vector<int64_t> gf_ptr;          // per group: its facets (strong-form facet ids, ascending)
+    std::vector<int> gf_fac;
+    std::vector<uint32_t> gbits;          // groups x words
+    std::vector<int> dof_leaf;            // per DOF: its leaf's index (leaves in node order)
+    std::vector<int> gch;                 // per group: facet chunks of the far kernel
+    std::vector<int64_t> gpo;             // per group: offset of its partial sums (points x chunks)
+    std::vector<int> blk_g, blk_p0, blk_ch;  // far-kernel blocks: group, first point, facet chunk
+    int64_t nparts = 0, maxf = 0;         // partial sums; the longest facet list
+};
+int plan_hsf(const Plan& P, const ClusterPlan& C, const std::vector<int>& c2f, int64_t nfac, int kc, HsfPlan& Q,
+             std::string& err);
+
+struct HsfDev {
+    int groups = 0, words = 0, md = 0, m = 0;
+    int64_t nparts = 0, nblocks = 0, maxf = 0;
+    int *gnode = nullptr, *gp_ptr = nullptr, *gp_idx = nullptr, *pgroup = nullptr, *plocal = nullptr, *gf_fac = nullptr;
+    int64_t *gf_ptr = nullptr, *gpo = nullptr;
+    uint32_t* gbits = nullptr;
+    int *dof_leaf = nullptr, *gch = nullptr, *blk_g = nullptr, *blk_p0 = nullptr, *blk_ch = nullptr;
+    double* cj = nullptr;     // per group facet: the near part's jump times 1/(2sm)
+    double* part = nullptr;   // far-kernel partial sums
+    // the H-matrix's far field: per node yh [md], cube centre [d] and side
+    const double *yh = nullptr, *center = nullptr, *side = nullptr;
+};
+
 }  // namespace fl

@@ -122,6 +122,7 @@ struct DevTables {
     int* sf_fac = nullptr;     // nfac*4: vertices a, b (1D: a twice), cell K+, cell K- (-1 on the boundary)
     double* sf_fn = nullptr;   // nfac*(dim+1): unit normal outward of K+, length (1D: 1)
     int* sf_c2f = nullptr;     // nc*nvpc: facets of every cell (original order)
+    std::vector<int> sf_c2f_host;  // its host copy (the cluster strong form's planner)
     int* sf_perm = nullptr;    // nc: internal -> original cell
     int *sf_v2e_ptr = nullptr, *sf_v2e = nullptr;  // vertex -> facets through it (2D)
     double* sf_rule = nullptr; // cell rule, edge rule, near-edge rule of the last call
@@ -235,6 +236,13 @@ int br_indicators(fl_ctx* h, double s, const double* u, const double* f, int k_c
                   double* eta, double* S, cudaStream_t st);
 int mark_max(fl_ctx* h, double s, const double* eta, double theta, uint8_t* dof_marks, uint8_t* cell_marks,
              cudaStream_t st);
+// the strong form by the cluster method (adaptive.cu): the facet topology's host data for the
+// planner, and the evaluation with the plan's device copies (far field: H's yh after the far chain)
+struct HsfDev;
+int sf_topology(fl_ctx* h, int pi, cudaStream_t st, const std::vector<int>** c2f, int64_t* nfac);
+int strong_form_cluster(fl_ctx* h, double s, const double* u, int kc, int ke, int kn, const HsfDev& g, double* S,
+                        cudaStream_t st);
+int br_from_strong_form(fl_ctx* h, double s, const double* f, int kc, const double* S, double* eta, cudaStream_t st);
 int refine_mesh(int dim, int64_t nv, const double* V, int64_t nc, const int32_t* C, const uint8_t* marks,
                 int64_t cap_v, int64_t cap_c, double* V_out, int32_t* C_out, int64_t* nv_out, int64_t* nc_out,
                 std::string& err);

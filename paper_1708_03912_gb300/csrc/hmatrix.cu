@@ -62,6 +62,9 @@ struct fl_hm {
     bool hn_planned = false;
     fl::HNearDev hn;
     int64_t hn_entries = 0, hn_bytes = 0;  // tile partial entries; bytes of the plan and workspace
+    // the strong form by the cluster method (fl_hmatrix_strong_form), planned per cell rule
+    int hsf_kc = 0;
+    fl::HsfDev hsf;
     double *xh = nullptr, *yh = nullptr;
     double* Pb = nullptr;  // per admissible pair: K_b xh[tau]
     // Jacobi-PCG with the product (fl_hmatrix_solve), allocated on first use
@@ -88,6 +91,8 @@ int hm_fail(fl_hm* H, int code, const std::string& msg) {
     if (H) H->err = msg;
     return code;
 }
+
+int hm_enqueue(fl_hm* H, const double* x_dev, double* y_dev, cudaStream_t st, cudaStream_t side, bool far_only);
 
 template <typename T>
 int hm_upload(fl_hm* H, T** dst, const std::vector<T>& src, cudaStream_t st) {
@@ -815,6 +820,72 @@ int fl_hmatrix_get_near(fl_hmatrix H, int64_t* nnz, int32_t* rowptr_dev, int32_t
     return FL_OK;
 }
 
+int fl_hmatrix_strong_form(fl_hmatrix H, const double* u_dev, int k_cell, int k_edge, int k_near, double* S_dev,
+                           void* stream) {
+    if (!H) return FL_EINVAL;
+    H->err.clear();
+    if (!u_dev || !S_dev) return hm_fail(H, FL_EINVAL, "NULL u or S");
+    if (k_cell < 1 || k_cell > 16) return hm_fail(H, FL_EINVAL, "k_cell in [1, 16]");
+    if (cudaSetDevice(H->device) != cudaSuccess) return hm_fail(H, FL_ECUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    fl_ctx* h = H->mesh;
+    int rc = FL_OK;
+    if (H->hsf_kc != k_cell) {
+        const std::vector<int>* c2f = nullptr;
+        int64_t nfac = 0;
+        if ((rc = fl::sf_topology(h, H->pi, st, &c2f, &nfac)) != FL_OK) return hm_fail(H, rc, h->err);
+        try {
+            fl::HsfPlan Q;
+            std::string err;
+            rc = fl::plan_hsf(h->plan[H->pi], H->plan, *c2f, nfac, k_cell, Q, err);
+            if (rc != FL_OK) return hm_fail(H, rc, err);
+            fl::HsfDev& g = H->hsf;
+            if ((rc = hm_upload(H, &g.gnode, Q.gnode, st)) || (rc = hm_upload(H, &g.gp_ptr, Q.gp_ptr, st)) ||
+                (rc = hm_upload(H, &g.gp_idx, Q.gp_idx, st)) || (rc = hm_upload(H, &g.pgroup, Q.pgroup, st)) ||
+                (rc = hm_upload(H, &g.plocal, Q.plocal, st)) || (rc = hm_upload(H, &g.gf_ptr, Q.gf_ptr, st)) ||
+                (rc = hm_upload(H, &g.gf_fac, Q.gf_fac, st)) || (rc = hm_upload(H, &g.gbits, Q.gbits, st)) ||
+                (rc = hm_upload(H, &g.dof_leaf, Q.dof_leaf, st)) || (rc = hm_upload(H, &g.gch, Q.gch, st)) ||
+                (rc = hm_upload(H, &g.gpo, Q.gpo, st)) || (rc = hm_upload(H, &g.blk_g, Q.blk_g, st)) ||
+                (rc = hm_upload(H, &g.blk_p0, Q.blk_p0, st)) || (rc = hm_upload(H, &g.blk_ch, Q.blk_ch, st)) ||
+                (rc = hm_alloc(H, &g.cj, Q.gf_fac.size())) || (rc = hm_alloc(H, &g.part, (size_t)Q.nparts)))
+                return rc;
+            g.groups = Q.groups;
+            g.words = Q.words;
+            g.nparts = Q.nparts;
+            g.nblocks = (int64_t)Q.blk_g.size();
+            g.maxf = Q.maxf;
+        } catch (const std::bad_alloc&) {
+            return hm_fail(H, FL_ENOMEM, "out of host memory");
+        }
+        H->hsf_kc = k_cell;
+    }
+    // the far field of u at every node, then the strong form
+    const int launches = fl::hm_enqueue(H, u_dev, nullptr, st, nullptr, true);
+    if (launches < 0) return hm_fail(H, FL_ECUDA, "far-field passes");
+    fl::count_launch(launches);
+    fl::HsfDev g = H->hsf;
+    g.m = H->m;
+    g.md = H->md;
+    g.yh = H->yh;
+    g.center = H->center;
+    g.side = H->side;
+    rc = fl::strong_form_cluster(h, H->s, u_dev, k_cell, k_edge, k_near, g, S_dev, st);
+    if (rc != FL_OK) return hm_fail(H, rc, h->err);
+    return FL_OK;
+}
+
+int fl_hmatrix_br_indicators(fl_hmatrix H, const double* u_dev, const double* f_dev, int k_cell, int k_edge,
+                             int k_near, double* eta_dev, double* S_dev, void* stream) {
+    if (!H) return FL_EINVAL;
+    H->err.clear();
+    if (!eta_dev || !S_dev) return hm_fail(H, FL_EINVAL, "NULL eta or S");
+    int rc = fl_hmatrix_strong_form(H, u_dev, k_cell, k_edge, k_near, S_dev, stream);
+    if (rc != FL_OK) return rc;
+    rc = fl::br_from_strong_form(H->mesh, H->s, f_dev, k_cell, S_dev, eta_dev, (cudaStream_t)stream);
+    if (rc != FL_OK) return hm_fail(H, rc, H->mesh->err);
+    return FL_OK;
+}
+
 int fl_hmatrix_near_info(fl_hmatrix H, int64_t* info) {
     if (!H || !info) return FL_EINVAL;
     info[0] = H->hn.ntiles;
@@ -831,21 +902,28 @@ namespace {
 // back to `st`; on `st` itself when side is null), the upward pass, couplings and downward
 // pass on `st`, then the leaf expansion, which adds the far field into y after the join.
 // Returns the launch count, or -1.
-int hm_enqueue(fl_hm* H, const double* x_dev, double* y_dev, cudaStream_t st, cudaStream_t side) {
+// far_only: the upward pass, couplings and downward pass alone (H->yh then holds, per node, the far
+// field of x expanded in the node's Chebyshev basis); y_dev and side are not used.
+int hm_enqueue(fl_hm* H, const double* x_dev, double* y_dev, cudaStream_t st, cudaStream_t side,
+               bool far_only) {
     const ClusterPlan& C = H->plan;
     const int64_t n = C.n;
     const int md = H->md, nn = C.nodes;
     int launches = 0;
+    if (far_only) side = nullptr;
     if (side) {
         if (cudaEventRecord(H->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(side, H->ev_fork, 0) != cudaSuccess)
             return -1;
     }
     cudaStream_t ns = side ? side : st;
-    near_spmv_kernel<<<blocks_for(n * 32, 256), 256, 0, ns>>>(n, H->nz_ptr, H->nz_col, H->nz_val, x_dev, y_dev);
+    if (!far_only) {
+        near_spmv_kernel<<<blocks_for(n * 32, 256), 256, 0, ns>>>(n, H->nz_ptr, H->nz_col, H->nz_val, x_dev, y_dev);
+        ++launches;
+    }
     if (side && cudaEventRecord(H->ev_join, side) != cudaSuccess) return -1;
     up_leaf_kernel<<<blocks_for((int64_t)H->nleaves * md, 128), 128, 0, st>>>(H->nleaves, md, H->leaves, H->lo_d,
                                                                              H->hi_d, H->perm, H->coef, x_dev, H->xh);
-    launches += 2;
+    launches += 1;
     // upward pass: the subtrees below the split level, one block each, then the top in one block
     if (H->nsub > 0) {
         if (md == 16) up_sub_kernel<16><<<H->nsub, 256, 0, st>>>(H->sub_levels, md, H->sub_off, H->sub_nodes, H->son_d, H->shift, H->xh);
@@ -884,8 +962,10 @@ int hm_enqueue(fl_hm* H, const double* x_dev, double* y_dev, cudaStream_t st, cu
         ++launches;
     }
     if (side && cudaStreamWaitEvent(st, H->ev_join, 0) != cudaSuccess) return -1;
-    down_leaf_kernel<<<blocks_for(n, 128), 128, 0, st>>>(n, md, H->perm, H->leaf_of, H->coef, H->yh, -H->C, y_dev);
-    ++launches;
+    if (!far_only) {
+        down_leaf_kernel<<<blocks_for(n, 128), 128, 0, st>>>(n, md, H->perm, H->leaf_of, H->coef, H->yh, -H->C, y_dev);
+        ++launches;
+    }
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 }  // namespace
@@ -923,7 +1003,7 @@ int fl_hmatrix_matvec(fl_hmatrix H, const double* x_dev, double* y_dev, void* st
             cudaGraph_t graph = nullptr;
             if (cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                 return hm_fail(H, FL_ECUDA, "graph capture");
-            launches = fl::hm_enqueue(H, x_dev, y_dev, H->cap, H->side_st);
+            launches = fl::hm_enqueue(H, x_dev, y_dev, H->cap, H->side_st, false);
             const cudaError_t ec = cudaStreamEndCapture(H->cap, &graph);
             if (launches < 0 || ec != cudaSuccess || !graph) {
                 if (graph) cudaGraphDestroy(graph);
@@ -946,7 +1026,7 @@ int fl_hmatrix_matvec(fl_hmatrix H, const double* x_dev, double* y_dev, void* st
         }
     } else {
         // inside a caller's capture, or more (x, y) pairs than kept graphs: launches on `st`
-        launches = fl::hm_enqueue(H, x_dev, y_dev, st, nullptr);
+        launches = fl::hm_enqueue(H, x_dev, y_dev, st, nullptr, false);
         if (launches < 0) return hm_fail(H, FL_ECUDA, "H-matrix product launch");
     }
     count_launch(launches);

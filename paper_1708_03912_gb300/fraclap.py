@@ -26,7 +26,8 @@ EXPORTS = ["fl_default_options", "fl_create", "fl_create_sector", "fl_destroy", 
            "fl_assemble", "fl_tune_assemble", "fl_set_far_variant", "fl_assemble_nearfield_csr", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
            "fl_heat_matrix", "fl_mass_apply", "fl_strong_form", "fl_br_indicators", "fl_mark_max", "fl_refine",
            "fl_cluster_plan", "fl_near_region_plan", "fl_hmatrix_create", "fl_hmatrix_set_near",
-           "fl_hmatrix_matvec", "fl_hmatrix_solve", "fl_hmatrix_info", "fl_hmatrix_assemble_near", "fl_hmatrix_near_info", "fl_hmatrix_get_near", "fl_hmatrix_last_error", "fl_hmatrix_destroy", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
+           "fl_hmatrix_matvec", "fl_hmatrix_solve", "fl_hmatrix_info", "fl_hmatrix_assemble_near", "fl_hmatrix_near_info", "fl_hmatrix_get_near",
+           "fl_hmatrix_strong_form", "fl_hmatrix_br_indicators", "fl_hmatrix_last_error", "fl_hmatrix_destroy", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
            "fl_matvec_f32_static",
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
            "fl_tune_batch", "fl_tune_matvec", "fl_tune_record", "fl_tune_lookup", "fl_tune_clear", "fl_tune_count", "fl_tune_save",
@@ -166,6 +167,10 @@ def lib():
     L.fl_hmatrix_near_info.restype = ci
     L.fl_hmatrix_get_near.argtypes = [vp, ctypes.POINTER(i64), vp, vp, vp, vp]
     L.fl_hmatrix_get_near.restype = ci
+    L.fl_hmatrix_strong_form.argtypes = [vp, vp, ci, ci, ci, vp, vp]
+    L.fl_hmatrix_strong_form.restype = ci
+    L.fl_hmatrix_br_indicators.argtypes = [vp, vp, vp, ci, ci, ci, vp, vp, vp]
+    L.fl_hmatrix_br_indicators.restype = ci
     L.fl_hmatrix_last_error.argtypes = [vp]
     L.fl_hmatrix_last_error.restype = ctypes.c_char_p
     L.fl_hmatrix_destroy.argtypes = [vp]
@@ -497,6 +502,7 @@ class HMatrix:
         self.hm = ctypes.c_void_p()
         _check(lib().fl_hmatrix_create(h, s, m, eta, leaf, ctypes.byref(self.hm), _stream(stream)), h)
         self.n = fl_num_dofs(h, s)
+        self.n_cells = fl_get_stats(h, s)["n_cells"]
 
     def _check(self, r):
         if r != FL_OK:
@@ -522,6 +528,24 @@ class HMatrix:
         self._check(lib().fl_hmatrix_get_near(self.hm, ctypes.byref(nnz), _ptr(rowptr), _ptr(col), _ptr(val),
                                               _stream(stream)))
         return rowptr, col[: nnz.value], val[: nnz.value]
+
+    def strong_form(self, u, k_cell=3, k_edge=4, k_near=16, stream=None):
+        """(-Delta)^s u_h by the cluster method at the cell-rule points: [cells, k_cell^2] tensor."""
+        import torch
+
+        S = torch.empty(self.n_cells, k_cell * k_cell, dtype=torch.float64, device=u.device)
+        self._check(lib().fl_hmatrix_strong_form(self.hm, _ptr(u), k_cell, k_edge, k_near, _ptr(S), _stream(stream)))
+        return S
+
+    def br_indicators(self, u, f=None, k_cell=3, k_edge=4, k_near=16, stream=None):
+        """(eta [n], S [cells, k_cell^2]) with the cluster method's strong form."""
+        import torch
+
+        S = torch.empty(self.n_cells, k_cell * k_cell, dtype=torch.float64, device=u.device)
+        eta = torch.empty(self.n, dtype=torch.float64, device=u.device)
+        self._check(lib().fl_hmatrix_br_indicators(self.hm, _ptr(u), _ptr(f) if f is not None else None, k_cell,
+                                                   k_edge, k_near, _ptr(eta), _ptr(S), _stream(stream)))
+        return eta, S
 
     def near_info(self):
         v = (ctypes.c_int64 * 3)()

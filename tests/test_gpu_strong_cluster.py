@@ -1,0 +1,95 @@
+"""GPU parity of the strong form by the cluster method (Section 6) against the oracle's
+restatement (oracle.cluster.strong_form_cluster: near partners by Lemma 4.1, admissible ones by
+Chebyshev interpolation at the point), and against the direct evaluation as the order grows."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import OracleMesh  # noqa: E402
+from oracle import adaptive as oad  # noqa: E402
+from oracle.cluster import strong_form_cluster  # noqa: E402
+from paper_1708_03912_gb300 import fraclap as F  # noqa: E402
+from paper_1708_03912_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+# the near part is Lemma 4.1's sum (double-word far facets, float64 near ones: 2^-40 of the sum
+# of the terms' absolute values, as for the direct form); the far part is a float64 sum of m^4
+# products per point on both sides
+TOL = 2.0 ** -40
+
+
+def _u(mesh_or_n, s):
+    om = mesh_or_n
+    vod, _ = om.dofs(s)
+    X = om.V[vod]
+    return np.cos(1.3 * X[:, 0]) * (1.0 - 0.4 * X[:, 1] ** 2) + 0.2 * X[:, 0] * X[:, 1]
+
+
+@pytest.mark.parametrize("s", [0.25, 0.75])
+def test_cluster_strong_form_matches_oracle(s):
+    V, T = synth.disc(5, 2.0)
+    om = OracleMesh(V, T)
+    u = _u(om, s)
+    m, eta, leaf = 3, 1.0, 8
+    So = strong_form_cluster(om, s, u, m=m, eta=eta, leaf=leaf)
+    _, size = oad.strong_form(om, s, u, with_abs=True)
+    mesh = F.Mesh(V, T)
+    H = F.HMatrix(mesh.h, s, m=m, eta=eta, leaf=leaf)
+    Sg = H.strong_form(torch.tensor(u, device="cuda")).cpu().numpy()
+    err = float(np.max(np.abs(Sg - So) / size))
+    print(f"s {s}: cluster strong form vs oracle {err:.2e} of the terms' size")
+    assert err <= TOL
+    # the same u again: the same bits (fixed summation orders)
+    Sg2 = H.strong_form(torch.tensor(u, device="cuda")).cpu().numpy()
+    assert np.array_equal(Sg, Sg2)
+    H.close()
+    mesh.close()
+
+
+def test_cluster_strong_form_converges_to_direct():
+    # L-shape level 3 (19188 cells): the cluster form against the direct one (fl_strong_form) for
+    # Chebyshev orders 2..6, leaves of 32, eta = 1; the indicators from it against the direct ones
+    V, T = synth.lshape(0.25, 3)
+    s = 0.5
+    mesh = F.Mesh(V, T)
+    A = mesh.assemble(s, "fp64")
+    b = mesh.load_vector(s)
+    u, _ = mesh.solve(A, b, tol=1e-10)
+    Sd = mesh.strong_form(s, u)
+    scale = float(Sd.abs().max())
+    errs = []
+    for m in (2, 3, 4, 5, 6):
+        H = F.HMatrix(mesh.h, s, m=m, eta=1.0, leaf=32)
+        Sc = H.strong_form(u)
+        errs.append(float((Sc - Sd).abs().max()) / scale)
+        if m == 6:
+            eta_c, _ = H.br_indicators(u)
+        H.close()
+    print("cluster strong form vs direct, m = 2..6:", errs)
+    assert all(b_ < a for a, b_ in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-6
+    eta_d = mesh.br_indicators(s, u)
+    rel = float(((eta_c - eta_d).abs() / eta_d.abs().max()).max())
+    print(f"indicators m = 6 vs direct: {rel:.2e}")
+    assert rel < 1e-5
+    mesh.close()
+
+
+def test_cluster_strong_form_errors():
+    V, T = synth.interval(16)
+    mesh = F.Mesh(V, T)
+    H = F.HMatrix(mesh.h, 0.5, m=3, leaf=4)
+    u = torch.ones(mesh.num_dofs(0.5), dtype=torch.float64, device="cuda")
+    with pytest.raises(F.FlError):
+        H.strong_form(u)  # 1D
+    H.close()
+    mesh.close()
+    V, T = synth.disc(4)
+    mesh = F.Mesh(V, T)
+    H = F.HMatrix(mesh.h, 0.3, m=3, leaf=4)
+    with pytest.raises(F.FlError):
+        H.strong_form(torch.ones(mesh.num_dofs(0.3), dtype=torch.float64, device="cuda"))  # s not a quarter
+    H.close()
+    mesh.close()
