@@ -39,6 +39,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -793,32 +794,41 @@ int ensure_sf_topology(fl_ctx* h, int pi, cudaStream_t st) {
             c2f_local[K * 2 + 1] = fid[P.C[K * 2 + 1]];
         }
     } else {
-        std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> edges;  // sorted key -> (cell, local edge)
+        // (edge key, cell, local edge) sorted: the cells of an edge are adjacent, lower cell first
+        struct Ent {
+            uint64_t key;
+            int K, j;
+        };
+        std::vector<Ent> ent((size_t)nc * 3);
         for (int64_t K = 0; K < nc; ++K)
             for (int j = 0; j < 3; ++j) {
                 const int a = P.C[K * 3 + j], b = P.C[K * 3 + (j + 1) % 3];
-                edges[{std::min(a, b), std::max(a, b)}].push_back({(int)K, j});
+                ent[(size_t)K * 3 + j] = {((uint64_t)std::min(a, b) << 32) | (uint32_t)std::max(a, b), (int)K, j};
             }
-        std::vector<std::pair<int, int>> order_int, order_bnd;  // (first cell, local edge) by cell order
-        for (auto& kv : edges) {
-            auto& L = kv.second;
-            std::sort(L.begin(), L.end());
-            if (L.size() > 2) return set_err(h, FL_EINVAL, "non-conforming mesh: an edge in more than two cells");
+        std::sort(ent.begin(), ent.end(), [](const Ent& x, const Ent& y) {
+            return x.key < y.key || (x.key == y.key && (x.K < y.K || (x.K == y.K && x.j < y.j)));
+        });
+        // per edge: its first entry and its size; numbering: interior facets by (K+, local edge),
+        // then boundary facets the same way
+        std::vector<std::pair<std::pair<int, int>, size_t>> lst[2];
+        for (size_t i = 0; i < ent.size();) {
+            size_t e = i + 1;
+            while (e < ent.size() && ent[e].key == ent[i].key) ++e;
+            if (e - i > 2) return set_err(h, FL_EINVAL, "non-conforming mesh: an edge in more than two cells");
+            lst[e - i == 2 ? 0 : 1].push_back({{ent[i].K, ent[i].j}, i});
+            i = e;
         }
-        // deterministic numbering: interior facets by (K+, local edge), then boundary facets
         for (int pass = 0; pass < 2; ++pass) {
-            std::vector<std::pair<std::pair<int, int>, std::pair<int, int>>> lst;
-            for (auto& kv : edges)
-                if ((kv.second.size() == 2) == (pass == 0)) lst.push_back({kv.second[0], kv.first});
-            std::sort(lst.begin(), lst.end());
-            for (auto& it : lst) {
-                const auto& L = edges[it.second];
-                const int K = L[0].first, j = L[0].second;
+            std::sort(lst[pass].begin(), lst[pass].end());
+            for (const auto& it : lst[pass]) {
+                const size_t i0 = it.second;
+                const bool two = pass == 0;
+                const int K = ent[i0].K, j = ent[i0].j;
                 Fac f{};
                 f.a = P.C[(int64_t)K * 3 + j];
                 f.b = P.C[(int64_t)K * 3 + (j + 1) % 3];
                 f.kp = K;
-                f.km = L.size() == 2 ? L[1].first : -1;
+                f.km = two ? ent[i0 + 1].K : -1;
                 const double ex = P.V[2 * f.b] - P.V[2 * f.a], ey = P.V[2 * f.b + 1] - P.V[2 * f.a + 1];
                 f.len = std::hypot(ex, ey);
                 // counter-clockwise cells: the outward normal is the edge vector turned clockwise
@@ -826,7 +836,8 @@ int ensure_sf_topology(fl_ctx* h, int pi, cudaStream_t st) {
                 f.n[1] = -ex / f.len;
                 const int id = (int)F.size();
                 F.push_back(f);
-                for (const auto& cj : L) c2f_local[(int64_t)cj.first * 3 + cj.second] = id;
+                c2f_local[(int64_t)K * 3 + j] = id;
+                if (two) c2f_local[(int64_t)ent[i0 + 1].K * 3 + ent[i0 + 1].j] = id;
             }
         }
     }
@@ -1162,38 +1173,62 @@ int plan_hsf(const Plan& P, const ClusterPlan& C, const std::vector<int>& c2f, i
     for (size_t b = 0; b + 1 < C.near.size(); b += 2) partners[C.near[b]].push_back(C.near[b + 1]);
     Q.gbits.assign((size_t)G * Q.words, 0u);
     Q.gf_ptr.assign(G + 1, 0);
-    std::vector<int64_t> cmark(nc, -1), fmark(nfac, -1);
-    std::vector<int> fl;
-    for (int g = 0; g < G; ++g) {
-        uint32_t* bits = &Q.gbits[(size_t)g * Q.words];
-        fl.clear();
-        if (Q.gnode[g] < 0) {
-            for (int l = 0; l < nl; ++l) bits[l >> 5] |= 1u << (l & 31);
-            for (int64_t e = 0; e < nfac; ++e) fl.push_back((int)e);
-        } else {
-            for (int tau : partners[Q.gnode[g]]) {
-                const int l = lidx[tau];
-                bits[l >> 5] |= 1u << (l & 31);
-                for (int pp = C.lo[tau]; pp < C.hi[tau]; ++pp) {
-                    const int v = P.vod[C.perm[pp]];
-                    for (int r = P.v2c_ptr[v]; r < P.v2c_ptr[v + 1]; ++r) {
-                        const int K = P.v2c[r];
-                        if (cmark[K] == g) continue;
-                        cmark[K] = g;
-                        for (int j = 0; j < 3; ++j) {
-                            const int e = c2f[(int64_t)K * 3 + j];
-                            if (fmark[e] == g) continue;
-                            fmark[e] = g;
-                            fl.push_back(e);
+    // in parallel over ranges of groups, the lists concatenated in group order
+    const int nthr = (int)std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
+    const int gchunk = (G + nthr - 1) / nthr;
+    std::vector<std::vector<int>> lists(nthr);
+    std::vector<std::vector<int64_t>> lens(nthr);
+    auto work = [&](int th) {
+        const int g0 = th * gchunk, g1 = std::min(G, g0 + gchunk);
+        if (g0 >= g1) return;
+        std::vector<int> cmark(nc, -1), fmark(nfac, -1), fl;
+        for (int g = g0; g < g1; ++g) {
+            uint32_t* bits = &Q.gbits[(size_t)g * Q.words];
+            fl.clear();
+            if (Q.gnode[g] < 0) {
+                for (int l = 0; l < nl; ++l) bits[l >> 5] |= 1u << (l & 31);
+                for (int64_t e = 0; e < nfac; ++e) fl.push_back((int)e);
+            } else {
+                for (int tau : partners[Q.gnode[g]]) {
+                    const int l = lidx[tau];
+                    bits[l >> 5] |= 1u << (l & 31);
+                    for (int pp = C.lo[tau]; pp < C.hi[tau]; ++pp) {
+                        const int v = P.vod[C.perm[pp]];
+                        for (int r = P.v2c_ptr[v]; r < P.v2c_ptr[v + 1]; ++r) {
+                            const int K = P.v2c[r];
+                            if (cmark[K] == g) continue;
+                            cmark[K] = g;
+                            for (int j = 0; j < 3; ++j) {
+                                const int e = c2f[(int64_t)K * 3 + j];
+                                if (fmark[e] == g) continue;
+                                fmark[e] = g;
+                                fl.push_back(e);
+                            }
                         }
                     }
                 }
+                std::sort(fl.begin(), fl.end());
             }
-            std::sort(fl.begin(), fl.end());
+            lists[th].insert(lists[th].end(), fl.begin(), fl.end());
+            lens[th].push_back((int64_t)fl.size());
         }
-        Q.gf_fac.insert(Q.gf_fac.end(), fl.begin(), fl.end());
-        Q.gf_ptr[g + 1] = (int64_t)Q.gf_fac.size();
-        Q.maxf = std::max<int64_t>(Q.maxf, (int64_t)fl.size());
+    };
+    {
+        std::vector<std::thread> th;
+        for (int t = 1; t < nthr; ++t) th.emplace_back(work, t);
+        work(0);
+        for (auto& x : th) x.join();
+    }
+    {
+        int g = 0;
+        for (int t = 0; t < nthr; ++t) {
+            Q.gf_fac.insert(Q.gf_fac.end(), lists[t].begin(), lists[t].end());
+            for (int64_t L : lens[t]) {
+                Q.gf_ptr[g + 1] = Q.gf_ptr[g] + L;
+                Q.maxf = std::max<int64_t>(Q.maxf, L);
+                ++g;
+            }
+        }
     }
     // far-kernel blocks: (group, 128 points, facet chunk); partial sums per group: points x chunks
     Q.gch.resize(G);

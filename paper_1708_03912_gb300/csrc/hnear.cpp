@@ -19,12 +19,37 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
 #include "cluster.h"
 
 namespace fl {
+namespace {
+
+int hw_threads() { return (int)std::max(1u, std::min(std::thread::hardware_concurrency(), 32u)); }
+
+template <typename Fn>
+void run_threads(int nthr, Fn fn) {
+    std::vector<std::thread> th;
+    for (int t = 1; t < nthr; ++t) th.emplace_back(fn, t);
+    fn(0);
+    for (auto& x : th) x.join();
+}
+
+// fn(lo, hi) over contiguous ranges of [0, n), one per thread
+template <typename Fn>
+void parallel_ranges(int64_t n, Fn fn) {
+    const int nthr = hw_threads();
+    const int64_t chunk = (n + nthr - 1) / nthr;
+    run_threads(nthr, [&](int t) {
+        const int64_t lo = (int64_t)t * chunk, hi = std::min(n, lo + chunk);
+        if (lo < hi) fn(lo, hi);
+    });
+}
+
+}  // namespace
 
 int plan_hnear(const Plan& P, const ClusterPlan& C, HNearPlan& Q, std::string& err) {
     Q = HNearPlan();
@@ -55,12 +80,17 @@ int plan_hnear(const Plan& P, const ClusterPlan& C, HNearPlan& Q, std::string& e
         for (int I : A)
             for (int J : B) rows[std::min(I, J)].push_back(std::max(I, J));
     }
+    parallel_ranges(nblk, [&](int64_t lo, int64_t hi) {
+        for (int64_t I = lo; I < hi; ++I) {
+            std::vector<int>& r = rows[I];
+            std::sort(r.begin(), r.end());
+            r.erase(std::unique(r.begin(), r.end()), r.end());
+        }
+    });
     Q.trow_ptr.assign(nblk + 1, 0);
     Q.toff.assign(1, 0);
     for (int64_t I = 0; I < nblk; ++I) {
         std::vector<int>& r = rows[I];
-        std::sort(r.begin(), r.end());
-        r.erase(std::unique(r.begin(), r.end()), r.end());
         const int64_t nI = P.L_ptr[I + 1] - P.L_ptr[I];
         for (int J : r) {
             Q.tiles.push_back((int)I);
@@ -97,38 +127,46 @@ int plan_hnear(const Plan& P, const ClusterPlan& C, HNearPlan& Q, std::string& e
             }
         const int64_t nt = (int64_t)Q.tiles.size() / 2;
         Q.rowmask.assign(nt, 0u);
-        std::vector<int> U;
-        int lastJ = -1;
-        for (int64_t t = 0; t < nt; ++t) {
-            const int I = Q.tiles[2 * t], J = Q.tiles[2 * t + 1];
-            if (J != lastJ) {  // leaves of block J's cells
+        // leaves of every block's cells
+        std::vector<int> bl_ptr(nblk + 1, 0), bl;
+        {
+            std::vector<int> U;
+            for (int64_t J = 0; J < nblk; ++J) {
                 U.clear();
-                for (int64_t k = (int64_t)J * TILE; k < std::min(nc, (int64_t)(J + 1) * TILE); ++k)
+                for (int64_t k = J * TILE; k < std::min(nc, (J + 1) * TILE); ++k)
                     for (int a = 0; a < m; ++a)
                         if (cl[k * m + a] >= 0) U.push_back(cl[k * m + a]);
                 std::sort(U.begin(), U.end());
                 U.erase(std::unique(U.begin(), U.end()), U.end());
-                lastJ = J;
+                bl.insert(bl.end(), U.begin(), U.end());
+                bl_ptr[J + 1] = (int)bl.size();
             }
-            uint32_t mask = 0;
-            for (int kk = 0; kk < TILE; ++kk) {
-                const int64_t k = (int64_t)I * TILE + kk;
-                if (k >= nc) break;
-                bool need = false;
-                for (int a = 0; a < m && !need; ++a) {
-                    const int la = cl[k * m + a];
-                    if (la < 0) continue;
-                    const uint64_t* row = &adj[(size_t)la * words];
-                    for (int lb : U)
-                        if ((row[lb / 64] >> (lb % 64)) & 1ull) {
-                            need = true;
-                            break;
-                        }
-                }
-                if (need) mask |= 1u << kk;
-            }
-            Q.rowmask[t] = mask;
         }
+        parallel_ranges(nt, [&](int64_t t0, int64_t t1) {
+            for (int64_t t = t0; t < t1; ++t) {
+                const int I = Q.tiles[2 * t], J = Q.tiles[2 * t + 1];
+                uint32_t mask = 0;
+                for (int kk = 0; kk < TILE; ++kk) {
+                    const int64_t k = (int64_t)I * TILE + kk;
+                    if (k >= nc) break;
+                    bool need = false;
+                    for (int a = 0; a < m && !need; ++a) {
+                        const int la = cl[k * m + a];
+                        if (la < 0) continue;
+                        const uint64_t* row = &adj[(size_t)la * words];
+                        for (int q = bl_ptr[J]; q < bl_ptr[J + 1]; ++q) {
+                            const int lb = bl[q];
+                            if ((row[lb / 64] >> (lb % 64)) & 1ull) {
+                                need = true;
+                                break;
+                            }
+                        }
+                    }
+                    if (need) mask |= 1u << kk;
+                }
+                Q.rowmask[t] = mask;
+            }
+        });
     }
     // ---- facet table: the boundary facets of Omega (ids 0 .. nf-1, as in the mesh plan), then
     // one oriented copy per (internal cell M, facet e of M) with the normal pointing into M
@@ -207,54 +245,89 @@ int plan_hnear(const Plan& P, const ClusterPlan& C, HNearPlan& Q, std::string& e
     // ---- per cell with DOFs: the facets of the boundary of N(K) and their classes
     // (2 / 3: shares two / one vertex with K, only boundary facets of Omega can; 1: a vertex
     // is a mesh neighbour of a vertex of K; 0: the rest)
-    Q.ef_ptr.assign(nc + 1, 0);
-    std::vector<int64_t> mark0(nv, -1), mark1(nv, -1);
-    std::vector<std::pair<int, int>> lst;
-    for (int64_t k = 0; k < nc; ++k) {
-        if (P.hasdof[k]) {
-            const int Ko = P.perm[k];
-            const int* c = &P.C[(int64_t)Ko * m];
-            for (int a = 0; a < m; ++a) {
-                mark0[c[a]] = k;
-                mark1[c[a]] = k;
-                for (int q = P.nbr_ptr[c[a]]; q < P.nbr_ptr[c[a] + 1]; ++q) mark1[P.nbr[q]] = k;
-            }
-            const int* N0 = &P.ex_idx[P.ex_ptr[k]];
-            const int* N1 = &P.ex_idx[P.ex_ptr[k + 1]];
-            lst.clear();
-            for (const int* it = N0; it != N1; ++it) {
-                const int M = *it;
-                for (int e = 0; e < m; ++e) {
-                    const int64_t slot = (int64_t)m * M + e;
-                    const int o = nbc[slot];
-                    if (o >= 0 && std::binary_search(N0, N1, o)) continue;  // inside N(K)
-                    const int f = fid[slot];
-                    int sh = 0, n1 = 0;
-                    for (int x = 0; x < d; ++x) {
-                        const int v = Q.F[(int64_t)f * d + x];
-                        sh += mark0[v] == k;
-                        n1 += mark1[v] == k;
-                    }
-                    int cls;
-                    if (sh > 0) {
-                        if (o >= 0) {
-                            err = "internal: a facet inside Omega touches K on the boundary of N(K)";
-                            return FL_EINVAL;
-                        }
-                        cls = (d == 1 || sh == 2) ? 2 : 3;
-                    } else {
-                        cls = n1 > 0 ? 1 : 0;
-                    }
-                    lst.push_back({f, cls});
+    // in parallel over ranges of cells; the ranges' lists are concatenated in cell order
+    const int nthr = hw_threads();
+    const int64_t chunk = (nc + nthr - 1) / nthr;
+    struct Part {
+        std::vector<int> cnt, fac, cls;
+        std::string err;
+    };
+    std::vector<Part> parts(nthr);
+    auto work = [&](int th) {
+        Part& o = parts[th];
+        const int64_t k0 = (int64_t)th * chunk, k1 = std::min(nc, k0 + chunk);
+        if (k0 >= k1) return;
+        std::vector<int64_t> mark0(nv, -1), mark1(nv, -1);
+        std::vector<std::pair<int, int>> lst;
+        for (int64_t k = k0; k < k1; ++k) {
+            int c0 = 0;
+            if (P.hasdof[k]) {
+                const int Ko = P.perm[k];
+                const int* c = &P.C[(int64_t)Ko * m];
+                for (int a = 0; a < m; ++a) {
+                    mark0[c[a]] = k;
+                    mark1[c[a]] = k;
+                    for (int q = P.nbr_ptr[c[a]]; q < P.nbr_ptr[c[a] + 1]; ++q) mark1[P.nbr[q]] = k;
                 }
+                const int* N0 = &P.ex_idx[P.ex_ptr[k]];
+                const int* N1 = &P.ex_idx[P.ex_ptr[k + 1]];
+                lst.clear();
+                for (const int* it = N0; it != N1; ++it) {
+                    const int M = *it;
+                    for (int e = 0; e < m; ++e) {
+                        const int64_t slot = (int64_t)m * M + e;
+                        const int ob = nbc[slot];
+                        if (ob >= 0 && std::binary_search(N0, N1, ob)) continue;  // inside N(K)
+                        const int f = fid[slot];
+                        int sh = 0, n1 = 0;
+                        for (int x = 0; x < d; ++x) {
+                            const int v = Q.F[(int64_t)f * d + x];
+                            sh += mark0[v] == k;
+                            n1 += mark1[v] == k;
+                        }
+                        int cls;
+                        if (sh > 0) {
+                            if (ob >= 0) {
+                                o.err = "internal: a facet inside Omega touches K on the boundary of N(K)";
+                                return;
+                            }
+                            cls = (d == 1 || sh == 2) ? 2 : 3;
+                        } else {
+                            cls = n1 > 0 ? 1 : 0;
+                        }
+                        lst.push_back({f, cls});
+                    }
+                }
+                std::sort(lst.begin(), lst.end());
+                for (const auto& pr : lst) {
+                    o.fac.push_back(pr.first);
+                    o.cls.push_back(pr.second);
+                }
+                c0 = (int)lst.size();
             }
-            std::sort(lst.begin(), lst.end());
-            for (const auto& pr : lst) {
-                Q.ef_fac.push_back(pr.first);
-                Q.ef_cls.push_back(pr.second);
-            }
+            o.cnt.push_back(c0);
         }
-        Q.ef_ptr[k + 1] = (int)Q.ef_fac.size();
+    };
+    run_threads(nthr, work);
+    for (const Part& o : parts)
+        if (!o.err.empty()) {
+            err = o.err;
+            return FL_EINVAL;
+        }
+    Q.ef_ptr.assign(nc + 1, 0);
+    {
+        int64_t k = 0;
+        for (const Part& o : parts)
+            for (int c : o.cnt) {
+                Q.ef_ptr[k + 1] = Q.ef_ptr[k] + c;
+                ++k;
+            }
+    }
+    Q.ef_fac.reserve(Q.ef_ptr[nc]);
+    Q.ef_cls.reserve(Q.ef_ptr[nc]);
+    for (const Part& o : parts) {
+        Q.ef_fac.insert(Q.ef_fac.end(), o.fac.begin(), o.fac.end());
+        Q.ef_cls.insert(Q.ef_cls.end(), o.cls.begin(), o.cls.end());
     }
     return FL_OK;
 }

@@ -1084,15 +1084,24 @@ class Mesh:
 
 
 def adaptive_loop(vertices, cells, s, steps, theta=0.8, f_nodal=None, tol=1e-10, k_cell=3, k_edge=4, k_near=16,
-                  max_dofs=None, dof_mode="interior", timings=False):
+                  max_dofs=None, dof_mode="interior", timings=False, cluster=None):
     """The adaptive loop of Section 7.  Per step: assemble A^s (float64) and b, solve A u = b
     (Jacobi-PCG), compute the BR indicators, mark with the maximum strategy (threshold theta) and
     refine the marked patches (newest-vertex bisection with closure).  f_nodal: None (f = 1) or
     a function of the vertex coordinates [nv, d] returning nodal values.  Stops after `steps`
     solves or once n exceeds max_dofs.  Returns one dict per step (host arrays: vertices,
     cells, u, eta, dof_marks, cell_marks; n, iterations; with timings, the milliseconds of
-    assembly, solve and indicators by CUDA events)."""
+    assembly, solve and indicators by CUDA events).
+
+    cluster: None (dense matrix, direct strong form) or a dict of HMatrix parameters (m, eta,
+    leaf): every step then uses the cluster method of Section 6 throughout -- the near field by
+    local computations, Jacobi-PCG on the H-matrix, the indicators from the cluster strong form --
+    and forms no dense matrix."""
     import torch
+
+    if cluster is not None:
+        return _adaptive_loop_cluster(vertices, cells, s, steps, theta, f_nodal, tol, k_cell, k_edge, k_near,
+                                      max_dofs, dof_mode, timings, dict(cluster))
 
     V = np.asarray(vertices, dtype=np.float64)
     C = np.asarray(cells, dtype=np.int32)
@@ -1126,6 +1135,55 @@ def adaptive_loop(vertices, cells, s, steps, theta=0.8, f_nodal=None, tol=1e-10,
                              "indicators": ev[2].elapsed_time(ev[3])}
             out.append(rec)
         finally:
+            mesh.close()
+        if max_dofs is not None and n >= max_dofs:
+            break
+        V, C = fl_refine(V, C, rec["cell_marks"])
+    return out
+
+
+def _adaptive_loop_cluster(vertices, cells, s, steps, theta, f_nodal, tol, k_cell, k_edge, k_near, max_dofs, dof_mode,
+                           timings, cp):
+    import torch
+
+    V = np.asarray(vertices, dtype=np.float64)
+    C = np.asarray(cells, dtype=np.int32)
+    out = []
+    for _ in range(steps):
+        mesh = Mesh(V, C, dof_mode=dof_mode)
+        H = None
+        try:
+            n = mesh.num_dofs(s)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if timings else None
+            fv = None
+            if f_nodal is not None:
+                fv = torch.as_tensor(np.ascontiguousarray(f_nodal(V), dtype=np.float64), device="cuda")
+            if ev:
+                ev[0].record()
+            H = HMatrix(mesh.h, s, m=cp.get("m", 4), eta=cp.get("eta", 1.0), leaf=cp.get("leaf", 32))
+            H.assemble_near()
+            b = mesh.load_vector(s, fv)
+            if ev:
+                ev[1].record()
+            u, info = H.solve(b, tol=tol)
+            if info.status != FL_OK:
+                raise FlError(info.status, "H-matrix solve did not converge")
+            if ev:
+                ev[2].record()
+            eta, _ = H.br_indicators(u, fv, k_cell, k_edge, k_near)
+            if ev:
+                ev[3].record()
+            dm, cm = mesh.mark_max(s, eta, theta)
+            torch.cuda.synchronize()
+            rec = {"vertices": V, "cells": C, "n": n, "u": u.cpu().numpy(), "eta": eta.cpu().numpy(),
+                   "dof_marks": dm.cpu().numpy(), "cell_marks": cm.cpu().numpy(), "iterations": info.iterations}
+            if ev:
+                rec["ms"] = {"assemble": ev[0].elapsed_time(ev[1]), "solve": ev[1].elapsed_time(ev[2]),
+                             "indicators": ev[2].elapsed_time(ev[3])}
+            out.append(rec)
+        finally:
+            if H is not None:
+                H.close()
             mesh.close()
         if max_dofs is not None and n >= max_dofs:
             break

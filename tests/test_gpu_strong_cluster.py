@@ -93,3 +93,28 @@ def test_cluster_strong_form_errors():
         H.strong_form(torch.ones(mesh.num_dofs(0.3), dtype=torch.float64, device="cuda"))  # s not a quarter
     H.close()
     mesh.close()
+
+
+def test_adaptive_loop_with_the_cluster_method():
+    # Section 7's loop on the L-shape from 96 cells with the cluster method throughout (near field by
+    # local computations, H-matrix PCG, cluster strong form; m = 6) against the dense loop: the same
+    # meshes while the indicators' difference stays below the marking threshold's margin, and the
+    # estimator at the last common size within a few per cent
+    from paper_1708_03912_gb300.fraclap import adaptive_loop
+
+    V, T = synth.lshape(0.25, 0)
+    dense = adaptive_loop(V, T, 0.5, 9, theta=0.8)
+    clus = adaptive_loop(V, T, 0.5, 9, theta=0.8, cluster={"m": 6, "eta": 1.0, "leaf": 32})
+    nd = [r["n"] for r in dense]
+    nc = [r["n"] for r in clus]
+    print("dense n", nd, "cluster n", nc)
+    same = 0
+    while same < min(len(nd), len(nc)) and nd[same] == nc[same] and np.array_equal(dense[same]["cells"], clus[same]["cells"]):
+        same += 1
+    assert same >= 4
+    for k in range(same):
+        ed = np.sqrt(np.sum(dense[k]["eta"] ** 2))
+        ec = np.sqrt(np.sum(clus[k]["eta"] ** 2))
+        assert abs(ec - ed) <= 1e-4 * ed, (k, ec, ed)
+        assert np.max(np.abs(clus[k]["u"] - dense[k]["u"])) <= 1e-5 * np.max(np.abs(dense[k]["u"]))
+    assert all(b >= a for a, b in zip(nc, nc[1:]))
