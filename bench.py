@@ -214,7 +214,7 @@ def build_problems(F, synth, m, svals, nrhs, nslices, V):
 # small named workloads for profilers (`--case`): rings, grading exponent, s
 CASES = {"disc25": (25, 1.0, 0.75), "gdisc30": (30, 2.0, 0.75), "gdisc30s5": (30, 2.0, 0.5), "disc10": (10, 1.0, 0.75)}
 # strong-form profiling cases: L-shape level, s
-SF_CASES = {"sf_lshape3": (3, 0.5), "sf_lshape5": (5, 0.5)}
+SF_CASES = {"sf_lshape3": (3, 0.5), "sf_lshape5": (5, 0.5), "hsf_lshape5": (5, 0.5)}
 # dense-product and H-matrix-product profiling cases
 MV_CASES = {"mv_f32_20000": (20000, "f32"), "mv_f64_20000": (20000, "f64"), "mv_f32_35693": (35693, "f32")}
 HM_CASES = {"hm_lshape4": (4, 4)}
@@ -320,16 +320,24 @@ def run_sf_case(args):
     u, _ = m.solve(A, m.load_vector(s), tol=1e-8)
     del A
     S = torch.empty((len(T), 9), dtype=torch.float64, device="cuda")
-    F.fl_strong_form(m.h, s, u, 3, 4, 16, S)
+    H = None
+    if args.case.startswith("hsf"):  # by the cluster method, m = 4, eta = 1, leaves of 32
+        H = F.HMatrix(m.h, s, m=4, eta=1.0, leaf=32)
+        call = lambda: H.strong_form(u, 3, 4, 16)  # noqa: E731
+    else:
+        call = lambda: F.fl_strong_form(m.h, s, u, 3, 4, 16, S)  # noqa: E731
+    call()
     ts = []
     for _ in range(args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        F.fl_strong_form(m.h, s, u, 3, 4, 16, S)
+        call()
         b.record()
         b.synchronize()
         ts.append(a.elapsed_time(b))
     print(f"case {args.case}: cells {len(T)} dofs {u.shape[0]} strong form ms " + " ".join(f"{t:.3f}" for t in ts))
+    if H is not None:
+        H.close()
     m.close()
     return 0
 
