@@ -622,15 +622,18 @@ __global__ void hsf_near_kernel(int64_t npts, int q, const double* __restrict__ 
     double farf = 0.0;
     const int cn = gnode[g];
     if (cn >= 0) {
-        double lx[12], ly[12];
+        double lx[12], ly[12], nx[12], ny[12];
         const double cx = center[2 * (int64_t)cn], cy = center[2 * (int64_t)cn + 1], L = side[cn];
+        for (int k = 0; k < m; ++k) {  // the nodes once (the same values as node by node)
+            nx[k] = hsf_cheb_node(cx, L, m, k);
+            ny[k] = hsf_cheb_node(cy, L, m, k);
+        }
         for (int k = 0; k < m; ++k) {
-            const double xk = hsf_cheb_node(cx, L, m, k), yk = hsf_cheb_node(cy, L, m, k);
             double vx = 1.0, vy = 1.0;
             for (int l = 0; l < m; ++l)
                 if (l != k) {
-                    vx *= (x0 - hsf_cheb_node(cx, L, m, l)) / (xk - hsf_cheb_node(cx, L, m, l));
-                    vy *= (x1 - hsf_cheb_node(cy, L, m, l)) / (yk - hsf_cheb_node(cy, L, m, l));
+                    vx *= (x0 - nx[l]) / (nx[k] - nx[l]);
+                    vy *= (x1 - ny[l]) / (ny[k] - ny[l]);
                 }
             lx[k] = vx;
             ly[k] = vy;
