@@ -16,8 +16,10 @@ def _u(mesh, s):
     return np.cos(1.3 * X[:, 0]) * (1.0 - 0.4 * X[:, 1] ** 2) + 0.2 * X[:, 0] * X[:, 1]
 
 
-def test_no_admissible_pair_is_the_direct_form():
-    V, T = synth.disc(4, 2.0)
+@pytest.mark.parametrize("case", ["disc", "lshape"])
+def test_no_admissible_pair_is_the_direct_form(case):
+    # (the L-shape's 96-cell mesh has corner cells without a DOF vertex)
+    V, T = synth.disc(4, 2.0) if case == "disc" else synth.lshape(0.25, 0)
     m = OracleMesh(V, T)
     s = 0.5
     u = _u(m, s)
