@@ -545,6 +545,8 @@ __global__ void hsf_near_kernel(int64_t npts, int q, const double* __restrict__ 
                                 const int* __restrict__ pgroup, const int* __restrict__ plocal,
                                 const uint32_t* __restrict__ gbits, int words, const int* __restrict__ dof_leaf,
                                 const int* __restrict__ gnode, const int* __restrict__ gp_ptr,
+                                const int64_t* __restrict__ gf_ptr, const int* __restrict__ gf_fac,
+                                const double* __restrict__ cj,
                                 const int* __restrict__ gch, const int64_t* __restrict__ gpo,
                                 const double* __restrict__ part, int m, int md, const double* __restrict__ yh,
                                 const double* __restrict__ center, const double* __restrict__ side, double s,
@@ -566,7 +568,7 @@ __global__ void hsf_near_kernel(int64_t npts, int q, const double* __restrict__ 
     }
     double g0x, g0y;
     hsf_grad(K0, cells, V, dov, u, dof_leaf, bits, g0x, g0y);
-    const double cown = 1.0 / mexp, cnbr = 1.0 / (2.0 * s * mexp), cA = 1.0 / (2.0 * s * mexp);
+    const double cown = 1.0 / mexp, cnbr = 1.0 / (2.0 * s * mexp);
     double near = 0.0;
     for (int j = 0; j < 3; ++j) {
         const int e = c2f[(int64_t)K0 * 3 + j];
@@ -595,19 +597,21 @@ __global__ void hsf_near_kernel(int64_t npts, int q, const double* __restrict__ 
             near += w * (cg * k0 - du * nd * k1 / (2.0 * s));
         }
     }
+    // the other facets through K0's vertices: their jumps from the group's list (ascending facet ids;
+    // a facet absent from it touches no near DOF, its jump is zero)
+    const int64_t fl0 = gf_ptr[g], fl1 = gf_ptr[g + 1];
     for (int j = 0; j < 3; ++j) {
         for (int qq = v2e_ptr[c[j]]; qq < v2e_ptr[c[j] + 1]; ++qq) {
             const int e = v2e[qq];
             if (e == c2f[(int64_t)K0 * 3] || e == c2f[(int64_t)K0 * 3 + 1] || e == c2f[(int64_t)K0 * 3 + 2]) continue;
-            const int kp = fac[4 * e + 2], km = fac[4 * e + 3];
-            double gx, gy;
-            hsf_grad(kp, cells, V, dov, u, dof_leaf, bits, gx, gy);
-            double J = fn[3 * e] * gx + fn[3 * e + 1] * gy;
-            if (km >= 0) {
-                hsf_grad(km, cells, V, dov, u, dof_leaf, bits, gx, gy);
-                J -= fn[3 * e] * gx + fn[3 * e + 1] * gy;
+            int64_t lo = fl0, hi = fl1;
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (gf_fac[mid] < e) lo = mid + 1;
+                else hi = mid;
             }
-            const double cjv = J * cA;
+            if (lo >= fl1 || gf_fac[lo] != e) continue;
+            const double cjv = cj[lo];
             for (int gq = 0; gq < ke; ++gq) {
                 const int64_t i = (int64_t)e * ke + gq;
                 const double dx = x0 - yrec[2 * i], dy = x1 - yrec[2 * i + 1];
@@ -1325,7 +1329,8 @@ int strong_form_cluster(fl_ctx* h, double s, const double* u, int kc, int ke, in
     }
     hsf_near_kernel<<<(unsigned)((npts + 127) / 128), 128, 0, st>>>(
         npts, q, X, lam, t.sf_perm, t.cells, t.V, t.dov, u, t.sf_c2f, t.sf_fac, t.sf_fn, kn, tn, wn, t.sf_v2e_ptr,
-        t.sf_v2e, ke, yrec, we, g.pgroup, g.plocal, g.gbits, g.words, g.dof_leaf, g.gnode, g.gp_ptr, g.gch, g.gpo,
+        t.sf_v2e, ke, yrec, we, g.pgroup, g.plocal, g.gbits, g.words, g.dof_leaf, g.gnode, g.gp_ptr, g.gf_ptr,
+        g.gf_fac, g.cj, g.gch, g.gpo,
         g.part, g.m, g.md, g.yh, g.center, g.side, s, mexp, frac_const(2, s), S);
     count_launch();
     SF_CUDA(h, cudaGetLastError());
