@@ -556,6 +556,19 @@ int fl_hmatrix_get_near(fl_hmatrix H, int64_t* nnz, int32_t* rowptr_dev, int32_t
  */
 int fl_hmatrix_strong_form(fl_hmatrix H, const double* u_dev, int k_cell, int k_edge, int k_near, double* S_dev,
                            void* stream);
+/*
+ * Host only: the plan of fl_hmatrix_strong_form for the partition (s, eta, leaf) and the cell rule
+ * k_cell.  sizes[0..3] receive the points (cells x k_cell^2), the groups, the facet-list entries and
+ * the facets of the strong form's facet table; with non-NULL arrays also pgroup [points] (the group
+ * of point q of internal cell k at k k_cell^2 + q; internal order as in fl_near_region_plan's
+ * cell_perm), gnode [groups] (the group's leaf node as numbered by fl_cluster_plan, -1 for the cells
+ * without a DOF vertex), gf_ptr [groups + 1] and gf_fac [entries] (per group its facets, ascending)
+ * and fac_vert [2 facets] (the facets' end vertices).  2D only (FL_ENOTIMPL).  Errors: FL_EINVAL,
+ * FL_ENOMEM, FL_ENOTIMPL.
+ */
+int fl_strong_form_cluster_plan(fl_handle h, double s, double eta, int leaf, int k_cell, int64_t* sizes,
+                                int32_t* pgroup, int32_t* gnode, int64_t* gf_ptr, int32_t* gf_fac,
+                                int32_t* fac_vert);
 /* The Babuska-Rheinboldt indicators (as fl_br_indicators, f_dev nodal or NULL for f = 1) from the
  * cluster method's strong form; S_dev [cells][k_cell^2] receives the strong form. */
 int fl_hmatrix_br_indicators(fl_hmatrix H, const double* u_dev, const double* f_dev, int k_cell, int k_edge,

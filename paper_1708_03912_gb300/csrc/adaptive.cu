@@ -757,18 +757,18 @@ int upload(fl_ctx* h, X** dst, const std::vector<X>& src, cudaStream_t st) {
 // Facets of the mesh for the strong form: interior facets first (the lower cell id is K+),
 // then boundary facets; cell -> facets in the cell's own order (2D edges v0v1, v1v2, v2v0;
 // 1D left, right end).
-int ensure_sf_topology(fl_ctx* h, int pi, cudaStream_t st) {
-    DevTables& t = h->dev[pi];
-    if (t.sf_ready) return FL_OK;
-    const Plan& P = h->plan[pi];
+struct SfFac {
+    int a, b, kp, km;
+    double n[2], len;
+};
+
+// host part: the facet list and cell -> facets (FL_EINVAL for a non-conforming mesh)
+int sf_build_facets(const Plan& P, std::vector<SfFac>& F, std::vector<int>& c2f_local, std::string& err) {
     const int d = P.dim, nvpc = P.nvpc;
     const int64_t nc = P.nc;
-    struct Fac {
-        int a, b, kp, km;
-        double n[2], len;
-    };
-    std::vector<Fac> F;
-    std::vector<int> c2f_local(nc * nvpc, -1);
+    using Fac = SfFac;
+    F.clear();
+    c2f_local.assign(nc * nvpc, -1);
     if (d == 1) {
         // facet per vertex; K+ = the cell whose right end it is (normal +1)
         std::vector<int> right(P.nv, -1), left(P.nv, -1);
@@ -821,7 +821,10 @@ int ensure_sf_topology(fl_ctx* h, int pi, cudaStream_t st) {
         for (size_t i = 0; i < ent.size();) {
             size_t e = i + 1;
             while (e < ent.size() && ent[e].key == ent[i].key) ++e;
-            if (e - i > 2) return set_err(h, FL_EINVAL, "non-conforming mesh: an edge in more than two cells");
+            if (e - i > 2) {
+                err = "non-conforming mesh: an edge in more than two cells";
+                return FL_EINVAL;
+            }
             lst[e - i == 2 ? 0 : 1].push_back({{ent[i].K, ent[i].j}, i});
             i = e;
         }
@@ -847,6 +850,21 @@ int ensure_sf_topology(fl_ctx* h, int pi, cudaStream_t st) {
                 if (two) c2f_local[(int64_t)ent[i0 + 1].K * 3 + ent[i0 + 1].j] = id;
             }
         }
+    }
+    return FL_OK;
+}
+
+int ensure_sf_topology(fl_ctx* h, int pi, cudaStream_t st) {
+    DevTables& t = h->dev[pi];
+    if (t.sf_ready) return FL_OK;
+    const Plan& P = h->plan[pi];
+    const int d = P.dim;
+    std::vector<SfFac> F;
+    std::vector<int> c2f_local;
+    {
+        std::string err;
+        const int rc = sf_build_facets(P, F, c2f_local, err);
+        if (rc != FL_OK) return set_err(h, rc, err);
     }
     int64_t nint = 0;
     for (const auto& f : F) nint += f.km >= 0;
@@ -1074,6 +1092,20 @@ int strong_form(fl_ctx* h, double s, const double* u, int kc, int ke, int kn, do
         count_launch();
     }
     SF_CUDA(h, cudaGetLastError());
+    return FL_OK;
+}
+
+int sf_facets_host(const Plan& P, std::vector<int>& c2f, std::vector<int>& fac_vert, int64_t* nfac) {
+    std::vector<SfFac> F;
+    std::string err;
+    const int rc = sf_build_facets(P, F, c2f, err);
+    if (rc != FL_OK) return rc;
+    fac_vert.resize(F.size() * 2);
+    for (size_t e = 0; e < F.size(); ++e) {
+        fac_vert[2 * e] = F[e].a;
+        fac_vert[2 * e + 1] = F[e].b;
+    }
+    *nfac = (int64_t)F.size();
     return FL_OK;
 }
 

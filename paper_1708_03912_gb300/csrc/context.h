@@ -240,6 +240,8 @@ int mark_max(fl_ctx* h, double s, const double* eta, double theta, uint8_t* dof_
 // planner, and the evaluation with the plan's device copies (far field: H's yh after the far chain)
 struct HsfDev;
 int sf_topology(fl_ctx* h, int pi, cudaStream_t st, const std::vector<int>** c2f, int64_t* nfac);
+// the same facets on the host alone: cell -> facets, and the two vertices of every facet
+int sf_facets_host(const Plan& P, std::vector<int>& c2f, std::vector<int>& fac_vert, int64_t* nfac);
 int strong_form_cluster(fl_ctx* h, double s, const double* u, int kc, int ke, int kn, const HsfDev& g, double* S,
                         cudaStream_t st);
 int br_from_strong_form(fl_ctx* h, double s, const double* f, int kc, const double* S, double* eta, cudaStream_t st);

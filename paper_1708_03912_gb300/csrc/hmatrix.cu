@@ -553,6 +553,42 @@ int fl_near_region_plan(fl_handle h, double s, double eta, int leaf, int64_t* si
     return FL_OK;
 }
 
+int fl_strong_form_cluster_plan(fl_handle h, double s, double eta, int leaf, int k_cell, int64_t* sizes,
+                                int32_t* pgroup, int32_t* gnode, int64_t* gf_ptr, int32_t* gf_fac,
+                                int32_t* fac_vert) {
+    if (!h || !sizes) return FL_EINVAL;
+    h->err.clear();
+    if (h->sym_K) return sym_unsupported(h, "fl_strong_form_cluster_plan");
+    if (k_cell < 1 || k_cell > 16) return set_err(h, FL_EINVAL, "k_cell in [1, 16]");
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    if (P.dim != 2) return set_err(h, FL_ENOTIMPL, "the cluster strong form is 2D");
+    try {
+        ClusterPlan C;
+        if (build_cluster_plan(P, eta, leaf, C) != FL_OK) return set_err(h, FL_EINVAL, "leaf < 1 or eta < 0");
+        std::vector<int> c2f, fv;
+        int64_t nfac = 0;
+        if (sf_facets_host(P, c2f, fv, &nfac) != FL_OK) return set_err(h, FL_EINVAL, "non-conforming mesh");
+        HsfPlan Q;
+        std::string err;
+        const int rc = plan_hsf(P, C, c2f, nfac, k_cell, Q, err);
+        if (rc != FL_OK) return set_err(h, rc, err);
+        sizes[0] = Q.npts;
+        sizes[1] = Q.groups;
+        sizes[2] = (int64_t)Q.gf_fac.size();
+        sizes[3] = nfac;
+        if (pgroup) std::copy(Q.pgroup.begin(), Q.pgroup.end(), pgroup);
+        if (gnode) std::copy(Q.gnode.begin(), Q.gnode.end(), gnode);
+        if (gf_ptr) std::copy(Q.gf_ptr.begin(), Q.gf_ptr.end(), gf_ptr);
+        if (gf_fac) std::copy(Q.gf_fac.begin(), Q.gf_fac.end(), gf_fac);
+        if (fac_vert) std::copy(fv.begin(), fv.end(), fac_vert);
+    } catch (const std::bad_alloc&) {
+        return set_err(h, FL_ENOMEM, "out of host memory");
+    }
+    return FL_OK;
+}
+
 void fl_hmatrix_destroy(fl_hmatrix H) {
     if (!H) return;
     if (!H->bufs.empty() || !H->graphs.empty()) {
