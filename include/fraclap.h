@@ -594,6 +594,13 @@ int fl_hmatrix_matvec(fl_hmatrix H, const double* x_dev, double* y_dev, void* st
  */
 int fl_hmatrix_solve(fl_hmatrix H, const double* b_dev, double* u_dev, const fl_solve_opts* o, fl_solve_info* info,
                      void* stream);
+/* The same solver for (alpha M + beta A) u = b with M the P1 mass matrix on the DOFs (fl_mass_apply)
+ * and A the H-matrix: the implicit time step of the fractional heat equation (Sections 2 and 5:
+ * (M + dt A^s) u^{k+1} = M u^k + dt F with alpha = 1, beta = dt) without a dense matrix.  The Jacobi
+ * diagonal is alpha M_ii + beta A_ii.  alpha >= 0, beta > 0 (else FL_EINVAL); alpha = 0, beta = 1 is
+ * fl_hmatrix_solve. */
+int fl_hmatrix_solve_shifted(fl_hmatrix H, double alpha, double beta, const double* b_dev, double* u_dev,
+                             const fl_solve_opts* o, fl_solve_info* info, void* stream);
 int fl_hmatrix_info(fl_hmatrix H, int64_t* info);
 const char* fl_hmatrix_last_error(fl_hmatrix H);
 void fl_hmatrix_destroy(fl_hmatrix H);

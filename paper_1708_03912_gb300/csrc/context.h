@@ -245,6 +245,9 @@ int sf_facets_host(const Plan& P, std::vector<int>& c2f, std::vector<int>& fac_v
 int strong_form_cluster(fl_ctx* h, double s, const double* u, int kc, int ke, int kn, const HsfDev& g, double* S,
                         cudaStream_t st);
 int br_from_strong_form(fl_ctx* h, double s, const double* f, int kc, const double* S, double* eta, cudaStream_t st);
+// Y = alpha M X + beta B, M the P1 mass matrix on the DOFs (assemble.cu; Y may be B)
+int mass_apply(fl_ctx* h, double s, int nrhs, double alpha, const double* X, int64_t ldx, double beta, const double* B,
+               int64_t ldb, double* Y, int64_t ldy, cudaStream_t st);
 int refine_mesh(int dim, int64_t nv, const double* V, int64_t nc, const int32_t* C, const uint8_t* marks,
                 int64_t cap_v, int64_t cap_c, double* V_out, int32_t* C_out, int64_t* nv_out, int64_t* nc_out,
                 std::string& err);

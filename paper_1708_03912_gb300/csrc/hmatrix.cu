@@ -69,6 +69,8 @@ struct fl_hm {
     double* Pb = nullptr;  // per admissible pair: K_b xh[tau]
     // Jacobi-PCG with the product (fl_hmatrix_solve), allocated on first use
     double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_dinv = nullptr;
+    bool dinv_ready = false;            // cg_dinv matches the near field and (dinv_alpha, dinv_beta)
+    double dinv_alpha = 0.0, dinv_beta = 1.0;
     double *cg_part = nullptr, *cg_scal = nullptr, *cg_host = nullptr;
     // products captured as CUDA graphs, keyed by (x, y): the near-field product runs on a second
     // stream beside the chain of small far-field launches, and the graph launches them at once
@@ -409,13 +411,25 @@ __global__ void down_leaf_kernel(int64_t n, int md, const int* perm, const int* 
 // ------------------------------------------------------------ Jacobi-PCG --
 constexpr int HCG_BLOCKS = 256, HCG_THREADS = 256;
 
-// dinv[i] = 1 / A_ii from the near field (the diagonal lies in every leaf's own block)
-__global__ void hcg_diag_kernel(int64_t n, const int* ptr, const int* col, const double* val, double* dinv) {
+// dinv[i] = 1 / (alpha M_ii + beta A_ii), A_ii from the near field (the diagonal lies in every leaf's
+// own block), M_ii = sum over the cells K around DOF i's vertex of 2 |K| / ((d+1)(d+2)) (P1 mass)
+__global__ void hcg_diag_kernel(int64_t n, const int* ptr, const int* col, const double* val, double alpha,
+                                double beta, int dim, const int* vod, const int64_t* v2c_ptr, const int* v2c,
+                                const double* jac_orig, double* dinv) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double d = 0.0;
     for (int e = ptr[i]; e < ptr[i + 1]; ++e)
         if (col[e] == i) d = val[e];
+    d *= beta;
+    if (alpha != 0.0) {
+        const double scale = dim == 2 ? 0.5 : 1.0;  // |K| = jac / 2 (2D), jac (1D)
+        const double den = 2.0 / ((dim + 1.0) * (dim + 2.0));
+        double m = 0.0;
+        const int v = vod[i];
+        for (int64_t q = v2c_ptr[v]; q < v2c_ptr[v + 1]; ++q) m += scale * jac_orig[v2c[q]] * den;
+        d += alpha * m;
+    }
     dinv[i] = d > 0.0 ? 1.0 / d : 0.0;
 }
 
@@ -796,6 +810,7 @@ int fl_hmatrix_set_near(fl_hmatrix H, const double* A_dev, int64_t lda, void* st
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return hm_fail(H, FL_ECUDA, std::string("near gather: ") + cudaGetErrorString(e));
     H->near_ready = true;
+    H->dinv_ready = false;
     return FL_OK;
 }
 
@@ -833,6 +848,7 @@ int fl_hmatrix_assemble_near(fl_hmatrix H, void* stream) {
     rc = fl::assemble_hnear(h, H->pi, H->s, H->hn, H->nnz, H->nz_row, H->nz_col, H->nz_val, st);
     if (rc != FL_OK) return hm_fail(H, rc, h->err);
     H->near_ready = true;
+    H->dinv_ready = false;
     return FL_OK;
 }
 
@@ -1084,9 +1100,15 @@ const char* fl_hmatrix_last_error(fl_hmatrix H) { return H ? H->err.c_str() : "n
 
 int fl_hmatrix_solve(fl_hmatrix H, const double* b_dev, double* u_dev, const fl_solve_opts* o, fl_solve_info* info,
                      void* stream) {
+    return fl_hmatrix_solve_shifted(H, 0.0, 1.0, b_dev, u_dev, o, info, stream);
+}
+
+int fl_hmatrix_solve_shifted(fl_hmatrix H, double alpha, double beta, const double* b_dev, double* u_dev,
+                             const fl_solve_opts* o, fl_solve_info* info, void* stream) {
     if (!H) return FL_EINVAL;
     H->err.clear();
     if (!b_dev || !u_dev || b_dev == u_dev) return hm_fail(H, FL_EINVAL, "bad b / u");
+    if (!(alpha >= 0.0) || !(beta > 0.0)) return hm_fail(H, FL_EINVAL, "alpha >= 0 and beta > 0 needed");
     if (!H->near_ready) return hm_fail(H, FL_EINVAL, "near field not set (fl_hmatrix_set_near)");
     fl_solve_opts d{};
     fl_default_solve_opts(&d);
@@ -1104,8 +1126,15 @@ int fl_hmatrix_solve(fl_hmatrix H, const double* b_dev, double* u_dev, const fl_
         void* hp = nullptr;
         if (pool_host_alloc(&hp, 4 * sizeof(double)) != cudaSuccess) return hm_fail(H, FL_ENOMEM, "pinned scalars");
         H->cg_host = (double*)hp;
-        hcg_diag_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, H->nz_ptr, H->nz_col, H->nz_val, H->cg_dinv);
+    }
+    const fl::DevTables& mt = H->mesh->dev[H->pi];
+    if (!H->dinv_ready || H->dinv_alpha != alpha || H->dinv_beta != beta) {
+        hcg_diag_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, H->nz_ptr, H->nz_col, H->nz_val, alpha, beta, H->d,
+                                                            mt.vod, mt.v2c_ptr, mt.v2c, mt.jac_orig, H->cg_dinv);
         count_launch();
+        H->dinv_ready = true;
+        H->dinv_alpha = alpha;
+        H->dinv_beta = beta;
     }
     double* r = H->cg_r;
     double* z = H->cg_z;
@@ -1133,6 +1162,10 @@ int fl_hmatrix_solve(fl_hmatrix H, const double* b_dev, double* u_dev, const fl_
     int it = 0;
     while (out.status == FL_ENOTCONV && it < op.maxit) {
         if ((rc = fl_hmatrix_matvec(H, p, q, stream)) != FL_OK) return rc;
+        if (alpha != 0.0 || beta != 1.0) {  // q = beta A p + alpha M p
+            if ((rc = fl::mass_apply(H->mesh, H->s, 1, alpha, p, 1, beta, q, 1, q, 1, st)) != FL_OK)
+                return hm_fail(H, rc, H->mesh->err);
+        }
         dots(p, q, nullptr, nullptr, sc + 2);  // sc[2] = p.q
         hcg_update_kernel<<<HCG_BLOCKS, HCG_THREADS, 0, st>>>(n, sc, p, q, H->cg_dinv, u_dev, r, z);
         dots(r, z, r, r, sc + 1);  // sc[1] = r.z (new), sc[2] = r.r

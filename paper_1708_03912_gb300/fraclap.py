@@ -27,7 +27,7 @@ EXPORTS = ["fl_default_options", "fl_create", "fl_create_sector", "fl_destroy", 
            "fl_heat_matrix", "fl_mass_apply", "fl_strong_form", "fl_br_indicators", "fl_mark_max", "fl_refine",
            "fl_cluster_plan", "fl_near_region_plan", "fl_strong_form_cluster_plan", "fl_hmatrix_create", "fl_hmatrix_set_near",
            "fl_hmatrix_matvec", "fl_hmatrix_solve", "fl_hmatrix_info", "fl_hmatrix_assemble_near", "fl_hmatrix_near_info", "fl_hmatrix_get_near",
-           "fl_hmatrix_strong_form", "fl_hmatrix_br_indicators", "fl_hmatrix_last_error", "fl_hmatrix_destroy", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
+           "fl_hmatrix_strong_form", "fl_hmatrix_br_indicators", "fl_hmatrix_solve_shifted", "fl_hmatrix_last_error", "fl_hmatrix_destroy", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
            "fl_matvec_f32_static",
            "fl_split_bf16_bytes", "fl_split_bf16", "fl_matmul_bf16", "fl_default_batch_opts", "fl_batch_solve",
            "fl_tune_batch", "fl_tune_matvec", "fl_tune_record", "fl_tune_lookup", "fl_tune_clear", "fl_tune_count", "fl_tune_save",
@@ -169,6 +169,9 @@ def lib():
     L.fl_hmatrix_near_info.restype = ci
     L.fl_hmatrix_get_near.argtypes = [vp, ctypes.POINTER(i64), vp, vp, vp, vp]
     L.fl_hmatrix_get_near.restype = ci
+    L.fl_hmatrix_solve_shifted.argtypes = [vp, dbl, dbl, vp, vp, ctypes.POINTER(fl_solve_opts),
+                                           ctypes.POINTER(fl_solve_info), vp]
+    L.fl_hmatrix_solve_shifted.restype = ci
     L.fl_hmatrix_strong_form.argtypes = [vp, vp, ci, ci, ci, vp, vp]
     L.fl_hmatrix_strong_form.restype = ci
     L.fl_hmatrix_br_indicators.argtypes = [vp, vp, vp, ci, ci, ci, vp, vp, vp]
@@ -520,6 +523,7 @@ class HMatrix:
         _check(lib().fl_hmatrix_create(h, s, m, eta, leaf, ctypes.byref(self.hm), _stream(stream)), h)
         self.n = fl_num_dofs(h, s)
         self.n_cells = fl_get_stats(h, s)["n_cells"]
+        self.h, self.s = h, s
 
     def _check(self, r):
         if r != FL_OK:
@@ -585,6 +589,39 @@ class HMatrix:
         if r not in (FL_OK, FL_ENOTCONV, FL_ENOTSPD):
             self._check(r)
         return u, info
+
+    def solve_shifted(self, b, alpha, beta, tol=1e-8, maxit=10000, u=None, stream=None):
+        """(alpha M + beta A_H) u = b by Jacobi-PCG with the H-matrix product (M the P1 mass
+        matrix): (u, fl_solve_info), ENOTCONV / ENOTSPD reported in info.status."""
+        import torch
+
+        o = fl_default_solve_opts()
+        o.tol, o.maxit = tol, maxit
+        info = fl_solve_info()
+        u = torch.empty_like(b) if u is None else u
+        r = lib().fl_hmatrix_solve_shifted(self.hm, alpha, beta, _ptr(b), _ptr(u), ctypes.byref(o),
+                                           ctypes.byref(info), _stream(stream))
+        if r not in (FL_OK, FL_ENOTCONV, FL_ENOTSPD):
+            self._check(r)
+        return u, info
+
+    def heat_steps(self, dt, u0, F, steps, tol=1e-10, stream=None):
+        """Implicit Euler for the fractional heat equation (Sections 2 and 5) with the cluster
+        method: (M + dt A) u^{k+1} = M u^k + dt F, `steps` steps from u0 (F the load vector).
+        Returns (u, list of fl_solve_info)."""
+        import torch
+
+        u = u0.clone()
+        rhs = torch.empty_like(u0)
+        infos = []
+        for _ in range(steps):
+            _check(lib().fl_mass_apply(self.h, self.s, 1, 1.0, _ptr(u), 1, dt, _ptr(F), 1, _ptr(rhs), 1,
+                                       _stream(stream)), self.h)
+            u, info = self.solve_shifted(rhs, 1.0, dt, tol=tol, stream=stream)
+            if info.status != FL_OK:
+                raise FlError(info.status, "heat step did not converge")
+            infos.append(info)
+        return u, infos
 
     def info(self):
         v = (ctypes.c_int64 * 6)()

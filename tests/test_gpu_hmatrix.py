@@ -234,3 +234,31 @@ def test_near_field_assembled_without_dense_tables():
     assert i.status == F.FL_OK and torch.isfinite(u).all()
     H.close()
     mesh.close()
+
+
+def test_heat_steps_with_the_hmatrix():
+    # implicit Euler (M + dt A) u^{k+1} = M u^k + dt F with the cluster method (shifted H-matrix PCG,
+    # near field by local computations) against the dense heat steps: within the far field's
+    # interpolation error
+    V, T = synth.disc(10, 2.0)
+    s, dt, steps = 0.5, 1e-3, 5
+    mesh = F.Mesh(V, T)
+    A = mesh.assemble(s, "fp64")
+    b = mesh.load_vector(s)
+    u0 = torch.zeros_like(b)
+    ud, _ = mesh.heat_steps(A, s, dt, u0, b, steps)
+    H = F.HMatrix(mesh.h, s, m=6, eta=1.0, leaf=16)
+    H.assemble_near()
+    uh, infos = H.heat_steps(dt, u0, b, steps)
+    err = float((uh - ud).abs().max() / ud.abs().max())
+    print(f"heat steps, H-matrix vs dense: {err:.2e}; CG steps {[i.iterations for i in infos]}")
+    assert err < 1e-5
+    assert all(i.status == F.FL_OK for i in infos)
+    # alpha = 0, beta = 1 is the plain solve
+    u1, i1 = H.solve(b, tol=1e-10)
+    u2, i2 = H.solve_shifted(b, 0.0, 1.0, tol=1e-10)
+    assert torch.equal(u1, u2) and i1.iterations == i2.iterations
+    with pytest.raises(F.FlError):
+        H.solve_shifted(b, 1.0, 0.0)
+    H.close()
+    mesh.close()
