@@ -219,7 +219,7 @@ SF_CASES = {"sf_lshape3": (3, 0.5), "sf_lshape5": (5, 0.5), "hsf_lshape5": (5, 0
 MV_CASES = {"mv_f32_20000": (20000, "f32"), "mv_f64_20000": (20000, "f64"), "mv_f32_35693": (35693, "f32")}
 HM_CASES = {"hm_lshape4": (4, 4)}
 # near field of the cluster method assembled directly: L-shape level (m = 4, leaves of 32, eta = 1)
-HN_CASES = {"hn_lshape5": 5, "hn_lshape3": 3}
+HN_CASES = {"hn_lshape5": 5, "hn_lshape3": 3, "hn_lshape5m": 5}  # ...m: the mixed mode
 
 
 def run_mv_case(args):
@@ -287,18 +287,19 @@ def run_hn_case(args):
     from paper_1708_03912_gb300 import synth
 
     V, T = synth.lshape(0.25, HN_CASES[args.case])
+    prec = "mixed" if args.case.endswith("m") else "fp64"
     mesh = F.Mesh(V, T)
     H = F.HMatrix(mesh.h, 0.5, m=4, eta=1.0, leaf=32)
-    H.assemble_near()
+    H.assemble_near(prec)
     ts = []
     for _ in range(args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        H.assemble_near()
+        H.assemble_near(prec)
         b.record()
         b.synchronize()
         ts.append(a.elapsed_time(b))
-    print(f"case {args.case}: n {H.n} near field {H.info()['near_entries']} entries, {H.near_info()['tiles']} tiles, "
+    print(f"case {args.case}: {prec}, n {H.n} near field {H.info()['near_entries']} entries, {H.near_info()['tiles']} tiles, "
           f"assembly ms " + " ".join(f"{v:.3f}" for v in ts))
     H.close()
     mesh.close()
@@ -636,6 +637,14 @@ def hmatrix_section(F, timed, A, h5, b=None):
             rec["jacobi_pcg"] = {"ms": timed(lambda: Hn.solve(b, tol=1e-8), reps=2, flush_between=False),
                                  "iterations": i_n.iterations,
                                  "max_error_vs_dense_solution": float((un - u_dense).abs().max() / u_dense.abs().max())}
+        if m == 4:  # the mixed mode of the same assembly
+            Hn.assemble_near("mixed")
+            rec["mixed"] = {"assembly_ms": timed(lambda: Hn.assemble_near("mixed"), reps=3, flush_between=False)}
+            _, _, vm = Hn.get_near()
+            rp, cl, _ = Hn.get_near()
+            rows = torch.repeat_interleave(torch.arange(n, device=A.device), (rp[1:] - rp[:-1]).long())
+            dg = torch.diagonal(A)
+            rec["mixed"]["error_scaled_vs_fp64"] = float(((vm - va).abs() / torch.sqrt(dg[rows] * dg[cl.long()])).max())
         out[f"m{m}"]["near_assembled"] = rec
         Hn.close()
         H.close()

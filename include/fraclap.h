@@ -528,13 +528,15 @@ int fl_hmatrix_set_near(fl_hmatrix H, const double* A_dev, int64_t lda, void* st
  *     by the divergence theorem the same quantity, integrated over fewer facets (its facets
  *     at distance 1 with the k_near rules, the others with k_far, the boundary facets of
  *     Omega that touch K with the singular rules of the boundary term).
- * Entries whose DOFs share no cell equal the dense float64 matrix's bit for bit; the others
- * differ from it by the quadrature error of the far part of the diagonal blocks.  The first
- * call plans (host) and allocates the tiles' workspace; later calls recompute the values.
- * Not for regional operators, symmetry-reduced handles or 2D boundary DOFs (FL_ENOTIMPL).
+ * precision FL_FP64: entries whose DOFs share no cell equal the dense float64 matrix's bit for bit;
+ * the others differ from it by the quadrature error of the far part of the diagonal blocks.
+ * FL_MIXED: the tiles, near and touching pairs and the identical pair in float32 as the mixed
+ * dense assembly (the tile partials summed with compensation), the rest float64.  The first call
+ * plans (host) and allocates the tiles' workspace; later calls recompute the values.  Not for
+ * regional operators, symmetry-reduced handles or 2D boundary DOFs (FL_ENOTIMPL).
  * Errors: FL_EINVAL, FL_ENOMEM, FL_ENOTIMPL, FL_ECUDA.
  */
-int fl_hmatrix_assemble_near(fl_hmatrix H, void* stream);
+int fl_hmatrix_assemble_near(fl_hmatrix H, int precision, void* stream);
 /* The near field as CSR over the DOFs (rows ascending, columns ascending in a row): *nnz
  * receives the entry count; non-NULL device arrays rowptr_dev [n + 1], col_dev [nnz] and
  * val_dev [nnz] (float64) receive the pattern and the values (the values need a near field,

@@ -1296,6 +1296,7 @@ __global__ void add_csr_kernel(int64_t nnz, const int* csr_row, const int* csr_c
 // summed as compose_far_kernel sums them; the product and the sum are not fused, so an entry
 // whose slots hold no diagonal block is bitwise the dense matrix's.  Tiles are found by
 // bisection in their row of the tile list; a tile missing from it (a broken plan) gives NaN.
+template <typename T>
 __global__ void hnear_compose_kernel(int64_t nnz, const int* __restrict__ nz_row, const int* __restrict__ nz_col,
                                      const int* __restrict__ csr_ptr, const int* __restrict__ csr_col,
                                      const int64_t* __restrict__ g_ptr, const int64_t* __restrict__ g_slot,
@@ -1303,7 +1304,7 @@ __global__ void hnear_compose_kernel(int64_t nnz, const int* __restrict__ nz_row
                                      const int* __restrict__ occ_blk, const int* __restrict__ occ_loc,
                                      const int* __restrict__ L_ptr, const int* __restrict__ trow_ptr,
                                      const int* __restrict__ tiles, const int64_t* __restrict__ toff,
-                                     const double* __restrict__ Pt, double negC, double* __restrict__ val) {
+                                     const T* __restrict__ Pt, double negC, double* __restrict__ val) {
     const int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (z >= nnz) return;
     const int i = nz_row[z], j = nz_col[z];
@@ -1322,6 +1323,12 @@ __global__ void hnear_compose_kernel(int64_t nnz, const int* __restrict__ nz_row
         }
     }
     double far = 0.0;
+    // float32 partials: a compensated float32 sum, as in compose_far_kernel
+    float ks = 0.f, kc = 0.f;
+    auto add = [&](T x) {
+        if constexpr (sizeof(T) == 4) kahan_add(ks, kc, x);
+        else far += x;
+    };
     bool missing = false;
     for (int oa = occ_ptr[lo]; oa < occ_ptr[lo + 1]; ++oa) {
         const int Ba = occ_blk[oa], la = occ_loc[oa];
@@ -1344,16 +1351,17 @@ __global__ void hnear_compose_kernel(int64_t nnz, const int* __restrict__ nz_row
             }
             const int64_t base = toff[a];
             if (Ba < Bb) {
-                far += Pt[base + (int64_t)la * (L_ptr[Bb + 1] - L_ptr[Bb]) + lb];
+                add(Pt[base + (int64_t)la * (L_ptr[Bb + 1] - L_ptr[Bb]) + lb]);
             } else if (Ba > Bb) {
-                far += Pt[base + (int64_t)lb * (L_ptr[Ba + 1] - L_ptr[Ba]) + la];
+                add(Pt[base + (int64_t)lb * (L_ptr[Ba + 1] - L_ptr[Ba]) + la]);
             } else {
                 const int64_t nL = L_ptr[Ba + 1] - L_ptr[Ba];
-                far += Pt[base + (int64_t)la * nL + lb];
-                far += Pt[base + (int64_t)lb * nL + la];
+                add(Pt[base + (int64_t)la * nL + lb]);
+                add(Pt[base + (int64_t)lb * nL + la]);
             }
         }
     }
+    if constexpr (sizeof(T) == 4) far = (double)ks - (double)kc;
     val[z] = missing ? __longlong_as_double(0x7ff8000000000000LL) : __dadd_rn(__dmul_rn(negC, far), acc);
 }
 
@@ -2398,15 +2406,17 @@ int assemble(fl_ctx* h, double s, int precision, double* A, int64_t lda, cudaStr
 // the boundary of N(K) in place of the far pairs' and the boundary facets' part (element
 // kernel, cluster mode), and the entries composed from these.  Float64 (double-word far pairs
 // where the dense float64 mode takes them).  No O(n^2) table or workspace is touched.
-int assemble_hnear(fl_ctx* h, int pi, double s, const HNearDev& q, int64_t nnz, const int* nz_row,
+int assemble_hnear(fl_ctx* h, int pi, double s, int precision, const HNearDev& q, int64_t nnz, const int* nz_row,
                    const int* nz_col, double* nz_val, cudaStream_t st) {
     const Plan& P = h->plan[pi];
+    if (precision != FL_FP64 && precision != FL_MIXED) return set_err(h, FL_EINVAL, "unknown precision");
+    const bool f32 = precision == FL_MIXED;
     if (P.sym_K) return sym_unsupported(h, "the cluster method's near-field assembly");
     if (h->opt.regional) return set_err(h, FL_ENOTIMPL, "the near-field assembly needs the boundary term (not regional)");
     if (P.dim == 2 && P.paper_all) return set_err(h, FL_ENOTIMPL, "2D boundary DOFs are not implemented");
     FL_CUDA_TRY(h, cudaSetDevice(h->device));
     FL_TRY(ensure_device(h, pi, st));
-    FL_TRY(ensure_rules(h, h->dev[pi], s, false, st));
+    FL_TRY(ensure_rules(h, h->dev[pi], s, f32, st));
     DevTables t = h->dev[pi];  // the mesh tables, with this assembly's tiles, facets and workspace
     t.tiles = q.tiles;
     t.toff = q.toff;
@@ -2428,12 +2438,18 @@ int assemble_hnear(fl_ctx* h, int pi, double s, const HNearDev& q, int64_t nnz, 
     const int64_t nc = P.nc;
     const unsigned gb = (unsigned)((nc + 127) / 128);
     if (nc > 0) {
-        if (D == 2) prep_points<double, 2><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts);
-        else prep_points<double, 1><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts);
+        if (f32) {
+            if (D == 2) prep_points<float, 2><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (float*)t.pts);
+            else prep_points<float, 1><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (float*)t.pts);
+        } else {
+            if (D == 2) prep_points<double, 2><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts);
+            else prep_points<double, 1><<<gb, 128, 0, st>>>(t.cvx, t.cen, t.rule + ro.far_lam, ro.qf, nc, (double*)t.pts);
+        }
         fl::count_launch();
     }
     FL_CUDA_TRY(h, cudaGetLastError());
-    const bool dw = D == 2 && far_dw_applies(h, P, pw);
+    const int pw32 = (pw == 4 || pw == 6) ? pw : 0;
+    const bool dw = !f32 && D == 2 && far_dw_applies(h, P, pw);
     if (dw) FL_TRY(prep_far_dw(h, P, t, ro, st));
     // the local pairs and the cell blocks on the second stream, beside the tiles (they share no
     // buffer with them); the streams join before the entries are composed
@@ -2445,16 +2461,17 @@ int assemble_hnear(fl_ctx* h, int pi, double s, const HNearDev& q, int64_t nnz, 
     }
     int rc = FL_OK;
     if (q.ntiles > 0) {
-        if (dw) rc = launch_far_dw(h, P, t, rb, ro, pw, st, q.ntiles);
+        if (f32) rc = launch_far<float>(h, P, t, rb, ro, expo, pw32, st, q.ntiles);
+        else if (dw) rc = launch_far_dw(h, P, t, rb, ro, pw, st, q.ntiles);
         else rc = launch_far<double>(h, P, t, rb, ro, expo, pw, st, q.ntiles);
     }
-    ElemArgs E = elem_args(h, P, t, ro, s, C, false);
+    ElemArgs E = elem_args(h, P, t, ro, s, C, f32);
     E.cluster = 1;
     E.nblk = 0;
     E.Pd = nullptr;
     E.Bf = nullptr;
-    int side_rc = launch_near_pairs(h, P, t, rb, ro, expo, pw, false, C, sst);
-    if (side_rc == FL_OK) side_rc = launch_touch_pairs(h, P, t, ro, s, C, pw, false, sst);
+    int side_rc = launch_near_pairs(h, P, t, rb, ro, expo, pw, f32, C, sst);
+    if (side_rc == FL_OK) side_rc = launch_touch_pairs(h, P, t, ro, s, C, pw, f32, sst);
     if (side_rc == FL_OK) side_rc = launch_element(h, E, pw, 1, sst);
     if (side_rc == FL_OK) side_rc = launch_element(h, E, pw, 2, sst);
     if (sst != st) {  // joined even after an error, so that the caller's stream never runs ahead
@@ -2464,9 +2481,15 @@ int assemble_hnear(fl_ctx* h, int pi, double s, const HNearDev& q, int64_t nnz, 
     FL_TRY(rc);
     FL_TRY(side_rc);
     if (nnz > 0) {
-        hnear_compose_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(
-            nnz, nz_row, nz_col, t.csr_ptr, t.csr_col, t.g_ptr, t.g_slot, t.contrib, t.occ_ptr, t.occ_blk, t.occ_loc,
-            t.L_ptr, q.trow_ptr, q.tiles, q.toff, q.P, -C, nz_val);
+        const unsigned g = (unsigned)((nnz + 255) / 256);
+        if (f32)
+            hnear_compose_kernel<float><<<g, 256, 0, st>>>(nnz, nz_row, nz_col, t.csr_ptr, t.csr_col, t.g_ptr, t.g_slot,
+                                                           t.contrib, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr,
+                                                           q.trow_ptr, q.tiles, q.toff, (const float*)q.P, -C, nz_val);
+        else
+            hnear_compose_kernel<double><<<g, 256, 0, st>>>(nnz, nz_row, nz_col, t.csr_ptr, t.csr_col, t.g_ptr,
+                                                            t.g_slot, t.contrib, t.occ_ptr, t.occ_blk, t.occ_loc, t.L_ptr,
+                                                            q.trow_ptr, q.tiles, q.toff, q.P, -C, nz_val);
         fl::count_launch();
     }
     FL_CUDA_TRY(h, cudaGetLastError());

@@ -228,7 +228,7 @@ int launch_near_dw(fl_ctx* h, const Plan& P, DevTables& t, const std::vector<dou
 // the cluster method's near field from local computations (assemble.cu): nnz entries (row, col
 // DOF ids) into nz_val; uses the handle's contribution slots and row-sum buffers
 struct HNearDev;
-int assemble_hnear(fl_ctx* h, int pi, double s, const HNearDev& q, int64_t nnz, const int* nz_row,
+int assemble_hnear(fl_ctx* h, int pi, double s, int precision, const HNearDev& q, int64_t nnz, const int* nz_row,
                    const int* nz_col, double* nz_val, cudaStream_t st);
 // adaptive loop (adaptive.cu, refine.cpp)
 int strong_form(fl_ctx* h, double s, const double* u, int k_cell, int k_edge, int k_near, double* S, cudaStream_t st);

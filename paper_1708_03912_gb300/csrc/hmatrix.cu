@@ -814,7 +814,7 @@ int fl_hmatrix_set_near(fl_hmatrix H, const double* A_dev, int64_t lda, void* st
     return FL_OK;
 }
 
-int fl_hmatrix_assemble_near(fl_hmatrix H, void* stream) {
+int fl_hmatrix_assemble_near(fl_hmatrix H, int precision, void* stream) {
     if (!H) return FL_EINVAL;
     H->err.clear();
     if (cudaSetDevice(H->device) != cudaSuccess) return hm_fail(H, FL_ECUDA, "cudaSetDevice");
@@ -845,7 +845,7 @@ int fl_hmatrix_assemble_near(fl_hmatrix H, void* stream) {
         H->hn_bytes = H->bytes - b0;
         H->hn_planned = true;
     }
-    rc = fl::assemble_hnear(h, H->pi, H->s, H->hn, H->nnz, H->nz_row, H->nz_col, H->nz_val, st);
+    rc = fl::assemble_hnear(h, H->pi, H->s, precision, H->hn, H->nnz, H->nz_row, H->nz_col, H->nz_val, st);
     if (rc != FL_OK) return hm_fail(H, rc, h->err);
     H->near_ready = true;
     H->dinv_ready = false;

@@ -163,7 +163,7 @@ def lib():
     L.fl_hmatrix_solve.restype = ci
     L.fl_hmatrix_info.argtypes = [vp, ctypes.POINTER(i64)]
     L.fl_hmatrix_info.restype = ci
-    L.fl_hmatrix_assemble_near.argtypes = [vp, vp]
+    L.fl_hmatrix_assemble_near.argtypes = [vp, ci, vp]
     L.fl_hmatrix_assemble_near.restype = ci
     L.fl_hmatrix_near_info.argtypes = [vp, ctypes.POINTER(i64)]
     L.fl_hmatrix_near_info.restype = ci
@@ -532,9 +532,10 @@ class HMatrix:
     def set_near(self, A, stream=None):
         self._check(lib().fl_hmatrix_set_near(self.hm, _ptr(A), A.stride(0), _stream(stream)))
 
-    def assemble_near(self, stream=None):
-        """Near-field entries by local computations (no dense matrix)."""
-        self._check(lib().fl_hmatrix_assemble_near(self.hm, _stream(stream)))
+    def assemble_near(self, precision="fp64", stream=None):
+        """Near-field entries by local computations (no dense matrix); precision "fp64" or "mixed"."""
+        prec = {"fp64": FL_FP64, "mixed": FL_MIXED}[precision]
+        self._check(lib().fl_hmatrix_assemble_near(self.hm, prec, _stream(stream)))
 
     def get_near(self, stream=None):
         """The near field as (rowptr, col, val) CUDA tensors (int32, int32, float64)."""

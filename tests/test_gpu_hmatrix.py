@@ -206,6 +206,17 @@ def test_near_field_assembled_at_size_against_dense():
     ua, ia = Ha.solve(b, tol=1e-10)
     assert idd.status == F.FL_OK and ia.status == F.FL_OK
     assert float((ua - ud).abs().max() / ud.abs().max()) < 1e-5
+    # the mixed mode (float32 tiles, near and touching pairs, identical pair): within the dense mixed
+    # mode's bound of the float64 entries
+    Hm = F.HMatrix(mesh.h, s, m=5, eta=1.0, leaf=32)
+    Hm.assemble_near("mixed")
+    _, _, vm = Hm.get_near()
+    relm = float(((vm - va).abs() / scale).max())
+    print(f"mixed near field vs float64: {relm:.2e} (scaled)")
+    assert relm < 2e-5
+    um, im = Hm.solve(b, tol=1e-10)
+    assert im.status == F.FL_OK and float((um - ua).abs().max() / ua.abs().max()) < 1e-4
+    Hm.close()
     # the dense assembly on the same handle is unchanged by it
     A2 = mesh.assemble(s, "fp64")
     assert torch.equal(A, A2)
