@@ -528,6 +528,26 @@ __global__ void __launch_bounds__(SF_THREADS) hsf_far_dw_kernel(
     if (valid) part[gpo[g] + (int64_t)ch * ng + i] = dw_to(acc);
 }
 
+// r2^{-s} and r2^{-(1+s)} for s = pw0 / 4 (pw0 in {1, 2, 3}) through t = r2^{-1/2}: products of t
+// and sqrt(t) in place of two general powers
+__device__ __forceinline__ void hsf_pows(double r2, int pw0, double& k0, double& k1) {
+    const double t = rsqrt(r2);
+    const double t2 = t * t;
+    if (pw0 == 2) {
+        k0 = t;
+        k1 = t2 * t;
+    } else {
+        const double q = sqrt(t);
+        if (pw0 == 1) {
+            k0 = q;
+            k1 = t2 * q;
+        } else {
+            k0 = t * q;
+            k1 = t2 * t * q;
+        }
+    }
+}
+
 __device__ __forceinline__ double hsf_cheb_node(double c, double L, int m, int k) {
     return c + 0.5 * L * cos((2.0 * (k + 1) - 1.0) * M_PI / (2.0 * m));
 }
@@ -550,7 +570,7 @@ __global__ void hsf_near_kernel(int64_t npts, int q, const double* __restrict__ 
                                 const int* __restrict__ gch, const int64_t* __restrict__ gpo,
                                 const double* __restrict__ part, int m, int md, const double* __restrict__ yh,
                                 const double* __restrict__ center, const double* __restrict__ side, double s,
-                                double mexp, double C, double* __restrict__ S) {
+                                double mexp, int pw0, double C, double* __restrict__ S) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npts) return;
     const int64_t kint = p / q;
@@ -590,8 +610,8 @@ __global__ void hsf_near_kernel(int64_t npts, int q, const double* __restrict__ 
             const double w = wn[gq] * n[2];
             const double dx = x0 - yx, dy = x1 - yy;
             const double r2 = dx * dx + dy * dy;
-            const double k0 = pow(r2, -0.5 * mexp);
-            const double k1 = pow(r2, -0.5 * (2.0 + 2.0 * s));
+            double k0, k1;
+            hsf_pows(r2, pw0, k0, k1);
             const double nd = n0x * dx + n0y * dy;
             const double du = Kn >= 0 ? g0x * dx + g0y * dy : ux;
             near += w * (cg * k0 - du * nd * k1 / (2.0 * s));
@@ -615,7 +635,9 @@ __global__ void hsf_near_kernel(int64_t npts, int q, const double* __restrict__ 
             for (int gq = 0; gq < ke; ++gq) {
                 const int64_t i = (int64_t)e * ke + gq;
                 const double dx = x0 - yrec[2 * i], dy = x1 - yrec[2 * i + 1];
-                near += we[gq] * fn[3 * e + 2] * cjv * pow(dx * dx + dy * dy, -0.5 * mexp);
+                double k0, k1;
+                hsf_pows(dx * dx + dy * dy, pw0, k0, k1);
+                near += we[gq] * fn[3 * e + 2] * cjv * k0;
             }
         }
     }
@@ -1363,7 +1385,7 @@ int strong_form_cluster(fl_ctx* h, double s, const double* u, int kc, int ke, in
         npts, q, X, lam, t.sf_perm, t.cells, t.V, t.dov, u, t.sf_c2f, t.sf_fac, t.sf_fn, kn, tn, wn, t.sf_v2e_ptr,
         t.sf_v2e, ke, yrec, we, g.pgroup, g.plocal, g.gbits, g.words, g.dof_leaf, g.gnode, g.gp_ptr, g.gf_ptr,
         g.gf_fac, g.cj, g.gch, g.gpo,
-        g.part, g.m, g.md, g.yh, g.center, g.side, s, mexp, frac_const(2, s), S);
+        g.part, g.m, g.md, g.yh, g.center, g.side, s, mexp, pw0, frac_const(2, s), S);
     count_launch();
     SF_CUDA(h, cudaGetLastError());
     return FL_OK;
