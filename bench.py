@@ -637,14 +637,18 @@ def hmatrix_section(F, timed, A, h5, b=None):
             rec["jacobi_pcg"] = {"ms": timed(lambda: Hn.solve(b, tol=1e-8), reps=2, flush_between=False),
                                  "iterations": i_n.iterations,
                                  "max_error_vs_dense_solution": float((un - u_dense).abs().max() / u_dense.abs().max())}
-        if m == 4:  # the mixed mode of the same assembly
-            Hn.assemble_near("mixed")
-            rec["mixed"] = {"assembly_ms": timed(lambda: Hn.assemble_near("mixed"), reps=3, flush_between=False)}
-            _, _, vm = Hn.get_near()
-            rp, cl, _ = Hn.get_near()
-            rows = torch.repeat_interleave(torch.arange(n, device=A.device), (rp[1:] - rp[:-1]).long())
-            dg = torch.diagonal(A)
-            rec["mixed"]["error_scaled_vs_fp64"] = float(((vm - va).abs() / torch.sqrt(dg[rows] * dg[cl.long()])).max())
+        if m == 4:  # the mixed mode of the same assembly (a failure is reported in the key, not fatal)
+            try:
+                Hn.assemble_near("mixed")
+                rec["mixed"] = {"assembly_ms": timed(lambda: Hn.assemble_near("mixed"), reps=3, flush_between=False)}
+                rp, cl, vm = Hn.get_near()
+                rows = torch.repeat_interleave(torch.arange(n, device=A.device), (rp[1:] - rp[:-1]).long())
+                dg = torch.diagonal(A)
+                rec["mixed"]["error_scaled_vs_fp64"] = float(
+                    ((vm - va).abs() / torch.sqrt(dg[rows] * dg[cl.long()])).max())
+                del rows, vm, rp, cl
+            except Exception as exc:  # noqa: BLE001
+                rec["mixed"] = {"error": f"{type(exc).__name__}: {exc}"}
         out[f"m{m}"]["near_assembled"] = rec
         Hn.close()
         H.close()
