@@ -769,6 +769,21 @@ def adaptive_section(F, synth, timed, peaks, sms, m, A, b, n_el):
         out["cluster"][f"m{mm}"] = {"strong_form_ms": ms_c, "speedup_vs_direct": sf_ms / ms_c,
                                     "max_error_vs_direct": float((Sc - S).abs().max() / S.abs().max())}
         H.close()
+    # facet-point evaluations of the cluster form from its host plan (each point against its group's
+    # facets; the few facets through the point's cell, summed in float64, are counted too)
+    try:
+        pl = F.fl_strong_form_cluster_plan(m.h, s, 1.0, 32, kc)
+        counts = np.bincount(pl["pgroup"], minlength=len(pl["gnode"])).astype(np.int64)
+        ev_c = int(np.sum(counts * np.diff(pl["gf_ptr"]))) * ke
+        ms4 = out["cluster"]["m4"]["strong_form_ms"]
+        ops_c = ev_c * SF_DW_OPS_PER_EVAL[int(round(4 * s))]
+        out["cluster"]["point_facet_evaluations"] = ev_c
+        out["cluster"]["roofline_whole_call_m4"] = {
+            "bound": "alu", "kernel": f"hsf_far_dw_kernel<{int(round(4 * s))}> and the float64 near kernel of the call",
+            "achieved": ops_c / (ms4 / 1000) / 1e12, "peak": peak_ops / 1e12, "unit": "T FP32-ops/s",
+            "frac": ops_c / (ms4 / 1000) / peak_ops, "peak_from": "SMs x 128 FP32 lanes x max SM clock (measured clock)"}
+    except Exception as exc:  # noqa: BLE001
+        out["cluster"]["roofline_whole_call_m4"] = {"error": f"{type(exc).__name__}: {exc}"}
     # the loop
     V0, T0 = synth.lshape(0.25, 0)
     torch.cuda.synchronize()
