@@ -1,7 +1,7 @@
 """Low-precision copies of the stiffness matrix and the products formed with them
 (oracle; test infrastructure only).
 
-The batched solver keeps the float64 matrix A as the judge of the residual and
+The batched solver keeps the float64 matrix A as the reference for the residual and
 iterates on a Jacobi-scaled copy in bfloat16.  What that copy and its product
 are, written out from their definitions:
 
