@@ -168,6 +168,63 @@ def oracle_sample(nrows):
                                      f"of the L-shape level {LSHAPE_LEVEL}, numpy float64")
 
 
+def _oracle_rows_worker(job):
+    """One process of the all-cores oracle timing (started by spawn): builds the headline mesh, then
+    times the oracle's assembly of its DOF rows; returns the seconds of that assembly."""
+    rows = job
+    from oracle import OracleMesh, assemble_matrix
+    from paper_1708_03912_gb300 import synth
+
+    V, T = synth.lshape(0.25, LSHAPE_LEVEL)
+    om = OracleMesh(V, T)
+    t0 = time.perf_counter()
+    assemble_matrix(om, LSHAPE_S, rows=rows)
+    return time.perf_counter() - t0
+
+
+def oracle_sample_all_cores(rows_per_process=1):
+    """The oracle on every host core: one spawned single-threaded process per core, each on its own
+    seeded DOF rows (successive rows of the same permutation as oracle_sample); the rate is all the
+    processes' ordered element pairs over the longest process's assembly time.  Returns (pairs per
+    second, seconds, processes, sample description)."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    from paper_1708_03912_gb300 import synth
+
+    if "om" not in _ORACLE:
+        from oracle import OracleMesh
+
+        V, T = synth.lshape(0.25, LSHAPE_LEVEL)
+        _ORACLE["om"] = OracleMesh(V, T)
+        _ORACLE["k"] = 0
+    om = _ORACLE["om"]
+    vod = om.dofs(LSHAPE_S)[0]
+    perm = np.random.default_rng(synth.SEED).permutation(len(vod))
+    try:
+        nproc = len(os.sched_getaffinity(0))  # the cores this process may run on
+    except AttributeError:
+        nproc = os.cpu_count() or 1
+    nproc = max(1, min(nproc, 64))
+    jobs, pairs = [], 0
+    for p in range(nproc):
+        k0 = _ORACLE["k"] + p * rows_per_process
+        rows = np.sort(perm[k0:k0 + rows_per_process])
+        active = set()
+        for r in rows:
+            active.update(om.cells_of_vertex[vod[r]])
+        pairs += 2 * len(active) * om.nc - len(active) ** 2
+        jobs.append(rows)
+    _ORACLE["k"] += nproc * rows_per_process
+    with mp.get_context("spawn").Pool(nproc) as pool:
+        secs = pool.map_async(_oracle_rows_worker, jobs).get(timeout=600)  # bounded: the pool is ended on exit
+    dt = max(secs)
+    return pairs / dt, dt, nproc, (f"{nproc} single-threaded processes x {rows_per_process} seeded DOF row(s) of the "
+                                   f"L-shape level {LSHAPE_LEVEL}, numpy float64; pairs of all processes over the "
+                                   f"longest assembly")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -1123,6 +1180,11 @@ def main():
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         v, dt, threads, desc = oracle_sample(2)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+        try:  # the same oracle on every host core (a failure is reported in the key, not fatal)
+            va, dta, procs, desca = oracle_sample_all_cores()
+            line["cpu_baseline"]["all_cores"] = {"value": va, "unit": UNIT, "cores": procs, "sample": desca}
+        except Exception as exc:  # noqa: BLE001
+            line["cpu_baseline"]["all_cores"] = {"error": f"{type(exc).__name__}: {exc}"}
     m.close()
     if rank == 0:
         print(json.dumps(line))
