@@ -218,7 +218,7 @@ def oracle_sample_all_cores(rows_per_process=1):
         jobs.append(rows)
     _ORACLE["k"] += nproc * rows_per_process
     with mp.get_context("spawn").Pool(nproc) as pool:
-        secs = pool.map_async(_oracle_rows_worker, jobs).get(timeout=600)  # bounded: the pool is ended on exit
+        secs = pool.map_async(_oracle_rows_worker, jobs).get(timeout=240)  # bounded: the pool is ended on exit
     dt = max(secs)
     return pairs / dt, dt, nproc, (f"{nproc} single-threaded processes x {rows_per_process} seeded DOF row(s) of the "
                                    f"L-shape level {LSHAPE_LEVEL}, numpy float64; pairs of all processes over the "
