@@ -553,8 +553,9 @@ int fl_hmatrix_get_near(fl_hmatrix H, int64_t* nnz, int32_t* rowptr_dev, int32_t
  * of u_F is -C sum_alpha L_alpha^sigma(x0) yh_sigma[alpha] with yh the far-field coefficients of
  * u from the H-matrix product's upward pass, couplings and downward pass.  Points of cells without
  * a DOF vertex take the strong form of u itself.  Needs no near field.  2D, s in {1/4, 1/2, 3/4},
- * interior DOFs (else FL_ENOTIMPL).  The first call for a k_cell plans (host).  Errors: FL_EINVAL,
- * FL_ENOMEM, FL_ENOTIMPL, FL_ECUDA.
+ * interior DOFs (else FL_ENOTIMPL).  The first call for a k_cell plans (host); a later call with another
+ * k_cell plans again, the earlier plan's device memory staying with H until fl_hmatrix_destroy.  Calls on
+ * one H must not overlap (they share its workspace).  Errors: FL_EINVAL, FL_ENOMEM, FL_ENOTIMPL, FL_ECUDA.
  */
 int fl_hmatrix_strong_form(fl_hmatrix H, const double* u_dev, int k_cell, int k_edge, int k_near, double* S_dev,
                            void* stream);
