@@ -122,3 +122,82 @@ def reduced_system(vertices, cells, K: int, s: float, f_sector=None, dof_mode: s
     R = (size / K)[:, None] * (A_rows @ P)
     b = load_vector(mesh, s, _whole_f(vertices, cells, K, mesh, f_sector), dof_mode)
     return (R + R.T) / 2.0, P.T @ b / K, reps
+
+
+def reduced_system_keff(vertices, cells, K: int, s: float, f_sector=None, dof_mode: str = "interior", orders=None):
+    """(A_red, b_red, reps) in Section 7's effective-kernel form: the sector's cells against the
+    K images of the sector's cells, each orbit of element pairs of the whole mesh (under the
+    rotation) evaluated once.  With the whole mesh's cells numbered copy by copy (copy l of sector
+    cell k is cell l n_s + k), an orbit of unordered pairs is represented by (k, copy l of k') with
+    k < k' and any l, or k = k' and 1 <= l <= K / 2 (l = K / 2 is an orbit of K / 2 pairs: weight
+    1/2); every cell once for the identical pair and the boundary term.  Each representative's full
+    contribution (both off-diagonal blocks and both diagonal-block terms) is added in orbit
+    coordinates, so A_red = P^T A P / K exactly for a rotation-invariant quadrature; the oracle's
+    touching rules take the lower cell index as K, which rotation does not preserve, so the two
+    differ by the quadrature error of those pairs.  b_red = P^T b / K.  2D rotations only."""
+    from .assemble import (QuadOrders, boundary_own_edge_2d, boundary_separated, boundary_vertex_2d,
+                           common_edge_2d, common_vertex_2d, frac_constant, identical_2d, separated_blocks)
+
+    orders = orders or QuadOrders()
+    Cs = np.asarray(cells)
+    ns = len(Cs)
+    mesh, P, reps = orbits(vertices, cells, K, s, dof_mode)
+    if mesh.dim != 2:
+        raise ValueError("rotations of a 2D sector only")
+    vod, dov = mesh.dofs(s, dof_mode)
+    orb = -np.ones(mesh.nv, dtype=np.int64)
+    orb[vod] = np.argmax(P, axis=1)
+    n_red = P.shape[1]
+    A = np.zeros((n_red, n_red))
+    C = frac_constant(2, s)
+    has_dof = (dov[mesh.C] >= 0).any(axis=1)
+
+    def add(rv, cv, blk, w=1.0):
+        for a, vi in enumerate(rv):
+            oi = orb[vi]
+            if oi < 0:
+                continue
+            for b, vj in enumerate(cv):
+                oj = orb[vj]
+                if oj >= 0:
+                    A[oi, oj] += w * blk[a, b]
+
+    nc = mesh.nc
+    idx = np.arange(nc)
+    for k in range(ns):
+        kk, ll = idx % ns, idx // ns
+        rep = (kk > k) | ((kk == k) & (ll >= 1) & (2 * ll <= K))
+        weight = np.where((kk == k) & (2 * ll == K), 0.5, 1.0)
+        shared, near = mesh.classify_cells(k)
+        partner = rep & (has_dof | has_dof[k])
+        for m in np.nonzero(partner & (shared > 0))[0]:
+            lo, hi = min(k, m), max(k, m)
+            if shared[m] == 2:
+                loc, blk = common_edge_2d(mesh, s, C, lo, hi, orders.k_touch)
+            else:
+                loc, blk = common_vertex_2d(mesh, s, C, lo, hi, orders.k_vertex)
+            add(loc, loc, blk, weight[m])
+        for sel, order in (((shared == 0) & near, orders.k_near), ((shared == 0) & ~near, orders.k_far)):
+            for m in np.nonzero(partner & sel)[0]:
+                off, blk_k, blk_m = separated_blocks(mesh, s, C, k, np.array([m]), order)
+                w = weight[m]
+                add(mesh.C[k], mesh.C[m], off[0], w)
+                add(mesh.C[m], mesh.C[k], off[0].T, w)
+                add(mesh.C[k], mesh.C[k], blk_k, w)
+                add(mesh.C[m], mesh.C[m], blk_m[0], w)
+        if has_dof[k]:
+            loc, blk = identical_2d(mesh, s, C, k, 2 * orders.k_touch)
+            add(loc, loc, blk)
+            fsh, fnear = mesh.classify_facets(k)
+            for f in np.nonzero(fsh > 0)[0]:
+                if fsh[f] == 2:
+                    loc, blk = boundary_own_edge_2d(mesh, s, C, k, f, orders.k_bnd)
+                else:
+                    loc, blk = boundary_vertex_2d(mesh, s, C, k, f, orders.k_bnd)
+                add(loc, loc, blk)
+            for sel, order in ((fnear & (fsh == 0), orders.k_near), (~fnear & (fsh == 0), orders.k_far)):
+                fs = np.nonzero(sel)[0]
+                if len(fs):
+                    add(mesh.C[k], mesh.C[k], boundary_separated(mesh, s, C, k, fs, order))
+    b = load_vector(mesh, s, _whole_f(vertices, cells, K, mesh, f_sector), dof_mode)
+    return A, P.T @ b / K, reps
