@@ -247,7 +247,8 @@ def _far_field_coefficients(tree: ClusterTree, far, s: float, x, m: int):
 
 
 def strong_form_cluster(mesh: OracleMesh, s: float, u_dof, m: int = 4, eta: float = 1.0, leaf: int = 32,
-                        k_cell: int = 3, k_edge: int = 4, k_near: int = 16, dof_mode: str = "interior"):
+                        k_cell: int = 3, k_edge: int = 4, k_near: int = 16, dof_mode: str = "interior",
+                        cells=None):
     """(-Delta)^s u_h at the cell-rule points of every cell [nc, q] by the cluster method
     (Section 6): for a point x0 of cell K0, i0 the DOF of K0 closest to x0 and sigma its leaf,
     u = u_N + u_F with u_N the part on the DOFs of sigma's inadmissible partners; the strong form
@@ -258,7 +259,7 @@ def strong_form_cluster(mesh: OracleMesh, s: float, u_dof, m: int = 4, eta: floa
 
     Readings: ties in "closest" go to the lower DOF index; a cell without a DOF vertex (all its
     vertices on the boundary) belongs to no support, so its points take the strong form of u
-    itself (no far part)."""
+    itself (no far part).  With `cells`, only the points of those cells: [len(cells), q]."""
     from .adaptive import cell_rule_points, strong_form
 
     tree = ClusterTree(mesh, s, leaf, dof_mode)
@@ -276,12 +277,13 @@ def strong_form_cluster(mesh: OracleMesh, s: float, u_dof, m: int = 4, eta: floa
     _, dov = mesh.dofs(s, dof_mode)
     X, _, _ = cell_rule_points(mesh, k_cell)
     q = X.shape[1]
-    out = np.zeros((mesh.nc, q))
+    cells = np.arange(mesh.nc) if cells is None else np.asarray(cells)
+    out = np.zeros((len(cells), q))
     opts = dict(k_cell=k_cell, k_edge=k_edge, k_near=k_near, dof_mode=dof_mode)
-    for k0 in range(mesh.nc):
+    for row, k0 in enumerate(cells):
         dofs = [int(dov[v]) for v in mesh.C[k0] if dov[v] >= 0]
         if not dofs:
-            out[k0] = strong_form(mesh, s, u_dof, cells=[k0], **opts)[0]
+            out[row] = strong_form(mesh, s, u_dof, cells=[k0], **opts)[0]
             continue
         cache = {}
         for a in range(q):
@@ -294,5 +296,5 @@ def strong_form_cluster(mesh: OracleMesh, s: float, u_dof, m: int = 4, eta: floa
                 for tau in partners.get(sigma, []):
                     uN[tree.dofs[tau]] = u_dof[tree.dofs[tau]]
                 cache[sigma] = strong_form(mesh, s, uN, cells=[k0], **opts)[0]
-            out[k0, a] = cache[sigma][a] - C * float(lagrange(tree, sigma, m, x0[None, :])[0] @ yh[sigma])
+            out[row, a] = cache[sigma][a] - C * float(lagrange(tree, sigma, m, x0[None, :])[0] @ yh[sigma])
     return out

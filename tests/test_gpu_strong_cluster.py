@@ -1,6 +1,11 @@
 """GPU parity of the strong form by the cluster method (Section 6) against the oracle's
 restatement (oracle.cluster.strong_form_cluster: near partners by Lemma 4.1, admissible ones by
 Chebyshev interpolation at the point), and against the direct evaluation as the order grows."""
+import hashlib
+import importlib.util
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -120,3 +125,73 @@ def test_adaptive_loop_with_the_cluster_method():
         assert abs(ec - ed) <= 1e-4 * ed, (k, ec, ed)
         assert np.max(np.abs(clus[k]["u"] - dense[k]["u"])) <= 1e-5 * np.max(np.abs(dense[k]["u"]))
     assert all(b >= a for a, b in zip(nc, nc[1:]))
+
+
+def _golden_module():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "make_golden.py")
+    spec = importlib.util.spec_from_file_location("make_golden", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _point_leaves(h, p, cells):
+    """The leaf each cell-rule point of `cells` is grouped with by the host plan [cells, q], and the
+    leaf of every DOF."""
+    plan = F.fl_strong_form_cluster_plan(h, p["s"], p["eta"], p["leaf"], p["k_cell"])
+    cp = F.fl_cluster_plan(h, p["s"], p["eta"], p["leaf"])
+    perm = F.fl_near_region_plan(h, p["s"], 2, p["eta"], p["leaf"])["cell_perm"]
+    q = p["k_cell"] ** 2
+    pos = np.empty(len(perm), dtype=np.int64)
+    pos[perm] = np.arange(len(perm))
+    gnode = np.asarray(plan["gnode"])
+    got = gnode[plan["pgroup"][(pos[cells][:, None] * q + np.arange(q)[None, :])]]
+    node = cp["node"]
+    leaf_of = np.full(len(cp["perm"]), -1)
+    for c in range(len(node)):
+        if node[c, 2] < 0:
+            leaf_of[cp["perm"][node[c, 0]:node[c, 1]]] = c
+    return got, leaf_of
+
+
+def _sampled_cells_error(G, S_cells, point_leaf, leaf_of):
+    """(error of the points grouped as the oracle grouped them, share of such points).  A point
+    grouped otherwise must be a near-tie of its two closest DOFs (the rule's nodes may differ in the
+    last bit between machines): its value belongs to the other leaf's split and is not compared."""
+    size = np.asarray(G["size"])
+    same = point_leaf == leaf_of[np.asarray(G["closest_dof"])]
+    assert np.all(same | (np.asarray(G["gap"]) < 1e-12))
+    err = float(np.max(np.abs(S_cells - np.asarray(G["values"]))[same] / size[same]))
+    return err, float(same.mean())
+
+
+def test_cluster_strong_form_full_size_sampled_cells():
+    # L-shape level 5 (73,432 cells), the strong-form workload the benchmark times (m = 4, eta = 1,
+    # leaves of 32): the cluster strong form at the points of seeded cells, the re-entrant corner's
+    # and a convex corner's cell against the oracle's values, stored by tests/golden/make_golden.py
+    # (minutes of oracle work at this size) and recomputed here should the mesh generator give
+    # another mesh on this machine
+    mg = _golden_module()
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "strong_form_cluster_lshape5.json")) as f:
+        G = json.load(f)
+    p = G["params"]
+    V, T = synth.lshape(0.25, p["level"])
+    if mg.mesh_hash(V, T) != G["mesh_hash"]:
+        G.update(mg.strong_form_cluster_cells(V, T, p))
+    s = p["s"]
+    mesh = F.Mesh(V, T)
+    vod = np.asarray(mesh.dof_vertices(s))
+    assert hashlib.sha256(np.ascontiguousarray(vod, dtype="<i8").tobytes()).hexdigest() == G["vod_hash"]
+    u = mg.smooth_u(np.asarray(V, dtype=np.float64)[vod])
+    cells = np.asarray(G["cells"])
+    point_leaf, leaf_of = _point_leaves(mesh.h, p, cells)
+    H = F.HMatrix(mesh.h, s, m=p["m"], eta=p["eta"], leaf=p["leaf"])
+    Sg = H.strong_form(torch.tensor(u, device="cuda"), p["k_cell"], p["k_edge"], p["k_near"]).cpu().numpy()
+    H.close()
+    mesh.close()
+    err, share = _sampled_cells_error(G, Sg[cells], point_leaf, leaf_of)
+    print(f"level 5 cluster strong form, {len(cells)} cells: {err:.2e} of the terms' size "
+          f"({share:.0%} of the points grouped as the oracle grouped them)")
+    assert share >= 0.5
+    assert err <= TOL
