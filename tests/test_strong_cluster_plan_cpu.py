@@ -66,3 +66,48 @@ def test_strong_form_cluster_plan(case):
                 for p_, q_ in ((a_, b_), (b_, c_), (c_, a_)):
                     want.add((min(p_, q_), max(p_, q_)))
         assert got == want, (g, sigma)
+
+
+def test_strong_form_cluster_grouping_with_ties():
+    # L-shape level 3 (19,188 cells, 172,692 points): the bisection meshes' right isosceles cells put
+    # many rule points at equal (or, after rounding, nearly equal) distance from two DOF vertices;
+    # every point's group is still the leaf of the closest DOF with ties to the lower DOF
+    V, T = synth.lshape(0.25, 3)
+    s, eta, leaf, kc = 0.5, 1.0, 32, 3
+    h = F.fl_create(V, T)
+    try:
+        plan = F.fl_strong_form_cluster_plan(h, s, eta, leaf, kc)
+        cp = F.fl_cluster_plan(h, s, eta, leaf)
+        perm = F.fl_near_region_plan(h, s, 2, eta, leaf)["cell_perm"]
+        vod = np.asarray(F.fl_dof_vertices(h, s))
+    finally:
+        F.fl_destroy(h)
+    om = OracleMesh(V, T)
+    dov = -np.ones(om.nv, dtype=np.int64)
+    dov[vod] = np.arange(len(vod))
+    node = cp["node"]
+    leaf_of = np.full(len(vod), -1)
+    for c in range(len(node)):
+        if node[c, 2] < 0:
+            leaf_of[cp["perm"][node[c, 0]:node[c, 1]]] = c
+    X, _, _ = cell_rule_points(om, kc)
+    q = X.shape[1]
+    D = om.V[om.C][:, None, :, :] - X[:, :, None, :]   # [cells, q, 3, 2]
+    d2 = D[..., 0] ** 2 + D[..., 1] ** 2
+    dof = dov[om.C]
+    best_d = np.full((om.nc, q), np.inf)
+    best_i = np.full((om.nc, q), len(vod))
+    for j in range(3):
+        dj = np.where(dof[:, j] >= 0, 1.0, np.inf)[:, None] * d2[:, :, j]
+        ij = np.where(dof[:, j] >= 0, dof[:, j], len(vod))[:, None]
+        take = (dj < best_d) | ((dj == best_d) & (ij < best_i))
+        best_d = np.where(take, dj, best_d)
+        best_i = np.where(take, ij, best_i)
+    assert np.all(best_i < len(vod))  # every cell of this mesh has a DOF vertex
+    second = np.sort(np.where((dof >= 0)[:, None, :], d2, np.inf), axis=2)[:, :, 1]
+    ties = np.sum(second == best_d)
+    assert ties > 1000  # the tie rule decides many points
+    pos = np.empty(om.nc, dtype=np.int64)
+    pos[perm] = np.arange(om.nc)
+    got = np.asarray(plan["gnode"])[plan["pgroup"].reshape(om.nc, q)[pos]]
+    assert np.array_equal(got, leaf_of[best_i])
