@@ -56,10 +56,13 @@ INTERVAL = {"cells": 128, "s": 0.25}
 # roofline below (per-point and per-tile work is not counted)
 DW_OPS_PER_EVAL = {5: 92, 6: 88, 7: 96}
 # DRAM bytes per far pair of far_tile_dw_kernel (partial tiles and per-point row sums written,
-# cell data read): 51.9 MB read + 2810.2 MB written over 242,559,275 far pairs in one ncu
-# capture of far_tile_dw_kernel<6,2,2> on the graded disc (22043 triangles, s = 1/2); the
-# kernel's traffic grows with the far pairs (tiles and row-sum blocks both scale with N_el^2)
-FAR_DW_DRAM_BYTES_PER_PAIR = (46037248 + 2808832512) / 242559275
+# cell data read) from the last ncu capture of far_tile_dw_kernel<6,2,2> on the graded disc
+# (22043 triangles, s = 1/2): 46.0 MB read + 2808.8 MB written over 242,559,275 far pairs; the
+# kernel's traffic grows with the far pairs (tiles and row-sum blocks both scale with N_el^2).
+# The kernel has changed since that capture (per-tile row masks, optional row sums), so the
+# roofline reports no traffic until it is captured again; the old figure stays as context.
+FAR_DW_DRAM_BYTES_PER_PAIR_LAST_CAPTURE = (46037248 + 2808832512) / 242559275
+FAR_DW_TRAFFIC_CURRENT = False
 
 
 def load_peaks():
@@ -1095,7 +1098,8 @@ def main():
     clock_hz = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
     peak_ops = sms * 128 * clock_hz
     achieved = ops / (far_avg / 1000.0)
-    traffic = FAR_DW_DRAM_BYTES_PER_PAIR * stats["n_far_pairs"] if FAR_DW_DRAM_BYTES_PER_PAIR else None
+    traffic_last = FAR_DW_DRAM_BYTES_PER_PAIR_LAST_CAPTURE * stats["n_far_pairs"]
+    traffic = traffic_last if FAR_DW_TRAFFIC_CURRENT else None
     # the same evaluations on the float64 pipe: 24.7 float64 operations each (ncu, float64
     # far kernel, quasi-uniform disc), at 2 per clock and SM
     dp_roof_evals = sms * 2 * clock_hz / 24.7
@@ -1104,7 +1108,10 @@ def main():
     roofline = {"bound": "alu", "kernel": f"far_tile_dw_kernel<{pw},{shapes[variant]}>", "achieved": achieved / 1e12,
                 "peak": peak_ops / 1e12, "unit": "T FP32-ops/s", "frac": achieved / peak_ops, "traffic": traffic,
                 "evals_per_s": evals / (far_avg / 1000.0), "far_ms": far_avg, "evals_per_launch": evals,
-                "traffic_note": "ncu DRAM bytes per far pair on the graded disc x far pairs of this workload",
+                "traffic_note": ("ncu DRAM bytes per far pair on the graded disc x far pairs of this workload"
+                                 if FAR_DW_TRAFFIC_CURRENT else
+                                 "null: the kernel changed after its last ncu DRAM capture (row masks, optional row "
+                                 f"sums); that capture scaled to this workload gave {traffic_last:.4g} bytes per launch"),
                 "note": f"algorithmic FP32-pipe operations = far pairs x 256 evaluations x {DW_OPS_PER_EVAL[pw]} "
                         f"(double-word evaluation: difference, |x-y|^2, power, three weighted sums, column sum); "
                         f"peak = {sms} SMs x 128 FP32 lanes x max SM clock (of unit counts); far stage timed by CUDA "
