@@ -502,6 +502,18 @@ int fl_cluster_plan(fl_handle h, double s, double eta, int leaf, int64_t* sizes,
  */
 int fl_near_region_plan(fl_handle h, double s, double eta, int leaf, int64_t* sizes, int32_t* cell_perm,
                         int32_t* ef_ptr, int32_t* ef_fac, int32_t* ef_cls, int32_t* fac_vert, double* fac_normal);
+/*
+ * Host only, no device work: the element-block tiles of the same plan (Section 6, the near field's
+ * separated pairs at vertex-graph distance >= 2).  Blocks are 32 consecutive cells of the internal
+ * order (cell_perm above); a tile (I, J), I <= J, is listed when some inadmissible leaf pair (A, B) has
+ * a DOF of A in a cell of block I and a DOF of B in a cell of block J, or the other way round.
+ * *ntiles receives their number; with non-NULL arrays also tiles [2 ntiles] (I, J, ordered by (I, J))
+ * and rowmask [ntiles]: bit kk set when cell 32 I + kk has a DOF in a leaf that is near-paired with a
+ * leaf holding a DOF of some cell of block J (the separated pairs of the other row cells feed no
+ * near-field entry and are not computed).  Caller-owned host arrays.  Errors: FL_EINVAL, FL_ENOMEM.
+ */
+int fl_near_region_tiles(fl_handle h, double s, double eta, int leaf, int64_t* ntiles, int32_t* tiles,
+                         uint32_t* rowmask);
 
 /*
  * Builds the H-matrix of A^s on h's mesh: the plan above, then on the device the leaf

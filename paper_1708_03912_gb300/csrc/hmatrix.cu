@@ -567,6 +567,30 @@ int fl_near_region_plan(fl_handle h, double s, double eta, int leaf, int64_t* si
     return FL_OK;
 }
 
+int fl_near_region_tiles(fl_handle h, double s, double eta, int leaf, int64_t* ntiles, int32_t* tiles,
+                         uint32_t* rowmask) {
+    if (!h || !ntiles) return FL_EINVAL;
+    h->err.clear();
+    if (h->sym_K) return sym_unsupported(h, "fl_near_region_tiles");
+    const int pi = plan_for(h, s);
+    if (pi < 0) return FL_EINVAL;
+    const Plan& P = h->plan[pi];
+    try {
+        ClusterPlan C;
+        if (build_cluster_plan(P, eta, leaf, C) != FL_OK) return set_err(h, FL_EINVAL, "leaf < 1 or eta < 0");
+        HNearPlan Q;
+        std::string err;
+        const int rc = plan_hnear(P, C, Q, err);
+        if (rc != FL_OK) return set_err(h, rc, err);
+        *ntiles = (int64_t)Q.tiles.size() / 2;
+        if (tiles) std::copy(Q.tiles.begin(), Q.tiles.end(), tiles);
+        if (rowmask) std::copy(Q.rowmask.begin(), Q.rowmask.end(), rowmask);
+    } catch (const std::bad_alloc&) {
+        return set_err(h, FL_ENOMEM, "out of host memory");
+    }
+    return FL_OK;
+}
+
 int fl_strong_form_cluster_plan(fl_handle h, double s, double eta, int leaf, int k_cell, int64_t* sizes,
                                 int32_t* pgroup, int32_t* gnode, int64_t* gf_ptr, int32_t* gf_fac,
                                 int32_t* fac_vert) {

@@ -25,7 +25,7 @@ _CODES = {0: "FL_OK", 1: "FL_EINVAL", 2: "FL_ENOMEM", 3: "FL_ECUDA", 4: "FL_ENOT
 EXPORTS = ["fl_default_options", "fl_create", "fl_create_sector", "fl_destroy", "fl_last_error", "fl_num_dofs", "fl_dof_vertices",
            "fl_assemble", "fl_tune_assemble", "fl_set_far_variant", "fl_assemble_nearfield_csr", "fl_load_vector", "fl_matvec", "fl_convert", "fl_default_solve_opts", "fl_solve",
            "fl_heat_matrix", "fl_mass_apply", "fl_strong_form", "fl_br_indicators", "fl_mark_max", "fl_refine",
-           "fl_cluster_plan", "fl_near_region_plan", "fl_strong_form_cluster_plan", "fl_hmatrix_create", "fl_hmatrix_set_near",
+           "fl_cluster_plan", "fl_near_region_plan", "fl_near_region_tiles", "fl_strong_form_cluster_plan", "fl_hmatrix_create", "fl_hmatrix_set_near",
            "fl_hmatrix_matvec", "fl_hmatrix_solve", "fl_hmatrix_info", "fl_hmatrix_assemble_near", "fl_hmatrix_near_info", "fl_hmatrix_get_near",
            "fl_hmatrix_strong_form", "fl_hmatrix_br_indicators", "fl_hmatrix_solve_shifted", "fl_hmatrix_last_error", "fl_hmatrix_destroy", "fl_get_stats", "fl_set_profiling", "fl_stage_ms", "fl_launch_count", "fl_pool_trim", "fl_pool_stats",
            "fl_matvec_f32_static",
@@ -151,6 +151,8 @@ def lib():
     L.fl_cluster_plan.restype = ci
     L.fl_near_region_plan.argtypes = [vp, dbl, dbl, ci, ctypes.POINTER(i64), vp, vp, vp, vp, vp, vp]
     L.fl_near_region_plan.restype = ci
+    L.fl_near_region_tiles.argtypes = [vp, dbl, dbl, ci, ctypes.POINTER(i64), vp, vp]
+    L.fl_near_region_tiles.restype = ci
     L.fl_strong_form_cluster_plan.argtypes = [vp, dbl, dbl, ci, ci, ctypes.POINTER(i64), vp, vp, vp, vp, vp]
     L.fl_strong_form_cluster_plan.restype = ci
     L.fl_hmatrix_create.argtypes = [vp, dbl, ci, dbl, ci, ctypes.POINTER(vp), vp]
@@ -498,6 +500,17 @@ def fl_near_region_plan(h, s, dim, eta=1.0, leaf=32):
                                      out["ef_fac"].ctypes.data, out["ef_cls"].ctypes.data,
                                      out["fac_vert"].ctypes.data, out["fac_normal"].ctypes.data), h)
     return out
+
+
+def fl_near_region_tiles(h, s, eta=1.0, leaf=32):
+    """Host-only tile list of the direct near-field assembly: (tiles [ntiles, 2] int32 (I, J),
+    rowmask [ntiles] uint32) (numpy arrays)."""
+    nt = ctypes.c_int64()
+    _check(lib().fl_near_region_tiles(h, s, eta, leaf, ctypes.byref(nt), None, None), h)
+    tiles = np.zeros((nt.value, 2), dtype=np.int32)
+    rowmask = np.zeros(nt.value, dtype=np.uint32)
+    _check(lib().fl_near_region_tiles(h, s, eta, leaf, ctypes.byref(nt), tiles.ctypes.data, rowmask.ctypes.data), h)
+    return tiles, rowmask
 
 
 def fl_strong_form_cluster_plan(h, s, eta=1.0, leaf=32, k_cell=3):
