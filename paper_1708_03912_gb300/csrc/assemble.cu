@@ -1655,6 +1655,11 @@ int ensure_dense(fl_ctx* h, int pi, cudaStream_t st) {
     DevTables& t = h->dev[pi];
     FL_TRY(ensure_device(h, pi, st));
     if (t.dense_ready) return FL_OK;
+    try {
+        ensure_plan_tiles(h->plan[pi]);
+    } catch (const std::bad_alloc&) {
+        return set_err(h, FL_ENOMEM, "out of host memory for the tile list");
+    }
     const Plan& P = h->plan[pi];
     Uploads U;
     U.add(t.tiles, P.tiles);

@@ -390,7 +390,7 @@ int fl_get_stats(fl_handle h, double s, fl_stats* st) {
     o.n_vertices = P.nv;
     o.n_facets = P.nf;
     o.n_dofs = P.sym_K ? P.n_red : P.n;
-    o.n_tiles = (int64_t)P.tiles.size() / 2;
+    o.n_tiles = fl::plan_tile_count(P);
     o.n_touch_pairs = (int64_t)P.tp_type.size();
     o.n_near_pairs = (int64_t)P.np_a.size();
     int64_t nd = 0;

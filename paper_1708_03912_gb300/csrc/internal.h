@@ -54,7 +54,8 @@ struct Plan {
     std::vector<int> loc;            // nc * nvpc (internal): index into the block's L list or -1
     std::vector<int> inc_ptr, inc_ent;  // per global L position: lane*nvpc+slot entries
     int maxL = 0;
-    std::vector<int> tiles;          // ntiles * 2 (I <= J)
+    std::vector<int> tiles;          // ntiles * 2 (I <= J); empty until ensure_plan_tiles (the
+                                     // symmetry reduction's subset is built by plan_symmetry)
     std::vector<int64_t> toff;       // ntiles + 1 offsets into the partial-tile storage
     std::vector<int> occ_ptr, occ_blk, occ_loc;  // dof -> (block, local index) occurrences
     std::vector<int> ex_ptr, ex_idx; // internal cell -> sorted internal partners handled elsewhere
@@ -91,8 +92,15 @@ struct Plan {
 // centroids, with the cells flagged in `first`, if given, ahead of the rest).
 int plan_mesh(Plan& P, int dim, int64_t nv, const double* V, int64_t nc, const int32_t* C, std::string& err,
               const std::vector<char>* first = nullptr);
-// Builds the DOF-dependent part.
+// Builds the DOF-dependent part (all but the dense assembly's tile list).
 int plan_dofs(Plan& P, int paper_all, std::string& err);
+// The dense assembly's tile list: every block pair I <= J, ordered by (I, J), with the offsets of
+// their partial blocks.  Built on first use (the cluster method and the strong form never need
+// it: nblk^2 / 2 tiles, 40 M at 287 k cells); no-op once built or under the symmetry reduction.
+// May throw std::bad_alloc.
+void ensure_plan_tiles(Plan& P);
+// Number of tiles of the dense assembly, built or not.
+int64_t plan_tile_count(const Plan& P);
 // Symmetry reduction (symmetry.cpp).  replicate_sector: the K copies of a sector mesh rotated by
 // 2 pi l / K about the origin, vertices closer than 1e-10 in both coordinates merged (the
 // earliest one kept), cells copy by copy; vmap[l * nv + v] = whole vertex of copy l of v.

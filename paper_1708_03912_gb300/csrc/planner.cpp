@@ -305,16 +305,9 @@ int plan_dofs(Plan& P, int paper_all, std::string& err) {
         }
         csr_from_lists(inc, P.inc_ptr, P.inc_ent);
     }
-    // tiles (I <= J) and offsets of their partial blocks
+    // the tile list is built on first use (ensure_plan_tiles)
     P.tiles.clear();
-    P.toff.assign(1, 0);
-    for (int64_t I = 0; I < P.nblk; ++I)
-        for (int64_t J = I; J < P.nblk; ++J) {
-            P.tiles.push_back((int)I);
-            P.tiles.push_back((int)J);
-            int64_t nI = P.L_ptr[I + 1] - P.L_ptr[I], nJ = P.L_ptr[J + 1] - P.L_ptr[J];
-            P.toff.push_back(P.toff.back() + nI * nJ);
-        }
+    P.toff.clear();
     // occurrences of each DOF in block lists
     {
         std::vector<std::vector<int>> ob(P.n), ol(P.n);
@@ -705,6 +698,45 @@ int plan_dofs(Plan& P, int paper_all, std::string& err) {
         for (auto& x : th) x.join();
     }
     return FL_OK;
+}
+
+void ensure_plan_tiles(Plan& P) {
+    if (!P.tiles.empty() || P.sym_K) return;
+    const int64_t nb = P.nblk, nt = nb * (nb + 1) / 2;
+    // row I holds tiles (I, I) .. (I, nb - 1), whose partial blocks take n_I sum_{J >= I} n_J entries
+    std::vector<int64_t> suf(nb + 1, 0), row_t(nb + 1, 0), row_o(nb + 1, 0);
+    for (int64_t J = nb - 1; J >= 0; --J) suf[J] = suf[J + 1] + (P.L_ptr[J + 1] - P.L_ptr[J]);
+    for (int64_t I = 0; I < nb; ++I) {
+        row_t[I + 1] = row_t[I] + (nb - I);
+        row_o[I + 1] = row_o[I] + (int64_t)(P.L_ptr[I + 1] - P.L_ptr[I]) * suf[I];
+    }
+    P.tiles.resize(2 * nt);
+    P.toff.resize(nt + 1);
+    P.toff[nt] = row_o[nb];
+    // threads take row ranges of about equal tile counts
+    const int nthr = (int)std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
+    auto rows = [&](int t) {
+        const int64_t a = (int64_t)(std::lower_bound(row_t.begin(), row_t.end(), nt * t / nthr) - row_t.begin());
+        const int64_t b = (int64_t)(std::lower_bound(row_t.begin(), row_t.end(), nt * (t + 1) / nthr) - row_t.begin());
+        for (int64_t I = a; I < std::min(b, nb); ++I) {
+            const int64_t nI = P.L_ptr[I + 1] - P.L_ptr[I];
+            int64_t k = row_t[I], off = row_o[I];
+            for (int64_t J = I; J < nb; ++J, ++k) {
+                P.tiles[2 * k] = (int)I;
+                P.tiles[2 * k + 1] = (int)J;
+                P.toff[k] = off;
+                off += nI * (P.L_ptr[J + 1] - P.L_ptr[J]);
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nthr; ++t) th.emplace_back(rows, t);
+    rows(0);
+    for (auto& x : th) x.join();
+}
+
+int64_t plan_tile_count(const Plan& P) {
+    return (P.tiles.empty() && !P.sym_K) ? P.nblk * (P.nblk + 1) / 2 : (int64_t)P.tiles.size() / 2;
 }
 
 }  // namespace fl
