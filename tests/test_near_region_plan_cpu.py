@@ -145,3 +145,28 @@ def _far_partners(om, K):
         shared, near = om.classify_cells(K)
         _FAR_CACHE[key] = set(np.nonzero((shared == 0) & ~near)[0].tolist()) - {K}
     return _FAR_CACHE[key]
+
+
+def test_near_region_plans_reject_bad_arguments():
+    V, T = synth.disc(4)
+    h = F.fl_create(V, T)
+    try:
+        for call in (lambda: F.fl_near_region_tiles(h, 0.5, 1.0, 0),       # leaf < 1
+                     lambda: F.fl_near_region_tiles(h, 0.5, -1.0, 8),      # eta < 0
+                     lambda: F.fl_near_region_plan(h, 0.5, 2, 1.0, 0),
+                     lambda: F.fl_strong_form_cluster_plan(h, 0.5, 1.0, 8, 0)):  # k_cell < 1
+            with pytest.raises(F.FlError) as e:
+                call()
+            assert e.value.code == F.FL_EINVAL
+    finally:
+        F.fl_destroy(h)
+    # a sector handle (symmetry reduction) has no cluster plans
+    Vs, Ts = synth.sector(8, 3)
+    hs = F.fl_create_sector(Vs, Ts, 8)
+    try:
+        for call in (lambda: F.fl_near_region_tiles(hs, 0.5, 1.0, 8),
+                     lambda: F.fl_near_region_plan(hs, 0.5, 2, 1.0, 8)):
+            with pytest.raises(F.FlError):
+                call()
+    finally:
+        F.fl_destroy(hs)
