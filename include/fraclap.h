@@ -595,8 +595,6 @@ int fl_hmatrix_near_info(fl_hmatrix H, int64_t* info);
  * couplings, downward pass; fixed summation orders.  Errors: FL_EINVAL (no near field
  * yet), FL_ECUDA. */
 int fl_hmatrix_matvec(fl_hmatrix H, const double* x_dev, double* y_dev, void* stream);
-/* info[0..5]: nodes, admissible pairs, near-field leaf pairs, near-field entries, device
- * bytes held, tree depth. */
 /*
  * Solve A u = b with the cluster method's product in place of the dense one: Jacobi-PCG
  * (Section 5) on the H-matrix, the diagonal taken from the near field (exact entries), from
@@ -616,8 +614,15 @@ int fl_hmatrix_solve(fl_hmatrix H, const double* b_dev, double* u_dev, const fl_
  * fl_hmatrix_solve. */
 int fl_hmatrix_solve_shifted(fl_hmatrix H, double alpha, double beta, const double* b_dev, double* u_dev,
                              const fl_solve_opts* o, fl_solve_info* info, void* stream);
+/* info[0..5] (host, 6 int64): nodes, admissible pairs, near-field leaf pairs, near-field entries,
+ * device bytes held, tree depth.  Errors: FL_EINVAL (NULL H or info). */
 int fl_hmatrix_info(fl_hmatrix H, int64_t* info);
+/* The message of H's last failed call ("" if none; a fixed message for NULL H); owned by H, valid
+ * until its next call. */
 const char* fl_hmatrix_last_error(fl_hmatrix H);
+/* Frees H's device memory after synchronising its device (work queued by its calls completes
+ * first); NULL is a no-op.
+ * The mesh handle H was made from is not touched. */
 void fl_hmatrix_destroy(fl_hmatrix H);
 
 /* ------------------------------------------------------------------------
@@ -663,7 +668,9 @@ int fl_mg_vcycle(fl_mg_handle mg, const float* r_dev, float* z_dev, void* stream
    Returns FL_OK, FL_ENOTCONV or FL_ENOTSPD; info as for fl_solve. */
 int fl_mg_solve(fl_mg_handle mg, const double* b_dev, double* u_dev, double tol, int maxit, fl_solve_info* info,
                 void* stream);
+/* The message of mg's last failed call ("" if none or NULL mg); owned by mg. */
 const char* fl_mg_last_error(fl_mg_handle mg);
+/* Frees mg's device and pinned memory after synchronising its device; NULL is a no-op. */
 void fl_mg_destroy(fl_mg_handle mg);
 
 /* ------------------------------------------------------------------------
@@ -685,6 +692,8 @@ typedef struct fl_lp* fl_lp_handle;
    hidden layers seeded (splitmix64 / Box-Muller, variance 1/fan-in), output layer zero
    (the Jacobi preconditioner).  `mesh` must outlive the handle. */
 int fl_lp_create(fl_lp_handle* lp, fl_handle mesh, double s, int K, int hidden, uint64_t seed);
+/* Sizes of lp (0 for NULL lp): float32 parameters (the layout below), floats per training sample
+   row (G = 2K + 3 geometry features and the K + 1 stencil inputs: 40), samples collected so far. */
 int64_t fl_lp_num_params(fl_lp_handle lp);
 int fl_lp_num_features(fl_lp_handle lp);
 int64_t fl_lp_num_samples(fl_lp_handle lp);
@@ -722,7 +731,9 @@ int fl_lp_collect_noise(fl_lp_handle lp, const double* A_dev, int64_t lda, int c
 /* Adam (0.9, 0.999, 1e-8) on mini-batches drawn from the training set with splitmix64(seed,
    step, slot); *loss_host = loss of the last batch. */
 int fl_lp_train(fl_lp_handle lp, int steps, int64_t batch, float lr, uint64_t seed, float* loss_host, void* stream);
+/* The message of lp's last failed call ("" if none or NULL lp); owned by lp. */
 const char* fl_lp_last_error(fl_lp_handle lp);
+/* Frees lp's device memory after synchronising its device; NULL is a no-op. */
 void fl_lp_destroy(fl_lp_handle lp);
 
 typedef struct fl_fcg_info {
@@ -781,14 +792,19 @@ int fl_tune_batch(fl_handle h, int nprob, const fl_batch_problem* probs, int rep
 int fl_tune_matvec(int dtype, const void* A_dev, int64_t lda, int64_t n, const double* x_dev,
                    double* y_dev, int reps, int* best_per_sm, double* best_ms, void* stream);
 
+/* Sets the entry (current device, kernel, n, nrhs, nslices) of the process-wide tuning table to
+   (p0, p1, ms), replacing an earlier one.  Thread-safe.  FL_EINVAL for an empty kernel name or n < 1. */
 int fl_tune_record(const char* kernel, int64_t n, int nrhs, int nslices, int p0, int p1, double ms);
 /* FL_OK and the parameters if the current device has an entry, else FL_ENOTIMPL. */
 int fl_tune_lookup(const char* kernel, int64_t n, int nrhs, int nslices, int* p0, int* p1);
+/* Empty the table / the number of its entries (all devices). */
 void fl_tune_clear(void);
 int fl_tune_count(void);
 /* Write / merge the table as JSON: {"entries": [{"device", "kernel", "n", "nrhs", "nslices",
    "p0", "p1", "ms"}, ...]}.  FL_EINVAL on I/O or format errors. */
 int fl_tune_save(const char* path);
+/* Merge a saved table: each entry replaces the one with the same key (device, kernel, n, nrhs,
+   nslices).  FL_EINVAL if the file cannot be read or parsed (the table is then unchanged). */
 int fl_tune_load(const char* path);
 
 /* ------------------------------------------------------------------------
